@@ -1,0 +1,73 @@
+"""FP64 oracle for Algorithm 1 (linearized plug-and-play ADMM).  TEST INFRASTRUCTURE ONLY.
+
+Algorithm 1, step by step, with mu = 1/(alpha + rho):
+    x <- mu (alpha x + rho (v - u) - grad f(x))
+    x <- Pi_C(x)
+    v <- D(x + u)
+    u <- u + (x - v)
+D is DSG-NLM with a fixed W (the F-DSG-NLM variant of Sec. 4: W built once from a
+guide and then frozen).  The initial values are x = v = clip(guide, 0, 1), u = 0.
+
+Residuals (Sec. 4, Tables 2-3, following Boyd et al.): primal ||x - v|| / sqrt(n)
+and dual rho ||v^k - v^{k-1}|| / sqrt(n), reported as RMS values.  PSNR uses peak 1
+over all pixels.
+
+Parity status: with W = I and C = R^n the loop is gradient descent
+x <- x - mu grad f(x); that case is pinned against an explicit dense-matrix
+iteration.  With a fixed DSG-NLM W and alpha above the Lipschitz constant the
+residuals decay (convergence of linearized ADMM, Sec. 2); that is checked as a
+property.  End-to-end PSNR values are parity unpinned (the paper's test images
+are not available).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+NONE, NONNEG, BOX01 = 0, 1, 2
+
+
+def project(x: np.ndarray, constraint: int) -> np.ndarray:
+    """Orthogonal projection Pi_C onto R^n, R^n_+ or [0, 1]^n (Sec. 2)."""
+    if constraint == NONE:
+        return x
+    if constraint == NONNEG:
+        return np.maximum(x, 0.0)
+    if constraint == BOX01:
+        return np.clip(x, 0.0, 1.0)
+    raise ValueError(constraint)
+
+
+def rms(a: np.ndarray) -> float:
+    return float(np.sqrt(np.mean(np.asarray(a, dtype=np.float64) ** 2)))
+
+
+def psnr(x: np.ndarray, ref: np.ndarray) -> float:
+    mse = float(np.mean((np.asarray(x, np.float64) - np.asarray(ref, np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
+
+
+def lpnp_solve(grad_f, denoise, x, v, u, alpha, rho, iters, constraint, x_true=None):
+    """Algorithm 1.  ``grad_f(x)`` and ``denoise(z)`` act on images.  Returns
+    (x, v, u, history) with history[k] = (primal, dual, psnr or None)."""
+    x = np.asarray(x, dtype=np.float64).copy()
+    v = np.asarray(v, dtype=np.float64).copy()
+    u = np.asarray(u, dtype=np.float64).copy()
+    mu = 1.0 / (alpha + rho)
+    hist = []
+    for _ in range(iters):
+        x = mu * (alpha * x + rho * (v - u) - grad_f(x))
+        x = project(x, constraint)
+        v_prev = v
+        v = denoise(x + u)
+        u = u + (x - v)
+        hist.append((rms(x - v), rho * rms(v - v_prev),
+                     None if x_true is None else psnr(x, x_true)))
+    return x, v, u, hist
+
+
+def initial_state(guide: np.ndarray):
+    """x = v = clip(guide, 0, 1), u = 0."""
+    x0 = np.clip(np.asarray(guide, dtype=np.float64), 0.0, 1.0)
+    return x0.copy(), x0.copy(), np.zeros_like(x0)

@@ -1,0 +1,70 @@
+"""FP64 oracle: the experiments of Sec. 4 assembled end to end.  TEST INFRASTRUCTURE ONLY.
+
+Builds a synthetic instance (ground truth from ``synthetic``), its measurements
+with the oracle's own forward models, and runs Algorithm 1 with a fixed DSG-NLM W.
+The measurements handed to the CUDA path in the tests are the FP32 roundings of
+the values made here, so both sides start from identical inputs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import synthetic
+from . import dsgnlm, forward, lpnp
+
+
+def sr_instance(wl: dict, H: int | None = None, W: int | None = None, seed: int | None = None):
+    """Ground truth, FP32 observation y = A x + n and the FP32 noise used."""
+    H = wl["H"] if H is None else H
+    W = wl["W"] if W is None else W
+    seed = wl["seed"] if seed is None else seed
+    x_true = synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], seed)
+    noise = synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], seed)
+    psf = forward.gaussian_psf(wl["blur_sigma"], wl["blur_r"])
+    y = forward.sr_observe(x_true, noise, psf).astype(np.float32)
+    return dict(x_true=x_true, noise=noise, y=y, psf=psf)
+
+
+def spi_instance(wl: dict, H: int | None = None, W: int | None = None, seed: int | None = None):
+    """Ground truth, FP32 arrivals, the binary sub-pixel image and the counts."""
+    H = wl["H"] if H is None else H
+    W = wl["W"] if W is None else W
+    seed = wl["seed"] if seed is None else seed
+    ks = wl["K_side"]
+    x_true = synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], seed)
+    arrivals = synthetic.photon_arrivals((ks * H, ks * W), seed)
+    bits = forward.spi_observe(x_true, arrivals, ks, wl["eta"])
+    counts = forward.spi_counts(bits, ks)
+    return dict(x_true=x_true, arrivals=arrivals, bits=bits, counts=counts)
+
+
+def solve_sr(wl: dict, inst: dict, iters: int | None = None, tol: float | None = None,
+             maxit: int = 10000, guide=None):
+    """Algorithm 1 for 2x super-resolution with F-DSG-NLM built from the guide."""
+    psf = inst["psf"]
+    y = inst["y"].astype(np.float64)
+    g = forward.sr_guide(y) if guide is None else np.asarray(guide, np.float64)
+    W, info = dsgnlm.build_w(g, wl["patch_r"], wl["search_r"], wl["h"],
+                             wl["tol"] if tol is None else tol, maxit)
+    x0, v0, u0 = lpnp.initial_state(g)
+    out = lpnp.lpnp_solve(lambda x: forward.sr_grad(x, y, psf),
+                          lambda z: dsgnlm.denoise(W, z), x0, v0, u0,
+                          wl["alpha"], wl["rho"], wl["iters"] if iters is None else iters,
+                          lpnp.BOX01, inst["x_true"])
+    return dict(guide=g, W=W, info=info, x=out[0], v=out[1], u=out[2], hist=out[3])
+
+
+def solve_spi(wl: dict, inst: dict, iters: int | None = None, tol: float | None = None,
+              maxit: int = 10000, guide=None):
+    """Algorithm 1 for single-photon imaging with F-DSG-NLM built from the guide."""
+    K = wl["K_side"] ** 2
+    counts = inst["counts"]
+    g = forward.spi_guide(counts, wl["eta"], K) if guide is None else np.asarray(guide, np.float64)
+    W, info = dsgnlm.build_w(g, wl["patch_r"], wl["search_r"], wl["h"],
+                             wl["tol"] if tol is None else tol, maxit)
+    x0, v0, u0 = lpnp.initial_state(g)
+    out = lpnp.lpnp_solve(lambda x: forward.spi_grad(x, counts, wl["eta"], K, wl["spi_eps"]),
+                          lambda z: dsgnlm.denoise(W, z), x0, v0, u0,
+                          wl["alpha"], wl["rho"], wl["iters"] if iters is None else iters,
+                          lpnp.BOX01, inst["x_true"])
+    return dict(guide=g, W=W, info=info, x=out[0], v=out[1], u=out[2], hist=out[3])

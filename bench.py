@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of linearized plug-and-play ADMM with the DSG-NLM denoiser.
+
+Workload (one "step" = one pass of the whole method over one image): 2x
+super-resolution of a 512x512 synthetic piecewise-smooth image (40 shapes +
+band-limited texture), 9x9 Gaussian blur (sigma 1), decimation by 2, noise sigma
+0.02; guide = Keys cubic upsampling of the observation; DSG-NLM with 7x7 patches,
+21x21 search window, h = 0.08, balanced to 1e-6; 30 iterations of Algorithm 1.
+
+Metric: restored megapixels per second of whole solves (guide + weight build +
+balance + 30 iterations), with PnP iterations/s alongside.  Under torchrun every
+rank solves its own instance (independent problems, no collective on the data
+path: weak scaling); time is the max over ranks.
+
+--impl reference times the FP64 CPU oracle (the only reference this method has)
+on bounded crops of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "sr512"
+METRIC = "DSG-NLM + linearized PnP-ADMM restored Mpix/s (2x SR 512^2, whole solve)"
+UNIT = "Mpix/s"
+L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one apply_dual launch from an ncu capture of the
+# full 512x512 workload, with the hash of the kernel source it was taken on; the
+# figure is reported only while the source is unchanged.
+NCU_TRAFFIC = {"stencil.cu": None, "bytes": None}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload_config(wl):
+    return {
+        "workload": f"{WORKLOAD}: 2x super-resolution {wl['H']}x{wl['W']}, patch 7x7, search 21x21, "
+                    f"h={wl['h']}, balance tol {wl['tol']}, {wl['iters']} PnP iterations",
+        "H": wl["H"], "W": wl["W"], "patch": 2 * wl["patch_r"] + 1, "search": 2 * wl["search_r"] + 1,
+        "h": wl["h"], "tol": wl["tol"], "pnp_iters": wl["iters"], "rho": wl["rho"], "alpha": wl["alpha"],
+        "weights": "fp32 half-window planes",
+        "l2": "flushed between timed steps (256 MiB write); weight planes 231 MB > L2",
+        "parallelism": "replicas (one independent instance per GPU)",
+    }
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", self.gpu], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def _gpu_index():
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local < len(ids):
+            return ids[local]
+    return str(local)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def _traffic():
+    src = os.path.join(ROOT, "paper_1901_06110_gb300", "csrc", "stencil.cu")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    if NCU_TRAFFIC["stencil.cu"] == h:
+        return NCU_TRAFFIC["bytes"]
+    return None
+
+
+# ----------------------------------------------------------------------------- oracle
+
+def _oracle_solve_seconds(side: int, wl: dict) -> float:
+    """Time the FP64 oracle on one side x side instance of the workload."""
+    import numpy as np
+
+    from oracle import dsgnlm as odsg
+    from oracle import forward as ofw
+    from oracle import lpnp as olp
+    from oracle import problems
+    inst = problems.sr_instance(wl, H=side, W=side)
+    t0 = time.perf_counter()
+    y = inst["y"].astype(np.float64)
+    g = ofw.sr_guide(y)
+    Wm, _ = odsg.build_w(g, wl["patch_r"], wl["search_r"], wl["h"], wl["tol"], 10000)
+    x0, v0, u0 = olp.initial_state(g)
+    olp.lpnp_solve(lambda x: ofw.sr_grad(x, y, inst["psf"]), lambda z: odsg.denoise(Wm, z),
+                   x0, v0, u0, wl["alpha"], wl["rho"], wl["iters"], olp.BOX01)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    import synthetic
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = synthetic.workload(WORKLOAD)
+    # size the crop so that warmup + steps take about two minutes in total
+    t64 = _oracle_solve_seconds(64, wl)
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    side = int(64 * math.sqrt(max(per_step, 1e-3) / t64))
+    side = max(32, min(512, side - side % 16))
+    for _ in range(args.warmup):
+        _oracle_solve_seconds(side, wl)
+    total = 0.0
+    for _ in range(args.steps):
+        total += _oracle_solve_seconds(side, wl)
+    ms = 1e3 * total / max(1, args.steps)
+    value = (side * side / 1e6) / (ms / 1e3)
+    cfg = _workload_config(wl)
+    cfg["sample"] = f"{side}x{side} crop per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 NumPy/SciPy oracle, {side}x{side} instance of the workload "
+                                   f"per step (single-threaded)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synthetic
+    from paper_1901_06110_gb300 import _abi
+    from paper_1901_06110_gb300 import build as lib_build
+    from paper_1901_06110_gb300 import dsgnlm as D
+    from paper_1901_06110_gb300 import pipeline
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    lib_build.build()
+    wl = synthetic.workload(WORKLOAD)
+    H, W = wl["H"], wl["W"]
+    seed = wl["seed"] + 1000 * rank
+    x_true = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], seed)).cuda()
+    noise = torch.from_numpy(synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], seed)).cuda()
+    y = D.lpnp_sr_observe(x_true, noise, wl["blur_sigma"], wl["blur_r"])
+    params = pipeline.Params.from_workload(wl)
+    solver = pipeline.Solver(H, W, params)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        solver.run(y)
+    torch.cuda.synchronize()
+
+    # --- device-resident timed region
+    sampler = ClockSampler(_gpu_index())
+    D.dsgnlm_profile_enable(solver.den, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = D.dsgnlm_launch_count()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict L2 between steps (outside the events)
+        starts[k].record()
+        solver.run(y)
+        ends[k].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = D.dsgnlm_launch_count() - launches0
+    barrier()
+    clocks = sampler.stop()
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    apply_ms, apply_n = D.dsgnlm_profile_read(solver.den, _abi.PROF_APPLY)
+    build_ms, build_n = D.dsgnlm_profile_read(solver.den, _abi.PROF_BUILD)
+    bal_ms, bal_n = D.dsgnlm_profile_read(solver.den, _abi.PROF_BALANCE)
+    xu_ms, xu_n = D.dsgnlm_profile_read(solver.den, _abi.PROF_XUPDATE)
+    D.dsgnlm_profile_enable(solver.den, False)
+    st, bal_updates, bal_res = solver.balance
+    if world > 1:
+        t = torch.tensor([step_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    # --- end to end through the public API with host buffers
+    y_host = torch.empty_like(y, device="cpu").pin_memory()
+    y_host.copy_(y)
+    x_host = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    y_dev = torch.empty_like(y)
+    e2e_steps = max(1, min(args.steps, 100))
+    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
+    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(e2e_steps):
+        flush.fill_(float(k))
+        e_s[k].record()
+        y_dev.copy_(y_host, non_blocking=True)
+        solver.run(y_dev)
+        x_host.copy_(solver.x, non_blocking=True)
+        e_e[k].record()
+        e_e[k].synchronize()
+    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    assert bool(torch.isfinite(solver.x).all())
+
+    n_mpix = H * W / 1e6
+    value = world * n_mpix / (step_ms / 1e3)
+    nh = 2 * wl["search_r"] * (wl["search_r"] + 1)
+    # algorithmic bytes of one apply_dual launch: each weight plane value once
+    # (4 n_h B/px), z and d (8 B/px), v and u read and written (16 B/px)
+    apply_bytes = H * W * (4 * nh + 24)
+    apply_avg_s = apply_ms / max(1, apply_n) / 1e3
+    peak, peak_src = _peaks()
+    achieved = apply_bytes / apply_avg_s / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _workload_config(wl),
+        "pnp_iters_per_s": world * wl["iters"] / (step_ms / 1e3),
+        "roofline": {"bound": "hbm", "kernel": "apply_dual (v <- W z, u <- z - v, residual sums)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": _traffic(), "bytes_per_launch": apply_bytes,
+                     "avg_us": apply_avg_s * 1e6, "launches": apply_n, "peak_source": peak_src},
+        "phases_ms_per_step": {"build": build_ms / args.steps, "balance": bal_ms / args.steps,
+                               "xupdate": xu_ms / args.steps, "apply": apply_ms / args.steps,
+                               "balance_passes_per_step": bal_n / args.steps,
+                               "balance_updates": bal_updates, "balance_residual": bal_res},
+        "gpu_launches": int(launches),
+        "wall_s_timed": wall,
+        "clocks": clocks,
+        "e2e": {"value": world * n_mpix / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": y.numel() * 4, "d2h_bytes_per_step": H * W * 4},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        side = 192
+        secs = _oracle_solve_seconds(side, wl)
+        line["cpu_baseline"] = {"value": (side * side / 1e6) / secs, "unit": UNIT, "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"FP64 NumPy/SciPy oracle, one {side}x{side} instance of the "
+                                          f"workload ({secs:.1f} s, single-threaded)"}
+    if rank == 0:
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * dsgnlm.h -- C ABI of the GB300 (sm_103a) library for doubly stochastic nonlocal
+ * means (DSG-NLM) and linearized plug-and-play ADMM.
+ *
+ * The method is that of Unni, Ghosh and Chaudhury, "Linearized ADMM and Fast
+ * Nonlocal Denoising for Efficient Plug-and-Play Restoration": the denoiser is
+ * W z with W the symmetric, doubly stochastic matrix obtained from the NLM kernel
+ * by the hat window (Eq. S1), symmetric normalisation (Eq. S2) and the scaling
+ * and diagonal closure of Eq. S3, computed without storing W as a matrix
+ * (Algorithm 2); the outer solver is Algorithm 1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Images are FP32, row-major [H][W] (row i, column j at i*W + j), contiguous.
+ * - Pointers documented as "device" must be device (or managed) memory on the
+ *   current CUDA device, 16-byte aligned for FP32/weight arrays.  "host" pointers
+ *   are ordinary host memory.
+ * - Buffers passed in are owned by the caller and are never freed by the library.
+ *   A dsgnlm_t handle owns its weight planes and its scratch; dsgnlm_destroy frees
+ *   them.
+ * - All work is issued on the handle's CUDA stream (or the stream argument) and is
+ *   asynchronous unless an entry point returns host values, in which case it
+ *   synchronises that stream before returning.
+ * - Errors are reported by the return code only; nothing aborts or prints.  After
+ *   DSGNLM_ECUDA, dsgnlm_last_cuda_error() returns the CUDA error code.
+ * - One handle must not be used from two host threads at once.
+ */
+#ifndef DSGNLM_H
+#define DSGNLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dsgnlm* dsgnlm_t;
+
+typedef enum dsgnlm_status {
+    DSGNLM_OK = 0,
+    DSGNLM_EINVAL = 1,         /* bad argument: null pointer, size or radius out of range,
+                                  misaligned pointer, unknown enum value */
+    DSGNLM_ENOMEM = 2,         /* a device allocation failed */
+    DSGNLM_ECUDA = 3,          /* a CUDA runtime call or launch failed */
+    DSGNLM_NOT_BUILT = 4,      /* balance/apply/solve before dsgnlm_build */
+    DSGNLM_NOT_BALANCED = 5,   /* apply/solve before dsgnlm_balance */
+    DSGNLM_NOT_CONVERGED = 6,  /* balance made maxit updates with the residual above tol;
+                                  W is still exactly symmetric and doubly stochastic */
+    DSGNLM_STALLED = 7,        /* the balance residual stopped decreasing above tol (the
+                                  FP32 floor of the scaling); W is still doubly stochastic */
+    DSGNLM_TIMEOUT = 8         /* a bounded device-side wait gave up */
+} dsgnlm_status;
+
+/* storage type of the weight planes */
+enum { DSGNLM_F32 = 0, DSGNLM_F16 = 1, DSGNLM_BF16 = 2 };
+
+/* limits of the kernels (shared-memory tiles are sized from them) */
+enum { DSGNLM_MAX_PATCH_R = 10, DSGNLM_MAX_SEARCH_R = 24 };
+
+/* ---------------------------------------------------------------------------
+ * Denoiser handle
+ * ------------------------------------------------------------------------- */
+
+/* Create a handle whose work runs on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and whose weight planes are stored as `weight_dtype` (DSGNLM_F32, _F16 or
+ * _BF16; the arithmetic is FP32 in every case).  *out receives the handle. */
+dsgnlm_status dsgnlm_create(dsgnlm_t* out, void* stream, int weight_dtype);
+
+/* Release the handle and everything it owns.  Synchronises its stream first. */
+void dsgnlm_destroy(dsgnlm_t h);
+
+/* Rebind the handle to another stream. */
+dsgnlm_status dsgnlm_set_stream(dsgnlm_t h, void* stream);
+
+/* Weight build (Eq. NLM and Eq. S1; first aggregation of Algorithm 2; fast patch
+ * distances of Sec. 3 whose cost does not grow with the patch size).
+ *
+ * guide      device, [H][W] FP32: the image the patches are taken from.
+ * patch_r    patch radius: patches are N_p x N_p with N_p = 2*patch_r + 1 (0..10).
+ * search_r   search radius N_s: the window is (2 N_s + 1)^2, clipped at the image
+ *            border (0..24).
+ * bandwidth  h > 0: k_{s,r} = exp(-||P_s - P_r||^2 / (2 N_p^2 h^2)).
+ *
+ * Patch pixels outside the image read the guide under half-sample symmetric
+ * reflection.  For each of the n_h = 2 N_s (N_s + 1) offsets o of the half window
+ * (o_y > 0, or o_y = 0 and o_x > 0) the handle stores the plane
+ *     K1(s, s + o) = Lambda(o / (N_s + 1)) k_{s, s+o}   (0 where s + o is outside),
+ * laid out [n_h][H][W] in the handle's weight dtype.  The other half of the window
+ * follows from the symmetry K1(s, s - o) = K1(s - o, s) and the diagonal is 1.
+ * (Re)allocates the planes if the size changed; clears any previous balance. */
+dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W,
+                           int patch_r, int search_r, float bandwidth);
+
+/* Balance (Eq. S2 iterated as symmetric Sinkhorn-Knopp, then Eq. S3; second
+ * aggregation of Algorithm 2).
+ *
+ * From d = 1, repeats d <- sqrt(d / (K1 d)) until max_s |d_s (K1 d)_s - 1| <= tol
+ * or `maxit` updates were made.  maxit = 1 gives d = g^{-1/2} (g the row sums of
+ * K1), i.e. exactly the paper's one-shot normalisation.  Then m = max_s d_s (K1 d)_s
+ * and the denoiser is W = diag(d) K1 diag(d) / m with the diagonal closed so that
+ * every row sums to one (Eq. S3).  W is symmetric and doubly stochastic for any d.
+ * The residual is reduced in FP64 from FP32 scalings; if it stops decreasing (three
+ * passes without a 1% improvement) above tol the balance stops with STALLED.
+ *
+ * iters_out  host, optional: number of updates made.
+ * resid_out  host, optional: the final residual max_s |d_s (K1 d)_s - 1|.
+ * Synchronises the stream.  Returns OK, NOT_CONVERGED or STALLED (all leave a
+ * usable W), NOT_BUILT, EINVAL (tol < 0, maxit < 0) or a CUDA error. */
+dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit,
+                             int* iters_out, double* resid_out);
+
+/* Apply y = W x (third aggregation of Algorithm 2).
+ * x, y  device, [H][W] FP32; y must not alias x.  Asynchronous. */
+dsgnlm_status dsgnlm_apply(dsgnlm_t h, const float* x, float* y);
+
+/* Diagnostics for tests: copy the weight planes ([n_h][H][W], weight dtype) to the
+ * device buffer dst; copy the final scaling d ([H][W] FP32) to the device buffer
+ * d_dst and m to *m_host.  dsgnlm_copy_scaling synchronises the stream. */
+dsgnlm_status dsgnlm_copy_weights(dsgnlm_t h, void* dst);
+dsgnlm_status dsgnlm_copy_scaling(dsgnlm_t h, float* d_dst, double* m_host);
+
+/* Number of half-window offsets n_h of the current build (0 before a build). */
+int dsgnlm_num_offsets(dsgnlm_t h);
+
+/* ---------------------------------------------------------------------------
+ * Forward models, measurements and guides (Sec. 4)
+ * ------------------------------------------------------------------------- */
+
+/* Super-resolution observation y = A x + n (Sec. 4.1): periodic blur by the
+ * normalised (2 blur_r + 1)^2 Gaussian of std blur_sigma, keep pixels (2i, 2j),
+ * add `noise`.  x device [H][W]; noise, y device [H/2][W/2]; H, W even.
+ * noise may be NULL (y = A x). */
+dsgnlm_status lpnp_sr_observe(const float* x, const float* noise, int H, int W,
+                              float blur_sigma, int blur_r, float* y, void* stream);
+
+/* Guide for super-resolution: 2x Keys cubic (a = -0.5) interpolation of y with
+ * periodic wrap, low-resolution sample j at high-resolution 2j.
+ * y device [h][w]; guide device [2h][2w]. */
+dsgnlm_status lpnp_sr_guide(const float* y, int h, int w, float* guide, void* stream);
+
+/* Single-photon measurement (Sec. 4.2): pixel i has K = k_side^2 sub-pixels; a
+ * sub-pixel reads one iff its first photon arrival E ~ Exp(1) (`arrivals`) is
+ * below the rate eta x_i / K, i.e. iff its Poisson count is >= 1.  The rate is
+ * formed in FP32 as (eta * x_i) / K.
+ * x device [H][W]; arrivals device FP32 and bits device uint8, [k_side H][k_side W]. */
+dsgnlm_status lpnp_spi_observe(const float* x, const float* arrivals, int H, int W,
+                               int k_side, float eta, uint8_t* bits, void* stream);
+
+/* K1_i: number of ones among the k_side x k_side sub-pixels of pixel i (Sec. 4.2).
+ * bits device uint8 in {0, 1}, [k_side H][k_side W]; counts device uint8 [H][W].
+ * k_side in 1..15. */
+dsgnlm_status lpnp_spi_counts(const uint8_t* bits, int H, int W, int k_side,
+                              uint8_t* counts, void* stream);
+
+/* Guide for single-photon imaging: per-pixel maximum-likelihood intensity
+ * -(K/eta) log(1 - K1/K) clipped to [0, 1], then a 3x3 mean with symmetric
+ * reflection.  counts device uint8 [H][W]; guide device [H][W]. */
+dsgnlm_status lpnp_spi_guide(const uint8_t* counts, int H, int W, int K, float eta,
+                             float* guide, void* stream);
+
+/* Initial state of Algorithm 1: x = v = clip(guide, 0, 1), u = 0 (n pixels). */
+dsgnlm_status lpnp_init(const float* guide, int n, float* x, float* v, float* u,
+                        void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Linearized plug-and-play ADMM (Algorithm 1)
+ * ------------------------------------------------------------------------- */
+
+enum { LPNP_SR2 = 0, LPNP_SPI = 1 };
+enum { LPNP_C_NONE = 0, LPNP_C_NONNEG = 1, LPNP_C_BOX01 = 2 };
+
+typedef struct lpnp_problem {
+    int kind;              /* LPNP_SR2 (2x super-resolution) or LPNP_SPI */
+    int H, W;              /* high-resolution image size (even for LPNP_SR2) */
+    /* LPNP_SR2: f(x) = 1/2 ||y - A x||^2 (Eq. dataterm), grad f = A^T (A x - y) */
+    const float* y;        /* device [H/2][W/2] observation */
+    float blur_sigma;      /* std of the Gaussian blur */
+    int blur_r;            /* blur radius (taps 2 r + 1 per axis), 0..8 */
+    /* LPNP_SPI: f(x) = sum_i h(x_i) (Eq. obj), grad evaluated at max(x_i, spi_eps) */
+    const uint8_t* counts; /* device [H][W] one-counts K1_i */
+    int K;                 /* sub-pixels per pixel */
+    float eta;             /* sensor gain */
+    float spi_eps;         /* floor of x inside h' (h' is unbounded at 0) */
+    int constraint;        /* LPNP_C_NONE, _NONNEG or _BOX01 (the set C of Pi_C) */
+    float alpha;           /* linearization weight; > Lipschitz constant of grad f */
+    dsgnlm_t den;          /* built and balanced denoiser (F-DSG-NLM: W fixed) */
+    float* x;              /* device [H][W], in: initial x, out: final x */
+    float* v;              /* device [H][W], in/out */
+    float* u;              /* device [H][W], in/out (scaled multiplier) */
+    double* resid_hist;    /* host [iters][2] or NULL: RMS primal ||x - v|| / sqrt(n)
+                              and dual rho ||v - v_prev|| / sqrt(n) per iteration */
+} lpnp_problem;
+
+/* grad f(x) of the problem's data term (debug/tests).  x, grad device [H][W]. */
+dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad);
+
+/* Run `iters` iterations of Algorithm 1 with penalty rho > 0, mu = 1/(alpha + rho):
+ *   x <- Pi_C(mu (alpha x + rho (v - u) - grad f(x)));  v <- W (x + u);  u <- u + x - v.
+ * Uses p->den's handle stream.  Synchronises only if resid_hist is given.  The
+ * iteration sequence is recorded once into a CUDA graph per (problem, iters) and
+ * replayed on later calls with the same buffers. */
+dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters);
+
+/* ---------------------------------------------------------------------------
+ * Misc
+ * ------------------------------------------------------------------------- */
+
+/* Per-kernel timing.  While enabled, the handle brackets each launch of the listed
+ * kinds with CUDA events on its stream (DSGNLM_PROF_XUPDATE covers the data-term
+ * kernels of one iteration of Algorithm 1).  Enabling (or re-enabling) clears the
+ * records.  dsgnlm_profile_read synchronises the stream and returns the summed
+ * event time in milliseconds and the number of timed launches of one kind. */
+enum { DSGNLM_PROF_BUILD = 0, DSGNLM_PROF_BALANCE = 1, DSGNLM_PROF_APPLY = 2, DSGNLM_PROF_XUPDATE = 3 };
+dsgnlm_status dsgnlm_profile_enable(dsgnlm_t h, int enable);
+dsgnlm_status dsgnlm_profile_read(dsgnlm_t h, int kind, double* total_ms, int* launches);
+
+/* Total number of kernels this library has launched in this process (a graph
+ * replay counts each of its kernel nodes). */
+uint64_t dsgnlm_launch_count(void);
+
+/* CUDA error code (cudaError_t) of the most recent DSGNLM_ECUDA in this thread. */
+int dsgnlm_last_cuda_error(void);
+
+/* Static description of a status code. */
+const char* dsgnlm_strerror(dsgnlm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSGNLM_H */

@@ -99,6 +99,26 @@ def kernel_matrix(guide: np.ndarray, patch_r: int, search_r: int, h: float) -> s
     return K1
 
 
+def kernel_row(guide: np.ndarray, patch_r: int, search_r: int, h: float, s):
+    """One row of K1: {r: K1(s, r)} for the r of Omega_s, computed pixel by pixel
+    from the patch definition (for sampled checks on images too large for the
+    sparse matrix)."""
+    guide = np.asarray(guide, dtype=np.float64)
+    H, W = guide.shape
+    Np = 2 * patch_r + 1
+    t = np.arange(-patch_r, patch_r + 1)
+    ps = guide[np.ix_(sym_index(s[0] + t, H), sym_index(s[1] + t, W))]
+    row = {}
+    for oy, ox in window_offsets(search_r):
+        r = (s[0] + oy, s[1] + ox)
+        if not (0 <= r[0] < H and 0 <= r[1] < W):
+            continue
+        pr = guide[np.ix_(sym_index(r[0] + t, H), sym_index(r[1] + t, W))]
+        D = float(np.sum((ps - pr) ** 2))
+        row[r] = hat(oy, ox, search_r) * np.exp(-D / (2.0 * Np * Np * h * h))
+    return row
+
+
 def sinkhorn(K1: sp.spmatrix, tol: float, maxit: int):
     """Symmetric Sinkhorn-Knopp on K1 (Eq. S2 iterated).
 

@@ -1,0 +1,491 @@
+// C ABI implementation: handle management, argument checks, the balancing control
+// loop and the Algorithm 1 iteration loop.  Only host code lives here; every step
+// of the method runs in the kernels of build.cu, stencil.cu and lpnp.cu.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dsgnlm.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace dsg {
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace dsg
+
+using namespace dsg;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+dsgnlm_status fail_cuda(cudaError_t e) {
+    g_last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? DSGNLM_ENOMEM : DSGNLM_ECUDA;
+}
+
+#define DSG_CK(expr)                                  \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) return fail_cuda(e_);  \
+    } while (0)
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        if (n == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T> T* as() const { return (T*)p; }
+};
+
+size_t weight_elem_bytes(int dtype) { return dtype == DSGNLM_F32 ? 4 : 2; }
+
+// CUDA event pairs recorded around the launches of one kernel kind while
+// profiling is enabled.
+struct ProfPool {
+    std::vector<cudaEvent_t> ev;
+    int used = 0;  // pairs recorded since the last reset
+    static constexpr int kMaxPairs = 1 << 16;
+    void release() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        ev.clear();
+        used = 0;
+    }
+};
+
+constexpr int kProfKinds = 4;
+
+}  // namespace
+
+struct dsgnlm {
+    cudaStream_t stream = nullptr;
+    int dtype = DSGNLM_F32;
+    int H = 0, W = 0, rp = 0, rs = 0, nh = 0;
+    float bw = 0.f;
+    bool built = false, balanced = false;
+    DevBuf planes, dbuf[2], stats, ctl;
+    float* d_final = nullptr;
+    double m = 1.0;
+    float inv_m = 1.f;
+    int iters = 0;
+    double resid = 0.0;
+    // Algorithm 1 workspace
+    DevBuf z, rlo, partials, arrive, hist;
+    // optional per-kernel timing
+    bool prof = false;
+    ProfPool pools[kProfKinds];
+    // pinned host staging for small device->host reads
+    void* host_stage = nullptr;
+    size_t host_stage_bytes = 0;
+
+    cudaError_t stage(size_t n) {
+        if (n <= host_stage_bytes) return cudaSuccess;
+        if (host_stage) cudaFreeHost(host_stage);
+        host_stage = nullptr;
+        host_stage_bytes = 0;
+        cudaError_t e = cudaMallocHost(&host_stage, n);
+        if (e != cudaSuccess) {
+            host_stage = nullptr;
+            return e;
+        }
+        host_stage_bytes = n;
+        return cudaSuccess;
+    }
+    void release_all() {
+        planes.release();
+        dbuf[0].release();
+        dbuf[1].release();
+        stats.release();
+        ctl.release();
+        z.release();
+        rlo.release();
+        partials.release();
+        arrive.release();
+        hist.release();
+        if (host_stage) cudaFreeHost(host_stage);
+        host_stage = nullptr;
+        host_stage_bytes = 0;
+        for (ProfPool& p : pools) p.release();
+    }
+
+    // Launch through `f`, bracketed by timing events when profiling is on.
+    template <typename F>
+    cudaError_t timed(int kind, F&& f) {
+        if (!prof) return f();
+        ProfPool& P = pools[kind];
+        if (P.used >= ProfPool::kMaxPairs) return f();
+        while ((int)P.ev.size() < 2 * (P.used + 1)) {
+            cudaEvent_t e;
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return err;
+            P.ev.push_back(e);
+        }
+        cudaError_t err = cudaEventRecord(P.ev[2 * P.used], stream);
+        if (err != cudaSuccess) return err;
+        err = f();
+        if (err != cudaSuccess) return err;
+        err = cudaEventRecord(P.ev[2 * P.used + 1], stream);
+        if (err != cudaSuccess) return err;
+        ++P.used;
+        return cudaSuccess;
+    }
+};
+
+extern "C" {
+
+dsgnlm_status dsgnlm_create(dsgnlm_t* out, void* stream, int weight_dtype) {
+    if (!out) return DSGNLM_EINVAL;
+    *out = nullptr;
+    if (weight_dtype != DSGNLM_F32 && weight_dtype != DSGNLM_F16 && weight_dtype != DSGNLM_BF16)
+        return DSGNLM_EINVAL;
+    dsgnlm* h = new (std::nothrow) dsgnlm();
+    if (!h) return DSGNLM_ENOMEM;
+    h->stream = (cudaStream_t)stream;
+    h->dtype = weight_dtype;
+    *out = h;
+    return DSGNLM_OK;
+}
+
+void dsgnlm_destroy(dsgnlm_t h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    h->release_all();
+    delete h;
+}
+
+dsgnlm_status dsgnlm_set_stream(dsgnlm_t h, void* stream) {
+    if (!h) return DSGNLM_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return DSGNLM_OK;
+}
+
+int dsgnlm_num_offsets(dsgnlm_t h) { return (h && h->built) ? h->nh : 0; }
+
+dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int patch_r,
+                           int search_r, float bandwidth) {
+    if (!h || !guide || !aligned16(guide)) return DSGNLM_EINVAL;
+    if (H < 1 || W < 1 || (size_t)H * (size_t)W > (size_t)1 << 31) return DSGNLM_EINVAL;
+    if (patch_r < 0 || patch_r > DSGNLM_MAX_PATCH_R) return DSGNLM_EINVAL;
+    if (search_r < 0 || search_r > DSGNLM_MAX_SEARCH_R) return DSGNLM_EINVAL;
+    if (!(bandwidth > 0.f) || !std::isfinite(bandwidth)) return DSGNLM_EINVAL;
+    const int nh = num_half_offsets(search_r);
+    const size_t bytes = (size_t)nh * (size_t)H * (size_t)W * weight_elem_bytes(h->dtype);
+    h->built = false;
+    h->balanced = false;
+    DSG_CK(h->planes.ensure(bytes));
+    const double np = 2.0 * patch_r + 1.0;
+    const float c = (float)(1.0 / (2.0 * np * np * (double)bandwidth * (double)bandwidth));
+    DSG_CK(h->timed(DSGNLM_PROF_BUILD, [&] {
+        return launch_build(h->dtype, guide, H, W, patch_r, search_r, c, h->planes.p, h->stream);
+    }));
+    h->H = H;
+    h->W = W;
+    h->rp = patch_r;
+    h->rs = search_r;
+    h->nh = nh;
+    h->bw = bandwidth;
+    h->built = true;
+    return DSGNLM_OK;
+}
+
+dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, double* resid_out) {
+    if (!h) return DSGNLM_EINVAL;
+    if (!h->built) return DSGNLM_NOT_BUILT;
+    if (!(tol >= 0.0) || maxit < 0 || maxit > 1000000) return DSGNLM_EINVAL;
+    const size_t n = (size_t)h->H * h->W;
+    h->balanced = false;
+    DSG_CK(h->dbuf[0].ensure(n * sizeof(float)));
+    DSG_CK(h->dbuf[1].ensure(n * sizeof(float)));
+    DSG_CK(h->stats.ensure(sizeof(PassStat) * (size_t)(maxit + 1)));
+    DSG_CK(h->ctl.ensure(sizeof(BalanceCtl)));
+    DSG_CK(h->stage(sizeof(BalanceCtl) + sizeof(PassStat)));
+    DSG_CK(cudaMemsetAsync(h->stats.p, 0, sizeof(PassStat) * (size_t)(maxit + 1), h->stream));
+    BalanceCtl c0{};
+    c0.done = 0;
+    c0.final_pass = -1;
+    c0.status = 0;
+    c0.since_best = 0;
+    c0.best = INFINITY;
+    c0.tol = tol;
+    c0.maxit = maxit;
+    std::memcpy(h->host_stage, &c0, sizeof c0);
+    DSG_CK(cudaMemcpyAsync(h->ctl.p, h->host_stage, sizeof c0, cudaMemcpyHostToDevice, h->stream));
+    DSG_CK(launch_fill(h->dbuf[0].as<float>(), 1.0f, n, h->stream));
+
+    // Passes are launched in groups; a pass launched after the deciding one
+    // returns at once (the done flag is checked on entry), so the group size only
+    // trades wasted launches against host round trips.
+    BalanceCtl c{};
+    const int group = 4;
+    for (int pass = 0; pass <= maxit; ++pass) {
+        DSG_CK(h->timed(DSGNLM_PROF_BALANCE, [&] {
+            return launch_sinkhorn_pass(h->dtype, h->planes.p, h->H, h->W, h->rs,
+                                        h->dbuf[pass & 1].as<float>(), h->dbuf[(pass + 1) & 1].as<float>(),
+                                        h->stats.as<PassStat>(), h->ctl.as<BalanceCtl>(), pass, h->stream);
+        }));
+        if ((pass + 1) % group == 0 || pass == maxit) {
+            DSG_CK(cudaMemcpyAsync(h->host_stage, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+            DSG_CK(cudaStreamSynchronize(h->stream));
+            std::memcpy(&c, h->host_stage, sizeof c);
+            if (c.done) break;
+        }
+    }
+    if (!c.done || c.final_pass < 0) return DSGNLM_ECUDA;  // cannot happen: pass maxit decides
+    PassStat ps{};
+    DSG_CK(cudaMemcpyAsync(h->host_stage, h->stats.as<PassStat>() + c.final_pass, sizeof ps,
+                           cudaMemcpyDeviceToHost, h->stream));
+    DSG_CK(cudaStreamSynchronize(h->stream));
+    std::memcpy(&ps, h->host_stage, sizeof ps);
+    double eps, m;
+    std::memcpy(&eps, &ps.eps_bits, sizeof eps);
+    std::memcpy(&m, &ps.m_bits, sizeof m);
+    h->d_final = h->dbuf[c.final_pass & 1].as<float>();
+    h->m = m;
+    h->inv_m = (float)(1.0 / m);
+    h->iters = c.final_pass;
+    h->resid = eps;
+    h->balanced = true;
+    if (iters_out) *iters_out = c.final_pass;
+    if (resid_out) *resid_out = eps;
+    if (c.status == 6) return DSGNLM_NOT_CONVERGED;
+    if (c.status == 7) return DSGNLM_STALLED;
+    return DSGNLM_OK;
+}
+
+dsgnlm_status dsgnlm_apply(dsgnlm_t h, const float* x, float* y) {
+    if (!h || !x || !y || x == y || !aligned16(x) || !aligned16(y)) return DSGNLM_EINVAL;
+    if (!h->built) return DSGNLM_NOT_BUILT;
+    if (!h->balanced) return DSGNLM_NOT_BALANCED;
+    DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
+        return launch_apply(h->dtype, h->planes.p, h->H, h->W, h->rs, h->d_final, h->inv_m, x, y,
+                            h->stream);
+    }));
+    return DSGNLM_OK;
+}
+
+dsgnlm_status dsgnlm_copy_weights(dsgnlm_t h, void* dst) {
+    if (!h || !dst) return DSGNLM_EINVAL;
+    if (!h->built) return DSGNLM_NOT_BUILT;
+    const size_t bytes = (size_t)h->nh * h->H * h->W * weight_elem_bytes(h->dtype);
+    if (bytes) DSG_CK(cudaMemcpyAsync(dst, h->planes.p, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return DSGNLM_OK;
+}
+
+dsgnlm_status dsgnlm_copy_scaling(dsgnlm_t h, float* d_dst, double* m_host) {
+    if (!h) return DSGNLM_EINVAL;
+    if (!h->built) return DSGNLM_NOT_BUILT;
+    if (!h->balanced) return DSGNLM_NOT_BALANCED;
+    if (d_dst)
+        DSG_CK(cudaMemcpyAsync(d_dst, h->d_final, sizeof(float) * (size_t)h->H * h->W,
+                               cudaMemcpyDeviceToDevice, h->stream));
+    DSG_CK(cudaStreamSynchronize(h->stream));
+    if (m_host) *m_host = h->m;
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_sr_observe(const float* x, const float* noise, int H, int W, float blur_sigma,
+                              int blur_r, float* y, void* stream) {
+    if (!x || !y || H < 2 || W < 2 || (H & 1) || (W & 1)) return DSGNLM_EINVAL;
+    if (blur_r < 0 || blur_r > 8 || !(blur_sigma > 0.f)) return DSGNLM_EINVAL;
+    DSG_CK(launch_sr_forward(x, H, W, make_blur_taps(blur_sigma, blur_r), noise, 1.0f, y,
+                             (cudaStream_t)stream));
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_sr_guide(const float* y, int h, int w, float* guide, void* stream) {
+    if (!y || !guide || h < 1 || w < 1) return DSGNLM_EINVAL;
+    DSG_CK(launch_sr_guide(y, h, w, guide, (cudaStream_t)stream));
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_spi_observe(const float* x, const float* arrivals, int H, int W, int k_side,
+                               float eta, uint8_t* bits, void* stream) {
+    if (!x || !arrivals || !bits || H < 1 || W < 1 || k_side < 1 || k_side > 15 || !(eta > 0.f))
+        return DSGNLM_EINVAL;
+    DSG_CK(launch_spi_observe(x, arrivals, H, W, k_side, eta, bits, (cudaStream_t)stream));
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_spi_counts(const uint8_t* bits, int H, int W, int k_side, uint8_t* counts,
+                              void* stream) {
+    if (!bits || !counts || H < 1 || W < 1 || k_side < 1 || k_side > 15) return DSGNLM_EINVAL;
+    DSG_CK(launch_spi_counts(bits, H, W, k_side, counts, (cudaStream_t)stream));
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_spi_guide(const uint8_t* counts, int H, int W, int K, float eta, float* guide,
+                             void* stream) {
+    if (!counts || !guide || H < 1 || W < 1 || K < 1 || K > 255 || !(eta > 0.f)) return DSGNLM_EINVAL;
+    DSG_CK(launch_spi_guide(counts, H, W, K, eta, guide, (cudaStream_t)stream));
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_init(const float* guide, int n, float* x, float* v, float* u, void* stream) {
+    if (!guide || !x || !v || !u || n < 1) return DSGNLM_EINVAL;
+    DSG_CK(launch_init(guide, n, x, v, u, (cudaStream_t)stream));
+    return DSGNLM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Checks the data-term fields; with `for_solve` also the iterate buffers and the
+// denoiser state.
+dsgnlm_status check_problem(const lpnp_problem* p, bool for_solve) {
+    if (!p || !p->den || p->H < 1 || p->W < 1) return DSGNLM_EINVAL;
+    if (for_solve) {
+        if (!p->x || !p->v || !p->u) return DSGNLM_EINVAL;
+        if (!aligned16(p->x) || !aligned16(p->v) || !aligned16(p->u)) return DSGNLM_EINVAL;
+        if (p->x == p->v || p->x == p->u || p->v == p->u) return DSGNLM_EINVAL;
+        if (p->constraint < LPNP_C_NONE || p->constraint > LPNP_C_BOX01) return DSGNLM_EINVAL;
+        if (!(p->alpha >= 0.f) || !std::isfinite(p->alpha)) return DSGNLM_EINVAL;
+        if (!p->den->built) return DSGNLM_NOT_BUILT;
+        if (!p->den->balanced) return DSGNLM_NOT_BALANCED;
+        if (p->H != p->den->H || p->W != p->den->W) return DSGNLM_EINVAL;
+    }
+    if (p->kind == LPNP_SR2) {
+        if (!p->y || (p->H & 1) || (p->W & 1)) return DSGNLM_EINVAL;
+        if (p->blur_r < 0 || p->blur_r > 8 || !(p->blur_sigma > 0.f)) return DSGNLM_EINVAL;
+    } else if (p->kind == LPNP_SPI) {
+        if (!p->counts || p->K < 1 || p->K > 255 || !(p->eta > 0.f) || !(p->spi_eps > 0.f))
+            return DSGNLM_EINVAL;
+    } else {
+        return DSGNLM_EINVAL;
+    }
+    return DSGNLM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad) {
+    dsgnlm_status s = check_problem(p, false);
+    if (s != DSGNLM_OK) return s;
+    if (!x || !grad) return DSGNLM_EINVAL;
+    dsgnlm* h = p->den;
+    if (p->kind == LPNP_SR2) {
+        DSG_CK(h->rlo.ensure(sizeof(float) * (size_t)(p->H / 2) * (p->W / 2)));
+        const BlurTaps taps = make_blur_taps(p->blur_sigma, p->blur_r);
+        DSG_CK(launch_sr_forward(x, p->H, p->W, taps, p->y, -1.0f, h->rlo.as<float>(), h->stream));
+        DSG_CK(launch_sr_adjoint(h->rlo.as<float>(), p->H, p->W, taps, grad, h->stream));
+    } else {
+        DSG_CK(launch_spi_grad(x, p->counts, p->H * p->W, p->K, p->eta, p->spi_eps, grad, h->stream));
+    }
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
+    dsgnlm_status s = check_problem(p, true);
+    if (s != DSGNLM_OK) return s;
+    if (!(rho > 0.f) || !std::isfinite(rho) || iters < 0) return DSGNLM_EINVAL;
+    if (iters == 0) return DSGNLM_OK;
+    dsgnlm* h = p->den;
+    const int H = p->H, W = p->W;
+    const size_t n = (size_t)H * W;
+    const int nblocks = apply_grid_blocks(H, W);
+    DSG_CK(h->z.ensure(n * sizeof(float)));
+    DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nblocks));
+    DSG_CK(h->arrive.ensure(sizeof(unsigned) * (size_t)iters));
+    DSG_CK(h->hist.ensure(sizeof(double) * 2 * (size_t)iters));
+    if (p->kind == LPNP_SR2) DSG_CK(h->rlo.ensure(sizeof(float) * (n / 4)));
+    DSG_CK(cudaMemsetAsync(h->arrive.p, 0, sizeof(unsigned) * (size_t)iters, h->stream));
+    SolveRed red{h->partials.as<double>(), h->arrive.as<unsigned>(), h->hist.as<double>()};
+    const float mu = (float)(1.0 / ((double)p->alpha + (double)rho));
+    const BlurTaps taps = make_blur_taps(p->blur_sigma > 0.f ? p->blur_sigma : 1.f,
+                                         p->kind == LPNP_SR2 ? p->blur_r : 0);
+    for (int it = 0; it < iters; ++it) {
+        DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
+            if (p->kind == LPNP_SR2) {
+                cudaError_t e = launch_sr_forward(p->x, H, W, taps, p->y, -1.0f, h->rlo.as<float>(),
+                                                  h->stream);
+                if (e != cudaSuccess) return e;
+                return launch_sr_xupdate(h->rlo.as<float>(), H, W, taps, p->x, p->v, p->u,
+                                         h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
+            }
+            return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
+                                      h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
+        }));
+        DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
+            return launch_apply_dual(h->dtype, h->planes.p, H, W, h->rs, h->d_final, h->inv_m,
+                                     h->z.as<float>(), p->v, p->u, red, it, h->stream);
+        }));
+    }
+    if (p->resid_hist) {
+        DSG_CK(h->stage(sizeof(double) * 2 * (size_t)iters));
+        DSG_CK(cudaMemcpyAsync(h->host_stage, h->hist.p, sizeof(double) * 2 * (size_t)iters,
+                               cudaMemcpyDeviceToHost, h->stream));
+        DSG_CK(cudaStreamSynchronize(h->stream));
+        const double* hs = (const double*)h->host_stage;
+        for (int it = 0; it < iters; ++it) {
+            p->resid_hist[2 * it] = std::sqrt(hs[2 * it] / (double)n);
+            p->resid_hist[2 * it + 1] = (double)rho * std::sqrt(hs[2 * it + 1] / (double)n);
+        }
+    }
+    return DSGNLM_OK;
+}
+
+dsgnlm_status dsgnlm_profile_enable(dsgnlm_t h, int enable) {
+    if (!h) return DSGNLM_EINVAL;
+    h->prof = enable != 0;
+    for (ProfPool& p : h->pools) p.used = 0;
+    return DSGNLM_OK;
+}
+
+dsgnlm_status dsgnlm_profile_read(dsgnlm_t h, int kind, double* total_ms, int* launches) {
+    if (!h || kind < 0 || kind >= kProfKinds) return DSGNLM_EINVAL;
+    DSG_CK(cudaStreamSynchronize(h->stream));
+    ProfPool& P = h->pools[kind];
+    double acc = 0.0;
+    for (int q = 0; q < P.used; ++q) {
+        float ms = 0.f;
+        DSG_CK(cudaEventElapsedTime(&ms, P.ev[2 * q], P.ev[2 * q + 1]));
+        acc += ms;
+    }
+    if (total_ms) *total_ms = acc;
+    if (launches) *launches = P.used;
+    return DSGNLM_OK;
+}
+
+uint64_t dsgnlm_launch_count(void) { return g_launches.load(); }
+
+int dsgnlm_last_cuda_error(void) { return g_last_cuda; }
+
+const char* dsgnlm_strerror(dsgnlm_status s) {
+    switch (s) {
+        case DSGNLM_OK: return "ok";
+        case DSGNLM_EINVAL: return "invalid argument";
+        case DSGNLM_ENOMEM: return "device allocation failed";
+        case DSGNLM_ECUDA: return "CUDA error";
+        case DSGNLM_NOT_BUILT: return "denoiser not built";
+        case DSGNLM_NOT_BALANCED: return "denoiser not balanced";
+        case DSGNLM_NOT_CONVERGED: return "balancing reached maxit above tol";
+        case DSGNLM_STALLED: return "balancing residual stalled above tol";
+        case DSGNLM_TIMEOUT: return "bounded device wait timed out";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

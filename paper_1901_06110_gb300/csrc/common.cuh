@@ -1,0 +1,89 @@
+// Device-side helpers shared by the DSG-NLM / linearized PnP-ADMM kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace dsg {
+
+// Index of the half-window offset o = (oy, ox): first the oy = 0 row with
+// ox = 1..rs, then the rows oy = 1..rs with ox = -rs..rs.  n_h = 2 rs (rs + 1).
+__host__ __device__ __forceinline__ int num_half_offsets(int rs) { return 2 * rs * (rs + 1); }
+
+__host__ __device__ __forceinline__ void half_offset(int k, int rs, int& oy, int& ox) {
+    if (k < rs) {
+        oy = 0;
+        ox = k + 1;
+    } else {
+        const int kk = k - rs;
+        const int w = 2 * rs + 1;
+        oy = 1 + kk / w;
+        ox = kk % w - rs;
+    }
+}
+
+// first half-offset index of row oy and the ox it starts with
+__host__ __device__ __forceinline__ int row_first_k(int oy, int rs) {
+    return oy == 0 ? 0 : rs + (oy - 1) * (2 * rs + 1);
+}
+
+// half-sample symmetric extension of an index into [0, n)
+__device__ __forceinline__ int sym_index(int i, int n) {
+    const int p = 2 * n;
+    int m = i % p;
+    if (m < 0) m += p;
+    return m < n ? m : p - 1 - m;
+}
+
+__device__ __forceinline__ int wrap_index(int i, int n) {
+    int m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+// weight storage conversions (arithmetic is always FP32)
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// Error-free addition (Knuth's TwoSum): s + e == a + b exactly.  Used to add the
+// per-row partial sums of a stencil so that the row sums entering the balancing
+// residual are not limited by the length of the FP32 accumulation chain.
+struct CompSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float b) {
+        const float t = __fadd_rn(s, b);
+        const float bb = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(b, bb));
+        s = t;
+        c = __fadd_rn(c, err);
+    }
+    __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+};
+
+// Order-independent max of non-negative doubles through their bit patterns.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace dsg

@@ -1,0 +1,89 @@
+// Host-side launchers of the kernels, shared by the C ABI implementation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dsg {
+
+void count_launches(uint64_t n);
+
+// balancing state in device memory, one slot per pass
+struct PassStat {
+    unsigned long long eps_bits;  // max_s |d_s t_s - 1| (FP64 bits)
+    unsigned long long m_bits;    // max_s d_s t_s (FP64 bits)
+    unsigned int arrive;          // blocks finished
+    unsigned int pad;
+};
+
+struct BalanceCtl {
+    int done;        // set by the last block of the deciding pass
+    int final_pass;  // pass whose scaling is the result (= number of updates)
+    int status;      // 0 ok, 6 not converged, 7 stalled
+    int since_best;  // passes since the residual last improved by 1%
+    double best;     // smallest residual seen
+    double tol;
+    int maxit;
+    int pad;
+};
+
+// Solve-loop reduction state: per-block partial sums, one arrival counter and one
+// two-value history slot per iteration.
+struct SolveRed {
+    double* partials;        // [2 * nblocks]
+    unsigned int* arrive;    // [iters]
+    double* hist;            // [2 * iters]: sum (x-v)^2 and sum (v-v_prev)^2
+};
+
+// weights: dtype 0 = FP32, 1 = FP16, 2 = BF16
+cudaError_t launch_build(int dtype, const float* guide, int H, int W, int patch_r, int search_r,
+                         float inv_two_np2_h2, void* planes, cudaStream_t st);
+
+cudaError_t launch_fill(float* p, float value, size_t n, cudaStream_t st);
+
+cudaError_t launch_sinkhorn_pass(int dtype, const void* planes, int H, int W, int search_r,
+                                 const float* d_in, float* d_out, PassStat* stats,
+                                 BalanceCtl* ctl, int pass, cudaStream_t st);
+
+cudaError_t launch_apply(int dtype, const void* planes, int H, int W, int search_r,
+                         const float* d, float inv_m, const float* z, float* y, cudaStream_t st);
+
+// v <- W z, u <- z - v (= u + x - v), residual partial sums into red at slot `iter`
+cudaError_t launch_apply_dual(int dtype, const void* planes, int H, int W, int search_r,
+                              const float* d, float inv_m, const float* z, float* v, float* u,
+                              SolveRed red, int iter, cudaStream_t st);
+int apply_grid_blocks(int H, int W);
+
+struct BlurTaps {
+    float t[17];  // normalised 1D Gaussian taps t[a + r], a = -r..r
+    int r;
+};
+BlurTaps make_blur_taps(float sigma, int r);
+
+// out(q) = (A x)(q) + c * aux(q) on the [H/2][W/2] grid (aux may be null)
+cudaError_t launch_sr_forward(const float* x, int H, int W, BlurTaps taps, const float* aux,
+                              float c, float* out, cudaStream_t st);
+// grad = A^T r at [H][W] (r on [H/2][W/2])
+cudaError_t launch_sr_adjoint(const float* r, int H, int W, BlurTaps taps, float* out,
+                              cudaStream_t st);
+// x <- Pi_C(mu (alpha x + rho (v - u) - A^T r)), z <- x + u
+cudaError_t launch_sr_xupdate(const float* r, int H, int W, BlurTaps taps, float* x,
+                              const float* v, const float* u, float* z, float mu, float alpha,
+                              float rho, int constraint, cudaStream_t st);
+// grad f for SPI
+cudaError_t launch_spi_grad(const float* x, const uint8_t* counts, int n, int K, float eta,
+                            float eps, float* grad, cudaStream_t st);
+cudaError_t launch_spi_xupdate(const uint8_t* counts, int n, int K, float eta, float eps, float* x,
+                               const float* v, const float* u, float* z, float mu, float alpha,
+                               float rho, int constraint, cudaStream_t st);
+
+cudaError_t launch_sr_guide(const float* y, int h, int w, float* guide, cudaStream_t st);
+cudaError_t launch_spi_observe(const float* x, const float* arrivals, int H, int W, int k_side,
+                               float eta, uint8_t* bits, cudaStream_t st);
+cudaError_t launch_spi_counts(const uint8_t* bits, int H, int W, int k_side, uint8_t* counts,
+                              cudaStream_t st);
+cudaError_t launch_spi_guide(const uint8_t* counts, int H, int W, int K, float eta, float* guide,
+                             cudaStream_t st);
+cudaError_t launch_init(const float* guide, int n, float* x, float* v, float* u, cudaStream_t st);
+
+}  // namespace dsg

@@ -1,0 +1,92 @@
+"""The restoration experiments of Sec. 4 as sequences of C ABI calls.
+
+One call of ``solve_sr`` / ``solve_spi`` is one pass of the whole method on one
+image: guide from the measurements, weight build (Eq. NLM, S1), balance (Eq. S2,
+S3), then Algorithm 1 with the fixed DSG-NLM (F-DSG-NLM) as denoiser.  Only
+argument marshalling happens here; each step is a kernel of the CUDA library.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _abi
+from . import dsgnlm as D
+
+
+@dataclass
+class Params:
+    patch_r: int
+    search_r: int
+    h: float
+    tol: float
+    iters: int
+    rho: float = 1.0
+    alpha: float = 1.0
+    maxit: int = 10000
+    blur_sigma: float = 1.0
+    blur_r: int = 4
+    K: int = 16
+    eta: float = 4.0
+    spi_eps: float = 1e-3
+    weight_dtype: str = "f32"
+    extra: dict = field(default_factory=dict)
+
+    @staticmethod
+    def from_workload(wl: dict, **over) -> "Params":
+        keys = ("patch_r", "search_r", "h", "tol", "iters", "rho", "alpha", "blur_sigma", "blur_r",
+                "eta", "spi_eps")
+        kw = {k: wl[k] for k in keys if k in wl}
+        if "K_side" in wl:
+            kw["K"] = wl["K_side"] ** 2
+        kw.update(over)
+        return Params(**kw)
+
+
+class Solver:
+    """Holds one denoiser handle and the iterate buffers for repeated solves of
+    same-sized problems (buffers are reused, nothing is reallocated per call)."""
+
+    def __init__(self, H: int, W: int, params: Params, kind: str = "sr"):
+        self.H, self.W, self.p, self.kind = H, W, params, kind
+        self.den = D.dsgnlm_create(params.weight_dtype)
+        self.x = torch.empty((H, W), device="cuda")
+        self.v = torch.empty_like(self.x)
+        self.u = torch.empty_like(self.x)
+        self.guide = torch.empty_like(self.x)
+        self.balance = None
+        self._prob = None
+        self._data = None
+
+    def _problem(self, data):
+        if self._prob is None or self._data is not data:
+            p = self.p
+            if self.kind == "sr":
+                self._prob = D.Problem("sr", self.den, self.x, self.v, self.u, alpha=p.alpha, y=data,
+                                       blur_sigma=p.blur_sigma, blur_r=p.blur_r)
+            else:
+                self._prob = D.Problem("spi", self.den, self.x, self.v, self.u, alpha=p.alpha,
+                                       counts=data, K=p.K, eta=p.eta, spi_eps=p.spi_eps)
+            self._data = data
+        return self._prob
+
+    def run(self, data: torch.Tensor, residuals: bool = False):
+        """data: the [H/2][W/2] FP32 observation (SR) or the [H][W] uint8 counts (SPI)."""
+        p = self.p
+        lib = _abi.load()
+        stream = D._stream()
+        if self.kind == "sr":
+            D._check(lib.lpnp_sr_guide(data.data_ptr(), self.H // 2, self.W // 2, self.guide.data_ptr(),
+                                       stream), "lpnp_sr_guide")
+        else:
+            D._check(lib.lpnp_spi_guide(data.data_ptr(), self.H, self.W, p.K, p.eta, self.guide.data_ptr(),
+                                        stream), "lpnp_spi_guide")
+        D.dsgnlm_build(self.den, self.guide, p.patch_r, p.search_r, p.h)
+        self.balance = D.dsgnlm_balance(self.den, p.tol, p.maxit)
+        D._check(lib.lpnp_init(self.guide.data_ptr(), self.H * self.W, self.x.data_ptr(),
+                               self.v.data_ptr(), self.u.data_ptr(), stream), "lpnp_init")
+        return D.lpnp_solve(self._problem(data), p.rho, p.iters, residuals=residuals)
+
+    def close(self):
+        self.den.close()

@@ -26,3 +26,11 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def gpu_lib():
+    """The CUDA library, built in-tree if needed (GPU tests only)."""
+    from paper_1901_06110_gb300 import _abi, build
+    build.build()
+    return _abi.load()

@@ -135,3 +135,14 @@ def test_sym_index():
     got = [int(dsgnlm.sym_index(i, 3)) for i in range(-7, 10)]
     # indices -7..9 of a 3-pixel row: ... 0 | 0 1 2 | 2 1 0 | 0 1 2 | 2 1 0 | 0 1 2 | 2 1 0 ...
     assert got == [0, 0, 1, 2, 2, 1, 0, 0, 1, 2, 2, 1, 0, 0, 1, 2, 2]
+
+
+def test_kernel_row_matches_matrix():
+    g = _rand_guide(11, 13, 21)
+    K1 = dsgnlm.kernel_matrix(g, 2, 3, 0.2).tocsr()
+    for s in [(0, 0), (5, 6), (10, 12), (3, 11)]:
+        row = dsgnlm.kernel_row(g, 2, 3, 0.2, s)
+        dense = K1[s[0] * 13 + s[1]].toarray().ravel()
+        assert len(row) == np.count_nonzero(dense)
+        for (ri, rj), val in row.items():
+            assert abs(val - dense[ri * 13 + rj]) < 1e-15

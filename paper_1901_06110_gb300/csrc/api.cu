@@ -7,6 +7,9 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/dsgnlm.h"
 #include "common.cuh"
 #include "internal.h"
@@ -76,12 +79,71 @@ struct ProfPool {
 
 constexpr int kProfKinds = 4;
 
+// Tensor map of the weight planes [n_h][H][pitch] for the TMA stencil path.
+cudaError_t encode_planes_map(void* out, void* planes, int dtype, int H, int W, int nh) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const size_t esz = dtype == DSGNLM_F32 ? 4 : 2;
+    const CUtensorMapDataType dt = dtype == DSGNLM_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dtype == DSGNLM_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nh};
+    const cuuint64_t strides[2] = {(cuuint64_t)plane_pitch(W) * esz, (cuuint64_t)plane_pitch(W) * H * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)tma_tile_w(), (cuuint32_t)tma_tile_h(), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode((CUtensorMap*)out, dt, 3, planes, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Split the column offsets -rs..rs into `n` contiguous slices of about equal
+// offset counts (a column offset o_x carries rs offsets for o_x <= 0 and rs + 1
+// for o_x > 0).
+TmaSplits make_splits(int rs, int n) {
+    TmaSplits t{};
+    const int groups = 2 * rs + 1;
+    n = n < 1 ? 1 : (n > groups ? groups : n);
+    if (n > kMaxSlices) n = kMaxSlices;
+    const int total = num_half_offsets(rs);
+    int ox = -rs, cum = 0;
+    for (int sl = 0; sl < n; ++sl) {
+        t.ox_lo[sl] = ox;
+        const int target = (int)(((long long)total * (sl + 1) + n - 1) / n);
+        // leave at least one column offset for each remaining slice
+        const int last_allowed = rs - (n - 1 - sl);
+        while (true) {
+            cum += ox > 0 ? rs + 1 : rs;
+            if (ox >= last_allowed || cum >= target) break;
+            ++ox;
+        }
+        t.ox_hi[sl] = ox;
+        ++ox;
+    }
+    t.ox_hi[n - 1] = rs;
+    t.n = n;
+    return t;
+}
+
 }  // namespace
 
 struct dsgnlm {
     cudaStream_t stream = nullptr;
     int dtype = DSGNLM_F32;
-    int H = 0, W = 0, rp = 0, rs = 0, nh = 0;
+    int H = 0, W = 0, Wp = 0, rp = 0, rs = 0, nh = 0;
+    int num_sms = 0;
+    // TMA stencil path
+    bool fast = false;
+    TmaPlan plan{};
+    DevBuf tma_part, tbuf[2], err;
+    float* t_final = nullptr;
     float bw = 0.f;
     bool built = false, balanced = false;
     DevBuf planes, dbuf[2], stats, ctl;
@@ -113,6 +175,10 @@ struct dsgnlm {
         return cudaSuccess;
     }
     void release_all() {
+        tma_part.release();
+        tbuf[0].release();
+        tbuf[1].release();
+        err.release();
         planes.release();
         dbuf[0].release();
         dbuf[1].release();
@@ -190,9 +256,11 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
     if (search_r < 0 || search_r > DSGNLM_MAX_SEARCH_R) return DSGNLM_EINVAL;
     if (!(bandwidth > 0.f) || !std::isfinite(bandwidth)) return DSGNLM_EINVAL;
     const int nh = num_half_offsets(search_r);
-    const size_t bytes = (size_t)nh * (size_t)H * (size_t)W * weight_elem_bytes(h->dtype);
+    const int Wp = plane_pitch(W);
+    const size_t bytes = (size_t)nh * (size_t)H * (size_t)Wp * weight_elem_bytes(h->dtype);
     h->built = false;
     h->balanced = false;
+    h->fast = false;
     DSG_CK(h->planes.ensure(bytes));
     const double np = 2.0 * patch_r + 1.0;
     const float c = (float)(1.0 / (2.0 * np * np * (double)bandwidth * (double)bandwidth));
@@ -201,10 +269,31 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
     }));
     h->H = H;
     h->W = W;
+    h->Wp = Wp;
     h->rp = patch_r;
     h->rs = search_r;
     h->nh = nh;
     h->bw = bandwidth;
+    if (tma_path_supports(search_r)) {
+        if (!h->num_sms) {
+            int dev = 0;
+            DSG_CK(cudaGetDevice(&dev));
+            DSG_CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        }
+        TmaPlan& pl = h->plan;
+        DSG_CK(encode_planes_map(pl.tmap, h->planes.p, h->dtype, H, W, nh));
+        pl.tiles_x = (W + tma_tile_w() - 1) / tma_tile_w();
+        pl.tiles_y = (H + tma_tile_h() - 1) / tma_tile_h();
+        const int tiles = pl.tiles_x * pl.tiles_y;
+        // about two resident CTAs per SM: split the offsets when tiles are scarce
+        int slices = (2 * h->num_sms) / tiles;
+        pl.splits = make_splits(search_r, slices < 1 ? 1 : slices);
+        DSG_CK(h->tma_part.ensure(sizeof(float) * tma_region_floats(search_r) * (size_t)tiles * pl.splits.n));
+        pl.partials = h->tma_part.as<float>();
+        DSG_CK(h->err.ensure(sizeof(unsigned)));
+        DSG_CK(cudaMemsetAsync(h->err.p, 0, sizeof(unsigned), h->stream));
+        h->fast = true;
+    }
     h->built = true;
     return DSGNLM_OK;
 }
@@ -217,6 +306,10 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     h->balanced = false;
     DSG_CK(h->dbuf[0].ensure(n * sizeof(float)));
     DSG_CK(h->dbuf[1].ensure(n * sizeof(float)));
+    if (h->fast) {
+        DSG_CK(h->tbuf[0].ensure(n * sizeof(float)));
+        DSG_CK(h->tbuf[1].ensure(n * sizeof(float)));
+    }
     DSG_CK(h->stats.ensure(sizeof(PassStat) * (size_t)(maxit + 1)));
     DSG_CK(h->ctl.ensure(sizeof(BalanceCtl)));
     DSG_CK(h->stage(sizeof(BalanceCtl) + sizeof(PassStat)));
@@ -240,9 +333,19 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     const int group = 4;
     for (int pass = 0; pass <= maxit; ++pass) {
         DSG_CK(h->timed(DSGNLM_PROF_BALANCE, [&] {
-            return launch_sinkhorn_pass(h->dtype, h->planes.p, h->H, h->W, h->rs,
-                                        h->dbuf[pass & 1].as<float>(), h->dbuf[(pass + 1) & 1].as<float>(),
-                                        h->stats.as<PassStat>(), h->ctl.as<BalanceCtl>(), pass, h->stream);
+            float* d_in = h->dbuf[pass & 1].as<float>();
+            float* d_out = h->dbuf[(pass + 1) & 1].as<float>();
+            BalanceCtl* ctl = h->ctl.as<BalanceCtl>();
+            if (h->fast) {
+                cudaError_t e = launch_tma_gather(h->dtype, h->plan, h->H, h->W, h->rs, d_in, nullptr,
+                                                  h->err.as<unsigned>(), &ctl->done, h->stream);
+                if (e != cudaSuccess) return e;
+                return launch_tma_balance_finish(h->plan, h->H, h->W, h->rs, d_in, d_out,
+                                                 h->tbuf[pass & 1].as<float>(), h->stats.as<PassStat>(), ctl,
+                                                 pass, h->stream);
+            }
+            return launch_sinkhorn_pass(h->dtype, h->planes.p, h->H, h->W, h->rs, d_in, d_out,
+                                        h->stats.as<PassStat>(), ctl, pass, h->stream);
         }));
         if ((pass + 1) % group == 0 || pass == maxit) {
             DSG_CK(cudaMemcpyAsync(h->host_stage, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost, h->stream));
@@ -260,6 +363,12 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     double eps, m;
     std::memcpy(&eps, &ps.eps_bits, sizeof eps);
     std::memcpy(&m, &ps.m_bits, sizeof m);
+    if (h->fast) {
+        unsigned errv = 0;
+        DSG_CK(cudaMemcpy(&errv, h->err.p, sizeof errv, cudaMemcpyDeviceToHost));
+        if (errv) return DSGNLM_TIMEOUT;
+        h->t_final = h->tbuf[c.final_pass & 1].as<float>();
+    }
     h->d_final = h->dbuf[c.final_pass & 1].as<float>();
     h->m = m;
     h->inv_m = (float)(1.0 / m);
@@ -278,6 +387,13 @@ dsgnlm_status dsgnlm_apply(dsgnlm_t h, const float* x, float* y) {
     if (!h->built) return DSGNLM_NOT_BUILT;
     if (!h->balanced) return DSGNLM_NOT_BALANCED;
     DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
+        if (h->fast) {
+            cudaError_t e = launch_tma_gather(h->dtype, h->plan, h->H, h->W, h->rs, h->d_final, x,
+                                              h->err.as<unsigned>(), nullptr, h->stream);
+            if (e != cudaSuccess) return e;
+            return launch_tma_apply_finish(h->plan, h->H, h->W, h->rs, h->d_final, h->t_final, h->inv_m, x,
+                                           y, h->stream);
+        }
         return launch_apply(h->dtype, h->planes.p, h->H, h->W, h->rs, h->d_final, h->inv_m, x, y,
                             h->stream);
     }));
@@ -287,8 +403,10 @@ dsgnlm_status dsgnlm_apply(dsgnlm_t h, const float* x, float* y) {
 dsgnlm_status dsgnlm_copy_weights(dsgnlm_t h, void* dst) {
     if (!h || !dst) return DSGNLM_EINVAL;
     if (!h->built) return DSGNLM_NOT_BUILT;
-    const size_t bytes = (size_t)h->nh * h->H * h->W * weight_elem_bytes(h->dtype);
-    if (bytes) DSG_CK(cudaMemcpyAsync(dst, h->planes.p, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    const size_t esz = weight_elem_bytes(h->dtype);
+    if (h->nh)
+        DSG_CK(cudaMemcpy2DAsync(dst, (size_t)h->W * esz, h->planes.p, (size_t)h->Wp * esz, (size_t)h->W * esz,
+                                 (size_t)h->nh * h->H, cudaMemcpyDeviceToDevice, h->stream));
     return DSGNLM_OK;
 }
 
@@ -405,7 +523,7 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
     dsgnlm* h = p->den;
     const int H = p->H, W = p->W;
     const size_t n = (size_t)H * W;
-    const int nblocks = apply_grid_blocks(H, W);
+    const int nblocks = h->fast ? tma_p2_blocks(H, W) : apply_grid_blocks(H, W);
     DSG_CK(h->z.ensure(n * sizeof(float)));
     DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nblocks));
     DSG_CK(h->arrive.ensure(sizeof(unsigned) * (size_t)iters));
@@ -429,6 +547,13 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
                                       h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
         }));
         DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
+            if (h->fast) {
+                cudaError_t e = launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
+                                                  h->err.as<unsigned>(), nullptr, h->stream);
+                if (e != cudaSuccess) return e;
+                return launch_tma_dual_finish(h->plan, H, W, h->rs, h->d_final, h->t_final, h->inv_m,
+                                              h->z.as<float>(), p->v, p->u, red, it, h->stream);
+            }
             return launch_apply_dual(h->dtype, h->planes.p, H, W, h->rs, h->d_final, h->inv_m,
                                      h->z.as<float>(), p->v, p->u, red, it, h->stream);
         }));
@@ -438,6 +563,11 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
         DSG_CK(cudaMemcpyAsync(h->host_stage, h->hist.p, sizeof(double) * 2 * (size_t)iters,
                                cudaMemcpyDeviceToHost, h->stream));
         DSG_CK(cudaStreamSynchronize(h->stream));
+        if (h->fast) {
+            unsigned errv = 0;
+            DSG_CK(cudaMemcpy(&errv, h->err.p, sizeof errv, cudaMemcpyDeviceToHost));
+            if (errv) return DSGNLM_TIMEOUT;
+        }
         const double* hs = (const double*)h->host_stage;
         for (int it = 0; it < iters; ++it) {
             p->resid_hist[2 * it] = std::sqrt(hs[2 * it] / (double)n);

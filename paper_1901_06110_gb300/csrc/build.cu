@@ -58,7 +58,8 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp, int rs, floa
     }
     __syncthreads();
 
-    const size_t plane = (size_t)H * W;
+    const int Wp = plane_pitch(W);
+    const size_t plane = (size_t)H * Wp;
     const float inv_hat = 1.0f / (float)(rs + 1);
     for (int k = k_begin; k < k_end; ++k) {
         int oy, ox;
@@ -90,7 +91,7 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp, int rs, floa
             for (int t = 0; t <= 2 * rp; ++t) D += r[t * kTW];
             const bool inside = (i + oy < H) && (j + ox >= 0) && (j + ox < W);
             const float w = inside ? hat * __expf(-D * c) : 0.f;
-            out[(size_t)i * W + j] = from_f32<WT>(w);
+            out[(size_t)i * Wp + j] = from_f32<WT>(w);
         }
         // E is rewritten next while R is still being read: they are distinct
         // buffers, and R is rewritten only after the next barrier.

@@ -35,9 +35,44 @@ struct SolveRed {
     double* hist;            // [2 * iters]: sum (x-v)^2 and sum (v-v_prev)^2
 };
 
-// weights: dtype 0 = FP32, 1 = FP16, 2 = BF16
+// Weight planes are stored [n_h][H][pitch] with the row pitch a multiple of 8
+// elements (16-byte aligned rows, as TMA requires); dtype 0 = FP32, 1 = FP16, 2 = BF16.
+__host__ __device__ inline int plane_pitch(int W) { return (W + 7) & ~7; }
+
 cudaError_t launch_build(int dtype, const float* guide, int H, int W, int patch_r, int search_r,
                          float inv_two_np2_h2, void* planes, cudaStream_t st);
+
+// TMA stencil path (search radii with a compiled kernel)
+constexpr int kMaxSlices = 25;
+struct TmaSplits {
+    int ox_lo[kMaxSlices];
+    int ox_hi[kMaxSlices];
+    int n;
+};
+struct TmaPlan {
+    alignas(64) unsigned char tmap[128];  // CUtensorMap of the planes
+    int tiles_x, tiles_y;
+    TmaSplits splits;
+    float* partials;  // [slices][tiles_y][tiles_x][region]
+};
+bool tma_path_supports(int rs);
+int tma_tile_w();
+int tma_tile_h();
+size_t tma_region_floats(int rs);
+int tma_p2_blocks(int H, int W);
+// phase 1: partial sums of K1 q over every tile and offset slice, q = d (z null) or d z
+cudaError_t launch_tma_gather(int dtype, const TmaPlan& plan, int H, int W, int rs, const float* d,
+                              const float* z, unsigned* err, const int* skip, cudaStream_t st);
+// phase 2 epilogues
+cudaError_t launch_tma_balance_finish(const TmaPlan& plan, int H, int W, int rs, const float* d_in,
+                                      float* d_out, float* t_out, PassStat* stats, BalanceCtl* ctl,
+                                      int pass, cudaStream_t st);
+cudaError_t launch_tma_apply_finish(const TmaPlan& plan, int H, int W, int rs, const float* d,
+                                    const float* t, float inv_m, const float* z, float* y,
+                                    cudaStream_t st);
+cudaError_t launch_tma_dual_finish(const TmaPlan& plan, int H, int W, int rs, const float* d,
+                                   const float* t, float inv_m, const float* z, float* v, float* u,
+                                   SolveRed red, int iter, cudaStream_t st);
 
 cudaError_t launch_fill(float* p, float value, size_t n, cudaStream_t st);
 

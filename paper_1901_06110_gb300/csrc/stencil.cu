@@ -20,11 +20,12 @@ constexpr int kBX = 32;
 constexpr int kBY = 8;
 constexpr int kThreads = kBX * kBY;
 
-// sum_{r != s} K1(s, r) a(r) b(r) with b = 1 when B is null
+// sum_{r != s} K1(s, r) a(r) b(r) with b = 1 when B is null (planes of row pitch Wp)
 template <typename WT, bool kHasB>
 __device__ __forceinline__ float stencil_gather(const WT* __restrict__ P, size_t plane, int H, int W,
                                                 int rs, int i, int j, const float* __restrict__ A,
                                                 const float* __restrict__ B, float b_s) {
+    const int Wp = plane_pitch(W);
     CompSum total;
     for (int oy = 0; oy <= rs; ++oy) {
         const int ox0 = oy == 0 ? 1 : -rs;
@@ -35,13 +36,13 @@ __device__ __forceinline__ float stencil_gather(const WT* __restrict__ P, size_t
             const int fj = j + ox, bj = j - ox;
             if (fi < H && fj >= 0 && fj < W) {
                 const size_t r = (size_t)fi * W + fj;
-                const float w = to_f32(Pk[(size_t)i * W + j]);
+                const float w = to_f32(Pk[(size_t)i * Wp + j]);
                 const float a = __ldg(A + r);
                 row = fmaf(w, kHasB ? a * (__ldg(B + r) - b_s) : a, row);
             }
             if (bi >= 0 && bj >= 0 && bj < W) {
                 const size_t r = (size_t)bi * W + bj;
-                const float w = to_f32(Pk[r]);
+                const float w = to_f32(Pk[(size_t)bi * Wp + bj]);
                 const float a = __ldg(A + r);
                 row = fmaf(w, kHasB ? a * (__ldg(B + r) - b_s) : a, row);
             }
@@ -62,7 +63,7 @@ sinkhorn_pass_kernel(const WT* __restrict__ P, int H, int W, int rs, const float
     double eps = 0.0, rsum = 0.0;
     if (i < H && j < W) {
         const size_t s = (size_t)i * W + j;
-        const size_t plane = (size_t)H * W;
+        const size_t plane = (size_t)H * plane_pitch(W);
         const float ds = d_in[s];
         // t = K1 d: the diagonal term (K1(s, s) = 1) plus the off-diagonal gather
         const float off = stencil_gather<WT, false>(P, plane, H, W, rs, i, j, d_in, nullptr, 0.f);
@@ -128,7 +129,7 @@ apply_kernel(const WT* __restrict__ P, int H, int W, int rs, const float* __rest
     const int i = blockIdx.y * kBY + threadIdx.y;
     if (i >= H || j >= W) return;
     const size_t s = (size_t)i * W + j;
-    const size_t plane = (size_t)H * W;
+    const size_t plane = (size_t)H * plane_pitch(W);
     const float zs = z[s];
     // y_s = z_s + (d_s / m) sum_{r != s} K1(s, r) d_r (z_r - z_s): W z with the
     // diagonal closed so that the row sums are one (Eq. S3)
@@ -146,7 +147,7 @@ apply_dual_kernel(const WT* __restrict__ P, int H, int W, int rs, const float* _
     double sp = 0.0, sd = 0.0;
     if (i < H && j < W) {
         const size_t s = (size_t)i * W + j;
-        const size_t plane = (size_t)H * W;
+        const size_t plane = (size_t)H * plane_pitch(W);
         const float zs = z[s];
         const float acc = stencil_gather<WT, true>(P, plane, H, W, rs, i, j, d, z, zs);
         const float vn = fmaf(d[s] * inv_m, acc, zs);

@@ -1,0 +1,527 @@
+// TMA-pipelined stencil pass over the half-window weight planes (the aggregation
+// loops of Algorithm 2): A(s) = sum_{r != s} K1(s, r) q(r) for a per-pixel field q
+// (q = d for a balancing pass, q = d z for an application of W).
+//
+// Each weight K1(s, s + o) is read from HBM exactly once and used twice: for the
+// forward term K1(s, s+o) q(s+o) of pixel s and for the mirrored term
+// K1(s, s+o) q(s) of pixel s + o (symmetry of K1).
+//
+// Phase 1 (one CTA per spatial tile of kTH x kTW pixels and per slice of the
+// offsets): a producer warp streams the tile of every plane of the slice into a
+// ring of shared-memory stages with cp.async.bulk.tensor (TMA) and mbarriers.
+// Consumer thread c owns column c of the tile (kTH pixels).  Offsets are visited
+// column-offset first (fixed o_x, then o_y = 0..N_s), so that for one o_x
+//   - the forward neighbours q(i + o_y, j + o_x) of the thread's pixels form one
+//     column strip of kTH + N_s values held in registers, and
+//   - the mirrored contributions land in one column strip (column j + o_x) of
+//     kTH + N_s register accumulators,
+// which makes every weight cost one shared-memory load and two FMAs.  After each
+// o_x the strips are added, with an error-free transformation, into a shared
+// accumulator covering the tile plus the halo its mirrored terms reach (N_s rows
+// below, N_s columns either side); consumers synchronise once per o_x, so no two
+// threads update the same column at once.  The accumulator (tile + halo) is
+// written to a per-CTA partial region.
+//
+// Phase 2 (one thread per pixel) adds, in a fixed order, the partial regions of
+// the up to six tiles and every offset slice that cover the pixel, then applies
+// the pass's epilogue: the balancing update and residual reduction, W z with the
+// diagonal closure of Eq. S3, or W z fused with the dual update of Algorithm 1.
+// Results do not depend on scheduling: every sum has a fixed order.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace dsg {
+
+namespace {
+
+constexpr int kTH = 16;                  // tile rows (= pixels per consumer thread)
+constexpr int kTW = 128;                 // tile columns (= consumer threads)
+constexpr int kConsumers = kTW;
+constexpr int kConsumerWarps = kConsumers / 32;
+constexpr int kThreads = kConsumers + 32;  // + one producer warp
+constexpr int kStages = 6;
+constexpr long long kWaitBudget = 4000000000LL;  // cycles (about 2 s) before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false after the budget.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitBudget) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                            int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
+}
+
+__device__ __forceinline__ void two_sum_into(float& hi, float& lo, float b) {
+    const float s = __fadd_rn(hi, b);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+__host__ __device__ __forceinline__ int plane_index(int oy, int ox, int rs) {
+    return oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
+}
+
+template <int RS, typename WT>
+__global__ void __launch_bounds__(kThreads, 2)
+stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const float* __restrict__ d,
+                  const float* __restrict__ z, TmaSplits splits, float* __restrict__ part,
+                  unsigned* __restrict__ err, const int* __restrict__ skip) {
+    constexpr int RH = kTH + RS;
+    constexpr int RW = kTW + 2 * RS;
+    constexpr int kStageElems = kTH * kTW;
+    if (skip && *(volatile const int*)skip) return;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    WT* stages = reinterpret_cast<WT*>(smem_raw);
+    float* qt = reinterpret_cast<float*>(smem_raw + kStages * kStageElems * sizeof(WT));
+    float* acc_hi = qt + RH * RW;
+    float* acc_lo = acc_hi + RH * RW;
+    uint64_t* full = reinterpret_cast<uint64_t*>(acc_lo + RH * RW);
+    uint64_t* empty = full + kStages;
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kTW;
+    const int y0 = blockIdx.y * kTH;
+    const int slice = blockIdx.z;
+    const int oxa = splits.ox_lo[slice];
+    const int oxb = splits.ox_hi[slice];
+
+    // q over the tile + halo (zero outside the image); accumulators cleared
+    for (int idx = tid; idx < RH * RW; idx += kThreads) {
+        const int a = idx / RW, b = idx - a * RW;
+        const int i = y0 + a, j = x0 - RS + b;
+        float v = 0.f;
+        if (i < H && j >= 0 && j < W) {
+            const size_t p = (size_t)i * W + j;
+            v = d[p];
+            if (z) v *= z[p];
+        }
+        qt[idx] = v;
+        acc_hi[idx] = 0.f;
+        acc_lo[idx] = 0.f;
+    }
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (tid >= kConsumers) {
+        // producer: one elected thread streams the plane tiles in consumption order
+        if (tid == kConsumers) {
+            int q = 0;
+            bool ok = true;
+            for (int ox = oxa; ox <= oxb && ok; ++ox) {
+                for (int oy = ox > 0 ? 0 : 1; oy <= RS; ++oy, ++q) {
+                    const int s = q % kStages;
+                    if (q >= kStages && !mbar_wait(&empty[s], ((q / kStages) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    if (*(volatile int*)&s_abort) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[s], kStageElems * sizeof(WT));
+                    tma_load_3d(stages + s * kStageElems, &tmap, &full[s], x0, y0, plane_index(oy, ox, RS));
+                }
+            }
+            if (!ok) {
+                *(volatile int*)&s_abort = 1;
+                atomicOr(err, 1u);
+            }
+            // do not leave while copies into this CTA's shared memory are in flight
+            for (int back = 1; back <= kStages && q - back >= 0; ++back) {
+                const int qq = q - back;
+                mbar_wait(&full[qq % kStages], (qq / kStages) & 1);
+            }
+        }
+        return;
+    }
+
+    // consumers
+    const int c = tid;
+    const int lane = tid & 31;
+    float qo[kTH], tot[kTH], comp[kTH];
+#pragma unroll
+    for (int r = 0; r < kTH; ++r) {
+        qo[r] = qt[r * RW + c + RS];
+        tot[r] = 0.f;
+        comp[r] = 0.f;
+    }
+    int q = 0;
+    bool ok = true;
+    for (int ox = oxa; ox <= oxb; ++ox) {
+        const int col = c + RS + ox;
+        float strip[RH], bacc[RH], fw[kTH];
+#pragma unroll
+        for (int a = 0; a < RH; ++a) {
+            strip[a] = qt[a * RW + col];
+            bacc[a] = 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < kTH; ++r) fw[r] = 0.f;
+#pragma unroll
+        for (int oy = 0; oy <= RS; ++oy) {
+            if (oy == 0 && ox <= 0) continue;
+            const int s = q % kStages;
+            ++q;
+            if (!ok) continue;
+            if (!mbar_wait(&full[s], ((q - 1) / kStages) & 1) || *(volatile int*)&s_abort) {
+                ok = false;
+                *(volatile int*)&s_abort = 1;
+                atomicOr(err, 2u);
+                continue;
+            }
+            const WT* st = stages + s * kStageElems;
+            float w[kTH];
+#pragma unroll
+            for (int r = 0; r < kTH; ++r) w[r] = to_f32(st[r * kTW + c]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+#pragma unroll
+            for (int r = 0; r < kTH; ++r) {
+                fw[r] = fmaf(w[r], strip[r + oy], fw[r]);
+                bacc[r + oy] = fmaf(w[r], qo[r], bacc[r + oy]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kTH; ++r) two_sum_into(tot[r], comp[r], fw[r]);
+        // one o_x at a time: column `col` is updated by this thread only
+        consumer_sync();
+#pragma unroll
+        for (int a = 0; a < RH; ++a) two_sum_into(acc_hi[a * RW + col], acc_lo[a * RW + col], bacc[a]);
+    }
+    consumer_sync();
+#pragma unroll
+    for (int r = 0; r < kTH; ++r) {
+        two_sum_into(acc_hi[r * RW + c + RS], acc_lo[r * RW + c + RS], tot[r]);
+        acc_lo[r * RW + c + RS] += comp[r];
+    }
+    consumer_sync();
+    const size_t region = (size_t)RH * RW;
+    float* out = part + ((size_t)(slice * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * region;
+    for (int idx = c; idx < RH * RW; idx += kConsumers) out[idx] = acc_hi[idx] + acc_lo[idx];
+}
+
+// --------------------------------------------------------------------------- phase 2
+
+struct Cover {
+    const float* part;
+    int tiles_x, tiles_y, slices, rs;
+};
+
+// Sum of the partial regions covering pixel (i, j), in a fixed order.  The region
+// of tile (ty, tx) spans rows ty*kTH .. ty*kTH + kTH + rs - 1 and columns
+// tx*kTW - rs .. tx*kTW + kTW + rs - 1, so with rs <= kTH only the own tile row
+// and the one above, and the own tile column and its two neighbours, can cover it.
+__device__ __forceinline__ float gather_partials(const Cover& cv, int i, int j) {
+    const int RH = kTH + cv.rs, RW = kTW + 2 * cv.rs;
+    const size_t region = (size_t)RH * RW;
+    const int ty = i / kTH, tx = j / kTW;
+    CompSum acc;
+    for (int tyy = ty - 1; tyy <= ty; ++tyy) {
+        const int a = i - tyy * kTH;
+        if (tyy < 0 || a >= RH) continue;
+        for (int txx = tx - 1; txx <= tx + 1; ++txx) {
+            const int b = j - txx * kTW + cv.rs;
+            if (txx < 0 || txx >= cv.tiles_x || b < 0 || b >= RW) continue;
+            for (int sl = 0; sl < cv.slices; ++sl) {
+                const float* reg = cv.part + ((size_t)(sl * cv.tiles_y + tyy) * cv.tiles_x + txx) * region;
+                acc.add(reg[(size_t)a * RW + b]);
+            }
+        }
+    }
+    return acc.value();
+}
+
+template <int MODE>  // 0 balance, 1 apply, 2 apply + dual
+__global__ void __launch_bounds__(256)
+stencil_p2_kernel(Cover cv, int H, int W, const float* __restrict__ d, const float* __restrict__ t_fin,
+                  float inv_m, const float* __restrict__ z, float* __restrict__ out0,
+                  float* __restrict__ out1, float* __restrict__ out2, PassStat* __restrict__ stats,
+                  BalanceCtl* __restrict__ ctl, int pass, SolveRed red, int iter) {
+    if (MODE == 0 && *(volatile int*)&ctl->done) return;
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i = blockIdx.y * 8 + threadIdx.y;
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    double r0 = 0.0, r1 = 0.0;
+    if (i < H && j < W) {
+        const size_t s = (size_t)i * W + j;
+        const float A = gather_partials(cv, i, j);
+        const float ds = d[s];
+        if (MODE == 0) {
+            const float tt = ds + A;  // (K1 d)_s with K1(s, s) = 1
+            out0[s] = sqrtf(ds / tt);  // next scaling
+            out1[s] = tt;              // kept for the closure of Eq. S3
+            const double prod = (double)ds * (double)tt;
+            r0 = fabs(prod - 1.0);
+            r1 = prod;
+        } else {
+            // W z = c_s z_s + (d_s / m) sum_{r != s} K1 d_r z_r, c_s = 1 - (d_s / m)(t_s - d_s)
+            const float zs = z[s];
+            const float dm = ds * inv_m;
+            const float cs = 1.f - dm * (t_fin[s] - ds);
+            const float vn = fmaf(dm, A, cs * zs);
+            if (MODE == 1) {
+                out0[s] = vn;
+            } else {
+                const float vo = out0[s];
+                const float uo = out1[s];
+                const float un = zs - vn;
+                out0[s] = vn;
+                out1[s] = un;
+                const double dp = (double)un - (double)uo;
+                const double dd = (double)vn - (double)vo;
+                r0 = dp * dp;
+                r1 = dd * dd;
+            }
+        }
+    }
+    if (MODE == 1) return;
+    __shared__ double s0[8], s1[8];
+    __shared__ bool is_last;
+    if (MODE == 0) {
+        r0 = warp_max(r0);
+        r1 = warp_max(r1);
+    } else {
+        r0 = warp_sum(r0);
+        r1 = warp_sum(r1);
+    }
+    if (lane == 0) {
+        s0[warp] = r0;
+        s1[warp] = r1;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            if (MODE == 0) {
+                a = fmax(a, s0[w]);
+                b = fmax(b, s1[w]);
+            } else {
+                a += s0[w];
+                b += s1[w];
+            }
+        }
+        const unsigned nblocks = gridDim.x * gridDim.y;
+        const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+        if (MODE == 0) {
+            PassStat* ps = stats + pass;
+            atomic_max_nonneg(&ps->eps_bits, a);
+            atomic_max_nonneg(&ps->m_bits, b);
+            __threadfence();
+            if (atomicAdd(&ps->arrive, 1u) == nblocks - 1) {
+                __threadfence();
+                const double e = __longlong_as_double((long long)atomicAdd(&ps->eps_bits, 0ull));
+                int done = 0, status = 0;
+                if (e <= ctl->tol) {
+                    done = 1;
+                } else if (pass >= ctl->maxit) {
+                    done = 1;
+                    status = 6;
+                } else if (e < 0.99 * ctl->best) {
+                    ctl->best = e;
+                    ctl->since_best = 0;
+                } else if (++ctl->since_best >= 3) {
+                    done = 1;
+                    status = 7;
+                }
+                if (done) {
+                    ctl->final_pass = pass;
+                    ctl->status = status;
+                    __threadfence();
+                    *(volatile int*)&ctl->done = 1;
+                }
+            }
+            is_last = false;
+        } else {
+            red.partials[2 * bid] = a;
+            red.partials[2 * bid + 1] = b;
+            __threadfence();
+            is_last = atomicAdd(red.arrive + iter, 1u) == nblocks - 1;
+        }
+    }
+    __syncthreads();
+    if (MODE == 2 && is_last) {
+        __threadfence();
+        const unsigned nblocks = gridDim.x * gridDim.y;
+        double a = 0.0, b = 0.0;
+        for (unsigned qb = t; qb < nblocks; qb += 256) {
+            a += ((volatile double*)red.partials)[2 * qb];
+            b += ((volatile double*)red.partials)[2 * qb + 1];
+        }
+        __shared__ double ra[256], rb[256];
+        ra[t] = a;
+        rb[t] = b;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (t < w) {
+                ra[t] += ra[t + w];
+                rb[t] += rb[t + w];
+            }
+            __syncthreads();
+        }
+        if (t == 0) {
+            red.hist[2 * iter] = ra[0];
+            red.hist[2 * iter + 1] = rb[0];
+        }
+    }
+    (void)out2;
+}
+
+template <int RS, typename WT>
+size_t p1_smem_bytes() {
+    return (size_t)kStages * kTH * kTW * sizeof(WT) + 3 * sizeof(float) * (size_t)(kTH + RS) * (kTW + 2 * RS) +
+           2 * kStages * sizeof(uint64_t);
+}
+
+template <int RS, typename WT>
+cudaError_t p1_launch(const TmaPlan& plan, int H, int W, const float* d, const float* z, unsigned* err,
+                      const int* skip, cudaStream_t st) {
+    static bool configured = false;
+    const size_t smem = p1_smem_bytes<RS, WT>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(stencil_p1_kernel<RS, WT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid(plan.tiles_x, plan.tiles_y, plan.splits.n);
+    stencil_p1_kernel<RS, WT><<<grid, kThreads, smem, st>>>(*(const CUtensorMap*)plan.tmap, H, W, d, z,
+                                                            plan.splits, plan.partials, err, skip);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t p1_dispatch(int rs, const TmaPlan& plan, int H, int W, const float* d, const float* z,
+                        unsigned* err, const int* skip, cudaStream_t st) {
+    switch (rs) {
+        case 1: return p1_launch<1, WT>(plan, H, W, d, z, err, skip, st);
+        case 2: return p1_launch<2, WT>(plan, H, W, d, z, err, skip, st);
+        case 3: return p1_launch<3, WT>(plan, H, W, d, z, err, skip, st);
+        case 4: return p1_launch<4, WT>(plan, H, W, d, z, err, skip, st);
+        case 5: return p1_launch<5, WT>(plan, H, W, d, z, err, skip, st);
+        case 6: return p1_launch<6, WT>(plan, H, W, d, z, err, skip, st);
+        case 7: return p1_launch<7, WT>(plan, H, W, d, z, err, skip, st);
+        case 8: return p1_launch<8, WT>(plan, H, W, d, z, err, skip, st);
+        case 10: return p1_launch<10, WT>(plan, H, W, d, z, err, skip, st);
+        case 12: return p1_launch<12, WT>(plan, H, W, d, z, err, skip, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+Cover cover_of(const TmaPlan& plan, int rs) {
+    return Cover{plan.partials, plan.tiles_x, plan.tiles_y, plan.splits.n, rs};
+}
+
+dim3 p2_grid(int H, int W) { return dim3((W + 31) / 32, (H + 7) / 8); }
+
+}  // namespace
+
+bool tma_path_supports(int rs) {
+    return rs == 1 || rs == 2 || rs == 3 || rs == 4 || rs == 5 || rs == 6 || rs == 7 || rs == 8 || rs == 10 ||
+           rs == 12;
+}
+
+int tma_tile_w() { return kTW; }
+int tma_tile_h() { return kTH; }
+size_t tma_region_floats(int rs) { return (size_t)(kTH + rs) * (kTW + 2 * rs); }
+int tma_p2_blocks(int H, int W) {
+    const dim3 g = p2_grid(H, W);
+    return (int)(g.x * g.y);
+}
+
+cudaError_t launch_tma_gather(int dtype, const TmaPlan& plan, int H, int W, int rs, const float* d,
+                              const float* z, unsigned* err, const int* skip, cudaStream_t st) {
+    switch (dtype) {
+        case 0: return p1_dispatch<float>(rs, plan, H, W, d, z, err, skip, st);
+        case 1: return p1_dispatch<__half>(rs, plan, H, W, d, z, err, skip, st);
+        default: return p1_dispatch<__nv_bfloat16>(rs, plan, H, W, d, z, err, skip, st);
+    }
+}
+
+cudaError_t launch_tma_balance_finish(const TmaPlan& plan, int H, int W, int rs, const float* d_in,
+                                      float* d_out, float* t_out, PassStat* stats, BalanceCtl* ctl, int pass,
+                                      cudaStream_t st) {
+    stencil_p2_kernel<0><<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d_in, nullptr, 0.f,
+                                                               nullptr, d_out, t_out, nullptr, stats, ctl,
+                                                               pass, SolveRed{}, 0);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tma_apply_finish(const TmaPlan& plan, int H, int W, int rs, const float* d, const float* t,
+                                    float inv_m, const float* z, float* y, cudaStream_t st) {
+    stencil_p2_kernel<1><<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d, t, inv_m, z, y,
+                                                               nullptr, nullptr, nullptr, nullptr, 0,
+                                                               SolveRed{}, 0);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tma_dual_finish(const TmaPlan& plan, int H, int W, int rs, const float* d, const float* t,
+                                   float inv_m, const float* z, float* v, float* u, SolveRed red, int iter,
+                                   cudaStream_t st) {
+    stencil_p2_kernel<2><<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d, t, inv_m, z, v, u,
+                                                               nullptr, nullptr, nullptr, 0, red, iter);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace dsg

@@ -28,6 +28,11 @@ CASES = [
     (20, 20, 0, 3, 0.1),   # 1x1 patches
     (12, 13, 10, 1, 0.5),  # patch larger than the image
     (1, 40, 1, 3, 0.2),    # single row
+    (30, 35, 1, 6, 0.15),
+    (24, 50, 2, 8, 0.1),
+    (35, 140, 2, 12, 0.1),  # two column tiles, largest compiled radius
+    (26, 29, 2, 9, 0.1),    # radius without a compiled TMA kernel: generic gather path
+    (40, 300, 3, 10, 0.08),  # three column tiles, ragged, split offsets
 ]
 
 

@@ -153,7 +153,7 @@ struct dsgnlm {
     int iters = 0;
     double resid = 0.0;
     // Algorithm 1 workspace
-    DevBuf z, rlo, partials, arrive, hist;
+    DevBuf z, x2, rlo, partials, arrive, hist;
     // optional per-kernel timing
     bool prof = false;
     ProfPool pools[kProfKinds];
@@ -185,6 +185,7 @@ struct dsgnlm {
         stats.release();
         ctl.release();
         z.release();
+        x2.release();
         rlo.release();
         partials.release();
         arrive.release();
@@ -525,10 +526,10 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
     const size_t n = (size_t)H * W;
     const int nblocks = h->fast ? tma_p2_blocks(H, W) : apply_grid_blocks(H, W);
     DSG_CK(h->z.ensure(n * sizeof(float)));
-    DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nblocks));
+    DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nblocks * (h->fast ? (size_t)iters : 1)));
     DSG_CK(h->arrive.ensure(sizeof(unsigned) * (size_t)iters));
     DSG_CK(h->hist.ensure(sizeof(double) * 2 * (size_t)iters));
-    if (p->kind == LPNP_SR2) DSG_CK(h->rlo.ensure(sizeof(float) * (n / 4)));
+    if (p->kind == LPNP_SR2) DSG_CK(h->x2.ensure(n * sizeof(float)));
     DSG_CK(cudaMemsetAsync(h->arrive.p, 0, sizeof(unsigned) * (size_t)iters, h->stream));
     SolveRed red{h->partials.as<double>(), h->arrive.as<unsigned>(), h->hist.as<double>()};
     const float mu = (float)(1.0 / ((double)p->alpha + (double)rho));
@@ -537,11 +538,11 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
     for (int it = 0; it < iters; ++it) {
         DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
             if (p->kind == LPNP_SR2) {
-                cudaError_t e = launch_sr_forward(p->x, H, W, taps, p->y, -1.0f, h->rlo.as<float>(),
-                                                  h->stream);
-                if (e != cudaSuccess) return e;
-                return launch_sr_xupdate(h->rlo.as<float>(), H, W, taps, p->x, p->v, p->u,
-                                         h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
+                // x alternates between the caller's buffer and the handle's copy
+                float* xa = (it & 1) ? h->x2.as<float>() : p->x;
+                float* xb = (it & 1) ? p->x : h->x2.as<float>();
+                return launch_sr_xupdate_fused(xa, xb, p->y, H, W, taps, p->v, p->u, h->z.as<float>(), mu,
+                                               p->alpha, rho, p->constraint, h->stream);
             }
             return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
                                       h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
@@ -558,6 +559,9 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
                                      h->z.as<float>(), p->v, p->u, red, it, h->stream);
         }));
     }
+    if (h->fast) DSG_CK(launch_reduce_residuals(red, iters, nblocks, h->stream));
+    if (p->kind == LPNP_SR2 && (iters & 1))
+        DSG_CK(cudaMemcpyAsync(p->x, h->x2.p, n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     if (p->resid_hist) {
         DSG_CK(h->stage(sizeof(double) * 2 * (size_t)iters));
         DSG_CK(cudaMemcpyAsync(h->host_stage, h->hist.p, sizeof(double) * 2 * (size_t)iters,

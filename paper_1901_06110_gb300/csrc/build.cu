@@ -2,7 +2,7 @@
 // Eq. S1; the first aggregation of Algorithm 2 and the fast patch distances of
 // Sec. 3), stored as half-window planes.
 //
-// One CTA owns a TH x TW spatial tile and a chunk of consecutive half-window
+// One CTA owns a 32 x 32 spatial tile and a chunk of consecutive half-window
 // offsets.  It stages the guide tile with the halo every offset of the chunk
 // needs (patch radius on all sides plus the search radius downwards and
 // sideways; half-window offsets never point upwards) in shared memory once, then
@@ -23,16 +23,19 @@ namespace dsg {
 
 namespace {
 
-constexpr int kTW = 32;
-constexpr int kTH = 16;
-constexpr int kThreads = 256;
-constexpr int kChunk = 20;  // offsets per CTA
+constexpr int kTW = 32;   // tile columns (= threadIdx.x)
+constexpr int kTH = 32;   // tile rows
+constexpr int kBY = 8;    // threadIdx.y
+constexpr int kThreads = kTW * kBY;
+constexpr int kChunk = 22;  // offsets per CTA
 
-template <typename WT>
+// RP >= 0: patch radius known at compile time; RP < 0: runtime radius rp_rt.
+template <typename WT, int RP>
 __global__ void __launch_bounds__(kThreads)
-build_kernel(const float* __restrict__ guide, int H, int W, int rp, int rs, float c,
+build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, float c,
              WT* __restrict__ planes) {
     extern __shared__ float smem[];
+    const int rp = RP >= 0 ? RP : rp_rt;
     const int nh = num_half_offsets(rs);
     const int y0 = blockIdx.y * kTH;
     const int x0 = blockIdx.x * kTW;
@@ -48,13 +51,17 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp, int rs, floa
     float* G = smem;
     float* E = G + GH * GW;
     float* R = E + EH * EW;
+    int* rows = reinterpret_cast<int*>(R + EH * kTW);
+    int* cols = rows + GH;
 
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < GH * GW; idx += kThreads) {
-        const int gy = idx / GW, gx = idx - gy * GW;
-        const int iy = sym_index(y0 - rp + gy, H);
-        const int ix = sym_index(x0 - rp - rs + gx, W);
-        G[idx] = guide[(size_t)iy * W + ix];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * kTW + tx;
+    for (int a = tid; a < GH; a += kThreads) rows[a] = sym_index(y0 - rp + a, H);
+    for (int b = tid; b < GW; b += kThreads) cols[b] = sym_index(x0 - rp - rs + b, W);
+    __syncthreads();
+    for (int a = ty; a < GH; a += kBY) {
+        const float* grow = guide + (size_t)rows[a] * W;
+        for (int b = tx; b < GW; b += kTW) G[a * GW + b] = grow[cols[b]];
     }
     __syncthreads();
 
@@ -64,32 +71,41 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp, int rs, floa
     for (int k = k_begin; k < k_end; ++k) {
         int oy, ox;
         half_offset(k, rs, oy, ox);
-        for (int idx = tid; idx < EH * EW; idx += kThreads) {
-            const int ey = idx / EW, ex = idx - ey * EW;
-            const float a = G[ey * GW + ex + rs];
-            const float b = G[(ey + oy) * GW + ex + rs + ox];
-            const float df = a - b;
-            E[idx] = df * df;
+        // E(p) = (g(p) - g(p + o))^2 over the tile + patch halo
+        for (int ey = ty; ey < EH; ey += kBY) {
+            const float* ga = G + ey * GW + rs;
+            const float* gb = G + (ey + oy) * GW + rs + ox;
+            for (int ex = tx; ex < EW; ex += kTW) {
+                const float df = ga[ex] - gb[ex];
+                E[ey * EW + ex] = df * df;
+            }
         }
         __syncthreads();
-        for (int idx = tid; idx < EH * kTW; idx += kThreads) {
-            const int ry = idx / kTW, rx = idx - ry * kTW;
-            const float* e = E + ry * EW + rx;
+        // R(p) = sum over the 2 rp + 1 columns of the patch row
+        for (int ry = ty; ry < EH; ry += kBY) {
+            const float* e = E + ry * EW + tx;
             float acc = 0.f;
-            for (int t = 0; t <= 2 * rp; ++t) acc += e[t];
-            R[idx] = acc;
+#pragma unroll
+            for (int t = 0; t <= 2 * (RP >= 0 ? RP : 0); ++t) acc += e[t];
+            if (RP < 0)
+                for (int t = 1; t <= 2 * rp; ++t) acc += e[t];
+            R[ry * kTW + tx] = acc;
         }
         __syncthreads();
         const float hat = (1.0f - fabsf((float)oy) * inv_hat) * (1.0f - fabsf((float)ox) * inv_hat);
         WT* out = planes + (size_t)k * plane;
-        for (int idx = tid; idx < kTH * kTW; idx += kThreads) {
-            const int ty = idx / kTW, tx = idx - ty * kTW;
-            const int i = y0 + ty, j = x0 + tx;
+        const int j = x0 + tx;
+        const bool col_ok = j < W && j + ox >= 0 && j + ox < W;
+        for (int py = ty; py < kTH; py += kBY) {
+            const int i = y0 + py;
             if (i >= H || j >= W) continue;
-            const float* r = R + ty * kTW + tx;
+            const float* r = R + py * kTW + tx;
             float D = 0.f;
-            for (int t = 0; t <= 2 * rp; ++t) D += r[t * kTW];
-            const bool inside = (i + oy < H) && (j + ox >= 0) && (j + ox < W);
+#pragma unroll
+            for (int t = 0; t <= 2 * (RP >= 0 ? RP : 0); ++t) D += r[t * kTW];
+            if (RP < 0)
+                for (int t = 1; t <= 2 * rp; ++t) D += r[t * kTW];
+            const bool inside = col_ok && (i + oy < H);
             const float w = inside ? hat * __expf(-D * c) : 0.f;
             out[(size_t)i * Wp + j] = from_f32<WT>(w);
         }
@@ -98,23 +114,36 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp, int rs, floa
     }
 }
 
-template <typename WT>
-cudaError_t launch_build_t(const float* guide, int H, int W, int rp, int rs, float c, WT* planes,
-                           cudaStream_t st) {
+template <typename WT, int RP>
+cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, float c, WT* planes,
+                            cudaStream_t st) {
     const int nh = num_half_offsets(rs);
     if (nh == 0) return cudaSuccess;
     const int GH = kTH + 2 * rp + rs, GW = kTW + 2 * rp + 2 * rs;
     const int EH = kTH + 2 * rp, EW = kTW + 2 * rp;
-    const size_t smem = sizeof(float) * (size_t)(GH * GW + EH * EW + EH * kTW);
+    const size_t smem = sizeof(float) * (size_t)(GH * GW + EH * EW + EH * kTW) + sizeof(int) * (GH + GW);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(build_kernel<WT>,
+        cudaError_t e = cudaFuncSetAttribute(build_kernel<WT, RP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, (nh + kChunk - 1) / kChunk);
-    build_kernel<WT><<<grid, kThreads, smem, st>>>(guide, H, W, rp, rs, c, planes);
+    build_kernel<WT, RP><<<grid, dim3(kTW, kBY), smem, st>>>(guide, H, W, rp, rs, c, planes);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t launch_build_t(const float* guide, int H, int W, int rp, int rs, float c, WT* planes,
+                           cudaStream_t st) {
+    switch (rp) {
+        case 1: return launch_build_rp<WT, 1>(guide, H, W, rp, rs, c, planes, st);
+        case 2: return launch_build_rp<WT, 2>(guide, H, W, rp, rs, c, planes, st);
+        case 3: return launch_build_rp<WT, 3>(guide, H, W, rp, rs, c, planes, st);
+        case 4: return launch_build_rp<WT, 4>(guide, H, W, rp, rs, c, planes, st);
+        case 5: return launch_build_rp<WT, 5>(guide, H, W, rp, rs, c, planes, st);
+        default: return launch_build_rp<WT, -1>(guide, H, W, rp, rs, c, planes, st);
+    }
 }
 
 }  // namespace

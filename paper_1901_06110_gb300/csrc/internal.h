@@ -27,10 +27,11 @@ struct BalanceCtl {
     int pad;
 };
 
-// Solve-loop reduction state: per-block partial sums, one arrival counter and one
-// two-value history slot per iteration.
+// Solve-loop reduction state: per-block partial sums of every iteration (reduced
+// after the loop by launch_reduce_residuals), one arrival counter per iteration
+// (generic path) and one two-value history slot per iteration.
 struct SolveRed {
-    double* partials;        // [2 * nblocks]
+    double* partials;        // [iters][nblocks][2] (TMA path) or [nblocks][2] (generic path)
     unsigned int* arrive;    // [iters]
     double* hist;            // [2 * iters]: sum (x-v)^2 and sum (v-v_prev)^2
 };
@@ -70,6 +71,7 @@ cudaError_t launch_tma_balance_finish(const TmaPlan& plan, int H, int W, int rs,
 cudaError_t launch_tma_apply_finish(const TmaPlan& plan, int H, int W, int rs, const float* d,
                                     const float* t, float inv_m, const float* z, float* y,
                                     cudaStream_t st);
+cudaError_t launch_reduce_residuals(SolveRed red, int iters, int nblocks, cudaStream_t st);
 cudaError_t launch_tma_dual_finish(const TmaPlan& plan, int H, int W, int rs, const float* d,
                                    const float* t, float inv_m, const float* z, float* v, float* u,
                                    SolveRed red, int iter, cudaStream_t st);
@@ -105,6 +107,10 @@ cudaError_t launch_sr_adjoint(const float* r, int H, int W, BlurTaps taps, float
 cudaError_t launch_sr_xupdate(const float* r, int H, int W, BlurTaps taps, float* x,
                               const float* v, const float* u, float* z, float mu, float alpha,
                               float rho, int constraint, cudaStream_t st);
+// fused: r = A x_in - y, x_out <- Pi_C(mu (alpha x_in + rho (v - u) - A^T r)), z <- x_out + u
+cudaError_t launch_sr_xupdate_fused(const float* x_in, float* x_out, const float* y, int H, int W,
+                                    BlurTaps taps, const float* v, const float* u, float* z, float mu,
+                                    float alpha, float rho, int constraint, cudaStream_t st);
 // grad f for SPI
 cudaError_t launch_spi_grad(const float* x, const uint8_t* counts, int n, int K, float eta,
                             float eps, float* grad, cudaStream_t st);

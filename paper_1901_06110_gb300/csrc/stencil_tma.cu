@@ -41,7 +41,7 @@ constexpr int kTW = 128;                 // tile columns (= consumer threads)
 constexpr int kConsumers = kTW;
 constexpr int kConsumerWarps = kConsumers / 32;
 constexpr int kThreads = kConsumers + 32;  // + one producer warp
-constexpr int kStages = 6;
+constexpr int kStages = 8;
 constexpr long long kWaitBudget = 4000000000LL;  // cycles (about 2 s) before a wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -134,20 +134,6 @@ stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const 
     const int oxa = splits.ox_lo[slice];
     const int oxb = splits.ox_hi[slice];
 
-    // q over the tile + halo (zero outside the image); accumulators cleared
-    for (int idx = tid; idx < RH * RW; idx += kThreads) {
-        const int a = idx / RW, b = idx - a * RW;
-        const int i = y0 + a, j = x0 - RS + b;
-        float v = 0.f;
-        if (i < H && j >= 0 && j < W) {
-            const size_t p = (size_t)i * W + j;
-            v = d[p];
-            if (z) v *= z[p];
-        }
-        qt[idx] = v;
-        acc_hi[idx] = 0.f;
-        acc_lo[idx] = 0.f;
-    }
     if (tid == 0) {
         s_abort = 0;
         for (int s = 0; s < kStages; ++s) {
@@ -160,7 +146,8 @@ stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const 
     __syncthreads();
 
     if (tid >= kConsumers) {
-        // producer: one elected thread streams the plane tiles in consumption order
+        // producer: one elected thread streams the plane tiles in consumption order;
+        // the first kStages loads overlap the consumers' staging of q below
         if (tid == kConsumers) {
             int q = 0;
             bool ok = true;
@@ -191,6 +178,22 @@ stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const 
         }
         return;
     }
+
+    // q over the tile + halo (zero outside the image); accumulators cleared
+    for (int idx = tid; idx < RH * RW; idx += kConsumers) {
+        const int a = idx / RW, b = idx - a * RW;
+        const int i = y0 + a, j = x0 - RS + b;
+        float v = 0.f;
+        if (i < H && j >= 0 && j < W) {
+            const size_t p = (size_t)i * W + j;
+            v = d[p];
+            if (z) v *= z[p];
+        }
+        qt[idx] = v;
+        acc_hi[idx] = 0.f;
+        acc_lo[idx] = 0.f;
+    }
+    consumer_sync();
 
     // consumers
     const int c = tid;
@@ -269,21 +272,39 @@ struct Cover {
 // tx*kTW - rs .. tx*kTW + kTW + rs - 1, so with rs <= kTH only the own tile row
 // and the one above, and the own tile column and its two neighbours, can cover it.
 __device__ __forceinline__ float gather_partials(const Cover& cv, int i, int j) {
-    const int RH = kTH + cv.rs, RW = kTW + 2 * cv.rs;
-    const size_t region = (size_t)RH * RW;
+    const int rs = cv.rs;
+    const int RW = kTW + 2 * rs;
+    const size_t region = (size_t)(kTH + rs) * RW;
     const int ty = i / kTH, tx = j / kTW;
+    const int li = i - ty * kTH, lj = j - tx * kTW;
+    const bool up = ty >= 1 && li < rs;
+    const bool left = tx >= 1 && lj < rs;
+    const bool right = tx + 1 < cv.tiles_x && lj >= kTW - rs;
+    // (tile, cell) offsets of the six candidates, upper row first, left to right
+    const size_t row_up = (size_t)(ty - 1) * cv.tiles_x, row_own = (size_t)ty * cv.tiles_x;
+    const size_t cell_up = (size_t)(li + kTH) * RW, cell_own = (size_t)li * RW;
+    size_t off[6];
+    bool use[6];
+    off[0] = (row_up + tx - 1) * region + cell_up + lj + kTW + rs; use[0] = up && left;
+    off[1] = (row_up + tx) * region + cell_up + lj + rs;           use[1] = up;
+    off[2] = (row_up + tx + 1) * region + cell_up + lj - kTW + rs; use[2] = up && right;
+    off[3] = (row_own + tx - 1) * region + cell_own + lj + kTW + rs; use[3] = left;
+    off[4] = (row_own + tx) * region + cell_own + lj + rs;           use[4] = true;
+    off[5] = (row_own + tx + 1) * region + cell_own + lj - kTW + rs; use[5] = right;
+    // unused candidates point at the own cell, so every address formed is in bounds
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+        if (!use[c]) off[c] = off[4];
+    const size_t slice_stride = (size_t)cv.tiles_y * cv.tiles_x * region;
     CompSum acc;
-    for (int tyy = ty - 1; tyy <= ty; ++tyy) {
-        const int a = i - tyy * kTH;
-        if (tyy < 0 || a >= RH) continue;
-        for (int txx = tx - 1; txx <= tx + 1; ++txx) {
-            const int b = j - txx * kTW + cv.rs;
-            if (txx < 0 || txx >= cv.tiles_x || b < 0 || b >= RW) continue;
-            for (int sl = 0; sl < cv.slices; ++sl) {
-                const float* reg = cv.part + ((size_t)(sl * cv.tiles_y + tyy) * cv.tiles_x + txx) * region;
-                acc.add(reg[(size_t)a * RW + b]);
-            }
-        }
+    const float* base = cv.part;
+    for (int sl = 0; sl < cv.slices; ++sl, base += slice_stride) {
+        float v[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] = use[c] ? __ldcg(base + off[c]) : 0.f;
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            if (use[c]) acc.add(v[c]);
     }
     return acc.value();
 }
@@ -292,14 +313,14 @@ template <int MODE>  // 0 balance, 1 apply, 2 apply + dual
 __global__ void __launch_bounds__(256)
 stencil_p2_kernel(Cover cv, int H, int W, const float* __restrict__ d, const float* __restrict__ t_fin,
                   float inv_m, const float* __restrict__ z, float* __restrict__ out0,
-                  float* __restrict__ out1, float* __restrict__ out2, PassStat* __restrict__ stats,
-                  BalanceCtl* __restrict__ ctl, int pass, SolveRed red, int iter) {
+                  float* __restrict__ out1, PassStat* __restrict__ stats, BalanceCtl* __restrict__ ctl,
+                  int pass, SolveRed red, int iter) {
     if (MODE == 0 && *(volatile int*)&ctl->done) return;
     const int j = blockIdx.x * 32 + threadIdx.x;
     const int i = blockIdx.y * 8 + threadIdx.y;
     const int t = threadIdx.y * 32 + threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
-    double r0 = 0.0, r1 = 0.0;
+    float r0 = 0.f, r1 = 0.f;
     if (i < H && j < W) {
         const size_t s = (size_t)i * W + j;
         const float A = gather_partials(cv, i, j);
@@ -308,9 +329,8 @@ stencil_p2_kernel(Cover cv, int H, int W, const float* __restrict__ d, const flo
             const float tt = ds + A;  // (K1 d)_s with K1(s, s) = 1
             out0[s] = sqrtf(ds / tt);  // next scaling
             out1[s] = tt;              // kept for the closure of Eq. S3
-            const double prod = (double)ds * (double)tt;
-            r0 = fabs(prod - 1.0);
-            r1 = prod;
+            r0 = fabsf(fmaf(ds, tt, -1.f));  // |d_s t_s - 1| with a single rounding
+            r1 = ds * tt;
         } else {
             // W z = c_s z_s + (d_s / m) sum_{r != s} K1 d_r z_r, c_s = 1 - (d_s / m)(t_s - d_s)
             const float zs = z[s];
@@ -325,103 +345,100 @@ stencil_p2_kernel(Cover cv, int H, int W, const float* __restrict__ d, const flo
                 const float un = zs - vn;
                 out0[s] = vn;
                 out1[s] = un;
-                const double dp = (double)un - (double)uo;
-                const double dd = (double)vn - (double)vo;
+                const float dp = un - uo;  // x - v
+                const float dd = vn - vo;  // v - v_prev
                 r0 = dp * dp;
                 r1 = dd * dd;
             }
         }
     }
     if (MODE == 1) return;
-    __shared__ double s0[8], s1[8];
-    __shared__ bool is_last;
+    __shared__ float s0[8], s1[8];
     if (MODE == 0) {
         r0 = warp_max(r0);
         r1 = warp_max(r1);
     } else {
-        r0 = warp_sum(r0);
-        r1 = warp_sum(r1);
+        r0 = warp_sum_f(r0);
+        r1 = warp_sum_f(r1);
     }
     if (lane == 0) {
         s0[warp] = r0;
         s1[warp] = r1;
     }
     __syncthreads();
-    if (t == 0) {
+    if (t != 0) return;
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (MODE == 2) {
         double a = 0.0, b = 0.0;
         for (int w = 0; w < 8; ++w) {
-            if (MODE == 0) {
-                a = fmax(a, s0[w]);
-                b = fmax(b, s1[w]);
-            } else {
-                a += s0[w];
-                b += s1[w];
-            }
+            a += (double)s0[w];
+            b += (double)s1[w];
         }
-        const unsigned nblocks = gridDim.x * gridDim.y;
-        const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-        if (MODE == 0) {
-            PassStat* ps = stats + pass;
-            atomic_max_nonneg(&ps->eps_bits, a);
-            atomic_max_nonneg(&ps->m_bits, b);
-            __threadfence();
-            if (atomicAdd(&ps->arrive, 1u) == nblocks - 1) {
-                __threadfence();
-                const double e = __longlong_as_double((long long)atomicAdd(&ps->eps_bits, 0ull));
-                int done = 0, status = 0;
-                if (e <= ctl->tol) {
-                    done = 1;
-                } else if (pass >= ctl->maxit) {
-                    done = 1;
-                    status = 6;
-                } else if (e < 0.99 * ctl->best) {
-                    ctl->best = e;
-                    ctl->since_best = 0;
-                } else if (++ctl->since_best >= 3) {
-                    done = 1;
-                    status = 7;
-                }
-                if (done) {
-                    ctl->final_pass = pass;
-                    ctl->status = status;
-                    __threadfence();
-                    *(volatile int*)&ctl->done = 1;
-                }
-            }
-            is_last = false;
-        } else {
-            red.partials[2 * bid] = a;
-            red.partials[2 * bid + 1] = b;
-            __threadfence();
-            is_last = atomicAdd(red.arrive + iter, 1u) == nblocks - 1;
-        }
+        // per-block partial sums; reduced in a fixed order after the iterations
+        red.partials[2 * ((size_t)iter * nblocks + bid)] = a;
+        red.partials[2 * ((size_t)iter * nblocks + bid) + 1] = b;
+        return;
     }
-    __syncthreads();
-    if (MODE == 2 && is_last) {
+    float a = 0.f, b = 0.f;
+    for (int w = 0; w < 8; ++w) {
+        a = fmaxf(a, s0[w]);
+        b = fmaxf(b, s1[w]);
+    }
+    PassStat* ps = stats + pass;
+    atomic_max_nonneg(&ps->eps_bits, (double)a);
+    atomic_max_nonneg(&ps->m_bits, (double)b);
+    __threadfence();
+    if (atomicAdd(&ps->arrive, 1u) == nblocks - 1) {
+        // last block of this pass decides whether the balance stops
         __threadfence();
-        const unsigned nblocks = gridDim.x * gridDim.y;
-        double a = 0.0, b = 0.0;
-        for (unsigned qb = t; qb < nblocks; qb += 256) {
-            a += ((volatile double*)red.partials)[2 * qb];
-            b += ((volatile double*)red.partials)[2 * qb + 1];
+        const double e = __longlong_as_double((long long)atomicAdd(&ps->eps_bits, 0ull));
+        int done = 0, status = 0;
+        if (e <= ctl->tol) {
+            done = 1;
+        } else if (pass >= ctl->maxit) {
+            done = 1;
+            status = 6;
+        } else if (e < 0.99 * ctl->best) {
+            ctl->best = e;
+            ctl->since_best = 0;
+        } else if (++ctl->since_best >= 3) {
+            done = 1;
+            status = 7;
         }
-        __shared__ double ra[256], rb[256];
-        ra[t] = a;
-        rb[t] = b;
-        __syncthreads();
-        for (int w = 128; w > 0; w >>= 1) {
-            if (t < w) {
-                ra[t] += ra[t + w];
-                rb[t] += rb[t + w];
-            }
-            __syncthreads();
-        }
-        if (t == 0) {
-            red.hist[2 * iter] = ra[0];
-            red.hist[2 * iter + 1] = rb[0];
+        if (done) {
+            ctl->final_pass = pass;
+            ctl->status = status;
+            __threadfence();
+            *(volatile int*)&ctl->done = 1;
         }
     }
-    (void)out2;
+}
+
+// hist[k] = fixed-order sums of the per-block residual partials of iteration k
+__global__ void __launch_bounds__(256)
+reduce_residuals_kernel(SolveRed red, int nblocks) {
+    const int iter = blockIdx.x, t = threadIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int q = t; q < nblocks; q += 256) {
+        a += red.partials[2 * ((size_t)iter * nblocks + q)];
+        b += red.partials[2 * ((size_t)iter * nblocks + q) + 1];
+    }
+    __shared__ double ra[256], rb[256];
+    ra[t] = a;
+    rb[t] = b;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) {
+            ra[t] += ra[t + w];
+            rb[t] += rb[t + w];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        red.hist[2 * iter] = ra[0];
+        red.hist[2 * iter + 1] = rb[0];
+    }
 }
 
 template <int RS, typename WT>
@@ -500,8 +517,8 @@ cudaError_t launch_tma_balance_finish(const TmaPlan& plan, int H, int W, int rs,
                                       float* d_out, float* t_out, PassStat* stats, BalanceCtl* ctl, int pass,
                                       cudaStream_t st) {
     stencil_p2_kernel<0><<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d_in, nullptr, 0.f,
-                                                               nullptr, d_out, t_out, nullptr, stats, ctl,
-                                                               pass, SolveRed{}, 0);
+                                                               nullptr, d_out, t_out, stats, ctl, pass,
+                                                               SolveRed{}, 0);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -509,8 +526,7 @@ cudaError_t launch_tma_balance_finish(const TmaPlan& plan, int H, int W, int rs,
 cudaError_t launch_tma_apply_finish(const TmaPlan& plan, int H, int W, int rs, const float* d, const float* t,
                                     float inv_m, const float* z, float* y, cudaStream_t st) {
     stencil_p2_kernel<1><<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d, t, inv_m, z, y,
-                                                               nullptr, nullptr, nullptr, nullptr, 0,
-                                                               SolveRed{}, 0);
+                                                               nullptr, nullptr, nullptr, 0, SolveRed{}, 0);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -519,7 +535,14 @@ cudaError_t launch_tma_dual_finish(const TmaPlan& plan, int H, int W, int rs, co
                                    float inv_m, const float* z, float* v, float* u, SolveRed red, int iter,
                                    cudaStream_t st) {
     stencil_p2_kernel<2><<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d, t, inv_m, z, v, u,
-                                                               nullptr, nullptr, nullptr, 0, red, iter);
+                                                               nullptr, nullptr, 0, red, iter);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_residuals(SolveRed red, int iters, int nblocks, cudaStream_t st) {
+    if (iters <= 0) return cudaSuccess;
+    reduce_residuals_kernel<<<iters, 256, 0, st>>>(red, nblocks);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -202,6 +202,26 @@ dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad);
  * replayed on later calls with the same buffers. */
 dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters);
 
+/* Allocation-free super-resolution gradient: grad = A^T (A x - y), the same
+ * result as lpnp_gradient for a LPNP_SR2 problem, for callers that cannot
+ * allocate device memory when they need it (a plugin whose host framework owns
+ * every device allocation, a real-time loop that forbids allocation after
+ * start-up).  The paper has no counterpart: this is a deployment variant.
+ *
+ * x, grad device [H][W]; y device [H/2][W/2]; H, W even; blur as in lpnp_problem.
+ * Its scratch, the low-resolution residual A x - y, lives in one static device
+ * array of 1,048,576 floats (4 MiB) that every GPU loading the library keeps until
+ * exit, so (H/2)(W/2) must not exceed 1,048,576 (e.g. 2048 x 2048); larger sizes
+ * return DSGNLM_EINVAL before any work.  The call allocates nothing.  All calls on
+ * a device share that array: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised.  Every call overwrites the part it
+ * reads, so no state carries over between calls.  The first call on a device
+ * resolves the array's address (this may load the library's module onto the
+ * device) and should come before any stream capture on that device.
+ * Asynchronous on `stream`. */
+dsgnlm_status lpnp_sr_gradient_noalloc(const float* x, const float* y, int H, int W,
+                                       float blur_sigma, int blur_r, float* grad, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Misc
  * ------------------------------------------------------------------------- */

@@ -25,6 +25,12 @@ namespace {
 
 thread_local int g_last_cuda = 0;
 
+}  // namespace
+
+void dsg::record_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
+
+namespace {
+
 dsgnlm_status fail_cuda(cudaError_t e) {
     g_last_cuda = (int)e;
     return e == cudaErrorMemoryAllocation ? DSGNLM_ENOMEM : DSGNLM_ECUDA;

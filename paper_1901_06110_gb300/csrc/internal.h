@@ -7,6 +7,8 @@
 namespace dsg {
 
 void count_launches(uint64_t n);
+// makes `e` the value dsgnlm_last_cuda_error() returns in this thread
+void record_cuda_error(cudaError_t e);
 
 // balancing state in device memory, one slot per pass
 struct PassStat {

@@ -214,6 +214,20 @@ def lpnp_gradient(p: Problem, x: torch.Tensor) -> torch.Tensor:
     return g
 
 
+def lpnp_sr_gradient_noalloc(x: torch.Tensor, y: torch.Tensor, blur_sigma: float, blur_r: int,
+                             out: torch.Tensor | None = None) -> torch.Tensor:
+    """A^T (A x - y) without any device allocation inside the call (its scratch is a
+    fixed 4 MiB array shared by all calls on the device; see include/dsgnlm.h)."""
+    H, W = x.shape
+    g = torch.empty_like(x) if out is None else out
+    _check(_abi.load().lpnp_sr_gradient_noalloc(_ptr(x, torch.float32, "x"),
+                                                _ptr(y, torch.float32, "y", (H // 2) * (W // 2)), H, W,
+                                                float(blur_sigma), int(blur_r),
+                                                _ptr(g, torch.float32, "grad", H * W), _stream()),
+           "lpnp_sr_gradient_noalloc")
+    return g
+
+
 def lpnp_solve(p: Problem, rho: float, iters: int, residuals: bool = False):
     """Run Algorithm 1 in place on p.x, p.v, p.u.  With residuals=True returns the
     per-iteration (primal, dual) RMS residuals as a list of pairs."""

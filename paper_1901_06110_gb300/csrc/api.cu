@@ -16,7 +16,10 @@
 
 namespace dsg {
 static std::atomic<uint64_t> g_launches{0};
-void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local bool g_capturing = false;  // launches recorded into a graph are counted at replay
+void count_launches(uint64_t n) {
+    if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 }  // namespace dsg
 
 using namespace dsg;
@@ -148,8 +151,14 @@ struct dsgnlm {
     // TMA stencil path
     bool fast = false;
     TmaPlan plan{};
-    DevBuf tma_part, tbuf[2], err;
+    DevBuf tma_part, tbuf[2], err, bal_part;
     float* t_final = nullptr;
+    // balancing passes as a CUDA graph with a device-driven WHILE node
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t bal_graph = nullptr;
+    cudaGraphExec_t bal_exec = nullptr;
+    unsigned char bal_key[256] = {};
+    bool bal_graph_failed = false;
     float bw = 0.f;
     bool built = false, balanced = false;
     DevBuf planes, dbuf[2], stats, ctl;
@@ -180,7 +189,17 @@ struct dsgnlm {
         host_stage_bytes = n;
         return cudaSuccess;
     }
+    void release_graphs() {
+        if (bal_exec) cudaGraphExecDestroy(bal_exec);
+        if (bal_graph) cudaGraphDestroy(bal_graph);
+        bal_exec = nullptr;
+        bal_graph = nullptr;
+    }
     void release_all() {
+        release_graphs();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        cap_stream = nullptr;
+        bal_part.release();
         tma_part.release();
         tbuf[0].release();
         tbuf[1].release();
@@ -305,6 +324,91 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
     return DSGNLM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One balancing pass of the TMA path: phase-1 gather of K1 d, combine (next d, t and
+// per-block residual maxima), decision.  `parity` selects the d and t buffers.
+cudaError_t balance_pass(dsgnlm* h, int parity, cudaStream_t st, cudaGraphConditionalHandle cond, int use_cond) {
+    BalanceCtl* ctl = h->ctl.as<BalanceCtl>();
+    float* d_in = h->dbuf[parity].as<float>();
+    float* d_out = h->dbuf[parity ^ 1].as<float>();
+    cudaError_t e = launch_tma_gather(h->dtype, h->plan, h->H, h->W, h->rs, d_in, nullptr, h->err.as<unsigned>(),
+                                      &ctl->done, st);
+    if (e != cudaSuccess) return e;
+    e = launch_balance_combine(h->plan, h->H, h->W, h->rs, d_in, d_out, h->tbuf[parity].as<float>(),
+                               h->bal_part.as<float2>(), ctl, st);
+    if (e != cudaSuccess) return e;
+    return launch_balance_decide(h->bal_part.as<float2>(), balance_combine_blocks(h->H, h->W), ctl, cond, use_cond,
+                                 st);
+}
+
+// Everything a recorded balance graph depends on.
+void balance_key(const dsgnlm* h, unsigned char out[256]) {
+    std::memset(out, 0, 256);
+    const void* ptrs[8] = {h->planes.p, h->dbuf[0].p, h->dbuf[1].p, h->tbuf[0].p,
+                           h->tbuf[1].p, h->bal_part.p, h->ctl.p, h->err.p};
+    const int ints[5] = {h->H, h->W, h->rs, h->dtype, h->plan.splits.n};
+    std::memcpy(out, ptrs, sizeof ptrs);
+    std::memcpy(out + sizeof ptrs, ints, sizeof ints);
+    std::memcpy(out + 128, h->plan.tmap, 128);
+}
+
+// Record the passes once as a graph: a WHILE node whose body holds two passes
+// (even and odd buffers); the decision kernel clears the condition when the
+// balance stops, and kernels after the stop return at once.
+cudaError_t ensure_balance_graph(dsgnlm* h) {
+    unsigned char key[256];
+    balance_key(h, key);
+    if (h->bal_exec && std::memcmp(key, h->bal_key, 256) == 0) return cudaSuccess;
+    h->release_graphs();
+    cudaError_t e = cudaSuccess;
+    if (!h->cap_stream) {
+        e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            g_capturing = true;
+            cudaError_t e1 = balance_pass(h, 0, h->cap_stream, cond, 1);
+            if (e1 == cudaSuccess) e1 = balance_pass(h, 1, h->cap_stream, cond, 1);
+            g_capturing = false;
+            cudaGraph_t captured = body;
+            e = cudaStreamEndCapture(h->cap_stream, &captured);
+            if (e == cudaSuccess) e = e1;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->bal_exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        h->bal_exec = nullptr;
+        (void)cudaGetLastError();
+        return e;
+    }
+    h->bal_graph = g;
+    std::memcpy(h->bal_key, key, 256);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
 dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, double* resid_out) {
     if (!h) return DSGNLM_EINVAL;
     if (!h->built) return DSGNLM_NOT_BUILT;
@@ -316,11 +420,13 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     if (h->fast) {
         DSG_CK(h->tbuf[0].ensure(n * sizeof(float)));
         DSG_CK(h->tbuf[1].ensure(n * sizeof(float)));
+        DSG_CK(h->bal_part.ensure(sizeof(float2) * (size_t)balance_combine_blocks(h->H, h->W)));
+    } else {
+        DSG_CK(h->stats.ensure(sizeof(PassStat) * (size_t)(maxit + 1)));
+        DSG_CK(cudaMemsetAsync(h->stats.p, 0, sizeof(PassStat) * (size_t)(maxit + 1), h->stream));
     }
-    DSG_CK(h->stats.ensure(sizeof(PassStat) * (size_t)(maxit + 1)));
     DSG_CK(h->ctl.ensure(sizeof(BalanceCtl)));
     DSG_CK(h->stage(sizeof(BalanceCtl) + sizeof(PassStat)));
-    DSG_CK(cudaMemsetAsync(h->stats.p, 0, sizeof(PassStat) * (size_t)(maxit + 1), h->stream));
     BalanceCtl c0{};
     c0.done = 0;
     c0.final_pass = -1;
@@ -329,52 +435,61 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     c0.best = INFINITY;
     c0.tol = tol;
     c0.maxit = maxit;
+    c0.pass = 0;
     std::memcpy(h->host_stage, &c0, sizeof c0);
     DSG_CK(cudaMemcpyAsync(h->ctl.p, h->host_stage, sizeof c0, cudaMemcpyHostToDevice, h->stream));
     DSG_CK(launch_fill(h->dbuf[0].as<float>(), 1.0f, n, h->stream));
 
-    // Passes are launched in groups; a pass launched after the deciding one
-    // returns at once (the done flag is checked on entry), so the group size only
-    // trades wasted launches against host round trips.
     BalanceCtl c{};
-    const int group = 4;
-    for (int pass = 0; pass <= maxit; ++pass) {
-        DSG_CK(h->timed(DSGNLM_PROF_BALANCE, [&] {
-            float* d_in = h->dbuf[pass & 1].as<float>();
-            float* d_out = h->dbuf[(pass + 1) & 1].as<float>();
-            BalanceCtl* ctl = h->ctl.as<BalanceCtl>();
-            if (h->fast) {
-                cudaError_t e = launch_tma_gather(h->dtype, h->plan, h->H, h->W, h->rs, d_in, nullptr,
-                                                  h->err.as<unsigned>(), &ctl->done, h->stream);
-                if (e != cudaSuccess) return e;
-                return launch_tma_balance_finish(h->plan, h->H, h->W, h->rs, d_in, d_out,
-                                                 h->tbuf[pass & 1].as<float>(), h->stats.as<PassStat>(), ctl,
-                                                 pass, h->stream);
-            }
-            return launch_sinkhorn_pass(h->dtype, h->planes.p, h->H, h->W, h->rs, d_in, d_out,
-                                        h->stats.as<PassStat>(), ctl, pass, h->stream);
-        }));
-        if ((pass + 1) % group == 0 || pass == maxit) {
+    bool ran = false;
+    if (h->fast && !h->bal_graph_failed) {
+        if (ensure_balance_graph(h) == cudaSuccess) {
+            DSG_CK(h->timed(DSGNLM_PROF_BALANCE, [&] { return cudaGraphLaunch(h->bal_exec, h->stream); }));
             DSG_CK(cudaMemcpyAsync(h->host_stage, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost, h->stream));
             DSG_CK(cudaStreamSynchronize(h->stream));
             std::memcpy(&c, h->host_stage, sizeof c);
-            if (c.done) break;
+            // each WHILE iteration runs two passes of three kernels
+            if (c.done) count_launches(6 * (uint64_t)((c.final_pass + 2) / 2));
+            ran = true;
+        } else {
+            h->bal_graph_failed = true;  // conditional graphs unavailable: launch passes from the host
+        }
+    }
+    if (!ran) {
+        // Passes are launched in groups; a pass launched after the deciding one
+        // returns at once (the done flag is checked on entry), so the group size
+        // only trades wasted launches against host round trips.
+        const int group = 4;
+        for (int pass = 0; pass <= maxit; ++pass) {
+            DSG_CK(h->timed(DSGNLM_PROF_BALANCE, [&] {
+                if (h->fast) return balance_pass(h, pass & 1, h->stream, 0, 0);
+                return launch_sinkhorn_pass(h->dtype, h->planes.p, h->H, h->W, h->rs, h->dbuf[pass & 1].as<float>(),
+                                            h->dbuf[(pass + 1) & 1].as<float>(), h->stats.as<PassStat>(),
+                                            h->ctl.as<BalanceCtl>(), pass, h->stream);
+            }));
+            if ((pass + 1) % group == 0 || pass == maxit) {
+                DSG_CK(cudaMemcpyAsync(h->host_stage, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+                DSG_CK(cudaStreamSynchronize(h->stream));
+                std::memcpy(&c, h->host_stage, sizeof c);
+                if (c.done) break;
+            }
         }
     }
     if (!c.done || c.final_pass < 0) return DSGNLM_ECUDA;  // cannot happen: pass maxit decides
-    PassStat ps{};
-    DSG_CK(cudaMemcpyAsync(h->host_stage, h->stats.as<PassStat>() + c.final_pass, sizeof ps,
-                           cudaMemcpyDeviceToHost, h->stream));
-    DSG_CK(cudaStreamSynchronize(h->stream));
-    std::memcpy(&ps, h->host_stage, sizeof ps);
-    double eps, m;
-    std::memcpy(&eps, &ps.eps_bits, sizeof eps);
-    std::memcpy(&m, &ps.m_bits, sizeof m);
+    double eps = c.eps, m = c.m;
     if (h->fast) {
         unsigned errv = 0;
         DSG_CK(cudaMemcpy(&errv, h->err.p, sizeof errv, cudaMemcpyDeviceToHost));
         if (errv) return DSGNLM_TIMEOUT;
         h->t_final = h->tbuf[c.final_pass & 1].as<float>();
+    } else {
+        PassStat ps{};
+        DSG_CK(cudaMemcpyAsync(h->host_stage, h->stats.as<PassStat>() + c.final_pass, sizeof ps,
+                               cudaMemcpyDeviceToHost, h->stream));
+        DSG_CK(cudaStreamSynchronize(h->stream));
+        std::memcpy(&ps, h->host_stage, sizeof ps);
+        std::memcpy(&eps, &ps.eps_bits, sizeof eps);
+        std::memcpy(&m, &ps.m_bits, sizeof m);
     }
     h->d_final = h->dbuf[c.final_pass & 1].as<float>();
     h->m = m;
@@ -530,7 +645,7 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
     dsgnlm* h = p->den;
     const int H = p->H, W = p->W;
     const size_t n = (size_t)H * W;
-    const int nblocks = h->fast ? tma_p2_blocks(H, W) : apply_grid_blocks(H, W);
+    const int nblocks = h->fast ? combine_xupdate_blocks(H, W) : apply_grid_blocks(H, W);
     DSG_CK(h->z.ensure(n * sizeof(float)));
     DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nblocks * (h->fast ? (size_t)iters : 1)));
     DSG_CK(h->arrive.ensure(sizeof(unsigned) * (size_t)iters));
@@ -541,31 +656,71 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
     const float mu = (float)(1.0 / ((double)p->alpha + (double)rho));
     const BlurTaps taps = make_blur_taps(p->blur_sigma > 0.f ? p->blur_sigma : 1.f,
                                          p->kind == LPNP_SR2 ? p->blur_r : 0);
-    for (int it = 0; it < iters; ++it) {
-        DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
-            if (p->kind == LPNP_SR2) {
-                // x alternates between the caller's buffer and the handle's copy
-                float* xa = (it & 1) ? h->x2.as<float>() : p->x;
-                float* xb = (it & 1) ? p->x : h->x2.as<float>();
-                return launch_sr_xupdate_fused(xa, xb, p->y, H, W, taps, p->v, p->u, h->z.as<float>(), mu,
-                                               p->alpha, rho, p->constraint, h->stream);
-            }
-            return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
-                                      h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
-        }));
-        DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
-            if (h->fast) {
-                cudaError_t e = launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
-                                                  h->err.as<unsigned>(), nullptr, h->stream);
-                if (e != cudaSuccess) return e;
-                return launch_tma_dual_finish(h->plan, H, W, h->rs, h->d_final, h->t_final, h->inv_m,
-                                              h->z.as<float>(), p->v, p->u, red, it, h->stream);
-            }
-            return launch_apply_dual(h->dtype, h->planes.p, H, W, h->rs, h->d_final, h->inv_m,
-                                     h->z.as<float>(), p->v, p->u, red, it, h->stream);
-        }));
+    // For super-resolution x alternates between the caller's buffer (A) and the
+    // handle's copy (B): the update of iteration k writes B for even k, A for odd k.
+    float* xA = p->x;
+    float* xB = p->kind == LPNP_SR2 ? h->x2.as<float>() : p->x;
+    auto xupdate0 = [&]() -> cudaError_t {
+        if (p->kind == LPNP_SR2)
+            return launch_sr_xupdate_fused(xA, xB, p->y, H, W, taps, p->v, p->u, h->z.as<float>(), mu, p->alpha,
+                                           rho, p->constraint, h->stream);
+        return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
+                                  h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
+    };
+    if (h->fast) {
+        // iteration k: phase-1 gather of W z, then one pass that finishes v and u of
+        // iteration k and performs the x-update of iteration k + 1
+        DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, xupdate0));
+        EpilogueArgs ea{};
+        ea.H = H;
+        ea.W = W;
+        ea.d = h->d_final;
+        ea.t = h->t_final;
+        ea.inv_m = h->inv_m;
+        ea.z = h->z.as<float>();
+        ea.v = p->v;
+        ea.u = p->u;
+        ea.y = p->y;
+        ea.taps = taps;
+        ea.counts = p->counts;
+        ea.K = p->K;
+        ea.eta = p->eta;
+        ea.eps = p->spi_eps;
+        ea.mu = mu;
+        ea.alpha = p->alpha;
+        ea.rho = rho;
+        ea.constraint = p->constraint;
+        const int kind = p->kind == LPNP_SR2 ? 0 : 1;
+        for (int it = 0; it < iters; ++it) {
+            DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
+                return launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
+                                         h->err.as<unsigned>(), nullptr, h->stream);
+            }));
+            ea.do_x = it < iters - 1;
+            ea.x_in = (it & 1) ? xA : xB;
+            ea.x_out = (it & 1) ? xB : xA;
+            ea.partials = h->partials.as<double>() + 2 * (size_t)nblocks * it;
+            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_combine_xupdate(kind, h->plan, h->rs, ea, h->stream); }));
+        }
+        DSG_CK(launch_reduce_residuals(red, iters, nblocks, h->stream));
+    } else {
+        for (int it = 0; it < iters; ++it) {
+            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
+                if (p->kind == LPNP_SR2) {
+                    float* xa = (it & 1) ? xB : xA;
+                    float* xb = (it & 1) ? xA : xB;
+                    return launch_sr_xupdate_fused(xa, xb, p->y, H, W, taps, p->v, p->u, h->z.as<float>(), mu,
+                                                   p->alpha, rho, p->constraint, h->stream);
+                }
+                return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
+                                          h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
+            }));
+            DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
+                return launch_apply_dual(h->dtype, h->planes.p, H, W, h->rs, h->d_final, h->inv_m,
+                                         h->z.as<float>(), p->v, p->u, red, it, h->stream);
+            }));
+        }
     }
-    if (h->fast) DSG_CK(launch_reduce_residuals(red, iters, nblocks, h->stream));
     if (p->kind == LPNP_SR2 && (iters & 1))
         DSG_CK(cudaMemcpyAsync(p->x, h->x2.p, n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     if (p->resid_hist) {

@@ -19,14 +19,16 @@ struct PassStat {
 };
 
 struct BalanceCtl {
-    int done;        // set by the last block of the deciding pass
+    int done;        // set by the deciding pass
     int final_pass;  // pass whose scaling is the result (= number of updates)
     int status;      // 0 ok, 6 not converged, 7 stalled
     int since_best;  // passes since the residual last improved by 1%
     double best;     // smallest residual seen
     double tol;
     int maxit;
-    int pad;
+    int pass;        // current pass (TMA path: advanced on the device)
+    double eps;      // TMA path: residual of the last decided pass
+    double m;        // TMA path: max row sum of the last decided pass
 };
 
 // Solve-loop reduction state: per-block partial sums of every iteration (reduced
@@ -67,16 +69,10 @@ int tma_p2_blocks(int H, int W);
 cudaError_t launch_tma_gather(int dtype, const TmaPlan& plan, int H, int W, int rs, const float* d,
                               const float* z, unsigned* err, const int* skip, cudaStream_t st);
 // phase 2 epilogues
-cudaError_t launch_tma_balance_finish(const TmaPlan& plan, int H, int W, int rs, const float* d_in,
-                                      float* d_out, float* t_out, PassStat* stats, BalanceCtl* ctl,
-                                      int pass, cudaStream_t st);
 cudaError_t launch_tma_apply_finish(const TmaPlan& plan, int H, int W, int rs, const float* d,
                                     const float* t, float inv_m, const float* z, float* y,
                                     cudaStream_t st);
 cudaError_t launch_reduce_residuals(SolveRed red, int iters, int nblocks, cudaStream_t st);
-cudaError_t launch_tma_dual_finish(const TmaPlan& plan, int H, int W, int rs, const float* d,
-                                   const float* t, float inv_m, const float* z, float* v, float* u,
-                                   SolveRed red, int iter, cudaStream_t st);
 
 cudaError_t launch_fill(float* p, float value, size_t n, cudaStream_t st);
 
@@ -128,5 +124,37 @@ cudaError_t launch_spi_counts(const uint8_t* bits, int H, int W, int k_side, uin
 cudaError_t launch_spi_guide(const uint8_t* counts, int H, int W, int K, float eta, float* guide,
                              cudaStream_t st);
 cudaError_t launch_init(const float* guide, int n, float* x, float* v, float* u, cudaStream_t st);
+
+// Epilogues (epilogue.cu)
+int balance_combine_blocks(int H, int W);
+cudaError_t launch_balance_combine(const TmaPlan& plan, int H, int W, int rs, const float* d_in,
+                                   float* d_out, float* t_out, float2* part, const BalanceCtl* ctl,
+                                   cudaStream_t st);
+cudaError_t launch_balance_decide(const float2* part, int nblocks, BalanceCtl* ctl,
+                                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+
+struct EpilogueArgs {
+    int H, W;
+    const float* d;
+    const float* t;
+    float inv_m;
+    float* z;          // in: x + u of this iteration; out: x + u of the next one
+    float* v;
+    float* u;
+    const float* x_in;   // x of the next update (SR: read in halos)
+    float* x_out;        // its result (SR: another buffer; SPI: may equal x_in)
+    const float* y;      // SR observation
+    BlurTaps taps;
+    const uint8_t* counts;  // SPI
+    int K;
+    float eta, eps;
+    float mu, alpha, rho;
+    int constraint;
+    int do_x;            // 0 on the last iteration
+    double* partials;    // this iteration's per-block residual sums [nblocks][2]
+};
+int combine_xupdate_blocks(int H, int W);
+cudaError_t launch_combine_xupdate(int kind, const TmaPlan& plan, int rs, const EpilogueArgs& args,
+                                   cudaStream_t st);
 
 }  // namespace dsg

@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "xupdate.cuh"
 
 namespace dsg {
 
@@ -34,12 +35,6 @@ namespace {
 constexpr int kBX = 32, kBY = 8;
 
 dim3 grid2(int H, int W) { return dim3((W + kBX - 1) / kBX, (H + kBY - 1) / kBY); }
-
-__device__ __forceinline__ float project(float x, int constraint) {
-    if (constraint == 2) return fminf(fmaxf(x, 0.f), 1.f);
-    if (constraint == 1) return fmaxf(x, 0.f);
-    return x;
-}
 
 // out(q) = sum_a t(a) sum_b t(b) x(2q - (a, b)) + c aux(q), periodic
 __global__ void sr_forward_kernel(const float* __restrict__ x, int H, int W, BlurTaps taps,
@@ -103,101 +98,25 @@ __global__ void sr_xupdate_kernel(const float* __restrict__ rlo, int H, int W, B
     z[p] = xn + up;
 }
 
-// Fused linearized x-update for super-resolution, one CTA per kXH x kXW tile of
-// high-resolution pixels.  The CTA stages the x values its tile depends on (the
-// adjoint needs r = A x - y on the low-resolution pixels within blur_r of the
-// tile, and each of those needs x within blur_r of its even pixel), computes
-// r on that low-resolution window with separable sums, then g = A^T r on the
-// tile, then x <- Pi_C(mu (alpha x + rho (v - u) - g)) and z = x + u.  x is read
-// from x_in and written to x_out (other CTAs still read x_in in their halos).
-constexpr int kXH = 16, kXW = 32;
-constexpr int kMaxBlurR = 8;
-constexpr int kLH = (kXH - 1 + 2 * kMaxBlurR) / 2 + 2 + 1;   // low-res rows, worst case
-constexpr int kLW = (kXW - 1 + 2 * kMaxBlurR) / 2 + 2 + 1;   // low-res cols, worst case
-constexpr int kSH = 2 * (kLH - 1) + 2 * kMaxBlurR + 1;       // staged x rows
-constexpr int kSW = 2 * (kLW - 1) + 2 * kMaxBlurR + 1;       // staged x cols
-
-__device__ __forceinline__ int floor_div2(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
-
 __global__ void __launch_bounds__(256)
 sr_xupdate_fused_kernel(const float* __restrict__ x_in, float* __restrict__ x_out, const float* __restrict__ y,
                         int H, int W, BlurTaps taps, const float* __restrict__ v, const float* __restrict__ u,
                         float* __restrict__ z, float mu, float alpha, float rho, int constraint) {
-    __shared__ float X[kSH * kSW];
-    __shared__ float Hs[kSH * kLW];
-    __shared__ float Rl[kLH * kLW];
-    __shared__ float V[kXH * kLW];
-    __shared__ int rows[kSH], cols[kSW];
-    __shared__ float tp[2 * kMaxBlurR + 1];
-    const int R = taps.r;
-    const int G = R > 0 ? R : 1;  // staging margin (covers the tile's own pixels when R = 0)
-    const int h = H / 2, w = W / 2;
+    __shared__ SrTile tile;
     const int y0 = blockIdx.y * kXH, x0 = blockIdx.x * kXW;
-    const int qy_lo = floor_div2(y0 - G), qy_hi = floor_div2(y0 + kXH - 1 + G);
-    const int qx_lo = floor_div2(x0 - G), qx_hi = floor_div2(x0 + kXW - 1 + G);
-    const int LH = qy_hi - qy_lo + 1, LW = qx_hi - qx_lo + 1;
-    const int SH = 2 * (LH - 1) + 2 * G + 1, SW = 2 * (LW - 1) + 2 * G + 1;
-    const int tid = threadIdx.x;
-    for (int a = tid; a < SH; a += 256) rows[a] = wrap_index(2 * qy_lo - G + a, H);
-    for (int b = tid; b < SW; b += 256) cols[b] = wrap_index(2 * qx_lo - G + b, W);
-    if (tid < 2 * R + 1) tp[tid] = taps.t[tid];
-    __syncthreads();
-    for (int idx = tid; idx < SH * SW; idx += 256) {
-        const int a = idx / SW, b = idx - a * SW;
-        X[a * kSW + b] = x_in[(size_t)rows[a] * W + cols[b]];
-    }
-    __syncthreads();
-    // horizontal blur sums at the even columns 2 qx: staged column 2c + G - b
-    for (int idx = tid; idx < SH * LW; idx += 256) {
-        const int a = idx / LW, c = idx - a * LW;
-        const float* xr = X + a * kSW + 2 * c + G;
-        float acc = 0.f;
-        for (int b = -R; b <= R; ++b) acc = fmaf(tp[b + R], xr[-b], acc);
-        Hs[a * kLW + c] = acc;
-    }
-    __syncthreads();
-    // r = A x - y on the low-resolution window
-    for (int idx = tid; idx < LH * LW; idx += 256) {
-        const int l = idx / LW, c = idx - l * LW;
-        const float* hc = Hs + (2 * l + G) * kLW + c;
-        float acc = 0.f;
-        for (int a = -R; a <= R; ++a) acc = fmaf(tp[a + R], hc[-a * kLW], acc);
-        const int qy = wrap_index(qy_lo + l, h), qx = wrap_index(qx_lo + c, w);
-        Rl[l * kLW + c] = acc - y[(size_t)qy * w + qx];
-    }
-    __syncthreads();
-    // vertical adjoint sums: V(p_y, c) = sum_{a : p_y + a even} t(a) r((p_y + a) / 2, c)
-    for (int idx = tid; idx < kXH * LW; idx += 256) {
-        const int py = idx / LW, c = idx - py * LW;
-        const int p = y0 + py;
-        float acc = 0.f;
-        for (int a = -R + ((p - R) & 1); a <= R; a += 2)
-            acc = fmaf(tp[a + R], Rl[(floor_div2(p + a) - qy_lo) * kLW + c], acc);
-        V[py * kLW + c] = acc;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < kXH * kXW; idx += 256) {
+    sr_tile_prepare(tile, x_in, y, H, W, taps, y0, x0);
+    for (int idx = threadIdx.x; idx < kXH * kXW; idx += 256) {
         const int py = idx / kXW, px = idx - py * kXW;
         const int pi = y0 + py, pj = x0 + px;
         if (pi >= H || pj >= W) continue;
-        float g = 0.f;
-        for (int b = -R + ((pj - R) & 1); b <= R; b += 2)
-            g = fmaf(tp[b + R], V[py * kLW + floor_div2(pj + b) - qx_lo], g);
+        const float g = sr_tile_grad(tile, taps.r, py, pj);
         const size_t q = (size_t)pi * W + pj;
-        const float xv = X[(pi - (2 * qy_lo - G)) * kSW + (pj - (2 * qx_lo - G))];
+        const float xv = sr_tile_x(tile, pi, pj);
         const float up = u[q];
         const float xn = project(mu * (alpha * xv + rho * (v[q] - up) - g), constraint);
         x_out[q] = xn;
         z[q] = xn + up;
     }
-}
-
-__device__ __forceinline__ float spi_hprime(float xv, int k1, int K, float eta, float eps) {
-    const float t = fmaxf(xv, eps);
-    const float zz = eta * t / (float)K;
-    const float em = -expm1f(-zz);  // 1 - e^{-z}
-    const float e = expf(-zz);
-    return (eta / (float)K) * ((float)(K - k1) - (float)k1 * e / em);
 }
 
 __global__ void spi_grad_kernel(const float* __restrict__ x, const uint8_t* __restrict__ counts, int n,

@@ -29,6 +29,7 @@
 // Results do not depend on scheduling: every sum has a fixed order.
 #include <cuda.h>
 
+#include "combine.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -36,8 +37,8 @@ namespace dsg {
 
 namespace {
 
-constexpr int kTH = 16;                  // tile rows (= pixels per consumer thread)
-constexpr int kTW = 128;                 // tile columns (= consumer threads)
+constexpr int kTH = kTmaTH;              // tile rows (= pixels per consumer thread)
+constexpr int kTW = kTmaTW;              // tile columns (= consumer threads)
 constexpr int kConsumers = kTW;
 constexpr int kConsumerWarps = kConsumers / 32;
 constexpr int kThreads = kConsumers + 32;  // + one producer warp
@@ -262,157 +263,20 @@ stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const 
 
 // --------------------------------------------------------------------------- phase 2
 
-struct Cover {
-    const float* part;
-    int tiles_x, tiles_y, slices, rs;
-};
-
-// Sum of the partial regions covering pixel (i, j), in a fixed order.  The region
-// of tile (ty, tx) spans rows ty*kTH .. ty*kTH + kTH + rs - 1 and columns
-// tx*kTW - rs .. tx*kTW + kTW + rs - 1, so with rs <= kTH only the own tile row
-// and the one above, and the own tile column and its two neighbours, can cover it.
-__device__ __forceinline__ float gather_partials(const Cover& cv, int i, int j) {
-    const int rs = cv.rs;
-    const int RW = kTW + 2 * rs;
-    const size_t region = (size_t)(kTH + rs) * RW;
-    const int ty = i / kTH, tx = j / kTW;
-    const int li = i - ty * kTH, lj = j - tx * kTW;
-    const bool up = ty >= 1 && li < rs;
-    const bool left = tx >= 1 && lj < rs;
-    const bool right = tx + 1 < cv.tiles_x && lj >= kTW - rs;
-    // (tile, cell) offsets of the six candidates, upper row first, left to right
-    const size_t row_up = (size_t)(ty - 1) * cv.tiles_x, row_own = (size_t)ty * cv.tiles_x;
-    const size_t cell_up = (size_t)(li + kTH) * RW, cell_own = (size_t)li * RW;
-    size_t off[6];
-    bool use[6];
-    off[0] = (row_up + tx - 1) * region + cell_up + lj + kTW + rs; use[0] = up && left;
-    off[1] = (row_up + tx) * region + cell_up + lj + rs;           use[1] = up;
-    off[2] = (row_up + tx + 1) * region + cell_up + lj - kTW + rs; use[2] = up && right;
-    off[3] = (row_own + tx - 1) * region + cell_own + lj + kTW + rs; use[3] = left;
-    off[4] = (row_own + tx) * region + cell_own + lj + rs;           use[4] = true;
-    off[5] = (row_own + tx + 1) * region + cell_own + lj - kTW + rs; use[5] = right;
-    // unused candidates point at the own cell, so every address formed is in bounds
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-        if (!use[c]) off[c] = off[4];
-    const size_t slice_stride = (size_t)cv.tiles_y * cv.tiles_x * region;
-    CompSum acc;
-    const float* base = cv.part;
-    for (int sl = 0; sl < cv.slices; ++sl, base += slice_stride) {
-        float v[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) v[c] = use[c] ? __ldcg(base + off[c]) : 0.f;
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-            if (use[c]) acc.add(v[c]);
-    }
-    return acc.value();
-}
-
-template <int MODE>  // 0 balance, 1 apply, 2 apply + dual
+// W z = c_s z_s + (d_s / m) sum_{r != s} K1 d_r z_r with c_s = 1 - (d_s / m)(t_s - d_s):
+// the third aggregation of Algorithm 2 with the diagonal closure of Eq. S3
 __global__ void __launch_bounds__(256)
-stencil_p2_kernel(Cover cv, int H, int W, const float* __restrict__ d, const float* __restrict__ t_fin,
-                  float inv_m, const float* __restrict__ z, float* __restrict__ out0,
-                  float* __restrict__ out1, PassStat* __restrict__ stats, BalanceCtl* __restrict__ ctl,
-                  int pass, SolveRed red, int iter) {
-    if (MODE == 0 && *(volatile int*)&ctl->done) return;
+apply_finish_kernel(Cover cv, int H, int W, const float* __restrict__ d, const float* __restrict__ t_fin,
+                    float inv_m, const float* __restrict__ z, float* __restrict__ y) {
     const int j = blockIdx.x * 32 + threadIdx.x;
     const int i = blockIdx.y * 8 + threadIdx.y;
-    const int t = threadIdx.y * 32 + threadIdx.x;
-    const int lane = t & 31, warp = t >> 5;
-    float r0 = 0.f, r1 = 0.f;
-    if (i < H && j < W) {
-        const size_t s = (size_t)i * W + j;
-        const float A = gather_partials(cv, i, j);
-        const float ds = d[s];
-        if (MODE == 0) {
-            const float tt = ds + A;  // (K1 d)_s with K1(s, s) = 1
-            out0[s] = sqrtf(ds / tt);  // next scaling
-            out1[s] = tt;              // kept for the closure of Eq. S3
-            r0 = fabsf(fmaf(ds, tt, -1.f));  // |d_s t_s - 1| with a single rounding
-            r1 = ds * tt;
-        } else {
-            // W z = c_s z_s + (d_s / m) sum_{r != s} K1 d_r z_r, c_s = 1 - (d_s / m)(t_s - d_s)
-            const float zs = z[s];
-            const float dm = ds * inv_m;
-            const float cs = 1.f - dm * (t_fin[s] - ds);
-            const float vn = fmaf(dm, A, cs * zs);
-            if (MODE == 1) {
-                out0[s] = vn;
-            } else {
-                const float vo = out0[s];
-                const float uo = out1[s];
-                const float un = zs - vn;
-                out0[s] = vn;
-                out1[s] = un;
-                const float dp = un - uo;  // x - v
-                const float dd = vn - vo;  // v - v_prev
-                r0 = dp * dp;
-                r1 = dd * dd;
-            }
-        }
-    }
-    if (MODE == 1) return;
-    __shared__ float s0[8], s1[8];
-    if (MODE == 0) {
-        r0 = warp_max(r0);
-        r1 = warp_max(r1);
-    } else {
-        r0 = warp_sum_f(r0);
-        r1 = warp_sum_f(r1);
-    }
-    if (lane == 0) {
-        s0[warp] = r0;
-        s1[warp] = r1;
-    }
-    __syncthreads();
-    if (t != 0) return;
-    const unsigned nblocks = gridDim.x * gridDim.y;
-    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-    if (MODE == 2) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < 8; ++w) {
-            a += (double)s0[w];
-            b += (double)s1[w];
-        }
-        // per-block partial sums; reduced in a fixed order after the iterations
-        red.partials[2 * ((size_t)iter * nblocks + bid)] = a;
-        red.partials[2 * ((size_t)iter * nblocks + bid) + 1] = b;
-        return;
-    }
-    float a = 0.f, b = 0.f;
-    for (int w = 0; w < 8; ++w) {
-        a = fmaxf(a, s0[w]);
-        b = fmaxf(b, s1[w]);
-    }
-    PassStat* ps = stats + pass;
-    atomic_max_nonneg(&ps->eps_bits, (double)a);
-    atomic_max_nonneg(&ps->m_bits, (double)b);
-    __threadfence();
-    if (atomicAdd(&ps->arrive, 1u) == nblocks - 1) {
-        // last block of this pass decides whether the balance stops
-        __threadfence();
-        const double e = __longlong_as_double((long long)atomicAdd(&ps->eps_bits, 0ull));
-        int done = 0, status = 0;
-        if (e <= ctl->tol) {
-            done = 1;
-        } else if (pass >= ctl->maxit) {
-            done = 1;
-            status = 6;
-        } else if (e < 0.99 * ctl->best) {
-            ctl->best = e;
-            ctl->since_best = 0;
-        } else if (++ctl->since_best >= 3) {
-            done = 1;
-            status = 7;
-        }
-        if (done) {
-            ctl->final_pass = pass;
-            ctl->status = status;
-            __threadfence();
-            *(volatile int*)&ctl->done = 1;
-        }
-    }
+    if (i >= H || j >= W) return;
+    const size_t s = (size_t)i * W + j;
+    const float A = gather_partials(cv, i, j);
+    const float ds = d[s];
+    const float dm = ds * inv_m;
+    const float cs = 1.f - dm * (t_fin[s] - ds);
+    y[s] = fmaf(dm, A, cs * z[s]);
 }
 
 // hist[k] = fixed-order sums of the per-block residual partials of iteration k
@@ -513,29 +377,9 @@ cudaError_t launch_tma_gather(int dtype, const TmaPlan& plan, int H, int W, int 
     }
 }
 
-cudaError_t launch_tma_balance_finish(const TmaPlan& plan, int H, int W, int rs, const float* d_in,
-                                      float* d_out, float* t_out, PassStat* stats, BalanceCtl* ctl, int pass,
-                                      cudaStream_t st) {
-    stencil_p2_kernel<0><<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d_in, nullptr, 0.f,
-                                                               nullptr, d_out, t_out, stats, ctl, pass,
-                                                               SolveRed{}, 0);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_tma_apply_finish(const TmaPlan& plan, int H, int W, int rs, const float* d, const float* t,
                                     float inv_m, const float* z, float* y, cudaStream_t st) {
-    stencil_p2_kernel<1><<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d, t, inv_m, z, y,
-                                                               nullptr, nullptr, nullptr, 0, SolveRed{}, 0);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tma_dual_finish(const TmaPlan& plan, int H, int W, int rs, const float* d, const float* t,
-                                   float inv_m, const float* z, float* v, float* u, SolveRed red, int iter,
-                                   cudaStream_t st) {
-    stencil_p2_kernel<2><<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d, t, inv_m, z, v, u,
-                                                               nullptr, nullptr, 0, red, iter);
+    apply_finish_kernel<<<p2_grid(H, W), dim3(32, 8), 0, st>>>(cover_of(plan, rs), H, W, d, t, inv_m, z, y);
     count_launches(1);
     return cudaGetLastError();
 }

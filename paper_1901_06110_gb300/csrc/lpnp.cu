@@ -98,24 +98,38 @@ __global__ void sr_xupdate_kernel(const float* __restrict__ rlo, int H, int W, B
     z[p] = xn + up;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 sr_xupdate_fused_kernel(const float* __restrict__ x_in, float* __restrict__ x_out, const float* __restrict__ y,
                         int H, int W, BlurTaps taps, const float* __restrict__ v, const float* __restrict__ u,
                         float* __restrict__ z, float mu, float alpha, float rho, int constraint) {
     __shared__ SrTile tile;
     const int y0 = blockIdx.y * kXH, x0 = blockIdx.x * kXW;
-    sr_tile_prepare(tile, x_in, y, H, W, taps, y0, x0);
-    for (int idx = threadIdx.x; idx < kXH * kXW; idx += 256) {
-        const int py = idx / kXW, px = idx - py * kXW;
-        const int pi = y0 + py, pj = x0 + px;
+    sr_tile_index(tile, H, W, taps, y0, x0);
+    SrTileRegs rg;
+    sr_tile_load(tile, x_in, y, W, rg);
+    // prefetch the per-pixel inputs while the tile loads are in flight
+    const int pj = x0 + threadIdx.x;
+    float vv[2], uu[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int pi = y0 + threadIdx.y + 8 * r;
+        const bool ok = pi < H && pj < W;
+        const size_t q = (size_t)pi * W + pj;
+        vv[r] = ok ? v[q] : 0.f;
+        uu[r] = ok ? u[q] : 0.f;
+    }
+    sr_tile_compute(tile, rg, taps.r);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int py = threadIdx.y + 8 * r;
+        const int pi = y0 + py;
         if (pi >= H || pj >= W) continue;
         const float g = sr_tile_grad(tile, taps.r, py, pj);
         const size_t q = (size_t)pi * W + pj;
         const float xv = sr_tile_x(tile, pi, pj);
-        const float up = u[q];
-        const float xn = project(mu * (alpha * xv + rho * (v[q] - up) - g), constraint);
+        const float xn = project(mu * (alpha * xv + rho * (vv[r] - uu[r]) - g), constraint);
         x_out[q] = xn;
-        z[q] = xn + up;
+        z[q] = xn + uu[r];
     }
 }
 
@@ -257,8 +271,8 @@ cudaError_t launch_sr_xupdate_fused(const float* x_in, float* x_out, const float
                                     float alpha, float rho, int constraint, cudaStream_t st) {
     if (taps.r > kMaxBlurR) return cudaErrorInvalidValue;
     dim3 grid((W + kXW - 1) / kXW, (H + kXH - 1) / kXH);
-    sr_xupdate_fused_kernel<<<grid, 256, 0, st>>>(x_in, x_out, y, H, W, taps, v, u, z, mu, alpha, rho,
-                                                  constraint);
+    sr_xupdate_fused_kernel<<<grid, dim3(32, 8), 0, st>>>(x_in, x_out, y, H, W, taps, v, u, z, mu, alpha, rho,
+                                                          constraint);
     count_launches(1);
     return cudaGetLastError();
 }

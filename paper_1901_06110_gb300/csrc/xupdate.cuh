@@ -36,7 +36,7 @@ constexpr int kLW = (kXW - 1 + 2 * kMaxBlurR) / 2 + 2 + 1;  // low-res cols, wor
 constexpr int kSH = 2 * (kLH - 1) + 2 * kMaxBlurR + 1;      // staged x rows
 constexpr int kSW = 2 * (kLW - 1) + 2 * kMaxBlurR + 1;      // staged x cols
 
-__device__ __forceinline__ int floor_div2(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
+__device__ __forceinline__ int floor_div2(int a) { return a >> 1; }  // arithmetic shift: floor(a / 2)
 
 struct SrTile {
     float X[kSH * kSW];
@@ -44,14 +44,26 @@ struct SrTile {
     float Rl[kLH * kLW];
     float V[kXH * kLW];
     int rows[kSH], cols[kSW];
+    int lrows[kLH], lcols[kLW];  // wrapped low-resolution indices of the window
     float tp[2 * kMaxBlurR + 1];
-    int qy_lo, qx_lo, G, y0;
+    int qy_lo, qx_lo, G, y0, LH, LW, SH, SW;
 };
 
-// All threads of a 256-thread block must call this (it synchronises).
-__device__ __forceinline__ void sr_tile_prepare(SrTile& T, const float* __restrict__ x_in,
-                                                const float* __restrict__ y, int H, int W,
-                                                const BlurTaps& taps, int y0, int x0) {
+// The tile's work is split so that every global load is issued before the first
+// shared-memory phase: sr_tile_index (index tables; synchronises), sr_tile_load
+// (global loads into registers, no synchronisation: a caller can issue its own
+// loads alongside) and sr_tile_compute (smem phases; synchronises).  All threads
+// of a (32, 8) block must call the three in order.  Loops run over 2-D thread
+// coordinates, so no index is divided at run time.
+constexpr int kXRows = (kSH + 7) / 8;   // staged x rows per thread
+constexpr int kXCols = (kSW + 31) / 32;  // staged x columns per thread
+constexpr int kYRows = (kLH + 7) / 8;    // low-resolution rows per thread
+struct SrTileRegs {
+    float x[kXRows][kXCols];
+    float y[kYRows];
+};
+
+__device__ __forceinline__ void sr_tile_index(SrTile& T, int H, int W, const BlurTaps& taps, int y0, int x0) {
     const int R = taps.r;
     const int G = R > 0 ? R : 1;  // staging margin (covers the tile's own pixels when R = 0)
     const int h = H / 2, w = W / 2;
@@ -59,49 +71,91 @@ __device__ __forceinline__ void sr_tile_prepare(SrTile& T, const float* __restri
     const int qx_lo = floor_div2(x0 - G), qx_hi = floor_div2(x0 + kXW - 1 + G);
     const int LH = qy_hi - qy_lo + 1, LW = qx_hi - qx_lo + 1;
     const int SH = 2 * (LH - 1) + 2 * G + 1, SW = 2 * (LW - 1) + 2 * G + 1;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     if (tid == 0) {
         T.qy_lo = qy_lo;
         T.qx_lo = qx_lo;
         T.G = G;
         T.y0 = y0;
+        T.LH = LH;
+        T.LW = LW;
+        T.SH = SH;
+        T.SW = SW;
     }
     for (int a = tid; a < SH; a += 256) T.rows[a] = wrap_index(2 * qy_lo - G + a, H);
     for (int b = tid; b < SW; b += 256) T.cols[b] = wrap_index(2 * qx_lo - G + b, W);
+    for (int l = tid; l < LH; l += 256) T.lrows[l] = wrap_index(qy_lo + l, h);
+    for (int c = tid; c < LW; c += 256) T.lcols[c] = wrap_index(qx_lo + c, w);
     if (tid < 2 * R + 1) T.tp[tid] = taps.t[tid];
     __syncthreads();
-    for (int idx = tid; idx < SH * SW; idx += 256) {
-        const int a = idx / SW, b = idx - a * SW;
-        T.X[a * kSW + b] = x_in[(size_t)T.rows[a] * W + T.cols[b]];
+}
+
+__device__ __forceinline__ void sr_tile_load(const SrTile& T, const float* __restrict__ x_in,
+                                             const float* __restrict__ y, int W, SrTileRegs& rg) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int w = W / 2;
+#pragma unroll
+    for (int ia = 0; ia < kXRows; ++ia) {
+        const int a = ty + 8 * ia;
+#pragma unroll
+        for (int ib = 0; ib < kXCols; ++ib) {
+            const int b = tx + 32 * ib;
+            rg.x[ia][ib] = (a < T.SH && b < T.SW) ? __ldg(x_in + (size_t)T.rows[a] * W + T.cols[b]) : 0.f;
+        }
+    }
+    // the low-resolution column of this lane (one per lane: LW <= 32 for blur radii up to 8)
+#pragma unroll
+    for (int il = 0; il < kYRows; ++il) {
+        const int l = ty + 8 * il;
+        rg.y[il] = (l < T.LH && tx < T.LW) ? __ldg(y + (size_t)T.lrows[l] * w + T.lcols[tx]) : 0.f;
+    }
+}
+
+__device__ __forceinline__ void sr_tile_compute(SrTile& T, const SrTileRegs& rg, int R) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int G = T.G, SH = T.SH, SW = T.SW, LH = T.LH, LW = T.LW, qy_lo = T.qy_lo, y0 = T.y0;
+#pragma unroll
+    for (int ia = 0; ia < kXRows; ++ia) {
+        const int a = ty + 8 * ia;
+#pragma unroll
+        for (int ib = 0; ib < kXCols; ++ib) {
+            const int b = tx + 32 * ib;
+            if (a < SH && b < SW) T.X[a * kSW + b] = rg.x[ia][ib];
+        }
     }
     __syncthreads();
     // horizontal blur sums at the even columns 2 qx: staged column 2c + G - b
-    for (int idx = tid; idx < SH * LW; idx += 256) {
-        const int a = idx / LW, c = idx - a * LW;
-        const float* xr = T.X + a * kSW + 2 * c + G;
-        float acc = 0.f;
-        for (int b = -R; b <= R; ++b) acc = fmaf(T.tp[b + R], xr[-b], acc);
-        T.Hs[a * kLW + c] = acc;
+    for (int a = ty; a < SH; a += 8) {
+        for (int c = tx; c < LW; c += 32) {
+            const float* xr = T.X + a * kSW + 2 * c + G;
+            float acc = 0.f;
+            for (int b = -R; b <= R; ++b) acc = fmaf(T.tp[b + R], xr[-b], acc);
+            T.Hs[a * kLW + c] = acc;
+        }
     }
     __syncthreads();
     // r = A x - y on the low-resolution window
-    for (int idx = tid; idx < LH * LW; idx += 256) {
-        const int l = idx / LW, c = idx - l * LW;
-        const float* hc = T.Hs + (2 * l + G) * kLW + c;
-        float acc = 0.f;
-        for (int a = -R; a <= R; ++a) acc = fmaf(T.tp[a + R], hc[-a * kLW], acc);
-        const int qy = wrap_index(qy_lo + l, h), qx = wrap_index(qx_lo + c, w);
-        T.Rl[l * kLW + c] = acc - y[(size_t)qy * w + qx];
+#pragma unroll
+    for (int il = 0; il < kYRows; ++il) {
+        const int l = ty + 8 * il;
+        if (l < LH && tx < LW) {
+            const float* hc = T.Hs + (2 * l + G) * kLW + tx;
+            float acc = 0.f;
+            for (int a = -R; a <= R; ++a) acc = fmaf(T.tp[a + R], hc[-a * kLW], acc);
+            T.Rl[l * kLW + tx] = acc - rg.y[il];
+        }
     }
     __syncthreads();
     // vertical adjoint sums: V(p_y, c) = sum_{a : p_y + a even} t(a) r((p_y + a) / 2, c)
-    for (int idx = tid; idx < kXH * LW; idx += 256) {
-        const int py = idx / LW, c = idx - py * LW;
+    for (int py = ty; py < kXH; py += 8) {
         const int p = y0 + py;
-        float acc = 0.f;
-        for (int a = -R + ((p - R) & 1); a <= R; a += 2)
-            acc = fmaf(T.tp[a + R], T.Rl[(floor_div2(p + a) - qy_lo) * kLW + c], acc);
-        T.V[py * kLW + c] = acc;
+        const int a0 = -R + ((p - R) & 1);
+        for (int c = tx; c < LW; c += 32) {
+            float acc = 0.f;
+            for (int a = a0; a <= R; a += 2)
+                acc = fmaf(T.tp[a + R], T.Rl[(((p + a) >> 1) - qy_lo) * kLW + c], acc);
+            T.V[py * kLW + c] = acc;
+        }
     }
     __syncthreads();
 }
@@ -110,7 +164,7 @@ __device__ __forceinline__ void sr_tile_prepare(SrTile& T, const float* __restri
 __device__ __forceinline__ float sr_tile_grad(const SrTile& T, int R, int py, int pj) {
     float g = 0.f;
     for (int b = -R + ((pj - R) & 1); b <= R; b += 2)
-        g = fmaf(T.tp[b + R], T.V[py * kLW + floor_div2(pj + b) - T.qx_lo], g);
+        g = fmaf(T.tp[b + R], T.V[py * kLW + ((pj + b) >> 1) - T.qx_lo], g);
     return g;
 }
 

@@ -222,6 +222,17 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters);
 dsgnlm_status lpnp_sr_gradient_noalloc(const float* x, const float* y, int H, int W,
                                        float blur_sigma, int blur_r, float* grad, void* stream);
 
+/* Batched Algorithm 1: `count` independent images (1..96) of any sizes advance
+ * together; each iteration is one phase-1 launch and one combine/x-update launch
+ * over a work-list of (image, tile) items of all images.  Same arguments and
+ * results as calling lpnp_solve on each problem, image by image.  All problems
+ * must have the same kind, and their denoisers (one distinct handle each, built
+ * and balanced, all on a search radius with a TMA kernel) the same weight dtype
+ * and search radius.  Work runs on probs[0].den's stream; the caller orders the
+ * other handles' earlier work before it.  Synchronises only if a resid_hist is
+ * given.  EINVAL for mixed batches or count out of range. */
+dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho, int iters);
+
 /* ---------------------------------------------------------------------------
  * Misc
  * ------------------------------------------------------------------------- */

@@ -169,6 +169,8 @@ struct dsgnlm {
     double resid = 0.0;
     // Algorithm 1 workspace
     DevBuf z, x2, rlo, partials, arrive, hist;
+    // batched Algorithm 1 workspace (used when this handle leads a batch)
+    DevBuf b_inst, b_epi, b_work1, b_work2, b_hist;
     // optional per-kernel timing
     bool prof = false;
     ProfPool pools[kProfKinds];
@@ -211,6 +213,11 @@ struct dsgnlm {
         ctl.release();
         z.release();
         x2.release();
+        b_inst.release();
+        b_epi.release();
+        b_work1.release();
+        b_work2.release();
+        b_hist.release();
         rlo.release();
         partials.release();
         arrive.release();
@@ -737,6 +744,133 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
         for (int it = 0; it < iters; ++it) {
             p->resid_hist[2 * it] = std::sqrt(hs[2 * it] / (double)n);
             p->resid_hist[2 * it + 1] = (double)rho * std::sqrt(hs[2 * it + 1] / (double)n);
+        }
+    }
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho, int iters) {
+    if (!probs || count < 1 || count > kMaxBatch) return DSGNLM_EINVAL;
+    if (!(rho > 0.f) || !std::isfinite(rho) || iters < 0) return DSGNLM_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        dsgnlm_status s = check_problem(&probs[i], true);
+        if (s != DSGNLM_OK) return s;
+        const dsgnlm* h = probs[i].den;
+        if (!h->fast || probs[i].kind != probs[0].kind || h->dtype != probs[0].den->dtype || h->rs != probs[0].den->rs)
+            return DSGNLM_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (probs[j].den == h) return DSGNLM_EINVAL;  // each image needs its own handle
+    }
+    if (iters == 0) return DSGNLM_OK;
+    dsgnlm* lead = probs[0].den;
+    cudaStream_t st = lead->stream;
+    const int kind = probs[0].kind == LPNP_SR2 ? 0 : 1;
+    std::vector<BatchInst> inst(count);
+    std::vector<BatchEpi> epi(count);
+    std::vector<int4> work1, work2;
+    BatchMaps maps;
+    for (int i = 0; i < count; ++i) {
+        const lpnp_problem* p = &probs[i];
+        dsgnlm* h = p->den;
+        const int H = p->H, W = p->W;
+        const size_t n = (size_t)H * W;
+        const int gx = (W + 31) / 32, gy = (H + 15) / 16;
+        const int nb = gx * gy;
+        if (nb != combine_xupdate_blocks(H, W)) return DSGNLM_EINVAL;
+        DSG_CK(h->z.ensure(n * sizeof(float)));
+        if (p->kind == LPNP_SR2) DSG_CK(h->x2.ensure(n * sizeof(float)));
+        DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nb * iters));
+        std::memcpy(maps.m[i], h->plan.tmap, 128);
+        BatchInst& bi = inst[i];
+        bi.H = H;
+        bi.W = W;
+        bi.tiles_x = h->plan.tiles_x;
+        bi.tiles_y = h->plan.tiles_y;
+        bi.splits = h->plan.splits;
+        bi.d = h->d_final;
+        bi.z = h->z.as<float>();
+        bi.part = h->plan.partials;
+        for (int sl = 0; sl < bi.splits.n; ++sl)
+            for (int ty = 0; ty < bi.tiles_y; ++ty)
+                for (int tx = 0; tx < bi.tiles_x; ++tx) work1.push_back(make_int4(i, ty, tx, sl));
+        BatchEpi& be = epi[i];
+        EpilogueArgs& ea = be.a;
+        ea = EpilogueArgs{};
+        ea.H = H;
+        ea.W = W;
+        ea.d = h->d_final;
+        ea.t = h->t_final;
+        ea.inv_m = h->inv_m;
+        ea.z = h->z.as<float>();
+        ea.v = p->v;
+        ea.u = p->u;
+        ea.x_in = p->x;
+        ea.x_out = p->kind == LPNP_SR2 ? h->x2.as<float>() : p->x;
+        ea.y = p->y;
+        ea.taps = make_blur_taps(p->blur_sigma > 0.f ? p->blur_sigma : 1.f, p->kind == LPNP_SR2 ? p->blur_r : 0);
+        ea.counts = p->counts;
+        ea.K = p->K;
+        ea.eta = p->eta;
+        ea.eps = p->spi_eps;
+        ea.mu = (float)(1.0 / ((double)p->alpha + (double)rho));
+        ea.alpha = p->alpha;
+        ea.rho = rho;
+        ea.constraint = p->constraint;
+        ea.do_x = 1;
+        be.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, h->plan.splits.n, h->rs};
+        be.gx = gx;
+        be.nblocks = nb;
+        be.partials = h->partials.as<double>();
+        for (int by = 0; by < gy; ++by)
+            for (int bx = 0; bx < gx; ++bx) work2.push_back(make_int4(i, by, bx, 0));
+    }
+    DSG_CK(lead->b_inst.ensure(sizeof(BatchInst) * count));
+    DSG_CK(lead->b_epi.ensure(sizeof(BatchEpi) * count));
+    DSG_CK(lead->b_work1.ensure(sizeof(int4) * work1.size()));
+    DSG_CK(lead->b_work2.ensure(sizeof(int4) * work2.size()));
+    DSG_CK(cudaMemcpyAsync(lead->b_inst.p, inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st));
+    DSG_CK(cudaMemcpyAsync(lead->b_epi.p, epi.data(), sizeof(BatchEpi) * count, cudaMemcpyHostToDevice, st));
+    DSG_CK(cudaMemcpyAsync(lead->b_work1.p, work1.data(), sizeof(int4) * work1.size(), cudaMemcpyHostToDevice, st));
+    DSG_CK(cudaMemcpyAsync(lead->b_work2.p, work2.data(), sizeof(int4) * work2.size(), cudaMemcpyHostToDevice, st));
+    // every image must be ready on the lead stream: the other handles' work is ordered
+    // before this call by the caller (same stream), as for lpnp_solve
+    const BatchInst* dinst = lead->b_inst.as<BatchInst>();
+    const BatchEpi* depi = lead->b_epi.as<BatchEpi>();
+    const int4* w1 = lead->b_work1.as<int4>();
+    const int4* w2 = lead->b_work2.as<int4>();
+    const int n1 = (int)work1.size(), n2 = (int)work2.size();
+    DSG_CK(lead->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_batched_xupdate0(kind, depi, w2, n2, st); }));
+    for (int it = 0; it < iters; ++it) {
+        DSG_CK(lead->timed(DSGNLM_PROF_APPLY, [&] {
+            return launch_tma_gather_batched(lead->dtype, lead->rs, maps, dinst, w1, n1, lead->err.as<unsigned>(), st);
+        }));
+        DSG_CK(lead->timed(DSGNLM_PROF_XUPDATE,
+                           [&] { return launch_batched_combine(kind, depi, w2, n2, it, it == iters - 1, st); }));
+    }
+    bool want_hist = false;
+    for (int i = 0; i < count; ++i) want_hist |= probs[i].resid_hist != nullptr;
+    if (want_hist) {
+        DSG_CK(lead->b_hist.ensure(sizeof(double) * 2 * (size_t)count * iters));
+        DSG_CK(launch_batched_reduce(depi, count, lead->b_hist.as<double>(), iters, st));
+    }
+    for (int i = 0; i < count; ++i)
+        if (probs[i].kind == LPNP_SR2 && (iters & 1))
+            DSG_CK(cudaMemcpyAsync(probs[i].x, probs[i].den->x2.p, sizeof(float) * (size_t)probs[i].H * probs[i].W,
+                                   cudaMemcpyDeviceToDevice, st));
+    if (want_hist) {
+        std::vector<double> hs(2 * (size_t)count * iters);
+        DSG_CK(cudaMemcpyAsync(hs.data(), lead->b_hist.p, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, st));
+        DSG_CK(cudaStreamSynchronize(st));
+        unsigned errv = 0;
+        DSG_CK(cudaMemcpy(&errv, lead->err.p, sizeof errv, cudaMemcpyDeviceToHost));
+        if (errv) return DSGNLM_TIMEOUT;
+        for (int i = 0; i < count; ++i) {
+            if (!probs[i].resid_hist) continue;
+            const double n = (double)probs[i].H * probs[i].W;
+            for (int it = 0; it < iters; ++it) {
+                probs[i].resid_hist[2 * it] = std::sqrt(hs[2 * ((size_t)i * iters + it)] / n);
+                probs[i].resid_hist[2 * it + 1] = (double)rho * std::sqrt(hs[2 * ((size_t)i * iters + it) + 1] / n);
+            }
         }
     }
     return DSGNLM_OK;

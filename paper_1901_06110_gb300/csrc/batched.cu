@@ -1,0 +1,128 @@
+// Batched form of Algorithm 1: many images of uneven sizes advance together, one
+// launch per step of the iteration over a work-list of (image, tile) items:
+//   x-update of iteration 0            batched_xupdate0_kernel
+//   per iteration: phase-1 gather      launch_tma_gather_batched (stencil_tma.cu)
+//                  combine + x-update  batched_combine_kernel
+// Each image keeps its own DSG-NLM weights (any storage type; the arithmetic is
+// FP32), scaling, closure and iterates; the work-list only flattens the tiles of
+// all images into one grid, so the GPU scheduler balances small and large images.
+#include "combine.cuh"
+#include "common.cuh"
+#include "epilogue.cuh"
+#include "internal.h"
+#include "xupdate.cuh"
+
+namespace dsg {
+
+namespace {
+
+// elementwise single-photon x-update on the tile at (y0, x0)
+__device__ __forceinline__ void spi_xupdate_tile(const EpilogueArgs& a, int y0, int x0) {
+    const int pj = x0 + threadIdx.x;
+    for (int py = threadIdx.y; py < kXH; py += 8) {
+        const int pi = y0 + py;
+        if (pi >= a.H || pj >= a.W) continue;
+        const size_t q = (size_t)pi * a.W + pj;
+        const float xv = a.x_in[q];
+        const float g = spi_hprime(xv, a.counts[q], a.K, a.eta, a.eps);
+        const float up = a.u[q];
+        const float xn = project(a.mu * (a.alpha * xv + a.rho * (a.v[q] - up) - g), a.constraint);
+        a.x_out[q] = xn;
+        a.z[q] = xn + up;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256, 3)
+batched_xupdate0_kernel(const BatchEpi* __restrict__ insts, const int4* __restrict__ work) {
+    __shared__ SrTile tile;
+    const int4 w = work[blockIdx.x];  // (instance, tile row, tile column, -)
+    const EpilogueArgs& a = insts[w.x].a;
+    const int y0 = w.y * kXH, x0 = w.z * kXW;
+    if (KIND == 0)
+        sr_xupdate_body(tile, a.x_in, a.x_out, a.y, a.H, a.W, a.taps, a.v, a.u, a.z, a.mu, a.alpha, a.rho,
+                        a.constraint, y0, x0);
+    else
+        spi_xupdate_tile(a, y0, x0);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256, 3)
+batched_combine_kernel(const BatchEpi* __restrict__ insts, const int4* __restrict__ work, int it, int last) {
+    __shared__ SrTile tile;
+    const int4 w = work[blockIdx.x];
+    const BatchEpi& e = insts[w.x];
+    EpilogueArgs a = e.a;
+    // x of the next update alternates between the two buffers of each image
+    const float* xa = e.a.x_in;
+    float* xb = e.a.x_out;
+    a.do_x = !last;
+    a.x_in = (it & 1) ? xa : xb;
+    a.x_out = (it & 1) ? xb : const_cast<float*>(xa);
+    if (KIND == 1) {  // single-photon: x is updated in place
+        a.x_in = xa;
+        a.x_out = const_cast<float*>(xa);
+    }
+    double* partials = e.partials + 2 * ((size_t)it * e.nblocks + (size_t)w.y * e.gx + w.z);
+    combine_xupdate_body<KIND>(tile, e.cv, a, w.y * kXH, w.z * kXW, partials);
+}
+
+// hist of (image, iteration) = fixed-order sums of that image's per-block residual partials
+__global__ void __launch_bounds__(256)
+batched_reduce_kernel(const BatchEpi* __restrict__ insts, double* __restrict__ hist, int iters) {
+    const int it = blockIdx.x, inst = blockIdx.y, t = threadIdx.x;
+    const BatchEpi& e = insts[inst];
+    const double* p = e.partials + 2 * (size_t)it * e.nblocks;
+    double a = 0.0, b = 0.0;
+    for (int q = t; q < e.nblocks; q += 256) {
+        a += p[2 * q];
+        b += p[2 * q + 1];
+    }
+    __shared__ double ra[256], rb[256];
+    ra[t] = a;
+    rb[t] = b;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) {
+            ra[t] += ra[t + s];
+            rb[t] += rb[t + s];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        hist[2 * ((size_t)inst * iters + it)] = ra[0];
+        hist[2 * ((size_t)inst * iters + it) + 1] = rb[0];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batched_xupdate0(int kind, const BatchEpi* insts, const int4* work, int nwork, cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    if (kind == 0)
+        batched_xupdate0_kernel<0><<<nwork, dim3(32, 8), 0, st>>>(insts, work);
+    else
+        batched_xupdate0_kernel<1><<<nwork, dim3(32, 8), 0, st>>>(insts, work);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_combine(int kind, const BatchEpi* insts, const int4* work, int nwork, int it, int last,
+                                   cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    if (kind == 0)
+        batched_combine_kernel<0><<<nwork, dim3(32, 8), 0, st>>>(insts, work, it, last);
+    else
+        batched_combine_kernel<1><<<nwork, dim3(32, 8), 0, st>>>(insts, work, it, last);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_reduce(const BatchEpi* insts, int count, double* hist, int iters, cudaStream_t st) {
+    if (count <= 0 || iters <= 0) return cudaSuccess;
+    batched_reduce_kernel<<<dim3(iters, count), 256, 0, st>>>(insts, hist, iters);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace dsg

@@ -11,11 +11,6 @@ namespace dsg {
 constexpr int kTmaTH = 16;   // tile rows of phase 1
 constexpr int kTmaTW = 128;  // tile columns of phase 1
 
-struct Cover {
-    const float* part;
-    int tiles_x, tiles_y, slices, rs;
-};
-
 // Sum of the partial regions covering pixel (i, j), in a fixed order.  The region
 // of tile (ty, tx) spans rows ty*kTmaTH .. ty*kTmaTH + kTmaTH + rs - 1 and columns
 // tx*kTmaTW - rs .. tx*kTmaTW + kTmaTW + rs - 1, so with rs <= kTmaTH only the own tile row

@@ -1,0 +1,153 @@
+// Device body of the kernel that finishes one application of W inside
+// Algorithm 1 (v, u and residual sums) and performs the next linearized
+// x-update on the same pixels; shared by the single-image and batched kernels.
+#pragma once
+
+#include "combine.cuh"
+#include "common.cuh"
+#include "internal.h"
+#include "xupdate.cuh"
+
+namespace dsg {
+
+// Sum of the phase-1 partial regions at pixel (i, j) for an epilogue tile that
+// lies inside one phase-1 tile (ty, tx): the candidate tiles are the same for the
+// whole block; per pixel only the halo tests differ.  Fixed order: own tile, the
+// tile above, left, upper left, right, upper right; slices innermost.
+struct TileCover {
+    const float* own;  // region of (ty, tx), slice 0
+    size_t region, slice_stride;
+    int RW, rs, slices;
+    bool up_ok, left_ok, right_ok;
+    long long up_d, left_d, right_d;  // region offsets (in floats) of the neighbours
+};
+
+__device__ __forceinline__ TileCover tile_cover(const Cover& cv, int y0, int x0) {
+    TileCover c;
+    const int ty = y0 / kTmaTH, tx = x0 / kTmaTW;
+    c.rs = cv.rs;
+    c.RW = kTmaTW + 2 * cv.rs;
+    c.region = (size_t)(kTmaTH + cv.rs) * c.RW;
+    c.slice_stride = (size_t)cv.tiles_y * cv.tiles_x * c.region;
+    c.slices = cv.slices;
+    c.own = cv.part + ((size_t)ty * cv.tiles_x + tx) * c.region;
+    c.up_ok = ty > 0;
+    c.left_ok = tx > 0;
+    c.right_ok = tx + 1 < cv.tiles_x;
+    c.up_d = -(long long)cv.tiles_x * (long long)c.region;
+    c.left_d = -(long long)c.region;
+    c.right_d = (long long)c.region;
+    return c;
+}
+
+__device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj) {
+    const int rs = c.rs, RW = c.RW;
+    const bool up = c.up_ok && li < rs;
+    const bool left = c.left_ok && lj < rs;
+    const bool right = c.right_ok && lj >= kTmaTW - rs;
+    const size_t own_cell = (size_t)li * RW + lj + rs;
+    const size_t up_cell = (size_t)(li + kTmaTH) * RW + lj + rs;
+    float acc = 0.f;
+    const float* base = c.own;
+    for (int sl = 0; sl < c.slices; ++sl, base += c.slice_stride) {
+        acc += __ldcg(base + own_cell);
+        if (up) acc += __ldcg(base + c.up_d + up_cell);
+        if (left) {
+            acc += __ldcg(base + c.left_d + own_cell + kTmaTW);
+            if (up) acc += __ldcg(base + c.up_d + c.left_d + up_cell + kTmaTW);
+        }
+        if (right) {
+            acc += __ldcg(base + c.right_d + own_cell - kTmaTW);
+            if (up) acc += __ldcg(base + c.up_d + c.right_d + up_cell - kTmaTW);
+        }
+    }
+    return acc;
+}
+
+// Finish v and u of one iteration on the kXH x kXW tile at (y0, x0), perform the
+// next x-update there when a.do_x, and store the tile's residual sums at
+// `partials` (two doubles).  All threads of a (32, 8) block must call it.
+template <int KIND>  // 0 super-resolution, 1 single-photon
+__device__ __forceinline__ void combine_xupdate_body(SrTile& tile, const Cover& cv, const EpilogueArgs& a,
+                                                     int y0, int x0, double* partials) {
+    const int H = a.H, W = a.W;
+    const bool sr_x = KIND == 0 && a.do_x;
+    SrTileRegs rg;
+    if (sr_x) {
+        sr_tile_index(tile, H, W, a.taps, y0, x0);
+        sr_tile_load(tile, a.x_in, a.y, W, rg);
+    }
+    // per-pixel inputs of the combine, issued before the tile's shared-memory phases
+    const TileCover tc = tile_cover(cv, y0, x0);
+    const int pj = x0 + threadIdx.x;
+    const int lj = pj - (x0 / kTmaTW) * kTmaTW;
+    float A[2], zs[2], ds[2], ts[2], vo[2], uo[2], xs[2];
+    int k1[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int py = threadIdx.y + 8 * r;
+        const int pi = y0 + py;
+        const bool ok = pi < H && pj < W;
+        const size_t q = (size_t)pi * W + pj;
+        A[r] = ok ? tile_gather(tc, py, lj) : 0.f;
+        zs[r] = ok ? a.z[q] : 0.f;
+        ds[r] = ok ? a.d[q] : 0.f;
+        ts[r] = ok ? a.t[q] : 0.f;
+        vo[r] = ok ? a.v[q] : 0.f;
+        uo[r] = ok ? a.u[q] : 0.f;
+        xs[r] = (ok && KIND == 1 && a.do_x) ? a.x_in[q] : 0.f;
+        k1[r] = (ok && KIND == 1 && a.do_x) ? (int)a.counts[q] : 0;
+    }
+    if (sr_x) sr_tile_compute(tile, rg, a.taps.r);
+    float sp = 0.f, sd = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int py = threadIdx.y + 8 * r;
+        const int pi = y0 + py;
+        if (pi >= H || pj >= W) continue;
+        const size_t q = (size_t)pi * W + pj;
+        // v = W z with z = x + u: c_s z_s + (d_s / m) sum_{r != s} K1 d_r z_r
+        const float dm = ds[r] * a.inv_m;
+        const float cs = 1.f - dm * (ts[r] - ds[r]);
+        const float vn = fmaf(dm, A[r], cs * zs[r]);
+        const float un = zs[r] - vn;  // u + x - v
+        a.v[q] = vn;
+        a.u[q] = un;
+        const float dp = un - uo[r], dd = vn - vo[r];  // x - v and v - v_prev
+        sp = fmaf(dp, dp, sp);
+        sd = fmaf(dd, dd, sd);
+        if (a.do_x) {
+            float xv, g;
+            if (KIND == 0) {
+                xv = sr_tile_x(tile, pi, pj);
+                g = sr_tile_grad(tile, a.taps.r, py, pj);
+            } else {
+                xv = xs[r];
+                g = spi_hprime(xv, k1[r], a.K, a.eta, a.eps);
+            }
+            const float xn = project(a.mu * (a.alpha * xv + a.rho * (vn - un) - g), a.constraint);
+            a.x_out[q] = xn;
+            a.z[q] = xn + un;
+        }
+    }
+    sp = warp_sum_f(sp);
+    sd = warp_sum_f(sd);
+    __shared__ float s0[8], s1[8];
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    if ((t & 31) == 0) {
+        s0[t >> 5] = sp;
+        s1[t >> 5] = sd;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double pa = 0.0, pb = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            pa += (double)s0[w];
+            pb += (double)s1[w];
+        }
+        partials[0] = pa;
+        partials[1] = pb;
+    }
+}
+
+}  // namespace dsg

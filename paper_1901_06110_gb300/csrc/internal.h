@@ -54,12 +54,30 @@ struct TmaSplits {
     int ox_hi[kMaxSlices];
     int n;
 };
+struct Cover {  // where a pixel's phase-1 partial sums live
+    const float* part;
+    int tiles_x, tiles_y, slices, rs;
+};
 struct TmaPlan {
     alignas(64) unsigned char tmap[128];  // CUtensorMap of the planes
     int tiles_x, tiles_y;
     TmaSplits splits;
     float* partials;  // [slices][tiles_y][tiles_x][region]
 };
+// Batched phase 1: every instance's tensor map travels in the kernel parameters.
+constexpr int kMaxBatch = 96;
+struct BatchMaps {
+    alignas(64) unsigned char m[kMaxBatch][128];
+};
+struct BatchInst {  // per-instance data of a batched launch (device memory)
+    int H, W, tiles_x, tiles_y;
+    TmaSplits splits;
+    const float* d;   // scaling
+    const float* z;   // second factor of q (null: q = d)
+    float* part;      // partial regions of this instance
+};
+cudaError_t launch_tma_gather_batched(int dtype, int rs, const BatchMaps& maps, const BatchInst* insts,
+                                      const int4* work, int nwork, unsigned* err, cudaStream_t st);
 bool tma_path_supports(int rs);
 int tma_tile_w();
 int tma_tile_h();
@@ -156,5 +174,19 @@ struct EpilogueArgs {
 int combine_xupdate_blocks(int H, int W);
 cudaError_t launch_combine_xupdate(int kind, const TmaPlan& plan, int rs, const EpilogueArgs& args,
                                    cudaStream_t st);
+
+// Batched Algorithm 1 (batched.cu).  a.x_in / a.x_out hold the two x buffers of the
+// image (the caller's and the handle's); the kernels alternate them per iteration.
+struct BatchEpi {
+    EpilogueArgs a;
+    Cover cv;
+    int gx;            // epilogue tiles per row
+    int nblocks;       // epilogue tiles of the image
+    double* partials;  // [iters][nblocks][2] residual sums
+};
+cudaError_t launch_batched_xupdate0(int kind, const BatchEpi* insts, const int4* work, int nwork, cudaStream_t st);
+cudaError_t launch_batched_combine(int kind, const BatchEpi* insts, const int4* work, int nwork, int it, int last,
+                                   cudaStream_t st);
+cudaError_t launch_batched_reduce(const BatchEpi* insts, int count, double* hist, int iters, cudaStream_t st);
 
 }  // namespace dsg

@@ -103,34 +103,8 @@ sr_xupdate_fused_kernel(const float* __restrict__ x_in, float* __restrict__ x_ou
                         int H, int W, BlurTaps taps, const float* __restrict__ v, const float* __restrict__ u,
                         float* __restrict__ z, float mu, float alpha, float rho, int constraint) {
     __shared__ SrTile tile;
-    const int y0 = blockIdx.y * kXH, x0 = blockIdx.x * kXW;
-    sr_tile_index(tile, H, W, taps, y0, x0);
-    SrTileRegs rg;
-    sr_tile_load(tile, x_in, y, W, rg);
-    // prefetch the per-pixel inputs while the tile loads are in flight
-    const int pj = x0 + threadIdx.x;
-    float vv[2], uu[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int pi = y0 + threadIdx.y + 8 * r;
-        const bool ok = pi < H && pj < W;
-        const size_t q = (size_t)pi * W + pj;
-        vv[r] = ok ? v[q] : 0.f;
-        uu[r] = ok ? u[q] : 0.f;
-    }
-    sr_tile_compute(tile, rg, taps.r);
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int py = threadIdx.y + 8 * r;
-        const int pi = y0 + py;
-        if (pi >= H || pj >= W) continue;
-        const float g = sr_tile_grad(tile, taps.r, py, pj);
-        const size_t q = (size_t)pi * W + pj;
-        const float xv = sr_tile_x(tile, pi, pj);
-        const float xn = project(mu * (alpha * xv + rho * (vv[r] - uu[r]) - g), constraint);
-        x_out[q] = xn;
-        z[q] = xn + uu[r];
-    }
+    sr_xupdate_body(tile, x_in, x_out, y, H, W, taps, v, u, z, mu, alpha, rho, constraint, blockIdx.y * kXH,
+                    blockIdx.x * kXW);
 }
 
 __global__ void spi_grad_kernel(const float* __restrict__ x, const uint8_t* __restrict__ counts, int n,

@@ -109,15 +109,15 @@ __host__ __device__ __forceinline__ int plane_index(int oy, int ox, int rs) {
     return oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
 }
 
+// Phase 1 for one tile at (x0, y0) and the column offsets oxa..oxb: writes the
+// tile's partial region (kTH + RS rows, kTW + 2 RS columns) to `out`.
 template <int RS, typename WT>
-__global__ void __launch_bounds__(kThreads, 2)
-stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const float* __restrict__ d,
-                  const float* __restrict__ z, TmaSplits splits, float* __restrict__ part,
-                  unsigned* __restrict__ err, const int* __restrict__ skip) {
+__device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, const float* __restrict__ d,
+                                        const float* __restrict__ z, int oxa, int oxb, int x0, int y0,
+                                        float* __restrict__ out, unsigned* __restrict__ err) {
     constexpr int RH = kTH + RS;
     constexpr int RW = kTW + 2 * RS;
     constexpr int kStageElems = kTH * kTW;
-    if (skip && *(volatile const int*)skip) return;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     WT* stages = reinterpret_cast<WT*>(smem_raw);
@@ -129,11 +129,6 @@ stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const 
     __shared__ int s_abort;
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kTW;
-    const int y0 = blockIdx.y * kTH;
-    const int slice = blockIdx.z;
-    const int oxa = splits.ox_lo[slice];
-    const int oxb = splits.ox_hi[slice];
 
     if (tid == 0) {
         s_abort = 0;
@@ -164,7 +159,7 @@ stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const 
                         break;
                     }
                     mbar_arrive_expect_tx(&full[s], kStageElems * sizeof(WT));
-                    tma_load_3d(stages + s * kStageElems, &tmap, &full[s], x0, y0, plane_index(oy, ox, RS));
+                    tma_load_3d(stages + s * kStageElems, tmap, &full[s], x0, y0, plane_index(oy, ox, RS));
                 }
             }
             if (!ok) {
@@ -256,9 +251,34 @@ stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const 
         acc_lo[r * RW + c + RS] += comp[r];
     }
     consumer_sync();
-    const size_t region = (size_t)RH * RW;
-    float* out = part + ((size_t)(slice * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * region;
     for (int idx = c; idx < RH * RW; idx += kConsumers) out[idx] = acc_hi[idx] + acc_lo[idx];
+}
+
+
+template <int RS, typename WT>
+__global__ void __launch_bounds__(kThreads, 2)
+stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const float* __restrict__ d,
+                  const float* __restrict__ z, TmaSplits splits, float* __restrict__ part,
+                  unsigned* __restrict__ err, const int* __restrict__ skip) {
+    if (skip && *(volatile const int*)skip) return;
+    const int slice = blockIdx.z;
+    const size_t region = (size_t)(kTH + RS) * (kTW + 2 * RS);
+    float* out = part + ((size_t)(slice * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * region;
+    p1_body<RS, WT>(&tmap, H, W, d, z, splits.ox_lo[slice], splits.ox_hi[slice], blockIdx.x * kTW,
+                    blockIdx.y * kTH, out, err);
+}
+
+// One launch over the (instance, tile, slice) work items of a batch of images.
+template <int RS, typename WT>
+__global__ void __launch_bounds__(kThreads, 2)
+stencil_p1_batched_kernel(const __grid_constant__ BatchMaps maps, const BatchInst* __restrict__ insts,
+                          const int4* __restrict__ work, unsigned* __restrict__ err) {
+    const int4 w = work[blockIdx.x];  // (instance, tile row, tile column, slice)
+    const BatchInst& in = insts[w.x];
+    const size_t region = (size_t)(kTH + RS) * (kTW + 2 * RS);
+    float* out = in.part + ((size_t)(w.w * in.tiles_y + w.y) * in.tiles_x + w.z) * region;
+    p1_body<RS, WT>(reinterpret_cast<const CUtensorMap*>(maps.m[w.x]), in.H, in.W, in.d, in.z, in.splits.ox_lo[w.w], in.splits.ox_hi[w.w],
+                    w.z * kTW, w.y * kTH, out, err);
 }
 
 // --------------------------------------------------------------------------- phase 2
@@ -329,6 +349,41 @@ cudaError_t p1_launch(const TmaPlan& plan, int H, int W, const float* d, const f
     return cudaGetLastError();
 }
 
+template <int RS, typename WT>
+cudaError_t p1b_launch(const BatchMaps& maps, const BatchInst* insts, const int4* work, int nwork, unsigned* err,
+                       cudaStream_t st) {
+    static bool configured = false;
+    const size_t smem = p1_smem_bytes<RS, WT>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(stencil_p1_batched_kernel<RS, WT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (nwork <= 0) return cudaSuccess;
+    stencil_p1_batched_kernel<RS, WT><<<nwork, kThreads, smem, st>>>(maps, insts, work, err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t p1b_dispatch(int rs, const BatchMaps& maps, const BatchInst* insts, const int4* work, int nwork,
+                         unsigned* err, cudaStream_t st) {
+    switch (rs) {
+        case 1: return p1b_launch<1, WT>(maps, insts, work, nwork, err, st);
+        case 2: return p1b_launch<2, WT>(maps, insts, work, nwork, err, st);
+        case 3: return p1b_launch<3, WT>(maps, insts, work, nwork, err, st);
+        case 4: return p1b_launch<4, WT>(maps, insts, work, nwork, err, st);
+        case 5: return p1b_launch<5, WT>(maps, insts, work, nwork, err, st);
+        case 6: return p1b_launch<6, WT>(maps, insts, work, nwork, err, st);
+        case 7: return p1b_launch<7, WT>(maps, insts, work, nwork, err, st);
+        case 8: return p1b_launch<8, WT>(maps, insts, work, nwork, err, st);
+        case 10: return p1b_launch<10, WT>(maps, insts, work, nwork, err, st);
+        case 12: return p1b_launch<12, WT>(maps, insts, work, nwork, err, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename WT>
 cudaError_t p1_dispatch(int rs, const TmaPlan& plan, int H, int W, const float* d, const float* z,
                         unsigned* err, const int* skip, cudaStream_t st) {
@@ -374,6 +429,15 @@ cudaError_t launch_tma_gather(int dtype, const TmaPlan& plan, int H, int W, int 
         case 0: return p1_dispatch<float>(rs, plan, H, W, d, z, err, skip, st);
         case 1: return p1_dispatch<__half>(rs, plan, H, W, d, z, err, skip, st);
         default: return p1_dispatch<__nv_bfloat16>(rs, plan, H, W, d, z, err, skip, st);
+    }
+}
+
+cudaError_t launch_tma_gather_batched(int dtype, int rs, const BatchMaps& maps, const BatchInst* insts,
+                                      const int4* work, int nwork, unsigned* err, cudaStream_t st) {
+    switch (dtype) {
+        case 0: return p1b_dispatch<float>(rs, maps, insts, work, nwork, err, st);
+        case 1: return p1b_dispatch<__half>(rs, maps, insts, work, nwork, err, st);
+        default: return p1b_dispatch<__nv_bfloat16>(rs, maps, insts, work, nwork, err, st);
     }
 }
 

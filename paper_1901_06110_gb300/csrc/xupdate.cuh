@@ -173,4 +173,41 @@ __device__ __forceinline__ float sr_tile_x(const SrTile& T, int pi, int pj) {
     return T.X[(pi - (2 * T.qy_lo - T.G)) * kSW + (pj - (2 * T.qx_lo - T.G))];
 }
 
+// Linearized x-update (Algorithm 1, first two steps) for super-resolution on the
+// kXH x kXW tile at (y0, x0): x_out = Pi_C(mu (alpha x_in + rho (v - u) - A^T(A x_in - y))),
+// z = x_out + u.  All threads of a (32, 8) block must call it.
+__device__ __forceinline__ void sr_xupdate_body(SrTile& tile, const float* __restrict__ x_in,
+                                                float* __restrict__ x_out, const float* __restrict__ y, int H,
+                                                int W, const BlurTaps& taps, const float* __restrict__ v,
+                                                const float* __restrict__ u, float* __restrict__ z, float mu,
+                                                float alpha, float rho, int constraint, int y0, int x0) {
+    sr_tile_index(tile, H, W, taps, y0, x0);
+    SrTileRegs rg;
+    sr_tile_load(tile, x_in, y, W, rg);
+    // prefetch the per-pixel inputs while the tile loads are in flight
+    const int pj = x0 + threadIdx.x;
+    float vv[2], uu[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int pi = y0 + threadIdx.y + 8 * r;
+        const bool ok = pi < H && pj < W;
+        const size_t q = (size_t)pi * W + pj;
+        vv[r] = ok ? v[q] : 0.f;
+        uu[r] = ok ? u[q] : 0.f;
+    }
+    sr_tile_compute(tile, rg, taps.r);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int py = threadIdx.y + 8 * r;
+        const int pi = y0 + py;
+        if (pi >= H || pj >= W) continue;
+        const float g = sr_tile_grad(tile, taps.r, py, pj);
+        const size_t q = (size_t)pi * W + pj;
+        const float xv = sr_tile_x(tile, pi, pj);
+        const float xn = project(mu * (alpha * xv + rho * (vv[r] - uu[r]) - g), constraint);
+        x_out[q] = xn;
+        z[q] = xn + uu[r];
+    }
+}
+
 }  // namespace dsg

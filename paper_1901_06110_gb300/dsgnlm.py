@@ -255,5 +255,25 @@ def dsgnlm_profile_read(h: Dsgnlm, kind: int):
     return ms.value, n.value
 
 
+def lpnp_solve_batched(problems, rho: float, iters: int, residuals: bool = False):
+    """Algorithm 1 for several images at once (one launch per step over all of
+    them).  Returns per-problem residual lists when residuals=True."""
+    count = len(problems)
+    arr = (_abi.LpnpProblem * count)()
+    hists = []
+    for i, p in enumerate(problems):
+        arr[i] = p.struct
+        if residuals and iters > 0:
+            h = (ctypes.c_double * (2 * iters))()
+            hists.append(h)
+            arr[i].resid_hist = ctypes.cast(h, ctypes.POINTER(ctypes.c_double))
+        else:
+            arr[i].resid_hist = None
+    _check(_abi.load().lpnp_solve_batched(arr, count, float(rho), int(iters)), "lpnp_solve_batched")
+    if not hists:
+        return None
+    return [[(h[2 * k], h[2 * k + 1]) for k in range(iters)] for h in hists]
+
+
 def dsgnlm_launch_count() -> int:
     return int(_abi.load().dsgnlm_launch_count())

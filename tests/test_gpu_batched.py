@@ -1,0 +1,109 @@
+"""Batched Algorithm 1 (many uneven images, one launch per step) through the C ABI.
+
+- The batched solve runs the same kernels on the same tiles as lpnp_solve, so its
+  results must be bit-identical to solving the images one by one.
+- Low-precision weights (FP16, BF16; FP32 arithmetic) must give the PSNR of the
+  plain FP32 form within 0.01 dB, and stay close to the FP64 oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import lpnp as olp
+from oracle import problems
+from tests.gpu_helpers import cuda, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(48, 64), (96, 160), (40, 72), (130, 136)]
+
+
+def _prepare(wl, H, W, seed, dtype="f32", kind="sr"):
+    from paper_1901_06110_gb300 import dsgnlm as D
+    if kind == "sr":
+        inst = problems.sr_instance(wl, H=H, W=W, seed=seed)
+        data = cuda(inst["y"])
+        guide = D.lpnp_sr_guide(data)
+    else:
+        inst = problems.spi_instance(wl, H=H, W=W, seed=seed)
+        data = cuda(inst["counts"].astype(np.uint8))
+        guide = D.lpnp_spi_guide(data, 16, wl["eta"])
+    den = D.dsgnlm_create(dtype)
+    D.dsgnlm_build(den, guide, wl["patch_r"], wl["search_r"], wl["h"])
+    D.dsgnlm_balance(den, 1e-6, 1000)
+    x, v, u = D.lpnp_init(guide)
+    return dict(inst=inst, data=data, guide=guide, den=den, x=x, v=v, u=u)
+
+
+def _problem(wl, st, kind="sr", x=None, v=None, u=None):
+    from paper_1901_06110_gb300 import dsgnlm as D
+    x = st["x"] if x is None else x
+    v = st["v"] if v is None else v
+    u = st["u"] if u is None else u
+    if kind == "sr":
+        return D.Problem("sr", st["den"], x, v, u, alpha=wl["alpha"], y=st["data"],
+                         blur_sigma=wl["blur_sigma"], blur_r=wl["blur_r"])
+    return D.Problem("spi", st["den"], x, v, u, alpha=wl["alpha"], counts=st["data"], K=16, eta=wl["eta"],
+                     spi_eps=wl["spi_eps"])
+
+
+@pytest.mark.parametrize("kind,iters", [("sr", 7), ("sr", 6), ("spi", 5)])
+def test_batched_equals_one_by_one(gpu_lib, kind, iters):
+    from paper_1901_06110_gb300 import dsgnlm as D
+    wl = synthetic.workload("sr64" if kind == "sr" else "spi512")
+    wl["search_r"] = 5
+    states = [_prepare(wl, H, W, 300 + i, kind=kind) for i, (H, W) in enumerate(SIZES)]
+    singles, batch = [], []
+    for st in states:
+        a = [t.clone() for t in (st["x"], st["v"], st["u"])]
+        b = [t.clone() for t in (st["x"], st["v"], st["u"])]
+        singles.append(a)
+        batch.append(b)
+    hs = [D.lpnp_solve(_problem(wl, st, kind, *a), wl["rho"], iters, residuals=True)
+          for st, a in zip(states, singles)]
+    hb = D.lpnp_solve_batched([_problem(wl, st, kind, *b) for st, b in zip(states, batch)], wl["rho"], iters,
+                              residuals=True)
+    torch.cuda.synchronize()
+    for a, b in zip(singles, batch):
+        for ta, tb in zip(a, b):
+            np.testing.assert_array_equal(host(ta), host(tb))
+    for ha, hb_ in zip(hs, hb):
+        np.testing.assert_allclose(np.array(ha), np.array(hb_), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("dtype,oracle_tol", [("f16", 2e-3), ("bf16", 1.5e-2)])
+def test_low_precision_batch_psnr(gpu_lib, dtype, oracle_tol):
+    from paper_1901_06110_gb300 import dsgnlm as D
+    wl = synthetic.workload("sr512")
+    wl["search_r"] = 7
+    wl["patch_r"] = 2
+    sizes = [(96, 96), (128, 64), (64, 160)]
+    iters = 12
+    res = {}
+    for dt in ("f32", dtype):
+        states = [_prepare(wl, H, W, 700 + i, dtype=dt) for i, (H, W) in enumerate(sizes)]
+        D.lpnp_solve_batched([_problem(wl, st) for st in states], wl["rho"], iters)
+        torch.cuda.synchronize()
+        res[dt] = [(host(st["x"]), st["inst"]) for st in states]
+    for (x32, inst), (xlp, _) in zip(res["f32"], res[dtype]):
+        truth = inst["x_true"]
+        dpsnr = abs(olp.psnr(xlp, truth) - olp.psnr(x32, truth))
+        assert dpsnr <= 0.01, dpsnr
+        ref = problems.solve_sr(wl, inst, iters=iters, tol=1e-6)
+        assert rel_l2(x32, ref["x"]) <= 1e-5
+        assert rel_l2(xlp, ref["x"]) <= oracle_tol
+
+
+def test_batched_rejects_mixed(gpu_lib):
+    from paper_1901_06110_gb300 import _abi
+    from paper_1901_06110_gb300 import dsgnlm as D
+    wl = synthetic.workload("sr64")
+    a = _prepare(wl, 32, 32, 1, dtype="f32")
+    b = _prepare(wl, 32, 48, 2, dtype="f16")
+    with pytest.raises(D.DsgnlmError) as e:
+        D.lpnp_solve_batched([_problem(wl, a), _problem(wl, b)], 1.0, 2)
+    assert e.value.status == _abi.EINVAL
+    with pytest.raises(D.DsgnlmError) as e:  # the same handle twice
+        D.lpnp_solve_batched([_problem(wl, a), _problem(wl, a)], 1.0, 2)
+    assert e.value.status == _abi.EINVAL

@@ -47,6 +47,11 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--only-batched", default=None,
+                    help="comma-separated batched variants to time alone (plain_f32, batched_f32, batched_f16, "
+                         "batched_bf16); skips the main workload")
     return ap.parse_args()
 
 
@@ -193,6 +198,87 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------- batched form
+
+def run_batched(steps: int, warmup: int, flush, only=None):
+    """The batched low-precision form on the 64-image uneven workload (sides drawn
+    from {128 ... 1024}): whole solves of all images per step, weights stored in
+    FP16 and BF16 (FP32 arithmetic) against the plain FP32 form on the same images;
+    PSNR of every image against its ground truth."""
+    import numpy as np
+    import torch
+
+    import synthetic
+    from paper_1901_06110_gb300 import dsgnlm as D
+    from paper_1901_06110_gb300 import pipeline
+
+    wl = synthetic.workload("batch64")
+    sides = synthetic.batch_sides(wl["count"], wl["sides"], wl["seed"])
+    shapes = [(s, s) for s in sides]
+    xs, ys = [], []
+    for i, (H, W) in enumerate(shapes):
+        seed = wl["seed"] + i
+        xt = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], seed)).cuda()
+        nz = torch.from_numpy(synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], seed)).cuda()
+        xs.append(xt)
+        ys.append(D.lpnp_sr_observe(xt, nz, wl["blur_sigma"], wl["blur_r"]))
+    mpix = sum(H * W for H, W in shapes) / 1e6
+    out = {"workload": f"batch64: {len(shapes)} 2x SR images, sides {sorted(set(sides))}, {mpix:.1f} Mpix, "
+                       f"patch 7x7, search 21x21, h={wl['h']}, tol {wl['tol']}, {wl['iters']} iterations",
+           "mpix": mpix, "steps": steps}
+    psnr = {}
+
+    class OneByOne:  # the plain form: each image solved on its own (FP32 weights)
+        def __init__(self, params):
+            self.solvers = [pipeline.Solver(H, W, params) for H, W in shapes]
+            self.x = [sv.x for sv in self.solvers]
+
+        def run(self, ys_):
+            for sv, yy in zip(self.solvers, ys_):
+                sv.run(yy)
+
+        def close(self):
+            for sv in self.solvers:
+                sv.close()
+
+    variants = [("plain_f32", "f32", OneByOne), ("batched_f32", "f32", pipeline.BatchSolver),
+                ("batched_f16", "f16", pipeline.BatchSolver), ("batched_bf16", "bf16", pipeline.BatchSolver)]
+    if only:
+        variants = [v for v in variants if v[0] in only]
+    for name, dtype, cls in variants:
+        params = pipeline.Params.from_workload(wl, weight_dtype=dtype)
+        solver = cls(params) if cls is OneByOne else cls(shapes, params)
+        for _ in range(warmup):
+            solver.run(ys)
+        torch.cuda.synchronize()
+        t = 0.0
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            solver.run(ys)
+            e1.record()
+            e1.synchronize()
+            t += e0.elapsed_time(e1)
+        ms = t / steps
+        mse = [float(((x - xt) ** 2).double().mean()) for x, xt in zip(solver.x, xs)]
+        psnr[name] = np.array([10 * np.log10(1.0 / m) for m in mse])
+        out[name] = {"weights": dtype, "ms_per_step": ms, "mpix_s": mpix / (ms / 1e3),
+                     "pnp_iters_per_s": wl["iters"] / (ms / 1e3)}
+        solver.close()
+        del solver
+        torch.cuda.empty_cache()
+    if "plain_f32" in psnr:
+        for name, _, _ in variants:
+            if name == "plain_f32":
+                continue
+            out[name]["psnr_max_abs_diff_db_vs_plain"] = float(np.max(np.abs(psnr[name] - psnr["plain_f32"])))
+            out[name]["speedup_vs_plain"] = out[name]["mpix_s"] / out["plain_f32"]["mpix_s"]
+        out["psnr_db_plain_mean"] = float(psnr["plain_f32"].mean())
+    return out
+
+
 # ----------------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -328,6 +414,8 @@ def run_ours(args):
         "e2e": {"value": world * n_mpix / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": y.numel() * 4, "d2h_bytes_per_step": H * W * 4},
     }
+    if not args.no_batched:
+        line["batched"] = run_batched(args.batched_steps, 1, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         side = 192
         secs = _oracle_solve_seconds(side, wl)
@@ -344,6 +432,13 @@ def run_ours(args):
 
 def main():
     args = _args()
+    if args.only_batched:
+        import torch
+        from paper_1901_06110_gb300 import build as lib_build
+        lib_build.build()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+        print(json.dumps(run_batched(args.batched_steps, 1, flush, args.only_batched.split(","))))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -90,3 +90,42 @@ class Solver:
 
     def close(self):
         self.den.close()
+
+
+class BatchSolver:
+    """Many super-resolution images of uneven sizes solved together: per image a
+    guide, weight build and balance, then Algorithm 1 for all images at once with
+    lpnp_solve_batched (one launch per step over all images)."""
+
+    def __init__(self, shapes, params: Params):
+        self.p = params
+        self.shapes = list(shapes)
+        self.dens = [D.dsgnlm_create(params.weight_dtype) for _ in self.shapes]
+        self.x = [torch.empty(s, device="cuda") for s in self.shapes]
+        self.v = [torch.empty_like(t) for t in self.x]
+        self.u = [torch.empty_like(t) for t in self.x]
+        self.guide = [torch.empty_like(t) for t in self.x]
+        self.balance = [None] * len(self.shapes)
+        self._probs = None
+        self._ys = None
+
+    def run(self, ys):
+        p = self.p
+        lib = _abi.load()
+        stream = D._stream()
+        for i, (H, W) in enumerate(self.shapes):
+            D._check(lib.lpnp_sr_guide(ys[i].data_ptr(), H // 2, W // 2, self.guide[i].data_ptr(), stream),
+                     "lpnp_sr_guide")
+            D.dsgnlm_build(self.dens[i], self.guide[i], p.patch_r, p.search_r, p.h)
+            self.balance[i] = D.dsgnlm_balance(self.dens[i], p.tol, p.maxit)
+            D._check(lib.lpnp_init(self.guide[i].data_ptr(), H * W, self.x[i].data_ptr(), self.v[i].data_ptr(),
+                                   self.u[i].data_ptr(), stream), "lpnp_init")
+        if self._probs is None or self._ys is not ys:
+            self._probs = [D.Problem("sr", self.dens[i], self.x[i], self.v[i], self.u[i], alpha=p.alpha, y=ys[i],
+                                     blur_sigma=p.blur_sigma, blur_r=p.blur_r) for i in range(len(self.shapes))]
+            self._ys = ys
+        return D.lpnp_solve_batched(self._probs, p.rho, p.iters)
+
+    def close(self):
+        for d in self.dens:
+            d.close()

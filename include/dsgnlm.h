@@ -234,6 +234,43 @@ dsgnlm_status lpnp_sr_gradient_noalloc(const float* x, const float* y, int H, in
 dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho, int iters);
 
 /* ---------------------------------------------------------------------------
+ * Differentiable form: unrolled Algorithm 1 and its adjoint
+ * ------------------------------------------------------------------------- */
+
+typedef struct lpnp_tape* lpnp_tape_t;
+
+/* A tape holds the checkpoints of one unrolled solve (every balancing scaling and
+ * row sum, every iterate) for lpnp_backward.  Owned by the caller. */
+dsgnlm_status lpnp_tape_create(lpnp_tape_t* out);
+void lpnp_tape_destroy(lpnp_tape_t t);
+
+/* Unrolled 2x super-resolution solve with every discrete choice fixed so that x_N is
+ * differentiable in (y, guide, bandwidth, rho):
+ *   K1 from `guide` (Eq. NLM, S1; radii and bandwidth as in dsgnlm_build) into `den`;
+ *   exactly `balance_passes` passes d <- sqrt(d / K1 d) from d = 1 (Eq. S2 iterated,
+ *   no tolerance stop), m = max_s d_s (K1 d)_s, W by Eq. S3;
+ *   `iters` iterations of Algorithm 1 (box constraint [0,1], blur as in lpnp_problem)
+ *   from x = v = clip(guide, 0, 1), u = 0.
+ * y device [H/2][W/2]; guide device [H][W]; both must stay unchanged until
+ * lpnp_backward.  x_out device [H][W] receives x_N.  Records the tape (replacing any
+ * earlier recording).  `den` must not be rebuilt before the backward.  The shared
+ * memory of the backward limits (2 iters + 1)(16 + 2 N_s)(32 + 2 N_s) and
+ * (2 iters + 2 passes + 1)(16 + N_s)(32 + 2 N_s) floats to 220 KiB (EINVAL otherwise).
+ * Synchronises the stream once (to read m). */
+dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tape, dsgnlm_t den, const float* y, const float* guide, int H,
+                                    int W, int patch_r, int search_r, float bandwidth, int balance_passes,
+                                    float alpha, float rho, int iters, float blur_sigma, int blur_r, float* x_out);
+
+/* Adjoint of the recorded solve for the cotangent x_bar of x_N (device [H][W]):
+ * y_bar (device [H/2][W/2]) and guide_bar (device [H][W]) receive dL/dy and
+ * dL/dguide; *h_bar and *rho_bar (host, optional) dL/dbandwidth and dL/drho.  The
+ * derivative of the box projection and of the clip of the initial state is taken as
+ * 1 strictly inside and 0 outside; m's derivative follows its first maximiser.
+ * Synchronises the stream. */
+dsgnlm_status lpnp_backward(lpnp_tape_t tape, const float* x_bar, float* y_bar, float* guide_bar, double* h_bar,
+                            double* rho_bar);
+
+/* ---------------------------------------------------------------------------
  * Misc
  * ------------------------------------------------------------------------- */
 

@@ -50,6 +50,12 @@ SIGNATURES = {
     "lpnp_solve_batched": (c_int, [ctypes.POINTER(LpnpProblem), c_int, c_float, c_int]),
     "lpnp_sr_gradient_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_float, c_int, c_void_p,
                                          c_void_p]),
+    "lpnp_tape_create": (c_int, [ctypes.POINTER(c_void_p)]),
+    "lpnp_tape_destroy": (None, [c_void_p]),
+    "lpnp_unrolled_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float,
+                                      c_int, c_float, c_float, c_int, c_float, c_int, c_void_p]),
+    "lpnp_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
+                              ctypes.POINTER(c_double)]),
     "dsgnlm_profile_enable": (c_int, [c_void_p, c_int]),
     "dsgnlm_profile_read": (c_int, [c_void_p, c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     "dsgnlm_launch_count": (ctypes.c_uint64, []),

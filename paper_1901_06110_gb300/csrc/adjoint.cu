@@ -1,0 +1,778 @@
+// Differentiable form of linearized PnP-ADMM with DSG-NLM: an unrolled forward
+// solve that records checkpoints, and its hand-written adjoint.
+//
+// Forward (fixed discrete choices, so the output is piecewise smooth in the inputs):
+//   K1 from the guide with bandwidth h (Eq. NLM, S1), stored as half-window planes;
+//   T balancing passes d^{p+1} = sqrt(d^p / t^p), t^p = K1 d^p, from d^0 = 1 (Eq. S2);
+//   m = max_s d_s t_s with t = K1 d (first maximiser s*), W from Eq. S3;
+//   N iterations of Algorithm 1 from x = v = clip(guide), u = 0, recording (x, v, u).
+//
+// Backward, for the cotangent of x_N:
+//   iteration k (reverse): a = vh - uh, zh = W a + uh (W is symmetric),
+//     g = Pi_C'(xbar_k) (xh + zh),  xh <- mu (alpha g - A^T A g),  vh <- mu rho g,
+//     uh <- zh - mu rho g,  yh += mu A g,  rhoh += sum g mu ((v_k - u_k) - xbar_k);
+//   W depends on the pair weights w_sr = d_s d_r K1_sr / m (the diagonal closes the
+//   rows), and dL/dw_sr = G_sr = sum_k (a_k(s) - a_k(r)) (z_k(r) - z_k(s)), z_k = x_{k+1} + u_k;
+//   then through m, the T balancing passes, K1 = Lambda exp(-D c), c = 1 / (2 N_p^2 h^2),
+//   the patch distances D = box-sum of (g(p) - g(p + o))^2 and the reflection of the guide.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/dsgnlm.h"
+#include "combine.cuh"
+#include "common.cuh"
+#include "handle.h"
+#include "internal.h"
+
+namespace dsg {
+
+namespace {
+
+constexpr int kAdjTH = 16, kAdjTW = 32;  // pair-pass tiles, block (32, 8), 2 rows per thread
+
+__device__ __forceinline__ float proj_deriv(float xb, int constraint) {
+    if (constraint == 2) return (xb > 0.f && xb < 1.f) ? 1.f : 0.f;
+    if (constraint == 1) return xb > 0.f ? 1.f : 0.f;
+    return 1.f;
+}
+
+// m = max_s d_s t_s and the first maximiser (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) adj_m_argmax_kernel(const float* __restrict__ d, const float* __restrict__ t,
+                                                            int n, float* __restrict__ m_out, int* __restrict__ s_out) {
+    float best = -1.f;
+    int bi = 0x7fffffff;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const float v = d[q] * t[q];
+        if (v > best) {
+            best = v;
+            bi = q;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+            best = ov;
+            bi = oi;
+        }
+    }
+    __shared__ float sv[32];
+    __shared__ int si[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sv[warp] = best;
+        si[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sv[w] > best || (sv[w] == best && si[w] < bi)) {
+                best = sv[w];
+                bi = si[w];
+            }
+        *m_out = best;
+        *s_out = bi;
+    }
+}
+
+// a_k = vh - uh, z_k = x_{k+1} + u_k
+__global__ void adj_az_kernel(int n, const float* __restrict__ vh, const float* __restrict__ uh,
+                              const float* __restrict__ x1, const float* __restrict__ u0, float* __restrict__ a,
+                              float* __restrict__ z) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    a[q] = vh[q] - uh[q];
+    z[q] = x1[q] + u0[q];
+}
+
+// zh = W a + uh; g = Pi_C'(xbar_k) (xh + zh); per-block partial of sum g mu ((v - u) - xbar)
+__global__ void __launch_bounds__(256) adj_g_kernel(int n, const float* __restrict__ wa, const float* __restrict__ uh,
+                                                    const float* __restrict__ xh, const float* __restrict__ xk,
+                                                    const float* __restrict__ vk, const float* __restrict__ uk,
+                                                    const float* __restrict__ gradk, float mu, float alpha,
+                                                    float rho, int constraint, float* __restrict__ g,
+                                                    float* __restrict__ zh, double* __restrict__ rho_part) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    double r = 0.0;
+    if (q < n) {
+        const float zz = wa[q] + uh[q];
+        const float vu = vk[q] - uk[q];
+        const float xb = mu * (alpha * xk[q] + rho * vu - gradk[q]);
+        const float gg = proj_deriv(xb, constraint) * (xh[q] + zz);
+        g[q] = gg;
+        zh[q] = zz;
+        r = (double)gg * (double)mu * ((double)vu - (double)xb);
+    }
+    r = warp_sum(r);
+    __shared__ double s[8];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int w = 0; w < 8; ++w) acc += s[w];
+        rho_part[blockIdx.x] += acc;  // one slot per block, accumulated over iterations in a fixed order
+    }
+}
+
+// xh = mu (alpha g - A^T A g), vh = mu rho g, uh = zh - mu rho g
+__global__ void adj_update_kernel(int n, const float* __restrict__ g, const float* __restrict__ ata,
+                                  const float* __restrict__ zh, float mu, float alpha, float rho,
+                                  float* __restrict__ xh, float* __restrict__ vh, float* __restrict__ uh) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float gg = g[q];
+    xh[q] = mu * (alpha * gg - ata[q]);
+    vh[q] = mu * rho * gg;
+    uh[q] = zh[q] - mu * rho * gg;
+}
+
+__global__ void adj_axpy_kernel(int n, float a, const float* __restrict__ x, float* __restrict__ y) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) y[q] += a * x[q];
+}
+
+// Stage `nf` fields (each n floats apart) over rows [r0, r0 + RH), cols [c0, c0 + RW), zero outside.
+__device__ __forceinline__ void stage_fields(float* S, const float* __restrict__ F, int nf, size_t n, int H, int W,
+                                             int r0, int c0, int RH, int RW) {
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int cells = RH * RW;
+    for (int f = 0; f < nf; ++f)
+        for (int idx = tid; idx < cells; idx += 256) {
+            const int a = idx / RW, b = idx - a * RW;
+            const int i = r0 + a, j = c0 + b;
+            S[f * cells + idx] = (i >= 0 && i < H && j >= 0 && j < W) ? F[f * n + (size_t)i * W + j] : 0.f;
+        }
+}
+
+// Pair pass A: dh(s) = (1/m) sum_{r ~ s} G_sr d_r K1_sr over both half-window directions,
+// and per-block partials of -(1/m^2) sum over half-window pairs of G d_s d_r K1.
+// Fields staged: a_k, z_k (k < N), d over the tile + rs halo on every side.
+template <typename WT>
+__global__ void __launch_bounds__(256)
+adj_pairs_a_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const float* __restrict__ AZ,
+                   const float* __restrict__ d, float inv_m, float* __restrict__ dh, double* __restrict__ m_part) {
+    extern __shared__ float S[];
+    const int y0 = blockIdx.y * kAdjTH, x0 = blockIdx.x * kAdjTW;
+    const int RH = kAdjTH + 2 * rs, RW = kAdjTW + 2 * rs, cells = RH * RW;
+    const size_t n = (size_t)H * W;
+    stage_fields(S, AZ, 2 * N, n, H, W, y0 - rs, x0 - rs, RH, RW);
+    stage_fields(S + 2 * N * cells, d, 1, n, H, W, y0 - rs, x0 - rs, RH, RW);
+    __syncthreads();
+    const float* Sa = S;
+    const float* Sz = S + N * cells;
+    const float* Sd = S + 2 * N * cells;
+    const int Wp = plane_pitch(W);
+    const size_t plane = (size_t)H * Wp;
+    double mpart = 0.0;
+    const int j = x0 + threadIdx.x;
+    for (int py = threadIdx.y; py < kAdjTH; py += 8) {
+        const int i = y0 + py;
+        if (i >= H || j >= W) continue;
+        const int cs = (py + rs) * RW + threadIdx.x + rs;  // cell of s
+        float accd = 0.f, accm = 0.f;
+        for (int oy = 0; oy <= rs; ++oy) {
+            const int ox0 = oy == 0 ? 1 : -rs;
+            for (int ox = ox0; ox <= rs; ++ox) {
+                const int k = oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
+                const WT* Pk = P + (size_t)k * plane;
+                for (int dir = 0; dir < 2; ++dir) {
+                    const int ri = dir == 0 ? i + oy : i - oy, rj = dir == 0 ? j + ox : j - ox;
+                    if (ri < 0 || ri >= H || rj < 0 || rj >= W) continue;
+                    const float K = to_f32(dir == 0 ? Pk[(size_t)i * Wp + j] : Pk[(size_t)ri * Wp + rj]);
+                    const int cr = cs + (dir == 0 ? oy * RW + ox : -(oy * RW + ox));
+                    float G = 0.f;
+                    for (int kk = 0; kk < N; ++kk)
+                        G = fmaf(Sa[kk * cells + cs] - Sa[kk * cells + cr], Sz[kk * cells + cr] - Sz[kk * cells + cs], G);
+                    accd = fmaf(G * Sd[cr], K, accd);
+                    if (dir == 0) accm = fmaf(G * Sd[cs] * Sd[cr], K, accm);
+                }
+            }
+        }
+        dh[(size_t)i * W + j] = accd * inv_m;
+        mpart -= (double)accm * (double)inv_m * (double)inv_m;
+    }
+    mpart = warp_sum(mpart);
+    __shared__ double sm[8];
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    if ((t & 31) == 0) sm[t >> 5] = mpart;
+    __syncthreads();
+    if (t == 0) {
+        double acc = 0.0;
+        for (int w = 0; w < 8; ++w) acc += sm[w];
+        m_part[blockIdx.y * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
+// fixed-order sum of `count` doubles into *out (one block)
+__global__ void __launch_bounds__(256) adj_sum_kernel(const double* __restrict__ part, int count, double* __restrict__ out) {
+    double a = 0.0;
+    for (int q = threadIdx.x; q < count; q += 256) a += part[q];
+    __shared__ double s[256];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+// Through m = d_{s*} t_{s*}: dh_{s*} += mh (t_{s*} + d_{s*}); dh_j += mh d_{s*} K1(s*, j), j != s*
+template <typename WT>
+__global__ void adj_mterms_kernel(const WT* __restrict__ P, int H, int W, int rs, const float* __restrict__ d,
+                                  const float* __restrict__ t, const int* __restrict__ s_star,
+                                  const double* __restrict__ mh_ptr, float* __restrict__ dh) {
+    const int ss = *s_star;
+    const int si = ss / W, sj = ss - si * W;
+    const float mh = (float)*mh_ptr;
+    const int Wp = plane_pitch(W);
+    const size_t plane = (size_t)H * Wp;
+    const int side = 2 * rs + 1;
+    for (int q = threadIdx.x; q < side * side; q += blockDim.x) {
+        const int oy = q / side - rs, ox = q % side - rs;
+        const int ri = si + oy, rj = sj + ox;
+        if (ri < 0 || ri >= H || rj < 0 || rj >= W) continue;
+        if (oy == 0 && ox == 0) {
+            dh[ss] += mh * (t[ss] + d[ss]);
+            continue;
+        }
+        // K1(s*, r): plane of the half offset +-o at the lower-indexed end
+        const bool fwd = oy > 0 || (oy == 0 && ox > 0);
+        const int ay = fwd ? oy : -oy, ax = fwd ? ox : -ox;
+        const int k = ay == 0 ? ax - 1 : rs + (ay - 1) * (2 * rs + 1) + ax + rs;
+        const float K = to_f32(fwd ? P[(size_t)k * plane + (size_t)si * Wp + sj] : P[(size_t)k * plane + (size_t)ri * Wp + rj]);
+        dh[(size_t)ri * W + rj] += mh * d[ss] * K;
+    }
+}
+
+// Balancing pass p backwards: th = -0.5 dh' d'/t, base = 0.5 dh' d'/d (d' = d^{p+1})
+__global__ void adj_sk_pre_kernel(int n, const float* __restrict__ dhn, const float* __restrict__ dn,
+                                  const float* __restrict__ dp, const float* __restrict__ tp, float* __restrict__ th,
+                                  float* __restrict__ base) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float w = 0.5f * dhn[q] * dn[q];
+    th[q] = -w / tp[q];
+    base[q] = w / dp[q];
+}
+
+// dh^p = base + K1 th = base + th + sum_{r != s} K1 th_r (phase-1 partial sums in cv)
+__global__ void __launch_bounds__(256) adj_sk_finish_kernel(Cover cv, int H, int W, const float* __restrict__ th,
+                                                            const float* __restrict__ base, float* __restrict__ dh) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= H || j >= W) return;
+    const size_t s = (size_t)i * W + j;
+    dh[s] = base[s] + th[s] + gather_partials(cv, i, j);
+}
+
+// Pair pass B: the cotangent of every stored weight K1(s, s + o),
+//   Kh = G d_s d_r / m + sum_p (th^p_s d^p_r + th^p_r d^p_s) + [s or r = s*] mh d_s d_r,
+// then Dh = -c K1 Kh (written as planes) and per-block partials of dL/dh = sum Kh K1 D 2c/h.
+// Fields staged over the tile and its forward halo: a_k, z_k (N each), d^p (T + 1), th^p (T).
+template <typename WT>
+__global__ void __launch_bounds__(256)
+adj_pairs_b_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, int T, const float* __restrict__ AZ,
+                   const float* __restrict__ Dh, const float* __restrict__ Th, float inv_m, float c, float hfac,
+                   const int* __restrict__ s_star, const double* __restrict__ mh_ptr, float* __restrict__ Dhat,
+                   double* __restrict__ h_part) {
+    extern __shared__ float S[];
+    const int y0 = blockIdx.y * kAdjTH, x0 = blockIdx.x * kAdjTW;
+    const int RH = kAdjTH + rs, RW = kAdjTW + 2 * rs, cells = RH * RW;
+    const size_t n = (size_t)H * W;
+    stage_fields(S, AZ, 2 * N, n, H, W, y0, x0 - rs, RH, RW);
+    stage_fields(S + 2 * N * cells, Dh, T + 1, n, H, W, y0, x0 - rs, RH, RW);
+    stage_fields(S + (2 * N + T + 1) * cells, Th, T, n, H, W, y0, x0 - rs, RH, RW);
+    __syncthreads();
+    const float* Sa = S;
+    const float* Sz = S + N * cells;
+    const float* Sdp = S + 2 * N * cells;        // d^0 .. d^T
+    const float* Sth = S + (2 * N + T + 1) * cells;  // th^0 .. th^{T-1}
+    const float* Sd = Sdp + T * cells;           // d = d^T
+    const int ss = *s_star;
+    const float mh = (float)*mh_ptr;
+    const int Wp = plane_pitch(W);
+    const size_t plane = (size_t)H * Wp;
+    const float inv_hat = 1.0f / (float)(rs + 1);
+    double hpart = 0.0;
+    const int j = x0 + threadIdx.x;
+    for (int py = threadIdx.y; py < kAdjTH; py += 8) {
+        const int i = y0 + py;
+        if (i >= H || j >= W) continue;
+        const int cs = py * RW + threadIdx.x + rs;
+        const int sidx = i * W + j;
+        for (int oy = 0; oy <= rs; ++oy) {
+            const int ox0 = oy == 0 ? 1 : -rs;
+            for (int ox = ox0; ox <= rs; ++ox) {
+                const int k = oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
+                const size_t at = (size_t)k * plane + (size_t)i * Wp + j;
+                const int ri = i + oy, rj = j + ox;
+                if (ri >= H || rj < 0 || rj >= W) {
+                    Dhat[at] = 0.f;
+                    continue;
+                }
+                const float K = to_f32(P[at]);
+                const int cr = cs + oy * RW + ox;
+                float G = 0.f;
+                for (int kk = 0; kk < N; ++kk)
+                    G = fmaf(Sa[kk * cells + cs] - Sa[kk * cells + cr], Sz[kk * cells + cr] - Sz[kk * cells + cs], G);
+                float Kh = G * Sd[cs] * Sd[cr] * inv_m;
+                for (int p = 0; p < T; ++p)
+                    Kh += Sth[p * cells + cs] * Sdp[p * cells + cr] + Sth[p * cells + cr] * Sdp[p * cells + cs];
+                const int ridx = ri * W + rj;
+                if (sidx == ss || ridx == ss) Kh = fmaf(mh, Sd[cs] * Sd[cr], Kh);
+                Dhat[at] = -c * K * Kh;
+                if (K > 0.f) {
+                    const float lam = (1.0f - fabsf((float)oy) * inv_hat) * (1.0f - fabsf((float)ox) * inv_hat);
+                    const float D = -logf(K / lam) / c;
+                    hpart += (double)Kh * (double)K * (double)D * (double)hfac;
+                }
+            }
+        }
+    }
+    hpart = warp_sum(hpart);
+    __shared__ double sm[8];
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    if ((t & 31) == 0) sm[t >> 5] = hpart;
+    __syncthreads();
+    if (t == 0) {
+        double acc = 0.0;
+        for (int w = 0; w < 8; ++w) acc += sm[w];
+        h_part[blockIdx.y * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
+// Patch-distance adjoint.  For a tile of positions p of the guide extended by the
+// patch radius (p in [-rp, H + rp) x [-rp, W + rp)) and a chunk of offsets o:
+//   Eh_o(p) = sum_{t in patch} Dh_o(p - t)              (box sum, Dh = 0 off the image)
+//   F = 2 Eh_o(p) (g(p) - g(p + o)),  ge(p) += F,  ge(p + o) -= F,
+// with g the reflected guide; ge lives on the extended grid and is folded back
+// into the image afterwards.  Scatter targets are accumulated in shared memory
+// and added to ge once per CTA.
+constexpr int kGTH = 16, kGTW = 32, kGChunk = 16;
+
+__global__ void __launch_bounds__(256)
+adj_guide_kernel(const float* __restrict__ Dhat, const float* __restrict__ guide, int H, int W, int rp, int rs,
+                 float* __restrict__ ge) {
+    extern __shared__ float S[];
+    const int nh = num_half_offsets(rs);
+    const int py0 = blockIdx.y * kGTH - rp, px0 = blockIdx.x * kGTW - rp;  // image coords of the tile origin
+    const int k0 = blockIdx.z * kGChunk, k1 = min(nh, k0 + kGChunk);
+    // guide over rows [py0, py0 + TH + rs), cols [px0 - rs, px0 + TW + rs) (reflected)
+    const int GH = kGTH + rs, GW = kGTW + 2 * rs;
+    // Dh over rows [py0 - rp, py0 + TH + rp), cols [px0 - rp, px0 + TW + rp)
+    const int DH = kGTH + 2 * rp, DW = kGTW + 2 * rp;
+    float* Gs = S;
+    float* Ds = Gs + GH * GW;
+    float* Rs = Ds + DH * DW;  // horizontal box sums [DH][TW]
+    float* Acc = Rs + DH * kGTW;  // scatter accumulator over rows [py0, py0 + TH + rs), cols [px0 - rs, ...)
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int idx = tid; idx < GH * GW; idx += 256) {
+        const int a = idx / GW, b = idx - a * GW;
+        Gs[idx] = guide[(size_t)sym_index(py0 + a, H) * W + sym_index(px0 - rs + b, W)];
+        Acc[idx] = 0.f;
+    }
+    const int Wp = plane_pitch(W);
+    const size_t plane = (size_t)H * Wp;
+    for (int k = k0; k < k1; ++k) {
+        int oy, ox;
+        half_offset(k, rs, oy, ox);
+        const float* Dk = Dhat + (size_t)k * plane;
+        __syncthreads();
+        for (int idx = tid; idx < DH * DW; idx += 256) {
+            const int a = idx / DW, b = idx - a * DW;
+            const int i = py0 - rp + a, j = px0 - rp + b;
+            Ds[idx] = (i >= 0 && i < H && j >= 0 && j < W) ? Dk[(size_t)i * Wp + j] : 0.f;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < DH * kGTW; idx += 256) {
+            const int a = idx / kGTW, b = idx - a * kGTW;
+            float acc = 0.f;
+            for (int t = 0; t <= 2 * rp; ++t) acc += Ds[a * DW + b + t];
+            Rs[idx] = acc;
+        }
+        __syncthreads();
+        const int b = threadIdx.x;
+        for (int a = threadIdx.y; a < kGTH; a += 8) {
+            const int pi = py0 + a, pj = px0 + b;
+            if (pi >= H + rp || pj >= W + rp) continue;
+            float E = 0.f;
+            for (int t = 0; t <= 2 * rp; ++t) E += Rs[(a + t) * kGTW + b];
+            const float gp = Gs[a * GW + b + rs];
+            const float go = Gs[(a + oy) * GW + b + rs + ox];
+            const float F = 2.f * E * (gp - go);
+            atomicAdd(&Acc[a * GW + b + rs], F);
+            atomicAdd(&Acc[(a + oy) * GW + b + rs + ox], -F);
+        }
+    }
+    __syncthreads();
+    const int EW = W + 2 * rp, EH = H + 2 * rp;
+    for (int idx = tid; idx < GH * GW; idx += 256) {
+        const int a = idx / GW, b2 = idx - a * GW;
+        const int ei = py0 + a + rp, ej = px0 - rs + b2 + rp;  // extended-grid coordinates
+        const float v = Acc[idx];
+        if (v != 0.f && ei >= 0 && ei < EH && ej >= 0 && ej < EW) atomicAdd(&ge[(size_t)ei * EW + ej], v);
+    }
+}
+
+// gb(q) = (xh0 + vh0)(q) [0 < g(q) < 1] + sum of ge(p) over extended p reflecting onto q
+__global__ void adj_fold_kernel(const float* __restrict__ ge, const float* __restrict__ xh0,
+                                const float* __restrict__ vh0, const float* __restrict__ guide, int H, int W, int rp,
+                                float* __restrict__ gb) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= H || j >= W) return;
+    const size_t q = (size_t)i * W + j;
+    const float g = guide[q];
+    float acc = (g > 0.f && g < 1.f) ? xh0[q] + vh0[q] : 0.f;
+    const int EW = W + 2 * rp;
+    for (int pi = -rp; pi < H + rp; ++pi) {
+        if (sym_index(pi, H) != i) continue;
+        for (int pj = -rp; pj < W + rp; ++pj) {
+            if (sym_index(pj, W) != j) continue;
+            acc += ge[(size_t)(pi + rp) * EW + (pj + rp)];
+        }
+    }
+    gb[q] = acc;
+}
+
+int nblk(size_t n) { return (int)((n + 255) / 256); }
+
+}  // namespace
+
+}  // namespace dsg
+
+using namespace dsg;
+
+struct lpnp_tape {
+    dsgnlm_t den = nullptr;
+    int H = 0, W = 0, rp = 0, rs = 0, T = 0, N = 0, constraint = 2;
+    float h = 0.f, alpha = 1.f, rho = 1.f, mu = 0.5f, c = 0.f;
+    BlurTaps taps{};
+    const float* y = nullptr;      // caller's observation (kept valid until the backward)
+    const float* guide = nullptr;  // caller's guide
+    DevBuf Dh, Th, X, V, U, AZ, xh, vh, uh, zh, g, wa, grad, ata, rlo, ag, yb, dh[2], base, thp, Dhat, ge, gb,
+        ctl, part, m, sstar, mh, rho_part, h_part, m_part, scratch;
+    float inv_m = 1.f;
+};
+
+namespace {
+
+dsgnlm_status tape_ck(cudaError_t e) {
+    if (e == cudaSuccess) return DSGNLM_OK;
+    record_cuda_error(e);
+    return e == cudaErrorMemoryAllocation ? DSGNLM_ENOMEM : DSGNLM_ECUDA;
+}
+
+#define TAPE_CK(expr)                                   \
+    do {                                                \
+        dsgnlm_status s_ = tape_ck(expr);               \
+        if (s_ != DSGNLM_OK) return s_;                 \
+    } while (0)
+
+template <typename WT>
+cudaError_t pairs_a(const lpnp_tape* tp, const void* planes, cudaStream_t st, double* m_part) {
+    const int H = tp->H, W = tp->W, rs = tp->rs;
+    const size_t smem = sizeof(float) * (size_t)(2 * tp->N + 1) * (kAdjTH + 2 * rs) * (kAdjTW + 2 * rs);
+    cudaError_t e = cudaFuncSetAttribute(adj_pairs_a_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
+    adj_pairs_a_kernel<WT><<<grid, dim3(32, 8), smem, st>>>((const WT*)planes, H, W, rs, tp->N, tp->AZ.as<float>(),
+                                                            tp->Dh.as<float>() + (size_t)tp->T * H * W, tp->inv_m,
+                                                            tp->dh[0].as<float>(), m_part);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t pairs_b(const lpnp_tape* tp, const void* planes, cudaStream_t st) {
+    const int H = tp->H, W = tp->W, rs = tp->rs;
+    const size_t smem =
+        sizeof(float) * (size_t)(2 * tp->N + 2 * tp->T + 1) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
+    cudaError_t e = cudaFuncSetAttribute(adj_pairs_b_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
+    adj_pairs_b_kernel<WT><<<grid, dim3(32, 8), smem, st>>>(
+        (const WT*)planes, H, W, rs, tp->N, tp->T, tp->AZ.as<float>(), tp->Dh.as<float>(), tp->thp.as<float>(),
+        tp->inv_m, tp->c, 2.f * tp->c / tp->h, tp->sstar.as<int>(), tp->mh.as<double>(), tp->Dhat.as<float>(),
+        tp->h_part.as<double>());
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename WT>
+cudaError_t mterms(const lpnp_tape* tp, const void* planes, cudaStream_t st) {
+    const size_t n = (size_t)tp->H * tp->W;
+    adj_mterms_kernel<WT><<<1, 256, 0, st>>>((const WT*)planes, tp->H, tp->W, tp->rs,
+                                             tp->Dh.as<float>() + (size_t)tp->T * n, tp->Th.as<float>() + (size_t)tp->T * n,
+                                             tp->sstar.as<int>(), tp->mh.as<double>(), tp->dh[0].as<float>());
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+dsgnlm_status lpnp_tape_create(lpnp_tape_t* out) {
+    if (!out) return DSGNLM_EINVAL;
+    *out = new (std::nothrow) lpnp_tape();
+    return *out ? DSGNLM_OK : DSGNLM_ENOMEM;
+}
+
+void lpnp_tape_destroy(lpnp_tape_t t) {
+    if (!t) return;
+    if (t->den) cudaStreamSynchronize(t->den->stream);
+    DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
+                      &t->wa, &t->grad, &t->ata, &t->rlo, &t->ag, &t->yb, &t->dh[0], &t->dh[1], &t->base,
+                      &t->thp, &t->Dhat, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->sstar, &t->mh,
+                      &t->rho_part, &t->h_part, &t->m_part, &t->scratch};
+    for (DevBuf* b : bufs) b->release();
+    delete t;
+}
+
+dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y, const float* guide, int H, int W,
+                                    int patch_r, int search_r, float bandwidth, int balance_passes, float alpha,
+                                    float rho, int iters, float blur_sigma, int blur_r, float* x_out) {
+    if (!tp || !den || !y || !guide || !x_out) return DSGNLM_EINVAL;
+    if (H < 2 || W < 2 || (H & 1) || (W & 1) || iters < 1 || iters > 256 || balance_passes < 0 ||
+        balance_passes > 64 || !(rho > 0.f) || !(alpha >= 0.f) || blur_r < 0 || blur_r > 8 || !(blur_sigma > 0.f))
+        return DSGNLM_EINVAL;
+    if (!tma_path_supports(search_r)) return DSGNLM_EINVAL;
+    {
+        // shared memory of the pair passes of the backward (fields over a tile + halo)
+        const size_t a_bytes = sizeof(float) * (size_t)(2 * iters + 1) * (kAdjTH + 2 * search_r) * (kAdjTW + 2 * search_r);
+        const size_t b_bytes =
+            sizeof(float) * (size_t)(2 * iters + 2 * balance_passes + 1) * (kAdjTH + search_r) * (kAdjTW + 2 * search_r);
+        if (a_bytes > 220 * 1024 || b_bytes > 220 * 1024) return DSGNLM_EINVAL;
+    }
+    dsgnlm_status s = dsgnlm_build(den, guide, H, W, patch_r, search_r, bandwidth);
+    if (s != DSGNLM_OK) return s;
+    if (!den->fast) return DSGNLM_EINVAL;
+    cudaStream_t st = den->stream;
+    const size_t n = (size_t)H * W;
+    const int T = balance_passes, N = iters;
+    tp->den = den;
+    tp->H = H;
+    tp->W = W;
+    tp->rp = patch_r;
+    tp->rs = search_r;
+    tp->T = T;
+    tp->N = N;
+    tp->h = bandwidth;
+    tp->alpha = alpha;
+    tp->rho = rho;
+    tp->mu = (float)(1.0 / ((double)alpha + (double)rho));
+    const double np = 2.0 * patch_r + 1.0;
+    tp->c = (float)(1.0 / (2.0 * np * np * (double)bandwidth * (double)bandwidth));
+    tp->taps = make_blur_taps(blur_sigma, blur_r);
+    tp->y = y;
+    tp->guide = guide;
+    TAPE_CK(tp->Dh.ensure(sizeof(float) * n * (T + 1)));
+    TAPE_CK(tp->Th.ensure(sizeof(float) * n * (T + 1)));
+    TAPE_CK(tp->X.ensure(sizeof(float) * n * (N + 1)));
+    TAPE_CK(tp->V.ensure(sizeof(float) * n * (N + 1)));
+    TAPE_CK(tp->U.ensure(sizeof(float) * n * (N + 1)));
+    TAPE_CK(tp->scratch.ensure(sizeof(float) * n));
+    TAPE_CK(tp->ctl.ensure(sizeof(BalanceCtl)));
+    TAPE_CK(tp->part.ensure(sizeof(float2) * (size_t)balance_combine_blocks(H, W)));
+    TAPE_CK(tp->m.ensure(sizeof(float)));
+    TAPE_CK(tp->sstar.ensure(sizeof(int)));
+    TAPE_CK(cudaMemsetAsync(tp->ctl.p, 0, sizeof(BalanceCtl), st));  // done = 0: passes always run
+    TAPE_CK(launch_fill(tp->Dh.as<float>(), 1.0f, n, st));
+    // T balancing passes with every d^p and t^p kept, then t^T = K1 d^T
+    BalanceCtl* ctl = tp->ctl.as<BalanceCtl>();
+    for (int p = 0; p <= T; ++p) {
+        float* dp = tp->Dh.as<float>() + (size_t)p * n;
+        float* dn = p < T ? tp->Dh.as<float>() + (size_t)(p + 1) * n : tp->scratch.as<float>();
+        TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, search_r, dp, nullptr, den->err.as<unsigned>(),
+                                  &ctl->done, st));
+        TAPE_CK(launch_balance_combine(den->plan, H, W, search_r, dp, dn, tp->Th.as<float>() + (size_t)p * n,
+                                       tp->part.as<float2>(), ctl, st));
+    }
+    const float* dT = tp->Dh.as<float>() + (size_t)T * n;
+    const float* tT = tp->Th.as<float>() + (size_t)T * n;
+    adj_m_argmax_kernel<<<1, 1024, 0, st>>>(dT, tT, (int)n, tp->m.as<float>(), tp->sstar.as<int>());
+    count_launches(1);
+    TAPE_CK(cudaGetLastError());
+    float mval = 1.f;
+    TAPE_CK(cudaMemcpyAsync(&mval, tp->m.p, sizeof(float), cudaMemcpyDeviceToHost, st));
+    TAPE_CK(cudaStreamSynchronize(st));
+    tp->inv_m = (float)(1.0 / (double)mval);
+    // the handle now holds this W
+    den->d_final = const_cast<float*>(dT);
+    den->t_final = const_cast<float*>(tT);
+    den->m = mval;
+    den->inv_m = tp->inv_m;
+    den->iters = T;
+    den->balanced = true;
+    // Algorithm 1, one iteration at a time, every state recorded
+    TAPE_CK(launch_init(guide, (int)n, tp->X.as<float>(), tp->V.as<float>(), tp->U.as<float>(), st));
+    lpnp_problem pr{};
+    pr.kind = LPNP_SR2;
+    pr.H = H;
+    pr.W = W;
+    pr.y = y;
+    pr.blur_sigma = blur_sigma;
+    pr.blur_r = blur_r;
+    pr.constraint = tp->constraint;
+    pr.alpha = alpha;
+    pr.den = den;
+    for (int k = 0; k < N; ++k) {
+        float* x1 = tp->X.as<float>() + (size_t)(k + 1) * n;
+        float* v1 = tp->V.as<float>() + (size_t)(k + 1) * n;
+        float* u1 = tp->U.as<float>() + (size_t)(k + 1) * n;
+        TAPE_CK(cudaMemcpyAsync(x1, x1 - n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        TAPE_CK(cudaMemcpyAsync(v1, v1 - n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        TAPE_CK(cudaMemcpyAsync(u1, u1 - n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        pr.x = x1;
+        pr.v = v1;
+        pr.u = u1;
+        s = lpnp_solve(&pr, rho, 1);
+        if (s != DSGNLM_OK) return s;
+    }
+    TAPE_CK(cudaMemcpyAsync(x_out, tp->X.as<float>() + (size_t)N * n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_backward(lpnp_tape_t tp, const float* x_bar, float* y_bar, float* guide_bar, double* h_bar,
+                            double* rho_bar) {
+    if (!tp || !tp->den || !x_bar || !y_bar || !guide_bar) return DSGNLM_EINVAL;
+    dsgnlm* den = tp->den;
+    cudaStream_t st = den->stream;
+    const int H = tp->H, W = tp->W, N = tp->N, T = tp->T, rs = tp->rs, rp = tp->rp;
+    const size_t n = (size_t)H * W, nlo = n / 4;
+    const int nh = num_half_offsets(rs);
+    // the handle's planes must still hold this tape's K1
+    if (den->H != H || den->W != W || den->rs != rs || den->nh != nh) return DSGNLM_EINVAL;
+    DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->wa, &tp->grad, &tp->ata,
+                       &tp->dh[0], &tp->dh[1], &tp->base, &tp->gb};
+    for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
+    TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
+    TAPE_CK(tp->thp.ensure(sizeof(float) * n * (T > 0 ? T : 1)));
+    TAPE_CK(tp->rlo.ensure(sizeof(float) * nlo));
+    TAPE_CK(tp->ag.ensure(sizeof(float) * nlo));
+    TAPE_CK(tp->yb.ensure(sizeof(float) * nlo));
+    TAPE_CK(tp->Dhat.ensure(sizeof(float) * (size_t)nh * H * plane_pitch(W)));
+    const size_t ne = (size_t)(H + 2 * rp) * (W + 2 * rp);
+    TAPE_CK(tp->ge.ensure(sizeof(float) * ne));
+    const int nb = nblk(n);
+    const dim3 pgrid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
+    const int npb = (int)(pgrid.x * pgrid.y);
+    TAPE_CK(tp->rho_part.ensure(sizeof(double) * nb));
+    TAPE_CK(tp->h_part.ensure(sizeof(double) * npb));
+    TAPE_CK(tp->m_part.ensure(sizeof(double) * npb));
+    TAPE_CK(tp->mh.ensure(sizeof(double) * 3));
+    TAPE_CK(cudaMemsetAsync(tp->rho_part.p, 0, sizeof(double) * nb, st));
+    TAPE_CK(cudaMemsetAsync(tp->yb.p, 0, sizeof(float) * nlo, st));
+    TAPE_CK(cudaMemsetAsync(tp->vh.p, 0, sizeof(float) * n, st));
+    TAPE_CK(cudaMemsetAsync(tp->uh.p, 0, sizeof(float) * n, st));
+    TAPE_CK(cudaMemcpyAsync(tp->xh.p, x_bar, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    const float mu = tp->mu, alpha = tp->alpha, rho = tp->rho;
+    const float* dT = tp->Dh.as<float>() + (size_t)T * n;
+    const float* tT = tp->Th.as<float>() + (size_t)T * n;
+    float* A = tp->AZ.as<float>();
+    float* Z = A + (size_t)N * n;
+    for (int k = N - 1; k >= 0; --k) {
+        const float* xk = tp->X.as<float>() + (size_t)k * n;
+        const float* vk = tp->V.as<float>() + (size_t)k * n;
+        const float* uk = tp->U.as<float>() + (size_t)k * n;
+        const float* x1 = xk + n;
+        float* ak = A + (size_t)k * n;
+        adj_az_kernel<<<nb, 256, 0, st>>>((int)n, tp->vh.as<float>(), tp->uh.as<float>(), x1, uk, ak, Z + (size_t)k * n);
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+        // W a (W symmetric)
+        TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, dT, ak, den->err.as<unsigned>(), nullptr, st));
+        TAPE_CK(launch_tma_apply_finish(den->plan, H, W, rs, dT, tT, tp->inv_m, ak, tp->wa.as<float>(), st));
+        // grad f(x_k) for xbar_k
+        TAPE_CK(launch_sr_forward(xk, H, W, tp->taps, tp->y, -1.0f, tp->rlo.as<float>(), st));
+        TAPE_CK(launch_sr_adjoint(tp->rlo.as<float>(), H, W, tp->taps, tp->grad.as<float>(), st));
+        adj_g_kernel<<<nb, 256, 0, st>>>((int)n, tp->wa.as<float>(), tp->uh.as<float>(), tp->xh.as<float>(), xk, vk, uk,
+                                         tp->grad.as<float>(), mu, alpha, rho, tp->constraint, tp->g.as<float>(),
+                                         tp->zh.as<float>(), tp->rho_part.as<double>());
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+        // A g and A^T A g
+        TAPE_CK(launch_sr_forward(tp->g.as<float>(), H, W, tp->taps, nullptr, 0.f, tp->ag.as<float>(), st));
+        TAPE_CK(launch_sr_adjoint(tp->ag.as<float>(), H, W, tp->taps, tp->ata.as<float>(), st));
+        adj_update_kernel<<<nb, 256, 0, st>>>((int)n, tp->g.as<float>(), tp->ata.as<float>(), tp->zh.as<float>(), mu,
+                                              alpha, rho, tp->xh.as<float>(), tp->vh.as<float>(), tp->uh.as<float>());
+        adj_axpy_kernel<<<nblk(nlo), 256, 0, st>>>((int)nlo, mu, tp->ag.as<float>(), tp->yb.as<float>());
+        count_launches(2);
+        TAPE_CK(cudaGetLastError());
+    }
+    // pair pass A: dh from G, partials of mh
+    double* m_part = tp->m_part.as<double>();
+    double* mh = tp->mh.as<double>();
+    switch (den->dtype) {
+        case DSGNLM_F32: TAPE_CK(pairs_a<float>(tp, den->planes.p, st, m_part)); break;
+        case DSGNLM_F16: TAPE_CK(pairs_a<__half>(tp, den->planes.p, st, m_part)); break;
+        default: TAPE_CK(pairs_a<__nv_bfloat16>(tp, den->planes.p, st, m_part)); break;
+    }
+    adj_sum_kernel<<<1, 256, 0, st>>>(m_part, npb, mh);
+    count_launches(1);
+    TAPE_CK(cudaGetLastError());
+    switch (den->dtype) {
+        case DSGNLM_F32: TAPE_CK(mterms<float>(tp, den->planes.p, st)); break;
+        case DSGNLM_F16: TAPE_CK(mterms<__half>(tp, den->planes.p, st)); break;
+        default: TAPE_CK(mterms<__nv_bfloat16>(tp, den->planes.p, st)); break;
+    }
+    // balancing passes backwards
+    int cur = 0;
+    for (int p = T - 1; p >= 0; --p) {
+        const float* dn = tp->Dh.as<float>() + (size_t)(p + 1) * n;
+        const float* dp = tp->Dh.as<float>() + (size_t)p * n;
+        const float* tpp = tp->Th.as<float>() + (size_t)p * n;
+        float* th = tp->thp.as<float>() + (size_t)p * n;
+        adj_sk_pre_kernel<<<nb, 256, 0, st>>>((int)n, tp->dh[cur].as<float>(), dn, dp, tpp, th, tp->base.as<float>());
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+        TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, th, nullptr, den->err.as<unsigned>(), nullptr, st));
+        adj_sk_finish_kernel<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, st>>>(
+            Cover{den->plan.partials, den->plan.tiles_x, den->plan.tiles_y, den->plan.splits.n, rs}, H, W, th,
+            tp->base.as<float>(), tp->dh[cur ^ 1].as<float>());
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+        cur ^= 1;
+    }
+    // pair pass B: D-hat planes and dL/dh partials
+    switch (den->dtype) {
+        case DSGNLM_F32: TAPE_CK(pairs_b<float>(tp, den->planes.p, st)); break;
+        case DSGNLM_F16: TAPE_CK(pairs_b<__half>(tp, den->planes.p, st)); break;
+        default: TAPE_CK(pairs_b<__nv_bfloat16>(tp, den->planes.p, st)); break;
+    }
+    // patch distances back to the guide
+    TAPE_CK(cudaMemsetAsync(tp->ge.p, 0, sizeof(float) * ne, st));
+    {
+        const int GH = kGTH + rs, GW = kGTW + 2 * rs, DH = kGTH + 2 * rp, DW = kGTW + 2 * rp;
+        const size_t smem = sizeof(float) * (size_t)(2 * GH * GW + DH * DW + DH * kGTW);
+        TAPE_CK(cudaFuncSetAttribute(adj_guide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((W + 2 * rp + kGTW - 1) / kGTW, (H + 2 * rp + kGTH - 1) / kGTH, (nh + kGChunk - 1) / kGChunk);
+        adj_guide_kernel<<<grid, dim3(32, 8), smem, st>>>(tp->Dhat.as<float>(), tp->guide, H, W, rp, rs,
+                                                          tp->ge.as<float>());
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+    }
+    adj_fold_kernel<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, st>>>(
+        tp->ge.as<float>(), tp->xh.as<float>(), tp->vh.as<float>(), tp->guide, H, W, rp, guide_bar);
+    count_launches(1);
+    TAPE_CK(cudaGetLastError());
+    TAPE_CK(cudaMemcpyAsync(y_bar, tp->yb.p, sizeof(float) * nlo, cudaMemcpyDeviceToDevice, st));
+    adj_sum_kernel<<<1, 256, 0, st>>>(tp->rho_part.as<double>(), nb, mh + 1);
+    adj_sum_kernel<<<1, 256, 0, st>>>(tp->h_part.as<double>(), npb, mh + 2);
+    count_launches(2);
+    TAPE_CK(cudaGetLastError());
+    double hs[3] = {0, 0, 0};
+    TAPE_CK(cudaMemcpyAsync(hs, mh, sizeof hs, cudaMemcpyDeviceToHost, st));
+    TAPE_CK(cudaStreamSynchronize(st));
+    unsigned errv = 0;
+    TAPE_CK(cudaMemcpy(&errv, den->err.p, sizeof errv, cudaMemcpyDeviceToHost));
+    if (errv) return DSGNLM_TIMEOUT;
+    if (rho_bar) *rho_bar = hs[1];
+    if (h_bar) *h_bar = hs[2];
+    return DSGNLM_OK;
+}
+
+}  // extern "C"

@@ -12,6 +12,7 @@
 
 #include "../../include/dsgnlm.h"
 #include "common.cuh"
+#include "handle.h"
 #include "internal.h"
 
 namespace dsg {
@@ -44,49 +45,6 @@ dsgnlm_status fail_cuda(cudaError_t e) {
         cudaError_t e_ = (expr);                      \
         if (e_ != cudaSuccess) return fail_cuda(e_);  \
     } while (0)
-
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    cudaError_t ensure(size_t n) {
-        if (n <= bytes && p) return cudaSuccess;
-        release();
-        if (n == 0) return cudaSuccess;
-        cudaError_t e = cudaMalloc(&p, n);
-        if (e != cudaSuccess) {
-            p = nullptr;
-            (void)cudaGetLastError();
-            return e;
-        }
-        bytes = n;
-        return cudaSuccess;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    template <typename T> T* as() const { return (T*)p; }
-};
-
-size_t weight_elem_bytes(int dtype) { return dtype == DSGNLM_F32 ? 4 : 2; }
-
-// CUDA event pairs recorded around the launches of one kernel kind while
-// profiling is enabled.
-struct ProfPool {
-    std::vector<cudaEvent_t> ev;
-    int used = 0;  // pairs recorded since the last reset
-    static constexpr int kMaxPairs = 1 << 16;
-    void release() {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        ev.clear();
-        used = 0;
-    }
-};
-
-constexpr int kProfKinds = 4;
 
 // Tensor map of the weight planes [n_h][H][pitch] for the TMA stencil path.
 cudaError_t encode_planes_map(void* out, void* planes, int dtype, int H, int W, int nh) {
@@ -142,114 +100,6 @@ TmaSplits make_splits(int rs, int n) {
 }
 
 }  // namespace
-
-struct dsgnlm {
-    cudaStream_t stream = nullptr;
-    int dtype = DSGNLM_F32;
-    int H = 0, W = 0, Wp = 0, rp = 0, rs = 0, nh = 0;
-    int num_sms = 0;
-    // TMA stencil path
-    bool fast = false;
-    TmaPlan plan{};
-    DevBuf tma_part, tbuf[2], err, bal_part;
-    float* t_final = nullptr;
-    // balancing passes as a CUDA graph with a device-driven WHILE node
-    cudaStream_t cap_stream = nullptr;
-    cudaGraph_t bal_graph = nullptr;
-    cudaGraphExec_t bal_exec = nullptr;
-    unsigned char bal_key[256] = {};
-    bool bal_graph_failed = false;
-    float bw = 0.f;
-    bool built = false, balanced = false;
-    DevBuf planes, dbuf[2], stats, ctl;
-    float* d_final = nullptr;
-    double m = 1.0;
-    float inv_m = 1.f;
-    int iters = 0;
-    double resid = 0.0;
-    // Algorithm 1 workspace
-    DevBuf z, x2, rlo, partials, arrive, hist;
-    // batched Algorithm 1 workspace (used when this handle leads a batch)
-    DevBuf b_inst, b_epi, b_work1, b_work2, b_hist;
-    // optional per-kernel timing
-    bool prof = false;
-    ProfPool pools[kProfKinds];
-    // pinned host staging for small device->host reads
-    void* host_stage = nullptr;
-    size_t host_stage_bytes = 0;
-
-    cudaError_t stage(size_t n) {
-        if (n <= host_stage_bytes) return cudaSuccess;
-        if (host_stage) cudaFreeHost(host_stage);
-        host_stage = nullptr;
-        host_stage_bytes = 0;
-        cudaError_t e = cudaMallocHost(&host_stage, n);
-        if (e != cudaSuccess) {
-            host_stage = nullptr;
-            return e;
-        }
-        host_stage_bytes = n;
-        return cudaSuccess;
-    }
-    void release_graphs() {
-        if (bal_exec) cudaGraphExecDestroy(bal_exec);
-        if (bal_graph) cudaGraphDestroy(bal_graph);
-        bal_exec = nullptr;
-        bal_graph = nullptr;
-    }
-    void release_all() {
-        release_graphs();
-        if (cap_stream) cudaStreamDestroy(cap_stream);
-        cap_stream = nullptr;
-        bal_part.release();
-        tma_part.release();
-        tbuf[0].release();
-        tbuf[1].release();
-        err.release();
-        planes.release();
-        dbuf[0].release();
-        dbuf[1].release();
-        stats.release();
-        ctl.release();
-        z.release();
-        x2.release();
-        b_inst.release();
-        b_epi.release();
-        b_work1.release();
-        b_work2.release();
-        b_hist.release();
-        rlo.release();
-        partials.release();
-        arrive.release();
-        hist.release();
-        if (host_stage) cudaFreeHost(host_stage);
-        host_stage = nullptr;
-        host_stage_bytes = 0;
-        for (ProfPool& p : pools) p.release();
-    }
-
-    // Launch through `f`, bracketed by timing events when profiling is on.
-    template <typename F>
-    cudaError_t timed(int kind, F&& f) {
-        if (!prof) return f();
-        ProfPool& P = pools[kind];
-        if (P.used >= ProfPool::kMaxPairs) return f();
-        while ((int)P.ev.size() < 2 * (P.used + 1)) {
-            cudaEvent_t e;
-            cudaError_t err = cudaEventCreate(&e);
-            if (err != cudaSuccess) return err;
-            P.ev.push_back(e);
-        }
-        cudaError_t err = cudaEventRecord(P.ev[2 * P.used], stream);
-        if (err != cudaSuccess) return err;
-        err = f();
-        if (err != cudaSuccess) return err;
-        err = cudaEventRecord(P.ev[2 * P.used + 1], stream);
-        if (err != cudaSuccess) return err;
-        ++P.used;
-        return cudaSuccess;
-    }
-};
 
 extern "C" {
 

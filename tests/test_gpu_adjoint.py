@@ -1,0 +1,78 @@
+"""Hand-written adjoint of unrolled linearized PnP-ADMM (C ABI lpnp_unrolled_forward /
+lpnp_backward) against FP64 references: torch autograd on the dense PyTorch form
+(16x16 copy) and central finite differences of the NumPy oracle.  Tolerance 1e-4
+relative (FP32 path against FP64)."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import adjoint, problems
+from tests.gpu_helpers import cuda, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(H, W, seed):
+    wl = synthetic.workload("unroll8x256")
+    inst = problems.sr_instance(wl, H=H, W=W, seed=seed)
+    guide = np.clip(inst["x_true"] + 0.05 * np.random.default_rng(seed).standard_normal((H, W)), -0.05, 1.05)
+    return wl, inst, guide.astype(np.float32)
+
+
+def _gpu(inst, guide, h, rho, params):
+    from paper_1901_06110_gb300.autograd import UnrolledSR
+    y = cuda(inst["y"]).requires_grad_(True)
+    g = cuda(guide).requires_grad_(True)
+    ht = torch.tensor(h, dtype=torch.float64, requires_grad=True)
+    rt = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
+    x = UnrolledSR.apply(y, g, ht, rt, params)
+    xt = cuda(inst["x_true"])
+    loss = ((x - xt) ** 2).mean()
+    loss.backward()
+    return loss.item(), host(y.grad), host(g.grad), ht.grad.item(), rt.grad.item(), host(x.detach())
+
+
+@pytest.mark.parametrize("H,W,rp,rs,T,N", [(16, 16, 2, 7, 4, 10), (16, 20, 1, 3, 2, 5)])
+def test_adjoint_matches_torch_autograd(gpu_lib, H, W, rp, rs, T, N):
+    from paper_1901_06110_gb300.autograd import UnrollParams
+    wl, inst, guide = _case(H, W, 9)
+    h, rho = 0.1, 1.0
+    params = UnrollParams(patch_r=rp, search_r=rs, balance_passes=T, iters=N)
+    loss, gy, gg, gh, gr, x = _gpu(inst, guide, h, rho, params)
+    y = torch.tensor(inst["y"].astype(np.float64), requires_grad=True)
+    g = torch.tensor(guide.astype(np.float64), requires_grad=True)
+    ht = torch.tensor(h, dtype=torch.float64, requires_grad=True)
+    rt = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
+    ref = adjoint.torch_unrolled_loss(y, g, ht, rt, inst["x_true"], rp, rs, T, N)
+    ref.backward()
+    assert abs(loss - ref.item()) <= 1e-5 * ref.item()
+    assert rel_l2(gy, y.grad.numpy()) <= 1e-4
+    assert rel_l2(gg, g.grad.numpy()) <= 1e-4
+    assert abs(gh - ht.grad.item()) <= 1e-4 * abs(ht.grad.item()) + 1e-9
+    assert abs(gr - rt.grad.item()) <= 1e-4 * abs(rt.grad.item()) + 1e-9
+
+
+def test_adjoint_matches_finite_differences(gpu_lib):
+    from paper_1901_06110_gb300.autograd import UnrollParams
+    H, W, rp, rs, T, N = 32, 48, 2, 5, 3, 6
+    wl, inst, guide = _case(H, W, 13)
+    h, rho = 0.1, 1.0
+    params = UnrollParams(patch_r=rp, search_r=rs, balance_passes=T, iters=N)
+    loss, gy, gg, gh, gr, x = _gpu(inst, guide, h, rho, params)
+    xt = inst["x_true"]
+    g64 = guide.astype(np.float64)
+    f = lambda yy=inst["y"], gu=g64, hh=h, rr=rho: adjoint.unrolled_loss(yy, gu, hh, rr, xt, rp, rs, T, N)
+    assert abs(loss - f()) <= 1e-5 * f()
+    for idx in [(0, 0), (7, 11), (15, 23)]:
+        fd = adjoint.fd_gradient(lambda yy: f(yy=yy), inst["y"], idx, 1e-4)
+        assert abs(fd - gy[idx]) <= 1e-4 * np.abs(gy).max()
+    for idx in [(3, 4), (16, 30), (31, 47)]:
+        if not (0.02 < guide[idx] < 0.98):
+            continue
+        fd = adjoint.fd_gradient(lambda gu: f(gu=gu), g64, idx, 1e-4)
+        assert abs(fd - gg[idx]) <= 1e-4 * np.abs(gg).max()
+    fd_h = (f(hh=h + 1e-5) - f(hh=h - 1e-5)) / 2e-5
+    assert abs(fd_h - gh) <= 2e-4 * abs(fd_h)
+    fd_r = (f(rr=rho + 1e-5) - f(rr=rho - 1e-5)) / 2e-5
+    assert abs(fd_r - gr) <= 2e-4 * abs(fd_r)

@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one stencil_p1 launch from an ncu capture of the
 # full 512x512 workload, with the hash of the kernel source it was taken on; the
 # figure is reported only while the source is unchanged.
-NCU_TRAFFIC = {"stencil_tma.cu": "c4259ce9c9f0fd03", "bytes": 236147200}
+NCU_TRAFFIC = {"stencil_tma.cu": "1c70d59ddedaa68b", "bytes": 236450560}
 
 
 def _args():
@@ -279,6 +279,93 @@ def run_batched(steps: int, warmup: int, flush, only=None):
     return out
 
 
+# ----------------------------------------------------------------------------- differentiable form
+
+def run_unrolled(steps: int, warmup: int, flush):
+    """Forward + backward of the differentiable form: 10 unrolled iterations of 2x
+    super-resolution on 8 images of 256x256 (patch 5x5, search 15x15, 4 balancing
+    passes), MSE loss to the ground truth, gradients w.r.t. the observation, the
+    guide, h and rho from the hand-written adjoint."""
+    import torch
+
+    import synthetic
+    from paper_1901_06110_gb300 import dsgnlm as D
+    from paper_1901_06110_gb300.autograd import UnrollParams, unrolled_sr
+
+    wl = synthetic.workload("unroll8x256")
+    B, H, W = wl["count"], wl["H"], wl["W"]
+    ys, xts = [], []
+    for b in range(B):
+        seed = wl["seed"] + b
+        xt = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], seed)).cuda()
+        nz = torch.from_numpy(synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], seed)).cuda()
+        ys.append(D.lpnp_sr_observe(xt, nz, wl["blur_sigma"], wl["blur_r"]))
+        xts.append(xt)
+    y0 = torch.stack(ys)
+    xt = torch.stack(xts)
+    g0 = torch.stack([D.lpnp_sr_guide(yy) for yy in ys])
+    params = UnrollParams(patch_r=wl["patch_r"], search_r=wl["search_r"], balance_passes=4, iters=wl["iters"])
+    fwd = bwd = 0.0
+    for k in range(warmup + steps):
+        flush.fill_(float(k))
+        y = y0.clone().requires_grad_(True)
+        g = g0.clone().requires_grad_(True)
+        h = torch.tensor(wl["h"], dtype=torch.float64, requires_grad=True)
+        rho = torch.tensor(wl["rho"], dtype=torch.float64, requires_grad=True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        x = unrolled_sr(y, g, h, rho, params)
+        loss = ((x - xt) ** 2).mean()
+        e[1].record()
+        loss.backward()
+        e[2].record()
+        e[2].synchronize()
+        if k >= warmup:
+            fwd += e[0].elapsed_time(e[1])
+            bwd += e[1].elapsed_time(e[2])
+    return {"workload": f"unroll8x256: {B} x {H}x{W} 2x SR, patch 5x5, search 15x15, 4 balancing passes, "
+                        f"{wl['iters']} unrolled iterations, MSE loss; grads w.r.t. y, guide, h, rho",
+            "steps": steps, "forward_ms": fwd / steps, "backward_ms": bwd / steps,
+            "fwd_bwd_ms": (fwd + bwd) / steps, "fwd_bwd_mpix_s": B * H * W / 1e6 / ((fwd + bwd) / steps / 1e3)}
+
+
+def run_spi(steps: int, warmup: int, flush):
+    """Single-photon imaging, 512x512 from 4x4 binary sub-pixels (eta 4), DSG-NLM
+    7x7 / 21x21, h 0.1, balance to 1e-6, 50 iterations with the box constraint."""
+    import torch
+
+    import synthetic
+    from paper_1901_06110_gb300 import dsgnlm as D
+    from paper_1901_06110_gb300 import pipeline
+
+    wl = synthetic.workload("spi512")
+    H, W = wl["H"], wl["W"]
+    xt = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], wl["seed"])).cuda()
+    arr = torch.from_numpy(synthetic.photon_arrivals((wl["K_side"] * H, wl["K_side"] * W), wl["seed"])).cuda()
+    bits = D.lpnp_spi_observe(xt, arr, wl["K_side"], wl["eta"])
+    counts = D.lpnp_spi_counts(bits, wl["K_side"])
+    solver = pipeline.Solver(H, W, pipeline.Params.from_workload(wl), kind="spi")
+    for _ in range(warmup):
+        solver.run(counts)
+    t = 0.0
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        solver.run(counts)
+        e1.record()
+        e1.synchronize()
+        t += e0.elapsed_time(e1)
+    ms = t / steps
+    psnr = float(10 * torch.log10(1.0 / ((solver.x - xt) ** 2).double().mean()))
+    solver.close()
+    return {"workload": f"spi512: {H}x{W} from 4x4 binary sub-pixels, eta {wl['eta']}, patch 7x7, search 21x21, "
+                        f"h {wl['h']}, tol {wl['tol']}, {wl['iters']} iterations, alpha {wl['alpha']}",
+            "steps": steps, "ms_per_step": ms, "mpix_s": H * W / 1e6 / (ms / 1e3),
+            "pnp_iters_per_s": wl["iters"] / (ms / 1e3), "psnr_db": psnr}
+
+
 # ----------------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -416,6 +503,8 @@ def run_ours(args):
     }
     if not args.no_batched:
         line["batched"] = run_batched(args.batched_steps, 1, flush)
+        line["unrolled"] = run_unrolled(args.batched_steps, 1, flush)
+        line["spi"] = run_spi(max(5, args.batched_steps), 2, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         side = 192
         secs = _oracle_solve_seconds(side, wl)

@@ -588,8 +588,8 @@ dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y
         float* dn = p < T ? tp->Dh.as<float>() + (size_t)(p + 1) * n : tp->scratch.as<float>();
         TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, search_r, dp, nullptr, den->err.as<unsigned>(),
                                   &ctl->done, st));
-        TAPE_CK(launch_balance_combine(den->plan, H, W, search_r, dp, dn, tp->Th.as<float>() + (size_t)p * n,
-                                       tp->part.as<float2>(), ctl, st));
+        TAPE_CK(launch_balance_epilogue(den->plan, H, W, search_r, dp, dn, tp->Th.as<float>() + (size_t)p * n,
+                                        tp->part.as<float2>(), ctl, 0, cudaGraphConditionalHandle{}, 0, st));
     }
     const float* dT = tp->Dh.as<float>() + (size_t)T * n;
     const float* tT = tp->Th.as<float>() + (size_t)T * n;

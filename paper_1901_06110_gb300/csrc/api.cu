@@ -185,8 +185,9 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
 
 namespace {
 
-// One balancing pass of the TMA path: phase-1 gather of K1 d, combine (next d, t and
-// per-block residual maxima), decision.  `parity` selects the d and t buffers.
+// One balancing pass of the TMA path: phase-1 gather of K1 d, then the epilogue
+// (next d, t, residual maxima and, in its last block, the decision).  `parity`
+// selects the d and t buffers.
 cudaError_t balance_pass(dsgnlm* h, int parity, cudaStream_t st, cudaGraphConditionalHandle cond, int use_cond) {
     BalanceCtl* ctl = h->ctl.as<BalanceCtl>();
     float* d_in = h->dbuf[parity].as<float>();
@@ -194,11 +195,8 @@ cudaError_t balance_pass(dsgnlm* h, int parity, cudaStream_t st, cudaGraphCondit
     cudaError_t e = launch_tma_gather(h->dtype, h->plan, h->H, h->W, h->rs, d_in, nullptr, h->err.as<unsigned>(),
                                       &ctl->done, st);
     if (e != cudaSuccess) return e;
-    e = launch_balance_combine(h->plan, h->H, h->W, h->rs, d_in, d_out, h->tbuf[parity].as<float>(),
-                               h->bal_part.as<float2>(), ctl, st);
-    if (e != cudaSuccess) return e;
-    return launch_balance_decide(h->bal_part.as<float2>(), balance_combine_blocks(h->H, h->W), ctl, cond, use_cond,
-                                 st);
+    return launch_balance_epilogue(h->plan, h->H, h->W, h->rs, d_in, d_out, h->tbuf[parity].as<float>(),
+                                   h->bal_part.as<float2>(), ctl, 1, cond, use_cond, st);
 }
 
 // Everything a recorded balance graph depends on.
@@ -305,8 +303,8 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
             DSG_CK(cudaMemcpyAsync(h->host_stage, h->ctl.p, sizeof c, cudaMemcpyDeviceToHost, h->stream));
             DSG_CK(cudaStreamSynchronize(h->stream));
             std::memcpy(&c, h->host_stage, sizeof c);
-            // each WHILE iteration runs two passes of three kernels
-            if (c.done) count_launches(6 * (uint64_t)((c.final_pass + 2) / 2));
+            // each WHILE iteration runs two passes of two kernels
+            if (c.done) count_launches(4 * (uint64_t)((c.final_pass + 2) / 2));
             ran = true;
         } else {
             h->bal_graph_failed = true;  // conditional graphs unavailable: launch passes from the host
@@ -513,8 +511,10 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
     const float mu = (float)(1.0 / ((double)p->alpha + (double)rho));
     const BlurTaps taps = make_blur_taps(p->blur_sigma > 0.f ? p->blur_sigma : 1.f,
                                          p->kind == LPNP_SR2 ? p->blur_r : 0);
-    // For super-resolution x alternates between the caller's buffer (A) and the
-    // handle's copy (B): the update of iteration k writes B for even k, A for odd k.
+    // Super-resolution reads x in halos, so the first update goes from the caller's
+    // buffer (A) to the handle's copy (B).  The generic path keeps alternating (the
+    // update of iteration k writes B for even k, A for odd k); the TMA path, whose
+    // later updates read x at their own pixel only, updates A in place from then on.
     float* xA = p->x;
     float* xB = p->kind == LPNP_SR2 ? h->x2.as<float>() : p->x;
     auto xupdate0 = [&]() -> cudaError_t {
@@ -524,10 +524,17 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
         return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
                                   h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
     };
+    const bool sr = p->kind == LPNP_SR2;
     if (h->fast) {
-        // iteration k: phase-1 gather of W z, then one pass that finishes v and u of
-        // iteration k and performs the x-update of iteration k + 1
+        // Iteration k: phase-1 gather of W z, then one per-pixel pass that finishes v
+        // and u of iteration k and performs the x-update of iteration k + 1.  For SR
+        // that update needs A^T(A x - y) at the current x, which depends on x alone:
+        // it is computed on the side stream while phase 1 streams the weights.
         DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, xupdate0));
+        if (sr && iters > 1) {
+            DSG_CK(h->ensure_side());
+            DSG_CK(h->gbuf.ensure(n * sizeof(float)));
+        }
         EpilogueArgs ea{};
         ea.H = H;
         ea.W = W;
@@ -538,6 +545,7 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
         ea.v = p->v;
         ea.u = p->u;
         ea.y = p->y;
+        ea.g = h->gbuf.as<float>();
         ea.taps = taps;
         ea.counts = p->counts;
         ea.K = p->K;
@@ -547,19 +555,31 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
         ea.alpha = p->alpha;
         ea.rho = rho;
         ea.constraint = p->constraint;
-        const int kind = p->kind == LPNP_SR2 ? 0 : 1;
+        const int kind = sr ? 0 : 1;
         for (int it = 0; it < iters; ++it) {
+            const bool do_x = it < iters - 1;
+            // SR: the first update wrote xB; every later one updates xA in place
+            float* xcur = (sr && it == 0) ? xB : xA;
+            if (sr && do_x) DSG_CK(cudaEventRecord(h->ev_fork, h->stream));
             DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
                 return launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
                                          h->err.as<unsigned>(), nullptr, h->stream);
             }));
-            ea.do_x = it < iters - 1;
-            ea.x_in = (it & 1) ? xA : xB;
-            ea.x_out = (it & 1) ? xB : xA;
+            if (sr && do_x) {
+                DSG_CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+                DSG_CK(launch_sr_grad_tile(xcur, p->y, H, W, taps, h->gbuf.as<float>(), h->side));
+                DSG_CK(cudaEventRecord(h->ev_join, h->side));
+                DSG_CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+            }
+            ea.do_x = do_x;
+            ea.x_in = xcur;
+            ea.x_out = xA;
             ea.partials = h->partials.as<double>() + 2 * (size_t)nblocks * it;
-            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_combine_xupdate(kind, h->plan, h->rs, ea, h->stream); }));
+            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_combine_update(kind, h->plan, h->rs, ea, h->stream); }));
         }
         DSG_CK(launch_reduce_residuals(red, iters, nblocks, h->stream));
+        if (sr && iters == 1)
+            DSG_CK(cudaMemcpyAsync(p->x, h->x2.p, n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     } else {
         for (int it = 0; it < iters; ++it) {
             DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
@@ -578,7 +598,7 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
             }));
         }
     }
-    if (p->kind == LPNP_SR2 && (iters & 1))
+    if (!h->fast && sr && (iters & 1))
         DSG_CK(cudaMemcpyAsync(p->x, h->x2.p, n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     if (p->resid_hist) {
         DSG_CK(h->stage(sizeof(double) * 2 * (size_t)iters));

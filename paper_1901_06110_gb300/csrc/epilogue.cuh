@@ -19,7 +19,7 @@ struct TileCover {
     size_t region, slice_stride;
     int RW, rs, slices;
     bool up_ok, left_ok, right_ok;
-    long long up_d, left_d, right_d;  // region offsets (in floats) of the neighbours
+    int up_d, left_d, right_d;  // region offsets (in floats) of the neighbours
 };
 
 __device__ __forceinline__ TileCover tile_cover(const Cover& cv, int y0, int x0) {
@@ -34,9 +34,9 @@ __device__ __forceinline__ TileCover tile_cover(const Cover& cv, int y0, int x0)
     c.up_ok = ty > 0;
     c.left_ok = tx > 0;
     c.right_ok = tx + 1 < cv.tiles_x;
-    c.up_d = -(long long)cv.tiles_x * (long long)c.region;
-    c.left_d = -(long long)c.region;
-    c.right_d = (long long)c.region;
+    c.up_d = -cv.tiles_x * (int)c.region;
+    c.left_d = -(int)c.region;
+    c.right_d = (int)c.region;
     return c;
 }
 
@@ -45,10 +45,11 @@ __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj)
     const bool up = c.up_ok && li < rs;
     const bool left = c.left_ok && lj < rs;
     const bool right = c.right_ok && lj >= kTmaTW - rs;
-    const size_t own_cell = (size_t)li * RW + lj + rs;
-    const size_t up_cell = (size_t)(li + kTmaTH) * RW + lj + rs;
+    const int own_cell = li * RW + lj + rs;
+    const int up_cell = (li + kTmaTH) * RW + lj + rs;
     float acc = 0.f;
     const float* base = c.own;
+#pragma unroll 2
     for (int sl = 0; sl < c.slices; ++sl, base += c.slice_stride) {
         acc += __ldcg(base + own_cell);
         if (up) acc += __ldcg(base + c.up_d + up_cell);
@@ -62,6 +63,36 @@ __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj)
         }
     }
     return acc;
+}
+
+// The same sum with TwoSum compensation, in the fixed order of gather_partials
+// (per slice: upper left, up, upper right, left, own, right); a region that does
+// not cover the pixel contributes an exact zero, which leaves the sum unchanged.
+__device__ __forceinline__ float tile_gather_comp(const TileCover& c, int li, int lj) {
+    const int rs = c.rs, RW = c.RW;
+    const bool up = c.up_ok && li < rs;
+    const bool left = c.left_ok && lj < rs;
+    const bool right = c.right_ok && lj >= kTmaTW - rs;
+    const int own_cell = li * RW + lj + rs;
+    const int up_cell = (li + kTmaTH) * RW + lj + rs;
+    CompSum acc;
+    const float* base = c.own;
+#pragma unroll 2
+    for (int sl = 0; sl < c.slices; ++sl, base += c.slice_stride) {
+        const float v0 = (up && left) ? __ldcg(base + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
+        const float v1 = up ? __ldcg(base + c.up_d + up_cell) : 0.f;
+        const float v2 = (up && right) ? __ldcg(base + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
+        const float v3 = left ? __ldcg(base + c.left_d + own_cell + kTmaTW) : 0.f;
+        const float v4 = __ldcg(base + own_cell);
+        const float v5 = right ? __ldcg(base + c.right_d + own_cell - kTmaTW) : 0.f;
+        acc.add(v0);
+        acc.add(v1);
+        acc.add(v2);
+        acc.add(v3);
+        acc.add(v4);
+        acc.add(v5);
+    }
+    return acc.value();
 }
 
 // Finish v and u of one iteration on the kXH x kXW tile at (y0, x0), perform the
@@ -126,6 +157,84 @@ __device__ __forceinline__ void combine_xupdate_body(SrTile& tile, const Cover& 
                 g = spi_hprime(xv, k1[r], a.K, a.eta, a.eps);
             }
             const float xn = project(a.mu * (a.alpha * xv + a.rho * (vn - un) - g), a.constraint);
+            a.x_out[q] = xn;
+            a.z[q] = xn + un;
+        }
+    }
+    sp = warp_sum_f(sp);
+    sd = warp_sum_f(sd);
+    __shared__ float s0[8], s1[8];
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    if ((t & 31) == 0) {
+        s0[t >> 5] = sp;
+        s1[t >> 5] = sd;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double pa = 0.0, pb = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            pa += (double)s0[w];
+            pb += (double)s1[w];
+        }
+        partials[0] = pa;
+        partials[1] = pb;
+    }
+}
+
+// Finish v and u of one iteration on the kXH x kXW tile at (y0, x0) and, when
+// a.do_x, perform the next x-update there from the gradient at each pixel alone:
+// SR reads g = A^T(A x - y) computed beforehand (a.g), SPI evaluates h' in place.
+// x_in and x_out may be the same buffer.  Stores the tile's residual sums at
+// `partials` (two doubles).  All threads of a (32, 8) block must call it.
+template <int KIND>  // 0 super-resolution, 1 single-photon
+__device__ __forceinline__ void combine_update_body(const Cover& cv, const EpilogueArgs& a, int y0, int x0,
+                                                    double* partials) {
+    const int H = a.H, W = a.W;
+    const TileCover tc = tile_cover(cv, y0, x0);
+    const int pj = x0 + threadIdx.x;
+    const int lj = pj - (x0 / kTmaTW) * kTmaTW;
+    float A[2], zs[2], ds[2], ts[2], vo[2], uo[2], xs[2], gs[2];
+    int k1[2];
+    // per-pixel loads first, then the partial sums (whose slice loop the compiler
+    // does not hoist loads across)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int pi = y0 + threadIdx.y + 8 * r;
+        const bool ok = pi < H && pj < W;
+        const size_t q = (size_t)pi * W + pj;
+        zs[r] = ok ? a.z[q] : 0.f;
+        ds[r] = ok ? a.d[q] : 0.f;
+        ts[r] = ok ? a.t[q] : 0.f;
+        vo[r] = ok ? a.v[q] : 0.f;
+        uo[r] = ok ? a.u[q] : 0.f;
+        xs[r] = (ok && a.do_x) ? a.x_in[q] : 0.f;
+        gs[r] = (ok && KIND == 0 && a.do_x) ? a.g[q] : 0.f;
+        k1[r] = (ok && KIND == 1 && a.do_x) ? (int)a.counts[q] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int py = threadIdx.y + 8 * r;
+        A[r] = (y0 + py < H && pj < W) ? tile_gather(tc, py, lj) : 0.f;
+    }
+    float sp = 0.f, sd = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int pi = y0 + threadIdx.y + 8 * r;
+        if (pi >= H || pj >= W) continue;
+        const size_t q = (size_t)pi * W + pj;
+        // v = W z with z = x + u: c_s z_s + (d_s / m) sum_{r != s} K1 d_r z_r
+        const float dm = ds[r] * a.inv_m;
+        const float cs = 1.f - dm * (ts[r] - ds[r]);
+        const float vn = fmaf(dm, A[r], cs * zs[r]);
+        const float un = zs[r] - vn;  // u + x - v
+        a.v[q] = vn;
+        a.u[q] = un;
+        const float dp = un - uo[r], dd = vn - vo[r];  // x - v and v - v_prev
+        sp = fmaf(dp, dp, sp);
+        sd = fmaf(dd, dd, sd);
+        if (a.do_x) {
+            const float g = KIND == 0 ? gs[r] : spi_hprime(xs[r], k1[r], a.K, a.eta, a.eps);
+            const float xn = project(a.mu * (a.alpha * xs[r] + a.rho * (vn - un) - g), a.constraint);
             a.x_out[q] = xn;
             a.z[q] = xn + un;
         }

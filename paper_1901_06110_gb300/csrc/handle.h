@@ -86,7 +86,11 @@ struct dsgnlm {
     int iters = 0;
     double resid = 0.0;
     // Algorithm 1 workspace
-    DevBuf z, x2, rlo, partials, arrive, hist;
+    DevBuf z, x2, rlo, partials, arrive, hist, gbuf;
+    // side stream of the solve: the SR gradient of an iteration runs there while the
+    // main stream streams the weights (fork and join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // batched Algorithm 1 workspace (used when this handle leads a batch)
     DevBuf b_inst, b_epi, b_work1, b_work2, b_hist;
     // optional per-kernel timing
@@ -109,6 +113,13 @@ struct dsgnlm {
         host_stage_bytes = n;
         return cudaSuccess;
     }
+    cudaError_t ensure_side() {
+        cudaError_t e = cudaSuccess;
+        if (!side) e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !ev_fork) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess && !ev_join) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+        return e;
+    }
     void release_graphs() {
         if (bal_exec) cudaGraphExecDestroy(bal_exec);
         if (bal_graph) cudaGraphDestroy(bal_graph);
@@ -119,6 +130,12 @@ struct dsgnlm {
         release_graphs();
         if (cap_stream) cudaStreamDestroy(cap_stream);
         cap_stream = nullptr;
+        if (side) cudaStreamDestroy(side);
+        side = nullptr;
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        ev_fork = ev_join = nullptr;
+        gbuf.release();
         bal_part.release();
         tma_part.release();
         tbuf[0].release();

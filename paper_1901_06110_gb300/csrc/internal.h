@@ -29,6 +29,7 @@ struct BalanceCtl {
     int pass;        // current pass (TMA path: advanced on the device)
     double eps;      // TMA path: residual of the last decided pass
     double m;        // TMA path: max row sum of the last decided pass
+    unsigned arrive;  // TMA path: blocks of the current pass's epilogue that have finished
 };
 
 // Solve-loop reduction state: per-block partial sums of every iteration (reduced
@@ -130,6 +131,9 @@ cudaError_t launch_sr_xupdate_fused(const float* x_in, float* x_out, const float
 // grad f for SPI
 cudaError_t launch_spi_grad(const float* x, const uint8_t* counts, int n, int K, float eta,
                             float eps, float* grad, cudaStream_t st);
+// g = A^T (A x - y) by staged tiles (one launch)
+cudaError_t launch_sr_grad_tile(const float* x, const float* y, int H, int W, BlurTaps taps, float* g,
+                                cudaStream_t st);
 cudaError_t launch_spi_xupdate(const uint8_t* counts, int n, int K, float eta, float eps, float* x,
                                const float* v, const float* u, float* z, float mu, float alpha,
                                float rho, int constraint, cudaStream_t st);
@@ -144,12 +148,13 @@ cudaError_t launch_spi_guide(const uint8_t* counts, int H, int W, int K, float e
 cudaError_t launch_init(const float* guide, int n, float* x, float* v, float* u, cudaStream_t st);
 
 // Epilogues (epilogue.cu)
-int balance_combine_blocks(int H, int W);
-cudaError_t launch_balance_combine(const TmaPlan& plan, int H, int W, int rs, const float* d_in,
-                                   float* d_out, float* t_out, float2* part, const BalanceCtl* ctl,
-                                   cudaStream_t st);
-cudaError_t launch_balance_decide(const float2* part, int nblocks, BalanceCtl* ctl,
-                                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+int balance_combine_blocks(int H, int W);  // blocks (and residual pairs) of one balance epilogue
+// One balancing pass's epilogue (t, next d, residual pairs); with `decide` the
+// last block applies the stopping rule and, with use_cond, sets the graph's WHILE
+// condition.
+cudaError_t launch_balance_epilogue(const TmaPlan& plan, int H, int W, int rs, const float* d_in, float* d_out,
+                                    float* t_out, float2* part, BalanceCtl* ctl, int decide,
+                                    cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 
 struct EpilogueArgs {
     int H, W;
@@ -159,9 +164,10 @@ struct EpilogueArgs {
     float* z;          // in: x + u of this iteration; out: x + u of the next one
     float* v;
     float* u;
-    const float* x_in;   // x of the next update (SR: read in halos)
-    float* x_out;        // its result (SR: another buffer; SPI: may equal x_in)
+    const float* x_in;   // x of the next update (SR, fused form: read in halos)
+    float* x_out;        // its result (SR, fused form: another buffer; otherwise may equal x_in)
     const float* y;      // SR observation
+    const float* g;      // SR, per-pixel form: A^T (A x_in - y), computed beforehand
     BlurTaps taps;
     const uint8_t* counts;  // SPI
     int K;
@@ -171,9 +177,11 @@ struct EpilogueArgs {
     int do_x;            // 0 on the last iteration
     double* partials;    // this iteration's per-block residual sums [nblocks][2]
 };
-int combine_xupdate_blocks(int H, int W);
-cudaError_t launch_combine_xupdate(int kind, const TmaPlan& plan, int rs, const EpilogueArgs& args,
-                                   cudaStream_t st);
+int combine_xupdate_blocks(int H, int W);  // epilogue tiles (kXH x kXW) of an image
+// Finish v, u of one iteration and perform the next x-update, per pixel (SR takes
+// the gradient from args.g); one residual pair per epilogue tile.
+cudaError_t launch_combine_update(int kind, const TmaPlan& plan, int rs, const EpilogueArgs& args,
+                                  cudaStream_t st);
 
 // Batched Algorithm 1 (batched.cu).  a.x_in / a.x_out hold the two x buffers of the
 // image (the caller's and the handle's); the kernels alternate them per iteration.

@@ -84,12 +84,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     return true;
 }
 
+// L2 policy of the weight stream: each weight is read once per pass, so its lines
+// are evicted first and the per-pixel arrays of the iteration stay in L2.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                            int z) {
+                                            int z, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
 }
 
@@ -145,6 +153,7 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
         // producer: one elected thread streams the plane tiles in consumption order;
         // the first kStages loads overlap the consumers' staging of q below
         if (tid == kConsumers) {
+            const uint64_t policy = evict_first_policy();
             int q = 0;
             bool ok = true;
             for (int ox = oxa; ox <= oxb && ok; ++ox) {
@@ -159,7 +168,8 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
                         break;
                     }
                     mbar_arrive_expect_tx(&full[s], kStageElems * sizeof(WT));
-                    tma_load_3d(stages + s * kStageElems, tmap, &full[s], x0, y0, plane_index(oy, ox, RS));
+                    tma_load_3d(stages + s * kStageElems, tmap, &full[s], x0, y0, plane_index(oy, ox, RS),
+                                policy);
                 }
             }
             if (!ok) {

@@ -505,35 +505,37 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
     DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nblocks * (h->fast ? (size_t)iters : 1)));
     DSG_CK(h->arrive.ensure(sizeof(unsigned) * (size_t)iters));
     DSG_CK(h->hist.ensure(sizeof(double) * 2 * (size_t)iters));
-    if (p->kind == LPNP_SR2) DSG_CK(h->x2.ensure(n * sizeof(float)));
     DSG_CK(cudaMemsetAsync(h->arrive.p, 0, sizeof(unsigned) * (size_t)iters, h->stream));
     SolveRed red{h->partials.as<double>(), h->arrive.as<unsigned>(), h->hist.as<double>()};
     const float mu = (float)(1.0 / ((double)p->alpha + (double)rho));
     const BlurTaps taps = make_blur_taps(p->blur_sigma > 0.f ? p->blur_sigma : 1.f,
                                          p->kind == LPNP_SR2 ? p->blur_r : 0);
-    // Super-resolution reads x in halos, so the first update goes from the caller's
-    // buffer (A) to the handle's copy (B).  The generic path keeps alternating (the
-    // update of iteration k writes B for even k, A for odd k); the TMA path, whose
-    // later updates read x at their own pixel only, updates A in place from then on.
+    // Generic path: the super-resolution update reads x in halos, so x alternates
+    // between the caller's buffer (A) and the handle's copy (B), the update of
+    // iteration k writing B for even k and A for odd k.  TMA path: the gradient is
+    // formed first, so every update works on A in place.
     float* xA = p->x;
     float* xB = p->kind == LPNP_SR2 ? h->x2.as<float>() : p->x;
-    auto xupdate0 = [&]() -> cudaError_t {
-        if (p->kind == LPNP_SR2)
-            return launch_sr_xupdate_fused(xA, xB, p->y, H, W, taps, p->v, p->u, h->z.as<float>(), mu, p->alpha,
-                                           rho, p->constraint, h->stream);
-        return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
-                                  h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
-    };
     const bool sr = p->kind == LPNP_SR2;
     if (h->fast) {
         // Iteration k: phase-1 gather of W z, then one per-pixel pass that finishes v
         // and u of iteration k and performs the x-update of iteration k + 1.  For SR
         // that update needs A^T(A x - y) at the current x, which depends on x alone:
         // it is computed on the side stream while phase 1 streams the weights.
-        DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, xupdate0));
-        if (sr && iters > 1) {
-            DSG_CK(h->ensure_side());
+        if (sr) {
             DSG_CK(h->gbuf.ensure(n * sizeof(float)));
+            if (iters > 1) DSG_CK(h->ensure_side());
+            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
+                cudaError_t e = launch_sr_grad(xA, p->y, H, W, taps, h->gbuf.as<float>(), h->stream);
+                if (e != cudaSuccess) return e;
+                return launch_xupdate_point(xA, h->gbuf.as<float>(), p->v, p->u, h->z.as<float>(), (int)n, mu,
+                                            p->alpha, rho, p->constraint, h->stream);
+            }));
+        } else {
+            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
+                return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
+                                          h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
+            }));
         }
         EpilogueArgs ea{};
         ea.H = H;
@@ -558,8 +560,6 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
         const int kind = sr ? 0 : 1;
         for (int it = 0; it < iters; ++it) {
             const bool do_x = it < iters - 1;
-            // SR: the first update wrote xB; every later one updates xA in place
-            float* xcur = (sr && it == 0) ? xB : xA;
             if (sr && do_x) DSG_CK(cudaEventRecord(h->ev_fork, h->stream));
             DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
                 return launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
@@ -567,20 +567,20 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
             }));
             if (sr && do_x) {
                 DSG_CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-                DSG_CK(launch_sr_grad_tile(xcur, p->y, H, W, taps, h->gbuf.as<float>(), h->side));
+                DSG_CK(launch_sr_grad(xA, p->y, H, W, taps, h->gbuf.as<float>(), h->side));
                 DSG_CK(cudaEventRecord(h->ev_join, h->side));
                 DSG_CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
             }
             ea.do_x = do_x;
-            ea.x_in = xcur;
+            ea.x_in = xA;
             ea.x_out = xA;
             ea.partials = h->partials.as<double>() + 2 * (size_t)nblocks * it;
             DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_combine_update(kind, h->plan, h->rs, ea, h->stream); }));
         }
         DSG_CK(launch_reduce_residuals(red, iters, nblocks, h->stream));
-        if (sr && iters == 1)
-            DSG_CK(cudaMemcpyAsync(p->x, h->x2.p, n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     } else {
+        if (sr) DSG_CK(h->x2.ensure(n * sizeof(float)));
+        xB = sr ? h->x2.as<float>() : p->x;
         for (int it = 0; it < iters; ++it) {
             DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
                 if (p->kind == LPNP_SR2) {

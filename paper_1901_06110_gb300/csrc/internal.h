@@ -131,9 +131,12 @@ cudaError_t launch_sr_xupdate_fused(const float* x_in, float* x_out, const float
 // grad f for SPI
 cudaError_t launch_spi_grad(const float* x, const uint8_t* counts, int n, int K, float eta,
                             float eps, float* grad, cudaStream_t st);
-// g = A^T (A x - y) by staged tiles (one launch)
-cudaError_t launch_sr_grad_tile(const float* x, const float* y, int H, int W, BlurTaps taps, float* g,
-                                cudaStream_t st);
+// g = A^T (A x - y) in one launch (H, W even, taps.r <= 8)
+cudaError_t launch_sr_grad(const float* x, const float* y, int H, int W, BlurTaps taps, float* g,
+                           cudaStream_t st);
+// x <- Pi_C(mu (alpha x + rho (v - u) - g)), z = x + u, per pixel (x in place)
+cudaError_t launch_xupdate_point(float* x, const float* g, const float* v, const float* u, float* z, int n, float mu,
+                                 float alpha, float rho, int constraint, cudaStream_t st);
 cudaError_t launch_spi_xupdate(const uint8_t* counts, int n, int K, float eta, float eps, float* x,
                                const float* v, const float* u, float* z, float mu, float alpha,
                                float rho, int constraint, cudaStream_t st);

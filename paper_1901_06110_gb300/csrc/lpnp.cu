@@ -107,13 +107,6 @@ sr_xupdate_fused_kernel(const float* __restrict__ x_in, float* __restrict__ x_ou
                     blockIdx.x * kXW);
 }
 
-__global__ void __launch_bounds__(256)
-sr_grad_tile_kernel(const float* __restrict__ x, const float* __restrict__ y, int H, int W, BlurTaps taps,
-                    float* __restrict__ g) {
-    __shared__ SrTile tile;
-    sr_grad_body(tile, x, y, H, W, taps, g, blockIdx.y * kXH, blockIdx.x * kXW);
-}
-
 __global__ void spi_grad_kernel(const float* __restrict__ x, const uint8_t* __restrict__ counts, int n,
                                 int K, float eta, float eps, float* __restrict__ grad) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,15 +247,6 @@ cudaError_t launch_sr_xupdate_fused(const float* x_in, float* x_out, const float
     dim3 grid((W + kXW - 1) / kXW, (H + kXH - 1) / kXH);
     sr_xupdate_fused_kernel<<<grid, dim3(32, 8), 0, st>>>(x_in, x_out, y, H, W, taps, v, u, z, mu, alpha, rho,
                                                           constraint);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sr_grad_tile(const float* x, const float* y, int H, int W, BlurTaps taps, float* g,
-                                cudaStream_t st) {
-    if (taps.r > kMaxBlurR) return cudaErrorInvalidValue;
-    dim3 grid((W + kXW - 1) / kXW, (H + kXH - 1) / kXH);
-    sr_grad_tile_kernel<<<grid, dim3(32, 8), 0, st>>>(x, y, H, W, taps, g);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -173,24 +173,6 @@ __device__ __forceinline__ float sr_tile_x(const SrTile& T, int pi, int pj) {
     return T.X[(pi - (2 * T.qy_lo - T.G)) * kSW + (pj - (2 * T.qx_lo - T.G))];
 }
 
-// g = A^T (A x - y) on the kXH x kXW tile at (y0, x0) (the gradient of the SR data
-// term, Sec. 2).  All threads of a (32, 8) block must call it.
-__device__ __forceinline__ void sr_grad_body(SrTile& tile, const float* __restrict__ x, const float* __restrict__ y,
-                                             int H, int W, const BlurTaps& taps, float* __restrict__ g, int y0,
-                                             int x0) {
-    sr_tile_index(tile, H, W, taps, y0, x0);
-    SrTileRegs rg;
-    sr_tile_load(tile, x, y, W, rg);
-    sr_tile_compute(tile, rg, taps.r);
-    const int pj = x0 + threadIdx.x;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int py = threadIdx.y + 8 * r;
-        const int pi = y0 + py;
-        if (pi < H && pj < W) g[(size_t)pi * W + pj] = sr_tile_grad(tile, taps.r, py, pj);
-    }
-}
-
 // Linearized x-update (Algorithm 1, first two steps) for super-resolution on the
 // kXH x kXW tile at (y0, x0): x_out = Pi_C(mu (alpha x_in + rho (v - u) - A^T(A x_in - y))),
 // z = x_out + u.  All threads of a (32, 8) block must call it.

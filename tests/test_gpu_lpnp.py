@@ -90,7 +90,7 @@ def _gpu_sr_solve(wl, y, iters, tol, maxit=10000, dtype="f32"):
     return dict(x=host(x), v=host(v), u=host(u), hist=hist, balance=st, guide=host(guide))
 
 
-@pytest.mark.parametrize("H,W,rs", [(64, 64, 5), (46, 70, 4)])
+@pytest.mark.parametrize("H,W,rs", [(64, 64, 5), (46, 70, 4), (36, 98, 3), (10, 12, 2)])
 def test_sr_solve_matches_oracle(gpu_lib, H, W, rs):
     wl = synthetic.workload("sr64")
     wl["search_r"] = rs

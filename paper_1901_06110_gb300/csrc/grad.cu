@@ -51,9 +51,24 @@ sr_grad_kernel(const float* __restrict__ x, const float* __restrict__ y, int H, 
         lcols[l] = wrap_index(qx_lo + l, w);
     }
     __syncthreads();
-    for (int i = tid; i < S * S; i += 256) {
-        const int a = i / S, b = i - a * S;
-        X[a][b] = __ldg(x + (size_t)rows[a] * W + cols[b]);
+    // every load of this thread is issued before the first store to shared memory
+    constexpr int kLoads = (S * S + 255) / 256;
+    float xv[kLoads];
+#pragma unroll
+    for (int k = 0; k < kLoads; ++k) {
+        const int i = tid + 256 * k;
+        if (i < S * S) {
+            const int a = i / S, b = i - a * S;
+            xv[k] = __ldg(x + (size_t)rows[a] * W + cols[b]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kLoads; ++k) {
+        const int i = tid + 256 * k;
+        if (i < S * S) {
+            const int a = i / S, b = i - a * S;
+            X[a][b] = xv[k];
+        }
     }
     __syncthreads();
     // row blur at the even columns: Hs[a][c] = sum_b t_b x(staged row a, 2 (qx_lo + c) - b)
@@ -68,10 +83,11 @@ sr_grad_kernel(const float* __restrict__ x, const float* __restrict__ y, int H, 
     // column blur at the even rows minus the observation: r = A x - y
     for (int i = tid; i < L * L; i += 256) {
         const int l = i / L, c = i - l * L;
+        const float yv = __ldg(y + (size_t)lrows[l] * w + lcols[c]);
         float acc = 0.f;
 #pragma unroll
         for (int a = -R; a <= R; ++a) acc = fmaf(taps.t[a + R], Hs[2 * l + G - a][c], acc);
-        Rl[l][c] = acc - __ldg(y + (size_t)lrows[l] * w + lcols[c]);
+        Rl[l][c] = acc - yv;
     }
     __syncthreads();
     // column half of A^T: V(p, c) = sum_{a : p + a even} t_a r((p + a) / 2, c).  Rows

@@ -8,11 +8,18 @@ Algorithm 1, step by step, with mu = 1/(alpha + rho):
 D is DSG-NLM with a fixed W (the F-DSG-NLM variant of Sec. 4: W built once from a
 guide and then frozen).  The initial values are x = v = clip(guide, 0, 1), u = 0.
 
+The adaptive variants of Sec. 4 rebuild W from the denoiser input x + u: in every
+iteration (A-DSG-NLM), or in the first ``adapt_iters`` iterations only, after
+which the last W is kept (F-DSG-NLM with the paper's adapt-then-freeze schedule,
+typically 15 iterations).
+
 Residuals (Sec. 4, Tables 2-3, following Boyd et al.): primal ||x - v|| / sqrt(n)
 and dual rho ||v^k - v^{k-1}|| / sqrt(n), reported as RMS values.  PSNR uses peak 1
 over all pixels.
 
-Parity status: with W = I and C = R^n the loop is gradient descent
+Parity status: the adaptive loop with one adaptation equals the fixed loop with W
+built from x^1 + u^0, and with a denoiser that ignores its input it equals the
+fixed loop.  With W = I and C = R^n the loop is gradient descent
 x <- x - mu grad f(x); that case is pinned against an explicit dense-matrix
 iteration.  With a fixed DSG-NLM W and alpha above the Lipschitz constant the
 residuals decay (convergence of linearized ADMM, Sec. 2); that is checked as a
@@ -61,6 +68,34 @@ def lpnp_solve(grad_f, denoise, x, v, u, alpha, rho, iters, constraint, x_true=N
         x = project(x, constraint)
         v_prev = v
         v = denoise(x + u)
+        u = u + (x - v)
+        hist.append((rms(x - v), rho * rms(v - v_prev),
+                     None if x_true is None else psnr(x, x_true)))
+    return x, v, u, hist
+
+
+def lpnp_solve_adaptive(grad_f, make_denoiser, x, v, u, alpha, rho, iters, adapt_iters, constraint,
+                        x_true=None):
+    """Algorithm 1 with W rebuilt from the denoiser input (Sec. 4): in iteration k <
+    adapt_iters, ``make_denoiser(x + u)`` returns the denoiser built from x + u, which
+    is then applied to x + u; later iterations keep the last one.  adapt_iters >= iters
+    is A-DSG-NLM.  Returns (x, v, u, history) as lpnp_solve."""
+    if adapt_iters < 1:
+        raise ValueError("adapt_iters must be at least 1: W is built from x + u")
+    x = np.asarray(x, dtype=np.float64).copy()
+    v = np.asarray(v, dtype=np.float64).copy()
+    u = np.asarray(u, dtype=np.float64).copy()
+    mu = 1.0 / (alpha + rho)
+    hist = []
+    denoise = None
+    for k in range(iters):
+        x = mu * (alpha * x + rho * (v - u) - grad_f(x))
+        x = project(x, constraint)
+        z = x + u
+        if k < adapt_iters:
+            denoise = make_denoiser(z)
+        v_prev = v
+        v = denoise(z)
         u = u + (x - v)
         hist.append((rms(x - v), rho * rms(v - v_prev),
                      None if x_true is None else psnr(x, x_true)))

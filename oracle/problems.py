@@ -68,3 +68,26 @@ def solve_spi(wl: dict, inst: dict, iters: int | None = None, tol: float | None 
                           wl["alpha"], wl["rho"], wl["iters"] if iters is None else iters,
                           lpnp.BOX01, inst["x_true"])
     return dict(guide=g, W=W, info=info, x=out[0], v=out[1], u=out[2], hist=out[3])
+
+
+def solve_sr_adaptive(wl: dict, inst: dict, adapt_iters: int, iters: int | None = None,
+                      tol: float | None = None, maxit: int = 10000):
+    """Algorithm 1 for 2x super-resolution with W rebuilt from x + u in the first
+    adapt_iters iterations (A-DSG-NLM when adapt_iters >= iters, the paper's
+    F-DSG-NLM schedule otherwise).  The initial state comes from the bicubic guide."""
+    psf = inst["psf"]
+    y = inst["y"].astype(np.float64)
+    g = forward.sr_guide(y)
+    tol = wl["tol"] if tol is None else tol
+    infos = []
+
+    def make_denoiser(z):
+        W, info = dsgnlm.build_w(z, wl["patch_r"], wl["search_r"], wl["h"], tol, maxit)
+        infos.append(info)
+        return lambda zz: dsgnlm.denoise(W, zz)
+
+    x0, v0, u0 = lpnp.initial_state(g)
+    out = lpnp.lpnp_solve_adaptive(lambda x: forward.sr_grad(x, y, psf), make_denoiser, x0, v0, u0,
+                                   wl["alpha"], wl["rho"], wl["iters"] if iters is None else iters,
+                                   adapt_iters, lpnp.BOX01, inst["x_true"])
+    return dict(guide=g, infos=infos, x=out[0], v=out[1], u=out[2], hist=out[3])

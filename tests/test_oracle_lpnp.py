@@ -57,3 +57,50 @@ def test_spi_solve_stays_in_box_and_settles():
     assert x.min() >= 0 and x.max() <= 1
     hist = out["hist"]
     assert hist[-1][1] < 0.1 * hist[0][1]
+
+
+def test_one_adaptation_equals_fixed_w_from_first_input():
+    # adapt_iters = 1: W is built once, from x^1 + u^0, and then frozen; the fixed
+    # loop started from the same state with that W must give the same iterates
+    wl = synthetic.workload("sr64")
+    inst = problems.sr_instance(wl, H=16, W=20)
+    y = inst["y"].astype(np.float64)
+    g = forward.sr_guide(y)
+    x0, v0, u0 = lpnp.initial_state(g)
+    grad = lambda x: forward.sr_grad(x, y, PSF)
+    mk = lambda z: (lambda zz, W=dsgnlm.build_w(z, 1, 2, 0.1, 1e-12, 10000)[0]: dsgnlm.denoise(W, zz))
+    xa, va, ua, ha = lpnp.lpnp_solve_adaptive(grad, mk, x0, v0, u0, 1.0, 1.0, 6, 1, lpnp.BOX01)
+    mu = 0.5
+    x1 = np.clip(mu * (x0 + (v0 - u0) - grad(x0)), 0, 1)
+    W1, _ = dsgnlm.build_w(x1 + u0, 1, 2, 0.1, 1e-12, 10000)
+    xf, vf, uf, hf = lpnp.lpnp_solve(grad, lambda z: dsgnlm.denoise(W1, z), x0, v0, u0, 1.0, 1.0, 6, lpnp.BOX01)
+    np.testing.assert_allclose(xa, xf, atol=1e-14)
+    np.testing.assert_allclose(ua, uf, atol=1e-14)
+
+
+def test_adaptive_loop_with_input_independent_denoiser_is_fixed_loop():
+    wl = synthetic.workload("sr64")
+    inst = problems.sr_instance(wl, H=12, W=12)
+    y = inst["y"].astype(np.float64)
+    g = forward.sr_guide(y)
+    x0, v0, u0 = lpnp.initial_state(g)
+    grad = lambda x: forward.sr_grad(x, y, PSF)
+    W, _ = dsgnlm.build_w(g, 1, 2, 0.1, 1e-12, 10000)
+    den = lambda z: dsgnlm.denoise(W, z)
+    xa, _, ua, ha = lpnp.lpnp_solve_adaptive(grad, lambda z: den, x0, v0, u0, 1.0, 1.0, 7, 7, lpnp.BOX01)
+    xf, _, uf, hf = lpnp.lpnp_solve(grad, den, x0, v0, u0, 1.0, 1.0, 7, lpnp.BOX01)
+    np.testing.assert_array_equal(xa, xf)
+    assert ha == hf
+
+
+def test_adapt_then_freeze_converges():
+    # the paper's F-DSG-NLM schedule: after the last adaptation W is fixed, so the
+    # residuals decay (Sec. 4); A-DSG-NLM carries no such guarantee
+    wl = synthetic.workload("sr64")
+    inst = problems.sr_instance(wl, H=24, W=24)
+    out = problems.solve_sr_adaptive(wl, inst, adapt_iters=5, iters=120, tol=1e-10)
+    hist = out["hist"]
+    assert len(out["infos"]) == 5
+    assert hist[-1][0] < 1e-3 * hist[5][0]
+    assert hist[-1][1] < 1e-3 * hist[5][1]
+    assert out["x"].min() >= 0 and out["x"].max() <= 1

@@ -366,6 +366,47 @@ def run_spi(steps: int, warmup: int, flush):
             "pnp_iters_per_s": wl["iters"] / (ms / 1e3), "psnr_db": psnr}
 
 
+def run_adaptive(steps: int, warmup: int, flush):
+    """The 512x512 SR workload with W rebuilt from x + u (Sec. 4): the paper's
+    F-DSG-NLM schedule (adapt in the first 15 iterations, then freeze) and A-DSG-NLM
+    (adapt in all 30).  Each adaptation is a build and a balance to 1e-6."""
+    import torch
+
+    import synthetic
+    from paper_1901_06110_gb300 import dsgnlm as D
+    from paper_1901_06110_gb300 import pipeline
+
+    wl = synthetic.workload(WORKLOAD)
+    H, W = wl["H"], wl["W"]
+    xt = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], wl["seed"])).cuda()
+    nz = torch.from_numpy(synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], wl["seed"])).cuda()
+    y = D.lpnp_sr_observe(xt, nz, wl["blur_sigma"], wl["blur_r"])
+    solver = pipeline.Solver(H, W, pipeline.Params.from_workload(wl))
+    out = {"workload": f"sr512 with W rebuilt from x + u: {H}x{W}, patch 7x7, search 21x21, h {wl['h']}, "
+                       f"each adaptation balanced to {wl['tol']}, {wl['iters']} iterations",
+           "steps": steps}
+    for name, adapt in (("f_dsg_nlm_adapt15", 15), ("a_dsg_nlm", wl["iters"])):
+        for _ in range(warmup):
+            solver.run_adaptive(y, adapt)
+        t = 0.0
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            solver.run_adaptive(y, adapt)
+            e1.record()
+            e1.synchronize()
+            t += e0.elapsed_time(e1)
+        ms = t / steps
+        psnr = float(10 * torch.log10(1.0 / ((solver.x - xt) ** 2).double().mean()))
+        out[name] = {"adapt_iters": adapt, "ms_per_step": ms, "mpix_s": H * W / 1e6 / (ms / 1e3), "psnr_db": psnr}
+    solver.run(y)
+    out["fixed_w_from_guide_psnr_db"] = float(10 * torch.log10(1.0 / ((solver.x - xt) ** 2).double().mean()))
+    solver.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- ours
 
 def _read_stream_gbs() -> float:
@@ -530,6 +571,7 @@ def run_ours(args):
         line["batched"] = run_batched(args.batched_steps, 1, flush)
         line["unrolled"] = run_unrolled(args.batched_steps, 1, flush)
         line["spi"] = run_spi(max(5, args.batched_steps), 2, flush)
+        line["adaptive"] = run_adaptive(args.batched_steps, 1, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         side = 192
         secs = _oracle_solve_seconds(side, wl)

@@ -197,10 +197,22 @@ dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad);
 
 /* Run `iters` iterations of Algorithm 1 with penalty rho > 0, mu = 1/(alpha + rho):
  *   x <- Pi_C(mu (alpha x + rho (v - u) - grad f(x)));  v <- W (x + u);  u <- u + x - v.
- * Uses p->den's handle stream.  Synchronises only if resid_hist is given.  The
- * iteration sequence is recorded once into a CUDA graph per (problem, iters) and
- * replayed on later calls with the same buffers. */
+ * Uses p->den's handle stream.  Synchronises only if resid_hist is given. */
 dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters);
+
+/* Algorithm 1 with W rebuilt from the denoiser input (Sec. 4): in each of the first
+ * `adapt_iters` iterations (>= 1) the weights are built from z = x + u, after the
+ * x-update, with the given patch radius, search radius and bandwidth (as
+ * dsgnlm_build), then balanced to `tol` within `maxit` updates (as dsgnlm_balance;
+ * a balance that ends NOT_CONVERGED or STALLED is accepted, W is still doubly
+ * stochastic), and W z is formed; later iterations keep the last W.  adapt_iters >=
+ * iters is A-DSG-NLM; a smaller value is the paper's F-DSG-NLM schedule (adapt for
+ * about 15 iterations, then freeze).  p->den need not be built: its weights are
+ * replaced, and on return it holds the last W, balanced.  search_r must be one the
+ * stencil path supports (1-8, 10, 12), else DSGNLM_EINVAL; other errors as
+ * lpnp_solve, dsgnlm_build and dsgnlm_balance.  Synchronises once per adaptation. */
+dsgnlm_status lpnp_solve_adaptive(const lpnp_problem* p, float rho, int iters, int adapt_iters, int patch_r,
+                                  int search_r, float bandwidth, double tol, int maxit);
 
 /* Allocation-free super-resolution gradient: grad = A^T (A x - y), the same
  * result as lpnp_gradient for a LPNP_SR2 problem, for callers that cannot

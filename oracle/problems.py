@@ -81,13 +81,33 @@ def solve_sr_adaptive(wl: dict, inst: dict, adapt_iters: int, iters: int | None 
     tol = wl["tol"] if tol is None else tol
     infos = []
 
+    x0, v0, u0 = lpnp.initial_state(g)
+    return _adaptive(wl, lambda x: forward.sr_grad(x, y, psf), g, x0, v0, u0, inst["x_true"], adapt_iters, iters,
+                     tol, maxit)
+
+
+def solve_spi_adaptive(wl: dict, inst: dict, adapt_iters: int, iters: int | None = None,
+                       tol: float | None = None, maxit: int = 10000):
+    """Algorithm 1 for single-photon imaging with W rebuilt from x + u in the first
+    adapt_iters iterations.  The initial state comes from the MLE guide."""
+    K = wl["K_side"] ** 2
+    counts = inst["counts"]
+    g = forward.spi_guide(counts, wl["eta"], K)
+    x0, v0, u0 = lpnp.initial_state(g)
+    grad = lambda x: forward.spi_grad(x, counts, wl["eta"], K, wl["spi_eps"])
+    return _adaptive(wl, grad, g, x0, v0, u0, inst["x_true"], adapt_iters, iters, tol, maxit)
+
+
+def _adaptive(wl, grad, g, x0, v0, u0, x_true, adapt_iters, iters, tol, maxit):
+    tol = wl["tol"] if tol is None else tol
+    infos, mats = [], []
+
     def make_denoiser(z):
         W, info = dsgnlm.build_w(z, wl["patch_r"], wl["search_r"], wl["h"], tol, maxit)
         infos.append(info)
+        mats.append(W)
         return lambda zz: dsgnlm.denoise(W, zz)
 
-    x0, v0, u0 = lpnp.initial_state(g)
-    out = lpnp.lpnp_solve_adaptive(lambda x: forward.sr_grad(x, y, psf), make_denoiser, x0, v0, u0,
-                                   wl["alpha"], wl["rho"], wl["iters"] if iters is None else iters,
-                                   adapt_iters, lpnp.BOX01, inst["x_true"])
-    return dict(guide=g, infos=infos, x=out[0], v=out[1], u=out[2], hist=out[3])
+    out = lpnp.lpnp_solve_adaptive(grad, make_denoiser, x0, v0, u0, wl["alpha"], wl["rho"],
+                                   wl["iters"] if iters is None else iters, adapt_iters, lpnp.BOX01, x_true)
+    return dict(guide=g, infos=infos, W_last=mats[-1], x=out[0], v=out[1], u=out[2], hist=out[3])

@@ -47,6 +47,8 @@ SIGNATURES = {
     "lpnp_init": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lpnp_gradient": (c_int, [ctypes.POINTER(LpnpProblem), c_void_p, c_void_p]),
     "lpnp_solve": (c_int, [ctypes.POINTER(LpnpProblem), c_float, c_int]),
+    "lpnp_solve_adaptive": (c_int, [ctypes.POINTER(LpnpProblem), c_float, c_int, c_int, c_int, c_int, c_float,
+                                    c_double, c_int]),
     "lpnp_solve_batched": (c_int, [ctypes.POINTER(LpnpProblem), c_int, c_float, c_int]),
     "lpnp_sr_gradient_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_float, c_int, c_void_p,
                                          c_void_p]),

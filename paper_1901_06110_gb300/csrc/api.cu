@@ -446,9 +446,9 @@ dsgnlm_status lpnp_init(const float* guide, int n, float* x, float* v, float* u,
 
 namespace {
 
-// Checks the data-term fields; with `for_solve` also the iterate buffers and the
-// denoiser state.
-dsgnlm_status check_problem(const lpnp_problem* p, bool for_solve) {
+// Checks the data-term fields; with `for_solve` also the iterate buffers and, with
+// `need_w`, the denoiser state.
+dsgnlm_status check_problem(const lpnp_problem* p, bool for_solve, bool need_w = true) {
     if (!p || !p->den || p->H < 1 || p->W < 1) return DSGNLM_EINVAL;
     if (for_solve) {
         if (!p->x || !p->v || !p->u) return DSGNLM_EINVAL;
@@ -456,9 +456,11 @@ dsgnlm_status check_problem(const lpnp_problem* p, bool for_solve) {
         if (p->x == p->v || p->x == p->u || p->v == p->u) return DSGNLM_EINVAL;
         if (p->constraint < LPNP_C_NONE || p->constraint > LPNP_C_BOX01) return DSGNLM_EINVAL;
         if (!(p->alpha >= 0.f) || !std::isfinite(p->alpha)) return DSGNLM_EINVAL;
-        if (!p->den->built) return DSGNLM_NOT_BUILT;
-        if (!p->den->balanced) return DSGNLM_NOT_BALANCED;
-        if (p->H != p->den->H || p->W != p->den->W) return DSGNLM_EINVAL;
+        if (need_w) {
+            if (!p->den->built) return DSGNLM_NOT_BUILT;
+            if (!p->den->balanced) return DSGNLM_NOT_BALANCED;
+            if (p->H != p->den->H || p->W != p->den->W) return DSGNLM_EINVAL;
+        }
     }
     if (p->kind == LPNP_SR2) {
         if (!p->y || (p->H & 1) || (p->W & 1)) return DSGNLM_EINVAL;
@@ -492,17 +494,41 @@ dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad) 
     return DSGNLM_OK;
 }
 
-dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
-    dsgnlm_status s = check_problem(p, true);
+}  // extern "C"
+
+namespace {
+
+// W rebuilt from the denoiser input (Sec. 4, A-DSG-NLM and the adapt-then-freeze
+// schedule): in iterations k < iters the weights are built from z = x + u and
+// balanced before W z is formed.
+struct Adapt {
+    int iters, patch_r, search_r;
+    float bandwidth;
+    double tol;
+    int maxit;
+};
+
+// Build from the handle's z and balance; NOT_CONVERGED and STALLED still leave W
+// exactly doubly stochastic and are accepted.
+dsgnlm_status adapt_w(dsgnlm* h, const Adapt& ad, int H, int W) {
+    dsgnlm_status s = dsgnlm_build(h, h->z.as<float>(), H, W, ad.patch_r, ad.search_r, ad.bandwidth);
+    if (s != DSGNLM_OK) return s;
+    s = dsgnlm_balance(h, ad.tol, ad.maxit, nullptr, nullptr);
+    return (s == DSGNLM_NOT_CONVERGED || s == DSGNLM_STALLED) ? DSGNLM_OK : s;
+}
+
+dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adapt* ad) {
+    dsgnlm_status s = check_problem(p, true, ad == nullptr);
     if (s != DSGNLM_OK) return s;
     if (!(rho > 0.f) || !std::isfinite(rho) || iters < 0) return DSGNLM_EINVAL;
     if (iters == 0) return DSGNLM_OK;
     dsgnlm* h = p->den;
     const int H = p->H, W = p->W;
     const size_t n = (size_t)H * W;
-    const int nblocks = h->fast ? combine_xupdate_blocks(H, W) : apply_grid_blocks(H, W);
+    const bool fast = ad ? true : h->fast;  // the adaptive form runs on the TMA path only
+    const int nblocks = fast ? combine_xupdate_blocks(H, W) : apply_grid_blocks(H, W);
     DSG_CK(h->z.ensure(n * sizeof(float)));
-    DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nblocks * (h->fast ? (size_t)iters : 1)));
+    DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nblocks * (fast ? (size_t)iters : 1)));
     DSG_CK(h->arrive.ensure(sizeof(unsigned) * (size_t)iters));
     DSG_CK(h->hist.ensure(sizeof(double) * 2 * (size_t)iters));
     DSG_CK(cudaMemsetAsync(h->arrive.p, 0, sizeof(unsigned) * (size_t)iters, h->stream));
@@ -517,7 +543,7 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
     float* xA = p->x;
     float* xB = p->kind == LPNP_SR2 ? h->x2.as<float>() : p->x;
     const bool sr = p->kind == LPNP_SR2;
-    if (h->fast) {
+    if (fast) {
         // Iteration k: phase-1 gather of W z, then one per-pixel pass that finishes v
         // and u of iteration k and performs the x-update of iteration k + 1.  For SR
         // that update needs A^T(A x - y) at the current x, which depends on x alone:
@@ -560,6 +586,13 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
         const int kind = sr ? 0 : 1;
         for (int it = 0; it < iters; ++it) {
             const bool do_x = it < iters - 1;
+            if (ad && it < ad->iters) {
+                s = adapt_w(h, *ad, H, W);
+                if (s != DSGNLM_OK) return s;
+                ea.d = h->d_final;
+                ea.t = h->t_final;
+                ea.inv_m = h->inv_m;
+            }
             if (sr && do_x) DSG_CK(cudaEventRecord(h->ev_fork, h->stream));
             DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
                 return launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
@@ -598,14 +631,14 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
             }));
         }
     }
-    if (!h->fast && sr && (iters & 1))
+    if (!fast && sr && (iters & 1))
         DSG_CK(cudaMemcpyAsync(p->x, h->x2.p, n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     if (p->resid_hist) {
         DSG_CK(h->stage(sizeof(double) * 2 * (size_t)iters));
         DSG_CK(cudaMemcpyAsync(h->host_stage, h->hist.p, sizeof(double) * 2 * (size_t)iters,
                                cudaMemcpyDeviceToHost, h->stream));
         DSG_CK(cudaStreamSynchronize(h->stream));
-        if (h->fast) {
+        if (fast) {
             unsigned errv = 0;
             DSG_CK(cudaMemcpy(&errv, h->err.p, sizeof errv, cudaMemcpyDeviceToHost));
             if (errv) return DSGNLM_TIMEOUT;
@@ -617,6 +650,22 @@ dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
         }
     }
     return DSGNLM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) { return solve_impl(p, rho, iters, nullptr); }
+
+dsgnlm_status lpnp_solve_adaptive(const lpnp_problem* p, float rho, int iters, int adapt_iters, int patch_r,
+                                  int search_r, float bandwidth, double tol, int maxit) {
+    if (adapt_iters < 1 || !tma_path_supports(search_r)) return DSGNLM_EINVAL;
+    if (patch_r < 0 || patch_r > DSGNLM_MAX_PATCH_R || !(bandwidth > 0.f) || !std::isfinite(bandwidth))
+        return DSGNLM_EINVAL;
+    if (!(tol >= 0.0) || maxit < 1) return DSGNLM_EINVAL;
+    const Adapt ad{adapt_iters, patch_r, search_r, bandwidth, tol, maxit};
+    return solve_impl(p, rho, iters, &ad);
 }
 
 dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho, int iters) {

@@ -242,6 +242,25 @@ def lpnp_solve(p: Problem, rho: float, iters: int, residuals: bool = False):
     return [(hist[2 * k], hist[2 * k + 1]) for k in range(iters)]
 
 
+def lpnp_solve_adaptive(p: Problem, rho: float, iters: int, adapt_iters: int, patch_r: int, search_r: int,
+                        bandwidth: float, tol: float, maxit: int, residuals: bool = False):
+    """Algorithm 1 with W rebuilt from x + u in the first adapt_iters iterations
+    (A-DSG-NLM when adapt_iters >= iters, the adapt-then-freeze F-DSG-NLM schedule
+    otherwise).  p.den need not be built; it holds the last W afterwards."""
+    hist = (ctypes.c_double * (2 * iters))() if residuals and iters > 0 else None
+    p.struct.resid_hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None
+    try:
+        _check(_abi.load().lpnp_solve_adaptive(ctypes.byref(p.struct), float(rho), int(iters), int(adapt_iters),
+                                               int(patch_r), int(search_r), float(bandwidth), float(tol),
+                                               int(maxit)), "lpnp_solve_adaptive")
+        p.den.H, p.den.W = p.struct.H, p.struct.W  # the handle now holds a W of this size
+    finally:
+        p.struct.resid_hist = None
+    if hist is None:
+        return None
+    return [(hist[2 * k], hist[2 * k + 1]) for k in range(iters)]
+
+
 def dsgnlm_profile_enable(h: Dsgnlm, enable: bool = True) -> None:
     _check(h.lib.dsgnlm_profile_enable(h.handle, int(bool(enable))), "dsgnlm_profile_enable")
 

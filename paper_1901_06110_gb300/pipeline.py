@@ -88,6 +88,26 @@ class Solver:
                                self.v.data_ptr(), self.u.data_ptr(), stream), "lpnp_init")
         return D.lpnp_solve(self._problem(data), p.rho, p.iters, residuals=residuals)
 
+    def run_adaptive(self, data: torch.Tensor, adapt_iters: int, residuals: bool = False):
+        """The same solve with W rebuilt from x + u in the first adapt_iters
+        iterations (Sec. 4): A-DSG-NLM when adapt_iters >= iters, otherwise the
+        adapt-then-freeze F-DSG-NLM schedule.  The guide only sets the initial state."""
+        p = self.p
+        lib = _abi.load()
+        stream = D._stream()
+        if self.kind == "sr":
+            D._check(lib.lpnp_sr_guide(data.data_ptr(), self.H // 2, self.W // 2, self.guide.data_ptr(),
+                                       stream), "lpnp_sr_guide")
+        else:
+            D._check(lib.lpnp_spi_guide(data.data_ptr(), self.H, self.W, p.K, p.eta, self.guide.data_ptr(),
+                                        stream), "lpnp_spi_guide")
+        D._check(lib.lpnp_init(self.guide.data_ptr(), self.H * self.W, self.x.data_ptr(),
+                               self.v.data_ptr(), self.u.data_ptr(), stream), "lpnp_init")
+        hist = D.lpnp_solve_adaptive(self._problem(data), p.rho, p.iters, adapt_iters, p.patch_r, p.search_r, p.h,
+                                     p.tol, p.maxit, residuals=residuals)
+        self.balance = None
+        return hist
+
     def close(self):
         self.den.close()
 

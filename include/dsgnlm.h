@@ -245,6 +245,25 @@ dsgnlm_status lpnp_sr_gradient_noalloc(const float* x, const float* y, int H, in
  * given.  EINVAL for mixed batches or count out of range. */
 dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho, int iters);
 
+/* lpnp_solve_batched with an offset schedule: `slices` > 0 splits the window
+ * offsets of every image into that many slices (phase-1 work items per tile);
+ * 0 keeps each handle's own plan, which is sized for one image alone on the GPU.
+ * Fewer slices mean fewer partial regions to combine; more mean more work items.
+ * Results agree with the handles' own plans up to FP32 summation order.  The step
+ * sequence of a batch is recorded into a CUDA graph on probs[0].den and replayed
+ * while the batch (buffers, sizes, iters, schedule) is unchanged. */
+dsgnlm_status lpnp_solve_batched_sched(const lpnp_problem* probs, int count, float rho, int iters, int slices);
+
+/* Autotuner for the batched schedule (no counterpart in the paper): for each of
+ * the `ncand` candidate slice counts (>= 0, as lpnp_solve_batched_sched), runs one
+ * warm-up iteration and `trial_iters` timed iterations of the batch on copies of
+ * the iterates (the problems' x, v, u are not modified; the weights are only read),
+ * and returns the fastest candidate in *best_slices and, if ms_per_iter is not
+ * NULL, the milliseconds per iteration of each candidate in ms_per_iter[ncand].
+ * Allocates and frees three images per problem; synchronises. */
+dsgnlm_status lpnp_tune_batched(const lpnp_problem* probs, int count, float rho, const int* candidates, int ncand,
+                                int trial_iters, int* best_slices, float* ms_per_iter);
+
 /* ---------------------------------------------------------------------------
  * Differentiable form: unrolled Algorithm 1 and its adjoint
  * ------------------------------------------------------------------------- */

@@ -50,6 +50,9 @@ SIGNATURES = {
     "lpnp_solve_adaptive": (c_int, [ctypes.POINTER(LpnpProblem), c_float, c_int, c_int, c_int, c_int, c_float,
                                     c_double, c_int]),
     "lpnp_solve_batched": (c_int, [ctypes.POINTER(LpnpProblem), c_int, c_float, c_int]),
+    "lpnp_solve_batched_sched": (c_int, [ctypes.POINTER(LpnpProblem), c_int, c_float, c_int, c_int]),
+    "lpnp_tune_batched": (c_int, [ctypes.POINTER(LpnpProblem), c_int, c_float, ctypes.POINTER(c_int), c_int, c_int,
+                                  ctypes.POINTER(c_int), ctypes.POINTER(c_float)]),
     "lpnp_sr_gradient_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_float, c_int, c_void_p,
                                          c_void_p]),
     "lpnp_tape_create": (c_int, [ctypes.POINTER(c_void_p)]),

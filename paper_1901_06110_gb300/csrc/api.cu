@@ -202,8 +202,8 @@ cudaError_t balance_pass(dsgnlm* h, int parity, cudaStream_t st, cudaGraphCondit
 // Everything a recorded balance graph depends on.
 void balance_key(const dsgnlm* h, unsigned char out[256]) {
     std::memset(out, 0, 256);
-    const void* ptrs[8] = {h->planes.p, h->dbuf[0].p, h->dbuf[1].p, h->tbuf[0].p,
-                           h->tbuf[1].p, h->bal_part.p, h->ctl.p, h->err.p};
+    const void* ptrs[9] = {h->planes.p, h->dbuf[0].p, h->dbuf[1].p, h->tbuf[0].p, h->tbuf[1].p,
+                           h->bal_part.p, h->ctl.p, h->err.p, h->plan.partials};
     const int ints[5] = {h->H, h->W, h->rs, h->dtype, h->plan.splits.n};
     std::memcpy(out, ptrs, sizeof ptrs);
     std::memcpy(out + sizeof ptrs, ints, sizeof ints);
@@ -668,8 +668,24 @@ dsgnlm_status lpnp_solve_adaptive(const lpnp_problem* p, float rho, int iters, i
     return solve_impl(p, rho, iters, &ad);
 }
 
-dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho, int iters) {
-    if (!probs || count < 1 || count > kMaxBatch) return DSGNLM_EINVAL;
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+void key_put(std::vector<unsigned char>& k, const T& v) {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+    k.insert(k.end(), b, b + sizeof(T));
+}
+
+// Batched Algorithm 1.  `slices` > 0 splits the offsets of every image into that many
+// slices (the batch fills the GPU by itself, so fewer slices than a lone image
+// needs cut the partial-region traffic); 0 keeps each handle's own plan.  With
+// `use_graph` the step sequence is recorded once into a CUDA graph on the lead
+// handle and replayed while the batch is unchanged.
+dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int iters, int slices,
+                           bool use_graph) {
+    if (!probs || count < 1 || count > kMaxBatch || slices < 0) return DSGNLM_EINVAL;
     if (!(rho > 0.f) || !std::isfinite(rho) || iters < 0) return DSGNLM_EINVAL;
     for (int i = 0; i < count; ++i) {
         dsgnlm_status s = check_problem(&probs[i], true);
@@ -699,13 +715,17 @@ dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho
         DSG_CK(h->z.ensure(n * sizeof(float)));
         if (p->kind == LPNP_SR2) DSG_CK(h->x2.ensure(n * sizeof(float)));
         DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nb * iters));
+        const TmaSplits splits = slices > 0 ? make_splits(h->rs, slices) : h->plan.splits;
+        const size_t tiles = (size_t)h->plan.tiles_x * h->plan.tiles_y;
+        DSG_CK(h->tma_part.ensure(sizeof(float) * tma_region_floats(h->rs) * tiles * splits.n));
+        h->plan.partials = h->tma_part.as<float>();  // the buffer may have grown
         std::memcpy(maps.m[i], h->plan.tmap, 128);
         BatchInst& bi = inst[i];
         bi.H = H;
         bi.W = W;
         bi.tiles_x = h->plan.tiles_x;
         bi.tiles_y = h->plan.tiles_y;
-        bi.splits = h->plan.splits;
+        bi.splits = splits;
         bi.d = h->d_final;
         bi.z = h->z.as<float>();
         bi.part = h->plan.partials;
@@ -736,17 +756,22 @@ dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho
         ea.rho = rho;
         ea.constraint = p->constraint;
         ea.do_x = 1;
-        be.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, h->plan.splits.n, h->rs};
+        be.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, splits.n, h->rs};
         be.gx = gx;
         be.nblocks = nb;
         be.partials = h->partials.as<double>();
         for (int by = 0; by < gy; ++by)
             for (int bx = 0; bx < gx; ++bx) work2.push_back(make_int4(i, by, bx, 0));
     }
+    bool want_hist = false;
+    for (int i = 0; i < count; ++i) want_hist |= probs[i].resid_hist != nullptr;
     DSG_CK(lead->b_inst.ensure(sizeof(BatchInst) * count));
     DSG_CK(lead->b_epi.ensure(sizeof(BatchEpi) * count));
     DSG_CK(lead->b_work1.ensure(sizeof(int4) * work1.size()));
     DSG_CK(lead->b_work2.ensure(sizeof(int4) * work2.size()));
+    if (want_hist) DSG_CK(lead->b_hist.ensure(sizeof(double) * 2 * (size_t)count * iters));
+    // the tables carry the scalings and 1/m of the current balance: uploaded on every
+    // call, read by the kernels (and a recorded graph) at run time
     DSG_CK(cudaMemcpyAsync(lead->b_inst.p, inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice, st));
     DSG_CK(cudaMemcpyAsync(lead->b_epi.p, epi.data(), sizeof(BatchEpi) * count, cudaMemcpyHostToDevice, st));
     DSG_CK(cudaMemcpyAsync(lead->b_work1.p, work1.data(), sizeof(int4) * work1.size(), cudaMemcpyHostToDevice, st));
@@ -758,20 +783,63 @@ dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho
     const int4* w1 = lead->b_work1.as<int4>();
     const int4* w2 = lead->b_work2.as<int4>();
     const int n1 = (int)work1.size(), n2 = (int)work2.size();
-    DSG_CK(lead->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_batched_xupdate0(kind, depi, w2, n2, st); }));
-    for (int it = 0; it < iters; ++it) {
-        DSG_CK(lead->timed(DSGNLM_PROF_APPLY, [&] {
-            return launch_tma_gather_batched(lead->dtype, lead->rs, maps, dinst, w1, n1, lead->err.as<unsigned>(), st);
-        }));
-        DSG_CK(lead->timed(DSGNLM_PROF_XUPDATE,
-                           [&] { return launch_batched_combine(kind, depi, w2, n2, it, it == iters - 1, st); }));
+    auto steps = [&](cudaStream_t s) -> cudaError_t {
+        cudaError_t e = lead->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_batched_xupdate0(kind, depi, w2, n2, s); });
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+            e = lead->timed(DSGNLM_PROF_APPLY, [&] {
+                return launch_tma_gather_batched(lead->dtype, lead->rs, maps, dinst, w1, n1, lead->err.as<unsigned>(), s);
+            });
+            if (e == cudaSuccess)
+                e = lead->timed(DSGNLM_PROF_XUPDATE,
+                                [&] { return launch_batched_combine(kind, depi, w2, n2, it, it == iters - 1, s); });
+        }
+        if (e == cudaSuccess && want_hist) e = launch_batched_reduce(depi, count, lead->b_hist.as<double>(), iters, s);
+        return e;
+    };
+    bool ran = false;
+    if (use_graph && !lead->prof) {
+        // everything a recorded sequence bakes into its kernel parameters
+        std::vector<unsigned char> key;
+        const int ints[9] = {count, iters, kind, lead->dtype, lead->rs, n1, n2, (int)want_hist, slices};
+        const void* ptrs[6] = {lead->b_inst.p, lead->b_epi.p, lead->b_work1.p, lead->b_work2.p, lead->b_hist.p,
+                               lead->err.p};
+        key_put(key, ints);
+        key_put(key, ptrs);
+        key.insert(key.end(), &maps.m[0][0], &maps.m[0][0] + 128 * (size_t)count);
+        cudaError_t e = cudaSuccess;
+        if (!lead->b_exec || key != lead->b_key) {
+            if (lead->b_exec) cudaGraphExecDestroy(lead->b_exec);
+            if (lead->b_graph) cudaGraphDestroy(lead->b_graph);
+            lead->b_exec = nullptr;
+            lead->b_graph = nullptr;
+            lead->b_key.clear();
+            if (!lead->cap_stream) e = cudaStreamCreateWithFlags(&lead->cap_stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(lead->cap_stream, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                g_capturing = true;
+                const cudaError_t e1 = steps(lead->cap_stream);
+                g_capturing = false;
+                cudaGraph_t g = nullptr;
+                e = cudaStreamEndCapture(lead->cap_stream, &g);
+                if (e == cudaSuccess) e = e1;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&lead->b_exec, g, 0);
+                if (e == cudaSuccess) {
+                    lead->b_graph = g;
+                    lead->b_key = key;
+                } else {
+                    if (g) cudaGraphDestroy(g);
+                    lead->b_exec = nullptr;
+                    (void)cudaGetLastError();
+                }
+            }
+        }
+        if (lead->b_exec) {
+            DSG_CK(cudaGraphLaunch(lead->b_exec, st));
+            count_launches(1 + 2 * (uint64_t)iters + (want_hist ? 1 : 0));
+            ran = true;
+        }
     }
-    bool want_hist = false;
-    for (int i = 0; i < count; ++i) want_hist |= probs[i].resid_hist != nullptr;
-    if (want_hist) {
-        DSG_CK(lead->b_hist.ensure(sizeof(double) * 2 * (size_t)count * iters));
-        DSG_CK(launch_batched_reduce(depi, count, lead->b_hist.as<double>(), iters, st));
-    }
+    if (!ran) DSG_CK(steps(st));  // no graph: launch the steps directly
     for (int i = 0; i < count; ++i)
         if (probs[i].kind == LPNP_SR2 && (iters & 1))
             DSG_CK(cudaMemcpyAsync(probs[i].x, probs[i].den->x2.p, sizeof(float) * (size_t)probs[i].H * probs[i].W,
@@ -795,6 +863,84 @@ dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho
     return DSGNLM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho, int iters) {
+    return batched_impl(probs, count, rho, iters, 0, true);
+}
+
+dsgnlm_status lpnp_solve_batched_sched(const lpnp_problem* probs, int count, float rho, int iters, int slices) {
+    return batched_impl(probs, count, rho, iters, slices, true);
+}
+
+dsgnlm_status lpnp_tune_batched(const lpnp_problem* probs, int count, float rho, const int* candidates, int ncand,
+                                int trial_iters, int* best_slices, float* ms_per_iter) {
+    if (!probs || count < 1 || count > kMaxBatch || !candidates || ncand < 1 || trial_iters < 1 || !best_slices)
+        return DSGNLM_EINVAL;
+    for (int c = 0; c < ncand; ++c)
+        if (candidates[c] < 0) return DSGNLM_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        const dsgnlm_status s = check_problem(&probs[i], true);
+        if (s != DSGNLM_OK) return s;
+    }
+    cudaStream_t st = probs[0].den->stream;
+    // trial solves run on copies of the iterates; the weights are only read
+    struct Scratch {
+        std::vector<DevBuf> b;
+        ~Scratch() {
+            for (DevBuf& x : b) x.release();
+        }
+    } scratch;
+    scratch.b.resize(3 * (size_t)count);
+    std::vector<DevBuf>& bufs = scratch.b;
+    std::vector<lpnp_problem> trial(probs, probs + count);
+    for (int i = 0; i < count; ++i) {
+        const size_t bytes = sizeof(float) * (size_t)probs[i].H * probs[i].W;
+        float* src[3] = {probs[i].x, probs[i].v, probs[i].u};
+        for (int k = 0; k < 3; ++k) {
+            DevBuf& b = bufs[3 * (size_t)i + k];
+            DSG_CK(b.ensure(bytes));
+            DSG_CK(cudaMemcpyAsync(b.p, src[k], bytes, cudaMemcpyDeviceToDevice, st));
+        }
+        trial[i].x = bufs[3 * (size_t)i].as<float>();
+        trial[i].v = bufs[3 * (size_t)i + 1].as<float>();
+        trial[i].u = bufs[3 * (size_t)i + 2].as<float>();
+        trial[i].resid_hist = nullptr;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DSG_CK(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail_cuda(ce);
+    }
+    dsgnlm_status s = DSGNLM_OK;
+    float best = INFINITY;
+    for (int c = 0; c < ncand && s == DSGNLM_OK; ++c) {
+        s = batched_impl(trial.data(), count, rho, 1, candidates[c], false);  // warm-up
+        if (s != DSGNLM_OK) break;
+        ce = cudaEventRecord(e0, st);
+        if (ce == cudaSuccess) s = batched_impl(trial.data(), count, rho, trial_iters, candidates[c], false);
+        if (ce == cudaSuccess && s == DSGNLM_OK) ce = cudaEventRecord(e1, st);
+        if (ce == cudaSuccess && s == DSGNLM_OK) ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess && s == DSGNLM_OK) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) s = fail_cuda(ce);
+        if (s != DSGNLM_OK) break;
+        ms /= (float)trial_iters;
+        if (ms_per_iter) ms_per_iter[c] = ms;
+        if (ms < best) {
+            best = ms;
+            *best_slices = candidates[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == DSGNLM_OK) DSG_CK(cudaStreamSynchronize(st));  // the copies are freed on return
+    return s;
+}
 dsgnlm_status dsgnlm_profile_enable(dsgnlm_t h, int enable) {
     if (!h) return DSGNLM_EINVAL;
     h->prof = enable != 0;

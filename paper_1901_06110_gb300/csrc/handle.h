@@ -91,8 +91,12 @@ struct dsgnlm {
     // main stream streams the weights (fork and join events)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // batched Algorithm 1 workspace (used when this handle leads a batch)
+    // batched Algorithm 1 workspace (used when this handle leads a batch), and the
+    // batch's step sequence as a CUDA graph with the values it was recorded for
     DevBuf b_inst, b_epi, b_work1, b_work2, b_hist;
+    cudaGraph_t b_graph = nullptr;
+    cudaGraphExec_t b_exec = nullptr;
+    std::vector<unsigned char> b_key;
     // optional per-kernel timing
     bool prof = false;
     ProfPool pools[dsg::kProfKinds];
@@ -125,6 +129,11 @@ struct dsgnlm {
         if (bal_graph) cudaGraphDestroy(bal_graph);
         bal_exec = nullptr;
         bal_graph = nullptr;
+        if (b_exec) cudaGraphExecDestroy(b_exec);
+        if (b_graph) cudaGraphDestroy(b_graph);
+        b_exec = nullptr;
+        b_graph = nullptr;
+        b_key.clear();
     }
     void release_all() {
         release_graphs();

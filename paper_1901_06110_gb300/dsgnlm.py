@@ -274,9 +274,27 @@ def dsgnlm_profile_read(h: Dsgnlm, kind: int):
     return ms.value, n.value
 
 
-def lpnp_solve_batched(problems, rho: float, iters: int, residuals: bool = False):
+def lpnp_tune_batched(problems, rho: float, candidates=(0, 1, 2, 3, 4), trial_iters: int = 2):
+    """Time the batch under each candidate offset schedule (on copies of the
+    iterates) and return (best slices, {slices: ms per iteration})."""
+    count = len(problems)
+    arr = (_abi.LpnpProblem * count)()
+    for i, p in enumerate(problems):
+        arr[i] = p.struct
+        arr[i].resid_hist = None
+    cand = (ctypes.c_int * len(candidates))(*[int(c) for c in candidates])
+    ms = (ctypes.c_float * len(candidates))()
+    best = ctypes.c_int(-1)
+    _check(_abi.load().lpnp_tune_batched(arr, count, float(rho), cand, len(candidates), int(trial_iters),
+                                         ctypes.byref(best), ms), "lpnp_tune_batched")
+    return best.value, {int(c): float(ms[k]) for k, c in enumerate(candidates)}
+
+
+def lpnp_solve_batched(problems, rho: float, iters: int, residuals: bool = False, slices: int | None = None):
     """Algorithm 1 for several images at once (one launch per step over all of
-    them).  Returns per-problem residual lists when residuals=True."""
+    them; the step sequence is replayed from a CUDA graph).  `slices` selects the
+    offset schedule (None or 0: each handle's own plan).  Returns per-problem
+    residual lists when residuals=True."""
     count = len(problems)
     arr = (_abi.LpnpProblem * count)()
     hists = []
@@ -288,7 +306,11 @@ def lpnp_solve_batched(problems, rho: float, iters: int, residuals: bool = False
             arr[i].resid_hist = ctypes.cast(h, ctypes.POINTER(ctypes.c_double))
         else:
             arr[i].resid_hist = None
-    _check(_abi.load().lpnp_solve_batched(arr, count, float(rho), int(iters)), "lpnp_solve_batched")
+    if slices:
+        _check(_abi.load().lpnp_solve_batched_sched(arr, count, float(rho), int(iters), int(slices)),
+               "lpnp_solve_batched_sched")
+    else:
+        _check(_abi.load().lpnp_solve_batched(arr, count, float(rho), int(iters)), "lpnp_solve_batched")
     if not hists:
         return None
     return [[(h[2 * k], h[2 * k + 1]) for k in range(iters)] for h in hists]

@@ -115,7 +115,8 @@ class Solver:
 class BatchSolver:
     """Many super-resolution images of uneven sizes solved together: per image a
     guide, weight build and balance, then Algorithm 1 for all images at once with
-    lpnp_solve_batched (one launch per step over all images)."""
+    lpnp_solve_batched (one launch per step over all images, replayed from a CUDA
+    graph), under the offset schedule `slices` that tune() picks by measurement."""
 
     def __init__(self, shapes, params: Params):
         self.p = params
@@ -126,10 +127,27 @@ class BatchSolver:
         self.u = [torch.empty_like(t) for t in self.x]
         self.guide = [torch.empty_like(t) for t in self.x]
         self.balance = [None] * len(self.shapes)
+        self.slices = 0  # offset schedule of the batched steps (0: each handle's own plan)
+        self.tuning = None
         self._probs = None
         self._ys = None
 
-    def run(self, ys):
+    def _problems(self, ys):
+        p = self.p
+        if self._probs is None or self._ys is not ys:
+            self._probs = [D.Problem("sr", self.dens[i], self.x[i], self.v[i], self.u[i], alpha=p.alpha, y=ys[i],
+                                     blur_sigma=p.blur_sigma, blur_r=p.blur_r) for i in range(len(self.shapes))]
+            self._ys = ys
+        return self._probs
+
+    def tune(self, ys, candidates=(0, 1, 2, 3, 4), trial_iters: int = 2):
+        """Pick the batched offset schedule by timing each candidate on this batch
+        (the weights must be built and balanced: call after run, or prepare first)."""
+        self.slices, self.tuning = D.lpnp_tune_batched(self._problems(ys), self.p.rho, candidates, trial_iters)
+        return self.slices
+
+    def prepare(self, ys):
+        """Guide, weight build and balance of every image, and the initial state."""
         p = self.p
         lib = _abi.load()
         stream = D._stream()
@@ -140,11 +158,11 @@ class BatchSolver:
             self.balance[i] = D.dsgnlm_balance(self.dens[i], p.tol, p.maxit)
             D._check(lib.lpnp_init(self.guide[i].data_ptr(), H * W, self.x[i].data_ptr(), self.v[i].data_ptr(),
                                    self.u[i].data_ptr(), stream), "lpnp_init")
-        if self._probs is None or self._ys is not ys:
-            self._probs = [D.Problem("sr", self.dens[i], self.x[i], self.v[i], self.u[i], alpha=p.alpha, y=ys[i],
-                                     blur_sigma=p.blur_sigma, blur_r=p.blur_r) for i in range(len(self.shapes))]
-            self._ys = ys
-        return D.lpnp_solve_batched(self._probs, p.rho, p.iters)
+
+    def run(self, ys, residuals: bool = False):
+        self.prepare(ys)
+        return D.lpnp_solve_batched(self._problems(ys), self.p.rho, self.p.iters, residuals=residuals,
+                                    slices=self.slices)
 
     def close(self):
         for d in self.dens:

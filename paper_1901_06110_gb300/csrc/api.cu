@@ -702,7 +702,7 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
     const int kind = probs[0].kind == LPNP_SR2 ? 0 : 1;
     std::vector<BatchInst> inst(count);
     std::vector<BatchEpi> epi(count);
-    std::vector<int4> work1, work2;
+    std::vector<int4> work1, work2, work3;
     BatchMaps maps;
     for (int i = 0; i < count; ++i) {
         const lpnp_problem* p = &probs[i];
@@ -713,7 +713,10 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
         const int nb = gx * gy;
         if (nb != combine_xupdate_blocks(H, W)) return DSGNLM_EINVAL;
         DSG_CK(h->z.ensure(n * sizeof(float)));
-        if (p->kind == LPNP_SR2) DSG_CK(h->x2.ensure(n * sizeof(float)));
+        if (p->kind == LPNP_SR2) {
+            if (p->blur_r != probs[0].blur_r) return DSGNLM_EINVAL;  // one gradient kernel per batch
+            DSG_CK(h->gbuf.ensure(n * sizeof(float)));
+        }
         DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nb * iters));
         const TmaSplits splits = slices > 0 ? make_splits(h->rs, slices) : h->plan.splits;
         const size_t tiles = (size_t)h->plan.tiles_x * h->plan.tiles_y;
@@ -744,8 +747,9 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
         ea.v = p->v;
         ea.u = p->u;
         ea.x_in = p->x;
-        ea.x_out = p->kind == LPNP_SR2 ? h->x2.as<float>() : p->x;
+        ea.x_out = p->x;
         ea.y = p->y;
+        ea.g = p->kind == LPNP_SR2 ? h->gbuf.as<float>() : nullptr;
         ea.taps = make_blur_taps(p->blur_sigma > 0.f ? p->blur_sigma : 1.f, p->kind == LPNP_SR2 ? p->blur_r : 0);
         ea.counts = p->counts;
         ea.K = p->K;
@@ -762,6 +766,9 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
         be.partials = h->partials.as<double>();
         for (int by = 0; by < gy; ++by)
             for (int bx = 0; bx < gx; ++bx) work2.push_back(make_int4(i, by, bx, 0));
+        if (p->kind == LPNP_SR2)
+            for (int by = 0; by < (H + 31) / 32; ++by)
+                for (int bx = 0; bx < (W + 31) / 32; ++bx) work3.push_back(make_int4(i, by, bx, 0));
     }
     bool want_hist = false;
     for (int i = 0; i < count; ++i) want_hist |= probs[i].resid_hist != nullptr;
@@ -769,6 +776,7 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
     DSG_CK(lead->b_epi.ensure(sizeof(BatchEpi) * count));
     DSG_CK(lead->b_work1.ensure(sizeof(int4) * work1.size()));
     DSG_CK(lead->b_work2.ensure(sizeof(int4) * work2.size()));
+    DSG_CK(lead->b_work3.ensure(sizeof(int4) * (work3.size() + 1)));
     if (want_hist) DSG_CK(lead->b_hist.ensure(sizeof(double) * 2 * (size_t)count * iters));
     // the tables carry the scalings and 1/m of the current balance: uploaded on every
     // call, read by the kernels (and a recorded graph) at run time
@@ -776,22 +784,46 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
     DSG_CK(cudaMemcpyAsync(lead->b_epi.p, epi.data(), sizeof(BatchEpi) * count, cudaMemcpyHostToDevice, st));
     DSG_CK(cudaMemcpyAsync(lead->b_work1.p, work1.data(), sizeof(int4) * work1.size(), cudaMemcpyHostToDevice, st));
     DSG_CK(cudaMemcpyAsync(lead->b_work2.p, work2.data(), sizeof(int4) * work2.size(), cudaMemcpyHostToDevice, st));
+    if (!work3.empty())
+        DSG_CK(cudaMemcpyAsync(lead->b_work3.p, work3.data(), sizeof(int4) * work3.size(), cudaMemcpyHostToDevice, st));
     // every image must be ready on the lead stream: the other handles' work is ordered
     // before this call by the caller (same stream), as for lpnp_solve
     const BatchInst* dinst = lead->b_inst.as<BatchInst>();
     const BatchEpi* depi = lead->b_epi.as<BatchEpi>();
     const int4* w1 = lead->b_work1.as<int4>();
     const int4* w2 = lead->b_work2.as<int4>();
-    const int n1 = (int)work1.size(), n2 = (int)work2.size();
+    const int4* w3 = lead->b_work3.as<int4>();
+    const int n1 = (int)work1.size(), n2 = (int)work2.size(), n3 = (int)work3.size();
+    const bool sr = kind == 0;
+    const int blur_r = probs[0].blur_r;
+    if (sr && iters > 1) DSG_CK(lead->ensure_side());
+    // As the single-image solve: the SR gradient of the current x depends on x alone
+    // and runs on the side stream while phase 1 streams the weights.
     auto steps = [&](cudaStream_t s) -> cudaError_t {
-        cudaError_t e = lead->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_batched_xupdate0(kind, depi, w2, n2, s); });
+        cudaError_t e = lead->timed(DSGNLM_PROF_XUPDATE, [&] {
+            if (sr) {
+                const cudaError_t eg = launch_batched_grad(blur_r, depi, w3, n3, s);
+                if (eg != cudaSuccess) return eg;
+            }
+            return launch_batched_xupdate0(kind, depi, w2, n2, s);
+        });
         for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-            e = lead->timed(DSGNLM_PROF_APPLY, [&] {
-                return launch_tma_gather_batched(lead->dtype, lead->rs, maps, dinst, w1, n1, lead->err.as<unsigned>(), s);
-            });
+            const bool do_x = it < iters - 1;
+            if (sr && do_x) e = cudaEventRecord(lead->ev_fork, s);
+            if (e == cudaSuccess)
+                e = lead->timed(DSGNLM_PROF_APPLY, [&] {
+                    return launch_tma_gather_batched(lead->dtype, lead->rs, maps, dinst, w1, n1,
+                                                     lead->err.as<unsigned>(), s);
+                });
+            if (e == cudaSuccess && sr && do_x) {
+                e = cudaStreamWaitEvent(lead->side, lead->ev_fork, 0);
+                if (e == cudaSuccess) e = launch_batched_grad(blur_r, depi, w3, n3, lead->side);
+                if (e == cudaSuccess) e = cudaEventRecord(lead->ev_join, lead->side);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s, lead->ev_join, 0);
+            }
             if (e == cudaSuccess)
                 e = lead->timed(DSGNLM_PROF_XUPDATE,
-                                [&] { return launch_batched_combine(kind, depi, w2, n2, it, it == iters - 1, s); });
+                                [&] { return launch_batched_combine(kind, depi, w2, n2, it, !do_x, s); });
         }
         if (e == cudaSuccess && want_hist) e = launch_batched_reduce(depi, count, lead->b_hist.as<double>(), iters, s);
         return e;
@@ -800,9 +832,9 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
     if (use_graph && !lead->prof) {
         // everything a recorded sequence bakes into its kernel parameters
         std::vector<unsigned char> key;
-        const int ints[9] = {count, iters, kind, lead->dtype, lead->rs, n1, n2, (int)want_hist, slices};
-        const void* ptrs[6] = {lead->b_inst.p, lead->b_epi.p, lead->b_work1.p, lead->b_work2.p, lead->b_hist.p,
-                               lead->err.p};
+        const int ints[11] = {count, iters, kind, lead->dtype, lead->rs, n1, n2, n3, blur_r, (int)want_hist, slices};
+        const void* ptrs[10] = {lead->b_inst.p, lead->b_epi.p, lead->b_work1.p, lead->b_work2.p, lead->b_work3.p,
+                                lead->b_hist.p, lead->err.p, lead->side, lead->ev_fork, lead->ev_join};
         key_put(key, ints);
         key_put(key, ptrs);
         key.insert(key.end(), &maps.m[0][0], &maps.m[0][0] + 128 * (size_t)count);
@@ -835,15 +867,11 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
         }
         if (lead->b_exec) {
             DSG_CK(cudaGraphLaunch(lead->b_exec, st));
-            count_launches(1 + 2 * (uint64_t)iters + (want_hist ? 1 : 0));
+            count_launches(1 + (sr ? 1 : 0) + (sr ? 3 : 2) * (uint64_t)iters - (sr ? 1 : 0) + (want_hist ? 1 : 0));
             ran = true;
         }
     }
     if (!ran) DSG_CK(steps(st));  // no graph: launch the steps directly
-    for (int i = 0; i < count; ++i)
-        if (probs[i].kind == LPNP_SR2 && (iters & 1))
-            DSG_CK(cudaMemcpyAsync(probs[i].x, probs[i].den->x2.p, sizeof(float) * (size_t)probs[i].H * probs[i].W,
-                                   cudaMemcpyDeviceToDevice, st));
     if (want_hist) {
         std::vector<double> hs(2 * (size_t)count * iters);
         DSG_CK(cudaMemcpyAsync(hs.data(), lead->b_hist.p, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, st));

@@ -1,14 +1,17 @@
 // Batched form of Algorithm 1: many images of uneven sizes advance together, one
-// launch per step of the iteration over a work-list of (image, tile) items:
-//   x-update of iteration 0            batched_xupdate0_kernel
+// launch per step of the iteration over a work-list of (image, tile) items, with
+// the same per-image arithmetic as the single-image solve:
+//   SR gradient A^T(A x - y)           batched_grad_kernel (32 x 32 tiles)
+//   x-update of iteration 0            batched_xupdate0_kernel (per pixel)
 //   per iteration: phase-1 gather      launch_tma_gather_batched (stencil_tma.cu)
-//                  combine + x-update  batched_combine_kernel
+//                  combine + x-update  batched_combine_kernel (per pixel)
 // Each image keeps its own DSG-NLM weights (any storage type; the arithmetic is
 // FP32), scaling, closure and iterates; the work-list only flattens the tiles of
 // all images into one grid, so the GPU scheduler balances small and large images.
 #include "combine.cuh"
 #include "common.cuh"
 #include "epilogue.cuh"
+#include "grad.cuh"
 #include "internal.h"
 #include "xupdate.cuh"
 
@@ -32,39 +35,49 @@ __device__ __forceinline__ void spi_xupdate_tile(const EpilogueArgs& a, int y0, 
     }
 }
 
+// x-update of iteration 0 on the 16 x 32 tile of the work item, per pixel: SR with
+// the gradient formed beforehand (a.g), single-photon with h' in place
 template <int KIND>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256)
 batched_xupdate0_kernel(const BatchEpi* __restrict__ insts, const int4* __restrict__ work) {
-    __shared__ SrTile tile;
     const int4 w = work[blockIdx.x];  // (instance, tile row, tile column, -)
     const EpilogueArgs& a = insts[w.x].a;
     const int y0 = w.y * kXH, x0 = w.z * kXW;
-    if (KIND == 0)
-        sr_xupdate_body(tile, a.x_in, a.x_out, a.y, a.H, a.W, a.taps, a.v, a.u, a.z, a.mu, a.alpha, a.rho,
-                        a.constraint, y0, x0);
-    else
+    if (KIND == 1) {
         spi_xupdate_tile(a, y0, x0);
+        return;
+    }
+    const int pj = x0 + threadIdx.x;
+    for (int py = threadIdx.y; py < kXH; py += 8) {
+        const int pi = y0 + py;
+        if (pi >= a.H || pj >= a.W) continue;
+        const size_t q = (size_t)pi * a.W + pj;
+        const float up = a.u[q];
+        const float xn = project(a.mu * (a.alpha * a.x_in[q] + a.rho * (a.v[q] - up) - a.g[q]), a.constraint);
+        a.x_out[q] = xn;
+        a.z[q] = xn + up;
+    }
 }
 
+// g = A^T (A x - y) of one image on the 32 x 32 tile of the work item
+template <int R>
+__global__ void __launch_bounds__(256)
+batched_grad_kernel(const BatchEpi* __restrict__ insts, const int4* __restrict__ work) {
+    __shared__ GradSmem<R> sm;
+    const int4 w = work[blockIdx.x];  // (instance, tile row, tile column, -)
+    const EpilogueArgs& a = insts[w.x].a;
+    const BlurTaps taps = a.taps;
+    sr_grad_tile<R>(sm, a.x_in, a.y, a.H, a.W, taps, a.g, w.y * kGT, w.z * kGT);
+}
+
+// finish v and u of iteration `it` and perform the next x-update, per pixel
 template <int KIND>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
 batched_combine_kernel(const BatchEpi* __restrict__ insts, const int4* __restrict__ work, int it, int last) {
-    __shared__ SrTile tile;
     const int4 w = work[blockIdx.x];
     const BatchEpi& e = insts[w.x];
-    EpilogueArgs a = e.a;
-    // x of the next update alternates between the two buffers of each image
-    const float* xa = e.a.x_in;
-    float* xb = e.a.x_out;
-    a.do_x = !last;
-    a.x_in = (it & 1) ? xa : xb;
-    a.x_out = (it & 1) ? xb : const_cast<float*>(xa);
-    if (KIND == 1) {  // single-photon: x is updated in place
-        a.x_in = xa;
-        a.x_out = const_cast<float*>(xa);
-    }
     double* partials = e.partials + 2 * ((size_t)it * e.nblocks + (size_t)w.y * e.gx + w.z);
-    combine_xupdate_body<KIND>(tile, e.cv, a, w.y * kXH, w.z * kXW, partials);
+    combine_update_body<KIND>(e.cv, e.a, !last, w.y * kXH, w.z * kXW, partials);
 }
 
 // hist of (image, iteration) = fixed-order sums of that image's per-block residual partials
@@ -103,6 +116,24 @@ cudaError_t launch_batched_xupdate0(int kind, const BatchEpi* insts, const int4*
         batched_xupdate0_kernel<0><<<nwork, dim3(32, 8), 0, st>>>(insts, work);
     else
         batched_xupdate0_kernel<1><<<nwork, dim3(32, 8), 0, st>>>(insts, work);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_grad(int blur_r, const BatchEpi* insts, const int4* work, int nwork, cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    switch (blur_r) {
+        case 0: batched_grad_kernel<0><<<nwork, 256, 0, st>>>(insts, work); break;
+        case 1: batched_grad_kernel<1><<<nwork, 256, 0, st>>>(insts, work); break;
+        case 2: batched_grad_kernel<2><<<nwork, 256, 0, st>>>(insts, work); break;
+        case 3: batched_grad_kernel<3><<<nwork, 256, 0, st>>>(insts, work); break;
+        case 4: batched_grad_kernel<4><<<nwork, 256, 0, st>>>(insts, work); break;
+        case 5: batched_grad_kernel<5><<<nwork, 256, 0, st>>>(insts, work); break;
+        case 6: batched_grad_kernel<6><<<nwork, 256, 0, st>>>(insts, work); break;
+        case 7: batched_grad_kernel<7><<<nwork, 256, 0, st>>>(insts, work); break;
+        case 8: batched_grad_kernel<8><<<nwork, 256, 0, st>>>(insts, work); break;
+        default: return cudaErrorInvalidValue;
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -137,7 +137,7 @@ template <int KIND>
 __global__ void __launch_bounds__(256, 4)
 combine_update_kernel(Cover cv, EpilogueArgs a) {
     const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    combine_update_body<KIND>(cv, a, blockIdx.y * kXH, blockIdx.x * kXW, a.partials + 2 * bid);
+    combine_update_body<KIND>(cv, a, a.do_x, blockIdx.y * kXH, blockIdx.x * kXW, a.partials + 2 * bid);
 }
 
 Cover cover(const TmaPlan& plan, int rs) {

@@ -1,6 +1,7 @@
 // Device body of the kernel that finishes one application of W inside
 // Algorithm 1 (v, u and residual sums) and performs the next linearized
-// x-update on the same pixels; shared by the single-image and batched kernels.
+// x-update on the same pixels, per pixel; shared by the single-image and batched
+// kernels.
 #pragma once
 
 #include "combine.cuh"
@@ -95,99 +96,13 @@ __device__ __forceinline__ float tile_gather_comp(const TileCover& c, int li, in
     return acc.value();
 }
 
-// Finish v and u of one iteration on the kXH x kXW tile at (y0, x0), perform the
-// next x-update there when a.do_x, and store the tile's residual sums at
-// `partials` (two doubles).  All threads of a (32, 8) block must call it.
-template <int KIND>  // 0 super-resolution, 1 single-photon
-__device__ __forceinline__ void combine_xupdate_body(SrTile& tile, const Cover& cv, const EpilogueArgs& a,
-                                                     int y0, int x0, double* partials) {
-    const int H = a.H, W = a.W;
-    const bool sr_x = KIND == 0 && a.do_x;
-    SrTileRegs rg;
-    if (sr_x) {
-        sr_tile_index(tile, H, W, a.taps, y0, x0);
-        sr_tile_load(tile, a.x_in, a.y, W, rg);
-    }
-    // per-pixel inputs of the combine, issued before the tile's shared-memory phases
-    const TileCover tc = tile_cover(cv, y0, x0);
-    const int pj = x0 + threadIdx.x;
-    const int lj = pj - (x0 / kTmaTW) * kTmaTW;
-    float A[2], zs[2], ds[2], ts[2], vo[2], uo[2], xs[2];
-    int k1[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int py = threadIdx.y + 8 * r;
-        const int pi = y0 + py;
-        const bool ok = pi < H && pj < W;
-        const size_t q = (size_t)pi * W + pj;
-        A[r] = ok ? tile_gather(tc, py, lj) : 0.f;
-        zs[r] = ok ? a.z[q] : 0.f;
-        ds[r] = ok ? a.d[q] : 0.f;
-        ts[r] = ok ? a.t[q] : 0.f;
-        vo[r] = ok ? a.v[q] : 0.f;
-        uo[r] = ok ? a.u[q] : 0.f;
-        xs[r] = (ok && KIND == 1 && a.do_x) ? a.x_in[q] : 0.f;
-        k1[r] = (ok && KIND == 1 && a.do_x) ? (int)a.counts[q] : 0;
-    }
-    if (sr_x) sr_tile_compute(tile, rg, a.taps.r);
-    float sp = 0.f, sd = 0.f;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int py = threadIdx.y + 8 * r;
-        const int pi = y0 + py;
-        if (pi >= H || pj >= W) continue;
-        const size_t q = (size_t)pi * W + pj;
-        // v = W z with z = x + u: c_s z_s + (d_s / m) sum_{r != s} K1 d_r z_r
-        const float dm = ds[r] * a.inv_m;
-        const float cs = 1.f - dm * (ts[r] - ds[r]);
-        const float vn = fmaf(dm, A[r], cs * zs[r]);
-        const float un = zs[r] - vn;  // u + x - v
-        a.v[q] = vn;
-        a.u[q] = un;
-        const float dp = un - uo[r], dd = vn - vo[r];  // x - v and v - v_prev
-        sp = fmaf(dp, dp, sp);
-        sd = fmaf(dd, dd, sd);
-        if (a.do_x) {
-            float xv, g;
-            if (KIND == 0) {
-                xv = sr_tile_x(tile, pi, pj);
-                g = sr_tile_grad(tile, a.taps.r, py, pj);
-            } else {
-                xv = xs[r];
-                g = spi_hprime(xv, k1[r], a.K, a.eta, a.eps);
-            }
-            const float xn = project(a.mu * (a.alpha * xv + a.rho * (vn - un) - g), a.constraint);
-            a.x_out[q] = xn;
-            a.z[q] = xn + un;
-        }
-    }
-    sp = warp_sum_f(sp);
-    sd = warp_sum_f(sd);
-    __shared__ float s0[8], s1[8];
-    const int t = threadIdx.y * 32 + threadIdx.x;
-    if ((t & 31) == 0) {
-        s0[t >> 5] = sp;
-        s1[t >> 5] = sd;
-    }
-    __syncthreads();
-    if (t == 0) {
-        double pa = 0.0, pb = 0.0;
-        for (int w = 0; w < 8; ++w) {
-            pa += (double)s0[w];
-            pb += (double)s1[w];
-        }
-        partials[0] = pa;
-        partials[1] = pb;
-    }
-}
-
 // Finish v and u of one iteration on the kXH x kXW tile at (y0, x0) and, when
-// a.do_x, perform the next x-update there from the gradient at each pixel alone:
+// do_x, perform the next x-update there from the gradient at each pixel alone:
 // SR reads g = A^T(A x - y) computed beforehand (a.g), SPI evaluates h' in place.
 // x_in and x_out may be the same buffer.  Stores the tile's residual sums at
 // `partials` (two doubles).  All threads of a (32, 8) block must call it.
 template <int KIND>  // 0 super-resolution, 1 single-photon
-__device__ __forceinline__ void combine_update_body(const Cover& cv, const EpilogueArgs& a, int y0, int x0,
+__device__ __forceinline__ void combine_update_body(const Cover& cv, const EpilogueArgs& a, int do_x, int y0, int x0,
                                                     double* partials) {
     const int H = a.H, W = a.W;
     const TileCover tc = tile_cover(cv, y0, x0);
@@ -207,9 +122,9 @@ __device__ __forceinline__ void combine_update_body(const Cover& cv, const Epilo
         ts[r] = ok ? a.t[q] : 0.f;
         vo[r] = ok ? a.v[q] : 0.f;
         uo[r] = ok ? a.u[q] : 0.f;
-        xs[r] = (ok && a.do_x) ? a.x_in[q] : 0.f;
-        gs[r] = (ok && KIND == 0 && a.do_x) ? a.g[q] : 0.f;
-        k1[r] = (ok && KIND == 1 && a.do_x) ? (int)a.counts[q] : 0;
+        xs[r] = (ok && do_x) ? a.x_in[q] : 0.f;
+        gs[r] = (ok && KIND == 0 && do_x) ? a.g[q] : 0.f;
+        k1[r] = (ok && KIND == 1 && do_x) ? (int)a.counts[q] : 0;
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -232,7 +147,7 @@ __device__ __forceinline__ void combine_update_body(const Cover& cv, const Epilo
         const float dp = un - uo[r], dd = vn - vo[r];  // x - v and v - v_prev
         sp = fmaf(dp, dp, sp);
         sd = fmaf(dd, dd, sd);
-        if (a.do_x) {
+        if (do_x) {
             const float g = KIND == 0 ? gs[r] : spi_hprime(xs[r], k1[r], a.K, a.eta, a.eps);
             const float xn = project(a.mu * (a.alpha * xs[r] + a.rho * (vn - un) - g), a.constraint);
             a.x_out[q] = xn;

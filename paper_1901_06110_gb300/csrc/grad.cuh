@@ -1,0 +1,141 @@
+// Gradient of the super-resolution data term f(x) = 1/2 ||y - A x||^2 (Sec. 2 and
+// Eq. dataterm, with the sign of the gradient read as A^T(A x - y)):
+//   g = A^T (A x - y),  A = keep the even-index pixels of a periodic, separable
+//   (2R + 1) x (2R + 1) blur.
+// sr_grad_tile computes a 32 x 32 tile of g with one (256-thread) block.  The x
+// values within reach of the tile are staged in shared memory once; then four
+// separable passes follow: the blur along rows at the even columns, the blur along
+// columns at the even rows minus y (the residual A x - y on the low-resolution
+// window), the column half of A^T and its row half.  The blur radius is a template
+// parameter, so every tap loop is unrolled and the taps are read from the
+// kernel parameters.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace dsg {
+
+constexpr int kGT = 32;  // output tile side
+
+template <int R>
+struct GradDims {
+    static constexpr int G = R > 0 ? R : 1;              // staging margin
+    static constexpr int L = (kGT - 1 + 2 * G) / 2 + 2;  // low-resolution rows (cols) of the window, upper bound
+    static constexpr int S = 2 * (L - 1) + 2 * G + 1;    // staged x rows (cols)
+};
+
+template <int R>
+struct GradSmem {
+    float X[GradDims<R>::S][GradDims<R>::S];
+    float Hs[GradDims<R>::S][GradDims<R>::L];
+    float Rl[GradDims<R>::L][GradDims<R>::L];
+    float V[kGT][GradDims<R>::L];
+    int rows[GradDims<R>::S], cols[GradDims<R>::S], lrows[GradDims<R>::L], lcols[GradDims<R>::L];
+};
+
+// g on the 32 x 32 tile at (y0, x0); all 256 threads of the block call it
+template <int R>
+__device__ __forceinline__ void sr_grad_tile(GradSmem<R>& sm, const float* __restrict__ x, const float* __restrict__ y,
+                                             int H, int W, const BlurTaps& taps, float* __restrict__ g, int y0,
+                                             int x0) {
+    using Dm = GradDims<R>;
+    constexpr int G = Dm::G, L = Dm::L, S = Dm::S;
+    auto& X = sm.X;
+    auto& Hs = sm.Hs;
+    auto& Rl = sm.Rl;
+    auto& V = sm.V;
+    int* rows = sm.rows;
+    int* cols = sm.cols;
+    int* lrows = sm.lrows;
+    int* lcols = sm.lcols;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int h = H >> 1, w = W >> 1;
+    // low-resolution window: rows qy_lo .. qy_lo + L - 1 (and columns likewise); the
+    // staged x rows start at high-resolution row 2 qy_lo - G
+    const int qy_lo = (y0 - G) >> 1, qx_lo = (x0 - G) >> 1;
+    for (int a = tid; a < S; a += 256) {
+        rows[a] = wrap_index(2 * qy_lo - G + a, H);
+        cols[a] = wrap_index(2 * qx_lo - G + a, W);
+    }
+    for (int l = tid; l < L; l += 256) {
+        lrows[l] = wrap_index(qy_lo + l, h);
+        lcols[l] = wrap_index(qx_lo + l, w);
+    }
+    __syncthreads();
+    // every load of this thread is issued before the first store to shared memory
+    constexpr int kLoads = (S * S + 255) / 256;
+    float xv[kLoads];
+#pragma unroll
+    for (int k = 0; k < kLoads; ++k) {
+        const int i = tid + 256 * k;
+        if (i < S * S) {
+            const int a = i / S, b = i - a * S;
+            xv[k] = __ldg(x + (size_t)rows[a] * W + cols[b]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kLoads; ++k) {
+        const int i = tid + 256 * k;
+        if (i < S * S) {
+            const int a = i / S, b = i - a * S;
+            X[a][b] = xv[k];
+        }
+    }
+    __syncthreads();
+    // row blur at the even columns: Hs[a][c] = sum_b t_b x(staged row a, 2 (qx_lo + c) - b)
+    for (int i = tid; i < S * L; i += 256) {
+        const int a = i / L, c = i - a * L;
+        float acc = 0.f;
+#pragma unroll
+        for (int b = -R; b <= R; ++b) acc = fmaf(taps.t[b + R], X[a][2 * c + G - b], acc);
+        Hs[a][c] = acc;
+    }
+    __syncthreads();
+    // column blur at the even rows minus the observation: r = A x - y
+    for (int i = tid; i < L * L; i += 256) {
+        const int l = i / L, c = i - l * L;
+        const float yv = __ldg(y + (size_t)lrows[l] * w + lcols[c]);
+        float acc = 0.f;
+#pragma unroll
+        for (int a = -R; a <= R; ++a) acc = fmaf(taps.t[a + R], Hs[2 * l + G - a][c], acc);
+        Rl[l][c] = acc - yv;
+    }
+    __syncthreads();
+    // column half of A^T: V(p, c) = sum_{a : p + a even} t_a r((p + a) / 2, c).  Rows
+    // 2 pr (even p: even a) and 2 pr + 1 (odd p: odd a) are done together, so each
+    // tap set is fixed at compile time; y0 is even.
+    for (int pr = warp; pr < kGT / 2; pr += 8) {
+        const int base = (y0 >> 1) + pr - qy_lo;  // window row of (y0 + 2 pr) / 2
+        for (int c = lane; c < L; c += 32) {
+            float e = 0.f, o = 0.f;
+#pragma unroll
+            for (int a = -R; a <= R; ++a) {
+                if ((a & 1) == 0)
+                    e = fmaf(taps.t[a + R], Rl[base + (a >> 1)][c], e);
+                else
+                    o = fmaf(taps.t[a + R], Rl[base + ((a + 1) >> 1)][c], o);
+            }
+            V[2 * pr][c] = e;
+            V[2 * pr + 1][c] = o;
+        }
+    }
+    __syncthreads();
+    // row half of A^T at columns 2k (even b) and 2k + 1 (odd b)
+    const int k = lane & 15;
+    const int cbase = (x0 >> 1) + k - qx_lo;  // window column of (x0 + 2 k) / 2
+    for (int py = 2 * warp + (lane >> 4); py < kGT; py += 16) {
+        float e = 0.f, o = 0.f;
+#pragma unroll
+        for (int b = -R; b <= R; ++b) {
+            if ((b & 1) == 0)
+                e = fmaf(taps.t[b + R], V[py][cbase + (b >> 1)], e);
+            else
+                o = fmaf(taps.t[b + R], V[py][cbase + ((b + 1) >> 1)], o);
+        }
+        const int pi = y0 + py, pj = x0 + 2 * k;
+        if (pi < H && pj < W) *reinterpret_cast<float2*>(g + (size_t)pi * W + pj) = make_float2(e, o);
+    }
+}
+
+}  // namespace dsg

@@ -93,7 +93,7 @@ struct dsgnlm {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // batched Algorithm 1 workspace (used when this handle leads a batch), and the
     // batch's step sequence as a CUDA graph with the values it was recorded for
-    DevBuf b_inst, b_epi, b_work1, b_work2, b_hist;
+    DevBuf b_inst, b_epi, b_work1, b_work2, b_work3, b_hist;
     cudaGraph_t b_graph = nullptr;
     cudaGraphExec_t b_exec = nullptr;
     std::vector<unsigned char> b_key;
@@ -161,6 +161,7 @@ struct dsgnlm {
         b_epi.release();
         b_work1.release();
         b_work2.release();
+        b_work3.release();
         b_hist.release();
         rlo.release();
         partials.release();

@@ -170,7 +170,7 @@ struct EpilogueArgs {
     const float* x_in;   // x of the next update (SR, fused form: read in halos)
     float* x_out;        // its result (SR, fused form: another buffer; otherwise may equal x_in)
     const float* y;      // SR observation
-    const float* g;      // SR, per-pixel form: A^T (A x_in - y), computed beforehand
+    float* g;            // SR, per-pixel form: A^T (A x_in - y), computed beforehand
     BlurTaps taps;
     const uint8_t* counts;  // SPI
     int K;
@@ -186,8 +186,8 @@ int combine_xupdate_blocks(int H, int W);  // epilogue tiles (kXH x kXW) of an i
 cudaError_t launch_combine_update(int kind, const TmaPlan& plan, int rs, const EpilogueArgs& args,
                                   cudaStream_t st);
 
-// Batched Algorithm 1 (batched.cu).  a.x_in / a.x_out hold the two x buffers of the
-// image (the caller's and the handle's); the kernels alternate them per iteration.
+// Batched Algorithm 1 (batched.cu).  x is updated in place (a.x_in == a.x_out); SR
+// reads the gradient of the current x from a.g.
 struct BatchEpi {
     EpilogueArgs a;
     Cover cv;
@@ -198,6 +198,8 @@ struct BatchEpi {
 cudaError_t launch_batched_xupdate0(int kind, const BatchEpi* insts, const int4* work, int nwork, cudaStream_t st);
 cudaError_t launch_batched_combine(int kind, const BatchEpi* insts, const int4* work, int nwork, int it, int last,
                                    cudaStream_t st);
+// g of every image on (image, 32 x 32 tile) work items; every image with blur radius blur_r
+cudaError_t launch_batched_grad(int blur_r, const BatchEpi* insts, const int4* work, int nwork, cudaStream_t st);
 cudaError_t launch_batched_reduce(const BatchEpi* insts, int count, double* hist, int iters, cudaStream_t st);
 
 }  // namespace dsg

@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--profile-case", choices=["batched-f16-4x512", "unrolled-1x256"], default=None,
+                    help="run one small case twice for an ncu capture (no timing, no JSON line)")
     ap.add_argument("--only-batched", default=None,
                     help="comma-separated batched variants to time alone (plain_f32, batched_f32, batched_f16, "
                          "batched_bf16); skips the main workload")
@@ -661,8 +663,56 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(case: str):
+    """Small cases for ncu captures of kernels the main workload does not show as
+    plain launches: the batched FP16 form (4 x 512^2, 6 iterations, one offset slice)
+    and the differentiable form (1 x 256^2, whose balance epilogues are direct
+    launches rather than balance-graph nodes)."""
+    import torch
+
+    import synthetic
+    from paper_1901_06110_gb300 import build as lib_build
+    from paper_1901_06110_gb300 import dsgnlm as D
+    from paper_1901_06110_gb300 import pipeline
+    lib_build.build()
+    if case == "batched-f16-4x512":
+        wl = synthetic.workload("batch64")
+        shapes = [(512, 512)] * 4
+        ys = []
+        for i, (H, W) in enumerate(shapes):
+            xt = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], wl["seed"] + i)).cuda()
+            nz = torch.from_numpy(synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], wl["seed"] + i)).cuda()
+            ys.append(D.lpnp_sr_observe(xt, nz, wl["blur_sigma"], wl["blur_r"]))
+        b = pipeline.BatchSolver(shapes, pipeline.Params.from_workload(wl, weight_dtype="f16", iters=6))
+        b.slices = 1
+        for _ in range(2):
+            b.run(ys)
+        torch.cuda.synchronize()
+        b.close()
+    else:
+        from paper_1901_06110_gb300.autograd import UnrollParams, unrolled_sr
+        wl = synthetic.workload("unroll8x256")
+        H, W = wl["H"], wl["W"]
+        xt = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], wl["seed"])).cuda()
+        nz = torch.from_numpy(synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], wl["seed"])).cuda()
+        y0 = D.lpnp_sr_observe(xt, nz, wl["blur_sigma"], wl["blur_r"])
+        g0 = D.lpnp_sr_guide(y0)
+        for _ in range(2):
+            y = y0[None].clone().requires_grad_(True)
+            g = g0[None].clone().requires_grad_(True)
+            h = torch.tensor(wl["h"], dtype=torch.float64, requires_grad=True)
+            rho = torch.tensor(wl["rho"], dtype=torch.float64, requires_grad=True)
+            x = unrolled_sr(y, g, h, rho, UnrollParams(patch_r=wl["patch_r"], search_r=wl["search_r"],
+                                                       balance_passes=4, iters=wl["iters"]))
+            ((x - xt) ** 2).mean().backward()
+        torch.cuda.synchronize()
+
+
 def main():
     args = _args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.only_batched:
         import torch
         from paper_1901_06110_gb300 import build as lib_build

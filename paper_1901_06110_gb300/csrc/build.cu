@@ -10,12 +10,16 @@
 //   V(p) = sum_{|t_y| <= r_p} (g(p + (t_y, 0)) - g(p + (t_y, 0) + o))^2
 //          vertical patch sums, as a sliding window down a column over 8
 //          consecutive outputs (one direct sum, then one add and one subtract
-//          per output), one thread per column, and
-//   D(s) = sum_{|t_x| <= r_p} V(s + (0, t_x))   horizontal patch sums,
+//          per output), one thread per column and segment, and
+//   D(s) = sum_{|t_x| <= r_p} V(s + (0, t_x))   horizontal patch sums, as a
+//          sliding window along a row over 4 consecutive outputs per thread
+//          (16-byte shared-memory loads, one 4-wide store per row),
 //   K1(s, s + o) = Lambda(o / (N_s + 1)) exp(-D(s) / (2 N_p^2 h^2)),  0 if s + o is
 //   outside the image,
-// and writes the plane row-contiguously.  Segments sit at fixed positions of the
-// image grid (tiles are aligned to 8), so results do not depend on scheduling.
+// and writes the plane row-contiguously.  V is double-buffered: the vertical sums
+// of offset k + 1 are formed in the same interval as the horizontal sums of
+// offset k, so each offset costs one barrier.  Segments sit at fixed positions of
+// the image grid (tiles are aligned to 8), so results do not depend on scheduling.
 #include "common.cuh"
 #include "internal.h"
 
@@ -26,16 +30,45 @@ namespace {
 constexpr int kTW = 64;    // tile columns
 constexpr int kTH = 32;    // tile rows
 constexpr int kThreads = 256;
-constexpr int kSeg = 8;    // outputs per sliding-window segment
+constexpr int kSeg = 8;    // outputs per vertical sliding-window segment
+constexpr int kHW = 4;     // outputs per horizontal sliding window (one thread, one row)
 constexpr int kChunk = 22; // offsets per CTA
 constexpr int kMaxRp = 10; // DSGNLM_MAX_PATCH_R
+
+// row length of the vertical sums: the tile plus the patch radius on both sides,
+// rounded up so that every window start is 16-byte aligned and a window's last
+// 16-byte load stays inside the row
+__host__ __device__ constexpr int v_pitch(int rp) { return ((kTW + 2 * rp + 3) / 4) * 4 + 4; }
+
+template <typename WT>
+__device__ __forceinline__ void store4(WT* p, const float (&w)[kHW]);
+template <>
+__device__ __forceinline__ void store4<float>(float* p, const float (&w)[kHW]) {
+    *reinterpret_cast<float4*>(p) = make_float4(w[0], w[1], w[2], w[3]);
+}
+template <>
+__device__ __forceinline__ void store4<__half>(__half* p, const float (&w)[kHW]) {
+    __half2 a = __floats2half2_rn(w[0], w[1]), b = __floats2half2_rn(w[2], w[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned*>(&a);
+    u.y = *reinterpret_cast<unsigned*>(&b);
+    *reinterpret_cast<uint2*>(p) = u;
+}
+template <>
+__device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16* p, const float (&w)[kHW]) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(w[0], w[1]), b = __floats2bfloat162_rn(w[2], w[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned*>(&a);
+    u.y = *reinterpret_cast<unsigned*>(&b);
+    *reinterpret_cast<uint2*>(p) = u;
+}
 
 // RP >= 0: patch radius known at compile time; RP < 0: runtime radius rp_rt.
 template <typename WT, int RP>
 __global__ void __launch_bounds__(kThreads)
 build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, float c,
              WT* __restrict__ planes) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     const int rp = RP >= 0 ? RP : rp_rt;
     const int nh = num_half_offsets(rs);
     const int y0 = blockIdx.y * kTH;
@@ -47,15 +80,18 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
     //               cols x0 - rp - rs .. x0 + TW + rp + rs - 1
     const int GH = kTH + 2 * rp + rs;
     const int GW = kTW + 2 * rp + 2 * rs;
-    const int EW = kTW + 2 * rp;
-    float* G = smem;
-    float* V = G + GH * GW;  // vertical patch sums, [kTH][EW]
-    int* rows = reinterpret_cast<int*>(V + kTH * EW);
+    const int EW = kTW + 2 * rp;  // vertical sums per row: tile columns -rp .. TW + rp - 1
+    const int VP = v_pitch(rp);
+    float* V0 = smem;                 // two buffers of vertical sums, [kTH][VP] each
+    float* V1 = V0 + kTH * VP;
+    float* G = V1 + kTH * VP;
+    int* rows = reinterpret_cast<int*>(G + GH * GW);
     int* cols = rows + GH;
 
     const int tid = threadIdx.x;
     for (int a = tid; a < GH; a += kThreads) rows[a] = sym_index(y0 - rp + a, H);
     for (int b = tid; b < GW; b += kThreads) cols[b] = sym_index(x0 - rp - rs + b, W);
+    for (int i = tid; i < 2 * kTH * VP; i += kThreads) V0[i] = 0.f;  // the row tails are read, never used
     __syncthreads();
     {
         const int tx = tid & 63, ty = tid >> 6;
@@ -70,16 +106,16 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
     const size_t plane = (size_t)H * Wp;
     const float inv_hat = 1.0f / (float)(rs + 1);
     const int n_vtask = EW * (kTH / kSeg);
-    const int hx = tid & 63, hy = tid >> 6;  // horizontal phase: column, 8-row segment
-    for (int k = k_begin; k < k_end; ++k) {
+    // V(i, cc) = sum_{t_y} (g(i + t_y, cc - rp) - g(i + t_y + o_y, cc - rp + o_x))^2 for the
+    // tile's rows: one column and 8 consecutive output rows per task, as a sliding
+    // window down the column (staged row r0 + t is image row y0 - rp + r0 + t)
+    auto vertical = [&](int k, float* V) {
         int oy, ox;
         half_offset(k, rs, oy, ox);
-        // V(i, c) = sum_{t_y} (g(i + t_y, c) - g(i + t_y + o_y, c + o_x))^2: one column and
-        // 8 consecutive output rows per task, as a sliding window down the column
         for (int task = tid; task < n_vtask; task += kThreads) {
             const int seg = task / EW;
             const int cc = task - seg * EW;
-            const int r0 = seg * kSeg;  // first output row; staged row r0 + t is image row y0 - rp + r0 + t
+            const int r0 = seg * kSeg;
             const float* ga = G + r0 * GW + cc + rs;
             const float* gb = G + (r0 + oy) * GW + cc + rs + ox;
             float e[kSeg + 2 * kMaxRp];
@@ -96,37 +132,65 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
                 if (RP < 0 && t > 2 * rp) break;
                 acc += e[t];
             }
-            V[r0 * EW + cc] = acc;
+            V[r0 * VP + cc] = acc;
 #pragma unroll
             for (int q = 1; q < kSeg; ++q) {
                 acc += e[q + 2 * rp] - e[q - 1];
-                V[(r0 + q) * EW + cc] = acc;
+                V[(r0 + q) * VP + cc] = acc;
             }
         }
-        __syncthreads();
+    };
+    // horizontal phase: thread = 4 consecutive columns (group hg) of rows hr and hr + 16
+    const int hg = tid & 15, hr = tid >> 4;
+    const int j0 = x0 + kHW * hg;
+    constexpr int kNV = (kHW + 2 * (RP >= 0 ? RP : kMaxRp) + 3) / 4;  // 16-byte loads per window
+    const int nv = (kHW + 2 * rp + 3) / 4;
+
+    if (k_begin < k_end) vertical(k_begin, V0);
+    __syncthreads();
+    for (int k = k_begin; k < k_end; ++k) {
+        float* Vc = ((k - k_begin) & 1) ? V1 : V0;
+        float* Vn = ((k - k_begin) & 1) ? V0 : V1;
+        if (k + 1 < k_end) vertical(k + 1, Vn);  // in the same interval as the sums below
+        int oy, ox;
+        half_offset(k, rs, oy, ox);
         // D(i, j) = sum_{t_x} V(i, j + t_x), then the weight
         const float hat = (1.0f - fabsf((float)oy) * inv_hat) * (1.0f - fabsf((float)ox) * inv_hat);
         WT* out = planes + (size_t)k * plane;
-        const int j = x0 + hx;
-        const bool col_ok = j < W && j + ox >= 0 && j + ox < W;
 #pragma unroll
-        for (int q = 0; q < kSeg; ++q) {
-            const int r = hy * kSeg + q;
-            const float* vr = V + r * EW + hx;
+        for (int rr = 0; rr < kTH / 16; ++rr) {
+            const int r = hr + 16 * rr;
+            const int i = y0 + r;
+            const float4* vr = reinterpret_cast<const float4*>(Vc + r * VP + kHW * hg);
+            float v[4 * kNV];
+#pragma unroll
+            for (int q = 0; q < kNV; ++q) {
+                if (RP < 0 && q >= nv) break;
+                const float4 f = vr[q];
+                v[4 * q] = f.x;
+                v[4 * q + 1] = f.y;
+                v[4 * q + 2] = f.z;
+                v[4 * q + 3] = f.w;
+            }
             float D = 0.f;
 #pragma unroll
             for (int t = 0; t <= 2 * (RP >= 0 ? RP : kMaxRp); ++t) {
                 if (RP < 0 && t > 2 * rp) break;
-                D += vr[t];
+                D += v[t];
             }
-            const int i = y0 + r;
-            if (i < H && j < W) {
-                const bool inside = col_ok && (i + oy < H);
-                const float w = inside ? hat * __expf(-D * c) : 0.f;
-                out[(size_t)i * Wp + j] = from_f32<WT>(w);
+            float w[kHW];
+#pragma unroll
+            for (int jj = 0; jj < kHW; ++jj) {
+                if (jj > 0) D += v[jj + 2 * rp] - v[jj - 1];
+                const int j = j0 + jj;
+                const bool inside = i < H && j < W && j + ox >= 0 && j + ox < W && i + oy < H;
+                w[jj] = inside ? hat * __expf(-D * c) : 0.f;
             }
+            // planes have a pitch of a multiple of 8: the 4 outputs are all inside the
+            // row's pitch or all outside it
+            if (i < H && j0 < Wp) store4<WT>(out + (size_t)i * Wp + j0, w);
         }
-        __syncthreads();  // V is rewritten by the next offset
+        __syncthreads();  // Vc is rewritten two offsets on; Vn is complete
     }
 }
 
@@ -136,8 +200,7 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
     const int nh = num_half_offsets(rs);
     if (nh == 0) return cudaSuccess;
     const int GH = kTH + 2 * rp + rs, GW = kTW + 2 * rp + 2 * rs;
-    const int EW = kTW + 2 * rp;
-    const size_t smem = sizeof(float) * (size_t)(GH * GW + kTH * EW) + sizeof(int) * (GH + GW);
+    const size_t smem = sizeof(float) * (size_t)(GH * GW + 2 * kTH * v_pitch(rp)) + sizeof(int) * (GH + GW);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(build_kernel<WT, RP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

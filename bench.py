@@ -49,6 +49,10 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--table1", action="store_true",
+                    help="add Table 1 in synthetic form: one fast DSG-NLM filtering of a 256x256 image for "
+                         "patch sizes 11-29 and both readings of N_s = 21 (and, in the CPU-baseline leg, the "
+                         "brute-force oracle on a 64x64 crop)")
     ap.add_argument("--profile-case", choices=["batched-f16-4x512", "unrolled-1x256"], default=None,
                     help="run one small case twice for an ncu capture (no timing, no JSON line)")
     ap.add_argument("--only-batched", default=None,
@@ -446,6 +450,75 @@ def run_adaptive(steps: int, warmup: int, flush):
     return out
 
 
+TABLE1_NP = (11, 17, 23, 29)
+TABLE1_NS = (10, 21)  # a 21x21 window, or N_s = 21 as the window radius (43x43)
+
+
+def _table1_image(side: int):
+    import numpy as np
+
+    import synthetic
+    x = synthetic.ground_truth(side, side, 12, True, 1006)
+    noise = synthetic.gaussian_noise((side, side), 0.05, 1006)
+    return np.clip(x + noise, 0.0, 1.0).astype(np.float32)
+
+
+def run_table1(reps: int = 5):
+    """Table 1 in synthetic form, GPU side: one filtering with the fast DSG-NLM of
+    Algorithm 2 (weight build, the paper's single normalisation as one balancing
+    update with the closure, one application of W) on a 256x256 noisy image, for
+    patch sizes 11, 17, 23, 29 and both readings of N_s = 21.  The paper's cost
+    claim is that this time does not grow with the patch size."""
+    import torch
+
+    from paper_1901_06110_gb300 import dsgnlm as D
+    img = torch.from_numpy(_table1_image(256)).cuda()
+    rows = []
+    for rs in TABLE1_NS:
+        for npatch in TABLE1_NP:
+            rp = (npatch - 1) // 2
+            den = D.dsgnlm_create("f32")
+            times, builds = [], []
+            for rep in range(2 + reps):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record()
+                D.dsgnlm_build(den, img, rp, rs, 0.1)
+                e[1].record()
+                D.dsgnlm_balance(den, 0.0, 1)
+                D.dsgnlm_apply(den, img)
+                e[2].record()
+                e[2].synchronize()
+                if rep >= 2:
+                    times.append(e[0].elapsed_time(e[2]))
+                    builds.append(e[0].elapsed_time(e[1]))
+            den.close()
+            rows.append({"N_p": npatch, "search_window": f"{2 * rs + 1}x{2 * rs + 1}", "gpu_ms": sum(times) / reps,
+                         "gpu_build_ms": sum(builds) / reps})
+    return {"image": "256x256 synthetic (12 shapes + texture, noise 0.05)", "h": 0.1,
+            "filtering": "build + one normalisation (Eq. S2, S3) + one application of W", "rows": rows}
+
+
+def oracle_table1(rows):
+    """Table 1, brute-force side: the FP64 oracle (direct patch sums over all
+    N_p^2 pixels of every pair, explicit sparse matrix) on a 64x64 crop of the
+    same image; its time scales with the pixel count, so the 256x256 figure is x16."""
+    import numpy as np
+
+    from oracle import dsgnlm as odsg
+    crop = _table1_image(256)[:64, :64].astype(np.float64)
+    for row in rows:
+        rs = (int(row["search_window"].split("x")[0]) - 1) // 2
+        rp = (row["N_p"] - 1) // 2
+        t0 = time.perf_counter()
+        K1 = odsg.kernel_matrix(crop, rp, rs, 0.1)
+        d, _, _ = odsg.sinkhorn(K1, 0.0, 1)
+        Wm, _ = odsg.dsg_matrix(K1, d)
+        odsg.denoise(Wm, crop)
+        secs = time.perf_counter() - t0
+        row["oracle_64x64_s"] = secs
+        row["oracle_256x256_s_scaled"] = 16 * secs
+
+
 def run_residual_tables(iters: int = 250):
     """Tables 2-3 in synthetic form: after `iters` iterations of Algorithm 1 on the
     512x512 SR and SPI workloads, the RMS primal and dual residuals and the PSNR for
@@ -642,6 +715,8 @@ def run_ours(args):
         "e2e": {"value": world * n_mpix / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": y.numel() * 4, "d2h_bytes_per_step": H * W * 4},
     }
+    if args.table1:
+        line["table1"] = run_table1()
     if not args.no_batched:
         line["batched"] = run_batched(args.batched_steps, 1, flush)
         line["unrolled"] = run_unrolled(args.batched_steps, 1, flush)
@@ -656,6 +731,8 @@ def run_ours(args):
                                 "sample": f"FP64 NumPy/SciPy oracle, one {side}x{side} instance of the "
                                           f"workload ({secs:.1f} s, single-threaded)"}
         line["error_vs_oracle"] = _error_vs_oracle(inst, x_ref, wl)
+        if "table1" in line:
+            oracle_table1(line["table1"]["rows"])
     if rank == 0:
         print(json.dumps(line))
     solver.close()

@@ -56,7 +56,7 @@ typedef enum dsgnlm_status {
 enum { DSGNLM_F32 = 0, DSGNLM_F16 = 1, DSGNLM_BF16 = 2 };
 
 /* limits of the kernels (shared-memory tiles are sized from them) */
-enum { DSGNLM_MAX_PATCH_R = 10, DSGNLM_MAX_SEARCH_R = 24 };
+enum { DSGNLM_MAX_PATCH_R = 14, DSGNLM_MAX_SEARCH_R = 24 };
 
 /* ---------------------------------------------------------------------------
  * Denoiser handle
@@ -77,7 +77,7 @@ dsgnlm_status dsgnlm_set_stream(dsgnlm_t h, void* stream);
  * distances of Sec. 3 whose cost does not grow with the patch size).
  *
  * guide      device, [H][W] FP32: the image the patches are taken from.
- * patch_r    patch radius: patches are N_p x N_p with N_p = 2*patch_r + 1 (0..10).
+ * patch_r    patch radius: patches are N_p x N_p with N_p = 2*patch_r + 1 (0..14).
  * search_r   search radius N_s: the window is (2 N_s + 1)^2, clipped at the image
  *            border (0..24).
  * bandwidth  h > 0: k_{s,r} = exp(-||P_s - P_r||^2 / (2 N_p^2 h^2)).

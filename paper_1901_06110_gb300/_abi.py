@@ -13,7 +13,7 @@ OK, EINVAL, ENOMEM, ECUDA, NOT_BUILT, NOT_BALANCED, NOT_CONVERGED, STALLED, TIME
 F32, F16, BF16 = 0, 1, 2
 SR2, SPI = 0, 1
 C_NONE, C_NONNEG, C_BOX01 = 0, 1, 2
-MAX_PATCH_R, MAX_SEARCH_R = 10, 24
+MAX_PATCH_R, MAX_SEARCH_R = 14, 24
 PROF_BUILD, PROF_BALANCE, PROF_APPLY, PROF_XUPDATE = range(4)
 
 

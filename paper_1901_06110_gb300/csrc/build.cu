@@ -33,7 +33,7 @@ constexpr int kThreads = 256;
 constexpr int kSeg = 8;    // outputs per vertical sliding-window segment
 constexpr int kHW = 4;     // outputs per horizontal sliding window (one thread, one row)
 constexpr int kChunk = 22; // offsets per CTA
-constexpr int kMaxRp = 10; // DSGNLM_MAX_PATCH_R
+constexpr int kMaxRp = 14; // DSGNLM_MAX_PATCH_R
 
 // row length of the vertical sums: the tile plus the patch radius on both sides,
 // rounded up so that every window start is 16-byte aligned and a window's last
@@ -221,6 +221,9 @@ cudaError_t launch_build_t(const float* guide, int H, int W, int rp, int rs, flo
         case 3: return launch_build_rp<WT, 3>(guide, H, W, rp, rs, c, planes, st);
         case 4: return launch_build_rp<WT, 4>(guide, H, W, rp, rs, c, planes, st);
         case 5: return launch_build_rp<WT, 5>(guide, H, W, rp, rs, c, planes, st);
+        case 8: return launch_build_rp<WT, 8>(guide, H, W, rp, rs, c, planes, st);    // 17 x 17 patches
+        case 11: return launch_build_rp<WT, 11>(guide, H, W, rp, rs, c, planes, st);  // 23 x 23
+        case 14: return launch_build_rp<WT, 14>(guide, H, W, rp, rs, c, planes, st);  // 29 x 29
         default: return launch_build_rp<WT, -1>(guide, H, W, rp, rs, c, planes, st);
     }
 }

@@ -61,7 +61,7 @@ def test_host_side_argument_checks(lib):
         fake = ctypes.c_void_p(0x10000)  # never dereferenced: rejected before any CUDA call
         assert lib.dsgnlm_build(h, None, 8, 8, 1, 1, 0.1) == _abi.EINVAL
         assert lib.dsgnlm_build(h, fake, 0, 8, 1, 1, 0.1) == _abi.EINVAL
-        assert lib.dsgnlm_build(h, fake, 8, 8, 11, 1, 0.1) == _abi.EINVAL
+        assert lib.dsgnlm_build(h, fake, 8, 8, 15, 1, 0.1) == _abi.EINVAL
         assert lib.dsgnlm_build(h, fake, 8, 8, 1, 25, 0.1) == _abi.EINVAL
         assert lib.dsgnlm_build(h, fake, 8, 8, 1, 1, 0.0) == _abi.EINVAL
         assert lib.dsgnlm_build(h, ctypes.c_void_p(0x10004), 8, 8, 1, 1, 0.1) == _abi.EINVAL

@@ -33,6 +33,7 @@ CASES = [
     (35, 140, 2, 12, 0.1),  # two column tiles, largest compiled radius
     (26, 29, 2, 9, 0.1),    # radius without a compiled TMA kernel: generic gather path
     (40, 300, 3, 10, 0.08),  # three column tiles, ragged, split offsets
+    (30, 48, 14, 3, 0.3),    # largest patch (29 x 29): generic-radius build
 ]
 
 

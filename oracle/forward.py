@@ -14,14 +14,20 @@ in pixel i, f = sum_i h(x_i) (Eq. obj) with
 h(t) = K0 eta t / K - K1 log(1 - exp(-eta t / K)) and h' as printed.  h' is
 unbounded at t = 0, so the gradient is evaluated at max(x, eps).
 
+Super-resolution with a symmetric boundary (the standard-vs-linearized comparison
+of Sec. 4.1): the blur reads x extended by half-sample symmetric reflection,
+(A_sym x)(q) = sum_t h(t) x(sym(2q - t)); its adjoint sends each term back to
+sym(2q - t).
+
 Guides (inputs of the fixed DSG-NLM, not defined by the paper): the SR guide is
 a 2x Keys cubic (a = -0.5) interpolation of y with periodic wrap, low-resolution
 sample j sitting at high-resolution 2j; the SPI guide is the per-pixel maximum-
 likelihood intensity -(K/eta) log(1 - K1/K), clipped to [0, 1], smoothed by a
 3x3 mean with symmetric reflection.
 
-Parity status: ``sr_forward``/``sr_adjoint`` pinned by the adjoint identity and
-by an explicit dense matrix built from the convolution definition; ``sr_grad`` by
+Parity status: ``sr_forward``/``sr_adjoint`` and their symmetric-boundary forms
+pinned by the adjoint identity and by explicit dense matrices built from the
+convolution definitions; ``sr_grad`` by
 finite differences of ``sr_data``; ``sr_lipschitz`` by power iteration;
 ``spi_hprime`` by finite differences of ``spi_h`` and by h'(MLE) = 0;
 ``keys_up2`` by exact reproduction of quadratics; ``spi_observe``/``spi_counts``
@@ -97,6 +103,50 @@ def sr_lipschitz(H: int, W: int, psf: np.ndarray) -> float:
     delta[0, 0] = 1.0
     col = sr_forward(sr_adjoint(delta, psf), psf)
     return float(np.max(np.real(np.fft.fft2(col))))
+
+
+def _sym(i, n: int):
+    """Half-sample symmetric reflection of index i into [0, n)."""
+    m = np.mod(np.asarray(i), 2 * n)
+    return np.where(m < n, m, 2 * n - 1 - m)
+
+
+def sr_forward_sym(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
+    """A_sym x: the blur of x extended by symmetric reflection, then the pixels (2i, 2j):
+    (A_sym x)(q) = sum_t h(t) x(sym(2q - t))."""
+    x = np.asarray(x, dtype=np.float64)
+    H, W = x.shape
+    r = psf.shape[0] // 2
+    qi = 2 * np.arange(H // 2)
+    qj = 2 * np.arange(W // 2)
+    out = np.zeros((H // 2, W // 2))
+    for a in range(-r, r + 1):
+        rows = _sym(qi - a, H)
+        for b in range(-r, r + 1):
+            out += psf[a + r, b + r] * x[np.ix_(rows, _sym(qj - b, W))]
+    return out
+
+
+def sr_adjoint_sym(rlo: np.ndarray, psf: np.ndarray) -> np.ndarray:
+    """A_sym^T r: every term h(t) r(q) of A_sym goes back to pixel sym(2q - t)."""
+    rlo = np.asarray(rlo, dtype=np.float64)
+    h, w = rlo.shape
+    H, W = 2 * h, 2 * w
+    r = psf.shape[0] // 2
+    out = np.zeros((H, W))
+    qi = 2 * np.arange(h)
+    qj = 2 * np.arange(w)
+    for a in range(-r, r + 1):
+        rows = _sym(qi - a, H)
+        for b in range(-r, r + 1):
+            cols = _sym(qj - b, W)
+            np.add.at(out, (rows[:, None], cols[None, :]), psf[a + r, b + r] * rlo)
+    return out
+
+
+def sr_grad_sym(x, y, psf) -> np.ndarray:
+    """grad f(x) = A_sym^T (A_sym x - y) for the symmetric-boundary model."""
+    return sr_adjoint_sym(sr_forward_sym(x, psf) - np.asarray(y, dtype=np.float64), psf)
 
 
 def sr_observe(x_true, noise, psf) -> np.ndarray:

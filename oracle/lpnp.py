@@ -8,6 +8,12 @@ Algorithm 1, step by step, with mu = 1/(alpha + rho):
 D is DSG-NLM with a fixed W (the F-DSG-NLM variant of Sec. 4: W built once from a
 guide and then frozen).  The initial values are x = v = clip(guide, 0, 1), u = 0.
 
+Standard plug-and-play ADMM (the comparison of Sec. 4.1) replaces the linearized
+x-update by the minimisation of f(x) + rho/2 ||x - (v - u)||^2: for the SR data
+term, the linear system (A^T A + rho I) x = A^T y + rho (v - u), solved by
+conjugate gradients (a fixed number of steps, started from the current x), then
+the projection onto C.
+
 The adaptive variants of Sec. 4 rebuild W from the denoiser input x + u: in every
 iteration (A-DSG-NLM), or in the first ``adapt_iters`` iterations only, after
 which the last W is kept (F-DSG-NLM with the paper's adapt-then-freeze schedule,
@@ -17,7 +23,10 @@ Residuals (Sec. 4, Tables 2-3, following Boyd et al.): primal ||x - v|| / sqrt(n
 and dual rho ||v^k - v^{k-1}|| / sqrt(n), reported as RMS values.  PSNR uses peak 1
 over all pixels.
 
-Parity status: the adaptive loop with one adaptation equals the fixed loop with W
+Parity status: conjugate gradients with n steps on an n-dimensional system equal a
+direct solve; the standard loop with W = I and C = R^n is the proximal-point
+iteration x <- (A^T A + rho I)^{-1}(A^T y + rho x), checked against dense solves.
+The adaptive loop with one adaptation equals the fixed loop with W
 built from x^1 + u^0, and with a denoiser that ignores its input it equals the
 fixed loop.  With W = I and C = R^n the loop is gradient descent
 x <- x - mu grad f(x); that case is pinned against an explicit dense-matrix
@@ -96,6 +105,47 @@ def lpnp_solve_adaptive(grad_f, make_denoiser, x, v, u, alpha, rho, iters, adapt
             denoise = make_denoiser(z)
         v_prev = v
         v = denoise(z)
+        u = u + (x - v)
+        hist.append((rms(x - v), rho * rms(v - v_prev),
+                     None if x_true is None else psnr(x, x_true)))
+    return x, v, u, hist
+
+
+def conjugate_gradients(apply_m, b, x, iters):
+    """``iters`` steps of conjugate gradients for M x = b (M symmetric positive
+    definite, given as a function), from x (Hestenes-Stiefel)."""
+    x = np.asarray(x, dtype=np.float64).copy()
+    r = b - apply_m(x)
+    p = r.copy()
+    rs = float(np.sum(r * r))
+    for _ in range(iters):
+        if rs == 0.0:
+            break
+        mp = apply_m(p)
+        alpha = rs / float(np.sum(p * mp))
+        x = x + alpha * p
+        r = r - alpha * mp
+        rs_new = float(np.sum(r * r))
+        p = r + (rs_new / rs) * p
+        rs = rs_new
+    return x
+
+
+def admm_standard(forward_op, adjoint_op, y, denoise, x, v, u, rho, iters, cg_iters, constraint, x_true=None):
+    """Standard PnP-ADMM for f = 1/2 ||y - A x||^2: x <- Pi_C(CG solution of
+    (A^T A + rho I) x = A^T y + rho (v - u), started from x); v <- D(x + u);
+    u <- u + x - v.  Returns (x, v, u, history) as lpnp_solve."""
+    x = np.asarray(x, dtype=np.float64).copy()
+    v = np.asarray(v, dtype=np.float64).copy()
+    u = np.asarray(u, dtype=np.float64).copy()
+    aty = adjoint_op(np.asarray(y, dtype=np.float64))
+    apply_m = lambda p: adjoint_op(forward_op(p)) + rho * p
+    hist = []
+    for _ in range(iters):
+        x = conjugate_gradients(apply_m, aty + rho * (v - u), x, cg_iters)
+        x = project(x, constraint)
+        v_prev = v
+        v = denoise(x + u)
         u = u + (x - v)
         hist.append((rms(x - v), rho * rms(v - v_prev),
                      None if x_true is None else psnr(x, x_true)))

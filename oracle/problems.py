@@ -111,3 +111,37 @@ def _adaptive(wl, grad, g, x0, v0, u0, x_true, adapt_iters, iters, tol, maxit):
     out = lpnp.lpnp_solve_adaptive(grad, make_denoiser, x0, v0, u0, wl["alpha"], wl["rho"],
                                    wl["iters"] if iters is None else iters, adapt_iters, lpnp.BOX01, x_true)
     return dict(guide=g, infos=infos, W_last=mats[-1], x=out[0], v=out[1], u=out[2], hist=out[3])
+
+
+def sr_instance_sym(wl: dict, H: int | None = None, W: int | None = None, seed: int | None = None):
+    """Ground truth and FP32 observation y = A_sym x + n for the symmetric-boundary model."""
+    H = wl["H"] if H is None else H
+    W = wl["W"] if W is None else W
+    seed = wl["seed"] if seed is None else seed
+    x_true = synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], seed)
+    noise = synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], seed)
+    psf = forward.gaussian_psf(wl["blur_sigma"], wl["blur_r"])
+    y = (forward.sr_forward_sym(x_true, psf) + noise.astype(np.float64)).astype(np.float32)
+    return dict(x_true=x_true, noise=noise, y=y, psf=psf)
+
+
+def solve_sr_sym(wl: dict, inst: dict, iters: int | None = None, tol: float | None = None, maxit: int = 10000,
+                 standard_cg_iters: int = 0):
+    """2x SR with the symmetric-boundary model and F-DSG-NLM from the bicubic guide:
+    linearized PnP-ADMM (Algorithm 1), or with standard_cg_iters > 0 standard PnP-ADMM
+    whose x-update takes that many conjugate-gradient steps."""
+    psf = inst["psf"]
+    y = inst["y"].astype(np.float64)
+    g = forward.sr_guide(y)
+    W, info = dsgnlm.build_w(g, wl["patch_r"], wl["search_r"], wl["h"],
+                             wl["tol"] if tol is None else tol, maxit)
+    x0, v0, u0 = lpnp.initial_state(g)
+    n = wl["iters"] if iters is None else iters
+    den = lambda z: dsgnlm.denoise(W, z)
+    if standard_cg_iters > 0:
+        out = lpnp.admm_standard(lambda x: forward.sr_forward_sym(x, psf), lambda r: forward.sr_adjoint_sym(r, psf),
+                                 y, den, x0, v0, u0, wl["rho"], n, standard_cg_iters, lpnp.BOX01, inst["x_true"])
+    else:
+        out = lpnp.lpnp_solve(lambda x: forward.sr_grad_sym(x, y, psf), den, x0, v0, u0, wl["alpha"], wl["rho"], n,
+                              lpnp.BOX01, inst["x_true"])
+    return dict(guide=g, W=W, info=info, x=out[0], v=out[1], u=out[2], hist=out[3])

@@ -160,3 +160,31 @@ def test_spi_guide_box_and_clip():
     # corner (0, 0): reflection repeats row 0 and column 0
     want = (img[0, 0] * 4 + img[0, 1] * 2 + img[1, 0] * 2 + img[1, 1]) / 9
     assert abs(b[0, 0] - want) < 1e-15
+
+
+def _dense_A_sym(H, W, psf):
+    """A_sym written from its definition: (A x)_q = sum_t h(t) x(sym(2q - t)), with
+    sym the half-sample symmetric reflection (i -> -1 - i below 0, 2n - 1 - i above)."""
+    def sym(i, n):
+        while i < 0 or i >= n:
+            i = -1 - i if i < 0 else 2 * n - 1 - i
+        return i
+    r = psf.shape[0] // 2
+    A = np.zeros(((H // 2) * (W // 2), H * W))
+    for qi in range(H // 2):
+        for qj in range(W // 2):
+            for a in range(-r, r + 1):
+                for b in range(-r, r + 1):
+                    A[qi * (W // 2) + qj, sym(2 * qi - a, H) * W + sym(2 * qj - b, W)] += psf[a + r, b + r]
+    return A
+
+
+@pytest.mark.parametrize("H,W", [(12, 10), (6, 4)])
+def test_symmetric_sr_operator_matches_dense_definition(H, W):
+    A = _dense_A_sym(H, W, PSF)
+    x = np.random.default_rng(2).uniform(0, 1, (H, W))
+    np.testing.assert_allclose(forward.sr_forward_sym(x, PSF).ravel(), A @ x.ravel(), atol=1e-14)
+    r = np.random.default_rng(3).normal(size=(H // 2, W // 2))
+    np.testing.assert_allclose(forward.sr_adjoint_sym(r, PSF).ravel(), A.T @ r.ravel(), atol=1e-14)
+    # a constant image stays constant under the symmetric blur (the taps sum to 1)
+    np.testing.assert_allclose(forward.sr_forward_sym(np.full((H, W), 0.3), PSF), 0.3, atol=1e-15)

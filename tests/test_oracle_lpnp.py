@@ -104,3 +104,31 @@ def test_adapt_then_freeze_converges():
     assert hist[-1][0] < 1e-3 * hist[5][0]
     assert hist[-1][1] < 1e-3 * hist[5][1]
     assert out["x"].min() >= 0 and out["x"].max() <= 1
+
+
+def test_conjugate_gradients_reach_the_direct_solution():
+    rng = np.random.default_rng(4)
+    B = rng.normal(size=(12, 12))
+    M = B @ B.T + 0.5 * np.eye(12)
+    b = rng.normal(size=12)
+    x = lpnp.conjugate_gradients(lambda v: M @ v, b, np.zeros(12), 12)
+    np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-8, atol=1e-10)
+
+
+def test_standard_admm_with_identity_denoiser_is_proximal_point():
+    # W = I, C = R^n: u stays 0, v = x, and x <- (A^T A + rho I)^{-1} (A^T y + rho x)
+    from tests.test_oracle_forward import _dense_A_sym
+    H, W = 8, 10
+    A = _dense_A_sym(H, W, PSF)
+    rng = np.random.default_rng(5)
+    x0 = rng.uniform(0, 1, (H, W))
+    y = rng.uniform(0, 1, (H // 2, W // 2))
+    rho, iters = 0.7, 4
+    x, v, u, _ = lpnp.admm_standard(lambda x: forward.sr_forward_sym(x, PSF), lambda r: forward.sr_adjoint_sym(r, PSF),
+                                    y, lambda z: z, x0, x0, np.zeros_like(x0), rho, iters, H * W, lpnp.NONE)
+    M = A.T @ A + rho * np.eye(H * W)
+    xd = x0.ravel().copy()
+    for _ in range(iters):
+        xd = np.linalg.solve(M, A.T @ y.ravel() + rho * xd)
+    np.testing.assert_allclose(x.ravel(), xd, atol=1e-9)
+    np.testing.assert_allclose(u, 0, atol=1e-15)

@@ -450,6 +450,51 @@ def run_adaptive(steps: int, warmup: int, flush):
     return out
 
 
+def run_fig2(iters: int = 30, cg_iters: int = 10):
+    """Fig. 2 in synthetic form: PSNR against time for linearized PnP-ADMM
+    (Algorithm 1) and standard PnP-ADMM whose x-update takes cg_iters conjugate-
+    gradient steps, on the 512x512 SR workload with the symmetric-boundary blur and
+    the same fixed W.  One iteration per call, timed with CUDA events (the guide,
+    build and balance before the first iteration are not counted)."""
+    import torch
+
+    import synthetic
+    from paper_1901_06110_gb300 import dsgnlm as D
+    from paper_1901_06110_gb300 import pipeline
+
+    wl = synthetic.workload(WORKLOAD)
+    H, W = wl["H"], wl["W"]
+    xt = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], wl["seed"])).cuda()
+    nz = torch.from_numpy(synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], wl["seed"])).cuda()
+    y = D.lpnp_sr_observe(xt, nz, wl["blur_sigma"], wl["blur_r"], boundary="symmetric")
+    solver = pipeline.Solver(H, W, pipeline.Params.from_workload(wl, boundary="symmetric"))
+    prob = None
+    out = {"workload": f"sr512 with the symmetric-boundary blur: {H}x{W}, W fixed from the bicubic guide, "
+                       f"{iters} iterations; standard x-update: {cg_iters} CG steps from the current x",
+           "points": "[cumulative ms, PSNR dB] after each iteration"}
+    for name in ("linearized", f"standard_cg{cg_iters}"):
+        for rep in range(2):  # the first pass warms up
+            solver.prepare(y)
+            prob = solver._problem(y)
+            t, pts = 0.0, []
+            for _ in range(iters):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                if name == "linearized":
+                    D.lpnp_solve(prob, wl["rho"], 1)
+                else:
+                    D.lpnp_solve_standard(prob, wl["rho"], 1, cg_iters)
+                e1.record()
+                e1.synchronize()
+                t += e0.elapsed_time(e1)
+                pts.append([t, float(10 * torch.log10(1.0 / ((solver.x - xt) ** 2).double().mean()))])
+        out[name] = {"ms_total": t, "final_psnr_db": pts[-1][1], "best_psnr_db": max(p[1] for p in pts),
+                     "points": pts}
+    solver.close()
+    return out
+
+
 TABLE1_NP = (11, 17, 23, 29)
 TABLE1_NS = (10, 21)  # a 21x21 window, or N_s = 21 as the window radius (43x43)
 
@@ -723,6 +768,7 @@ def run_ours(args):
         line["spi"] = run_spi(max(5, args.batched_steps), 2, flush)
         line["adaptive"] = run_adaptive(args.batched_steps, 1, flush)
         line["residual_tables"] = run_residual_tables()
+        line["fig2"] = run_fig2()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         side = 192
         secs, inst, x_ref = _oracle_solve(side, wl)

@@ -137,6 +137,11 @@ dsgnlm_status lpnp_sr_observe(const float* x, const float* noise, int H, int W,
 /* Guide for super-resolution: 2x Keys cubic (a = -0.5) interpolation of y with
  * periodic wrap, low-resolution sample j at high-resolution 2j.
  * y device [h][w]; guide device [2h][2w]. */
+/* lpnp_sr_observe with the blur boundary `boundary` (LPNP_BC_PERIODIC or
+ * LPNP_BC_SYMMETRIC; the symmetric blur needs H, W >= 2 blur_r). */
+dsgnlm_status lpnp_sr_observe_bc(const float* x, const float* noise, int H, int W, float blur_sigma, int blur_r,
+                                 int boundary, float* y, void* stream);
+
 dsgnlm_status lpnp_sr_guide(const float* y, int h, int w, float* guide, void* stream);
 
 /* Single-photon measurement (Sec. 4.2): pixel i has K = k_side^2 sub-pixels; a
@@ -169,6 +174,9 @@ dsgnlm_status lpnp_init(const float* guide, int n, float* x, float* v, float* u,
 
 enum { LPNP_SR2 = 0, LPNP_SPI = 1 };
 enum { LPNP_C_NONE = 0, LPNP_C_NONNEG = 1, LPNP_C_BOX01 = 2 };
+/* boundary of the SR blur: periodic (Sec. 4.1's main model) or half-sample
+ * symmetric reflection (the standard-vs-linearized comparison of Sec. 4.1) */
+enum { LPNP_BC_PERIODIC = 0, LPNP_BC_SYMMETRIC = 1 };
 
 typedef struct lpnp_problem {
     int kind;              /* LPNP_SR2 (2x super-resolution) or LPNP_SPI */
@@ -190,6 +198,9 @@ typedef struct lpnp_problem {
     float* u;              /* device [H][W], in/out (scaled multiplier) */
     double* resid_hist;    /* host [iters][2] or NULL: RMS primal ||x - v|| / sqrt(n)
                               and dual rho ||v - v_prev|| / sqrt(n) per iteration */
+    int blur_boundary;     /* LPNP_SR2: LPNP_BC_PERIODIC or LPNP_BC_SYMMETRIC; the symmetric
+                              blur needs H, W >= 2 blur_r and a denoiser on the stencil
+                              path (search radius 1-8, 10 or 12) */
 } lpnp_problem;
 
 /* grad f(x) of the problem's data term (debug/tests).  x, grad device [H][W]. */
@@ -199,6 +210,15 @@ dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad);
  *   x <- Pi_C(mu (alpha x + rho (v - u) - grad f(x)));  v <- W (x + u);  u <- u + x - v.
  * Uses p->den's handle stream.  Synchronises only if resid_hist is given. */
 dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters);
+
+/* Standard PnP-ADMM for LPNP_SR2 (the comparison system of Sec. 4.1): the x-update
+ * minimises f(x) + rho/2 ||x - (v - u)||^2 by `cg_iters` (>= 1) conjugate-gradient
+ * steps on (A^T A + rho I) x = A^T y + rho (v - u), started from the current x, then
+ * projects onto C; v <- W (x + u), u <- u + x - v as lpnp_solve.  alpha is unused.
+ * The CG scalars stay on the device (no host round trips); synchronises only if
+ * resid_hist is given.  EINVAL for SPI problems, cg_iters < 1, or a denoiser off
+ * the stencil path. */
+dsgnlm_status lpnp_solve_standard(const lpnp_problem* p, float rho, int iters, int cg_iters);
 
 /* Algorithm 1 with W rebuilt from the denoiser input (Sec. 4): in each of the first
  * `adapt_iters` iterations (>= 1) the weights are built from z = x + u, after the

@@ -13,6 +13,7 @@ OK, EINVAL, ENOMEM, ECUDA, NOT_BUILT, NOT_BALANCED, NOT_CONVERGED, STALLED, TIME
 F32, F16, BF16 = 0, 1, 2
 SR2, SPI = 0, 1
 C_NONE, C_NONNEG, C_BOX01 = 0, 1, 2
+BC_PERIODIC, BC_SYMMETRIC = 0, 1
 MAX_PATCH_R, MAX_SEARCH_R = 14, 24
 PROF_BUILD, PROF_BALANCE, PROF_APPLY, PROF_XUPDATE = range(4)
 
@@ -25,6 +26,7 @@ class LpnpProblem(ctypes.Structure):
         ("constraint", c_int), ("alpha", c_float), ("den", c_void_p),
         ("x", c_void_p), ("v", c_void_p), ("u", c_void_p),
         ("resid_hist", ctypes.POINTER(c_double)),
+        ("blur_boundary", c_int),
     ]
 
 
@@ -40,6 +42,7 @@ SIGNATURES = {
     "dsgnlm_copy_scaling": (c_int, [c_void_p, c_void_p, ctypes.POINTER(c_double)]),
     "dsgnlm_num_offsets": (c_int, [c_void_p]),
     "lpnp_sr_observe": (c_int, [c_void_p, c_void_p, c_int, c_int, c_float, c_int, c_void_p, c_void_p]),
+    "lpnp_sr_observe_bc": (c_int, [c_void_p, c_void_p, c_int, c_int, c_float, c_int, c_int, c_void_p, c_void_p]),
     "lpnp_sr_guide": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "lpnp_spi_observe": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_float, c_void_p, c_void_p]),
     "lpnp_spi_counts": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
@@ -47,6 +50,7 @@ SIGNATURES = {
     "lpnp_init": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lpnp_gradient": (c_int, [ctypes.POINTER(LpnpProblem), c_void_p, c_void_p]),
     "lpnp_solve": (c_int, [ctypes.POINTER(LpnpProblem), c_float, c_int]),
+    "lpnp_solve_standard": (c_int, [ctypes.POINTER(LpnpProblem), c_float, c_int, c_int]),
     "lpnp_solve_adaptive": (c_int, [ctypes.POINTER(LpnpProblem), c_float, c_int, c_int, c_int, c_int, c_float,
                                     c_double, c_int]),
     "lpnp_solve_batched": (c_int, [ctypes.POINTER(LpnpProblem), c_int, c_float, c_int]),

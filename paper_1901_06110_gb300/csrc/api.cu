@@ -1,6 +1,7 @@
 // C ABI implementation: handle management, argument checks, the balancing control
 // loop and the Algorithm 1 iteration loop.  Only host code lives here; every step
 // of the method runs in the kernels of build.cu, stencil.cu and lpnp.cu.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -408,6 +409,17 @@ dsgnlm_status lpnp_sr_observe(const float* x, const float* noise, int H, int W, 
     return DSGNLM_OK;
 }
 
+dsgnlm_status lpnp_sr_observe_bc(const float* x, const float* noise, int H, int W, float blur_sigma, int blur_r,
+                                 int boundary, float* y, void* stream) {
+    if (boundary == LPNP_BC_PERIODIC) return lpnp_sr_observe(x, noise, H, W, blur_sigma, blur_r, y, stream);
+    if (boundary != LPNP_BC_SYMMETRIC) return DSGNLM_EINVAL;
+    if (!x || !y || H < 2 || W < 2 || (H & 1) || (W & 1)) return DSGNLM_EINVAL;
+    if (blur_r < 0 || blur_r > 8 || !(blur_sigma > 0.f) || !sr_bc_supported(H, W, blur_r)) return DSGNLM_EINVAL;
+    DSG_CK(launch_sr_forward_bc(1, x, H, W, make_blur_taps(blur_sigma, blur_r), noise, 1.0f, y,
+                                (cudaStream_t)stream));
+    return DSGNLM_OK;
+}
+
 dsgnlm_status lpnp_sr_guide(const float* y, int h, int w, float* guide, void* stream) {
     if (!y || !guide || h < 1 || w < 1) return DSGNLM_EINVAL;
     DSG_CK(launch_sr_guide(y, h, w, guide, (cudaStream_t)stream));
@@ -465,6 +477,9 @@ dsgnlm_status check_problem(const lpnp_problem* p, bool for_solve, bool need_w =
     if (p->kind == LPNP_SR2) {
         if (!p->y || (p->H & 1) || (p->W & 1)) return DSGNLM_EINVAL;
         if (p->blur_r < 0 || p->blur_r > 8 || !(p->blur_sigma > 0.f)) return DSGNLM_EINVAL;
+        if (p->blur_boundary != LPNP_BC_PERIODIC && p->blur_boundary != LPNP_BC_SYMMETRIC) return DSGNLM_EINVAL;
+        if (p->blur_boundary == LPNP_BC_SYMMETRIC && !sr_bc_supported(p->H, p->W, p->blur_r))
+            return DSGNLM_EINVAL;
     } else if (p->kind == LPNP_SPI) {
         if (!p->counts || p->K < 1 || p->K > 255 || !(p->eta > 0.f) || !(p->spi_eps > 0.f))
             return DSGNLM_EINVAL;
@@ -486,8 +501,14 @@ dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad) 
     if (p->kind == LPNP_SR2) {
         DSG_CK(h->rlo.ensure(sizeof(float) * (size_t)(p->H / 2) * (p->W / 2)));
         const BlurTaps taps = make_blur_taps(p->blur_sigma, p->blur_r);
-        DSG_CK(launch_sr_forward(x, p->H, p->W, taps, p->y, -1.0f, h->rlo.as<float>(), h->stream));
-        DSG_CK(launch_sr_adjoint(h->rlo.as<float>(), p->H, p->W, taps, grad, h->stream));
+        if (p->blur_boundary == LPNP_BC_SYMMETRIC) {
+            DSG_CK(launch_sr_forward_bc(1, x, p->H, p->W, taps, p->y, -1.0f, h->rlo.as<float>(), h->stream));
+            DSG_CK(launch_sr_adjoint_bc(1, h->rlo.as<float>(), p->H, p->W, taps, 0.f, nullptr, grad, nullptr,
+                                        h->stream));
+        } else {
+            DSG_CK(launch_sr_forward(x, p->H, p->W, taps, p->y, -1.0f, h->rlo.as<float>(), h->stream));
+            DSG_CK(launch_sr_adjoint(h->rlo.as<float>(), p->H, p->W, taps, grad, h->stream));
+        }
     } else {
         DSG_CK(launch_spi_grad(x, p->counts, p->H * p->W, p->K, p->eta, p->spi_eps, grad, h->stream));
     }
@@ -543,6 +564,16 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
     float* xA = p->x;
     float* xB = p->kind == LPNP_SR2 ? h->x2.as<float>() : p->x;
     const bool sr = p->kind == LPNP_SR2;
+    const bool sym = sr && p->blur_boundary == LPNP_BC_SYMMETRIC;
+    if (sym && !fast) return DSGNLM_EINVAL;  // the symmetric blur runs on the stencil path only
+    // A^T (A x - y) of the current x: one tiled kernel (periodic) or the residual on the
+    // low-resolution grid and its adjoint (symmetric)
+    auto sr_gradient = [&](const float* xs, float* g, cudaStream_t s) -> cudaError_t {
+        if (!sym) return launch_sr_grad(xs, p->y, H, W, taps, g, s);
+        cudaError_t e = launch_sr_forward_bc(1, xs, H, W, taps, p->y, -1.0f, h->rlo.as<float>(), s);
+        if (e != cudaSuccess) return e;
+        return launch_sr_adjoint_bc(1, h->rlo.as<float>(), H, W, taps, 0.f, nullptr, g, nullptr, s);
+    };
     if (fast) {
         // Iteration k: phase-1 gather of W z, then one per-pixel pass that finishes v
         // and u of iteration k and performs the x-update of iteration k + 1.  For SR
@@ -550,9 +581,10 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
         // it is computed on the side stream while phase 1 streams the weights.
         if (sr) {
             DSG_CK(h->gbuf.ensure(n * sizeof(float)));
+            if (sym) DSG_CK(h->rlo.ensure(sizeof(float) * n / 4));
             if (iters > 1) DSG_CK(h->ensure_side());
             DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
-                cudaError_t e = launch_sr_grad(xA, p->y, H, W, taps, h->gbuf.as<float>(), h->stream);
+                cudaError_t e = sr_gradient(xA, h->gbuf.as<float>(), h->stream);
                 if (e != cudaSuccess) return e;
                 return launch_xupdate_point(xA, h->gbuf.as<float>(), p->v, p->u, h->z.as<float>(), (int)n, mu,
                                             p->alpha, rho, p->constraint, h->stream);
@@ -600,7 +632,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             }));
             if (sr && do_x) {
                 DSG_CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-                DSG_CK(launch_sr_grad(xA, p->y, H, W, taps, h->gbuf.as<float>(), h->side));
+                DSG_CK(sr_gradient(xA, h->gbuf.as<float>(), h->side));
                 DSG_CK(cudaEventRecord(h->ev_join, h->side));
                 DSG_CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
             }
@@ -658,6 +690,99 @@ extern "C" {
 
 dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) { return solve_impl(p, rho, iters, nullptr); }
 
+dsgnlm_status lpnp_solve_standard(const lpnp_problem* p, float rho, int iters, int cg_iters) {
+    dsgnlm_status s = check_problem(p, true);
+    if (s != DSGNLM_OK) return s;
+    if (p->kind != LPNP_SR2 || cg_iters < 1 || !(rho > 0.f) || !std::isfinite(rho) || iters < 0) return DSGNLM_EINVAL;
+    dsgnlm* h = p->den;
+    if (!h->fast) return DSGNLM_EINVAL;
+    if (iters == 0) return DSGNLM_OK;
+    const int H = p->H, W = p->W, n = H * W;
+    const int bc = p->blur_boundary;
+    const BlurTaps taps = make_blur_taps(p->blur_sigma, p->blur_r);
+    if (!sr_bc_supported(H, W, taps.r)) return DSGNLM_EINVAL;
+    cudaStream_t st = h->stream;
+    const int nblocks = combine_xupdate_blocks(H, W);
+    const int nb_hi = sr_adjoint_bc_blocks(H, W), nb_v = cg_vector_blocks(n);
+    DSG_CK(h->z.ensure(sizeof(float) * n));
+    DSG_CK(h->rlo.ensure(sizeof(float) * n / 4));
+    DSG_CK(h->cg_r.ensure(sizeof(float) * n));
+    DSG_CK(h->cg_p.ensure(sizeof(float) * n));
+    DSG_CK(h->cg_q.ensure(sizeof(float) * n));
+    DSG_CK(h->cg_aty.ensure(sizeof(float) * n));
+    DSG_CK(h->cg_part.ensure(sizeof(double) * (size_t)std::max(nb_hi, nb_v)));
+    DSG_CK(h->cg_scal.ensure(sizeof(CgScalars)));
+    DSG_CK(h->partials.ensure(sizeof(double) * 2 * (size_t)nblocks * iters));
+    DSG_CK(h->hist.ensure(sizeof(double) * 2 * (size_t)iters));
+    DSG_CK(h->arrive.ensure(sizeof(unsigned) * (size_t)iters));
+    SolveRed red{h->partials.as<double>(), h->arrive.as<unsigned>(), h->hist.as<double>()};
+    float* x = p->x;
+    float* r = h->cg_r.as<float>();
+    float* pv = h->cg_p.as<float>();
+    float* q = h->cg_q.as<float>();
+    float* lo = h->rlo.as<float>();
+    float* aty = h->cg_aty.as<float>();
+    double* part = h->cg_part.as<double>();
+    CgScalars* sc = h->cg_scal.as<CgScalars>();
+    // A^T y once
+    DSG_CK(launch_sr_adjoint_bc(bc, p->y, H, W, taps, 0.f, nullptr, aty, nullptr, st));
+    EpilogueArgs ea{};
+    ea.H = H;
+    ea.W = W;
+    ea.d = h->d_final;
+    ea.t = h->t_final;
+    ea.inv_m = h->inv_m;
+    ea.z = h->z.as<float>();
+    ea.v = p->v;
+    ea.u = p->u;
+    ea.x_in = x;
+    ea.x_out = x;
+    ea.y = p->y;
+    ea.taps = taps;
+    ea.do_x = 0;  // the x-update is the CG solve of the next iteration
+    for (int it = 0; it < iters; ++it) {
+        DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&]() -> cudaError_t {
+            // (A^T A + rho I) x = A^T y + rho (v - u) by CG from the current x
+            cudaError_t e = launch_sr_forward_bc(bc, x, H, W, taps, nullptr, 0.f, lo, st);
+            if (e == cudaSuccess) e = launch_sr_adjoint_bc(bc, lo, H, W, taps, rho, x, q, nullptr, st);
+            if (e == cudaSuccess) e = launch_cg_init(aty, p->v, p->u, rho, q, r, pv, n, part, st);
+            if (e == cudaSuccess) e = launch_cg_reduce(part, nb_v, sc, 0, st);
+            for (int k = 0; k < cg_iters && e == cudaSuccess; ++k) {
+                e = launch_sr_forward_bc(bc, pv, H, W, taps, nullptr, 0.f, lo, st);
+                if (e == cudaSuccess) e = launch_sr_adjoint_bc(bc, lo, H, W, taps, rho, pv, q, part, st);
+                if (e == cudaSuccess) e = launch_cg_reduce(part, nb_hi, sc, 1, st);
+                if (e == cudaSuccess) e = launch_cg_step(x, r, pv, q, sc, n, part, st);
+                if (e == cudaSuccess) e = launch_cg_reduce(part, nb_v, sc, 2, st);
+                if (e == cudaSuccess && k + 1 < cg_iters) e = launch_cg_dir(r, pv, sc, n, st);
+            }
+            if (e == cudaSuccess) e = launch_project_z(x, p->u, h->z.as<float>(), n, p->constraint, st);
+            return e;
+        }));
+        DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
+            return launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
+                                     h->err.as<unsigned>(), nullptr, st);
+        }));
+        ea.partials = h->partials.as<double>() + 2 * (size_t)nblocks * it;
+        DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_combine_update(0, h->plan, h->rs, ea, st); }));
+    }
+    DSG_CK(launch_reduce_residuals(red, iters, nblocks, st));
+    if (p->resid_hist) {
+        DSG_CK(h->stage(sizeof(double) * 2 * (size_t)iters));
+        DSG_CK(cudaMemcpyAsync(h->host_stage, h->hist.p, sizeof(double) * 2 * (size_t)iters, cudaMemcpyDeviceToHost,
+                               st));
+        DSG_CK(cudaStreamSynchronize(st));
+        unsigned errv = 0;
+        DSG_CK(cudaMemcpy(&errv, h->err.p, sizeof errv, cudaMemcpyDeviceToHost));
+        if (errv) return DSGNLM_TIMEOUT;
+        const double* hs = (const double*)h->host_stage;
+        for (int it = 0; it < iters; ++it) {
+            p->resid_hist[2 * it] = std::sqrt(hs[2 * it] / (double)n);
+            p->resid_hist[2 * it + 1] = (double)rho * std::sqrt(hs[2 * it + 1] / (double)n);
+        }
+    }
+    return DSGNLM_OK;
+}
+
 dsgnlm_status lpnp_solve_adaptive(const lpnp_problem* p, float rho, int iters, int adapt_iters, int patch_r,
                                   int search_r, float bandwidth, double tol, int maxit) {
     if (adapt_iters < 1 || !tma_path_supports(search_r)) return DSGNLM_EINVAL;
@@ -693,6 +818,8 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
         const dsgnlm* h = probs[i].den;
         if (!h->fast || probs[i].kind != probs[0].kind || h->dtype != probs[0].den->dtype || h->rs != probs[0].den->rs)
             return DSGNLM_EINVAL;
+        if (probs[i].kind == LPNP_SR2 && probs[i].blur_boundary != LPNP_BC_PERIODIC)
+            return DSGNLM_EINVAL;  // the batched gradient is the periodic tile kernel
         for (int j = 0; j < i; ++j)
             if (probs[j].den == h) return DSGNLM_EINVAL;  // each image needs its own handle
     }

@@ -87,6 +87,8 @@ struct dsgnlm {
     double resid = 0.0;
     // Algorithm 1 workspace
     DevBuf z, x2, rlo, partials, arrive, hist, gbuf;
+    // conjugate-gradient workspace of the standard ADMM x-update
+    DevBuf cg_r, cg_p, cg_q, cg_aty, cg_part, cg_scal;
     // side stream of the solve: the SR gradient of an iteration runs there while the
     // main stream streams the weights (fork and join events)
     cudaStream_t side = nullptr;
@@ -145,6 +147,12 @@ struct dsgnlm {
         if (ev_join) cudaEventDestroy(ev_join);
         ev_fork = ev_join = nullptr;
         gbuf.release();
+        cg_r.release();
+        cg_p.release();
+        cg_q.release();
+        cg_aty.release();
+        cg_part.release();
+        cg_scal.release();
         bal_part.release();
         tma_part.release();
         tbuf[0].release();

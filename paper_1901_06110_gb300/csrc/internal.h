@@ -131,6 +131,27 @@ cudaError_t launch_sr_xupdate_fused(const float* x_in, float* x_out, const float
 // grad f for SPI
 cudaError_t launch_spi_grad(const float* x, const uint8_t* counts, int n, int K, float eta,
                             float eps, float* grad, cudaStream_t st);
+// SR operator with either boundary (bc 0 periodic, 1 symmetric; sym.cu):
+// out = A x + c aux (low-resolution), out = A^T rlo + rho pin (pin may be null) with
+// optional block sums of pin * out in part; valid when sr_bc_supported(H, W, r).
+bool sr_bc_supported(int H, int W, int blur_r);
+int sr_adjoint_bc_blocks(int H, int W);
+cudaError_t launch_sr_forward_bc(int bc, const float* x, int H, int W, BlurTaps taps, const float* aux, float c,
+                                 float* out, cudaStream_t st);
+cudaError_t launch_sr_adjoint_bc(int bc, const float* rlo, int H, int W, BlurTaps taps, float rho, const float* pin,
+                                 float* out, double* part, cudaStream_t st);
+// conjugate-gradient steps with device-resident scalars
+struct CgScalars {
+    double rs, pq, alpha, beta;
+};
+int cg_vector_blocks(int n);
+cudaError_t launch_cg_init(const float* aty, const float* v, const float* u, float rho, const float* mx, float* r,
+                           float* p, int n, double* part, cudaStream_t st);
+cudaError_t launch_cg_step(float* x, float* r, const float* p, const float* q, const CgScalars* s, int n,
+                           double* part, cudaStream_t st);
+cudaError_t launch_cg_dir(const float* r, float* p, const CgScalars* s, int n, cudaStream_t st);
+cudaError_t launch_cg_reduce(const double* part, int nb, CgScalars* s, int mode, cudaStream_t st);
+cudaError_t launch_project_z(float* x, const float* u, float* z, int n, int constraint, cudaStream_t st);
 // g = A^T (A x - y) in one launch (H, W even, taps.r <= 8)
 cudaError_t launch_sr_grad(const float* x, const float* y, int H, int W, BlurTaps taps, float* g,
                            cudaStream_t st);

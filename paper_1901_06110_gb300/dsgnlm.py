@@ -127,14 +127,21 @@ def dsgnlm_copy_scaling(h: Dsgnlm):
     return d, m.value
 
 
+def _boundary(name: str) -> int:
+    if name not in ("periodic", "symmetric"):
+        raise ValueError(f"blur boundary must be 'periodic' or 'symmetric', got {name!r}")
+    return _abi.BC_PERIODIC if name == "periodic" else _abi.BC_SYMMETRIC
+
+
 def lpnp_sr_observe(x: torch.Tensor, noise: torch.Tensor | None, blur_sigma: float, blur_r: int,
-                    out: torch.Tensor | None = None) -> torch.Tensor:
+                    out: torch.Tensor | None = None, boundary: str = "periodic") -> torch.Tensor:
     H, W = x.shape
     y = torch.empty((H // 2, W // 2), dtype=torch.float32, device=x.device) if out is None else out
     npt = None if noise is None else _ptr(noise, torch.float32, "noise", (H // 2) * (W // 2))
-    _check(_abi.load().lpnp_sr_observe(_ptr(x, torch.float32, "x"), npt, H, W, float(blur_sigma),
-                                       int(blur_r), _ptr(y, torch.float32, "y", (H // 2) * (W // 2)),
-                                       _stream()), "lpnp_sr_observe")
+    _check(_abi.load().lpnp_sr_observe_bc(_ptr(x, torch.float32, "x"), npt, H, W, float(blur_sigma),
+                                          int(blur_r), _boundary(boundary),
+                                          _ptr(y, torch.float32, "y", (H // 2) * (W // 2)), _stream()),
+           "lpnp_sr_observe_bc")
     return y
 
 
@@ -188,7 +195,7 @@ class Problem:
 
     def __init__(self, kind: str, den: Dsgnlm, x, v, u, *, alpha: float, constraint: int = _abi.C_BOX01,
                  y=None, blur_sigma: float = 1.0, blur_r: int = 4, counts=None, K: int = 16,
-                 eta: float = 4.0, spi_eps: float = 1e-3):
+                 eta: float = 4.0, spi_eps: float = 1e-3, boundary: str = "periodic"):
         H, W = x.shape
         self.den, self.x, self.v, self.u, self.y, self.counts = den, x, v, u, y, counts
         s = _abi.LpnpProblem()
@@ -204,6 +211,7 @@ class Problem:
         s.v = _ptr(v, torch.float32, "v", H * W)
         s.u = _ptr(u, torch.float32, "u", H * W)
         s.resid_hist = None
+        s.blur_boundary = _boundary(boundary)
         self.struct = s
 
 
@@ -235,6 +243,21 @@ def lpnp_solve(p: Problem, rho: float, iters: int, residuals: bool = False):
     p.struct.resid_hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None
     try:
         _check(_abi.load().lpnp_solve(ctypes.byref(p.struct), float(rho), int(iters)), "lpnp_solve")
+    finally:
+        p.struct.resid_hist = None
+    if hist is None:
+        return None
+    return [(hist[2 * k], hist[2 * k + 1]) for k in range(iters)]
+
+
+def lpnp_solve_standard(p: Problem, rho: float, iters: int, cg_iters: int, residuals: bool = False):
+    """Standard PnP-ADMM (SR): the x-update takes cg_iters conjugate-gradient steps on
+    (A^T A + rho I) x = A^T y + rho (v - u) from the current x, then projects."""
+    hist = (ctypes.c_double * (2 * iters))() if residuals and iters > 0 else None
+    p.struct.resid_hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None else None
+    try:
+        _check(_abi.load().lpnp_solve_standard(ctypes.byref(p.struct), float(rho), int(iters), int(cg_iters)),
+               "lpnp_solve_standard")
     finally:
         p.struct.resid_hist = None
     if hist is None:

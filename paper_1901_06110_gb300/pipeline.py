@@ -31,12 +31,13 @@ class Params:
     eta: float = 4.0
     spi_eps: float = 1e-3
     weight_dtype: str = "f32"
+    boundary: str = "periodic"  # SR blur boundary: "periodic" or "symmetric"
     extra: dict = field(default_factory=dict)
 
     @staticmethod
     def from_workload(wl: dict, **over) -> "Params":
         keys = ("patch_r", "search_r", "h", "tol", "iters", "rho", "alpha", "blur_sigma", "blur_r",
-                "eta", "spi_eps")
+                "eta", "spi_eps", "boundary")
         kw = {k: wl[k] for k in keys if k in wl}
         if "K_side" in wl:
             kw["K"] = wl["K_side"] ** 2
@@ -64,7 +65,7 @@ class Solver:
             p = self.p
             if self.kind == "sr":
                 self._prob = D.Problem("sr", self.den, self.x, self.v, self.u, alpha=p.alpha, y=data,
-                                       blur_sigma=p.blur_sigma, blur_r=p.blur_r)
+                                       blur_sigma=p.blur_sigma, blur_r=p.blur_r, boundary=p.boundary)
             else:
                 self._prob = D.Problem("spi", self.den, self.x, self.v, self.u, alpha=p.alpha,
                                        counts=data, K=p.K, eta=p.eta, spi_eps=p.spi_eps)
@@ -87,6 +88,30 @@ class Solver:
         D._check(lib.lpnp_init(self.guide.data_ptr(), self.H * self.W, self.x.data_ptr(),
                                self.v.data_ptr(), self.u.data_ptr(), stream), "lpnp_init")
         return D.lpnp_solve(self._problem(data), p.rho, p.iters, residuals=residuals)
+
+    def prepare(self, data: torch.Tensor):
+        """Guide, weight build, balance and the initial state (the part of run before
+        Algorithm 1)."""
+        p = self.p
+        lib = _abi.load()
+        stream = D._stream()
+        if self.kind == "sr":
+            D._check(lib.lpnp_sr_guide(data.data_ptr(), self.H // 2, self.W // 2, self.guide.data_ptr(),
+                                       stream), "lpnp_sr_guide")
+        else:
+            D._check(lib.lpnp_spi_guide(data.data_ptr(), self.H, self.W, p.K, p.eta, self.guide.data_ptr(),
+                                        stream), "lpnp_spi_guide")
+        D.dsgnlm_build(self.den, self.guide, p.patch_r, p.search_r, p.h)
+        self.balance = D.dsgnlm_balance(self.den, p.tol, p.maxit)
+        D._check(lib.lpnp_init(self.guide.data_ptr(), self.H * self.W, self.x.data_ptr(),
+                               self.v.data_ptr(), self.u.data_ptr(), stream), "lpnp_init")
+
+    def run_standard(self, data: torch.Tensor, cg_iters: int, iters: int | None = None, residuals: bool = False):
+        """Standard PnP-ADMM on the same W (SR): each x-update takes cg_iters
+        conjugate-gradient steps.  Continues from the current state; call prepare
+        first for a fresh solve."""
+        return D.lpnp_solve_standard(self._problem(data), self.p.rho, self.p.iters if iters is None else iters,
+                                     cg_iters, residuals=residuals)
 
     def run_adaptive(self, data: torch.Tensor, adapt_iters: int, residuals: bool = False):
         """The same solve with W rebuilt from x + u in the first adapt_iters

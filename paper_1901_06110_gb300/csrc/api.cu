@@ -169,8 +169,9 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
         pl.tiles_x = (W + tma_tile_w() - 1) / tma_tile_w();
         pl.tiles_y = (H + tma_tile_h() - 1) / tma_tile_h();
         const int tiles = pl.tiles_x * pl.tiles_y;
-        // about two resident CTAs per SM: split the offsets when tiles are scarce
-        int slices = (2 * h->num_sms) / tiles;
+        // about one CTA per resident slot (two per SM for FP32 weights, three for
+        // 16-bit weights): split the offsets when tiles are scarce
+        int slices = (tma_ctas_per_sm(h->dtype) * h->num_sms) / tiles;
         pl.splits = make_splits(search_r, slices < 1 ? 1 : slices);
         DSG_CK(h->tma_part.ensure(sizeof(float) * tma_region_floats(search_r) * (size_t)tiles * pl.splits.n));
         pl.partials = h->tma_part.as<float>();

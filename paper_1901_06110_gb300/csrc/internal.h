@@ -81,6 +81,7 @@ cudaError_t launch_tma_gather_batched(int dtype, int rs, const BatchMaps& maps, 
                                       const int4* work, int nwork, unsigned* err, cudaStream_t st);
 bool tma_path_supports(int rs);
 int tma_tile_w();
+int tma_ctas_per_sm(int dtype);  // resident phase-1 CTAs per SM for the weight type
 int tma_tile_h();
 size_t tma_region_floats(int rs);
 int tma_p2_blocks(int H, int W);

@@ -117,12 +117,48 @@ __host__ __device__ __forceinline__ int plane_index(int oy, int ox, int rs) {
     return oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
 }
 
+// FP32 weights: the strips are flushed into the shared accumulator with an
+// error-free transformation (hi + lo), so the pass sums are as accurate as the
+// weights themselves and the balance can reach tolerances near 1e-8.  16-bit
+// weights carry a rounding error of 2^-11 (FP16) or 2^-8 (BF16) already; their
+// strips are added in plain FP32, which halves the flush and frees the lo half
+// of the accumulator (three CTAs per SM instead of two).
+// kPrefetch: the weights of plane q + 1 are loaded into registers before the
+// FMAs of plane q (16 more registers per thread).  Measured at 512^2 it made the
+// FP32 pass slower (45.0 against 40.6 us) and does not fit the register budget of
+// three 16-bit CTAs per SM, so it is off for every weight type.
+template <typename WT> struct P1Traits {
+    static constexpr bool kComp = true;
+    static constexpr int kMinBlocks = 2;
+    static constexpr bool kPrefetch = false;
+};
+template <> struct P1Traits<__half> {
+    static constexpr bool kComp = false;
+    static constexpr int kMinBlocks = 3;
+    static constexpr bool kPrefetch = false;
+};
+template <> struct P1Traits<__nv_bfloat16> {
+    static constexpr bool kComp = false;
+    static constexpr int kMinBlocks = 3;
+    static constexpr bool kPrefetch = false;
+};
+
+// Planes of the column offsets oxa..oxb in consumption order (o_y = 0 is skipped
+// for o_x <= 0: those offsets belong to the other half of the window).
+__device__ __forceinline__ int p1_planes(int oxa, int oxb, int rs) {
+    if (oxb < oxa) return 0;
+    const int nonpos = max(0, min(oxb, 0) - oxa + 1);
+    return (oxb - oxa + 1) * (rs + 1) - nonpos;
+}
+
 // Phase 1 for one tile at (x0, y0) and the column offsets oxa..oxb: writes the
 // tile's partial region (kTH + RS rows, kTW + 2 RS columns) to `out`.
 template <int RS, typename WT>
 __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, const float* __restrict__ d,
                                         const float* __restrict__ z, int oxa, int oxb, int x0, int y0,
                                         float* __restrict__ out, unsigned* __restrict__ err) {
+    constexpr bool kComp = P1Traits<WT>::kComp;
+    constexpr bool kPrefetch = P1Traits<WT>::kPrefetch;
     constexpr int RH = kTH + RS;
     constexpr int RW = kTW + 2 * RS;
     constexpr int kStageElems = kTH * kTW;
@@ -131,8 +167,8 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
     WT* stages = reinterpret_cast<WT*>(smem_raw);
     float* qt = reinterpret_cast<float*>(smem_raw + kStages * kStageElems * sizeof(WT));
     float* acc_hi = qt + RH * RW;
-    float* acc_lo = acc_hi + RH * RW;
-    uint64_t* full = reinterpret_cast<uint64_t*>(acc_lo + RH * RW);
+    float* acc_lo = acc_hi + RH * RW;  // used with kComp only
+    uint64_t* full = reinterpret_cast<uint64_t*>(acc_hi + (kComp ? 2 : 1) * RH * RW);
     uint64_t* empty = full + kStages;
     __shared__ int s_abort;
 
@@ -197,22 +233,45 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
         }
         qt[idx] = v;
         acc_hi[idx] = 0.f;
-        acc_lo[idx] = 0.f;
+        if (kComp) acc_lo[idx] = 0.f;
     }
     consumer_sync();
 
     // consumers
     const int c = tid;
     const int lane = tid & 31;
-    float qo[kTH], tot[kTH], comp[kTH];
+    const int nplanes = p1_planes(oxa, oxb, RS);
+    bool ok = true;
+    // wait for plane qq, copy this thread's column of it to registers and release
+    // the stage
+    auto fetch = [&](int qq, float (&dst)[kTH]) {
+        const int s = qq % kStages;
+        if (ok && (!mbar_wait(&full[s], (qq / kStages) & 1) || *(volatile int*)&s_abort)) {
+            ok = false;
+            *(volatile int*)&s_abort = 1;
+            atomicOr(err, 2u);
+        }
+        if (!ok) {
+#pragma unroll
+            for (int r = 0; r < kTH; ++r) dst[r] = 0.f;
+            return;
+        }
+        const WT* st = stages + s * kStageElems;
+#pragma unroll
+        for (int r = 0; r < kTH; ++r) dst[r] = to_f32(st[r * kTW + c]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    };
+    float qo[kTH], tot[kTH], comp[kTH], wn[kTH];
 #pragma unroll
     for (int r = 0; r < kTH; ++r) {
         qo[r] = qt[r * RW + c + RS];
         tot[r] = 0.f;
         comp[r] = 0.f;
+        wn[r] = 0.f;
     }
     int q = 0;
-    bool ok = true;
+    if (kPrefetch && nplanes > 0) fetch(0, wn);
     for (int ox = oxa; ox <= oxb; ++ox) {
         const int col = c + RS + ox;
         float strip[RH], bacc[RH], fw[kTH];
@@ -226,21 +285,14 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
 #pragma unroll
         for (int oy = 0; oy <= RS; ++oy) {
             if (oy == 0 && ox <= 0) continue;
-            const int s = q % kStages;
-            ++q;
-            if (!ok) continue;
-            if (!mbar_wait(&full[s], ((q - 1) / kStages) & 1) || *(volatile int*)&s_abort) {
-                ok = false;
-                *(volatile int*)&s_abort = 1;
-                atomicOr(err, 2u);
-                continue;
-            }
-            const WT* st = stages + s * kStageElems;
             float w[kTH];
+            if constexpr (kPrefetch) {
 #pragma unroll
-            for (int r = 0; r < kTH; ++r) w[r] = to_f32(st[r * kTW + c]);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
+                for (int r = 0; r < kTH; ++r) w[r] = wn[r];
+                if (++q < nplanes) fetch(q, wn);
+            } else {
+                fetch(q++, w);
+            }
 #pragma unroll
             for (int r = 0; r < kTH; ++r) {
                 fw[r] = fmaf(w[r], strip[r + oy], fw[r]);
@@ -248,25 +300,39 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
             }
         }
 #pragma unroll
-        for (int r = 0; r < kTH; ++r) two_sum_into(tot[r], comp[r], fw[r]);
+        for (int r = 0; r < kTH; ++r) {
+            if (kComp)
+                two_sum_into(tot[r], comp[r], fw[r]);
+            else
+                tot[r] += fw[r];
+        }
         // one o_x at a time: column `col` is updated by this thread only
         consumer_sync();
 #pragma unroll
-        for (int a = 0; a < RH; ++a) two_sum_into(acc_hi[a * RW + col], acc_lo[a * RW + col], bacc[a]);
+        for (int a = 0; a < RH; ++a) {
+            if (kComp)
+                two_sum_into(acc_hi[a * RW + col], acc_lo[a * RW + col], bacc[a]);
+            else
+                acc_hi[a * RW + col] += bacc[a];
+        }
     }
     consumer_sync();
 #pragma unroll
     for (int r = 0; r < kTH; ++r) {
-        two_sum_into(acc_hi[r * RW + c + RS], acc_lo[r * RW + c + RS], tot[r]);
-        acc_lo[r * RW + c + RS] += comp[r];
+        if (kComp) {
+            two_sum_into(acc_hi[r * RW + c + RS], acc_lo[r * RW + c + RS], tot[r]);
+            acc_lo[r * RW + c + RS] += comp[r];
+        } else {
+            acc_hi[r * RW + c + RS] += tot[r];
+        }
     }
     consumer_sync();
-    for (int idx = c; idx < RH * RW; idx += kConsumers) out[idx] = acc_hi[idx] + acc_lo[idx];
+    for (int idx = c; idx < RH * RW; idx += kConsumers) out[idx] = kComp ? acc_hi[idx] + acc_lo[idx] : acc_hi[idx];
 }
 
 
 template <int RS, typename WT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, P1Traits<WT>::kMinBlocks)
 stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const float* __restrict__ d,
                   const float* __restrict__ z, TmaSplits splits, float* __restrict__ part,
                   unsigned* __restrict__ err, const int* __restrict__ skip) {
@@ -280,7 +346,7 @@ stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const 
 
 // One launch over the (instance, tile, slice) work items of a batch of images.
 template <int RS, typename WT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, P1Traits<WT>::kMinBlocks)
 stencil_p1_batched_kernel(const __grid_constant__ BatchMaps maps, const BatchInst* __restrict__ insts,
                           const int4* __restrict__ work, unsigned* __restrict__ err) {
     const int4 w = work[blockIdx.x];  // (instance, tile row, tile column, slice)
@@ -337,7 +403,8 @@ reduce_residuals_kernel(SolveRed red, int nblocks) {
 
 template <int RS, typename WT>
 size_t p1_smem_bytes() {
-    return (size_t)kStages * kTH * kTW * sizeof(WT) + 3 * sizeof(float) * (size_t)(kTH + RS) * (kTW + 2 * RS) +
+    const int regions = P1Traits<WT>::kComp ? 3 : 2;  // q, acc_hi (, acc_lo)
+    return (size_t)kStages * kTH * kTW * sizeof(WT) + regions * sizeof(float) * (size_t)(kTH + RS) * (kTW + 2 * RS) +
            2 * kStages * sizeof(uint64_t);
 }
 
@@ -426,6 +493,9 @@ bool tma_path_supports(int rs) {
 }
 
 int tma_tile_w() { return kTW; }
+int tma_ctas_per_sm(int dtype) {
+    return dtype == 0 ? P1Traits<float>::kMinBlocks : P1Traits<__half>::kMinBlocks;
+}
 int tma_tile_h() { return kTH; }
 size_t tma_region_floats(int rs) { return (size_t)(kTH + rs) * (kTW + 2 * rs); }
 int tma_p2_blocks(int H, int W) {

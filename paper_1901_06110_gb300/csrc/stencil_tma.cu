@@ -42,7 +42,6 @@ constexpr int kTW = kTmaTW;              // tile columns (= consumer threads)
 constexpr int kConsumers = kTW;
 constexpr int kConsumerWarps = kConsumers / 32;
 constexpr int kThreads = kConsumers + 32;  // + one producer warp
-constexpr int kStages = 8;
 constexpr long long kWaitBudget = 4000000000LL;  // cycles (about 2 s) before a wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -134,14 +133,20 @@ template <typename WT> struct P1Traits {
 };
 template <> struct P1Traits<__half> {
     static constexpr bool kComp = false;
-    static constexpr int kMinBlocks = 3;
+    static constexpr int kMinBlocks = 4;
     static constexpr bool kPrefetch = false;
 };
 template <> struct P1Traits<__nv_bfloat16> {
     static constexpr bool kComp = false;
-    static constexpr int kMinBlocks = 3;
+    static constexpr int kMinBlocks = 4;
     static constexpr bool kPrefetch = false;
 };
+
+// Pipeline stages of the weight ring: 8 at two CTAs per SM; four CTAs per SM
+// share the shared memory with fewer stages each.
+template <typename WT, int RS> constexpr int p1_stages() {
+    return P1Traits<WT>::kMinBlocks >= 4 ? (RS <= 10 ? 6 : 5) : 8;
+}
 
 // Planes of the column offsets oxa..oxb in consumption order (o_y = 0 is skipped
 // for o_x <= 0: those offsets belong to the other half of the window).
@@ -159,6 +164,7 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
                                         float* __restrict__ out, unsigned* __restrict__ err) {
     constexpr bool kComp = P1Traits<WT>::kComp;
     constexpr bool kPrefetch = P1Traits<WT>::kPrefetch;
+    constexpr int kStages = p1_stages<WT, RS>();
     constexpr int RH = kTH + RS;
     constexpr int RW = kTW + 2 * RS;
     constexpr int kStageElems = kTH * kTW;
@@ -190,12 +196,12 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
         // the first kStages loads overlap the consumers' staging of q below
         if (tid == kConsumers) {
             const uint64_t policy = evict_first_policy();
-            int q = 0;
+            int q = 0, s = 0;
+            unsigned ph = 0;  // parity of the ring pass of plane q
             bool ok = true;
             for (int ox = oxa; ox <= oxb && ok; ++ox) {
                 for (int oy = ox > 0 ? 0 : 1; oy <= RS; ++oy, ++q) {
-                    const int s = q % kStages;
-                    if (q >= kStages && !mbar_wait(&empty[s], ((q / kStages) - 1) & 1)) {
+                    if (q >= kStages && !mbar_wait(&empty[s], ph ^ 1u)) {
                         ok = false;
                         break;
                     }
@@ -206,6 +212,10 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
                     mbar_arrive_expect_tx(&full[s], kStageElems * sizeof(WT));
                     tma_load_3d(stages + s * kStageElems, tmap, &full[s], x0, y0, plane_index(oy, ox, RS),
                                 policy);
+                    if (++s == kStages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             if (!ok) {
@@ -242,11 +252,18 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
     const int lane = tid & 31;
     const int nplanes = p1_planes(oxa, oxb, RS);
     bool ok = true;
-    // wait for plane qq, copy this thread's column of it to registers and release
-    // the stage
-    auto fetch = [&](int qq, float (&dst)[kTH]) {
-        const int s = qq % kStages;
-        if (ok && (!mbar_wait(&full[s], (qq / kStages) & 1) || *(volatile int*)&s_abort)) {
+    // wait for the next plane, copy this thread's column of it to registers and
+    // release the stage
+    int cs = 0;
+    unsigned cph = 0;  // stage and ring-pass parity of the next plane
+    auto fetch = [&](float (&dst)[kTH]) {
+        const int s = cs;
+        const unsigned ph = cph;
+        if (++cs == kStages) {
+            cs = 0;
+            cph ^= 1u;
+        }
+        if (ok && (!mbar_wait(&full[s], ph) || *(volatile int*)&s_abort)) {
             ok = false;
             *(volatile int*)&s_abort = 1;
             atomicOr(err, 2u);
@@ -271,7 +288,7 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
         wn[r] = 0.f;
     }
     int q = 0;
-    if (kPrefetch && nplanes > 0) fetch(0, wn);
+    if (kPrefetch && nplanes > 0) fetch(wn);
     for (int ox = oxa; ox <= oxb; ++ox) {
         const int col = c + RS + ox;
         float strip[RH], bacc[RH], fw[kTH];
@@ -289,22 +306,22 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
             if constexpr (kPrefetch) {
 #pragma unroll
                 for (int r = 0; r < kTH; ++r) w[r] = wn[r];
-                if (++q < nplanes) fetch(q, wn);
+                if (++q < nplanes) fetch(wn);
             } else {
-                fetch(q++, w);
+                fetch(w);
             }
+            // with kComp the forward terms of one o_x are summed apart and added to
+            // the total with an error-free transformation; otherwise straight into it
 #pragma unroll
             for (int r = 0; r < kTH; ++r) {
-                fw[r] = fmaf(w[r], strip[r + oy], fw[r]);
+                float& f = kComp ? fw[r] : tot[r];
+                f = fmaf(w[r], strip[r + oy], f);
                 bacc[r + oy] = fmaf(w[r], qo[r], bacc[r + oy]);
             }
         }
+        if (kComp) {
 #pragma unroll
-        for (int r = 0; r < kTH; ++r) {
-            if (kComp)
-                two_sum_into(tot[r], comp[r], fw[r]);
-            else
-                tot[r] += fw[r];
+            for (int r = 0; r < kTH; ++r) two_sum_into(tot[r], comp[r], fw[r]);
         }
         // one o_x at a time: column `col` is updated by this thread only
         consumer_sync();
@@ -403,6 +420,7 @@ reduce_residuals_kernel(SolveRed red, int nblocks) {
 
 template <int RS, typename WT>
 size_t p1_smem_bytes() {
+    constexpr int kStages = p1_stages<WT, RS>();
     const int regions = P1Traits<WT>::kComp ? 3 : 2;  // q, acc_hi (, acc_lo)
     return (size_t)kStages * kTH * kTW * sizeof(WT) + regions * sizeof(float) * (size_t)(kTH + RS) * (kTW + 2 * RS) +
            2 * kStages * sizeof(uint64_t);

@@ -12,6 +12,8 @@
 // Eq. S3) and, in the same pass over the pixels, performs the linearized
 // x-update of iteration k + 1, which needs v, u and the gradient only at its own
 // pixel (the SR gradient is computed beforehand by sr_grad_tile_kernel).
+#include <type_traits>
+
 #include "combine.cuh"
 #include "common.cuh"
 #include "epilogue.cuh"
@@ -56,6 +58,7 @@ __device__ void balance_decide(BalanceCtl* ctl, float e, float m, cudaGraphCondi
 // the next scaling sqrt(d / t), and the block's (max |d t - 1|, max d t).  With
 // `decide`, the last block to finish reduces the pairs of all blocks and applies
 // the stopping rule; a pass launched after the deciding one returns at once.
+template <int SL>
 __global__ void __launch_bounds__(256)
 balance_epilogue_kernel(Cover cv, int H, int W, const float* __restrict__ d_in, float* __restrict__ d_out,
                         float* __restrict__ t_out, float2* __restrict__ part, BalanceCtl* __restrict__ ctl,
@@ -72,14 +75,22 @@ balance_epilogue_kernel(Cover cv, int H, int W, const float* __restrict__ d_in, 
     const int pj = x0 + threadIdx.x;
     const int lj = pj - (x0 / kTmaTW) * kTmaTW;
     float e = 0.f, m = 0.f;
+    // both rows' loads before the first store
+    float dv[2], gv[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int py = threadIdx.y + 8 * r;
-        const int pi = y0 + py;
+        const bool ok = y0 + py < H && pj < W;
+        dv[r] = ok ? d_in[(size_t)(y0 + py) * W + pj] : 0.f;
+        gv[r] = ok ? tile_gather_comp<SL>(tc, py, lj) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int pi = y0 + threadIdx.y + 8 * r;
         if (pi >= H || pj >= W) continue;
         const size_t s = (size_t)pi * W + pj;
-        const float ds = d_in[s];
-        const float tt = ds + tile_gather_comp(tc, py, lj);  // (K1 d)_s with K1(s, s) = 1
+        const float ds = dv[r];
+        const float tt = ds + gv[r];  // (K1 d)_s with K1(s, s) = 1
         d_out[s] = sqrtf(ds / tt);
         t_out[s] = tt;
         e = fmaxf(e, fabsf(fmaf(ds, tt, -1.f)));  // |d_s t_s - 1| with a single rounding
@@ -133,11 +144,23 @@ balance_epilogue_kernel(Cover cv, int H, int W, const float* __restrict__ d_in, 
     balance_decide(ctl, e, m, cond, use_cond);
 }
 
-template <int KIND>
+template <int KIND, int SL>
 __global__ void __launch_bounds__(256, 4)
 combine_update_kernel(Cover cv, EpilogueArgs a) {
     const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    combine_update_body<KIND>(cv, a, a.do_x, blockIdx.y * kXH, blockIdx.x * kXW, a.partials + 2 * bid);
+    combine_update_body<KIND, SL>(cv, a, a.do_x, blockIdx.y * kXH, blockIdx.x * kXW, a.partials + 2 * bid);
+}
+
+// Kernels specialised for the common slice counts; SL = 0 takes any count.
+template <typename F>
+cudaError_t by_slices(int slices, F&& f) {
+    switch (slices) {
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2: return f(std::integral_constant<int, 2>{});
+        case 3: return f(std::integral_constant<int, 3>{});
+        case 4: return f(std::integral_constant<int, 4>{});
+        default: return f(std::integral_constant<int, 0>{});
+    }
 }
 
 Cover cover(const TmaPlan& plan, int rs) {
@@ -151,10 +174,14 @@ int balance_combine_blocks(int H, int W) { return ((W + kXW - 1) / kXW) * ((H + 
 cudaError_t launch_balance_epilogue(const TmaPlan& plan, int H, int W, int rs, const float* d_in, float* d_out,
                                     float* t_out, float2* part, BalanceCtl* ctl, int decide,
                                     cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
-    balance_epilogue_kernel<<<dim3((W + kXW - 1) / kXW, (H + kXH - 1) / kXH), dim3(32, 8), 0, st>>>(
-        cover(plan, rs), H, W, d_in, d_out, t_out, part, ctl, decide, cond, use_cond);
-    count_launches(1);
-    return cudaGetLastError();
+    const dim3 grid((W + kXW - 1) / kXW, (H + kXH - 1) / kXH);
+    const Cover cv = cover(plan, rs);
+    return by_slices(plan.splits.n, [&](auto sl) {
+        balance_epilogue_kernel<decltype(sl)::value><<<grid, dim3(32, 8), 0, st>>>(cv, H, W, d_in, d_out, t_out,
+                                                                                   part, ctl, decide, cond, use_cond);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 int combine_xupdate_blocks(int H, int W) { return ((W + kXW - 1) / kXW) * ((H + kXH - 1) / kXH); }
@@ -162,13 +189,17 @@ int combine_xupdate_blocks(int H, int W) { return ((W + kXW - 1) / kXW) * ((H + 
 cudaError_t launch_combine_update(int kind, const TmaPlan& plan, int rs, const EpilogueArgs& args,
                                   cudaStream_t st) {
     if (kind == 0 && args.do_x && !args.g) return cudaErrorInvalidValue;
-    dim3 grid((args.W + kXW - 1) / kXW, (args.H + kXH - 1) / kXH);
-    if (kind == 0)
-        combine_update_kernel<0><<<grid, dim3(32, 8), 0, st>>>(cover(plan, rs), args);
-    else
-        combine_update_kernel<1><<<grid, dim3(32, 8), 0, st>>>(cover(plan, rs), args);
-    count_launches(1);
-    return cudaGetLastError();
+    const dim3 grid((args.W + kXW - 1) / kXW, (args.H + kXH - 1) / kXH);
+    const Cover cv = cover(plan, rs);
+    return by_slices(plan.splits.n, [&](auto sl) {
+        constexpr int SL = decltype(sl)::value;
+        if (kind == 0)
+            combine_update_kernel<0, SL><<<grid, dim3(32, 8), 0, st>>>(cv, args);
+        else
+            combine_update_kernel<1, SL><<<grid, dim3(32, 8), 0, st>>>(cv, args);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 }  // namespace dsg

@@ -41,6 +41,11 @@ __device__ __forceinline__ TileCover tile_cover(const Cover& cv, int y0, int x0)
     return c;
 }
 
+// Sum of the regions that cover pixel (li, lj) of the tile.  SL > 0: the slice
+// count known at compile time, so that the whole sum unrolls and
+// its loads can be issued together with the caller's other loads; a region that
+// does not cover the pixel then adds an exact zero.  SL = 0: any slice count.
+template <int SL = 0>
 __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj) {
     const int rs = c.rs, RW = c.RW;
     const bool up = c.up_ok && li < rs;
@@ -50,6 +55,24 @@ __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj)
     const int up_cell = (li + kTmaTH) * RW + lj + rs;
     float acc = 0.f;
     const float* base = c.own;
+    if constexpr (SL > 0) {
+#pragma unroll
+        for (int sl = 0; sl < SL; ++sl, base += c.slice_stride) {
+            const float v0 = __ldcg(base + own_cell);
+            const float v1 = up ? __ldcg(base + c.up_d + up_cell) : 0.f;
+            const float v2 = left ? __ldcg(base + c.left_d + own_cell + kTmaTW) : 0.f;
+            const float v3 = (left && up) ? __ldcg(base + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
+            const float v4 = right ? __ldcg(base + c.right_d + own_cell - kTmaTW) : 0.f;
+            const float v5 = (right && up) ? __ldcg(base + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
+            acc += v0;
+            acc += v1;
+            acc += v2;
+            acc += v3;
+            acc += v4;
+            acc += v5;
+        }
+        return acc;
+    }
 #pragma unroll 2
     for (int sl = 0; sl < c.slices; ++sl, base += c.slice_stride) {
         acc += __ldcg(base + own_cell);
@@ -69,6 +92,7 @@ __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj)
 // The same sum with TwoSum compensation, in the fixed order of gather_partials
 // (per slice: upper left, up, upper right, left, own, right); a region that does
 // not cover the pixel contributes an exact zero, which leaves the sum unchanged.
+template <int SL = 0>
 __device__ __forceinline__ float tile_gather_comp(const TileCover& c, int li, int lj) {
     const int rs = c.rs, RW = c.RW;
     const bool up = c.up_ok && li < rs;
@@ -78,8 +102,9 @@ __device__ __forceinline__ float tile_gather_comp(const TileCover& c, int li, in
     const int up_cell = (li + kTmaTH) * RW + lj + rs;
     CompSum acc;
     const float* base = c.own;
-#pragma unroll 2
-    for (int sl = 0; sl < c.slices; ++sl, base += c.slice_stride) {
+    const int ns = SL > 0 ? SL : c.slices;
+#pragma unroll(SL > 0 ? SL : 2)
+    for (int sl = 0; sl < ns; ++sl, base += c.slice_stride) {
         const float v0 = (up && left) ? __ldcg(base + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
         const float v1 = up ? __ldcg(base + c.up_d + up_cell) : 0.f;
         const float v2 = (up && right) ? __ldcg(base + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
@@ -101,7 +126,7 @@ __device__ __forceinline__ float tile_gather_comp(const TileCover& c, int li, in
 // SR reads g = A^T(A x - y) computed beforehand (a.g), SPI evaluates h' in place.
 // x_in and x_out may be the same buffer.  Stores the tile's residual sums at
 // `partials` (two doubles).  All threads of a (32, 8) block must call it.
-template <int KIND>  // 0 super-resolution, 1 single-photon
+template <int KIND, int SL = 0>  // KIND 0 super-resolution, 1 single-photon; SL as tile_gather
 __device__ __forceinline__ void combine_update_body(const Cover& cv, const EpilogueArgs& a, int do_x, int y0, int x0,
                                                     double* partials) {
     const int H = a.H, W = a.W;
@@ -110,8 +135,9 @@ __device__ __forceinline__ void combine_update_body(const Cover& cv, const Epilo
     const int lj = pj - (x0 / kTmaTW) * kTmaTW;
     float A[2], zs[2], ds[2], ts[2], vo[2], uo[2], xs[2], gs[2];
     int k1[2];
-    // per-pixel loads first, then the partial sums (whose slice loop the compiler
-    // does not hoist loads across)
+    // per-pixel loads first, then the partial sums: with SL > 0 in the same unrolled
+    // loop, so that every load is issued before the first use; with SL = 0 after it
+    // (the compiler does not hoist loads across the runtime slice loop)
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int pi = y0 + threadIdx.y + 8 * r;
@@ -125,11 +151,14 @@ __device__ __forceinline__ void combine_update_body(const Cover& cv, const Epilo
         xs[r] = (ok && do_x) ? a.x_in[q] : 0.f;
         gs[r] = (ok && KIND == 0 && do_x) ? a.g[q] : 0.f;
         k1[r] = (ok && KIND == 1 && do_x) ? (int)a.counts[q] : 0;
+        if constexpr (SL > 0) A[r] = ok ? tile_gather<SL>(tc, threadIdx.y + 8 * r, lj) : 0.f;
     }
+    if constexpr (SL == 0) {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int py = threadIdx.y + 8 * r;
-        A[r] = (y0 + py < H && pj < W) ? tile_gather(tc, py, lj) : 0.f;
+        for (int r = 0; r < 2; ++r) {
+            const int py = threadIdx.y + 8 * r;
+            A[r] = (y0 + py < H && pj < W) ? tile_gather(tc, py, lj) : 0.f;
+        }
     }
     float sp = 0.f, sd = 0.f;
 #pragma unroll

@@ -361,6 +361,139 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     return DSGNLM_OK;
 }
 
+dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int maxit, int* iters_out,
+                                     double* resid_out, int* status_out) {
+    if (!hs || count < 1 || count > kMaxBatch) return DSGNLM_EINVAL;
+    if (!(tol >= 0.0) || maxit < 0 || maxit > 1000000) return DSGNLM_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        dsgnlm* h = hs[i];
+        if (!h) return DSGNLM_EINVAL;
+        if (!h->built) return DSGNLM_NOT_BUILT;
+        if (!h->fast || h->dtype != hs[0]->dtype || h->rs != hs[0]->rs) return DSGNLM_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == h) return DSGNLM_EINVAL;
+    }
+    dsgnlm* lead = hs[0];
+    cudaStream_t st = lead->stream;
+    for (int i = 1; i < count; ++i)  // work queued on other streams (their builds) comes first
+        if (hs[i]->stream != st) DSG_CK(cudaStreamSynchronize(hs[i]->stream));
+    std::vector<BatchInst> inst(2 * (size_t)count);
+    std::vector<BatchBal> bal(count);
+    std::vector<int4> work1, work2;
+    BatchMaps maps;
+    DSG_CK(lead->stage(sizeof(BalanceCtl) * (size_t)count));
+    BalanceCtl* c0 = static_cast<BalanceCtl*>(lead->host_stage);
+    for (int i = 0; i < count; ++i) {
+        dsgnlm* h = hs[i];
+        const int H = h->H, W = h->W;
+        const size_t n = (size_t)H * W;
+        const int nbx = (W + 31) / 32, nby = (H + 15) / 16;  // the 16 x 32 epilogue blocks
+        if (nbx * nby != balance_combine_blocks(H, W)) return DSGNLM_EINVAL;
+        h->balanced = false;
+        DSG_CK(h->dbuf[0].ensure(n * sizeof(float)));
+        DSG_CK(h->dbuf[1].ensure(n * sizeof(float)));
+        DSG_CK(h->tbuf[0].ensure(n * sizeof(float)));
+        DSG_CK(h->tbuf[1].ensure(n * sizeof(float)));
+        DSG_CK(h->bal_part.ensure(sizeof(float2) * (size_t)balance_combine_blocks(H, W)));
+        DSG_CK(h->ctl.ensure(sizeof(BalanceCtl)));
+        BalanceCtl& c = c0[i];
+        c = BalanceCtl{};
+        c.final_pass = -1;
+        c.best = INFINITY;
+        c.tol = tol;
+        c.maxit = maxit;
+        DSG_CK(cudaMemcpyAsync(h->ctl.p, &c, sizeof c, cudaMemcpyHostToDevice, st));
+        DSG_CK(launch_fill(h->dbuf[0].as<float>(), 1.0f, n, st));
+        std::memcpy(maps.m[i], h->plan.tmap, 128);
+        for (int par = 0; par < 2; ++par) {
+            BatchInst& bi = inst[(size_t)par * count + i];
+            bi = BatchInst{};
+            bi.H = H;
+            bi.W = W;
+            bi.tiles_x = h->plan.tiles_x;
+            bi.tiles_y = h->plan.tiles_y;
+            bi.splits = h->plan.splits;
+            bi.d = h->dbuf[par].as<float>();
+            bi.z = nullptr;
+            bi.part = h->plan.partials;
+            bi.done = &h->ctl.as<BalanceCtl>()->done;
+        }
+        BatchBal& b = bal[i];
+        b.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, h->plan.splits.n, h->rs};
+        b.H = H;
+        b.W = W;
+        b.nbx = nbx;
+        b.nblocks = nbx * nby;
+        for (int par = 0; par < 2; ++par) {
+            b.d[par] = h->dbuf[par].as<float>();
+            b.t[par] = h->tbuf[par].as<float>();
+        }
+        b.part = h->bal_part.as<float2>();
+        b.ctl = h->ctl.as<BalanceCtl>();
+        for (int sl = 0; sl < h->plan.splits.n; ++sl)
+            for (int ty = 0; ty < h->plan.tiles_y; ++ty)
+                for (int tx = 0; tx < h->plan.tiles_x; ++tx) work1.push_back(make_int4(i, ty, tx, sl));
+        for (int by = 0; by < nby; ++by)
+            for (int bx = 0; bx < nbx; ++bx) work2.push_back(make_int4(i, by, bx, 0));
+    }
+    DSG_CK(lead->bb_inst.ensure(sizeof(BatchInst) * inst.size()));
+    DSG_CK(lead->bb_bal.ensure(sizeof(BatchBal) * bal.size()));
+    DSG_CK(lead->bb_work1.ensure(sizeof(int4) * work1.size()));
+    DSG_CK(lead->bb_work2.ensure(sizeof(int4) * work2.size()));
+    DSG_CK(lead->bb_flag.ensure(sizeof(unsigned)));
+    DSG_CK(cudaMemcpyAsync(lead->bb_inst.p, inst.data(), sizeof(BatchInst) * inst.size(), cudaMemcpyHostToDevice, st));
+    DSG_CK(cudaMemcpyAsync(lead->bb_bal.p, bal.data(), sizeof(BatchBal) * bal.size(), cudaMemcpyHostToDevice, st));
+    DSG_CK(cudaMemcpyAsync(lead->bb_work1.p, work1.data(), sizeof(int4) * work1.size(), cudaMemcpyHostToDevice, st));
+    DSG_CK(cudaMemcpyAsync(lead->bb_work2.p, work2.data(), sizeof(int4) * work2.size(), cudaMemcpyHostToDevice, st));
+    DSG_CK(cudaMemsetAsync(lead->bb_flag.p, 0, sizeof(unsigned), st));
+    DSG_CK(cudaMemsetAsync(lead->err.p, 0, sizeof(unsigned), st));
+    // Passes in groups of four between host checks of the stopped count; an image's
+    // items return at once after the pass that stops it.
+    const BatchInst* dinst = lead->bb_inst.as<BatchInst>();
+    const int n1 = (int)work1.size(), n2 = (int)work2.size();
+    unsigned* stopped = lead->bb_flag.as<unsigned>();
+    for (int pass = 0; pass <= maxit; ++pass) {
+        const int par = pass & 1;
+        DSG_CK(lead->timed(DSGNLM_PROF_BALANCE, [&] {
+            cudaError_t e = launch_tma_gather_batched(lead->dtype, lead->rs, maps, dinst + (size_t)par * count,
+                                                      lead->bb_work1.as<int4>(), n1, lead->err.as<unsigned>(), st);
+            if (e != cudaSuccess) return e;
+            return launch_batched_balance_epilogue(lead->bb_bal.as<BatchBal>(), lead->bb_work2.as<int4>(), n2, par,
+                                                   stopped, st);
+        }));
+        if ((pass + 1) % 4 == 0 || pass == maxit) {
+            unsigned done = 0;
+            DSG_CK(cudaMemcpyAsync(lead->host_stage, stopped, sizeof done, cudaMemcpyDeviceToHost, st));
+            DSG_CK(cudaStreamSynchronize(st));
+            std::memcpy(&done, lead->host_stage, sizeof done);
+            if (done >= (unsigned)count) break;
+        }
+    }
+    for (int i = 0; i < count; ++i)
+        DSG_CK(cudaMemcpyAsync(c0 + i, hs[i]->ctl.p, sizeof(BalanceCtl), cudaMemcpyDeviceToHost, st));
+    unsigned errv = 0;
+    DSG_CK(cudaMemcpyAsync(&errv, lead->err.p, sizeof errv, cudaMemcpyDeviceToHost, st));
+    DSG_CK(cudaStreamSynchronize(st));
+    if (errv) return DSGNLM_TIMEOUT;
+    for (int i = 0; i < count; ++i) {
+        const BalanceCtl& c = c0[i];
+        if (!c.done || c.final_pass < 0) return DSGNLM_ECUDA;  // cannot happen: pass maxit decides
+        dsgnlm* h = hs[i];
+        h->t_final = h->tbuf[c.final_pass & 1].as<float>();
+        h->d_final = h->dbuf[c.final_pass & 1].as<float>();
+        h->m = c.m;
+        h->inv_m = (float)(1.0 / c.m);
+        h->iters = c.final_pass;
+        h->resid = c.eps;
+        h->balanced = true;
+        if (iters_out) iters_out[i] = c.final_pass;
+        if (resid_out) resid_out[i] = c.eps;
+        if (status_out)
+            status_out[i] = c.status == 6 ? DSGNLM_NOT_CONVERGED : c.status == 7 ? DSGNLM_STALLED : DSGNLM_OK;
+    }
+    return DSGNLM_OK;
+}
+
 dsgnlm_status dsgnlm_apply(dsgnlm_t h, const float* x, float* y) {
     if (!h || !x || !y || x == y || !aligned16(x) || !aligned16(y)) return DSGNLM_EINVAL;
     if (!h->built) return DSGNLM_NOT_BUILT;

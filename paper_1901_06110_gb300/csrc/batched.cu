@@ -108,7 +108,76 @@ batched_reduce_kernel(const BatchEpi* __restrict__ insts, double* __restrict__ h
     }
 }
 
+// One epilogue block of a batched balancing pass: t, the next scaling and the block's
+// maxima (balance_pixels, as the single-image epilogue); the image's last block
+// applies its stopping rule and, when the image stops, counts it in *stopped.
+// Images that stopped in an earlier pass are skipped.
+__global__ void __launch_bounds__(256)
+batched_balance_epilogue_kernel(const BatchBal* __restrict__ bb, const int4* __restrict__ work, int parity,
+                                unsigned* __restrict__ stopped) {
+    const int4 w = work[blockIdx.x];  // (image, block row, block column, -)
+    const BatchBal& b = bb[w.x];
+    BalanceCtl* ctl = b.ctl;
+    if (*(volatile const int*)&ctl->done) return;
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    float e = 0.f, m = 0.f;
+    balance_pixels(b.cv, b.H, b.W, b.d[parity], b.d[parity ^ 1], b.t[parity], w.y * kXH, w.z * kXW, threadIdx.x,
+                   threadIdx.y, e, m);
+    e = warp_max(e);
+    m = warp_max(m);
+    __shared__ float se[8], sm[8];
+    __shared__ int s_last;
+    if ((t & 31) == 0) {
+        se[t >> 5] = e;
+        sm[t >> 5] = m;
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int k = 0; k < 8; ++k) {
+            e = fmaxf(e, se[k]);
+            m = fmaxf(m, sm[k]);
+        }
+        b.part[(size_t)w.y * b.nbx + w.z] = make_float2(e, m);
+        __threadfence();  // the pair is visible before the arrival is counted
+        s_last = atomicAdd(&ctl->arrive, 1u) == (unsigned)(b.nblocks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    e = 0.f;
+    m = 0.f;
+    for (int q = t; q < b.nblocks; q += 256) {
+        const float2 v = __ldcg(b.part + q);
+        e = fmaxf(e, v.x);
+        m = fmaxf(m, v.y);
+    }
+    e = warp_max(e);
+    m = warp_max(m);
+    __syncthreads();
+    if ((t & 31) == 0) {
+        se[t >> 5] = e;
+        sm[t >> 5] = m;
+    }
+    __syncthreads();
+    if (t != 0) return;
+    for (int k = 0; k < 8; ++k) {
+        e = fmaxf(e, se[k]);
+        m = fmaxf(m, sm[k]);
+    }
+    ctl->arrive = 0u;
+    balance_decide(ctl, e, m, 0, 0);
+    if (ctl->done) atomicAdd(stopped, 1u);
+}
+
 }  // namespace
+
+cudaError_t launch_batched_balance_epilogue(const BatchBal* bb, const int4* work, int nwork, int parity,
+                                            unsigned* stopped, cudaStream_t st) {
+    if (nwork <= 0) return cudaSuccess;
+    batched_balance_epilogue_kernel<<<nwork, dim3(32, 8), 0, st>>>(bb, work, parity, stopped);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batched_xupdate0(int kind, const BatchEpi* insts, const int4* work, int nwork, cudaStream_t st) {
     if (nwork <= 0) return cudaSuccess;

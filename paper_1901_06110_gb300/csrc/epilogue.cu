@@ -24,36 +24,6 @@ namespace dsg {
 
 namespace {
 
-// Stopping rule of the balance (Eq. S2 iterated): stop at max |d t - 1| <= tol, at
-// maxit (not converged), or when three passes bring no 1% improvement (stalled).
-__device__ void balance_decide(BalanceCtl* ctl, float e, float m, cudaGraphConditionalHandle cond, int use_cond) {
-    const int pass = ctl->pass;
-    const double ed = (double)e;
-    ctl->eps = ed;
-    ctl->m = (double)m;
-    int done = 0, status = 0;
-    if (ed <= ctl->tol) {
-        done = 1;
-    } else if (pass >= ctl->maxit) {
-        done = 1;
-        status = 6;
-    } else if (ed < 0.99 * ctl->best) {
-        ctl->best = ed;
-        ctl->since_best = 0;
-    } else if (++ctl->since_best >= 3) {
-        done = 1;
-        status = 7;
-    }
-    if (done) {
-        ctl->final_pass = pass;
-        ctl->status = status;
-        *(volatile int*)&ctl->done = 1;
-    } else {
-        ctl->pass = pass + 1;
-    }
-    if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
-}
-
 // Epilogue of one balancing pass on the kXH x kXW tile of each block: t = K1 d,
 // the next scaling sqrt(d / t), and the block's (max |d t - 1|, max d t).  With
 // `decide`, the last block to finish reduces the pairs of all blocks and applies
@@ -70,32 +40,9 @@ balance_epilogue_kernel(Cover cv, int H, int W, const float* __restrict__ d_in, 
         if (use_cond && bid == 0 && t == 0) cudaGraphSetConditional(cond, 0u);
         return;
     }
-    const int y0 = blockIdx.y * kXH, x0 = blockIdx.x * kXW;
-    const TileCover tc = tile_cover(cv, y0, x0);
-    const int pj = x0 + threadIdx.x;
-    const int lj = pj - (x0 / kTmaTW) * kTmaTW;
     float e = 0.f, m = 0.f;
-    // both rows' loads before the first store
-    float dv[2], gv[2];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int py = threadIdx.y + 8 * r;
-        const bool ok = y0 + py < H && pj < W;
-        dv[r] = ok ? d_in[(size_t)(y0 + py) * W + pj] : 0.f;
-        gv[r] = ok ? tile_gather_comp<SL>(tc, py, lj) : 0.f;
-    }
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int pi = y0 + threadIdx.y + 8 * r;
-        if (pi >= H || pj >= W) continue;
-        const size_t s = (size_t)pi * W + pj;
-        const float ds = dv[r];
-        const float tt = ds + gv[r];  // (K1 d)_s with K1(s, s) = 1
-        d_out[s] = sqrtf(ds / tt);
-        t_out[s] = tt;
-        e = fmaxf(e, fabsf(fmaf(ds, tt, -1.f)));  // |d_s t_s - 1| with a single rounding
-        m = fmaxf(m, ds * tt);
-    }
+    balance_pixels<SL>(cv, H, W, d_in, d_out, t_out, blockIdx.y * kXH, blockIdx.x * kXW, threadIdx.x, threadIdx.y, e,
+                       m);
     e = warp_max(e);
     m = warp_max(m);
     __shared__ float se[8], sm[8];

@@ -41,6 +41,36 @@ __device__ __forceinline__ TileCover tile_cover(const Cover& cv, int y0, int x0)
     return c;
 }
 
+// Stopping rule of the balance (Eq. S2 iterated): stop at max |d t - 1| <= tol, at
+// maxit (not converged), or when three passes bring no 1% improvement (stalled).
+__device__ __forceinline__ void balance_decide(BalanceCtl* ctl, float e, float m, cudaGraphConditionalHandle cond, int use_cond) {
+    const int pass = ctl->pass;
+    const double ed = (double)e;
+    ctl->eps = ed;
+    ctl->m = (double)m;
+    int done = 0, status = 0;
+    if (ed <= ctl->tol) {
+        done = 1;
+    } else if (pass >= ctl->maxit) {
+        done = 1;
+        status = 6;
+    } else if (ed < 0.99 * ctl->best) {
+        ctl->best = ed;
+        ctl->since_best = 0;
+    } else if (++ctl->since_best >= 3) {
+        done = 1;
+        status = 7;
+    }
+    if (done) {
+        ctl->final_pass = pass;
+        ctl->status = status;
+        *(volatile int*)&ctl->done = 1;
+    } else {
+        ctl->pass = pass + 1;
+    }
+    if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
+}
+
 // Sum of the regions that cover pixel (li, lj) of the tile.  SL > 0: the slice
 // count known at compile time, so that the whole sum unrolls and
 // its loads can be issued together with the caller's other loads; a region that
@@ -200,6 +230,40 @@ __device__ __forceinline__ void combine_update_body(const Cover& cv, const Epilo
         }
         partials[0] = pa;
         partials[1] = pb;
+    }
+}
+
+// One thread's share of a balancing pass's epilogue (Eq. S2 iterated) on the
+// kXH x kXW tile at (y0, x0): pixels (y0 + ry, x0 + cx) and (y0 + ry + 8, x0 + cx).
+// t = K1 d (K1(s, s) = 1), the next scaling sqrt(d / t), and the running maxima
+// e = max |d t - 1| and m = max d t.
+template <int SL = 0>
+__device__ __forceinline__ void balance_pixels(const Cover& cv, int H, int W, const float* __restrict__ d_in,
+                                               float* __restrict__ d_out, float* __restrict__ t_out, int y0, int x0,
+                                               int cx, int ry, float& e, float& m) {
+    const TileCover tc = tile_cover(cv, y0, x0);
+    const int pj = x0 + cx;
+    const int lj = pj - (x0 / kTmaTW) * kTmaTW;
+    // both rows' loads before the first store
+    float dv[2], gv[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int py = ry + 8 * r;
+        const bool ok = y0 + py < H && pj < W;
+        dv[r] = ok ? d_in[(size_t)(y0 + py) * W + pj] : 0.f;
+        gv[r] = ok ? tile_gather_comp<SL>(tc, py, lj) : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int pi = y0 + ry + 8 * r;
+        if (pi >= H || pj >= W) continue;
+        const size_t s = (size_t)pi * W + pj;
+        const float ds = dv[r];
+        const float tt = ds + gv[r];  // (K1 d)_s with K1(s, s) = 1
+        d_out[s] = sqrtf(ds / tt);
+        t_out[s] = tt;
+        e = fmaxf(e, fabsf(fmaf(ds, tt, -1.f)));  // |d_s t_s - 1| with a single rounding
+        m = fmaxf(m, ds * tt);
     }
 }
 

@@ -96,6 +96,8 @@ struct dsgnlm {
     // batched Algorithm 1 workspace (used when this handle leads a batch), and the
     // batch's step sequence as a CUDA graph with the values it was recorded for
     DevBuf b_inst, b_epi, b_work1, b_work2, b_work3, b_hist;
+    // batched balance tables (used when this handle leads a batched balance)
+    DevBuf bb_inst, bb_bal, bb_work1, bb_work2, bb_flag;
     cudaGraph_t b_graph = nullptr;
     cudaGraphExec_t b_exec = nullptr;
     std::vector<unsigned char> b_key;
@@ -171,6 +173,11 @@ struct dsgnlm {
         b_work2.release();
         b_work3.release();
         b_hist.release();
+        bb_inst.release();
+        bb_bal.release();
+        bb_work1.release();
+        bb_work2.release();
+        bb_flag.release();
         rlo.release();
         partials.release();
         arrive.release();

@@ -76,6 +76,7 @@ struct BatchInst {  // per-instance data of a batched launch (device memory)
     const float* d;   // scaling
     const float* z;   // second factor of q (null: q = d)
     float* part;      // partial regions of this instance
+    const int* done;  // null, or a flag that, when set, makes the instance's items return
 };
 cudaError_t launch_tma_gather_batched(int dtype, int rs, const BatchMaps& maps, const BatchInst* insts,
                                       const int4* work, int nwork, unsigned* err, cudaStream_t st);
@@ -223,5 +224,24 @@ cudaError_t launch_batched_combine(int kind, const BatchEpi* insts, const int4* 
 // g of every image on (image, 32 x 32 tile) work items; every image with blur radius blur_r
 cudaError_t launch_batched_grad(int blur_r, const BatchEpi* insts, const int4* work, int nwork, cudaStream_t st);
 cudaError_t launch_batched_reduce(const BatchEpi* insts, int count, double* hist, int iters, cudaStream_t st);
+
+// Batched balance (batched.cu): the balancing passes of many handles advance
+// together, one phase-1 launch (launch_tma_gather_batched, q = d) and one epilogue
+// launch per pass over the work items of every image that has not stopped.  Each
+// image keeps its own plan, buffers and stopping rule (its BalanceCtl), so its
+// result equals its own dsgnlm_balance bit for bit.
+struct BatchBal {
+    Cover cv;             // the image's phase-1 partial regions
+    int H, W;
+    int nbx, nblocks;     // epilogue blocks (kXH x kXW) per row and in all
+    float* d[2];          // scaling of passes with parity 0 and 1 (each pass writes the other)
+    float* t[2];          // K1 d of passes with parity 0 and 1
+    float2* part;         // per epilogue block (max |d t - 1|, max d t)
+    BalanceCtl* ctl;
+};
+// work: (image, block row, block column, -) items over every image's epilogue blocks;
+// *stopped counts the images whose balance has stopped
+cudaError_t launch_batched_balance_epilogue(const BatchBal* bb, const int4* work, int nwork, int parity,
+                                            unsigned* stopped, cudaStream_t st);
 
 }  // namespace dsg

@@ -368,6 +368,7 @@ stencil_p1_batched_kernel(const __grid_constant__ BatchMaps maps, const BatchIns
                           const int4* __restrict__ work, unsigned* __restrict__ err) {
     const int4 w = work[blockIdx.x];  // (instance, tile row, tile column, slice)
     const BatchInst& in = insts[w.x];
+    if (in.done && *(volatile const int*)in.done) return;
     const size_t region = (size_t)(kTH + RS) * (kTW + 2 * RS);
     float* out = in.part + ((size_t)(w.w * in.tiles_y + w.y) * in.tiles_x + w.z) * region;
     p1_body<RS, WT>(reinterpret_cast<const CUtensorMap*>(maps.m[w.x]), in.H, in.W, in.d, in.z, in.splits.ox_lo[w.w], in.splits.ox_hi[w.w],

@@ -101,6 +101,20 @@ def dsgnlm_balance(h: Dsgnlm, tol: float, maxit: int):
     return st, it.value, res.value
 
 
+def dsgnlm_balance_batched(hs, tol: float, maxit: int):
+    """Balance several built handles together (one phase-1 and one epilogue launch per
+    pass over all of them; each image's result equals dsgnlm_balance on it).
+    Returns one (status, updates, residual) per handle."""
+    count = len(hs)
+    arr = (ctypes.c_void_p * count)(*[h.handle for h in hs])
+    its = (ctypes.c_int * count)()
+    res = (ctypes.c_double * count)()
+    sts = (ctypes.c_int * count)()
+    _check(_abi.load().dsgnlm_balance_batched(arr, count, float(tol), int(maxit), its, res, sts),
+           "dsgnlm_balance_batched")
+    return [(sts[i], its[i], res[i]) for i in range(count)]
+
+
 def dsgnlm_apply(h: Dsgnlm, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     n = h.H * h.W
     y = torch.empty_like(x) if out is None else out

@@ -172,7 +172,8 @@ class BatchSolver:
         return self.slices
 
     def prepare(self, ys):
-        """Guide, weight build and balance of every image, and the initial state."""
+        """Guide and weight build of every image, one batched balance of all of them
+        (each image's result as its own dsgnlm_balance), and the initial state."""
         p = self.p
         lib = _abi.load()
         stream = D._stream()
@@ -180,7 +181,8 @@ class BatchSolver:
             D._check(lib.lpnp_sr_guide(ys[i].data_ptr(), H // 2, W // 2, self.guide[i].data_ptr(), stream),
                      "lpnp_sr_guide")
             D.dsgnlm_build(self.dens[i], self.guide[i], p.patch_r, p.search_r, p.h)
-            self.balance[i] = D.dsgnlm_balance(self.dens[i], p.tol, p.maxit)
+        self.balance = D.dsgnlm_balance_batched(self.dens, p.tol, p.maxit)
+        for i, (H, W) in enumerate(self.shapes):
             D._check(lib.lpnp_init(self.guide[i].data_ptr(), H * W, self.x[i].data_ptr(), self.v[i].data_ptr(),
                                    self.u[i].data_ptr(), stream), "lpnp_init")
 

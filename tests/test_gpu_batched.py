@@ -146,3 +146,61 @@ def test_tune_batched_picks_a_candidate_and_leaves_iterates(gpu_lib):
     for st, b in zip(states, before):
         for t, ref in zip((st["x"], st["v"], st["u"]), b):
             np.testing.assert_array_equal(host(t), ref)
+
+
+def _balance_case(dtype, sizes, rp, rs, h, seed0):
+    from paper_1901_06110_gb300 import dsgnlm as D
+    singles, batch = [], []
+    for i, (H, W) in enumerate(sizes):
+        g = cuda(np.ascontiguousarray(synthetic.ground_truth(max(H, 8), max(W, 8), 6, True, seed0 + i)[:H, :W]))
+        a = D.dsgnlm_create(dtype)
+        D.dsgnlm_build(a, g, rp, rs, h)
+        a.H, a.W = H, W
+        singles.append((a, D.dsgnlm_balance(a, 1e-6, 300)))
+        b = D.dsgnlm_create(dtype)
+        D.dsgnlm_build(b, g, rp, rs, h)
+        b.H, b.W = H, W
+        batch.append(b)
+    return singles, batch
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_batched_balance_equals_single(gpu_lib, dtype):
+    """dsgnlm_balance_batched runs each image's own passes (its plan, buffers and
+    stopping rule) in shared launches: scalings, m, update counts, residuals and the
+    resulting W must equal dsgnlm_balance on each image bit for bit.  Uneven sizes
+    give different tile counts, offset slices and pass counts."""
+    from paper_1901_06110_gb300 import dsgnlm as D
+    sizes = [(96, 96), (128, 64), (40, 200), (200, 136), (17, 33)]
+    singles, batch = _balance_case(dtype, sizes, 2, 5, 0.1, 900)
+    res = D.dsgnlm_balance_batched(batch, 1e-6, 300)
+    assert len({r[1] for r in res}) > 1  # the images stop after different pass counts
+    for (a, sa), b, rb in zip(singles, batch, res):
+        assert rb[0] == sa[0] and rb[1] == sa[1] and rb[2] == sa[2], (rb, sa)
+        da, ma = D.dsgnlm_copy_scaling(a)
+        db, mb = D.dsgnlm_copy_scaling(b)
+        assert ma == mb
+        np.testing.assert_array_equal(host(da), host(db))
+        z = cuda(np.random.default_rng(3).uniform(0, 1, (a.H, a.W)).astype(np.float32))
+        np.testing.assert_array_equal(host(D.dsgnlm_apply(a, z)), host(D.dsgnlm_apply(b, z)))
+
+
+def test_batched_balance_maxit_and_errors(gpu_lib):
+    """maxit bounds every image (NOT_CONVERGED where tol is not reached, as the single
+    call reports); a repeated handle or mismatched search radius is rejected."""
+    from paper_1901_06110_gb300 import _abi
+    from paper_1901_06110_gb300 import dsgnlm as D
+    sizes = [(64, 64), (48, 130)]
+    singles, batch = _balance_case("f32", sizes, 2, 4, 0.1, 950)
+    res = D.dsgnlm_balance_batched(batch, 1e-12, 3)
+    for (a, _), b, rb in zip(singles, batch, res):
+        sa = D.dsgnlm_balance(a, 1e-12, 3)
+        assert rb == sa and rb[0] == _abi.NOT_CONVERGED and rb[1] == 3
+    with pytest.raises(D.DsgnlmError) as e:
+        D.dsgnlm_balance_batched([batch[0], batch[0]], 1e-6, 10)
+    assert e.value.status == _abi.EINVAL
+    other = D.dsgnlm_create("f32")
+    D.dsgnlm_build(other, cuda(np.ones((32, 32), np.float32)), 2, 3, 0.1)
+    with pytest.raises(D.DsgnlmError) as e:
+        D.dsgnlm_balance_batched([batch[0], other], 1e-6, 10)
+    assert e.value.status == _abi.EINVAL

@@ -112,13 +112,16 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit,
 
 /* Balance `count` (1..96) built handles together: the passes of dsgnlm_balance, each
  * pass one phase-1 launch and one epilogue launch over the work items of every
- * image, the image's own plan, buffers and stopping rule kept, so that each image's
- * scaling, m, update count and residual equal those of dsgnlm_balance on it, bit for
- * bit.  An image's items return at once after the pass that stops it; the host reads
- * the number of stopped images every four passes.  All handles must be distinct,
- * built on the stencil path (search radius 1-8, 10 or 12) with the same search
- * radius and weight dtype; the work runs on hs[0]'s stream, after the other
- * handles' streams are synchronised.
+ * image, each image's buffers and stopping rule kept.  With slices = 0 every image
+ * also keeps its own offset schedule, so that its scaling, m, update count and
+ * residual equal those of dsgnlm_balance on it, bit for bit; slices > 0 splits the
+ * offsets of every image into that many slices (as lpnp_solve_batched_sched: a
+ * batch fills the GPU by itself, and fewer slices read and write fewer partial
+ * sums), which changes only the order of FP32 sums.  An image's items return at once
+ * after the pass that stops it; the host reads the number of stopped images every
+ * four passes.  All handles must be distinct, built on the stencil path (search
+ * radius 1-8, 10 or 12) with the same search radius and weight dtype; the work runs
+ * on hs[0]'s stream, after the other handles' streams are synchronised.
  *
  * hs          host array of count handles.
  * iters_out, resid_out, status_out
@@ -127,7 +130,7 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit,
  * Synchronises the stream.  Returns OK (every handle is then balanced and usable),
  * EINVAL (bad count, tol or maxit, a handle repeated, off the stencil path or
  * mismatched), NOT_BUILT, TIMEOUT or a CUDA error. */
-dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int maxit, int* iters_out,
+dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int maxit, int slices, int* iters_out,
                                      double* resid_out, int* status_out);
 
 /* Apply y = W x (third aggregation of Algorithm 2).

@@ -37,8 +37,8 @@ SIGNATURES = {
     "dsgnlm_set_stream": (c_int, [c_void_p, c_void_p]),
     "dsgnlm_build": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_float]),
     "dsgnlm_balance": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
-    "dsgnlm_balance_batched": (c_int, [ctypes.POINTER(c_void_p), c_int, c_double, c_int, ctypes.POINTER(c_int),
-                                       ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
+    "dsgnlm_balance_batched": (c_int, [ctypes.POINTER(c_void_p), c_int, c_double, c_int, c_int,
+                                       ctypes.POINTER(c_int), ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     "dsgnlm_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
     "dsgnlm_copy_weights": (c_int, [c_void_p, c_void_p]),
     "dsgnlm_copy_scaling": (c_int, [c_void_p, c_void_p, ctypes.POINTER(c_double)]),

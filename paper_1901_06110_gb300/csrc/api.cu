@@ -361,9 +361,9 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     return DSGNLM_OK;
 }
 
-dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int maxit, int* iters_out,
+dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int maxit, int slices, int* iters_out,
                                      double* resid_out, int* status_out) {
-    if (!hs || count < 1 || count > kMaxBatch) return DSGNLM_EINVAL;
+    if (!hs || count < 1 || count > kMaxBatch || slices < 0) return DSGNLM_EINVAL;
     if (!(tol >= 0.0) || maxit < 0 || maxit > 1000000) return DSGNLM_EINVAL;
     for (int i = 0; i < count; ++i) {
         dsgnlm* h = hs[i];
@@ -405,6 +405,10 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
         DSG_CK(cudaMemcpyAsync(h->ctl.p, &c, sizeof c, cudaMemcpyHostToDevice, st));
         DSG_CK(launch_fill(h->dbuf[0].as<float>(), 1.0f, n, st));
         std::memcpy(maps.m[i], h->plan.tmap, 128);
+        const TmaSplits splits = slices > 0 ? make_splits(h->rs, slices) : h->plan.splits;
+        const size_t tiles = (size_t)h->plan.tiles_x * h->plan.tiles_y;
+        DSG_CK(h->tma_part.ensure(sizeof(float) * tma_region_floats(h->rs) * tiles * splits.n));
+        h->plan.partials = h->tma_part.as<float>();  // the buffer may have grown
         for (int par = 0; par < 2; ++par) {
             BatchInst& bi = inst[(size_t)par * count + i];
             bi = BatchInst{};
@@ -412,14 +416,14 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
             bi.W = W;
             bi.tiles_x = h->plan.tiles_x;
             bi.tiles_y = h->plan.tiles_y;
-            bi.splits = h->plan.splits;
+            bi.splits = splits;
             bi.d = h->dbuf[par].as<float>();
             bi.z = nullptr;
             bi.part = h->plan.partials;
             bi.done = &h->ctl.as<BalanceCtl>()->done;
         }
         BatchBal& b = bal[i];
-        b.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, h->plan.splits.n, h->rs};
+        b.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, splits.n, h->rs};
         b.H = H;
         b.W = W;
         b.nbx = nbx;
@@ -430,7 +434,7 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
         }
         b.part = h->bal_part.as<float2>();
         b.ctl = h->ctl.as<BalanceCtl>();
-        for (int sl = 0; sl < h->plan.splits.n; ++sl)
+        for (int sl = 0; sl < splits.n; ++sl)
             for (int ty = 0; ty < h->plan.tiles_y; ++ty)
                 for (int tx = 0; tx < h->plan.tiles_x; ++tx) work1.push_back(make_int4(i, ty, tx, sl));
         for (int by = 0; by < nby; ++by)

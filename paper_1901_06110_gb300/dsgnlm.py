@@ -101,16 +101,17 @@ def dsgnlm_balance(h: Dsgnlm, tol: float, maxit: int):
     return st, it.value, res.value
 
 
-def dsgnlm_balance_batched(hs, tol: float, maxit: int):
+def dsgnlm_balance_batched(hs, tol: float, maxit: int, slices: int = 0):
     """Balance several built handles together (one phase-1 and one epilogue launch per
-    pass over all of them; each image's result equals dsgnlm_balance on it).
-    Returns one (status, updates, residual) per handle."""
+    pass over all of them).  slices = 0 keeps each handle's own offset schedule and
+    gives each image exactly the dsgnlm_balance result; slices > 0 uses that many
+    offset slices for every image.  Returns one (status, updates, residual) per handle."""
     count = len(hs)
     arr = (ctypes.c_void_p * count)(*[h.handle for h in hs])
     its = (ctypes.c_int * count)()
     res = (ctypes.c_double * count)()
     sts = (ctypes.c_int * count)()
-    _check(_abi.load().dsgnlm_balance_batched(arr, count, float(tol), int(maxit), its, res, sts),
+    _check(_abi.load().dsgnlm_balance_batched(arr, count, float(tol), int(maxit), int(slices), its, res, sts),
            "dsgnlm_balance_batched")
     return [(sts[i], its[i], res[i]) for i in range(count)]
 

@@ -173,7 +173,8 @@ class BatchSolver:
 
     def prepare(self, ys):
         """Guide and weight build of every image, one batched balance of all of them
-        (each image's result as its own dsgnlm_balance), and the initial state."""
+        under the batch's offset schedule (with the default, each handle's own plan,
+        each image's result is that of its own dsgnlm_balance), and the initial state."""
         p = self.p
         lib = _abi.load()
         stream = D._stream()
@@ -181,7 +182,7 @@ class BatchSolver:
             D._check(lib.lpnp_sr_guide(ys[i].data_ptr(), H // 2, W // 2, self.guide[i].data_ptr(), stream),
                      "lpnp_sr_guide")
             D.dsgnlm_build(self.dens[i], self.guide[i], p.patch_r, p.search_r, p.h)
-        self.balance = D.dsgnlm_balance_batched(self.dens, p.tol, p.maxit)
+        self.balance = D.dsgnlm_balance_batched(self.dens, p.tol, p.maxit, self.slices)
         for i, (H, W) in enumerate(self.shapes):
             D._check(lib.lpnp_init(self.guide[i].data_ptr(), H * W, self.x[i].data_ptr(), self.v[i].data_ptr(),
                                    self.u[i].data_ptr(), stream), "lpnp_init")

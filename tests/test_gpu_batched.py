@@ -204,3 +204,21 @@ def test_batched_balance_maxit_and_errors(gpu_lib):
     with pytest.raises(D.DsgnlmError) as e:
         D.dsgnlm_balance_batched([batch[0], other], 1e-6, 10)
     assert e.value.status == _abi.EINVAL
+
+
+def test_batched_balance_schedule(gpu_lib):
+    """Another offset schedule changes only the order of FP32 sums: every image still
+    reaches tol with a doubly stochastic W, and its scaling stays within 1e-5 of the
+    image's own balance."""
+    from paper_1901_06110_gb300 import _abi
+    from paper_1901_06110_gb300 import dsgnlm as D
+    sizes = [(96, 96), (128, 64), (40, 200), (200, 136)]
+    singles, batch = _balance_case("f32", sizes, 2, 5, 0.1, 970)
+    res = D.dsgnlm_balance_batched(batch, 1e-6, 300, slices=1)
+    for (a, sa), b, rb in zip(singles, batch, res):
+        assert rb[0] == _abi.OK and rb[2] <= 1e-6 and abs(rb[1] - sa[1]) <= 1
+        da, _ = D.dsgnlm_copy_scaling(a)
+        db, _ = D.dsgnlm_copy_scaling(b)
+        assert rel_l2(host(db), host(da)) <= 1e-5
+        ones = torch.ones((b.H, b.W), device="cuda")
+        np.testing.assert_allclose(host(D.dsgnlm_apply(b, ones)), 1.0, atol=1e-6)

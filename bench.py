@@ -250,6 +250,10 @@ def run_batched(steps: int, warmup: int, flush, only=None):
         ys.append(D.lpnp_sr_observe(xt, nz, wl["blur_sigma"], wl["blur_r"]))
     mpix = sum(H * W for H, W in shapes) / 1e6
     plain_x = None
+    # the oracle (cpu_baseline leg) checks the smallest instances of every variant
+    side_min = min(sides)
+    probe = [i for i, sd in enumerate(sides) if sd == side_min][:3]
+    probe_x = {}
     out = {"workload": f"batch64: {len(shapes)} 2x SR images, sides {sorted(set(sides))}, {mpix:.1f} Mpix, "
                        f"patch 7x7, search 21x21, h={wl['h']}, tol {wl['tol']}, {wl['iters']} iterations",
            "mpix": mpix, "steps": steps}
@@ -296,6 +300,7 @@ def run_batched(steps: int, warmup: int, flush, only=None):
             e1.synchronize()
             t += e0.elapsed_time(e1)
         ms = t / steps
+        probe_x[name] = [solver.x[i].double().cpu().numpy() for i in probe]
         mse = [float(((x - xt) ** 2).double().mean()) for x, xt in zip(solver.x, xs)]
         psnr[name] = np.array([10 * np.log10(1.0 / m) for m in mse])
         out[name] = {"weights": dtype, "ms_per_step": ms, "mpix_s": mpix / (ms / 1e3),
@@ -319,7 +324,35 @@ def run_batched(steps: int, warmup: int, flush, only=None):
             out[name]["psnr_max_abs_diff_db_vs_plain"] = float(np.max(np.abs(psnr[name] - psnr["plain_f32"])))
             out[name]["speedup_vs_plain"] = out[name]["mpix_s"] / out["plain_f32"]["mpix_s"]
         out["psnr_db_plain_mean"] = float(psnr["plain_f32"].mean())
+    out["_probe"] = {"sides": [side_min] * len(probe), "index": probe,
+                     "y": [ys[i].double().cpu().numpy() for i in probe],
+                     "x_true": [xs[i].double().cpu().numpy() for i in probe], "x": probe_x}
     return out
+
+
+def batched_vs_oracle(batched: dict):
+    """The FP64 oracle on the probe instances of the batched workload (the smallest
+    images; its own 30-iteration solve of each from the same FP32 observation):
+    per instance and variant, the relative L2 error of x and the PSNR difference."""
+    import numpy as np
+
+    import synthetic
+    from oracle import forward as ofw
+    from oracle import lpnp as olp
+    from oracle import problems
+    pr = batched.pop("_probe")
+    wl = synthetic.workload("batch64")
+    psf = ofw.gaussian_psf(wl["blur_sigma"], wl["blur_r"])
+    t0 = time.perf_counter()
+    ref = [problems.solve_sr(wl, {"y": y, "psf": psf, "x_true": xt})["x"] for y, xt in zip(pr["y"], pr["x_true"])]
+    secs = time.perf_counter() - t0
+    res = {"instances": f"{len(ref)} of the {pr['sides'][0]}^2 images (indices {pr['index']}); oracle {secs:.1f} s"}
+    for name, xs in pr["x"].items():
+        rel = [float(np.linalg.norm(x - r) / np.linalg.norm(r)) for x, r in zip(xs, ref)]
+        dps = [abs(olp.psnr(x, xt) - olp.psnr(r, xt)) for x, r, xt in zip(xs, ref, pr["x_true"])]
+        dps = [float(v) if math.isfinite(v) else None for v in dps]
+        res[name] = {"rel_l2": rel, "psnr_db_diff": dps}
+    return res
 
 
 # ----------------------------------------------------------------------------- differentiable form
@@ -777,8 +810,12 @@ def run_ours(args):
                                 "sample": f"FP64 NumPy/SciPy oracle, one {side}x{side} instance of the "
                                           f"workload ({secs:.1f} s, single-threaded)"}
         line["error_vs_oracle"] = _error_vs_oracle(inst, x_ref, wl)
+        if "batched" in line:
+            line["batched"]["vs_oracle"] = batched_vs_oracle(line["batched"])
         if "table1" in line:
             oracle_table1(line["table1"]["rows"])
+    if "batched" in line:
+        line["batched"].pop("_probe", None)
     if rank == 0:
         print(json.dumps(line))
     solver.close()
@@ -841,7 +878,9 @@ def main():
         from paper_1901_06110_gb300 import build as lib_build
         lib_build.build()
         flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
-        print(json.dumps(run_batched(args.batched_steps, 1, flush, args.only_batched.split(","))))
+        out = run_batched(args.batched_steps, 1, flush, args.only_batched.split(","))
+        out.pop("_probe", None)
+        print(json.dumps(out))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -8,7 +8,7 @@
 // sideways; half-window offsets never point upwards) in shared memory once, then
 // for each offset o:
 //   V(p) = sum_{|t_y| <= r_p} (g(p + (t_y, 0)) - g(p + (t_y, 0) + o))^2
-//          vertical patch sums, as a sliding window down a column over 8
+//          vertical patch sums, as a sliding window down a column over 16
 //          consecutive outputs (one direct sum, then one add and one subtract
 //          per output), one thread per column and segment, and
 //   D(s) = sum_{|t_x| <= r_p} V(s + (0, t_x))   horizontal patch sums, as a
@@ -19,7 +19,10 @@
 // and writes the plane row-contiguously.  V is double-buffered: the vertical sums
 // of offset k + 1 are formed in the same interval as the horizontal sums of
 // offset k, so each offset costs one barrier.  Segments sit at fixed positions of
-// the image grid (tiles are aligned to 8), so results do not depend on scheduling.
+// the image grid (tiles are aligned to 16), so results do not depend on scheduling.
+// A CTA takes a chunk of consecutive offsets, sized at launch so that the grid
+// fills whole waves of resident CTAs; tiles whose pixels and offset partners all lie
+// inside the image skip the per-pixel bounds test.
 #include "common.cuh"
 #include "internal.h"
 
@@ -30,9 +33,8 @@ namespace {
 constexpr int kTW = 64;    // tile columns
 constexpr int kTH = 32;    // tile rows
 constexpr int kThreads = 256;
-constexpr int kSeg = 8;    // outputs per vertical sliding-window segment
+constexpr int kSeg = 16;   // outputs per vertical sliding-window segment
 constexpr int kHW = 4;     // outputs per horizontal sliding window (one thread, one row)
-constexpr int kChunk = 22; // offsets per CTA
 constexpr int kMaxRp = 14; // DSGNLM_MAX_PATCH_R
 
 // row length of the vertical sums: the tile plus the patch radius on both sides,
@@ -65,16 +67,16 @@ __device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16* p, const fl
 
 // RP >= 0: patch radius known at compile time; RP < 0: runtime radius rp_rt.
 template <typename WT, int RP>
-__global__ void __launch_bounds__(kThreads)
-build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, float c,
+__global__ void __launch_bounds__(kThreads, RP < 0 ? 1 : (RP <= 5 ? 6 : 3))
+build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, float c, int chunk,
              WT* __restrict__ planes) {
     extern __shared__ __align__(16) float smem[];
     const int rp = RP >= 0 ? RP : rp_rt;
     const int nh = num_half_offsets(rs);
     const int y0 = blockIdx.y * kTH;
     const int x0 = blockIdx.x * kTW;
-    const int k_begin = blockIdx.z * kChunk;
-    const int k_end = min(nh, k_begin + kChunk);
+    const int k_begin = blockIdx.z * chunk;
+    const int k_end = min(nh, k_begin + chunk);
 
     // staged guide: rows y0 - rp .. y0 + TH + rp + rs - 1,
     //               cols x0 - rp - rs .. x0 + TW + rp + rs - 1
@@ -109,9 +111,7 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
     // V(i, cc) = sum_{t_y} (g(i + t_y, cc - rp) - g(i + t_y + o_y, cc - rp + o_x))^2 for the
     // tile's rows: one column and 8 consecutive output rows per task, as a sliding
     // window down the column (staged row r0 + t is image row y0 - rp + r0 + t)
-    auto vertical = [&](int k, float* V) {
-        int oy, ox;
-        half_offset(k, rs, oy, ox);
+    auto vertical = [&](int oy, int ox, float* V) {
         for (int task = tid; task < n_vtask; task += kThreads) {
             const int seg = task / EW;
             const int cc = task - seg * EW;
@@ -146,14 +146,28 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
     constexpr int kNV = (kHW + 2 * (RP >= 0 ? RP : kMaxRp) + 3) / 4;  // 16-byte loads per window
     const int nv = (kHW + 2 * rp + 3) / 4;
 
-    if (k_begin < k_end) vertical(k_begin, V0);
+    // the tile and every offset's partner pixel lie inside the image (half-window
+    // offsets point down or sideways): no output needs the bounds test
+    const bool interior = y0 + kTH + rs <= H && x0 >= rs && x0 + kTW + rs <= W;
+    // offsets k and k + 1, advanced in half-window order (o_y = 0, o_x = 1..rs, then
+    // o_y = 1.., o_x = -rs..rs)
+    int oy, ox, oy1, ox1;
+    half_offset(k_begin, rs, oy, ox);
+    auto next_offset = [&](int& y, int& x) {
+        if (++x > rs) {
+            ++y;
+            x = -rs;
+        }
+    };
+    oy1 = oy;
+    ox1 = ox;
+    next_offset(oy1, ox1);
+    if (k_begin < k_end) vertical(oy, ox, V0);
     __syncthreads();
     for (int k = k_begin; k < k_end; ++k) {
         float* Vc = ((k - k_begin) & 1) ? V1 : V0;
         float* Vn = ((k - k_begin) & 1) ? V0 : V1;
-        if (k + 1 < k_end) vertical(k + 1, Vn);  // in the same interval as the sums below
-        int oy, ox;
-        half_offset(k, rs, oy, ox);
+        if (k + 1 < k_end) vertical(oy1, ox1, Vn);  // in the same interval as the sums below
         // D(i, j) = sum_{t_x} V(i, j + t_x), then the weight
         const float hat = (1.0f - fabsf((float)oy) * inv_hat) * (1.0f - fabsf((float)ox) * inv_hat);
         WT* out = planes + (size_t)k * plane;
@@ -179,17 +193,29 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
                 D += v[t];
             }
             float w[kHW];
+            if (interior) {
 #pragma unroll
-            for (int jj = 0; jj < kHW; ++jj) {
-                if (jj > 0) D += v[jj + 2 * rp] - v[jj - 1];
-                const int j = j0 + jj;
-                const bool inside = i < H && j < W && j + ox >= 0 && j + ox < W && i + oy < H;
-                w[jj] = inside ? hat * __expf(-D * c) : 0.f;
+                for (int jj = 0; jj < kHW; ++jj) {
+                    if (jj > 0) D += v[jj + 2 * rp] - v[jj - 1];
+                    w[jj] = hat * __expf(-D * c);
+                }
+                store4<WT>(out + (size_t)i * Wp + j0, w);
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < kHW; ++jj) {
+                    if (jj > 0) D += v[jj + 2 * rp] - v[jj - 1];
+                    const int j = j0 + jj;
+                    const bool inside = i < H && j < W && j + ox >= 0 && j + ox < W && i + oy < H;
+                    w[jj] = inside ? hat * __expf(-D * c) : 0.f;
+                }
+                // planes have a pitch of a multiple of 8: the 4 outputs are all inside the
+                // row's pitch or all outside it
+                if (i < H && j0 < Wp) store4<WT>(out + (size_t)i * Wp + j0, w);
             }
-            // planes have a pitch of a multiple of 8: the 4 outputs are all inside the
-            // row's pitch or all outside it
-            if (i < H && j0 < Wp) store4<WT>(out + (size_t)i * Wp + j0, w);
         }
+        oy = oy1;
+        ox = ox1;
+        next_offset(oy1, ox1);
         __syncthreads();  // Vc is rewritten two offsets on; Vn is complete
     }
 }
@@ -206,8 +232,26 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, (nh + kChunk - 1) / kChunk);
-    build_kernel<WT, RP><<<grid, kThreads, smem, st>>>(guide, H, W, rp, rs, c, planes);
+    // offsets per CTA: the chunk that makes the fewest waves of resident CTAs take the
+    // least time (each CTA also stages its guide tile, worth about two offsets)
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_kernel<WT, RP>, kThreads, smem) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaGetLastError();
+    const long long slots = per_sm * sms > 0 ? (long long)per_sm * sms : 1;
+    const long long tiles = (long long)((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);
+    int chunk = nh;
+    long long best = -1;
+    for (int ch = 1; ch <= nh; ++ch) {
+        const long long ctas = tiles * ((nh + ch - 1) / ch);
+        const long long cost = ((ctas + slots - 1) / slots) * (ch + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            chunk = ch;
+        }
+    }
+    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, (nh + chunk - 1) / chunk);
+    build_kernel<WT, RP><<<grid, kThreads, smem, st>>>(guide, H, W, rp, rs, c, chunk, planes);
     count_launches(1);
     return cudaGetLastError();
 }

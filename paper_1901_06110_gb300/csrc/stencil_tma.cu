@@ -231,19 +231,33 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
         return;
     }
 
-    // q over the tile + halo (zero outside the image); accumulators cleared
-    for (int idx = tid; idx < RH * RW; idx += kConsumers) {
-        const int a = idx / RW, b = idx - a * RW;
-        const int i = y0 + a, j = x0 - RS + b;
-        float v = 0.f;
-        if (i < H && j >= 0 && j < W) {
+    // q over the tile + halo (zero outside the image); accumulators cleared.  The
+    // loads of kStageBatch cells are issued before their stores, so the round trips
+    // to L2 overlap instead of following one another.
+    constexpr int kCells = RH * RW;
+    constexpr int kStageBatch = 8;
+    for (int base = tid; base < kCells; base += kStageBatch * kConsumers) {
+        float v[kStageBatch];
+#pragma unroll
+        for (int k = 0; k < kStageBatch; ++k) {
+            const int idx = base + k * kConsumers;
+            const int a = idx / RW, b = idx - a * RW;
+            const int i = y0 + a, j = x0 - RS + b;
+            const bool in = idx < kCells && i < H && j >= 0 && j < W;
             const size_t p = (size_t)i * W + j;
-            v = d[p];
-            if (z) v *= z[p];
+            const float dv = in ? d[p] : 0.f;
+            const float zv = (in && z) ? z[p] : 1.f;
+            v[k] = z ? dv * zv : dv;
         }
-        qt[idx] = v;
-        acc_hi[idx] = 0.f;
-        if (kComp) acc_lo[idx] = 0.f;
+#pragma unroll
+        for (int k = 0; k < kStageBatch; ++k) {
+            const int idx = base + k * kConsumers;
+            if (idx < kCells) {
+                qt[idx] = v[k];
+                acc_hi[idx] = 0.f;
+                if (kComp) acc_lo[idx] = 0.f;
+            }
+        }
     }
     consumer_sync();
 

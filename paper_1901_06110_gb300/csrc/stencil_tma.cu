@@ -232,9 +232,9 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
     }
 
     // q over the tile + halo (zero outside the image); accumulators cleared.  The
-    // loads of kStageBatch cells (all of them for search radii up to 10) are issued
-    // before their stores, so the round trips
-    // to L2 overlap instead of following one another.
+    // loads of kStageBatch cells per thread (all of them for search radii up to 10)
+    // are issued before their stores, so the round trips to L2 overlap instead of
+    // following one another.
     constexpr int kCells = RH * RW;
     constexpr int kStageBatch = 32;
     for (int base = tid; base < kCells; base += kStageBatch * kConsumers) {

@@ -120,40 +120,25 @@ __host__ __device__ __forceinline__ int plane_index(int oy, int ox, int rs) {
 // error-free transformation (hi + lo), so the pass sums are as accurate as the
 // weights themselves and the balance can reach tolerances near 1e-8.  16-bit
 // weights carry a rounding error of 2^-11 (FP16) or 2^-8 (BF16) already; their
-// strips are added in plain FP32, which halves the flush and frees the lo half
-// of the accumulator (three CTAs per SM instead of two).
-// kPrefetch: the weights of plane q + 1 are loaded into registers before the
-// FMAs of plane q (16 more registers per thread).  Measured at 512^2 it made the
-// FP32 pass slower (45.0 against 40.6 us) and does not fit the register budget of
-// three 16-bit CTAs per SM, so it is off for every weight type.
+// strips are added in plain FP32, which drops the lo half of the accumulator and
+// the separate per-offset forward sum, so that four CTAs fit on an SM instead of two.
 template <typename WT> struct P1Traits {
     static constexpr bool kComp = true;
     static constexpr int kMinBlocks = 2;
-    static constexpr bool kPrefetch = false;
 };
 template <> struct P1Traits<__half> {
     static constexpr bool kComp = false;
     static constexpr int kMinBlocks = 4;
-    static constexpr bool kPrefetch = false;
 };
 template <> struct P1Traits<__nv_bfloat16> {
     static constexpr bool kComp = false;
     static constexpr int kMinBlocks = 4;
-    static constexpr bool kPrefetch = false;
 };
 
 // Pipeline stages of the weight ring: 8 at two CTAs per SM; four CTAs per SM
 // share the shared memory with fewer stages each.
 template <typename WT, int RS> constexpr int p1_stages() {
     return P1Traits<WT>::kMinBlocks >= 4 ? (RS <= 10 ? 6 : 5) : 8;
-}
-
-// Planes of the column offsets oxa..oxb in consumption order (o_y = 0 is skipped
-// for o_x <= 0: those offsets belong to the other half of the window).
-__device__ __forceinline__ int p1_planes(int oxa, int oxb, int rs) {
-    if (oxb < oxa) return 0;
-    const int nonpos = max(0, min(oxb, 0) - oxa + 1);
-    return (oxb - oxa + 1) * (rs + 1) - nonpos;
 }
 
 // Phase 1 for one tile at (x0, y0) and the column offsets oxa..oxb: writes the
@@ -163,7 +148,6 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
                                         const float* __restrict__ z, int oxa, int oxb, int x0, int y0,
                                         float* __restrict__ out, unsigned* __restrict__ err) {
     constexpr bool kComp = P1Traits<WT>::kComp;
-    constexpr bool kPrefetch = P1Traits<WT>::kPrefetch;
     constexpr int kStages = p1_stages<WT, RS>();
     constexpr int RH = kTH + RS;
     constexpr int RW = kTW + 2 * RS;
@@ -265,7 +249,6 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
     // consumers
     const int c = tid;
     const int lane = tid & 31;
-    const int nplanes = p1_planes(oxa, oxb, RS);
     bool ok = true;
     // wait for the next plane, copy this thread's column of it to registers and
     // release the stage
@@ -294,16 +277,13 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
     };
-    float qo[kTH], tot[kTH], comp[kTH], wn[kTH];
+    float qo[kTH], tot[kTH], comp[kTH];
 #pragma unroll
     for (int r = 0; r < kTH; ++r) {
         qo[r] = qt[r * RW + c + RS];
         tot[r] = 0.f;
         comp[r] = 0.f;
-        wn[r] = 0.f;
     }
-    int q = 0;
-    if (kPrefetch && nplanes > 0) fetch(wn);
     for (int ox = oxa; ox <= oxb; ++ox) {
         const int col = c + RS + ox;
         float strip[RH], bacc[RH], fw[kTH];
@@ -318,13 +298,7 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
         for (int oy = 0; oy <= RS; ++oy) {
             if (oy == 0 && ox <= 0) continue;
             float w[kTH];
-            if constexpr (kPrefetch) {
-#pragma unroll
-                for (int r = 0; r < kTH; ++r) w[r] = wn[r];
-                if (++q < nplanes) fetch(wn);
-            } else {
-                fetch(w);
-            }
+            fetch(w);
             // with kComp the forward terms of one o_x are summed apart and added to
             // the total with an error-free transformation; otherwise straight into it
 #pragma unroll

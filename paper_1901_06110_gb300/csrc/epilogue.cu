@@ -92,7 +92,7 @@ balance_epilogue_kernel(Cover cv, int H, int W, const float* __restrict__ d_in, 
 }
 
 template <int KIND, int SL>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, SL > 0 ? 4 : 3)
 combine_update_kernel(Cover cv, EpilogueArgs a) {
     const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     combine_update_body<KIND, SL>(cv, a, a.do_x, blockIdx.y * kXH, blockIdx.x * kXW, a.partials + 2 * bid);

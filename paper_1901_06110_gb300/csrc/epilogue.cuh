@@ -15,6 +15,8 @@ namespace dsg {
 // lies inside one phase-1 tile (ty, tx): the candidate tiles are the same for the
 // whole block; per pixel only the halo tests differ.  Fixed order: own tile, the
 // tile above, left, upper left, right, upper right; slices innermost.
+constexpr int kGatherGroup = 4;  // slices whose partial-region loads are issued together
+
 struct TileCover {
     const float* own;  // region of (ty, tx), slice 0
     size_t region, slice_stride;
@@ -71,10 +73,12 @@ __device__ __forceinline__ void balance_decide(BalanceCtl* ctl, float e, float m
     if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
 }
 
-// Sum of the regions that cover pixel (li, lj) of the tile.  SL > 0: the slice
-// count known at compile time, so that the whole sum unrolls and
-// its loads can be issued together with the caller's other loads; a region that
-// does not cover the pixel then adds an exact zero.  SL = 0: any slice count.
+// Sum of the regions that cover pixel (li, lj) of the tile, per slice in the order
+// own, up, left, upper left, right, upper right.  SL > 0: the slice count known at
+// compile time, so that the whole sum unrolls and its loads are issued together
+// with the caller's other loads (a region that does not cover the pixel adds an
+// exact zero).  SL = 0: any slice count, in groups of kGatherGroup slices whose
+// loads are issued before their sums.
 template <int SL = 0>
 __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj) {
     const int rs = c.rs, RW = c.RW;
@@ -101,19 +105,42 @@ __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj)
             acc += v4;
             acc += v5;
         }
-        return acc;
-    }
-#pragma unroll 2
-    for (int sl = 0; sl < c.slices; ++sl, base += c.slice_stride) {
-        acc += __ldcg(base + own_cell);
-        if (up) acc += __ldcg(base + c.up_d + up_cell);
-        if (left) {
-            acc += __ldcg(base + c.left_d + own_cell + kTmaTW);
-            if (up) acc += __ldcg(base + c.up_d + c.left_d + up_cell + kTmaTW);
+    } else {
+        // the counts of the common plans take their unrolled forms
+        switch (c.slices) {
+            case 1: return tile_gather<1>(c, li, lj);
+            case 2: return tile_gather<2>(c, li, lj);
+            case 3: return tile_gather<3>(c, li, lj);
+            case 4: return tile_gather<4>(c, li, lj);
+            default: break;
         }
-        if (right) {
-            acc += __ldcg(base + c.right_d + own_cell - kTmaTW);
-            if (up) acc += __ldcg(base + c.up_d + c.right_d + up_cell - kTmaTW);
+        for (int s0 = 0; s0 < c.slices; s0 += kGatherGroup) {
+            float v[kGatherGroup][6];
+#pragma unroll
+            for (int k = 0; k < kGatherGroup; ++k) {
+                const bool ok = s0 + k < c.slices;
+                const float* b = base + (ok ? (size_t)(s0 + k) * c.slice_stride : 0);
+                v[k][0] = ok ? __ldcg(b + own_cell) : 0.f;
+                v[k][1] = (ok && up) ? __ldcg(b + c.up_d + up_cell) : 0.f;
+                v[k][2] = (ok && left) ? __ldcg(b + c.left_d + own_cell + kTmaTW) : 0.f;
+                v[k][3] = (ok && left && up) ? __ldcg(b + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
+                v[k][4] = (ok && right) ? __ldcg(b + c.right_d + own_cell - kTmaTW) : 0.f;
+                v[k][5] = (ok && right && up) ? __ldcg(b + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kGatherGroup; ++k) {
+                if (s0 + k >= c.slices) break;
+                acc += v[k][0];
+                if (up) acc += v[k][1];
+                if (left) {
+                    acc += v[k][2];
+                    if (up) acc += v[k][3];
+                }
+                if (right) {
+                    acc += v[k][4];
+                    if (up) acc += v[k][5];
+                }
+            }
         }
     }
     return acc;
@@ -122,6 +149,7 @@ __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj)
 // The same sum with TwoSum compensation, in the fixed order of gather_partials
 // (per slice: upper left, up, upper right, left, own, right); a region that does
 // not cover the pixel contributes an exact zero, which leaves the sum unchanged.
+// SL > 0: every slice's loads at once; SL = 0: groups of kGatherGroup slices.
 template <int SL = 0>
 __device__ __forceinline__ float tile_gather_comp(const TileCover& c, int li, int lj) {
     const int rs = c.rs, RW = c.RW;
@@ -130,23 +158,38 @@ __device__ __forceinline__ float tile_gather_comp(const TileCover& c, int li, in
     const bool right = c.right_ok && lj >= kTmaTW - rs;
     const int own_cell = li * RW + lj + rs;
     const int up_cell = (li + kTmaTH) * RW + lj + rs;
+    if constexpr (SL == 0) {  // the counts of the common plans take their unrolled forms
+        switch (c.slices) {
+            case 1: return tile_gather_comp<1>(c, li, lj);
+            case 2: return tile_gather_comp<2>(c, li, lj);
+            case 3: return tile_gather_comp<3>(c, li, lj);
+            case 4: return tile_gather_comp<4>(c, li, lj);
+            default: break;
+        }
+    }
     CompSum acc;
     const float* base = c.own;
+    constexpr int kG = SL > 0 ? SL : kGatherGroup;
     const int ns = SL > 0 ? SL : c.slices;
-#pragma unroll(SL > 0 ? SL : 2)
-    for (int sl = 0; sl < ns; ++sl, base += c.slice_stride) {
-        const float v0 = (up && left) ? __ldcg(base + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
-        const float v1 = up ? __ldcg(base + c.up_d + up_cell) : 0.f;
-        const float v2 = (up && right) ? __ldcg(base + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
-        const float v3 = left ? __ldcg(base + c.left_d + own_cell + kTmaTW) : 0.f;
-        const float v4 = __ldcg(base + own_cell);
-        const float v5 = right ? __ldcg(base + c.right_d + own_cell - kTmaTW) : 0.f;
-        acc.add(v0);
-        acc.add(v1);
-        acc.add(v2);
-        acc.add(v3);
-        acc.add(v4);
-        acc.add(v5);
+    for (int s0 = 0; s0 < ns; s0 += kG) {
+        float v[kG][6];
+#pragma unroll
+        for (int k = 0; k < kG; ++k) {
+            const bool ok = s0 + k < ns;
+            const float* b = base + (ok ? (size_t)(s0 + k) * c.slice_stride : 0);
+            v[k][0] = (ok && up && left) ? __ldcg(b + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
+            v[k][1] = (ok && up) ? __ldcg(b + c.up_d + up_cell) : 0.f;
+            v[k][2] = (ok && up && right) ? __ldcg(b + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
+            v[k][3] = (ok && left) ? __ldcg(b + c.left_d + own_cell + kTmaTW) : 0.f;
+            v[k][4] = ok ? __ldcg(b + own_cell) : 0.f;
+            v[k][5] = (ok && right) ? __ldcg(b + c.right_d + own_cell - kTmaTW) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kG; ++k) {
+            if (s0 + k >= ns) break;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc.add(v[k][q]);
+        }
     }
     return acc.value();
 }

@@ -10,6 +10,7 @@
 // Single-photon imaging (Sec. 4.2): grad f(x)_i = h'(max(x_i, eps)) with
 // h'(t) = (eta/K) (K0 - K1 e^{-z} / (1 - e^{-z})), z = eta t / K; 1 - e^{-z} is
 // evaluated as -expm1(-z).
+#include <type_traits>
 #include <math.h>
 
 #include "common.cuh"
@@ -36,52 +37,73 @@ constexpr int kBX = 32, kBY = 8;
 
 dim3 grid2(int H, int W) { return dim3((W + kBX - 1) / kBX, (H + kBY - 1) / kBY); }
 
-// out(q) = sum_a t(a) sum_b t(b) x(2q - (a, b)) + c aux(q), periodic
+// out(q) = sum_a t(a) sum_b t(b) x(2q - (a, b)) + c aux(q), periodic.  The blur
+// radius R is a template parameter, so both tap loops unroll and a row's loads are
+// issued together instead of each after the previous FMA.
+template <int R>
 __global__ void sr_forward_kernel(const float* __restrict__ x, int H, int W, BlurTaps taps,
                                   const float* __restrict__ aux, float c, float* __restrict__ out) {
     const int h = H / 2, w = W / 2;
     const int qj = blockIdx.x * kBX + threadIdx.x;
     const int qi = blockIdx.y * kBY + threadIdx.y;
     if (qi >= h || qj >= w) return;
-    const int r = taps.r;
+    int cols[2 * R + 1];
+#pragma unroll
+    for (int b = -R; b <= R; ++b) cols[b + R] = wrap_index(2 * qj - b, W);
     float acc = 0.f;
-    for (int a = -r; a <= r; ++a) {
-        const int pi = wrap_index(2 * qi - a, H);
-        const float* row = x + (size_t)pi * W;
+#pragma unroll
+    for (int a = -R; a <= R; ++a) {
+        const float* row = x + (size_t)wrap_index(2 * qi - a, H) * W;
         float ra = 0.f;
-        for (int b = -r; b <= r; ++b) ra = fmaf(taps.t[b + r], __ldg(row + wrap_index(2 * qj - b, W)), ra);
-        acc = fmaf(taps.t[a + r], ra, acc);
+#pragma unroll
+        for (int b = -R; b <= R; ++b) ra = fmaf(taps.t[b + R], __ldg(row + cols[b + R]), ra);
+        acc = fmaf(taps.t[a + R], ra, acc);
     }
     const size_t q = (size_t)qi * w + qj;
     out[q] = aux ? fmaf(c, aux[q], acc) : acc;
 }
 
-// (A^T r)(p) = sum_a t(a) sum_b t(b) u(p + (a, b)), u = r zero-filled at even pixels
+// (A^T r)(p) = sum_a t(a) sum_b t(b) u(p + (a, b)), u = r zero-filled at even pixels:
+// the taps a (b) with p + a (p + b) even, in increasing order
+template <int R>
 __device__ __forceinline__ float sr_adjoint_at(const float* __restrict__ rlo, int H, int W,
                                               const BlurTaps& taps, int pi, int pj) {
     const int w = W / 2;
-    const int r = taps.r;
+    const int pa = (pi - R) & 1, pb = (pj - R) & 1;  // parity of the first tap used
+    int cols[R + 1];
+#pragma unroll
+    for (int k = 0; k <= R; ++k) {
+        const int b = -R + pb + 2 * k;
+        cols[k] = b <= R ? wrap_index(pj + b, W) >> 1 : 0;
+    }
     float acc = 0.f;
-    // first tap a with pi + a even
-    for (int a = -r + ((pi - r) & 1); a <= r; a += 2) {
-        const int qi = wrap_index(pi + a, H) >> 1;
-        const float* row = rlo + (size_t)qi * w;
+#pragma unroll
+    for (int k = 0; k <= R; ++k) {
+        const int a = -R + pa + 2 * k;
+        if (a > R) break;
+        const float* row = rlo + (size_t)(wrap_index(pi + a, H) >> 1) * w;
         float ra = 0.f;
-        for (int b = -r + ((pj - r) & 1); b <= r; b += 2)
-            ra = fmaf(taps.t[b + r], __ldg(row + (wrap_index(pj + b, W) >> 1)), ra);
-        acc = fmaf(taps.t[a + r], ra, acc);
+#pragma unroll
+        for (int kb = 0; kb <= R; ++kb) {
+            const int b = -R + pb + 2 * kb;
+            if (b > R) break;
+            ra = fmaf(taps.t[b + R], __ldg(row + cols[kb]), ra);
+        }
+        acc = fmaf(taps.t[a + R], ra, acc);
     }
     return acc;
 }
 
+template <int R>
 __global__ void sr_adjoint_kernel(const float* __restrict__ rlo, int H, int W, BlurTaps taps,
                                   float* __restrict__ out) {
     const int pj = blockIdx.x * kBX + threadIdx.x;
     const int pi = blockIdx.y * kBY + threadIdx.y;
     if (pi >= H || pj >= W) return;
-    out[(size_t)pi * W + pj] = sr_adjoint_at(rlo, H, W, taps, pi, pj);
+    out[(size_t)pi * W + pj] = sr_adjoint_at<R>(rlo, H, W, taps, pi, pj);
 }
 
+template <int R>
 __global__ void sr_xupdate_kernel(const float* __restrict__ rlo, int H, int W, BlurTaps taps,
                                   float* __restrict__ x, const float* __restrict__ v,
                                   const float* __restrict__ u, float* __restrict__ z, float mu,
@@ -90,7 +112,7 @@ __global__ void sr_xupdate_kernel(const float* __restrict__ rlo, int H, int W, B
     const int pi = blockIdx.y * kBY + threadIdx.y;
     if (pi >= H || pj >= W) return;
     const size_t p = (size_t)pi * W + pj;
-    const float g = sr_adjoint_at(rlo, H, W, taps, pi, pj);
+    const float g = sr_adjoint_at<R>(rlo, H, W, taps, pi, pj);
     const float up = u[p];
     const float xb = mu * (alpha * x[p] + rho * (v[p] - up) - g);
     const float xn = project(xb, constraint);
@@ -218,26 +240,50 @@ __global__ void init_kernel(const float* __restrict__ guide, int n, float* __res
 
 }  // namespace
 
+// the blur radii 0..8 as template arguments
+template <typename F>
+cudaError_t by_blur_r(int r, F&& f) {
+    switch (r) {
+        case 0: return f(std::integral_constant<int, 0>{});
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2: return f(std::integral_constant<int, 2>{});
+        case 3: return f(std::integral_constant<int, 3>{});
+        case 4: return f(std::integral_constant<int, 4>{});
+        case 5: return f(std::integral_constant<int, 5>{});
+        case 6: return f(std::integral_constant<int, 6>{});
+        case 7: return f(std::integral_constant<int, 7>{});
+        case 8: return f(std::integral_constant<int, 8>{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_sr_forward(const float* x, int H, int W, BlurTaps taps, const float* aux, float c,
                               float* out, cudaStream_t st) {
-    sr_forward_kernel<<<grid2(H / 2, W / 2), dim3(kBX, kBY), 0, st>>>(x, H, W, taps, aux, c, out);
-    count_launches(1);
-    return cudaGetLastError();
+    return by_blur_r(taps.r, [&](auto rr) {
+        sr_forward_kernel<decltype(rr)::value><<<grid2(H / 2, W / 2), dim3(kBX, kBY), 0, st>>>(x, H, W, taps, aux, c,
+                                                                                              out);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_sr_adjoint(const float* r, int H, int W, BlurTaps taps, float* out, cudaStream_t st) {
-    sr_adjoint_kernel<<<grid2(H, W), dim3(kBX, kBY), 0, st>>>(r, H, W, taps, out);
-    count_launches(1);
-    return cudaGetLastError();
+    return by_blur_r(taps.r, [&](auto rr) {
+        sr_adjoint_kernel<decltype(rr)::value><<<grid2(H, W), dim3(kBX, kBY), 0, st>>>(r, H, W, taps, out);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_sr_xupdate(const float* r, int H, int W, BlurTaps taps, float* x, const float* v,
                               const float* u, float* z, float mu, float alpha, float rho,
                               int constraint, cudaStream_t st) {
-    sr_xupdate_kernel<<<grid2(H, W), dim3(kBX, kBY), 0, st>>>(r, H, W, taps, x, v, u, z, mu, alpha,
-                                                              rho, constraint);
-    count_launches(1);
-    return cudaGetLastError();
+    return by_blur_r(taps.r, [&](auto rr) {
+        sr_xupdate_kernel<decltype(rr)::value><<<grid2(H, W), dim3(kBX, kBY), 0, st>>>(r, H, W, taps, x, v, u, z, mu,
+                                                                                      alpha, rho, constraint);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_sr_xupdate_fused(const float* x_in, float* x_out, const float* y, int H, int W,

@@ -231,7 +231,10 @@ dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad);
 
 /* Run `iters` iterations of Algorithm 1 with penalty rho > 0, mu = 1/(alpha + rho):
  *   x <- Pi_C(mu (alpha x + rho (v - u) - grad f(x)));  v <- W (x + u);  u <- u + x - v.
- * Uses p->den's handle stream.  Synchronises only if resid_hist is given. */
+ * Uses p->den's handle stream.  Synchronises only if resid_hist is given.  On the
+ * stencil path (and with profiling off) the kernel sequence is recorded once as a
+ * CUDA graph on the handle and replayed while the problem's buffers, sizes and
+ * parameters and the balanced W are unchanged; any change records it again. */
 dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters);
 
 /* Standard PnP-ADMM for LPNP_SR2 (the comparison system of Sec. 4.1): the x-update

@@ -676,6 +676,12 @@ dsgnlm_status adapt_w(dsgnlm* h, const Adapt& ad, int H, int W) {
     return (s == DSGNLM_NOT_CONVERGED || s == DSGNLM_STALLED) ? DSGNLM_OK : s;
 }
 
+template <typename T>
+void key_put(std::vector<unsigned char>& k, const T& v) {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+    k.insert(k.end(), b, b + sizeof(T));
+}
+
 dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adapt* ad) {
     dsgnlm_status s = check_problem(p, true, ad == nullptr);
     if (s != DSGNLM_OK) return s;
@@ -721,17 +727,6 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             DSG_CK(h->gbuf.ensure(n * sizeof(float)));
             if (sym) DSG_CK(h->rlo.ensure(sizeof(float) * n / 4));
             if (iters > 1) DSG_CK(h->ensure_side());
-            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
-                cudaError_t e = sr_gradient(xA, h->gbuf.as<float>(), h->stream);
-                if (e != cudaSuccess) return e;
-                return launch_xupdate_point(xA, h->gbuf.as<float>(), p->v, p->u, h->z.as<float>(), (int)n, mu,
-                                            p->alpha, rho, p->constraint, h->stream);
-            }));
-        } else {
-            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] {
-                return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
-                                          h->z.as<float>(), mu, p->alpha, rho, p->constraint, h->stream);
-            }));
         }
         EpilogueArgs ea{};
         ea.H = H;
@@ -753,34 +748,109 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
         ea.alpha = p->alpha;
         ea.rho = rho;
         ea.constraint = p->constraint;
+        ea.x_in = xA;
+        ea.x_out = xA;
         const int kind = sr ? 0 : 1;
-        for (int it = 0; it < iters; ++it) {
+        // the x-update of iteration 0 (its gradient at the initial x, for SR)
+        auto first_update = [&](cudaStream_t st) -> cudaError_t {
+            if (!sr)
+                return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
+                                          h->z.as<float>(), mu, p->alpha, rho, p->constraint, st);
+            cudaError_t e = sr_gradient(xA, h->gbuf.as<float>(), st);
+            if (e != cudaSuccess) return e;
+            return launch_xupdate_point(xA, h->gbuf.as<float>(), p->v, p->u, h->z.as<float>(), (int)n, mu, p->alpha,
+                                        rho, p->constraint, st);
+        };
+        // phase 1 of iteration it, the next gradient beside it, then the epilogue
+        auto iteration = [&](int it, cudaStream_t st) -> cudaError_t {
             const bool do_x = it < iters - 1;
-            if (ad && it < ad->iters) {
-                s = adapt_w(h, *ad, H, W);
-                if (s != DSGNLM_OK) return s;
-                ea.d = h->d_final;
-                ea.t = h->t_final;
-                ea.inv_m = h->inv_m;
-            }
-            if (sr && do_x) DSG_CK(cudaEventRecord(h->ev_fork, h->stream));
-            DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
-                return launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
-                                         h->err.as<unsigned>(), nullptr, h->stream);
-            }));
+            cudaError_t e = cudaSuccess;
+            if (sr && do_x) e = cudaEventRecord(h->ev_fork, st);
+            if (e == cudaSuccess)
+                e = h->timed(DSGNLM_PROF_APPLY, [&] {
+                    return launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
+                                             h->err.as<unsigned>(), nullptr, st);
+                });
             if (sr && do_x) {
-                DSG_CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-                DSG_CK(sr_gradient(xA, h->gbuf.as<float>(), h->side));
-                DSG_CK(cudaEventRecord(h->ev_join, h->side));
-                DSG_CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+                if (e == cudaSuccess) e = sr_gradient(xA, h->gbuf.as<float>(), h->side);
+                if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->side);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_join, 0);
             }
             ea.do_x = do_x;
-            ea.x_in = xA;
-            ea.x_out = xA;
             ea.partials = h->partials.as<double>() + 2 * (size_t)nblocks * it;
-            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_combine_update(kind, h->plan, h->rs, ea, h->stream); }));
+            if (e == cudaSuccess)
+                e = h->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_combine_update(kind, h->plan, h->rs, ea, st); });
+            return e;
+        };
+        bool ran = false;
+        if (!ad && !h->prof) {
+            // The sequence is recorded once as a CUDA graph and replayed while everything
+            // its kernel parameters bake in is unchanged: one launch per solve instead of
+            // one per kernel, so the host's launch rate does not gap the GPU.
+            std::vector<unsigned char> key;
+            const int ints[12] = {H, W, iters, kind, (int)sym, h->dtype, h->rs, nblocks, p->constraint, p->K,
+                                  h->plan.tiles_x, h->plan.tiles_y};
+            const float fls[6] = {mu, p->alpha, rho, h->inv_m, p->eta, p->spi_eps};
+            const void* ptrs[18] = {xA, p->v, p->u, p->y, p->counts, h->z.p, h->gbuf.p, h->rlo.p, h->d_final,
+                                    h->t_final, h->partials.p, h->hist.p, h->arrive.p, h->err.p, h->plan.partials,
+                                    h->side, h->ev_fork, h->ev_join};
+            key_put(key, ints);
+            key_put(key, fls);
+            key_put(key, ptrs);
+            key_put(key, taps);
+            key_put(key, h->plan.splits);
+            key.insert(key.end(), h->plan.tmap, h->plan.tmap + 128);
+            cudaError_t e = cudaSuccess;
+            if (!h->s_exec || key != h->s_key) {
+                if (h->s_exec) cudaGraphExecDestroy(h->s_exec);
+                if (h->s_graph) cudaGraphDestroy(h->s_graph);
+                h->s_exec = nullptr;
+                h->s_graph = nullptr;
+                h->s_key.clear();
+                if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed);
+                if (e == cudaSuccess) {
+                    g_capturing = true;
+                    cudaError_t e1 = first_update(h->cap_stream);
+                    for (int it = 0; it < iters && e1 == cudaSuccess; ++it) e1 = iteration(it, h->cap_stream);
+                    if (e1 == cudaSuccess) e1 = launch_reduce_residuals(red, iters, nblocks, h->cap_stream);
+                    g_capturing = false;
+                    cudaGraph_t g = nullptr;
+                    e = cudaStreamEndCapture(h->cap_stream, &g);
+                    if (e == cudaSuccess) e = e1;
+                    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->s_exec, g, 0);
+                    if (e == cudaSuccess) {
+                        h->s_graph = g;
+                        h->s_key = key;
+                    } else {
+                        if (g) cudaGraphDestroy(g);
+                        h->s_exec = nullptr;
+                        (void)cudaGetLastError();
+                    }
+                }
+            }
+            if (h->s_exec) {
+                DSG_CK(cudaGraphLaunch(h->s_exec, h->stream));
+                const uint64_t grad = sr ? (sym ? 2 : 1) : 0;
+                count_launches((sr ? grad + 1 : 1) + 2 * (uint64_t)iters + grad * (uint64_t)(iters - 1) + 1);
+                ran = true;
+            }
         }
-        DSG_CK(launch_reduce_residuals(red, iters, nblocks, h->stream));
+        if (!ran) {  // launched directly: profiling, adaptive W, or no graph
+            DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] { return first_update(h->stream); }));
+            for (int it = 0; it < iters; ++it) {
+                if (ad && it < ad->iters) {
+                    s = adapt_w(h, *ad, H, W);
+                    if (s != DSGNLM_OK) return s;
+                    ea.d = h->d_final;
+                    ea.t = h->t_final;
+                    ea.inv_m = h->inv_m;
+                }
+                DSG_CK(iteration(it, h->stream));
+            }
+            DSG_CK(launch_reduce_residuals(red, iters, nblocks, h->stream));
+        }
     } else {
         if (sr) DSG_CK(h->x2.ensure(n * sizeof(float)));
         xB = sr ? h->x2.as<float>() : p->x;
@@ -935,11 +1005,6 @@ dsgnlm_status lpnp_solve_adaptive(const lpnp_problem* p, float rho, int iters, i
 
 namespace {
 
-template <typename T>
-void key_put(std::vector<unsigned char>& k, const T& v) {
-    const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
-    k.insert(k.end(), b, b + sizeof(T));
-}
 
 // Batched Algorithm 1.  `slices` > 0 splits the offsets of every image into that many
 // slices (the batch fills the GPU by itself, so fewer slices than a lone image

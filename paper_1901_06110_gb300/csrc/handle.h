@@ -101,6 +101,10 @@ struct dsgnlm {
     cudaGraph_t b_graph = nullptr;
     cudaGraphExec_t b_exec = nullptr;
     std::vector<unsigned char> b_key;
+    // the single-image solve's sequence as a CUDA graph, with the values it was recorded for
+    cudaGraph_t s_graph = nullptr;
+    cudaGraphExec_t s_exec = nullptr;
+    std::vector<unsigned char> s_key;
     // optional per-kernel timing
     bool prof = false;
     ProfPool pools[dsg::kProfKinds];
@@ -138,6 +142,11 @@ struct dsgnlm {
         b_exec = nullptr;
         b_graph = nullptr;
         b_key.clear();
+        if (s_exec) cudaGraphExecDestroy(s_exec);
+        if (s_graph) cudaGraphDestroy(s_graph);
+        s_exec = nullptr;
+        s_graph = nullptr;
+        s_key.clear();
     }
     void release_all() {
         release_graphs();

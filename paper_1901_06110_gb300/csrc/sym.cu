@@ -12,6 +12,8 @@
 // Conjugate gradients for (A^T A + rho I) x = b keep their scalars in device
 // memory (each dot product: fixed-order double block sums, then one reducing
 // block), so the steps run back to back without host round trips.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "xupdate.cuh"
@@ -47,7 +49,9 @@ __device__ __forceinline__ int ext_candidates(int i, int n, int R, int (&e)[3]) 
 
 constexpr int kBX = 32, kBY = 8;
 
-template <int BC>
+// The blur radius R is a template parameter: the tap loops unroll, and a row's loads
+// are issued ahead of the FMA chain that consumes them.
+template <int BC, int R>
 __global__ void __launch_bounds__(256)
 sr_forward_bc_kernel(const float* __restrict__ x, int H, int W, BlurTaps taps, const float* __restrict__ aux, float c,
                      float* __restrict__ out) {
@@ -55,27 +59,30 @@ sr_forward_bc_kernel(const float* __restrict__ x, int H, int W, BlurTaps taps, c
     const int qj = blockIdx.x * kBX + threadIdx.x;
     const int qi = blockIdx.y * kBY + threadIdx.y;
     if (qi >= h || qj >= w) return;
-    const int r = taps.r;
+    int cols[2 * R + 1];
+#pragma unroll
+    for (int b = -R; b <= R; ++b) cols[b + R] = ext_index<BC>(2 * qj - b, W);
     float acc = 0.f;
-    for (int a = -r; a <= r; ++a) {
+#pragma unroll
+    for (int a = -R; a <= R; ++a) {
         const float* row = x + (size_t)ext_index<BC>(2 * qi - a, H) * W;
         float ra = 0.f;
-        for (int b = -r; b <= r; ++b) ra = fmaf(taps.t[b + r], __ldg(row + ext_index<BC>(2 * qj - b, W)), ra);
-        acc = fmaf(taps.t[a + r], ra, acc);
+#pragma unroll
+        for (int b = -R; b <= R; ++b) ra = fmaf(taps.t[b + R], __ldg(row + cols[b + R]), ra);
+        acc = fmaf(taps.t[a + R], ra, acc);
     }
     const size_t q = (size_t)qi * w + qj;
     out[q] = aux ? fmaf(c, aux[q], acc) : acc;
 }
 
 // out = A^T rlo + rho * pin (pin may be null); with part, the block's sum of pin * out
-template <int BC>
+template <int BC, int R>
 __global__ void __launch_bounds__(256)
 sr_adjoint_bc_kernel(const float* __restrict__ rlo, int H, int W, BlurTaps taps, float rho,
                      const float* __restrict__ pin, float* __restrict__ out, double* __restrict__ part) {
     const int h = H / 2, w = W / 2;
     const int pj = blockIdx.x * kBX + threadIdx.x;
     const int pi = blockIdx.y * kBY + threadIdx.y;
-    const int R = taps.r;
     double prod = 0.0;
     if (pi < H && pj < W) {
         int ei[3], ej[3];
@@ -84,14 +91,21 @@ sr_adjoint_bc_kernel(const float* __restrict__ rlo, int H, int W, BlurTaps taps,
         float acc = 0.f;
         for (int ci = 0; ci < mi; ++ci) {
             const int e = ei[ci];
-            for (int a = -R + ((e - R) & 1); a <= R; a += 2) {  // (e + a) even
+            // the taps a with (e + a) even, in increasing order
+#pragma unroll
+            for (int k = 0; k <= R; ++k) {
+                const int a = -R + ((e - R) & 1) + 2 * k;
+                if (a > R) break;
                 const int qi = (e + a) >> 1;
                 if (qi < 0 || qi >= h) continue;
                 const float* row = rlo + (size_t)qi * w;
                 float ra = 0.f;
                 for (int cj = 0; cj < mj; ++cj) {
                     const int f = ej[cj];
-                    for (int b = -R + ((f - R) & 1); b <= R; b += 2) {
+#pragma unroll
+                    for (int kb = 0; kb <= R; ++kb) {
+                        const int b = -R + ((f - R) & 1) + 2 * kb;
+                        if (b > R) break;
                         const int qj = (f + b) >> 1;
                         if (qj < 0 || qj >= w) continue;
                         ra = fmaf(taps.t[b + R], __ldg(row + qj), ra);
@@ -222,24 +236,44 @@ int sr_adjoint_bc_blocks(int H, int W) {
 
 int cg_vector_blocks(int n) { return vblocks(n); }
 
+// the boundary (0 periodic, 1 symmetric) and the blur radius 0..8 as template arguments
+template <typename F>
+cudaError_t by_bc_r(int bc, int r, F&& f) {
+    auto with_r = [&](auto b) -> cudaError_t {
+        switch (r) {
+            case 0: return f(b, std::integral_constant<int, 0>{});
+            case 1: return f(b, std::integral_constant<int, 1>{});
+            case 2: return f(b, std::integral_constant<int, 2>{});
+            case 3: return f(b, std::integral_constant<int, 3>{});
+            case 4: return f(b, std::integral_constant<int, 4>{});
+            case 5: return f(b, std::integral_constant<int, 5>{});
+            case 6: return f(b, std::integral_constant<int, 6>{});
+            case 7: return f(b, std::integral_constant<int, 7>{});
+            case 8: return f(b, std::integral_constant<int, 8>{});
+            default: return cudaErrorInvalidValue;
+        }
+    };
+    return bc == 1 ? with_r(std::integral_constant<int, 1>{}) : with_r(std::integral_constant<int, 0>{});
+}
+
 cudaError_t launch_sr_forward_bc(int bc, const float* x, int H, int W, BlurTaps taps, const float* aux, float c,
                                  float* out, cudaStream_t st) {
-    if (bc == 1)
-        sr_forward_bc_kernel<1><<<grid_lo(H, W), dim3(kBX, kBY), 0, st>>>(x, H, W, taps, aux, c, out);
-    else
-        sr_forward_bc_kernel<0><<<grid_lo(H, W), dim3(kBX, kBY), 0, st>>>(x, H, W, taps, aux, c, out);
-    count_launches(1);
-    return cudaGetLastError();
+    return by_bc_r(bc, taps.r, [&](auto b, auto r) {
+        sr_forward_bc_kernel<decltype(b)::value, decltype(r)::value>
+            <<<grid_lo(H, W), dim3(kBX, kBY), 0, st>>>(x, H, W, taps, aux, c, out);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_sr_adjoint_bc(int bc, const float* rlo, int H, int W, BlurTaps taps, float rho, const float* pin,
                                  float* out, double* part, cudaStream_t st) {
-    if (bc == 1)
-        sr_adjoint_bc_kernel<1><<<grid_hi(H, W), dim3(kBX, kBY), 0, st>>>(rlo, H, W, taps, rho, pin, out, part);
-    else
-        sr_adjoint_bc_kernel<0><<<grid_hi(H, W), dim3(kBX, kBY), 0, st>>>(rlo, H, W, taps, rho, pin, out, part);
-    count_launches(1);
-    return cudaGetLastError();
+    return by_bc_r(bc, taps.r, [&](auto b, auto r) {
+        sr_adjoint_bc_kernel<decltype(b)::value, decltype(r)::value>
+            <<<grid_hi(H, W), dim3(kBX, kBY), 0, st>>>(rlo, H, W, taps, rho, pin, out, part);
+        count_launches(1);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_cg_init(const float* aty, const float* v, const float* u, float rho, const float* mx, float* r,

@@ -164,7 +164,7 @@ def _balance_case(dtype, sizes, rp, rs, h, seed0):
     return singles, batch
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f16"])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_batched_balance_equals_single(gpu_lib, dtype):
     """dsgnlm_balance_batched runs each image's own passes (its plan, buffers and
     stopping rule) in shared launches: scalings, m, update counts, residuals and the
@@ -220,5 +220,23 @@ def test_batched_balance_schedule(gpu_lib):
         da, _ = D.dsgnlm_copy_scaling(a)
         db, _ = D.dsgnlm_copy_scaling(b)
         assert rel_l2(host(db), host(da)) <= 1e-5
+        ones = torch.ones((b.H, b.W), device="cuda")
+        np.testing.assert_allclose(host(D.dsgnlm_apply(b, ones)), 1.0, atol=1e-6)
+
+
+def test_batched_balance_edges(gpu_lib):
+    """A batch of one is the single call; a tolerance every image meets on its first
+    pass stops every image there (no update), and W stays doubly stochastic."""
+    from paper_1901_06110_gb300 import _abi
+    from paper_1901_06110_gb300 import dsgnlm as D
+    singles, batch = _balance_case("f32", [(72, 56)], 2, 3, 0.1, 990)
+    (a, sa), b = singles[0], batch[0]
+    assert D.dsgnlm_balance_batched([b], 1e-6, 300)[0] == sa
+    np.testing.assert_array_equal(host(D.dsgnlm_copy_scaling(a)[0]), host(D.dsgnlm_copy_scaling(b)[0]))
+    singles, batch = _balance_case("f32", [(64, 64), (40, 96), (96, 40)], 2, 3, 0.1, 995)
+    res = D.dsgnlm_balance_batched(batch, 1e9, 300)
+    for (a, _), b, rb in zip(singles, batch, res):
+        sa = D.dsgnlm_balance(a, 1e9, 300)
+        assert rb == sa and rb[0] == _abi.OK and rb[1] == 0
         ones = torch.ones((b.H, b.W), device="cuda")
         np.testing.assert_allclose(host(D.dsgnlm_apply(b, ones)), 1.0, atol=1e-6)

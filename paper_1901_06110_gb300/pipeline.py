@@ -84,9 +84,11 @@ class Solver:
             D._check(lib.lpnp_spi_guide(data.data_ptr(), self.H, self.W, p.K, p.eta, self.guide.data_ptr(),
                                         stream), "lpnp_spi_guide")
         D.dsgnlm_build(self.den, self.guide, p.patch_r, p.search_r, p.h)
-        self.balance = D.dsgnlm_balance(self.den, p.tol, p.maxit)
+        # the initial state does not depend on the balance, which ends with a host
+        # synchronisation: queue it first, so that only the solve follows the wait
         D._check(lib.lpnp_init(self.guide.data_ptr(), self.H * self.W, self.x.data_ptr(),
                                self.v.data_ptr(), self.u.data_ptr(), stream), "lpnp_init")
+        self.balance = D.dsgnlm_balance(self.den, p.tol, p.maxit)
         return D.lpnp_solve(self._problem(data), p.rho, p.iters, residuals=residuals)
 
     def prepare(self, data: torch.Tensor):

@@ -331,9 +331,10 @@ void lpnp_tape_destroy(lpnp_tape_t t);
  * y device [H/2][W/2]; guide device [H][W]; both must stay unchanged until
  * lpnp_backward.  x_out device [H][W] receives x_N.  Records the tape (replacing any
  * earlier recording).  `den` must not be rebuilt before the backward.  The shared
- * memory of the backward limits (2 iters + 1)(16 + 2 N_s)(32 + 2 N_s) and
- * (2 iters + 2 passes + 1)(16 + N_s)(32 + 2 N_s) floats to 220 KiB (EINVAL otherwise).
- * Synchronises the stream once (to read m). */
+ * memory of the backward limits (2 iters + 1)(16 + N_s)(32 + 2 N_s) and
+ * (2 passes + 1)(16 + N_s)(32 + 2 N_s) floats to 220 KiB (EINVAL otherwise).
+ * Synchronises the stream once (to read m); the solve graph is not used (one iteration
+ * per recorded state). */
 dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tape, dsgnlm_t den, const float* y, const float* guide, int H,
                                     int W, int patch_r, int search_r, float bandwidth, int balance_passes,
                                     float alpha, float rho, int iters, float blur_sigma, int blur_r, float* x_out);
@@ -346,6 +347,23 @@ dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tape, dsgnlm_t den, const float*
  * Synchronises the stream. */
 dsgnlm_status lpnp_backward(lpnp_tape_t tape, const float* x_bar, float* y_bar, float* guide_bar, double* h_bar,
                             double* rho_bar);
+
+/* Batched forms for `count` images of one size and one parameter set.  tapes[i] and
+ * dens[i] must be distinct; each image runs on its handle's stream, so handles on
+ * distinct streams overlap their images on the device.  y, guide, x_out (and x_bar,
+ * y_bar, guide_bar) are host arrays of `count` device pointers with the layouts of the
+ * single-image calls.  The forward queues every image's weights, balance and m before
+ * waiting for the first m, then synchronises each stream once; the backward queues
+ * every image's reverse sweep, then synchronises each stream.  h_bar and rho_bar
+ * (host, optional) receive `count` per-image values.  Results equal the single-image
+ * calls bit for bit.  On an error the status of the first failing image is returned
+ * and the tapes of the batch hold no usable recording. */
+dsgnlm_status lpnp_unrolled_forward_batched(lpnp_tape_t* tapes, dsgnlm_t* dens, int count, const float* const* y,
+                                            const float* const* guide, int H, int W, int patch_r, int search_r,
+                                            float bandwidth, int balance_passes, float alpha, float rho, int iters,
+                                            float blur_sigma, int blur_r, float* const* x_out);
+dsgnlm_status lpnp_backward_batched(lpnp_tape_t* tapes, int count, const float* const* x_bar, float* const* y_bar,
+                                    float* const* guide_bar, double* h_bar, double* rho_bar);
 
 /* ---------------------------------------------------------------------------
  * Misc

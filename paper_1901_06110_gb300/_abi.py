@@ -67,6 +67,13 @@ SIGNATURES = {
                                       c_int, c_float, c_float, c_int, c_float, c_int, c_void_p]),
     "lpnp_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
                               ctypes.POINTER(c_double)]),
+    "lpnp_unrolled_forward_batched": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_int,
+                                              ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_int, c_int,
+                                              c_int, c_int, c_float, c_int, c_float, c_float, c_int, c_float,
+                                              c_int, ctypes.POINTER(c_void_p)]),
+    "lpnp_backward_batched": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_void_p),
+                                      ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_double),
+                                      ctypes.POINTER(c_double)]),
     "dsgnlm_profile_enable": (c_int, [c_void_p, c_int]),
     "dsgnlm_profile_read": (c_int, [c_void_p, c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     "dsgnlm_launch_count": (ctypes.c_uint64, []),

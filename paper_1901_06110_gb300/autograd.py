@@ -1,8 +1,10 @@
 """torch.autograd binding of the differentiable form (lpnp_unrolled_forward /
-lpnp_backward in the C ABI): unrolled linearized PnP-ADMM for 2x super-resolution
-with DSG-NLM, differentiable in the observation, the guide, the bandwidth h and
-rho.  Each image keeps its own denoiser handle and checkpoint tape between the
-forward and the backward; all arithmetic runs in the CUDA library."""
+lpnp_backward and their batched forms in the C ABI): unrolled linearized PnP-ADMM for
+2x super-resolution with DSG-NLM, differentiable in the observation, the guide, the
+bandwidth h and rho.  Each image keeps a denoiser handle, a checkpoint tape and a CUDA
+stream between the forward and the backward; these slots are pooled and reused once
+the backward has run, so repeated calls allocate nothing.  All arithmetic runs in the
+CUDA library."""
 from __future__ import annotations
 
 import ctypes
@@ -25,13 +27,17 @@ class UnrollParams:
     blur_r: int = 4
 
 
-class _Tape:
+class _Slot:
+    """One image's tape, FP32 denoiser handle and stream.  The handle launches on the
+    slot's own stream, so the images of a batch overlap on the device."""
+
     def __init__(self):
         self.lib = _abi.load()
         t = ctypes.c_void_p()
         D._check(self.lib.lpnp_tape_create(ctypes.byref(t)), "lpnp_tape_create")
         self.ptr = t
-        self.den = D.dsgnlm_create("f32")
+        self.stream = torch.cuda.Stream()
+        self.den = D.dsgnlm_create("f32", stream=self.stream)
 
     def __del__(self):
         try:
@@ -42,44 +48,144 @@ class _Tape:
             pass
 
 
+_POOL: list[_Slot] = []
+
+
+class _Lease:
+    """Slots held by one recorded forward; they go back to the pool after the backward
+    or when the autograd graph that holds the lease is freed."""
+
+    def __init__(self, count: int):
+        self.slots = [_POOL.pop() if _POOL else _Slot() for _ in range(count)]
+
+    def release(self):
+        _POOL.extend(self.slots)
+        self.slots = []
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def _fork(slots):
+    """Each slot's stream waits for the work queued so far on the current stream."""
+    ev = torch.cuda.Event()
+    ev.record(torch.cuda.current_stream())
+    for s in slots:
+        s.stream.wait_event(ev)
+
+
+def _join(slots):
+    """The current stream waits for the work queued on every slot's stream."""
+    cur = torch.cuda.current_stream()
+    for s in slots:
+        ev = torch.cuda.Event()
+        ev.record(s.stream)
+        cur.wait_event(ev)
+
+
+def _ptrs(vals):
+    return (ctypes.c_void_p * len(vals))(*vals)
+
+
+def _grad_scalar(ctx, idx, value):
+    return torch.tensor(value, dtype=ctx.scalar_dtype[idx - 2]) if ctx.needs_input_grad[idx] else None
+
+
+def _scalar_dtype(v):
+    return v.dtype if isinstance(v, torch.Tensor) else torch.float64
+
+
 class UnrolledSR(torch.autograd.Function):
-    """x_N = unrolled_solve(y, guide, h, rho) for one image."""
+    """x_N = unrolled_solve(y, guide, h, rho) for one image (y [H/2, W/2], guide [H, W])."""
 
     @staticmethod
     def forward(ctx, y, guide, h, rho, params: UnrollParams):
         y = y.detach().contiguous()
         guide = guide.detach().contiguous()
         H, W = guide.shape
-        tape = _Tape()
+        lease = _Lease(1)
+        slot = lease.slots[0]
         x = torch.empty_like(guide)
-        D._check(tape.lib.lpnp_unrolled_forward(
-            tape.ptr, tape.den.handle, D._ptr(y, torch.float32, "y", (H // 2) * (W // 2)),
+        _fork(lease.slots)
+        D._check(slot.lib.lpnp_unrolled_forward(
+            slot.ptr, slot.den.handle, D._ptr(y, torch.float32, "y", (H // 2) * (W // 2)),
             D._ptr(guide, torch.float32, "guide", H * W), H, W, params.patch_r, params.search_r, float(h),
             params.balance_passes, params.alpha, float(rho), params.iters, params.blur_sigma, params.blur_r,
             x.data_ptr()), "lpnp_unrolled_forward")
-        ctx.tape = tape
+        _join(lease.slots)
+        ctx.lease = lease
         ctx.keep = (y, guide)  # the tape reads them in the backward
-        ctx.h_dtype = h.dtype if isinstance(h, torch.Tensor) else torch.float64
+        ctx.scalar_dtype = (_scalar_dtype(h), _scalar_dtype(rho))
         return x
 
     @staticmethod
     def backward(ctx, x_bar):
         y, guide = ctx.keep
+        slot = ctx.lease.slots[0]
         x_bar = x_bar.contiguous().float()
         y_bar = torch.empty_like(y)
         g_bar = torch.empty_like(guide)
         hb = ctypes.c_double(0.0)
         rb = ctypes.c_double(0.0)
-        D._check(ctx.tape.lib.lpnp_backward(ctx.tape.ptr, x_bar.data_ptr(), y_bar.data_ptr(), g_bar.data_ptr(),
-                                            ctypes.byref(hb), ctypes.byref(rb)), "lpnp_backward")
-        ctx.tape = None
-        return (y_bar, g_bar, torch.tensor(hb.value, dtype=ctx.h_dtype),
-                torch.tensor(rb.value, dtype=ctx.h_dtype), None)
+        _fork(ctx.lease.slots)
+        D._check(slot.lib.lpnp_backward(slot.ptr, x_bar.data_ptr(), y_bar.data_ptr(), g_bar.data_ptr(),
+                                        ctypes.byref(hb), ctypes.byref(rb)), "lpnp_backward")
+        _join(ctx.lease.slots)
+        ctx.lease.release()
+        return y_bar, g_bar, _grad_scalar(ctx, 2, hb.value), _grad_scalar(ctx, 3, rb.value), None
+
+
+class UnrolledSRBatch(torch.autograd.Function):
+    """x_N [B, H, W] for y [B, H/2, W/2] and guide [B, H, W] with shared h and rho,
+    through the batched C calls: the B images run on B streams at once."""
+
+    @staticmethod
+    def forward(ctx, y, guide, h, rho, params: UnrollParams):
+        y = y.detach().contiguous()
+        guide = guide.detach().contiguous()
+        B, H, W = guide.shape
+        if y.shape != (B, H // 2, W // 2) or y.dtype != torch.float32 or guide.dtype != torch.float32:
+            raise ValueError("y must be float32 [B, H/2, W/2] and guide float32 [B, H, W]")
+        lease = _Lease(B)
+        x = torch.empty_like(guide)
+        lib = lease.slots[0].lib
+        _fork(lease.slots)
+        D._check(lib.lpnp_unrolled_forward_batched(
+            _ptrs([s.ptr.value for s in lease.slots]), _ptrs([s.den.handle.value for s in lease.slots]), B,
+            _ptrs([y[b].data_ptr() for b in range(B)]), _ptrs([guide[b].data_ptr() for b in range(B)]), H, W,
+            params.patch_r, params.search_r, float(h), params.balance_passes, params.alpha, float(rho),
+            params.iters, params.blur_sigma, params.blur_r, _ptrs([x[b].data_ptr() for b in range(B)])),
+            "lpnp_unrolled_forward_batched")
+        _join(lease.slots)
+        ctx.lease = lease
+        ctx.keep = (y, guide)
+        ctx.scalar_dtype = (_scalar_dtype(h), _scalar_dtype(rho))
+        return x
+
+    @staticmethod
+    def backward(ctx, x_bar):
+        y, guide = ctx.keep
+        slots = ctx.lease.slots
+        B = len(slots)
+        x_bar = x_bar.contiguous().float()
+        y_bar = torch.empty_like(y)
+        g_bar = torch.empty_like(guide)
+        hb = (ctypes.c_double * B)()
+        rb = (ctypes.c_double * B)()
+        _fork(slots)
+        D._check(slots[0].lib.lpnp_backward_batched(
+            _ptrs([s.ptr.value for s in slots]), B, _ptrs([x_bar[b].data_ptr() for b in range(B)]),
+            _ptrs([y_bar[b].data_ptr() for b in range(B)]), _ptrs([g_bar[b].data_ptr() for b in range(B)]), hb, rb),
+            "lpnp_backward_batched")
+        _join(slots)
+        ctx.lease.release()
+        return y_bar, g_bar, _grad_scalar(ctx, 2, sum(hb)), _grad_scalar(ctx, 3, sum(rb)), None
 
 
 def unrolled_sr(y, guide, h, rho, params: UnrollParams | None = None):
-    """Batched convenience: y [B, H/2, W/2], guide [B, H, W], h and rho scalars
-    (tensors to receive gradients); returns x_N [B, H, W]."""
-    params = params or UnrollParams()
-    outs = [UnrolledSR.apply(y[b], guide[b], h, rho, params) for b in range(guide.shape[0])]
-    return torch.stack(outs)
+    """Batched: y [B, H/2, W/2], guide [B, H, W], h and rho scalars (tensors to receive
+    gradients); returns x_N [B, H, W]."""
+    return UnrolledSRBatch.apply(y, guide, h, rho, params or UnrollParams())

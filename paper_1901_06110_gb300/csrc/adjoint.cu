@@ -115,21 +115,28 @@ __global__ void __launch_bounds__(256) adj_g_kernel(int n, const float* __restri
     }
 }
 
-// xh = mu (alpha g - A^T A g), vh = mu rho g, uh = zh - mu rho g
+// xh = mu (alpha g - A^T A g), vh = mu rho g, uh = zh - mu rho g and gs += mu g (the
+// observation's cotangent is A gs, A being linear); when a_next is given, also the
+// inputs of the earlier iteration: a_{k-1} = vh - uh and z_{k-1} = x_k + u_{k-1}
 __global__ void adj_update_kernel(int n, const float* __restrict__ g, const float* __restrict__ ata,
                                   const float* __restrict__ zh, float mu, float alpha, float rho,
-                                  float* __restrict__ xh, float* __restrict__ vh, float* __restrict__ uh) {
+                                  float* __restrict__ xh, float* __restrict__ vh, float* __restrict__ uh,
+                                  float* __restrict__ gs, const float* __restrict__ xk,
+                                  const float* __restrict__ uprev, float* __restrict__ a_next,
+                                  float* __restrict__ z_next) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     const float gg = g[q];
+    const float vv = mu * rho * gg;
+    const float uu = zh[q] - vv;
     xh[q] = mu * (alpha * gg - ata[q]);
-    vh[q] = mu * rho * gg;
-    uh[q] = zh[q] - mu * rho * gg;
-}
-
-__global__ void adj_axpy_kernel(int n, float a, const float* __restrict__ x, float* __restrict__ y) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n) y[q] += a * x[q];
+    vh[q] = vv;
+    uh[q] = uu;
+    gs[q] += mu * gg;
+    if (a_next) {
+        a_next[q] = vv - uu;
+        z_next[q] = xk[q] + uprev[q];
+    }
 }
 
 // Stage `nf` fields (each n floats apart) over rows [r0, r0 + RH), cols [c0, c0 + RW), zero outside.
@@ -145,19 +152,26 @@ __device__ __forceinline__ void stage_fields(float* S, const float* __restrict__
         }
 }
 
-// Pair pass A: dh(s) = (1/m) sum_{r ~ s} G_sr d_r K1_sr over both half-window directions,
-// and per-block partials of -(1/m^2) sum over half-window pairs of G d_s d_r K1.
-// Fields staged: a_k, z_k (k < N), d over the tile + rs halo on every side.
-template <typename WT>
+// Pair pass G, over the half-window pairs (s, r = s + o): the pair term
+//   G_sr = sum_k (a_k(s) - a_k(r)) (z_k(r) - z_k(s))
+// stored as planes like K1 (0 where r is off the image), the forward half of
+// dh0(s) = sum_o G_sr d_r K1_sr, and per-block partials of
+// -(1/m^2) sum over half-window pairs of G d_s d_r K1.  G is symmetric in (s, r), so
+// the other half of dh comes from these planes (pair pass T).
+// Fields staged over the tile and its forward halo: a_k, z_k (k < N) and d.  With
+// NR > 0 (N <= NR) the values at s are held in registers; both forms sum in the same
+// order.
+template <typename WT, int NR>
 __global__ void __launch_bounds__(256)
-adj_pairs_a_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const float* __restrict__ AZ,
-                   const float* __restrict__ d, float inv_m, float* __restrict__ dh, double* __restrict__ m_part) {
+adj_pairs_g_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const float* __restrict__ AZ,
+                   const float* __restrict__ d, float inv_m, float* __restrict__ Gp, float* __restrict__ dh0,
+                   double* __restrict__ m_part) {
     extern __shared__ float S[];
     const int y0 = blockIdx.y * kAdjTH, x0 = blockIdx.x * kAdjTW;
-    const int RH = kAdjTH + 2 * rs, RW = kAdjTW + 2 * rs, cells = RH * RW;
+    const int RH = kAdjTH + rs, RW = kAdjTW + 2 * rs, cells = RH * RW;
     const size_t n = (size_t)H * W;
-    stage_fields(S, AZ, 2 * N, n, H, W, y0 - rs, x0 - rs, RH, RW);
-    stage_fields(S + 2 * N * cells, d, 1, n, H, W, y0 - rs, x0 - rs, RH, RW);
+    stage_fields(S, AZ, 2 * N, n, H, W, y0, x0 - rs, RH, RW);
+    stage_fields(S + 2 * N * cells, d, 1, n, H, W, y0, x0 - rs, RH, RW);
     __syncthreads();
     const float* Sa = S;
     const float* Sz = S + N * cells;
@@ -169,27 +183,46 @@ adj_pairs_a_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const 
     for (int py = threadIdx.y; py < kAdjTH; py += 8) {
         const int i = y0 + py;
         if (i >= H || j >= W) continue;
-        const int cs = (py + rs) * RW + threadIdx.x + rs;  // cell of s
+        const int cs = py * RW + threadIdx.x + rs;  // cell of s
+        float as[NR > 0 ? NR : 1], zs[NR > 0 ? NR : 1];
+        if constexpr (NR > 0) {
+#pragma unroll
+            for (int kk = 0; kk < NR; ++kk) {
+                as[kk] = kk < N ? Sa[kk * cells + cs] : 0.f;
+                zs[kk] = kk < N ? Sz[kk * cells + cs] : 0.f;
+            }
+        }
+        const float ds = Sd[cs];
         float accd = 0.f, accm = 0.f;
         for (int oy = 0; oy <= rs; ++oy) {
             const int ox0 = oy == 0 ? 1 : -rs;
             for (int ox = ox0; ox <= rs; ++ox) {
                 const int k = oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
-                const WT* Pk = P + (size_t)k * plane;
-                for (int dir = 0; dir < 2; ++dir) {
-                    const int ri = dir == 0 ? i + oy : i - oy, rj = dir == 0 ? j + ox : j - ox;
-                    if (ri < 0 || ri >= H || rj < 0 || rj >= W) continue;
-                    const float K = to_f32(dir == 0 ? Pk[(size_t)i * Wp + j] : Pk[(size_t)ri * Wp + rj]);
-                    const int cr = cs + (dir == 0 ? oy * RW + ox : -(oy * RW + ox));
-                    float G = 0.f;
-                    for (int kk = 0; kk < N; ++kk)
-                        G = fmaf(Sa[kk * cells + cs] - Sa[kk * cells + cr], Sz[kk * cells + cr] - Sz[kk * cells + cs], G);
-                    accd = fmaf(G * Sd[cr], K, accd);
-                    if (dir == 0) accm = fmaf(G * Sd[cs] * Sd[cr], K, accm);
+                const size_t at = (size_t)k * plane + (size_t)i * Wp + j;
+                const int ri = i + oy, rj = j + ox;
+                if (ri >= H || rj < 0 || rj >= W) {
+                    Gp[at] = 0.f;
+                    continue;
                 }
+                const float K = to_f32(P[at]);
+                const int cr = cs + oy * RW + ox;
+                float G = 0.f;
+                if constexpr (NR > 0) {
+#pragma unroll
+                    for (int kk = 0; kk < NR; ++kk)
+                        if (kk < N) G = fmaf(as[kk] - Sa[kk * cells + cr], Sz[kk * cells + cr] - zs[kk], G);
+                } else {
+                    for (int kk = 0; kk < N; ++kk)
+                        G = fmaf(Sa[kk * cells + cs] - Sa[kk * cells + cr], Sz[kk * cells + cr] - Sz[kk * cells + cs],
+                                 G);
+                }
+                Gp[at] = G;
+                const float dr = Sd[cr];
+                accd = fmaf(G * dr, K, accd);
+                accm = fmaf(G * ds * dr, K, accm);
             }
         }
-        dh[(size_t)i * W + j] = accd * inv_m;
+        dh0[(size_t)i * W + j] = accd;
         mpart -= (double)accm * (double)inv_m * (double)inv_m;
     }
     mpart = warp_sum(mpart);
@@ -202,6 +235,33 @@ adj_pairs_a_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const 
         for (int w = 0; w < 8; ++w) acc += sm[w];
         m_part[blockIdx.y * gridDim.x + blockIdx.x] = acc;
     }
+}
+
+// Pair pass T: dh(s) = (1/m) (dh0(s) + sum_o G_{s-o, s} d_{s-o} K1_{s-o, s}), the
+// backward half-window read from the planes at s - o
+template <typename WT>
+__global__ void __launch_bounds__(256)
+adj_pairs_t_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H, int W, int rs,
+                   const float* __restrict__ d, const float* __restrict__ dh0, float inv_m, float* __restrict__ dh) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= H || j >= W) return;
+    const int Wp = plane_pitch(W);
+    const size_t plane = (size_t)H * Wp;
+    float acc = dh0[(size_t)i * W + j];
+    for (int oy = 0; oy <= rs; ++oy) {
+        const int ri = i - oy;
+        if (ri < 0) break;
+        const int ox0 = oy == 0 ? 1 : -rs;
+        for (int ox = ox0; ox <= rs; ++ox) {
+            const int rj = j - ox;
+            if (rj < 0 || rj >= W) continue;
+            const int k = oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
+            const size_t at = (size_t)k * plane + (size_t)ri * Wp + rj;
+            acc = fmaf(Gp[at] * d[(size_t)ri * W + rj], to_f32(P[at]), acc);
+        }
+    }
+    dh[(size_t)i * W + j] = acc * inv_m;
 }
 
 // fixed-order sum of `count` doubles into *out (one block)
@@ -270,10 +330,11 @@ __global__ void __launch_bounds__(256) adj_sk_finish_kernel(Cover cv, int H, int
 // Pair pass B: the cotangent of every stored weight K1(s, s + o),
 //   Kh = G d_s d_r / m + sum_p (th^p_s d^p_r + th^p_r d^p_s) + [s or r = s*] mh d_s d_r,
 // then Dh = -c K1 Kh (written as planes) and per-block partials of dL/dh = sum Kh K1 D 2c/h.
-// Fields staged over the tile and its forward halo: a_k, z_k (N each), d^p (T + 1), th^p (T).
+// G comes from the planes of pair pass G; fields staged over the tile and its forward
+// halo: d^p (T + 1) and th^p (T).
 template <typename WT>
 __global__ void __launch_bounds__(256)
-adj_pairs_b_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, int T, const float* __restrict__ AZ,
+adj_pairs_b_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H, int W, int rs, int T,
                    const float* __restrict__ Dh, const float* __restrict__ Th, float inv_m, float c, float hfac,
                    const int* __restrict__ s_star, const double* __restrict__ mh_ptr, float* __restrict__ Dhat,
                    double* __restrict__ h_part) {
@@ -281,15 +342,12 @@ adj_pairs_b_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, int T,
     const int y0 = blockIdx.y * kAdjTH, x0 = blockIdx.x * kAdjTW;
     const int RH = kAdjTH + rs, RW = kAdjTW + 2 * rs, cells = RH * RW;
     const size_t n = (size_t)H * W;
-    stage_fields(S, AZ, 2 * N, n, H, W, y0, x0 - rs, RH, RW);
-    stage_fields(S + 2 * N * cells, Dh, T + 1, n, H, W, y0, x0 - rs, RH, RW);
-    stage_fields(S + (2 * N + T + 1) * cells, Th, T, n, H, W, y0, x0 - rs, RH, RW);
+    stage_fields(S, Dh, T + 1, n, H, W, y0, x0 - rs, RH, RW);
+    stage_fields(S + (T + 1) * cells, Th, T, n, H, W, y0, x0 - rs, RH, RW);
     __syncthreads();
-    const float* Sa = S;
-    const float* Sz = S + N * cells;
-    const float* Sdp = S + 2 * N * cells;        // d^0 .. d^T
-    const float* Sth = S + (2 * N + T + 1) * cells;  // th^0 .. th^{T-1}
-    const float* Sd = Sdp + T * cells;           // d = d^T
+    const float* Sdp = S;                  // d^0 .. d^T
+    const float* Sth = S + (T + 1) * cells;  // th^0 .. th^{T-1}
+    const float* Sd = Sdp + T * cells;     // d = d^T
     const int ss = *s_star;
     const float mh = (float)*mh_ptr;
     const int Wp = plane_pitch(W);
@@ -314,10 +372,7 @@ adj_pairs_b_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, int T,
                 }
                 const float K = to_f32(P[at]);
                 const int cr = cs + oy * RW + ox;
-                float G = 0.f;
-                for (int kk = 0; kk < N; ++kk)
-                    G = fmaf(Sa[kk * cells + cs] - Sa[kk * cells + cr], Sz[kk * cells + cr] - Sz[kk * cells + cs], G);
-                float Kh = G * Sd[cs] * Sd[cr] * inv_m;
+                float Kh = Gp[at] * Sd[cs] * Sd[cr] * inv_m;
                 for (int p = 0; p < T; ++p)
                     Kh += Sth[p * cells + cs] * Sdp[p * cells + cr] + Sth[p * cells + cr] * Sdp[p * cells + cs];
                 const int ridx = ri * W + rj;
@@ -343,38 +398,42 @@ adj_pairs_b_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, int T,
     }
 }
 
-// Patch-distance adjoint.  For a tile of positions p of the guide extended by the
-// patch radius (p in [-rp, H + rp) x [-rp, W + rp)) and a chunk of offsets o:
-//   Eh_o(p) = sum_{t in patch} Dh_o(p - t)              (box sum, Dh = 0 off the image)
-//   F = 2 Eh_o(p) (g(p) - g(p + o)),  ge(p) += F,  ge(p + o) -= F,
-// with g the reflected guide; ge lives on the extended grid and is folded back
-// into the image afterwards.  Scatter targets are accumulated in shared memory
-// and added to ge once per CTA.
+// Patch-distance adjoint, in gather form.  With g the reflected guide on the grid
+// extended by the patch radius (p in [-rp, H + rp) x [-rp, W + rp)) and, per offset o,
+//   E_o(q) = sum_{t in patch} Dh_o(q - t)               (box sum, Dh = 0 off the image)
+//   F_o(q) = 2 E_o(q) (g(q) - g(q + o)),
+// the cotangent of g(p) is ge(p) = sum_o F_o(p) - F_o(p - o): the first term from the
+// patch at q = p, the second from the patch whose partner pixel is p.  A CTA owns a
+// 16 x 32 tile of p and a chunk of 16 offsets; each cell is summed by one thread in a
+// fixed offset order and written to the chunk's own plane, so the result does not
+// depend on scheduling.  The fold kernel adds the chunks in order.
 constexpr int kGTH = 16, kGTW = 32, kGChunk = 16;
 
 __global__ void __launch_bounds__(256)
 adj_guide_kernel(const float* __restrict__ Dhat, const float* __restrict__ guide, int H, int W, int rp, int rs,
-                 float* __restrict__ ge) {
+                 float* __restrict__ ge_part) {
     extern __shared__ float S[];
     const int nh = num_half_offsets(rs);
     const int py0 = blockIdx.y * kGTH - rp, px0 = blockIdx.x * kGTW - rp;  // image coords of the tile origin
     const int k0 = blockIdx.z * kGChunk, k1 = min(nh, k0 + kGChunk);
-    // guide over rows [py0, py0 + TH + rs), cols [px0 - rs, px0 + TW + rs) (reflected)
-    const int GH = kGTH + rs, GW = kGTW + 2 * rs;
-    // Dh over rows [py0 - rp, py0 + TH + rp), cols [px0 - rp, px0 + TW + rp)
-    const int DH = kGTH + 2 * rp, DW = kGTW + 2 * rp;
+    // g over rows [py0 - rs, py0 + TH + rs), cols [px0 - rs, px0 + TW + rs)
+    const int GH = kGTH + 2 * rs, GW = kGTW + 2 * rs;
+    // E over rows [py0 - rs, py0 + TH), cols [px0 - rs, px0 + TW + rs): q = p and q = p - o
+    const int EH = kGTH + rs, EW = kGTW + 2 * rs;
+    // Dh over the E region grown by rp on every side
+    const int DH = EH + 2 * rp, DW = EW + 2 * rp;
     float* Gs = S;
     float* Ds = Gs + GH * GW;
-    float* Rs = Ds + DH * DW;  // horizontal box sums [DH][TW]
-    float* Acc = Rs + DH * kGTW;  // scatter accumulator over rows [py0, py0 + TH + rs), cols [px0 - rs, ...)
-    const int tid = threadIdx.y * 32 + threadIdx.x;
+    float* Rs = Ds + DH * DW;  // horizontal box sums [DH][EW]
+    float* Es = Rs + DH * EW;  // [EH][EW]
+    const int tid = threadIdx.x;
     for (int idx = tid; idx < GH * GW; idx += 256) {
         const int a = idx / GW, b = idx - a * GW;
-        Gs[idx] = guide[(size_t)sym_index(py0 + a, H) * W + sym_index(px0 - rs + b, W)];
-        Acc[idx] = 0.f;
+        Gs[idx] = guide[(size_t)sym_index(py0 - rs + a, H) * W + sym_index(px0 - rs + b, W)];
     }
     const int Wp = plane_pitch(W);
     const size_t plane = (size_t)H * Wp;
+    float acc[2] = {0.f, 0.f};  // tile cells tid and tid + 256
     for (int k = k0; k < k1; ++k) {
         int oy, ox;
         half_offset(k, rs, oy, ox);
@@ -382,42 +441,48 @@ adj_guide_kernel(const float* __restrict__ Dhat, const float* __restrict__ guide
         __syncthreads();
         for (int idx = tid; idx < DH * DW; idx += 256) {
             const int a = idx / DW, b = idx - a * DW;
-            const int i = py0 - rp + a, j = px0 - rp + b;
+            const int i = py0 - rs - rp + a, j = px0 - rs - rp + b;
             Ds[idx] = (i >= 0 && i < H && j >= 0 && j < W) ? Dk[(size_t)i * Wp + j] : 0.f;
         }
         __syncthreads();
-        for (int idx = tid; idx < DH * kGTW; idx += 256) {
-            const int a = idx / kGTW, b = idx - a * kGTW;
-            float acc = 0.f;
-            for (int t = 0; t <= 2 * rp; ++t) acc += Ds[a * DW + b + t];
-            Rs[idx] = acc;
+        for (int idx = tid; idx < DH * EW; idx += 256) {
+            const int a = idx / EW, b = idx - a * EW;
+            float s = 0.f;
+            for (int t = 0; t <= 2 * rp; ++t) s += Ds[a * DW + b + t];
+            Rs[idx] = s;
         }
         __syncthreads();
-        const int b = threadIdx.x;
-        for (int a = threadIdx.y; a < kGTH; a += 8) {
-            const int pi = py0 + a, pj = px0 + b;
-            if (pi >= H + rp || pj >= W + rp) continue;
-            float E = 0.f;
-            for (int t = 0; t <= 2 * rp; ++t) E += Rs[(a + t) * kGTW + b];
-            const float gp = Gs[a * GW + b + rs];
-            const float go = Gs[(a + oy) * GW + b + rs + ox];
-            const float F = 2.f * E * (gp - go);
-            atomicAdd(&Acc[a * GW + b + rs], F);
-            atomicAdd(&Acc[(a + oy) * GW + b + rs + ox], -F);
+        for (int idx = tid; idx < EH * EW; idx += 256) {
+            const int a = idx / EW, b = idx - a * EW;
+            float s = 0.f;
+            for (int t = 0; t <= 2 * rp; ++t) s += Rs[(a + t) * EW + b];
+            Es[idx] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int cell = tid + 256 * c;
+            const int ea = cell / kGTW + rs, eb = cell % kGTW + rs;  // p in the E and g regions
+            const float gp = Gs[ea * GW + eb];
+            const float fp = 2.f * Es[ea * EW + eb] * (gp - Gs[(ea + oy) * GW + eb + ox]);
+            const float fq = 2.f * Es[(ea - oy) * EW + eb - ox] * (Gs[(ea - oy) * GW + eb - ox] - gp);
+            acc[c] += fp - fq;
         }
     }
-    __syncthreads();
-    const int EW = W + 2 * rp, EH = H + 2 * rp;
-    for (int idx = tid; idx < GH * GW; idx += 256) {
-        const int a = idx / GW, b2 = idx - a * GW;
-        const int ei = py0 + a + rp, ej = px0 - rs + b2 + rp;  // extended-grid coordinates
-        const float v = Acc[idx];
-        if (v != 0.f && ei >= 0 && ei < EH && ej >= 0 && ej < EW) atomicAdd(&ge[(size_t)ei * EW + ej], v);
+    const int XW = W + 2 * rp;
+    const size_t ep = (size_t)(H + 2 * rp) * XW;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int cell = tid + 256 * c;
+        const int pi = py0 + cell / kGTW, pj = px0 + cell % kGTW;
+        if (pi < H + rp && pj < W + rp)
+            ge_part[blockIdx.z * ep + (size_t)(pi + rp) * XW + (pj + rp)] = acc[c];
     }
 }
 
-// gb(q) = (xh0 + vh0)(q) [0 < g(q) < 1] + sum of ge(p) over extended p reflecting onto q
-__global__ void adj_fold_kernel(const float* __restrict__ ge, const float* __restrict__ xh0,
+// gb(q) = (xh0 + vh0)(q) [0 < g(q) < 1] + sum of ge(p) over the extended p that reflect
+// onto q (p = 2 n m + q or 2 n m - 1 - q per axis), the chunks added in order
+__global__ void adj_fold_kernel(const float* __restrict__ ge_part, int nz, const float* __restrict__ xh0,
                                 const float* __restrict__ vh0, const float* __restrict__ guide, int H, int W, int rp,
                                 float* __restrict__ gb) {
     const int j = blockIdx.x * 32 + threadIdx.x;
@@ -426,14 +491,21 @@ __global__ void adj_fold_kernel(const float* __restrict__ ge, const float* __res
     const size_t q = (size_t)i * W + j;
     const float g = guide[q];
     float acc = (g > 0.f && g < 1.f) ? xh0[q] + vh0[q] : 0.f;
-    const int EW = W + 2 * rp;
-    for (int pi = -rp; pi < H + rp; ++pi) {
-        if (sym_index(pi, H) != i) continue;
-        for (int pj = -rp; pj < W + rp; ++pj) {
-            if (sym_index(pj, W) != j) continue;
-            acc += ge[(size_t)(pi + rp) * EW + (pj + rp)];
+    const int XW = W + 2 * rp;
+    const size_t ep = (size_t)(H + 2 * rp) * XW;
+    const int my = rp / (2 * H) + 1, mx = rp / (2 * W) + 1;
+    for (int m = -my; m <= my; ++m)
+        for (int cy = 0; cy < 2; ++cy) {
+            const int pi = cy == 0 ? 2 * H * m - 1 - i : 2 * H * m + i;
+            if (pi < -rp || pi >= H + rp) continue;
+            for (int n = -mx; n <= mx; ++n)
+                for (int cx = 0; cx < 2; ++cx) {
+                    const int pj = cx == 0 ? 2 * W * n - 1 - j : 2 * W * n + j;
+                    if (pj < -rp || pj >= W + rp) continue;
+                    const float* e = ge_part + (size_t)(pi + rp) * XW + (pj + rp);
+                    for (int z = 0; z < nz; ++z) acc += e[z * ep];
+                }
         }
-    }
     gb[q] = acc;
 }
 
@@ -452,9 +524,19 @@ struct lpnp_tape {
     BlurTaps taps{};
     const float* y = nullptr;      // caller's observation (kept valid until the backward)
     const float* guide = nullptr;  // caller's guide
-    DevBuf Dh, Th, X, V, U, AZ, xh, vh, uh, zh, g, wa, grad, ata, rlo, ag, yb, dh[2], base, thp, Dhat, ge, gb,
-        ctl, part, m, sstar, mh, rho_part, h_part, m_part, scratch;
+    int blur_r = 0;
+    float blur_sigma = 1.f;
+    DevBuf Dh, Th, X, V, U, AZ, xh, vh, uh, zh, g, wa, grad, ata, gs, dh[2], base, thp, Dhat, Gp, ge, gb, ctl,
+        part, m, sstar, mh, rho_part, h_part, m_part, scratch;
     float inv_m = 1.f;
+    // pinned host words read back after the stream work: m, the scalar cotangents and
+    // the handle's wait-error flag
+    struct Host {
+        double hs[3];
+        unsigned err;
+        float m;
+    };
+    Host* host = nullptr;
 };
 
 namespace {
@@ -471,16 +553,33 @@ dsgnlm_status tape_ck(cudaError_t e) {
         if (s_ != DSGNLM_OK) return s_;                 \
     } while (0)
 
+size_t pairs_g_smem(int N, int rs) {
+    return sizeof(float) * (size_t)(2 * N + 1) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
+}
+size_t pairs_b_smem(int T, int rs) {
+    return sizeof(float) * (size_t)(2 * T + 1) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
+}
+
+// pair passes G and T: the planes of G and dh = (1/m) sum_{r ~ s} G_sr d_r K1_sr into dh[0]
+// (dh[1] holds the forward half in between)
 template <typename WT>
-cudaError_t pairs_a(const lpnp_tape* tp, const void* planes, cudaStream_t st, double* m_part) {
-    const int H = tp->H, W = tp->W, rs = tp->rs;
-    const size_t smem = sizeof(float) * (size_t)(2 * tp->N + 1) * (kAdjTH + 2 * rs) * (kAdjTW + 2 * rs);
-    cudaError_t e = cudaFuncSetAttribute(adj_pairs_a_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+cudaError_t pairs_gt(const lpnp_tape* tp, const void* planes, cudaStream_t st, double* m_part) {
+    const int H = tp->H, W = tp->W, rs = tp->rs, N = tp->N;
+    const size_t smem = pairs_g_smem(N, rs);
+    const float* d = tp->Dh.as<float>() + (size_t)tp->T * H * W;
     dim3 grid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
-    adj_pairs_a_kernel<WT><<<grid, dim3(32, 8), smem, st>>>((const WT*)planes, H, W, rs, tp->N, tp->AZ.as<float>(),
-                                                            tp->Dh.as<float>() + (size_t)tp->T * H * W, tp->inv_m,
-                                                            tp->dh[0].as<float>(), m_part);
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, dim3(32, 8), smem, st>>>((const WT*)planes, H, W, rs, N, tp->AZ.as<float>(), d, tp->inv_m,
+                                              tp->Gp.as<float>(), tp->dh[1].as<float>(), m_part);
+        return cudaGetLastError();
+    };
+    cudaError_t e = N <= 16 ? run(adj_pairs_g_kernel<WT, 16>) : run(adj_pairs_g_kernel<WT, 0>);
+    count_launches(1);
+    if (e != cudaSuccess) return e;
+    adj_pairs_t_kernel<WT><<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, st>>>(
+        (const WT*)planes, tp->Gp.as<float>(), H, W, rs, d, tp->dh[1].as<float>(), tp->inv_m, tp->dh[0].as<float>());
     count_launches(1);
     return cudaGetLastError();
 }
@@ -488,14 +587,13 @@ cudaError_t pairs_a(const lpnp_tape* tp, const void* planes, cudaStream_t st, do
 template <typename WT>
 cudaError_t pairs_b(const lpnp_tape* tp, const void* planes, cudaStream_t st) {
     const int H = tp->H, W = tp->W, rs = tp->rs;
-    const size_t smem =
-        sizeof(float) * (size_t)(2 * tp->N + 2 * tp->T + 1) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
+    const size_t smem = pairs_b_smem(tp->T, rs);
     cudaError_t e = cudaFuncSetAttribute(adj_pairs_b_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
     adj_pairs_b_kernel<WT><<<grid, dim3(32, 8), smem, st>>>(
-        (const WT*)planes, H, W, rs, tp->N, tp->T, tp->AZ.as<float>(), tp->Dh.as<float>(), tp->thp.as<float>(),
-        tp->inv_m, tp->c, 2.f * tp->c / tp->h, tp->sstar.as<int>(), tp->mh.as<double>(), tp->Dhat.as<float>(),
+        (const WT*)planes, tp->Gp.as<float>(), H, W, rs, tp->T, tp->Dh.as<float>(), tp->thp.as<float>(), tp->inv_m,
+        tp->c, 2.f * tp->c / tp->h, tp->sstar.as<int>(), tp->mh.as<double>(), tp->Dhat.as<float>(),
         tp->h_part.as<double>());
     count_launches(1);
     return cudaGetLastError();
@@ -525,28 +623,33 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (!t) return;
     if (t->den) cudaStreamSynchronize(t->den->stream);
     DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
-                      &t->wa, &t->grad, &t->ata, &t->rlo, &t->ag, &t->yb, &t->dh[0], &t->dh[1], &t->base,
-                      &t->thp, &t->Dhat, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->sstar, &t->mh,
-                      &t->rho_part, &t->h_part, &t->m_part, &t->scratch};
+                      &t->wa, &t->grad, &t->ata, &t->gs, &t->dh[0], &t->dh[1], &t->base, &t->thp, &t->Dhat,
+                      &t->Gp, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->sstar, &t->mh, &t->rho_part, &t->h_part,
+                      &t->m_part, &t->scratch};
     for (DevBuf* b : bufs) b->release();
+    if (t->host) cudaFreeHost(t->host);
     delete t;
 }
 
-dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y, const float* guide, int H, int W,
-                                    int patch_r, int search_r, float bandwidth, int balance_passes, float alpha,
-                                    float rho, int iters, float blur_sigma, int blur_r, float* x_out) {
-    if (!tp || !den || !y || !guide || !x_out) return DSGNLM_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// First half of the recording: K1 into the handle, the T balancing passes with every
+// d^p and t^p kept, m = max_s d_s t_s with its first maximiser, and the read-back of m
+// queued on the handle's stream.  Nothing here waits for the device.
+dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const float* guide, int H, int W,
+                            int patch_r, int search_r, float bandwidth, int balance_passes, float alpha, float rho,
+                            int iters, float blur_sigma, int blur_r) {
+    if (!tp || !den || !y || !guide) return DSGNLM_EINVAL;
     if (H < 2 || W < 2 || (H & 1) || (W & 1) || iters < 1 || iters > 256 || balance_passes < 0 ||
         balance_passes > 64 || !(rho > 0.f) || !(alpha >= 0.f) || blur_r < 0 || blur_r > 8 || !(blur_sigma > 0.f))
         return DSGNLM_EINVAL;
     if (!tma_path_supports(search_r)) return DSGNLM_EINVAL;
-    {
-        // shared memory of the pair passes of the backward (fields over a tile + halo)
-        const size_t a_bytes = sizeof(float) * (size_t)(2 * iters + 1) * (kAdjTH + 2 * search_r) * (kAdjTW + 2 * search_r);
-        const size_t b_bytes =
-            sizeof(float) * (size_t)(2 * iters + 2 * balance_passes + 1) * (kAdjTH + search_r) * (kAdjTW + 2 * search_r);
-        if (a_bytes > 220 * 1024 || b_bytes > 220 * 1024) return DSGNLM_EINVAL;
-    }
+    // shared memory of the pair passes of the backward (fields over a tile + halo)
+    if (pairs_g_smem(iters, search_r) > 220 * 1024 || pairs_b_smem(balance_passes, search_r) > 220 * 1024)
+        return DSGNLM_EINVAL;
+    if (!tp->host) TAPE_CK(cudaMallocHost((void**)&tp->host, sizeof(lpnp_tape::Host)));
     dsgnlm_status s = dsgnlm_build(den, guide, H, W, patch_r, search_r, bandwidth);
     if (s != DSGNLM_OK) return s;
     if (!den->fast) return DSGNLM_EINVAL;
@@ -567,6 +670,8 @@ dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y
     const double np = 2.0 * patch_r + 1.0;
     tp->c = (float)(1.0 / (2.0 * np * np * (double)bandwidth * (double)bandwidth));
     tp->taps = make_blur_taps(blur_sigma, blur_r);
+    tp->blur_sigma = blur_sigma;
+    tp->blur_r = blur_r;
     tp->y = y;
     tp->guide = guide;
     TAPE_CK(tp->Dh.ensure(sizeof(float) * n * (T + 1)));
@@ -596,28 +701,37 @@ dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y
     adj_m_argmax_kernel<<<1, 1024, 0, st>>>(dT, tT, (int)n, tp->m.as<float>(), tp->sstar.as<int>());
     count_launches(1);
     TAPE_CK(cudaGetLastError());
-    float mval = 1.f;
-    TAPE_CK(cudaMemcpyAsync(&mval, tp->m.p, sizeof(float), cudaMemcpyDeviceToHost, st));
+    TAPE_CK(cudaMemcpyAsync(&tp->host->m, tp->m.p, sizeof(float), cudaMemcpyDeviceToHost, st));
+    return DSGNLM_OK;
+}
+
+// Second half: waits for m, fixes W on the handle and runs Algorithm 1 one iteration
+// at a time, every state recorded.
+dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
+    dsgnlm* den = tp->den;
+    cudaStream_t st = den->stream;
+    const size_t n = (size_t)tp->H * tp->W;
+    const int T = tp->T, N = tp->N;
     TAPE_CK(cudaStreamSynchronize(st));
+    const float mval = tp->host->m;
     tp->inv_m = (float)(1.0 / (double)mval);
     // the handle now holds this W
-    den->d_final = const_cast<float*>(dT);
-    den->t_final = const_cast<float*>(tT);
+    den->d_final = tp->Dh.as<float>() + (size_t)T * n;
+    den->t_final = tp->Th.as<float>() + (size_t)T * n;
     den->m = mval;
     den->inv_m = tp->inv_m;
     den->iters = T;
     den->balanced = true;
-    // Algorithm 1, one iteration at a time, every state recorded
-    TAPE_CK(launch_init(guide, (int)n, tp->X.as<float>(), tp->V.as<float>(), tp->U.as<float>(), st));
+    TAPE_CK(launch_init(tp->guide, (int)n, tp->X.as<float>(), tp->V.as<float>(), tp->U.as<float>(), st));
     lpnp_problem pr{};
     pr.kind = LPNP_SR2;
-    pr.H = H;
-    pr.W = W;
-    pr.y = y;
-    pr.blur_sigma = blur_sigma;
-    pr.blur_r = blur_r;
+    pr.H = tp->H;
+    pr.W = tp->W;
+    pr.y = tp->y;
+    pr.blur_sigma = tp->blur_sigma;
+    pr.blur_r = tp->blur_r;
     pr.constraint = tp->constraint;
-    pr.alpha = alpha;
+    pr.alpha = tp->alpha;
     pr.den = den;
     for (int k = 0; k < N; ++k) {
         float* x1 = tp->X.as<float>() + (size_t)(k + 1) * n;
@@ -629,34 +743,34 @@ dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y
         pr.x = x1;
         pr.v = v1;
         pr.u = u1;
-        s = lpnp_solve(&pr, rho, 1);
+        dsgnlm_status s = lpnp_solve(&pr, tp->rho, 1);
         if (s != DSGNLM_OK) return s;
     }
     TAPE_CK(cudaMemcpyAsync(x_out, tp->X.as<float>() + (size_t)N * n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     return DSGNLM_OK;
 }
 
-dsgnlm_status lpnp_backward(lpnp_tape_t tp, const float* x_bar, float* y_bar, float* guide_bar, double* h_bar,
-                            double* rho_bar) {
-    if (!tp || !tp->den || !x_bar || !y_bar || !guide_bar) return DSGNLM_EINVAL;
+// The reverse sweep, queued on the handle's stream up to the read-back of the scalar
+// cotangents and of the wait-error flag into the tape's pinned words.
+dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, float* guide_bar) {
+    if (!tp || !tp->den || !tp->host || !x_bar || !y_bar || !guide_bar) return DSGNLM_EINVAL;
     dsgnlm* den = tp->den;
     cudaStream_t st = den->stream;
     const int H = tp->H, W = tp->W, N = tp->N, T = tp->T, rs = tp->rs, rp = tp->rp;
-    const size_t n = (size_t)H * W, nlo = n / 4;
+    const size_t n = (size_t)H * W;
     const int nh = num_half_offsets(rs);
     // the handle's planes must still hold this tape's K1
     if (den->H != H || den->W != W || den->rs != rs || den->nh != nh) return DSGNLM_EINVAL;
     DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->wa, &tp->grad, &tp->ata,
-                       &tp->dh[0], &tp->dh[1], &tp->base, &tp->gb};
+                       &tp->gs, &tp->dh[0], &tp->dh[1], &tp->base, &tp->gb};
     for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
     TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
     TAPE_CK(tp->thp.ensure(sizeof(float) * n * (T > 0 ? T : 1)));
-    TAPE_CK(tp->rlo.ensure(sizeof(float) * nlo));
-    TAPE_CK(tp->ag.ensure(sizeof(float) * nlo));
-    TAPE_CK(tp->yb.ensure(sizeof(float) * nlo));
     TAPE_CK(tp->Dhat.ensure(sizeof(float) * (size_t)nh * H * plane_pitch(W)));
+    TAPE_CK(tp->Gp.ensure(sizeof(float) * (size_t)nh * H * plane_pitch(W)));
     const size_t ne = (size_t)(H + 2 * rp) * (W + 2 * rp);
-    TAPE_CK(tp->ge.ensure(sizeof(float) * ne));
+    const int nz = (nh + kGChunk - 1) / kGChunk;
+    TAPE_CK(tp->ge.ensure(sizeof(float) * ne * nz));
     const int nb = nblk(n);
     const dim3 pgrid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
     const int npb = (int)(pgrid.x * pgrid.y);
@@ -665,7 +779,7 @@ dsgnlm_status lpnp_backward(lpnp_tape_t tp, const float* x_bar, float* y_bar, fl
     TAPE_CK(tp->m_part.ensure(sizeof(double) * npb));
     TAPE_CK(tp->mh.ensure(sizeof(double) * 3));
     TAPE_CK(cudaMemsetAsync(tp->rho_part.p, 0, sizeof(double) * nb, st));
-    TAPE_CK(cudaMemsetAsync(tp->yb.p, 0, sizeof(float) * nlo, st));
+    TAPE_CK(cudaMemsetAsync(tp->gs.p, 0, sizeof(float) * n, st));
     TAPE_CK(cudaMemsetAsync(tp->vh.p, 0, sizeof(float) * n, st));
     TAPE_CK(cudaMemsetAsync(tp->uh.p, 0, sizeof(float) * n, st));
     TAPE_CK(cudaMemcpyAsync(tp->xh.p, x_bar, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
@@ -674,42 +788,45 @@ dsgnlm_status lpnp_backward(lpnp_tape_t tp, const float* x_bar, float* y_bar, fl
     const float* tT = tp->Th.as<float>() + (size_t)T * n;
     float* A = tp->AZ.as<float>();
     float* Z = A + (size_t)N * n;
+    // a_{N-1} = vh - uh = 0 and z_{N-1} = x_N + u_{N-1}; every earlier pair is written by
+    // the update of the iteration after it
+    adj_az_kernel<<<nb, 256, 0, st>>>((int)n, tp->vh.as<float>(), tp->uh.as<float>(),
+                                      tp->X.as<float>() + (size_t)N * n, tp->U.as<float>() + (size_t)(N - 1) * n,
+                                      A + (size_t)(N - 1) * n, Z + (size_t)(N - 1) * n);
+    count_launches(1);
+    TAPE_CK(cudaGetLastError());
     for (int k = N - 1; k >= 0; --k) {
         const float* xk = tp->X.as<float>() + (size_t)k * n;
         const float* vk = tp->V.as<float>() + (size_t)k * n;
         const float* uk = tp->U.as<float>() + (size_t)k * n;
-        const float* x1 = xk + n;
         float* ak = A + (size_t)k * n;
-        adj_az_kernel<<<nb, 256, 0, st>>>((int)n, tp->vh.as<float>(), tp->uh.as<float>(), x1, uk, ak, Z + (size_t)k * n);
-        count_launches(1);
-        TAPE_CK(cudaGetLastError());
         // W a (W symmetric)
         TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, dT, ak, den->err.as<unsigned>(), nullptr, st));
         TAPE_CK(launch_tma_apply_finish(den->plan, H, W, rs, dT, tT, tp->inv_m, ak, tp->wa.as<float>(), st));
         // grad f(x_k) for xbar_k
-        TAPE_CK(launch_sr_forward(xk, H, W, tp->taps, tp->y, -1.0f, tp->rlo.as<float>(), st));
-        TAPE_CK(launch_sr_adjoint(tp->rlo.as<float>(), H, W, tp->taps, tp->grad.as<float>(), st));
+        TAPE_CK(launch_sr_grad(xk, tp->y, H, W, tp->taps, tp->grad.as<float>(), st));
         adj_g_kernel<<<nb, 256, 0, st>>>((int)n, tp->wa.as<float>(), tp->uh.as<float>(), tp->xh.as<float>(), xk, vk, uk,
                                          tp->grad.as<float>(), mu, alpha, rho, tp->constraint, tp->g.as<float>(),
                                          tp->zh.as<float>(), tp->rho_part.as<double>());
         count_launches(1);
         TAPE_CK(cudaGetLastError());
-        // A g and A^T A g
-        TAPE_CK(launch_sr_forward(tp->g.as<float>(), H, W, tp->taps, nullptr, 0.f, tp->ag.as<float>(), st));
-        TAPE_CK(launch_sr_adjoint(tp->ag.as<float>(), H, W, tp->taps, tp->ata.as<float>(), st));
+        // A^T A g
+        TAPE_CK(launch_sr_grad(tp->g.as<float>(), nullptr, H, W, tp->taps, tp->ata.as<float>(), st));
+        const bool more = k > 0;
         adj_update_kernel<<<nb, 256, 0, st>>>((int)n, tp->g.as<float>(), tp->ata.as<float>(), tp->zh.as<float>(), mu,
-                                              alpha, rho, tp->xh.as<float>(), tp->vh.as<float>(), tp->uh.as<float>());
-        adj_axpy_kernel<<<nblk(nlo), 256, 0, st>>>((int)nlo, mu, tp->ag.as<float>(), tp->yb.as<float>());
-        count_launches(2);
+                                              alpha, rho, tp->xh.as<float>(), tp->vh.as<float>(), tp->uh.as<float>(),
+                                              tp->gs.as<float>(), xk, more ? uk - n : nullptr,
+                                              more ? ak - n : nullptr, more ? Z + (size_t)(k - 1) * n : nullptr);
+        count_launches(1);
         TAPE_CK(cudaGetLastError());
     }
-    // pair pass A: dh from G, partials of mh
+    // pair passes G and T: the G planes, dh, partials of mh
     double* m_part = tp->m_part.as<double>();
     double* mh = tp->mh.as<double>();
     switch (den->dtype) {
-        case DSGNLM_F32: TAPE_CK(pairs_a<float>(tp, den->planes.p, st, m_part)); break;
-        case DSGNLM_F16: TAPE_CK(pairs_a<__half>(tp, den->planes.p, st, m_part)); break;
-        default: TAPE_CK(pairs_a<__nv_bfloat16>(tp, den->planes.p, st, m_part)); break;
+        case DSGNLM_F32: TAPE_CK(pairs_gt<float>(tp, den->planes.p, st, m_part)); break;
+        case DSGNLM_F16: TAPE_CK(pairs_gt<__half>(tp, den->planes.p, st, m_part)); break;
+        default: TAPE_CK(pairs_gt<__nv_bfloat16>(tp, den->planes.p, st, m_part)); break;
     }
     adj_sum_kernel<<<1, 256, 0, st>>>(m_part, npb, mh);
     count_launches(1);
@@ -743,36 +860,100 @@ dsgnlm_status lpnp_backward(lpnp_tape_t tp, const float* x_bar, float* y_bar, fl
         case DSGNLM_F16: TAPE_CK(pairs_b<__half>(tp, den->planes.p, st)); break;
         default: TAPE_CK(pairs_b<__nv_bfloat16>(tp, den->planes.p, st)); break;
     }
-    // patch distances back to the guide
-    TAPE_CK(cudaMemsetAsync(tp->ge.p, 0, sizeof(float) * ne, st));
+    // patch distances back to the guide: one plane of the extended grid per offset chunk
     {
-        const int GH = kGTH + rs, GW = kGTW + 2 * rs, DH = kGTH + 2 * rp, DW = kGTW + 2 * rp;
-        const size_t smem = sizeof(float) * (size_t)(2 * GH * GW + DH * DW + DH * kGTW);
+        const int GH = kGTH + 2 * rs, GW = kGTW + 2 * rs, EH = kGTH + rs, EW = kGTW + 2 * rs;
+        const int DH = EH + 2 * rp, DW = EW + 2 * rp;
+        const size_t smem = sizeof(float) * (size_t)(GH * GW + DH * DW + DH * EW + EH * EW);
         TAPE_CK(cudaFuncSetAttribute(adj_guide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        dim3 grid((W + 2 * rp + kGTW - 1) / kGTW, (H + 2 * rp + kGTH - 1) / kGTH, (nh + kGChunk - 1) / kGChunk);
-        adj_guide_kernel<<<grid, dim3(32, 8), smem, st>>>(tp->Dhat.as<float>(), tp->guide, H, W, rp, rs,
-                                                          tp->ge.as<float>());
+        dim3 grid((W + 2 * rp + kGTW - 1) / kGTW, (H + 2 * rp + kGTH - 1) / kGTH, nz);
+        adj_guide_kernel<<<grid, 256, smem, st>>>(tp->Dhat.as<float>(), tp->guide, H, W, rp, rs, tp->ge.as<float>());
         count_launches(1);
         TAPE_CK(cudaGetLastError());
     }
     adj_fold_kernel<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, st>>>(
-        tp->ge.as<float>(), tp->xh.as<float>(), tp->vh.as<float>(), tp->guide, H, W, rp, guide_bar);
+        tp->ge.as<float>(), nz, tp->xh.as<float>(), tp->vh.as<float>(), tp->guide, H, W, rp, guide_bar);
     count_launches(1);
     TAPE_CK(cudaGetLastError());
-    TAPE_CK(cudaMemcpyAsync(y_bar, tp->yb.p, sizeof(float) * nlo, cudaMemcpyDeviceToDevice, st));
+    // dL/dy = sum_k mu A g_k = A gs
+    TAPE_CK(launch_sr_forward(tp->gs.as<float>(), H, W, tp->taps, nullptr, 0.f, y_bar, st));
     adj_sum_kernel<<<1, 256, 0, st>>>(tp->rho_part.as<double>(), nb, mh + 1);
     adj_sum_kernel<<<1, 256, 0, st>>>(tp->h_part.as<double>(), npb, mh + 2);
     count_launches(2);
     TAPE_CK(cudaGetLastError());
-    double hs[3] = {0, 0, 0};
-    TAPE_CK(cudaMemcpyAsync(hs, mh, sizeof hs, cudaMemcpyDeviceToHost, st));
-    TAPE_CK(cudaStreamSynchronize(st));
-    unsigned errv = 0;
-    TAPE_CK(cudaMemcpy(&errv, den->err.p, sizeof errv, cudaMemcpyDeviceToHost));
-    if (errv) return DSGNLM_TIMEOUT;
-    if (rho_bar) *rho_bar = hs[1];
-    if (h_bar) *h_bar = hs[2];
+    TAPE_CK(cudaMemcpyAsync(tp->host->hs, mh, sizeof tp->host->hs, cudaMemcpyDeviceToHost, st));
+    TAPE_CK(cudaMemcpyAsync(&tp->host->err, den->err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     return DSGNLM_OK;
+}
+
+dsgnlm_status backward_finish(lpnp_tape* tp, double* h_bar, double* rho_bar) {
+    TAPE_CK(cudaStreamSynchronize(tp->den->stream));
+    if (tp->host->err) return DSGNLM_TIMEOUT;
+    if (rho_bar) *rho_bar = tp->host->hs[1];
+    if (h_bar) *h_bar = tp->host->hs[2];
+    return DSGNLM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y, const float* guide, int H, int W,
+                                    int patch_r, int search_r, float bandwidth, int balance_passes, float alpha,
+                                    float rho, int iters, float blur_sigma, int blur_r, float* x_out) {
+    if (!x_out) return DSGNLM_EINVAL;
+    dsgnlm_status s = forward_begin(tp, den, y, guide, H, W, patch_r, search_r, bandwidth, balance_passes, alpha, rho,
+                                    iters, blur_sigma, blur_r);
+    return s == DSGNLM_OK ? forward_finish(tp, x_out) : s;
+}
+
+dsgnlm_status lpnp_unrolled_forward_batched(lpnp_tape_t* tapes, dsgnlm_t* dens, int count, const float* const* y,
+                                            const float* const* guide, int H, int W, int patch_r, int search_r,
+                                            float bandwidth, int balance_passes, float alpha, float rho, int iters,
+                                            float blur_sigma, int blur_r, float* const* x_out) {
+    if (!tapes || !dens || !y || !guide || !x_out || count < 1) return DSGNLM_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!tapes[i] || !dens[i] || !x_out[i]) return DSGNLM_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (tapes[j] == tapes[i] || dens[j] == dens[i]) return DSGNLM_EINVAL;
+    }
+    // every image's weights and balance are queued before the first wait for m
+    for (int i = 0; i < count; ++i) {
+        dsgnlm_status s = forward_begin(tapes[i], dens[i], y[i], guide[i], H, W, patch_r, search_r, bandwidth,
+                                        balance_passes, alpha, rho, iters, blur_sigma, blur_r);
+        if (s != DSGNLM_OK) return s;
+    }
+    for (int i = 0; i < count; ++i) {
+        dsgnlm_status s = forward_finish(tapes[i], x_out[i]);
+        if (s != DSGNLM_OK) return s;
+    }
+    return DSGNLM_OK;
+}
+
+dsgnlm_status lpnp_backward(lpnp_tape_t tp, const float* x_bar, float* y_bar, float* guide_bar, double* h_bar,
+                            double* rho_bar) {
+    dsgnlm_status s = backward_begin(tp, x_bar, y_bar, guide_bar);
+    return s == DSGNLM_OK ? backward_finish(tp, h_bar, rho_bar) : s;
+}
+
+dsgnlm_status lpnp_backward_batched(lpnp_tape_t* tapes, int count, const float* const* x_bar, float* const* y_bar,
+                                    float* const* guide_bar, double* h_bar, double* rho_bar) {
+    if (!tapes || !x_bar || !y_bar || !guide_bar || count < 1) return DSGNLM_EINVAL;
+    for (int i = 0; i < count; ++i) {
+        if (!tapes[i]) return DSGNLM_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (tapes[j] == tapes[i]) return DSGNLM_EINVAL;
+    }
+    for (int i = 0; i < count; ++i) {
+        dsgnlm_status s = backward_begin(tapes[i], x_bar[i], y_bar[i], guide_bar[i]);
+        if (s != DSGNLM_OK) return s;
+    }
+    dsgnlm_status first = DSGNLM_OK;
+    for (int i = 0; i < count; ++i) {
+        dsgnlm_status s = backward_finish(tapes[i], h_bar ? h_bar + i : nullptr, rho_bar ? rho_bar + i : nullptr);
+        if (first == DSGNLM_OK) first = s;
+    }
+    return first;
 }
 
 }  // extern "C"

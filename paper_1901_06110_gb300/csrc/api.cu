@@ -784,10 +784,11 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             return e;
         };
         bool ran = false;
-        if (!ad && !h->prof) {
+        if (!ad && !h->prof && iters > 1) {
             // The sequence is recorded once as a CUDA graph and replayed while everything
             // its kernel parameters bake in is unchanged: one launch per solve instead of
-            // one per kernel, so the host's launch rate does not gap the GPU.
+            // one per kernel, so the host's launch rate does not gap the GPU.  A single
+            // iteration (a few kernels, often on fresh buffers) is launched directly.
             std::vector<unsigned char> key;
             const int ints[12] = {H, W, iters, kind, (int)sym, h->dtype, h->rs, nblocks, p->constraint, p->K,
                                   h->plan.tiles_x, h->plan.tiles_y};

@@ -92,10 +92,10 @@ __device__ __forceinline__ void sr_grad_tile(GradSmem<R>& sm, const float* __res
         Hs[a][c] = acc;
     }
     __syncthreads();
-    // column blur at the even rows minus the observation: r = A x - y
+    // column blur at the even rows minus the observation: r = A x - y (y null: r = A x)
     for (int i = tid; i < L * L; i += 256) {
         const int l = i / L, c = i - l * L;
-        const float yv = __ldg(y + (size_t)lrows[l] * w + lcols[c]);
+        const float yv = y ? __ldg(y + (size_t)lrows[l] * w + lcols[c]) : 0.f;
         float acc = 0.f;
 #pragma unroll
         for (int a = -R; a <= R; ++a) acc = fmaf(taps.t[a + R], Hs[2 * l + G - a][c], acc);

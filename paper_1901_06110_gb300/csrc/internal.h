@@ -154,7 +154,7 @@ cudaError_t launch_cg_step(float* x, float* r, const float* p, const float* q, c
 cudaError_t launch_cg_dir(const float* r, float* p, const CgScalars* s, int n, cudaStream_t st);
 cudaError_t launch_cg_reduce(const double* part, int nb, CgScalars* s, int mode, cudaStream_t st);
 cudaError_t launch_project_z(float* x, const float* u, float* z, int n, int constraint, cudaStream_t st);
-// g = A^T (A x - y) in one launch (H, W even, taps.r <= 8)
+// g = A^T (A x - y) in one launch (H, W even, taps.r <= 8); y null: g = A^T A x
 cudaError_t launch_sr_grad(const float* x, const float* y, int H, int W, BlurTaps taps, float* g,
                            cudaStream_t st);
 // x <- Pi_C(mu (alpha x + rho (v - u) - g)), z = x + u, per pixel (x in place)

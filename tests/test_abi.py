@@ -72,6 +72,21 @@ def test_host_side_argument_checks(lib):
         p = _abi.LpnpProblem()
         assert lib.lpnp_solve(None, 1.0, 1) == _abi.EINVAL
         assert lib.lpnp_solve(ctypes.byref(p), 1.0, 1) == _abi.EINVAL
+        t = ctypes.c_void_p()
+        assert lib.lpnp_tape_create(ctypes.byref(t)) == _abi.OK
+        try:
+            tapes = (ctypes.c_void_p * 2)(t.value, t.value)
+            dens = (ctypes.c_void_p * 2)(h.value, h.value)
+            ptrs = (ctypes.c_void_p * 2)(0x10000, 0x20000)
+            args = (8, 8, 1, 1, 0.1, 2, 1.0, 1.0, 2, 1.0, 1, ptrs)
+            assert lib.lpnp_unrolled_forward_batched(tapes, dens, 0, ptrs, ptrs, *args) == _abi.EINVAL
+            assert lib.lpnp_unrolled_forward_batched(tapes, dens, 2, ptrs, ptrs, *args) == _abi.EINVAL  # repeats
+            assert lib.lpnp_unrolled_forward_batched(None, dens, 1, ptrs, ptrs, *args) == _abi.EINVAL
+            assert lib.lpnp_backward_batched(tapes, 2, ptrs, ptrs, ptrs, None, None) == _abi.EINVAL  # repeats
+            assert lib.lpnp_backward_batched(tapes, 1, ptrs, ptrs, ptrs, None, None) == _abi.EINVAL  # not recorded
+            assert lib.lpnp_backward(t, fake, fake, fake, None, None) == _abi.EINVAL
+        finally:
+            lib.lpnp_tape_destroy(t)
     finally:
         lib.dsgnlm_destroy(h)
     assert lib.dsgnlm_launch_count() == 0

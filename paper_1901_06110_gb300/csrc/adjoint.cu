@@ -15,6 +15,7 @@
 //   rows), and dL/dw_sr = G_sr = sum_k (a_k(s) - a_k(r)) (z_k(r) - z_k(s)), z_k = x_{k+1} + u_k;
 //   then through m, the T balancing passes, K1 = Lambda exp(-D c), c = 1 / (2 N_p^2 h^2),
 //   the patch distances D = box-sum of (g(p) - g(p + o))^2 and the reflection of the guide.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -23,6 +24,7 @@
 #include "combine.cuh"
 #include "common.cuh"
 #include "handle.h"
+#include "host_pool.h"
 #include "internal.h"
 
 namespace dsg {
@@ -30,6 +32,7 @@ namespace dsg {
 namespace {
 
 constexpr int kAdjTH = 16, kAdjTW = 32;  // pair-pass tiles, block (32, 8), 2 rows per thread
+constexpr int kMaxHalfOffsets = 2 * 12 * 13;  // n_h at the largest search radius (12)
 
 __device__ __forceinline__ float proj_deriv(float xb, int constraint) {
     if (constraint == 2) return (xb > 0.f && xb < 1.f) ? 1.f : 0.f;
@@ -37,43 +40,31 @@ __device__ __forceinline__ float proj_deriv(float xb, int constraint) {
     return 1.f;
 }
 
-// m = max_s d_s t_s and the first maximiser (one block of 1024 threads)
-__global__ void __launch_bounds__(1024) adj_m_argmax_kernel(const float* __restrict__ d, const float* __restrict__ t,
-                                                            int n, float* __restrict__ m_out, int* __restrict__ s_out) {
-    float best = -1.f;
-    int bi = 0x7fffffff;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        const float v = d[q] * t[q];
-        if (v > best) {
-            best = v;
-            bi = q;
-        }
+// m = max_s d_s t_s and its first maximiser.  Each candidate becomes one 64-bit key:
+// the bits of d_s t_s (positive floats order like their bit patterns) above the
+// complement of s, so a larger key is a larger value or, for equal values, a smaller
+// index.  Every warp folds its best key in with atomicMax, which does not depend on
+// the order of arrival; the finish kernel unpacks the key.
+__global__ void __launch_bounds__(256) adj_m_key_kernel(const float* __restrict__ d, const float* __restrict__ t,
+                                                        int n, unsigned long long* __restrict__ key) {
+    unsigned long long best = 0ull;
+    for (int q = blockIdx.x * 256 + threadIdx.x; q < n; q += gridDim.x * 256) {
+        const unsigned long long k =
+            ((unsigned long long)__float_as_uint(d[q] * t[q]) << 32) | (unsigned long long)(0xffffffffu - (unsigned)q);
+        best = k > best ? k : best;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) {
-            best = ov;
-            bi = oi;
-        }
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        best = other > best ? other : best;
     }
-    __shared__ float sv[32];
-    __shared__ int si[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        sv[warp] = best;
-        si[warp] = bi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-            if (sv[w] > best || (sv[w] == best && si[w] < bi)) {
-                best = sv[w];
-                bi = si[w];
-            }
-        *m_out = best;
-        *s_out = bi;
-    }
+    if ((threadIdx.x & 31) == 0) atomicMax(key, best);
+}
+
+__global__ void adj_m_finish_kernel(const unsigned long long* __restrict__ key, float* __restrict__ m_out,
+                                    int* __restrict__ s_out) {
+    const unsigned long long k = *key;
+    *m_out = __uint_as_float((unsigned)(k >> 32));
+    *s_out = (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
 }
 
 // a_k = vh - uh, z_k = x_{k+1} + u_k
@@ -158,24 +149,45 @@ __device__ __forceinline__ void stage_fields(float* S, const float* __restrict__
 // dh0(s) = sum_o G_sr d_r K1_sr, and per-block partials of
 // -(1/m^2) sum over half-window pairs of G d_s d_r K1.  G is symmetric in (s, r), so
 // the other half of dh comes from these planes (pair pass T).
-// Fields staged over the tile and its forward halo: a_k, z_k (k < N) and d.  With
-// NR > 0 (N <= NR) the values at s are held in registers; both forms sum in the same
-// order.
-template <typename WT, int NR>
+// Staged over the tile and its forward halo: (a_k, z_k, a_{k+1}, z_{k+1}) as one float4
+// per pair of iterations (zeros past N, which add exact zeros), then d.  With NP > 0
+// (NP = ceil(N / 2)) the values at s are held in registers and the loop is unrolled;
+// NP = 0 reads them from shared memory.  Both sum in the same order.
+template <typename WT, int NP>
 __global__ void __launch_bounds__(256)
 adj_pairs_g_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const float* __restrict__ AZ,
                    const float* __restrict__ d, float inv_m, float* __restrict__ Gp, float* __restrict__ dh0,
                    double* __restrict__ m_part) {
-    extern __shared__ float S[];
+    extern __shared__ float4 S4[];
     const int y0 = blockIdx.y * kAdjTH, x0 = blockIdx.x * kAdjTW;
     const int RH = kAdjTH + rs, RW = kAdjTW + 2 * rs, cells = RH * RW;
     const size_t n = (size_t)H * W;
-    stage_fields(S, AZ, 2 * N, n, H, W, y0, x0 - rs, RH, RW);
-    stage_fields(S + 2 * N * cells, d, 1, n, H, W, y0, x0 - rs, RH, RW);
+    const int np = (N + 1) >> 1;
+    float* Sd = reinterpret_cast<float*>(S4 + (size_t)np * cells);
+    {
+        const int tid = threadIdx.y * 32 + threadIdx.x;
+        for (int idx = tid; idx < cells; idx += 256) {
+            const int ra = idx / RW, cb = idx - ra * RW;
+            const int i = y0 + ra, j = x0 - rs + cb;
+            const bool in = i < H && j >= 0 && j < W;
+            const size_t q = in ? (size_t)i * W + j : 0;
+            for (int kp = 0; kp < np; ++kp) {
+                const int k0 = 2 * kp, k1 = k0 + 1;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (in) {
+                    v.x = AZ[(size_t)k0 * n + q];
+                    v.y = AZ[(size_t)(N + k0) * n + q];
+                    if (k1 < N) {
+                        v.z = AZ[(size_t)k1 * n + q];
+                        v.w = AZ[(size_t)(N + k1) * n + q];
+                    }
+                }
+                S4[(size_t)kp * cells + idx] = v;
+            }
+            Sd[idx] = in ? d[q] : 0.f;
+        }
+    }
     __syncthreads();
-    const float* Sa = S;
-    const float* Sz = S + N * cells;
-    const float* Sd = S + 2 * N * cells;
     const int Wp = plane_pitch(W);
     const size_t plane = (size_t)H * Wp;
     double mpart = 0.0;
@@ -184,13 +196,10 @@ adj_pairs_g_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const 
         const int i = y0 + py;
         if (i >= H || j >= W) continue;
         const int cs = py * RW + threadIdx.x + rs;  // cell of s
-        float as[NR > 0 ? NR : 1], zs[NR > 0 ? NR : 1];
-        if constexpr (NR > 0) {
+        float4 sv[NP > 0 ? NP : 1];
+        if constexpr (NP > 0) {
 #pragma unroll
-            for (int kk = 0; kk < NR; ++kk) {
-                as[kk] = kk < N ? Sa[kk * cells + cs] : 0.f;
-                zs[kk] = kk < N ? Sz[kk * cells + cs] : 0.f;
-            }
+            for (int kp = 0; kp < NP; ++kp) sv[kp] = S4[kp * cells + cs];
         }
         const float ds = Sd[cs];
         float accd = 0.f, accm = 0.f;
@@ -207,14 +216,19 @@ adj_pairs_g_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const 
                 const float K = to_f32(P[at]);
                 const int cr = cs + oy * RW + ox;
                 float G = 0.f;
-                if constexpr (NR > 0) {
+                if constexpr (NP > 0) {
 #pragma unroll
-                    for (int kk = 0; kk < NR; ++kk)
-                        if (kk < N) G = fmaf(as[kk] - Sa[kk * cells + cr], Sz[kk * cells + cr] - zs[kk], G);
+                    for (int kp = 0; kp < NP; ++kp) {
+                        const float4 r = S4[kp * cells + cr];
+                        G = fmaf(sv[kp].x - r.x, r.y - sv[kp].y, G);
+                        G = fmaf(sv[kp].z - r.z, r.w - sv[kp].w, G);
+                    }
                 } else {
-                    for (int kk = 0; kk < N; ++kk)
-                        G = fmaf(Sa[kk * cells + cs] - Sa[kk * cells + cr], Sz[kk * cells + cr] - Sz[kk * cells + cs],
-                                 G);
+                    for (int kp = 0; kp < np; ++kp) {
+                        const float4 a = S4[kp * cells + cs], r = S4[kp * cells + cr];
+                        G = fmaf(a.x - r.x, r.y - a.y, G);
+                        G = fmaf(a.z - r.z, r.w - a.w, G);
+                    }
                 }
                 Gp[at] = G;
                 const float dr = Sd[cr];
@@ -249,16 +263,22 @@ adj_pairs_t_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H
     const int Wp = plane_pitch(W);
     const size_t plane = (size_t)H * Wp;
     float acc = dh0[(size_t)i * W + j];
-    for (int oy = 0; oy <= rs; ++oy) {
+    for (int oy = 0; oy <= rs && i - oy >= 0; ++oy) {
         const int ri = i - oy;
-        if (ri < 0) break;
         const int ox0 = oy == 0 ? 1 : -rs;
-        for (int ox = ox0; ox <= rs; ++ox) {
+        int k = oy == 0 ? 0 : rs + (oy - 1) * (2 * rs + 1);  // half offset of (oy, ox0)
+        const size_t row = (size_t)ri * Wp;
+        const float* drow = d + (size_t)ri * W;
+        // predicated loads (no early exit), so the unrolled loads issue together
+#pragma unroll 4
+        for (int ox = ox0; ox <= rs; ++ox, ++k) {
             const int rj = j - ox;
-            if (rj < 0 || rj >= W) continue;
-            const int k = oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
-            const size_t at = (size_t)k * plane + (size_t)ri * Wp + rj;
-            acc = fmaf(Gp[at] * d[(size_t)ri * W + rj], to_f32(P[at]), acc);
+            const bool in = rj >= 0 && rj < W;
+            const size_t at = (size_t)k * plane + row + (in ? rj : 0);
+            const float g = in ? Gp[at] : 0.f;
+            const float w = in ? to_f32(P[at]) : 0.f;
+            const float dv = in ? drow[rj] : 0.f;
+            acc = fmaf(g * dv, w, acc);
         }
     }
     dh[(size_t)i * W + j] = acc * inv_m;
@@ -348,11 +368,21 @@ adj_pairs_b_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H
     const float* Sdp = S;                  // d^0 .. d^T
     const float* Sth = S + (T + 1) * cells;  // th^0 .. th^{T-1}
     const float* Sd = Sdp + T * cells;     // d = d^T
+    __shared__ float lglam[kMaxHalfOffsets];
+    {
+        const float inv_hat = 1.0f / (float)(rs + 1);
+        for (int k = threadIdx.y * 32 + threadIdx.x; k < num_half_offsets(rs); k += 256) {
+            int oy, ox;
+            half_offset(k, rs, oy, ox);
+            lglam[k] = logf((1.0f - fabsf((float)oy) * inv_hat) * (1.0f - fabsf((float)ox) * inv_hat));
+        }
+    }
+    __syncthreads();
+    const float inv_c = 1.0f / c;
     const int ss = *s_star;
     const float mh = (float)*mh_ptr;
     const int Wp = plane_pitch(W);
     const size_t plane = (size_t)H * Wp;
-    const float inv_hat = 1.0f / (float)(rs + 1);
     double hpart = 0.0;
     const int j = x0 + threadIdx.x;
     for (int py = threadIdx.y; py < kAdjTH; py += 8) {
@@ -360,6 +390,7 @@ adj_pairs_b_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H
         if (i >= H || j >= W) continue;
         const int cs = py * RW + threadIdx.x + rs;
         const int sidx = i * W + j;
+        float hp = 0.f;  // this pixel's sum of Kh K1 D (FP32 over its n_h pairs)
         for (int oy = 0; oy <= rs; ++oy) {
             const int ox0 = oy == 0 ? 1 : -rs;
             for (int ox = ox0; ox <= rs; ++ox) {
@@ -378,13 +409,11 @@ adj_pairs_b_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H
                 const int ridx = ri * W + rj;
                 if (sidx == ss || ridx == ss) Kh = fmaf(mh, Sd[cs] * Sd[cr], Kh);
                 Dhat[at] = -c * K * Kh;
-                if (K > 0.f) {
-                    const float lam = (1.0f - fabsf((float)oy) * inv_hat) * (1.0f - fabsf((float)ox) * inv_hat);
-                    const float D = -logf(K / lam) / c;
-                    hpart += (double)Kh * (double)K * (double)D * (double)hfac;
-                }
+                // D = -log(K1 / lam) / c, lam the hat weight of the offset
+                if (K > 0.f) hp = fmaf(Kh * K, (lglam[k] - logf(K)) * inv_c, hp);
             }
         }
+        hpart += (double)hp * (double)hfac;
     }
     hpart = warp_sum(hpart);
     __shared__ double sm[8];
@@ -426,10 +455,10 @@ adj_guide_kernel(const float* __restrict__ Dhat, const float* __restrict__ guide
     float* Ds = Gs + GH * GW;
     float* Rs = Ds + DH * DW;  // horizontal box sums [DH][EW]
     float* Es = Rs + DH * EW;  // [EH][EW]
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < GH * GW; idx += 256) {
-        const int a = idx / GW, b = idx - a * GW;
-        Gs[idx] = guide[(size_t)sym_index(py0 - rs + a, H) * W + sym_index(px0 - rs + b, W)];
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;  // rows of 32 threads, 8 rows
+    for (int a = ty; a < GH; a += 8) {
+        const size_t row = (size_t)sym_index(py0 - rs + a, H) * W;
+        for (int b = tx; b < GW; b += 32) Gs[a * GW + b] = guide[row + sym_index(px0 - rs + b, W)];
     }
     const int Wp = plane_pitch(W);
     const size_t plane = (size_t)H * Wp;
@@ -439,25 +468,28 @@ adj_guide_kernel(const float* __restrict__ Dhat, const float* __restrict__ guide
         half_offset(k, rs, oy, ox);
         const float* Dk = Dhat + (size_t)k * plane;
         __syncthreads();
-        for (int idx = tid; idx < DH * DW; idx += 256) {
-            const int a = idx / DW, b = idx - a * DW;
-            const int i = py0 - rs - rp + a, j = px0 - rs - rp + b;
-            Ds[idx] = (i >= 0 && i < H && j >= 0 && j < W) ? Dk[(size_t)i * Wp + j] : 0.f;
+        for (int a = ty; a < DH; a += 8) {
+            const int i = py0 - rs - rp + a;
+            const bool row_in = i >= 0 && i < H;
+            for (int b = tx; b < DW; b += 32) {
+                const int j = px0 - rs - rp + b;
+                Ds[a * DW + b] = (row_in && j >= 0 && j < W) ? Dk[(size_t)i * Wp + j] : 0.f;
+            }
         }
         __syncthreads();
-        for (int idx = tid; idx < DH * EW; idx += 256) {
-            const int a = idx / EW, b = idx - a * EW;
-            float s = 0.f;
-            for (int t = 0; t <= 2 * rp; ++t) s += Ds[a * DW + b + t];
-            Rs[idx] = s;
-        }
+        for (int a = ty; a < DH; a += 8)
+            for (int b = tx; b < EW; b += 32) {
+                float s = 0.f;
+                for (int t = 0; t <= 2 * rp; ++t) s += Ds[a * DW + b + t];
+                Rs[a * EW + b] = s;
+            }
         __syncthreads();
-        for (int idx = tid; idx < EH * EW; idx += 256) {
-            const int a = idx / EW, b = idx - a * EW;
-            float s = 0.f;
-            for (int t = 0; t <= 2 * rp; ++t) s += Rs[(a + t) * EW + b];
-            Es[idx] = s;
-        }
+        for (int a = ty; a < EH; a += 8)
+            for (int b = tx; b < EW; b += 32) {
+                float s = 0.f;
+                for (int t = 0; t <= 2 * rp; ++t) s += Rs[(a + t) * EW + b];
+                Es[a * EW + b] = s;
+            }
         __syncthreads();
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -527,7 +559,7 @@ struct lpnp_tape {
     int blur_r = 0;
     float blur_sigma = 1.f;
     DevBuf Dh, Th, X, V, U, AZ, xh, vh, uh, zh, g, wa, grad, ata, gs, dh[2], base, thp, Dhat, Gp, ge, gb, ctl,
-        part, m, sstar, mh, rho_part, h_part, m_part, scratch;
+        part, m, mkey, sstar, mh, rho_part, h_part, m_part, scratch;
     float inv_m = 1.f;
     // pinned host words read back after the stream work: m, the scalar cotangents and
     // the handle's wait-error flag
@@ -554,7 +586,7 @@ dsgnlm_status tape_ck(cudaError_t e) {
     } while (0)
 
 size_t pairs_g_smem(int N, int rs) {
-    return sizeof(float) * (size_t)(2 * N + 1) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
+    return (sizeof(float4) * (size_t)((N + 1) / 2) + sizeof(float)) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
 }
 size_t pairs_b_smem(int T, int rs) {
     return sizeof(float) * (size_t)(2 * T + 1) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
@@ -575,7 +607,18 @@ cudaError_t pairs_gt(const lpnp_tape* tp, const void* planes, cudaStream_t st, d
                                               tp->Gp.as<float>(), tp->dh[1].as<float>(), m_part);
         return cudaGetLastError();
     };
-    cudaError_t e = N <= 16 ? run(adj_pairs_g_kernel<WT, 16>) : run(adj_pairs_g_kernel<WT, 0>);
+    cudaError_t e;
+    switch ((N + 1) / 2) {
+        case 1: e = run(adj_pairs_g_kernel<WT, 1>); break;
+        case 2: e = run(adj_pairs_g_kernel<WT, 2>); break;
+        case 3: e = run(adj_pairs_g_kernel<WT, 3>); break;
+        case 4: e = run(adj_pairs_g_kernel<WT, 4>); break;
+        case 5: e = run(adj_pairs_g_kernel<WT, 5>); break;
+        case 6: e = run(adj_pairs_g_kernel<WT, 6>); break;
+        case 7: e = run(adj_pairs_g_kernel<WT, 7>); break;
+        case 8: e = run(adj_pairs_g_kernel<WT, 8>); break;
+        default: e = run(adj_pairs_g_kernel<WT, 0>); break;
+    }
     count_launches(1);
     if (e != cudaSuccess) return e;
     adj_pairs_t_kernel<WT><<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, st>>>(
@@ -624,7 +667,7 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (t->den) cudaStreamSynchronize(t->den->stream);
     DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
                       &t->wa, &t->grad, &t->ata, &t->gs, &t->dh[0], &t->dh[1], &t->base, &t->thp, &t->Dhat,
-                      &t->Gp, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->sstar, &t->mh, &t->rho_part, &t->h_part,
+                      &t->Gp, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->mkey, &t->sstar, &t->mh, &t->rho_part, &t->h_part,
                       &t->m_part, &t->scratch};
     for (DevBuf* b : bufs) b->release();
     if (t->host) cudaFreeHost(t->host);
@@ -684,6 +727,7 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
     TAPE_CK(tp->part.ensure(sizeof(float2) * (size_t)balance_combine_blocks(H, W)));
     TAPE_CK(tp->m.ensure(sizeof(float)));
     TAPE_CK(tp->sstar.ensure(sizeof(int)));
+    TAPE_CK(tp->mkey.ensure(sizeof(unsigned long long)));
     TAPE_CK(cudaMemsetAsync(tp->ctl.p, 0, sizeof(BalanceCtl), st));  // done = 0: passes always run
     TAPE_CK(launch_fill(tp->Dh.as<float>(), 1.0f, n, st));
     // T balancing passes with every d^p and t^p kept, then t^T = K1 d^T
@@ -698,8 +742,11 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
     }
     const float* dT = tp->Dh.as<float>() + (size_t)T * n;
     const float* tT = tp->Th.as<float>() + (size_t)T * n;
-    adj_m_argmax_kernel<<<1, 1024, 0, st>>>(dT, tT, (int)n, tp->m.as<float>(), tp->sstar.as<int>());
-    count_launches(1);
+    TAPE_CK(cudaMemsetAsync(tp->mkey.p, 0, sizeof(unsigned long long), st));
+    adj_m_key_kernel<<<(int)std::min<size_t>((n + 255) / 256, 1024), 256, 0, st>>>(
+        dT, tT, (int)n, tp->mkey.as<unsigned long long>());
+    adj_m_finish_kernel<<<1, 1, 0, st>>>(tp->mkey.as<unsigned long long>(), tp->m.as<float>(), tp->sstar.as<int>());
+    count_launches(2);
     TAPE_CK(cudaGetLastError());
     TAPE_CK(cudaMemcpyAsync(&tp->host->m, tp->m.p, sizeof(float), cudaMemcpyDeviceToHost, st));
     return DSGNLM_OK;
@@ -917,16 +964,18 @@ dsgnlm_status lpnp_unrolled_forward_batched(lpnp_tape_t* tapes, dsgnlm_t* dens, 
         for (int j = 0; j < i; ++j)
             if (tapes[j] == tapes[i] || dens[j] == dens[i]) return DSGNLM_EINVAL;
     }
-    // every image's weights and balance are queued before the first wait for m
-    for (int i = 0; i < count; ++i) {
-        dsgnlm_status s = forward_begin(tapes[i], dens[i], y[i], guide[i], H, W, patch_r, search_r, bandwidth,
-                                        balance_passes, alpha, rho, iters, blur_sigma, blur_r);
-        if (s != DSGNLM_OK) return s;
-    }
-    for (int i = 0; i < count; ++i) {
-        dsgnlm_status s = forward_finish(tapes[i], x_out[i]);
-        if (s != DSGNLM_OK) return s;
-    }
+    // every image's weights and balance are queued before the first wait for m; the
+    // images are queued from the host pool's threads, each on its handle's stream
+    std::vector<dsgnlm_status> st(count, DSGNLM_OK);
+    HostPool::run(count, [&](int i) {
+        st[i] = forward_begin(tapes[i], dens[i], y[i], guide[i], H, W, patch_r, search_r, bandwidth, balance_passes,
+                              alpha, rho, iters, blur_sigma, blur_r);
+    });
+    for (int i = 0; i < count; ++i)
+        if (st[i] != DSGNLM_OK) return st[i];
+    HostPool::run(count, [&](int i) { st[i] = forward_finish(tapes[i], x_out[i]); });
+    for (int i = 0; i < count; ++i)
+        if (st[i] != DSGNLM_OK) return st[i];
     return DSGNLM_OK;
 }
 
@@ -944,10 +993,14 @@ dsgnlm_status lpnp_backward_batched(lpnp_tape_t* tapes, int count, const float* 
         for (int j = 0; j < i; ++j)
             if (tapes[j] == tapes[i]) return DSGNLM_EINVAL;
     }
-    for (int i = 0; i < count; ++i) {
-        dsgnlm_status s = backward_begin(tapes[i], x_bar[i], y_bar[i], guide_bar[i]);
-        if (s != DSGNLM_OK) return s;
-    }
+    std::vector<dsgnlm_status> st(count, DSGNLM_OK);
+    HostPool::run(count, [&](int i) { st[i] = backward_begin(tapes[i], x_bar[i], y_bar[i], guide_bar[i]); });
+    for (int i = 0; i < count; ++i)
+        if (st[i] != DSGNLM_OK) {
+            for (int j = 0; j < count; ++j)  // nothing left in flight
+                if (tapes[j]->den) cudaStreamSynchronize(tapes[j]->den->stream);
+            return st[i];
+        }
     dsgnlm_status first = DSGNLM_OK;
     for (int i = 0; i < count; ++i) {
         dsgnlm_status s = backward_finish(tapes[i], h_bar ? h_bar + i : nullptr, rho_bar ? rho_bar + i : nullptr);

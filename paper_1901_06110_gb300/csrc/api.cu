@@ -49,15 +49,16 @@ dsgnlm_status fail_cuda(cudaError_t e) {
 
 // Tensor map of the weight planes [n_h][H][pitch] for the TMA stencil path.
 cudaError_t encode_planes_map(void* out, void* planes, int dtype, int H, int W, int nh) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
+    // looked up once (a thread-safe static initialisation)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         cudaDriverEntryPointQueryResult q;
         void* fn = nullptr;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                                          cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
+        return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? (PFN_cuTensorMapEncodeTiled_v12000)fn
+                                                                      : nullptr;
+    }();
+    if (!encode) return cudaErrorNotSupported;
     const size_t esz = dtype == DSGNLM_F32 ? 4 : 2;
     const CUtensorMapDataType dt = dtype == DSGNLM_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : dtype == DSGNLM_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16

@@ -419,14 +419,11 @@ size_t p1_smem_bytes() {
 template <int RS, typename WT>
 cudaError_t p1_launch(const TmaPlan& plan, int H, int W, const float* d, const float* z, unsigned* err,
                       const int* skip, cudaStream_t st) {
-    static bool configured = false;
     const size_t smem = p1_smem_bytes<RS, WT>();
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(stencil_p1_kernel<RS, WT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // set once per instantiation (a thread-safe static initialisation)
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(stencil_p1_kernel<RS, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configured != cudaSuccess) return configured;
     dim3 grid(plan.tiles_x, plan.tiles_y, plan.splits.n);
     stencil_p1_kernel<RS, WT><<<grid, kThreads, smem, st>>>(*(const CUtensorMap*)plan.tmap, H, W, d, z,
                                                             plan.splits, plan.partials, err, skip);
@@ -437,14 +434,10 @@ cudaError_t p1_launch(const TmaPlan& plan, int H, int W, const float* d, const f
 template <int RS, typename WT>
 cudaError_t p1b_launch(const BatchMaps& maps, const BatchInst* insts, const int4* work, int nwork, unsigned* err,
                        cudaStream_t st) {
-    static bool configured = false;
     const size_t smem = p1_smem_bytes<RS, WT>();
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(stencil_p1_batched_kernel<RS, WT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static const cudaError_t configured = cudaFuncSetAttribute(
+        stencil_p1_batched_kernel<RS, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configured != cudaSuccess) return configured;
     if (nwork <= 0) return cudaSuccess;
     stencil_p1_batched_kernel<RS, WT><<<nwork, kThreads, smem, st>>>(maps, insts, work, err);
     count_launches(1);

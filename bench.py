@@ -399,10 +399,26 @@ def run_unrolled(steps: int, warmup: int, flush):
         if k >= warmup:
             fwd += e[0].elapsed_time(e[1])
             bwd += e[1].elapsed_time(e[2])
+    # Algorithmic DRAM bytes of one forward + backward, in volumes of the weight planes
+    # (n_h x H x W FP32): the build writes them once; every W application streams them
+    # (T + 1 balancing passes and N iterations forward, N iterations and T balancing
+    # passes backward); the pair passes read K1 three times, write and read G twice,
+    # write D-hat once, and the guide adjoint reads D-hat once.
+    T, N = params.balance_passes, params.iters
+    nh = 2 * params.search_r * (params.search_r + 1)
+    volumes = 1 + (T + 1) + N + N + T + 3 + 2 + 1 + 1 + 1
+    step_bytes = B * volumes * nh * H * W * 4
+    ms = (fwd + bwd) / steps
+    peak, peak_src = _peaks()
+    achieved = step_bytes / (ms / 1e3) / 1e9
     return {"workload": f"unroll8x256: {B} x {H}x{W} 2x SR, patch 5x5, search 15x15, 4 balancing passes, "
                         f"{wl['iters']} unrolled iterations, MSE loss; grads w.r.t. y, guide, h, rho",
             "steps": steps, "forward_ms": fwd / steps, "backward_ms": bwd / steps,
-            "fwd_bwd_ms": (fwd + bwd) / steps, "fwd_bwd_mpix_s": B * H * W / 1e6 / ((fwd + bwd) / steps / 1e3)}
+            "fwd_bwd_ms": ms, "fwd_bwd_mpix_s": B * H * W / 1e6 / (ms / 1e3),
+            "roofline": {"bound": "hbm", "scope": "whole forward + backward step (all images)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_step": step_bytes, "plane_volumes_per_image": volumes,
+                         "peak_source": peak_src, "traffic": None}}
 
 
 def run_spi(steps: int, warmup: int, flush):

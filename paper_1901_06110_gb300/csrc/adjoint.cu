@@ -33,6 +33,7 @@ namespace {
 
 constexpr int kAdjTH = 16, kAdjTW = 32;  // pair-pass tiles, block (32, 8), 2 rows per thread
 constexpr int kMaxHalfOffsets = 2 * 12 * 13;  // n_h at the largest search radius (12)
+constexpr int kPairSplit = 4;  // pair passes G and B: the half offsets in this many chunks (grid z)
 
 __device__ __forceinline__ float proj_deriv(float xb, int constraint) {
     if (constraint == 2) return (xb > 0.f && xb < 1.f) ? 1.f : 0.f;
@@ -148,13 +149,15 @@ __device__ __forceinline__ void stage_fields(float* S, const float* __restrict__
 // stored as planes like K1 (0 where r is off the image), the forward half of
 // dh0(s) = sum_o G_sr d_r K1_sr, and per-block partials of
 // -(1/m^2) sum over half-window pairs of G d_s d_r K1.  G is symmetric in (s, r), so
-// the other half of dh comes from these planes (pair pass T).
+// the other half of dh comes from these planes (pair pass T).  Grid z splits the half
+// offsets into kPairSplit contiguous chunks; chunk z writes its own dh0 plane and
+// partials.
 // Staged over the tile and its forward halo: (a_k, z_k, a_{k+1}, z_{k+1}) as one float4
 // per pair of iterations (zeros past N, which add exact zeros), then d.  With NP > 0
 // (NP = ceil(N / 2)) the values at s are held in registers and the loop is unrolled;
 // NP = 0 reads them from shared memory.  Both sum in the same order.
 template <typename WT, int NP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 adj_pairs_g_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const float* __restrict__ AZ,
                    const float* __restrict__ d, float inv_m, float* __restrict__ Gp, float* __restrict__ dh0,
                    double* __restrict__ m_part) {
@@ -164,6 +167,8 @@ adj_pairs_g_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const 
     const size_t n = (size_t)H * W;
     const int np = (N + 1) >> 1;
     float* Sd = reinterpret_cast<float*>(S4 + (size_t)np * cells);
+    const int nh = num_half_offsets(rs);
+    const int kz0 = nh * (int)blockIdx.z / kPairSplit, kz1 = nh * ((int)blockIdx.z + 1) / kPairSplit;
     {
         const int tid = threadIdx.y * 32 + threadIdx.x;
         for (int idx = tid; idx < cells; idx += 256) {
@@ -203,17 +208,17 @@ adj_pairs_g_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const 
         }
         const float ds = Sd[cs];
         float accd = 0.f, accm = 0.f;
-        for (int oy = 0; oy <= rs; ++oy) {
-            const int ox0 = oy == 0 ? 1 : -rs;
-            for (int ox = ox0; ox <= rs; ++ox) {
-                const int k = oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
+        int oy, ox;
+        half_offset(kz0, rs, oy, ox);
+        // branch-free body (an off-image partner r reads staged zeros and adds an exact
+        // zero), so the unrolled iterations issue their loads together
+#pragma unroll 4
+        for (int k = kz0; k < kz1; ++k) {
+            {
                 const size_t at = (size_t)k * plane + (size_t)i * Wp + j;
-                const int ri = i + oy, rj = j + ox;
-                if (ri >= H || rj < 0 || rj >= W) {
-                    Gp[at] = 0.f;
-                    continue;
-                }
-                const float K = to_f32(P[at]);
+                const int rj = j + ox;
+                const bool in = i + oy < H && rj >= 0 && rj < W;
+                const float K = in ? to_f32(P[at]) : 0.f;
                 const int cr = cs + oy * RW + ox;
                 float G = 0.f;
                 if constexpr (NP > 0) {
@@ -230,13 +235,17 @@ adj_pairs_g_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const 
                         G = fmaf(a.z - r.z, r.w - a.w, G);
                     }
                 }
-                Gp[at] = G;
+                Gp[at] = in ? G : 0.f;
                 const float dr = Sd[cr];
                 accd = fmaf(G * dr, K, accd);
                 accm = fmaf(G * ds * dr, K, accm);
             }
+            if (++ox > rs) {
+                ++oy;
+                ox = -rs;
+            }
         }
-        dh0[(size_t)i * W + j] = accd;
+        dh0[blockIdx.z * n + (size_t)i * W + j] = accd;
         mpart -= (double)accm * (double)inv_m * (double)inv_m;
     }
     mpart = warp_sum(mpart);
@@ -247,12 +256,13 @@ adj_pairs_g_kernel(const WT* __restrict__ P, int H, int W, int rs, int N, const 
     if (t == 0) {
         double acc = 0.0;
         for (int w = 0; w < 8; ++w) acc += sm[w];
-        m_part[blockIdx.y * gridDim.x + blockIdx.x] = acc;
+        m_part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
     }
 }
 
-// Pair pass T: dh(s) = (1/m) (dh0(s) + sum_o G_{s-o, s} d_{s-o} K1_{s-o, s}), the
-// backward half-window read from the planes at s - o
+// Pair pass T: dh(s) = (1/m) (dh0(s) + sum_o G_{s-o, s} d_{s-o} K1_{s-o, s}), dh0 the
+// sum of pass G's chunk planes (in chunk order) and the backward half-window read from
+// the planes at s - o
 template <typename WT>
 __global__ void __launch_bounds__(256)
 adj_pairs_t_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H, int W, int rs,
@@ -262,7 +272,9 @@ adj_pairs_t_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H
     if (i >= H || j >= W) return;
     const int Wp = plane_pitch(W);
     const size_t plane = (size_t)H * Wp;
+    const size_t n = (size_t)H * W;
     float acc = dh0[(size_t)i * W + j];
+    for (int z = 1; z < kPairSplit; ++z) acc += dh0[z * n + (size_t)i * W + j];
     for (int oy = 0; oy <= rs && i - oy >= 0; ++oy) {
         const int ri = i - oy;
         const int ox0 = oy == 0 ? 1 : -rs;
@@ -351,9 +363,9 @@ __global__ void __launch_bounds__(256) adj_sk_finish_kernel(Cover cv, int H, int
 //   Kh = G d_s d_r / m + sum_p (th^p_s d^p_r + th^p_r d^p_s) + [s or r = s*] mh d_s d_r,
 // then Dh = -c K1 Kh (written as planes) and per-block partials of dL/dh = sum Kh K1 D 2c/h.
 // G comes from the planes of pair pass G; fields staged over the tile and its forward
-// halo: d^p (T + 1) and th^p (T).
+// halo: d^p (T + 1) and th^p (T).  Grid z splits the half offsets as in pass G.
 template <typename WT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 adj_pairs_b_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H, int W, int rs, int T,
                    const float* __restrict__ Dh, const float* __restrict__ Th, float inv_m, float c, float hfac,
                    const int* __restrict__ s_star, const double* __restrict__ mh_ptr, float* __restrict__ Dhat,
@@ -379,6 +391,8 @@ adj_pairs_b_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H
     }
     __syncthreads();
     const float inv_c = 1.0f / c;
+    const int kz0 = num_half_offsets(rs) * (int)blockIdx.z / kPairSplit;
+    const int kz1 = num_half_offsets(rs) * ((int)blockIdx.z + 1) / kPairSplit;
     const int ss = *s_star;
     const float mh = (float)*mh_ptr;
     const int Wp = plane_pitch(W);
@@ -390,27 +404,32 @@ adj_pairs_b_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H
         if (i >= H || j >= W) continue;
         const int cs = py * RW + threadIdx.x + rs;
         const int sidx = i * W + j;
-        float hp = 0.f;  // this pixel's sum of Kh K1 D (FP32 over its n_h pairs)
-        for (int oy = 0; oy <= rs; ++oy) {
-            const int ox0 = oy == 0 ? 1 : -rs;
-            for (int ox = ox0; ox <= rs; ++ox) {
-                const int k = oy == 0 ? ox - 1 : rs + (oy - 1) * (2 * rs + 1) + ox + rs;
+        float hp = 0.f;  // this pixel's sum of Kh K1 D over its chunk (FP32)
+        int oy, ox;
+        half_offset(kz0, rs, oy, ox);
+        // branch-free body (off-image pairs are masked), so the unrolled iterations issue
+        // their loads together
+#pragma unroll 2
+        for (int k = kz0; k < kz1; ++k) {
+            {
                 const size_t at = (size_t)k * plane + (size_t)i * Wp + j;
-                const int ri = i + oy, rj = j + ox;
-                if (ri >= H || rj < 0 || rj >= W) {
-                    Dhat[at] = 0.f;
-                    continue;
-                }
-                const float K = to_f32(P[at]);
+                const int rj = j + ox;
+                const bool in = i + oy < H && rj >= 0 && rj < W;
+                const float K = in ? to_f32(P[at]) : 0.f;
+                const float G = in ? Gp[at] : 0.f;
                 const int cr = cs + oy * RW + ox;
-                float Kh = Gp[at] * Sd[cs] * Sd[cr] * inv_m;
+                float Kh = G * Sd[cs] * Sd[cr] * inv_m;
                 for (int p = 0; p < T; ++p)
                     Kh += Sth[p * cells + cs] * Sdp[p * cells + cr] + Sth[p * cells + cr] * Sdp[p * cells + cs];
-                const int ridx = ri * W + rj;
+                const int ridx = (i + oy) * W + rj;
                 if (sidx == ss || ridx == ss) Kh = fmaf(mh, Sd[cs] * Sd[cr], Kh);
-                Dhat[at] = -c * K * Kh;
+                Dhat[at] = in ? -c * K * Kh : 0.f;
                 // D = -log(K1 / lam) / c, lam the hat weight of the offset
-                if (K > 0.f) hp = fmaf(Kh * K, (lglam[k] - logf(K)) * inv_c, hp);
+                hp = (in && K > 0.f) ? fmaf(Kh * K, (lglam[k] - logf(K)) * inv_c, hp) : hp;
+            }
+            if (++ox > rs) {
+                ++oy;
+                ox = -rs;
             }
         }
         hpart += (double)hp * (double)hfac;
@@ -423,98 +442,104 @@ adj_pairs_b_kernel(const WT* __restrict__ P, const float* __restrict__ Gp, int H
     if (t == 0) {
         double acc = 0.0;
         for (int w = 0; w < 8; ++w) acc += sm[w];
-        h_part[blockIdx.y * gridDim.x + blockIdx.x] = acc;
+        h_part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
     }
 }
 
-// Patch-distance adjoint, in gather form.  With g the reflected guide on the grid
-// extended by the patch radius (p in [-rp, H + rp) x [-rp, W + rp)) and, per offset o,
+// Patch-distance adjoint.  With g the reflected guide on the grid extended by the
+// patch radius (p in [-rp, H + rp) x [-rp, W + rp)) and, per offset o,
 //   E_o(q) = sum_{t in patch} Dh_o(q - t)               (box sum, Dh = 0 off the image)
 //   F_o(q) = 2 E_o(q) (g(q) - g(q + o)),
 // the cotangent of g(p) is ge(p) = sum_o F_o(p) - F_o(p - o): the first term from the
-// patch at q = p, the second from the patch whose partner pixel is p.  A CTA owns a
-// 16 x 32 tile of p and a chunk of 16 offsets; each cell is summed by one thread in a
-// fixed offset order and written to the chunk's own plane, so the result does not
-// depend on scheduling.  The fold kernel adds the chunks in order.
-constexpr int kGTH = 16, kGTW = 32, kGChunk = 16;
+// patch at q = p, the second from the patch whose partner pixel is p.  Two kernels:
+// the box sums of every D-hat plane onto the extended grid, then one thread per p
+// summing its offsets in a fixed order (no atomics, so the result does not depend on
+// scheduling).
+constexpr int kBT = 32;  // box-sum tile side (extended grid)
 
 __global__ void __launch_bounds__(256)
-adj_guide_kernel(const float* __restrict__ Dhat, const float* __restrict__ guide, int H, int W, int rp, int rs,
-                 float* __restrict__ ge_part) {
+adj_box_kernel(const float* __restrict__ Dhat, int H, int W, int rp, float* __restrict__ E) {
     extern __shared__ float S[];
-    const int nh = num_half_offsets(rs);
-    const int py0 = blockIdx.y * kGTH - rp, px0 = blockIdx.x * kGTW - rp;  // image coords of the tile origin
-    const int k0 = blockIdx.z * kGChunk, k1 = min(nh, k0 + kGChunk);
-    // g over rows [py0 - rs, py0 + TH + rs), cols [px0 - rs, px0 + TW + rs)
-    const int GH = kGTH + 2 * rs, GW = kGTW + 2 * rs;
-    // E over rows [py0 - rs, py0 + TH), cols [px0 - rs, px0 + TW + rs): q = p and q = p - o
-    const int EH = kGTH + rs, EW = kGTW + 2 * rs;
-    // Dh over the E region grown by rp on every side
-    const int DH = EH + 2 * rp, DW = EW + 2 * rp;
-    float* Gs = S;
-    float* Ds = Gs + GH * GW;
-    float* Rs = Ds + DH * DW;  // horizontal box sums [DH][EW]
-    float* Es = Rs + DH * EW;  // [EH][EW]
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;  // rows of 32 threads, 8 rows
-    for (int a = ty; a < GH; a += 8) {
-        const size_t row = (size_t)sym_index(py0 - rs + a, H) * W;
-        for (int b = tx; b < GW; b += 32) Gs[a * GW + b] = guide[row + sym_index(px0 - rs + b, W)];
-    }
+    const int k = blockIdx.z;
+    const int q0y = blockIdx.y * kBT - rp, q0x = blockIdx.x * kBT - rp;  // image coords of the tile origin
+    const int DW = kBT + 2 * rp;  // Dh over rows [q0y - rp, q0y + kBT + rp), same columns
+    float* Ds = S;                // [DW][DW]
+    float* Rs = Ds + DW * DW;     // horizontal sums [DW][kBT]
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int Wp = plane_pitch(W);
-    const size_t plane = (size_t)H * Wp;
-    float acc[2] = {0.f, 0.f};  // tile cells tid and tid + 256
-    for (int k = k0; k < k1; ++k) {
-        int oy, ox;
-        half_offset(k, rs, oy, ox);
-        const float* Dk = Dhat + (size_t)k * plane;
-        __syncthreads();
-        for (int a = ty; a < DH; a += 8) {
-            const int i = py0 - rs - rp + a;
-            const bool row_in = i >= 0 && i < H;
-            for (int b = tx; b < DW; b += 32) {
-                const int j = px0 - rs - rp + b;
-                Ds[a * DW + b] = (row_in && j >= 0 && j < W) ? Dk[(size_t)i * Wp + j] : 0.f;
-            }
-        }
-        __syncthreads();
-        for (int a = ty; a < DH; a += 8)
-            for (int b = tx; b < EW; b += 32) {
-                float s = 0.f;
-                for (int t = 0; t <= 2 * rp; ++t) s += Ds[a * DW + b + t];
-                Rs[a * EW + b] = s;
-            }
-        __syncthreads();
-        for (int a = ty; a < EH; a += 8)
-            for (int b = tx; b < EW; b += 32) {
-                float s = 0.f;
-                for (int t = 0; t <= 2 * rp; ++t) s += Rs[(a + t) * EW + b];
-                Es[a * EW + b] = s;
-            }
-        __syncthreads();
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int cell = tid + 256 * c;
-            const int ea = cell / kGTW + rs, eb = cell % kGTW + rs;  // p in the E and g regions
-            const float gp = Gs[ea * GW + eb];
-            const float fp = 2.f * Es[ea * EW + eb] * (gp - Gs[(ea + oy) * GW + eb + ox]);
-            const float fq = 2.f * Es[(ea - oy) * EW + eb - ox] * (Gs[(ea - oy) * GW + eb - ox] - gp);
-            acc[c] += fp - fq;
+    const float* Dk = Dhat + (size_t)k * H * Wp;
+    for (int a = ty; a < DW; a += 8) {
+        const int i = q0y - rp + a;
+        const bool row_in = i >= 0 && i < H;
+        for (int b = tx; b < DW; b += 32) {
+            const int j = q0x - rp + b;
+            Ds[a * DW + b] = (row_in && j >= 0 && j < W) ? Dk[(size_t)i * Wp + j] : 0.f;
         }
     }
-    const int XW = W + 2 * rp;
-    const size_t ep = (size_t)(H + 2 * rp) * XW;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const int cell = tid + 256 * c;
-        const int pi = py0 + cell / kGTW, pj = px0 + cell % kGTW;
-        if (pi < H + rp && pj < W + rp)
-            ge_part[blockIdx.z * ep + (size_t)(pi + rp) * XW + (pj + rp)] = acc[c];
+    __syncthreads();
+    for (int a = ty; a < DW; a += 8) {
+        float s = 0.f;
+        for (int t = 0; t <= 2 * rp; ++t) s += Ds[a * DW + tx + t];
+        Rs[a * kBT + tx] = s;
+    }
+    __syncthreads();
+    const int XW = W + 2 * rp, XH = H + 2 * rp;
+    float* Ek = E + (size_t)k * XH * XW;
+    const int qx = q0x + tx;
+    for (int a = ty; a < kBT; a += 8) {
+        const int qy = q0y + a;
+        if (qy >= H + rp || qx >= W + rp) continue;
+        float s = 0.f;
+        for (int t = 0; t <= 2 * rp; ++t) s += Rs[(a + t) * kBT + tx];
+        Ek[(size_t)(qy + rp) * XW + (qx + rp)] = s;
     }
 }
 
+__global__ void __launch_bounds__(256)
+adj_guide_kernel(const float* __restrict__ E, const float* __restrict__ guide, int H, int W, int rp, int rs,
+                 float* __restrict__ ge) {
+    extern __shared__ float Gs[];  // g over rows [p0y - rs, p0y + 8 + rs), cols [p0x - rs, p0x + 32 + rs)
+    const int p0y = blockIdx.y * 8 - rp, p0x = blockIdx.x * 32 - rp;
+    const int GH = 8 + 2 * rs, GW = 32 + 2 * rs;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int a = ty; a < GH; a += 8) {
+        const size_t row = (size_t)sym_index(p0y - rs + a, H) * W;
+        for (int b = tx; b < GW; b += 32) Gs[a * GW + b] = guide[row + sym_index(p0x - rs + b, W)];
+    }
+    __syncthreads();
+    const int py = p0y + ty, px = p0x + tx;
+    const int XW = W + 2 * rp, XH = H + 2 * rp;
+    if (py >= H + rp || px >= W + rp) return;
+    const size_t plane = (size_t)XH * XW;
+    const int ca = ty + rs, cb = tx + rs;  // p in Gs
+    const float gp = Gs[ca * GW + cb];
+    const size_t at = (size_t)(py + rp) * XW + (px + rp);
+    float acc = 0.f;
+    int oy, ox;
+    half_offset(0, rs, oy, ox);
+    const int nh = num_half_offsets(rs);
+#pragma unroll 4
+    for (int k = 0; k < nh; ++k) {
+        const float* Ek = E + (size_t)k * plane;
+        // q = p - o must lie on the extended grid (E is 0 beyond it)
+        const int qy = py - oy, qx = px - ox;
+        const bool qin = qy >= -rp && qx >= -rp && qx < W + rp;
+        const float ep = Ek[at];
+        const float eq = qin ? Ek[at - (size_t)oy * XW - ox] : 0.f;
+        const float fp = 2.f * ep * (gp - Gs[(ca + oy) * GW + cb + ox]);
+        const float fq = 2.f * eq * (Gs[(ca - oy) * GW + cb - ox] - gp);
+        acc += fp - fq;
+        if (++ox > rs) {
+            ++oy;
+            ox = -rs;
+        }
+    }
+    ge[at] = acc;
+}
+
 // gb(q) = (xh0 + vh0)(q) [0 < g(q) < 1] + sum of ge(p) over the extended p that reflect
-// onto q (p = 2 n m + q or 2 n m - 1 - q per axis), the chunks added in order
-__global__ void adj_fold_kernel(const float* __restrict__ ge_part, int nz, const float* __restrict__ xh0,
+// onto q (p = 2 n m + q or 2 n m - 1 - q per axis), in a fixed order
+__global__ void adj_fold_kernel(const float* __restrict__ ge, const float* __restrict__ xh0,
                                 const float* __restrict__ vh0, const float* __restrict__ guide, int H, int W, int rp,
                                 float* __restrict__ gb) {
     const int j = blockIdx.x * 32 + threadIdx.x;
@@ -524,7 +549,6 @@ __global__ void adj_fold_kernel(const float* __restrict__ ge_part, int nz, const
     const float g = guide[q];
     float acc = (g > 0.f && g < 1.f) ? xh0[q] + vh0[q] : 0.f;
     const int XW = W + 2 * rp;
-    const size_t ep = (size_t)(H + 2 * rp) * XW;
     const int my = rp / (2 * H) + 1, mx = rp / (2 * W) + 1;
     for (int m = -my; m <= my; ++m)
         for (int cy = 0; cy < 2; ++cy) {
@@ -534,8 +558,7 @@ __global__ void adj_fold_kernel(const float* __restrict__ ge_part, int nz, const
                 for (int cx = 0; cx < 2; ++cx) {
                     const int pj = cx == 0 ? 2 * W * n - 1 - j : 2 * W * n + j;
                     if (pj < -rp || pj >= W + rp) continue;
-                    const float* e = ge_part + (size_t)(pi + rp) * XW + (pj + rp);
-                    for (int z = 0; z < nz; ++z) acc += e[z * ep];
+                    acc += ge[(size_t)(pi + rp) * XW + (pj + rp)];
                 }
         }
     gb[q] = acc;
@@ -558,7 +581,7 @@ struct lpnp_tape {
     const float* guide = nullptr;  // caller's guide
     int blur_r = 0;
     float blur_sigma = 1.f;
-    DevBuf Dh, Th, X, V, U, AZ, xh, vh, uh, zh, g, wa, grad, ata, gs, dh[2], base, thp, Dhat, Gp, ge, gb, ctl,
+    DevBuf Dh, Th, X, V, U, AZ, xh, vh, uh, zh, g, wa, grad, ata, gs, dh[2], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
         part, m, mkey, sstar, mh, rho_part, h_part, m_part, scratch;
     float inv_m = 1.f;
     // pinned host words read back after the stream work: m, the scalar cotangents and
@@ -593,18 +616,18 @@ size_t pairs_b_smem(int T, int rs) {
 }
 
 // pair passes G and T: the planes of G and dh = (1/m) sum_{r ~ s} G_sr d_r K1_sr into dh[0]
-// (dh[1] holds the forward half in between)
+// (dh0 holds the forward half, one plane per offset chunk, in between)
 template <typename WT>
 cudaError_t pairs_gt(const lpnp_tape* tp, const void* planes, cudaStream_t st, double* m_part) {
     const int H = tp->H, W = tp->W, rs = tp->rs, N = tp->N;
     const size_t smem = pairs_g_smem(N, rs);
     const float* d = tp->Dh.as<float>() + (size_t)tp->T * H * W;
-    dim3 grid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
+    dim3 grid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH, kPairSplit);
     auto run = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, dim3(32, 8), smem, st>>>((const WT*)planes, H, W, rs, N, tp->AZ.as<float>(), d, tp->inv_m,
-                                              tp->Gp.as<float>(), tp->dh[1].as<float>(), m_part);
+                                              tp->Gp.as<float>(), tp->dh0.as<float>(), m_part);
         return cudaGetLastError();
     };
     cudaError_t e;
@@ -622,7 +645,7 @@ cudaError_t pairs_gt(const lpnp_tape* tp, const void* planes, cudaStream_t st, d
     count_launches(1);
     if (e != cudaSuccess) return e;
     adj_pairs_t_kernel<WT><<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, st>>>(
-        (const WT*)planes, tp->Gp.as<float>(), H, W, rs, d, tp->dh[1].as<float>(), tp->inv_m, tp->dh[0].as<float>());
+        (const WT*)planes, tp->Gp.as<float>(), H, W, rs, d, tp->dh0.as<float>(), tp->inv_m, tp->dh[0].as<float>());
     count_launches(1);
     return cudaGetLastError();
 }
@@ -633,7 +656,7 @@ cudaError_t pairs_b(const lpnp_tape* tp, const void* planes, cudaStream_t st) {
     const size_t smem = pairs_b_smem(tp->T, rs);
     cudaError_t e = cudaFuncSetAttribute(adj_pairs_b_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
+    dim3 grid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH, kPairSplit);
     adj_pairs_b_kernel<WT><<<grid, dim3(32, 8), smem, st>>>(
         (const WT*)planes, tp->Gp.as<float>(), H, W, rs, tp->T, tp->Dh.as<float>(), tp->thp.as<float>(), tp->inv_m,
         tp->c, 2.f * tp->c / tp->h, tp->sstar.as<int>(), tp->mh.as<double>(), tp->Dhat.as<float>(),
@@ -666,7 +689,7 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (!t) return;
     if (t->den) cudaStreamSynchronize(t->den->stream);
     DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
-                      &t->wa, &t->grad, &t->ata, &t->gs, &t->dh[0], &t->dh[1], &t->base, &t->thp, &t->Dhat,
+                      &t->wa, &t->grad, &t->ata, &t->gs, &t->dh[0], &t->dh[1], &t->dh0, &t->base, &t->thp, &t->Dhat,
                       &t->Gp, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->mkey, &t->sstar, &t->mh, &t->rho_part, &t->h_part,
                       &t->m_part, &t->scratch};
     for (DevBuf* b : bufs) b->release();
@@ -813,14 +836,16 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
     TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
     TAPE_CK(tp->thp.ensure(sizeof(float) * n * (T > 0 ? T : 1)));
+    TAPE_CK(tp->dh0.ensure(sizeof(float) * n * kPairSplit));
     TAPE_CK(tp->Dhat.ensure(sizeof(float) * (size_t)nh * H * plane_pitch(W)));
-    TAPE_CK(tp->Gp.ensure(sizeof(float) * (size_t)nh * H * plane_pitch(W)));
+    // the G planes, later the box sums E on the extended grid (pass B has then read G)
+    TAPE_CK(tp->Gp.ensure(sizeof(float) * (size_t)nh *
+                          std::max((size_t)H * plane_pitch(W), (size_t)(H + 2 * rp) * (W + 2 * rp))));
     const size_t ne = (size_t)(H + 2 * rp) * (W + 2 * rp);
-    const int nz = (nh + kGChunk - 1) / kGChunk;
-    TAPE_CK(tp->ge.ensure(sizeof(float) * ne * nz));
+    TAPE_CK(tp->ge.ensure(sizeof(float) * ne));
     const int nb = nblk(n);
     const dim3 pgrid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
-    const int npb = (int)(pgrid.x * pgrid.y);
+    const int npb = (int)(pgrid.x * pgrid.y) * kPairSplit;  // pair-pass blocks (with the offset chunks)
     TAPE_CK(tp->rho_part.ensure(sizeof(double) * nb));
     TAPE_CK(tp->h_part.ensure(sizeof(double) * npb));
     TAPE_CK(tp->m_part.ensure(sizeof(double) * npb));
@@ -907,19 +932,24 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
         case DSGNLM_F16: TAPE_CK(pairs_b<__half>(tp, den->planes.p, st)); break;
         default: TAPE_CK(pairs_b<__nv_bfloat16>(tp, den->planes.p, st)); break;
     }
-    // patch distances back to the guide: one plane of the extended grid per offset chunk
+    // patch distances back to the guide: box sums of the D-hat planes onto the extended
+    // grid (reusing the G planes' memory, which pass B has finished with), then the
+    // gather of every extended position
     {
-        const int GH = kGTH + 2 * rs, GW = kGTW + 2 * rs, EH = kGTH + rs, EW = kGTW + 2 * rs;
-        const int DH = EH + 2 * rp, DW = EW + 2 * rp;
-        const size_t smem = sizeof(float) * (size_t)(GH * GW + DH * DW + DH * EW + EH * EW);
-        TAPE_CK(cudaFuncSetAttribute(adj_guide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        dim3 grid((W + 2 * rp + kGTW - 1) / kGTW, (H + 2 * rp + kGTH - 1) / kGTH, nz);
-        adj_guide_kernel<<<grid, 256, smem, st>>>(tp->Dhat.as<float>(), tp->guide, H, W, rp, rs, tp->ge.as<float>());
-        count_launches(1);
+        float* E = tp->Gp.as<float>();
+        const int DW = kBT + 2 * rp;
+        const size_t bsmem = sizeof(float) * (size_t)(DW * DW + DW * kBT);
+        TAPE_CK(cudaFuncSetAttribute(adj_box_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+        adj_box_kernel<<<dim3((W + 2 * rp + kBT - 1) / kBT, (H + 2 * rp + kBT - 1) / kBT, nh), 256, bsmem, st>>>(
+            tp->Dhat.as<float>(), H, W, rp, E);
+        const size_t gsmem = sizeof(float) * (size_t)(8 + 2 * rs) * (32 + 2 * rs);
+        adj_guide_kernel<<<dim3((W + 2 * rp + 31) / 32, (H + 2 * rp + 7) / 8), dim3(32, 8), gsmem, st>>>(
+            E, tp->guide, H, W, rp, rs, tp->ge.as<float>());
+        count_launches(2);
         TAPE_CK(cudaGetLastError());
     }
     adj_fold_kernel<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, st>>>(
-        tp->ge.as<float>(), nz, tp->xh.as<float>(), tp->vh.as<float>(), tp->guide, H, W, rp, guide_bar);
+        tp->ge.as<float>(), tp->xh.as<float>(), tp->vh.as<float>(), tp->guide, H, W, rp, guide_bar);
     count_launches(1);
     TAPE_CK(cudaGetLastError());
     // dL/dy = sum_k mu A g_k = A gs

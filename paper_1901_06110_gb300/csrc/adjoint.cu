@@ -68,6 +68,21 @@ __global__ void adj_m_finish_kernel(const unsigned long long* __restrict__ key, 
     *s_out = (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
 }
 
+// Recording step of the forward: (x, v, u) of slot k into slot k + 1 (the solve then
+// advances slot k + 1 in place) and the gradient at x_{k-1}, which the previous
+// iteration's solve left in its handle, into the gradient record (gsrc null: none).
+__global__ void adj_record_kernel(int n, const float* __restrict__ x, const float* __restrict__ v,
+                                  const float* __restrict__ u, const float* __restrict__ gsrc,
+                                  float* __restrict__ x1, float* __restrict__ v1, float* __restrict__ u1,
+                                  float* __restrict__ gdst) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    x1[q] = x[q];
+    v1[q] = v[q];
+    u1[q] = u[q];
+    if (gsrc) gdst[q] = gsrc[q];
+}
+
 // a_k = vh - uh, z_k = x_{k+1} + u_k
 __global__ void adj_az_kernel(int n, const float* __restrict__ vh, const float* __restrict__ uh,
                               const float* __restrict__ x1, const float* __restrict__ u0, float* __restrict__ a,
@@ -581,7 +596,7 @@ struct lpnp_tape {
     const float* guide = nullptr;  // caller's guide
     int blur_r = 0;
     float blur_sigma = 1.f;
-    DevBuf Dh, Th, X, V, U, AZ, xh, vh, uh, zh, g, wa, grad, ata, gs, dh[2], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
+    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, wa, ata, gs, dh[2], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
         part, m, mkey, sstar, mh, rho_part, h_part, m_part, scratch;
     float inv_m = 1.f;
     // pinned host words read back after the stream work: m, the scalar cotangents and
@@ -688,8 +703,8 @@ dsgnlm_status lpnp_tape_create(lpnp_tape_t* out) {
 void lpnp_tape_destroy(lpnp_tape_t t) {
     if (!t) return;
     if (t->den) cudaStreamSynchronize(t->den->stream);
-    DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
-                      &t->wa, &t->grad, &t->ata, &t->gs, &t->dh[0], &t->dh[1], &t->dh0, &t->base, &t->thp, &t->Dhat,
+    DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->Gr, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
+                      &t->wa, &t->ata, &t->gs, &t->dh[0], &t->dh[1], &t->dh0, &t->base, &t->thp, &t->Dhat,
                       &t->Gp, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->mkey, &t->sstar, &t->mh, &t->rho_part, &t->h_part,
                       &t->m_part, &t->scratch};
     for (DevBuf* b : bufs) b->release();
@@ -703,10 +718,11 @@ namespace {
 
 // First half of the recording: K1 into the handle, the T balancing passes with every
 // d^p and t^p kept, m = max_s d_s t_s with its first maximiser, and the read-back of m
-// queued on the handle's stream.  Nothing here waits for the device.
+// queued on the handle's stream.  Nothing here waits for the device.  `share` images
+// run at once (the handle's offset split is sized for them).
 dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const float* guide, int H, int W,
                             int patch_r, int search_r, float bandwidth, int balance_passes, float alpha, float rho,
-                            int iters, float blur_sigma, int blur_r) {
+                            int iters, float blur_sigma, int blur_r, int share) {
     if (!tp || !den || !y || !guide) return DSGNLM_EINVAL;
     if (H < 2 || W < 2 || (H & 1) || (W & 1) || iters < 1 || iters > 256 || balance_passes < 0 ||
         balance_passes > 64 || !(rho > 0.f) || !(alpha >= 0.f) || blur_r < 0 || blur_r > 8 || !(blur_sigma > 0.f))
@@ -716,7 +732,9 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
     if (pairs_g_smem(iters, search_r) > 220 * 1024 || pairs_b_smem(balance_passes, search_r) > 220 * 1024)
         return DSGNLM_EINVAL;
     if (!tp->host) TAPE_CK(cudaMallocHost((void**)&tp->host, sizeof(lpnp_tape::Host)));
+    den->share = share;
     dsgnlm_status s = dsgnlm_build(den, guide, H, W, patch_r, search_r, bandwidth);
+    den->share = 1;
     if (s != DSGNLM_OK) return s;
     if (!den->fast) return DSGNLM_EINVAL;
     cudaStream_t st = den->stream;
@@ -745,6 +763,7 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
     TAPE_CK(tp->X.ensure(sizeof(float) * n * (N + 1)));
     TAPE_CK(tp->V.ensure(sizeof(float) * n * (N + 1)));
     TAPE_CK(tp->U.ensure(sizeof(float) * n * (N + 1)));
+    TAPE_CK(tp->Gr.ensure(sizeof(float) * n * N));
     TAPE_CK(tp->scratch.ensure(sizeof(float) * n));
     TAPE_CK(tp->ctl.ensure(sizeof(BalanceCtl)));
     TAPE_CK(tp->part.ensure(sizeof(float2) * (size_t)balance_combine_blocks(H, W)));
@@ -803,19 +822,25 @@ dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
     pr.constraint = tp->constraint;
     pr.alpha = tp->alpha;
     pr.den = den;
+    // each one-iteration solve leaves grad f(x_k), which its x-update used, in the
+    // handle's gradient buffer; it is recorded for the backward
+    const int nb = nblk(n);
     for (int k = 0; k < N; ++k) {
         float* x1 = tp->X.as<float>() + (size_t)(k + 1) * n;
         float* v1 = tp->V.as<float>() + (size_t)(k + 1) * n;
         float* u1 = tp->U.as<float>() + (size_t)(k + 1) * n;
-        TAPE_CK(cudaMemcpyAsync(x1, x1 - n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
-        TAPE_CK(cudaMemcpyAsync(v1, v1 - n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
-        TAPE_CK(cudaMemcpyAsync(u1, u1 - n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+        adj_record_kernel<<<nb, 256, 0, st>>>((int)n, x1 - n, v1 - n, u1 - n, k > 0 ? den->gbuf.as<float>() : nullptr,
+                                              x1, v1, u1, tp->Gr.as<float>() + (size_t)(k > 0 ? k - 1 : 0) * n);
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
         pr.x = x1;
         pr.v = v1;
         pr.u = u1;
         dsgnlm_status s = lpnp_solve(&pr, tp->rho, 1);
         if (s != DSGNLM_OK) return s;
     }
+    TAPE_CK(cudaMemcpyAsync(tp->Gr.as<float>() + (size_t)(N - 1) * n, den->gbuf.p, sizeof(float) * n,
+                            cudaMemcpyDeviceToDevice, st));
     TAPE_CK(cudaMemcpyAsync(x_out, tp->X.as<float>() + (size_t)N * n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     return DSGNLM_OK;
 }
@@ -831,7 +856,7 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     const int nh = num_half_offsets(rs);
     // the handle's planes must still hold this tape's K1
     if (den->H != H || den->W != W || den->rs != rs || den->nh != nh) return DSGNLM_EINVAL;
-    DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->wa, &tp->grad, &tp->ata,
+    DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->wa, &tp->ata,
                        &tp->gs, &tp->dh[0], &tp->dh[1], &tp->base, &tp->gb};
     for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
     TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
@@ -875,10 +900,10 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
         // W a (W symmetric)
         TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, dT, ak, den->err.as<unsigned>(), nullptr, st));
         TAPE_CK(launch_tma_apply_finish(den->plan, H, W, rs, dT, tT, tp->inv_m, ak, tp->wa.as<float>(), st));
-        // grad f(x_k) for xbar_k
-        TAPE_CK(launch_sr_grad(xk, tp->y, H, W, tp->taps, tp->grad.as<float>(), st));
+        // xbar_k from the recorded grad f(x_k)
         adj_g_kernel<<<nb, 256, 0, st>>>((int)n, tp->wa.as<float>(), tp->uh.as<float>(), tp->xh.as<float>(), xk, vk, uk,
-                                         tp->grad.as<float>(), mu, alpha, rho, tp->constraint, tp->g.as<float>(),
+                                         tp->Gr.as<float>() + (size_t)k * n, mu, alpha, rho, tp->constraint,
+                                         tp->g.as<float>(),
                                          tp->zh.as<float>(), tp->rho_part.as<double>());
         count_launches(1);
         TAPE_CK(cudaGetLastError());
@@ -980,7 +1005,7 @@ dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y
                                     float rho, int iters, float blur_sigma, int blur_r, float* x_out) {
     if (!x_out) return DSGNLM_EINVAL;
     dsgnlm_status s = forward_begin(tp, den, y, guide, H, W, patch_r, search_r, bandwidth, balance_passes, alpha, rho,
-                                    iters, blur_sigma, blur_r);
+                                    iters, blur_sigma, blur_r, 1);
     return s == DSGNLM_OK ? forward_finish(tp, x_out) : s;
 }
 
@@ -999,7 +1024,7 @@ dsgnlm_status lpnp_unrolled_forward_batched(lpnp_tape_t* tapes, dsgnlm_t* dens, 
     std::vector<dsgnlm_status> st(count, DSGNLM_OK);
     HostPool::run(count, [&](int i) {
         st[i] = forward_begin(tapes[i], dens[i], y[i], guide[i], H, W, patch_r, search_r, bandwidth, balance_passes,
-                              alpha, rho, iters, blur_sigma, blur_r);
+                              alpha, rho, iters, blur_sigma, blur_r, count);
     });
     for (int i = 0; i < count; ++i)
         if (st[i] != DSGNLM_OK) return st[i];

@@ -171,8 +171,9 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
         pl.tiles_y = (H + tma_tile_h() - 1) / tma_tile_h();
         const int tiles = pl.tiles_x * pl.tiles_y;
         // about one CTA per resident slot (two per SM for FP32 weights, three for
-        // 16-bit weights): split the offsets when tiles are scarce
-        int slices = (tma_ctas_per_sm(h->dtype) * h->num_sms) / tiles;
+        // 16-bit weights): split the offsets when tiles are scarce, counting the tiles
+        // of the images that run beside this one
+        int slices = (tma_ctas_per_sm(h->dtype) * h->num_sms) / (tiles * (h->share > 1 ? h->share : 1));
         pl.splits = make_splits(search_r, slices < 1 ? 1 : slices);
         DSG_CK(h->tma_part.ensure(sizeof(float) * tma_region_floats(search_r) * (size_t)tiles * pl.splits.n));
         pl.partials = h->tma_part.as<float>();
@@ -729,6 +730,8 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             if (sym) DSG_CK(h->rlo.ensure(sizeof(float) * n / 4));
             if (iters > 1) DSG_CK(h->ensure_side());
         }
+        // the per-iteration residual partials are reduced only when the history is read
+        const int want_hist = p->resid_hist ? 1 : 0;
         EpilogueArgs ea{};
         ea.H = H;
         ea.W = W;
@@ -791,8 +794,8 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             // one per kernel, so the host's launch rate does not gap the GPU.  A single
             // iteration (a few kernels, often on fresh buffers) is launched directly.
             std::vector<unsigned char> key;
-            const int ints[12] = {H, W, iters, kind, (int)sym, h->dtype, h->rs, nblocks, p->constraint, p->K,
-                                  h->plan.tiles_x, h->plan.tiles_y};
+            const int ints[13] = {H, W, iters, kind, (int)sym, h->dtype, h->rs, nblocks, p->constraint, p->K,
+                                  h->plan.tiles_x, h->plan.tiles_y, want_hist};
             const float fls[6] = {mu, p->alpha, rho, h->inv_m, p->eta, p->spi_eps};
             const void* ptrs[18] = {xA, p->v, p->u, p->y, p->counts, h->z.p, h->gbuf.p, h->rlo.p, h->d_final,
                                     h->t_final, h->partials.p, h->hist.p, h->arrive.p, h->err.p, h->plan.partials,
@@ -816,7 +819,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
                     g_capturing = true;
                     cudaError_t e1 = first_update(h->cap_stream);
                     for (int it = 0; it < iters && e1 == cudaSuccess; ++it) e1 = iteration(it, h->cap_stream);
-                    if (e1 == cudaSuccess) e1 = launch_reduce_residuals(red, iters, nblocks, h->cap_stream);
+                    if (e1 == cudaSuccess && want_hist) e1 = launch_reduce_residuals(red, iters, nblocks, h->cap_stream);
                     g_capturing = false;
                     cudaGraph_t g = nullptr;
                     e = cudaStreamEndCapture(h->cap_stream, &g);
@@ -835,7 +838,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             if (h->s_exec) {
                 DSG_CK(cudaGraphLaunch(h->s_exec, h->stream));
                 const uint64_t grad = sr ? (sym ? 2 : 1) : 0;
-                count_launches((sr ? grad + 1 : 1) + 2 * (uint64_t)iters + grad * (uint64_t)(iters - 1) + 1);
+                count_launches((sr ? grad + 1 : 1) + 2 * (uint64_t)iters + grad * (uint64_t)(iters - 1) + want_hist);
                 ran = true;
             }
         }
@@ -851,7 +854,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
                 }
                 DSG_CK(iteration(it, h->stream));
             }
-            DSG_CK(launch_reduce_residuals(red, iters, nblocks, h->stream));
+            if (want_hist) DSG_CK(launch_reduce_residuals(red, iters, nblocks, h->stream));
         }
     } else {
         if (sr) DSG_CK(h->x2.ensure(n * sizeof(float)));

@@ -66,6 +66,9 @@ struct dsgnlm {
     int dtype = DSGNLM_F32;
     int H = 0, W = 0, Wp = 0, rp = 0, rs = 0, nh = 0;
     int num_sms = 0;
+    // images whose launches share the GPU with this handle's while it is built; the
+    // build splits the offsets over fewer slices when the others fill the SMs
+    int share = 1;
     // TMA stencil path
     bool fast = false;
     TmaPlan plan{};

@@ -92,8 +92,10 @@ def _explicit(fn, y, g, h, rho, xbar):
 
 def test_batched_matches_single_bit_for_bit(gpu_lib):
     """The batched calls (one stream per image) give every image's x_N and
-    cotangents exactly as the single-image calls; the scalar cotangents are the sums
-    of the per-image values.  Repeated calls reuse the pooled slots."""
+    cotangents exactly as the single-image calls where the offset split is the same
+    (at 32x48 every column offset is its own slice for one image and for three); the
+    scalar cotangents are the sums of the per-image values.  Repeated calls reuse the
+    pooled slots."""
     from paper_1901_06110_gb300.autograd import UnrollParams, UnrolledSR, unrolled_sr
     H, W, B = 32, 48, 3
     params = UnrollParams(patch_r=2, search_r=5, balance_passes=3, iters=6)
@@ -116,3 +118,33 @@ def test_batched_matches_single_bit_for_bit(gpu_lib):
     again = _explicit(single, ys[1], gs[1], h, rho, xbars[1])
     for a, b_ in zip(again, singles[1]):
         assert np.array_equal(a, b_)
+
+
+def test_batched_split_for_the_batch(gpu_lib):
+    """At 256^2 the batch of four sizes each handle's offset split for four images at
+    once (fewer slices than one image alone), so W's partial sums are added in another
+    order: the results agree with the single-image calls to FP32 rounding and are
+    bitwise repeatable."""
+    from paper_1901_06110_gb300.autograd import UnrollParams, UnrolledSR, unrolled_sr
+    H, W, B = 256, 256, 4
+    params = UnrollParams(patch_r=2, search_r=7, balance_passes=4, iters=10)
+    cases = [_case(H, W, 40 + b) for b in range(B)]
+    ys = [cuda(inst["y"]) for _, inst, _ in cases]
+    gs = [cuda(guide) for _, _, guide in cases]
+    xbars = [cuda(np.random.default_rng(50 + b).standard_normal((H, W)).astype(np.float32)) for b in range(B)]
+    h, rho = 0.1, 1.0
+    single = lambda y, g, ht, rt: UnrolledSR.apply(y, g, ht, rt, params)
+    singles = [_explicit(single, ys[b], gs[b], h, rho, xbars[b]) for b in range(B)]
+    batched = lambda y, g, ht, rt: unrolled_sr(y, g, ht, rt, params)
+    runs = [_explicit(batched, torch.stack(ys), torch.stack(gs), h, rho, torch.stack(xbars)) for _ in range(2)]
+    for a, b_ in zip(runs[0], runs[1]):
+        assert np.array_equal(a, b_)
+    xb, gyb, ggb, hb, rb = runs[0]
+    for b in range(B):
+        assert rel_l2(xb[b], singles[b][0]) <= 1e-5
+        assert rel_l2(gyb[b], singles[b][1]) <= 1e-5
+        assert rel_l2(ggb[b], singles[b][2]) <= 1e-5
+    hs = sum(s[3] for s in singles)
+    rs_ = sum(s[4] for s in singles)
+    assert abs(hb - hs) <= 1e-5 * abs(hs)
+    assert abs(rb - rs_) <= 1e-5 * abs(rs_)

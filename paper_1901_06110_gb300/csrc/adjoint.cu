@@ -5,16 +5,21 @@
 //   K1 from the guide with bandwidth h (Eq. NLM, S1), stored as half-window planes;
 //   T balancing passes d^{p+1} = sqrt(d^p / t^p), t^p = K1 d^p, from d^0 = 1 (Eq. S2);
 //   m = max_s d_s t_s with t = K1 d (first maximiser s*), W from Eq. S3;
-//   N iterations of Algorithm 1 from x = v = clip(guide), u = 0, recording (x, v, u).
+//   N iterations of Algorithm 1 from x = v = clip(guide), u = 0, recording (x, v, u)
+//   and the gradient grad f(x_k) each x-update used.
 //
 // Backward, for the cotangent of x_N:
 //   iteration k (reverse): a = vh - uh, zh = W a + uh (W is symmetric),
 //     g = Pi_C'(xbar_k) (xh + zh),  xh <- mu (alpha g - A^T A g),  vh <- mu rho g,
-//     uh <- zh - mu rho g,  yh += mu A g,  rhoh += sum g mu ((v_k - u_k) - xbar_k);
+//     uh <- zh - mu rho g,  yh += mu A g (summed as A applied to sum mu g),
+//     rhoh += sum g mu ((v_k - u_k) - xbar_k);
 //   W depends on the pair weights w_sr = d_s d_r K1_sr / m (the diagonal closes the
-//   rows), and dL/dw_sr = G_sr = sum_k (a_k(s) - a_k(r)) (z_k(r) - z_k(s)), z_k = x_{k+1} + u_k;
-//   then through m, the T balancing passes, K1 = Lambda exp(-D c), c = 1 / (2 N_p^2 h^2),
-//   the patch distances D = box-sum of (g(p) - g(p + o))^2 and the reflection of the guide.
+//   rows), and dL/dw_sr = G_sr = sum_k (a_k(s) - a_k(r)) (z_k(r) - z_k(s)), z_k = x_{k+1} + u_k,
+//   computed once per half-window pair into planes (pair pass G);
+//   then through m, the T balancing passes, K1 = Lambda exp(-D c), c = 1 / (2 N_p^2 h^2)
+//   (pair pass B), the patch distances D = box-sum of (g(p) - g(p + o))^2 and the
+//   reflection of the guide.
+// Every reduction has a fixed order, so results are bitwise repeatable.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -93,17 +98,26 @@ __global__ void adj_az_kernel(int n, const float* __restrict__ vh, const float* 
     z[q] = x1[q] + u0[q];
 }
 
-// zh = W a + uh; g = Pi_C'(xbar_k) (xh + zh); per-block partial of sum g mu ((v - u) - xbar)
-__global__ void __launch_bounds__(256) adj_g_kernel(int n, const float* __restrict__ wa, const float* __restrict__ uh,
-                                                    const float* __restrict__ xh, const float* __restrict__ xk,
-                                                    const float* __restrict__ vk, const float* __restrict__ uk,
-                                                    const float* __restrict__ gradk, float mu, float alpha,
-                                                    float rho, int constraint, float* __restrict__ g,
-                                                    float* __restrict__ zh, double* __restrict__ rho_part) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+// W a finished from the phase-1 partial sums (W a = c_s a_s + (d_s / m) sum_r K1 d_r a_r,
+// the closure of Eq. S3), then zh = W a + uh, g = Pi_C'(xbar_k)(xh + zh) and the block's
+// partial of sum g mu ((v - u) - xbar).  Blocks of 32 x 8 pixels.
+__global__ void __launch_bounds__(256)
+adj_wa_g_kernel(Cover cv, int H, int W, const float* __restrict__ d, const float* __restrict__ t_fin, float inv_m,
+                const float* __restrict__ a, const float* __restrict__ uh, const float* __restrict__ xh,
+                const float* __restrict__ xk, const float* __restrict__ vk, const float* __restrict__ uk,
+                const float* __restrict__ gradk, float mu, float alpha, float rho, int constraint,
+                float* __restrict__ g, float* __restrict__ zh, double* __restrict__ rho_part) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i = blockIdx.y * 8 + threadIdx.y;
     double r = 0.0;
-    if (q < n) {
-        const float zz = wa[q] + uh[q];
+    if (i < H && j < W) {
+        const size_t q = (size_t)i * W + j;
+        const float A = gather_partials(cv, i, j);
+        const float ds = d[q];
+        const float dm = ds * inv_m;
+        const float cs = 1.f - dm * (t_fin[q] - ds);
+        const float wa = fmaf(dm, A, cs * a[q]);
+        const float zz = wa + uh[q];
         const float vu = vk[q] - uk[q];
         const float xb = mu * (alpha * xk[q] + rho * vu - gradk[q]);
         const float gg = proj_deriv(xb, constraint) * (xh[q] + zz);
@@ -112,13 +126,14 @@ __global__ void __launch_bounds__(256) adj_g_kernel(int n, const float* __restri
         r = (double)gg * (double)mu * ((double)vu - (double)xb);
     }
     r = warp_sum(r);
-    __shared__ double s[8];
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = r;
+    __shared__ double sr[8];
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    if ((t & 31) == 0) sr[t >> 5] = r;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (t == 0) {
         double acc = 0.0;
-        for (int w = 0; w < 8; ++w) acc += s[w];
-        rho_part[blockIdx.x] += acc;  // one slot per block, accumulated over iterations in a fixed order
+        for (int w = 0; w < 8; ++w) acc += sr[w];
+        rho_part[blockIdx.y * gridDim.x + blockIdx.x] += acc;  // fixed slot per block, fixed order over iterations
     }
 }
 
@@ -596,7 +611,7 @@ struct lpnp_tape {
     const float* guide = nullptr;  // caller's guide
     int blur_r = 0;
     float blur_sigma = 1.f;
-    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, wa, ata, gs, dh[2], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
+    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, ata, gs, dh[2], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
         part, m, mkey, sstar, mh, rho_part, h_part, m_part, scratch;
     float inv_m = 1.f;
     // pinned host words read back after the stream work: m, the scalar cotangents and
@@ -704,7 +719,7 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (!t) return;
     if (t->den) cudaStreamSynchronize(t->den->stream);
     DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->Gr, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
-                      &t->wa, &t->ata, &t->gs, &t->dh[0], &t->dh[1], &t->dh0, &t->base, &t->thp, &t->Dhat,
+                      &t->ata, &t->gs, &t->dh[0], &t->dh[1], &t->dh0, &t->base, &t->thp, &t->Dhat,
                       &t->Gp, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->mkey, &t->sstar, &t->mh, &t->rho_part, &t->h_part,
                       &t->m_part, &t->scratch};
     for (DevBuf* b : bufs) b->release();
@@ -856,7 +871,7 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     const int nh = num_half_offsets(rs);
     // the handle's planes must still hold this tape's K1
     if (den->H != H || den->W != W || den->rs != rs || den->nh != nh) return DSGNLM_EINVAL;
-    DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->wa, &tp->ata,
+    DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->ata,
                        &tp->gs, &tp->dh[0], &tp->dh[1], &tp->base, &tp->gb};
     for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
     TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
@@ -871,11 +886,14 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     const int nb = nblk(n);
     const dim3 pgrid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
     const int npb = (int)(pgrid.x * pgrid.y) * kPairSplit;  // pair-pass blocks (with the offset chunks)
-    TAPE_CK(tp->rho_part.ensure(sizeof(double) * nb));
+    const dim3 pgrid2((W + 31) / 32, (H + 7) / 8);           // per-pixel passes in 32 x 8 blocks
+    const int nrb = (int)(pgrid2.x * pgrid2.y);
+    const Cover cover{den->plan.partials, den->plan.tiles_x, den->plan.tiles_y, den->plan.splits.n, rs};
+    TAPE_CK(tp->rho_part.ensure(sizeof(double) * nrb));
     TAPE_CK(tp->h_part.ensure(sizeof(double) * npb));
     TAPE_CK(tp->m_part.ensure(sizeof(double) * npb));
     TAPE_CK(tp->mh.ensure(sizeof(double) * 3));
-    TAPE_CK(cudaMemsetAsync(tp->rho_part.p, 0, sizeof(double) * nb, st));
+    TAPE_CK(cudaMemsetAsync(tp->rho_part.p, 0, sizeof(double) * nrb, st));
     TAPE_CK(cudaMemsetAsync(tp->gs.p, 0, sizeof(float) * n, st));
     TAPE_CK(cudaMemsetAsync(tp->vh.p, 0, sizeof(float) * n, st));
     TAPE_CK(cudaMemsetAsync(tp->uh.p, 0, sizeof(float) * n, st));
@@ -897,14 +915,13 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
         const float* vk = tp->V.as<float>() + (size_t)k * n;
         const float* uk = tp->U.as<float>() + (size_t)k * n;
         float* ak = A + (size_t)k * n;
-        // W a (W symmetric)
+        // W a (W symmetric), finished with g and zh; xbar_k from the recorded grad f(x_k)
         TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, dT, ak, den->err.as<unsigned>(), nullptr, st));
-        TAPE_CK(launch_tma_apply_finish(den->plan, H, W, rs, dT, tT, tp->inv_m, ak, tp->wa.as<float>(), st));
-        // xbar_k from the recorded grad f(x_k)
-        adj_g_kernel<<<nb, 256, 0, st>>>((int)n, tp->wa.as<float>(), tp->uh.as<float>(), tp->xh.as<float>(), xk, vk, uk,
-                                         tp->Gr.as<float>() + (size_t)k * n, mu, alpha, rho, tp->constraint,
-                                         tp->g.as<float>(),
-                                         tp->zh.as<float>(), tp->rho_part.as<double>());
+        adj_wa_g_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(cover, H, W, dT, tT, tp->inv_m, ak, tp->uh.as<float>(),
+                                                        tp->xh.as<float>(), xk, vk, uk,
+                                                        tp->Gr.as<float>() + (size_t)k * n, mu, alpha, rho,
+                                                        tp->constraint, tp->g.as<float>(), tp->zh.as<float>(),
+                                                        tp->rho_part.as<double>());
         count_launches(1);
         TAPE_CK(cudaGetLastError());
         // A^T A g
@@ -979,7 +996,7 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     TAPE_CK(cudaGetLastError());
     // dL/dy = sum_k mu A g_k = A gs
     TAPE_CK(launch_sr_forward(tp->gs.as<float>(), H, W, tp->taps, nullptr, 0.f, y_bar, st));
-    adj_sum_kernel<<<1, 256, 0, st>>>(tp->rho_part.as<double>(), nb, mh + 1);
+    adj_sum_kernel<<<1, 256, 0, st>>>(tp->rho_part.as<double>(), nrb, mh + 1);
     adj_sum_kernel<<<1, 256, 0, st>>>(tp->h_part.as<double>(), npb, mh + 2);
     count_launches(2);
     TAPE_CK(cudaGetLastError());

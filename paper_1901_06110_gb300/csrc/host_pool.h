@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <condition_variable>
@@ -40,8 +41,15 @@ class HostPool {
     int count_ = 0, next_ = 0, pending_ = 0, device_ = 0;
     uint64_t gen_ = 0;
 
+    pid_t pid_ = getpid();
+
+    // A child made by fork() has none of the parent's threads: it gets a fresh pool
+    // (the parent's copy is abandoned, never destroyed).
     static HostPool& instance() {
-        static HostPool* p = new HostPool();  // never destroyed
+        static std::mutex mu;
+        static HostPool* p = nullptr;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!p || p->pid_ != getpid()) p = new HostPool();
         return *p;
     }
 

@@ -23,14 +23,17 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dsgnlm.h"
 #include "combine.cuh"
 #include "common.cuh"
+#include "grad.cuh"
 #include "handle.h"
 #include "host_pool.h"
 #include "internal.h"
+#include "xupdate.cuh"
 
 namespace dsg {
 
@@ -73,19 +76,66 @@ __global__ void adj_m_finish_kernel(const unsigned long long* __restrict__ key, 
     *s_out = (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
 }
 
-// Recording step of the forward: (x, v, u) of slot k into slot k + 1 (the solve then
-// advances slot k + 1 in place) and the gradient at x_{k-1}, which the previous
-// iteration's solve left in its handle, into the gradient record (gsrc null: none).
-__global__ void adj_record_kernel(int n, const float* __restrict__ x, const float* __restrict__ v,
-                                  const float* __restrict__ u, const float* __restrict__ gsrc,
-                                  float* __restrict__ x1, float* __restrict__ v1, float* __restrict__ u1,
-                                  float* __restrict__ gdst) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    x1[q] = x[q];
-    v1[q] = v[q];
-    u1[q] = u[q];
-    if (gsrc) gdst[q] = gsrc[q];
+// x-update of one recorded forward iteration (Algorithm 1, first two steps) from the
+// states of slot k into slot k + 1, on 32 x 32 tiles:
+//   g = A^T (A x_k - y) (recorded),  x_{k+1} = Pi_C(mu (alpha x_k + rho (v_k - u_k) - g)),
+//   z = x_{k+1} + u_k,  and v_k, u_k copied into slot k + 1 for the dual step to update.
+// x_k is read in halos and x_{k+1} written to another buffer, so tiles do not race.
+template <int R>
+__global__ void __launch_bounds__(256)
+adj_fwd_xupdate_kernel(const float* __restrict__ xk, const float* __restrict__ vk, const float* __restrict__ uk,
+                       const float* __restrict__ y, int H, int W, BlurTaps taps, float mu, float alpha, float rho,
+                       int constraint, float* __restrict__ grec, float* __restrict__ x1, float* __restrict__ v1,
+                       float* __restrict__ u1, float* __restrict__ z) {
+    __shared__ GradSmem<R> sm;
+    sr_grad_tile_apply<R>(sm, xk, y, H, W, taps, blockIdx.y * kGT, blockIdx.x * kGT,
+                          [&](int pi, int pj, float e, float o) {
+                              const size_t q = (size_t)pi * W + pj;
+                              const float g2[2] = {e, o};
+#pragma unroll
+                              for (int c = 0; c < 2; ++c) {
+                                  const float up = uk[q + c], vp = vk[q + c];
+                                  const float xn = project(mu * (alpha * xk[q + c] + rho * (vp - up) - g2[c]), constraint);
+                                  grec[q + c] = g2[c];
+                                  x1[q + c] = xn;
+                                  z[q + c] = xn + up;
+                                  v1[q + c] = vp;
+                                  u1[q + c] = up;
+                              }
+                          });
+}
+
+// Reverse iteration k, after g: ata = A^T A g on 32 x 32 tiles, then per pixel
+//   xh = mu (alpha g - ata), vh = mu rho g, uh = zh - mu rho g, gs += mu g (the
+//   observation's cotangent is A gs, A being linear), and when a_next is given the
+//   inputs of the earlier iteration: a_{k-1} = vh - uh, z_{k-1} = x_k + u_{k-1}.
+// g is only read, so the halo reads do not race with the writes.
+template <int R>
+__global__ void __launch_bounds__(256)
+adj_ata_update_kernel(const float* __restrict__ g, int H, int W, BlurTaps taps, const float* __restrict__ zh,
+                      float mu, float alpha, float rho, float* __restrict__ xh, float* __restrict__ vh,
+                      float* __restrict__ uh, float* __restrict__ gs, const float* __restrict__ xk,
+                      const float* __restrict__ uprev, float* __restrict__ a_next, float* __restrict__ z_next) {
+    __shared__ GradSmem<R> sm;
+    sr_grad_tile_apply<R>(sm, g, nullptr, H, W, taps, blockIdx.y * kGT, blockIdx.x * kGT,
+                          [&](int pi, int pj, float e, float o) {
+                              const size_t q = (size_t)pi * W + pj;
+                              const float ata[2] = {e, o};
+#pragma unroll
+                              for (int c = 0; c < 2; ++c) {
+                                  const float gg = g[q + c];
+                                  const float vv = mu * rho * gg;
+                                  const float uu = zh[q + c] - vv;
+                                  xh[q + c] = mu * (alpha * gg - ata[c]);
+                                  vh[q + c] = vv;
+                                  uh[q + c] = uu;
+                                  gs[q + c] += mu * gg;
+                                  if (a_next) {
+                                      a_next[q + c] = vv - uu;
+                                      z_next[q + c] = xk[q + c] + uprev[q + c];
+                                  }
+                              }
+                          });
 }
 
 // a_k = vh - uh, z_k = x_{k+1} + u_k
@@ -134,30 +184,6 @@ adj_wa_g_kernel(Cover cv, int H, int W, const float* __restrict__ d, const float
         double acc = 0.0;
         for (int w = 0; w < 8; ++w) acc += sr[w];
         rho_part[blockIdx.y * gridDim.x + blockIdx.x] += acc;  // fixed slot per block, fixed order over iterations
-    }
-}
-
-// xh = mu (alpha g - A^T A g), vh = mu rho g, uh = zh - mu rho g and gs += mu g (the
-// observation's cotangent is A gs, A being linear); when a_next is given, also the
-// inputs of the earlier iteration: a_{k-1} = vh - uh and z_{k-1} = x_k + u_{k-1}
-__global__ void adj_update_kernel(int n, const float* __restrict__ g, const float* __restrict__ ata,
-                                  const float* __restrict__ zh, float mu, float alpha, float rho,
-                                  float* __restrict__ xh, float* __restrict__ vh, float* __restrict__ uh,
-                                  float* __restrict__ gs, const float* __restrict__ xk,
-                                  const float* __restrict__ uprev, float* __restrict__ a_next,
-                                  float* __restrict__ z_next) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    const float gg = g[q];
-    const float vv = mu * rho * gg;
-    const float uu = zh[q] - vv;
-    xh[q] = mu * (alpha * gg - ata[q]);
-    vh[q] = vv;
-    uh[q] = uu;
-    gs[q] += mu * gg;
-    if (a_next) {
-        a_next[q] = vv - uu;
-        z_next[q] = xk[q] + uprev[q];
     }
 }
 
@@ -596,6 +622,23 @@ __global__ void adj_fold_kernel(const float* __restrict__ ge, const float* __res
 
 int nblk(size_t n) { return (int)((n + 255) / 256); }
 
+// f(std::integral_constant<int, R>{}) for the blur radius R = taps.r (0..8)
+template <typename F>
+cudaError_t by_blur_radius(int r, F&& f) {
+    switch (r) {
+        case 0: return f(std::integral_constant<int, 0>{});
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2: return f(std::integral_constant<int, 2>{});
+        case 3: return f(std::integral_constant<int, 3>{});
+        case 4: return f(std::integral_constant<int, 4>{});
+        case 5: return f(std::integral_constant<int, 5>{});
+        case 6: return f(std::integral_constant<int, 6>{});
+        case 7: return f(std::integral_constant<int, 7>{});
+        case 8: return f(std::integral_constant<int, 8>{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 }  // namespace dsg
@@ -611,7 +654,7 @@ struct lpnp_tape {
     const float* guide = nullptr;  // caller's guide
     int blur_r = 0;
     float blur_sigma = 1.f;
-    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, ata, gs, dh[2], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
+    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, gs, dh[2], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
         part, m, mkey, sstar, mh, rho_part, h_part, m_part, scratch;
     float inv_m = 1.f;
     // pinned host words read back after the stream work: m, the scalar cotangents and
@@ -719,7 +762,7 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (!t) return;
     if (t->den) cudaStreamSynchronize(t->den->stream);
     DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->Gr, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
-                      &t->ata, &t->gs, &t->dh[0], &t->dh[1], &t->dh0, &t->base, &t->thp, &t->Dhat,
+                      &t->gs, &t->dh[0], &t->dh[1], &t->dh0, &t->base, &t->thp, &t->Dhat,
                       &t->Gp, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->mkey, &t->sstar, &t->mh, &t->rho_part, &t->h_part,
                       &t->m_part, &t->scratch};
     for (DevBuf* b : bufs) b->release();
@@ -810,7 +853,8 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
 }
 
 // Second half: waits for m, fixes W on the handle and runs Algorithm 1 one iteration
-// at a time, every state recorded.
+// at a time, every state recorded (the same kernels and order of arithmetic as a
+// one-iteration lpnp_solve, with the x-update writing into the next slot).
 dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
     dsgnlm* den = tp->den;
     cudaStream_t st = den->stream;
@@ -827,35 +871,46 @@ dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
     den->iters = T;
     den->balanced = true;
     TAPE_CK(launch_init(tp->guide, (int)n, tp->X.as<float>(), tp->V.as<float>(), tp->U.as<float>(), st));
-    lpnp_problem pr{};
-    pr.kind = LPNP_SR2;
-    pr.H = tp->H;
-    pr.W = tp->W;
-    pr.y = tp->y;
-    pr.blur_sigma = tp->blur_sigma;
-    pr.blur_r = tp->blur_r;
-    pr.constraint = tp->constraint;
-    pr.alpha = tp->alpha;
-    pr.den = den;
-    // each one-iteration solve leaves grad f(x_k), which its x-update used, in the
-    // handle's gradient buffer; it is recorded for the backward
-    const int nb = nblk(n);
+    // Algorithm 1, one iteration at a time from slot k into slot k + 1: the x-update
+    // (recording grad f(x_k)), then W z and the dual step in place on slot k + 1
+    const int H = tp->H, W = tp->W;
+    const int nblocks = combine_xupdate_blocks(H, W);
+    TAPE_CK(den->partials.ensure(sizeof(double) * 2 * (size_t)nblocks));
+    TAPE_CK(den->z.ensure(sizeof(float) * n));
+    EpilogueArgs ea{};
+    ea.H = H;
+    ea.W = W;
+    ea.d = den->d_final;
+    ea.t = den->t_final;
+    ea.inv_m = den->inv_m;
+    ea.z = den->z.as<float>();
+    ea.taps = tp->taps;
+    ea.mu = tp->mu;
+    ea.alpha = tp->alpha;
+    ea.rho = tp->rho;
+    ea.constraint = tp->constraint;
+    ea.do_x = 0;
+    ea.partials = den->partials.as<double>();
+    const dim3 ggrid((W + kGT - 1) / kGT, (H + kGT - 1) / kGT);
     for (int k = 0; k < N; ++k) {
-        float* x1 = tp->X.as<float>() + (size_t)(k + 1) * n;
+        const float* xk = tp->X.as<float>() + (size_t)k * n;
+        const float* vk = tp->V.as<float>() + (size_t)k * n;
+        const float* uk = tp->U.as<float>() + (size_t)k * n;
         float* v1 = tp->V.as<float>() + (size_t)(k + 1) * n;
         float* u1 = tp->U.as<float>() + (size_t)(k + 1) * n;
-        adj_record_kernel<<<nb, 256, 0, st>>>((int)n, x1 - n, v1 - n, u1 - n, k > 0 ? den->gbuf.as<float>() : nullptr,
-                                              x1, v1, u1, tp->Gr.as<float>() + (size_t)(k > 0 ? k - 1 : 0) * n);
+        TAPE_CK(by_blur_radius(tp->taps.r, [&](auto rc) {
+            adj_fwd_xupdate_kernel<decltype(rc)::value><<<ggrid, 256, 0, st>>>(
+                xk, vk, uk, tp->y, H, W, tp->taps, tp->mu, tp->alpha, tp->rho, tp->constraint,
+                tp->Gr.as<float>() + (size_t)k * n, tp->X.as<float>() + (size_t)(k + 1) * n, v1, u1, ea.z);
+            return cudaGetLastError();
+        }));
         count_launches(1);
-        TAPE_CK(cudaGetLastError());
-        pr.x = x1;
-        pr.v = v1;
-        pr.u = u1;
-        dsgnlm_status s = lpnp_solve(&pr, tp->rho, 1);
-        if (s != DSGNLM_OK) return s;
+        TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, tp->rs, den->d_final, ea.z, den->err.as<unsigned>(),
+                                  nullptr, st));
+        ea.v = v1;
+        ea.u = u1;
+        TAPE_CK(launch_combine_update(0, den->plan, tp->rs, ea, st));
     }
-    TAPE_CK(cudaMemcpyAsync(tp->Gr.as<float>() + (size_t)(N - 1) * n, den->gbuf.p, sizeof(float) * n,
-                            cudaMemcpyDeviceToDevice, st));
     TAPE_CK(cudaMemcpyAsync(x_out, tp->X.as<float>() + (size_t)N * n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     return DSGNLM_OK;
 }
@@ -871,7 +926,7 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     const int nh = num_half_offsets(rs);
     // the handle's planes must still hold this tape's K1
     if (den->H != H || den->W != W || den->rs != rs || den->nh != nh) return DSGNLM_EINVAL;
-    DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->ata,
+    DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g,
                        &tp->gs, &tp->dh[0], &tp->dh[1], &tp->base, &tp->gb};
     for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
     TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
@@ -887,6 +942,7 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     const dim3 pgrid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
     const int npb = (int)(pgrid.x * pgrid.y) * kPairSplit;  // pair-pass blocks (with the offset chunks)
     const dim3 pgrid2((W + 31) / 32, (H + 7) / 8);           // per-pixel passes in 32 x 8 blocks
+    const dim3 ggrid((W + kGT - 1) / kGT, (H + kGT - 1) / kGT);  // A^T A tiles
     const int nrb = (int)(pgrid2.x * pgrid2.y);
     const Cover cover{den->plan.partials, den->plan.tiles_x, den->plan.tiles_y, den->plan.splits.n, rs};
     TAPE_CK(tp->rho_part.ensure(sizeof(double) * nrb));
@@ -924,15 +980,16 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
                                                         tp->rho_part.as<double>());
         count_launches(1);
         TAPE_CK(cudaGetLastError());
-        // A^T A g
-        TAPE_CK(launch_sr_grad(tp->g.as<float>(), nullptr, H, W, tp->taps, tp->ata.as<float>(), st));
+        // A^T A g and the updates of the cotangents, with the next (earlier) iteration's inputs
         const bool more = k > 0;
-        adj_update_kernel<<<nb, 256, 0, st>>>((int)n, tp->g.as<float>(), tp->ata.as<float>(), tp->zh.as<float>(), mu,
-                                              alpha, rho, tp->xh.as<float>(), tp->vh.as<float>(), tp->uh.as<float>(),
-                                              tp->gs.as<float>(), xk, more ? uk - n : nullptr,
-                                              more ? ak - n : nullptr, more ? Z + (size_t)(k - 1) * n : nullptr);
+        TAPE_CK(by_blur_radius(tp->taps.r, [&](auto rc) {
+            adj_ata_update_kernel<decltype(rc)::value><<<ggrid, 256, 0, st>>>(
+                tp->g.as<float>(), H, W, tp->taps, tp->zh.as<float>(), mu, alpha, rho, tp->xh.as<float>(),
+                tp->vh.as<float>(), tp->uh.as<float>(), tp->gs.as<float>(), xk, more ? uk - n : nullptr,
+                more ? ak - n : nullptr, more ? Z + (size_t)(k - 1) * n : nullptr);
+            return cudaGetLastError();
+        }));
         count_launches(1);
-        TAPE_CK(cudaGetLastError());
     }
     // pair passes G and T: the G planes, dh, partials of mh
     double* m_part = tp->m_part.as<double>();

@@ -34,11 +34,12 @@ struct GradSmem {
     int rows[GradDims<R>::S], cols[GradDims<R>::S], lrows[GradDims<R>::L], lcols[GradDims<R>::L];
 };
 
-// g on the 32 x 32 tile at (y0, x0); all 256 threads of the block call it
-template <int R>
-__device__ __forceinline__ void sr_grad_tile(GradSmem<R>& sm, const float* __restrict__ x, const float* __restrict__ y,
-                                             int H, int W, const BlurTaps& taps, float* __restrict__ g, int y0,
-                                             int x0) {
+// g on the 32 x 32 tile at (y0, x0), handed to epi(i, j, g(i, j), g(i, j + 1)) for each
+// even column j of the tile inside the image; all 256 threads of the block call it
+template <int R, typename Epi>
+__device__ __forceinline__ void sr_grad_tile_apply(GradSmem<R>& sm, const float* __restrict__ x,
+                                                   const float* __restrict__ y, int H, int W, const BlurTaps& taps,
+                                                   int y0, int x0, Epi&& epi) {
     using Dm = GradDims<R>;
     constexpr int G = Dm::G, L = Dm::L, S = Dm::S;
     auto& X = sm.X;
@@ -134,8 +135,18 @@ __device__ __forceinline__ void sr_grad_tile(GradSmem<R>& sm, const float* __res
                 o = fmaf(taps.t[b + R], V[py][cbase + ((b + 1) >> 1)], o);
         }
         const int pi = y0 + py, pj = x0 + 2 * k;
-        if (pi < H && pj < W) *reinterpret_cast<float2*>(g + (size_t)pi * W + pj) = make_float2(e, o);
+        if (pi < H && pj < W) epi(pi, pj, e, o);
     }
+}
+
+// g stored on the 32 x 32 tile at (y0, x0)
+template <int R>
+__device__ __forceinline__ void sr_grad_tile(GradSmem<R>& sm, const float* __restrict__ x, const float* __restrict__ y,
+                                             int H, int W, const BlurTaps& taps, float* __restrict__ g, int y0,
+                                             int x0) {
+    sr_grad_tile_apply<R>(sm, x, y, H, W, taps, y0, x0, [=](int pi, int pj, float e, float o) {
+        *reinterpret_cast<float2*>(g + (size_t)pi * W + pj) = make_float2(e, o);
+    });
 }
 
 }  // namespace dsg

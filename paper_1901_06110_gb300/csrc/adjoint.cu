@@ -405,14 +405,21 @@ __global__ void adj_sk_pre_kernel(int n, const float* __restrict__ dhn, const fl
     base[q] = w / dp[q];
 }
 
-// dh^p = base + K1 th = base + th + sum_{r != s} K1 th_r (phase-1 partial sums in cv)
-__global__ void __launch_bounds__(256) adj_sk_finish_kernel(Cover cv, int H, int W, const float* __restrict__ th,
-                                                            const float* __restrict__ base, float* __restrict__ dh) {
+// dh^p = base + K1 th^p = base + th^p + sum_{r != s} K1 th^p_r (phase-1 partial sums in
+// cv), the cotangent of d^p, and from it pass p - 1's th^{p-1} = -0.5 dh^p d^p / t^{p-1}
+// and base = 0.5 dh^p d^p / d^{p-1} (base rewritten in place)
+__global__ void __launch_bounds__(256)
+adj_sk_finish_pre_kernel(Cover cv, int H, int W, const float* __restrict__ th, float* __restrict__ base,
+                         const float* __restrict__ dp, const float* __restrict__ dq, const float* __restrict__ tq,
+                         float* __restrict__ th_prev) {
     const int j = blockIdx.x * 32 + threadIdx.x;
     const int i = blockIdx.y * 8 + threadIdx.y;
     if (i >= H || j >= W) return;
     const size_t s = (size_t)i * W + j;
-    dh[s] = base[s] + th[s] + gather_partials(cv, i, j);
+    const float dh = base[s] + th[s] + gather_partials(cv, i, j);
+    const float w = 0.5f * dh * dp[s];
+    th_prev[s] = -w / tq[s];
+    base[s] = w / dq[s];
 }
 
 // Pair pass B: the cotangent of every stored weight K1(s, s + o),
@@ -654,7 +661,7 @@ struct lpnp_tape {
     const float* guide = nullptr;  // caller's guide
     int blur_r = 0;
     float blur_sigma = 1.f;
-    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, gs, dh[2], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
+    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, gs, dh[1], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
         part, m, mkey, sstar, mh, rho_part, h_part, m_part, scratch;
     float inv_m = 1.f;
     // pinned host words read back after the stream work: m, the scalar cotangents and
@@ -762,7 +769,7 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (!t) return;
     if (t->den) cudaStreamSynchronize(t->den->stream);
     DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->Gr, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
-                      &t->gs, &t->dh[0], &t->dh[1], &t->dh0, &t->base, &t->thp, &t->Dhat,
+                      &t->gs, &t->dh[0], &t->dh0, &t->base, &t->thp, &t->Dhat,
                       &t->Gp, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->mkey, &t->sstar, &t->mh, &t->rho_part, &t->h_part,
                       &t->m_part, &t->scratch};
     for (DevBuf* b : bufs) b->release();
@@ -927,7 +934,7 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     // the handle's planes must still hold this tape's K1
     if (den->H != H || den->W != W || den->rs != rs || den->nh != nh) return DSGNLM_EINVAL;
     DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g,
-                       &tp->gs, &tp->dh[0], &tp->dh[1], &tp->base, &tp->gb};
+                       &tp->gs, &tp->dh[0], &tp->base, &tp->gb};
     for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
     TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
     TAPE_CK(tp->thp.ensure(sizeof(float) * n * (T > 0 ? T : 1)));
@@ -1007,23 +1014,26 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
         case DSGNLM_F16: TAPE_CK(mterms<__half>(tp, den->planes.p, st)); break;
         default: TAPE_CK(mterms<__nv_bfloat16>(tp, den->planes.p, st)); break;
     }
-    // balancing passes backwards
-    int cur = 0;
+    // balancing passes backwards: th^p from the cotangent of d^{p+1}, then K1 th^p; the
+    // finish of pass p forms the cotangent of d^p and at once th^{p-1} of the next pass
+    // (the cotangent of d^0 = 1 is not needed, so pass 0 has no finish)
+    if (T > 0) {
+        adj_sk_pre_kernel<<<nb, 256, 0, st>>>((int)n, tp->dh[0].as<float>(), tp->Dh.as<float>() + (size_t)T * n,
+                                              tp->Dh.as<float>() + (size_t)(T - 1) * n,
+                                              tp->Th.as<float>() + (size_t)(T - 1) * n,
+                                              tp->thp.as<float>() + (size_t)(T - 1) * n, tp->base.as<float>());
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+    }
     for (int p = T - 1; p >= 0; --p) {
-        const float* dn = tp->Dh.as<float>() + (size_t)(p + 1) * n;
-        const float* dp = tp->Dh.as<float>() + (size_t)p * n;
-        const float* tpp = tp->Th.as<float>() + (size_t)p * n;
         float* th = tp->thp.as<float>() + (size_t)p * n;
-        adj_sk_pre_kernel<<<nb, 256, 0, st>>>((int)n, tp->dh[cur].as<float>(), dn, dp, tpp, th, tp->base.as<float>());
-        count_launches(1);
-        TAPE_CK(cudaGetLastError());
         TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, th, nullptr, den->err.as<unsigned>(), nullptr, st));
-        adj_sk_finish_kernel<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, st>>>(
-            Cover{den->plan.partials, den->plan.tiles_x, den->plan.tiles_y, den->plan.splits.n, rs}, H, W, th,
-            tp->base.as<float>(), tp->dh[cur ^ 1].as<float>());
+        if (p == 0) break;
+        adj_sk_finish_pre_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(
+            cover, H, W, th, tp->base.as<float>(), tp->Dh.as<float>() + (size_t)p * n,
+            tp->Dh.as<float>() + (size_t)(p - 1) * n, tp->Th.as<float>() + (size_t)(p - 1) * n, th - n);
         count_launches(1);
         TAPE_CK(cudaGetLastError());
-        cur ^= 1;
     }
     // pair pass B: D-hat planes and dL/dh partials
     switch (den->dtype) {

@@ -33,7 +33,9 @@ def _gpu(inst, guide, h, rho, params):
     return loss.item(), host(y.grad), host(g.grad), ht.grad.item(), rt.grad.item(), host(x.detach())
 
 
-@pytest.mark.parametrize("H,W,rp,rs,T,N", [(16, 16, 2, 7, 4, 10), (16, 20, 1, 3, 2, 5)])
+@pytest.mark.parametrize("H,W,rp,rs,T,N", [(16, 16, 2, 7, 4, 10), (16, 20, 1, 3, 2, 5),
+                                            (16, 16, 1, 2, 0, 1),   # no balancing pass, one iteration
+                                            (12, 16, 2, 3, 1, 2)])  # one pass, H not a tile multiple
 def test_adjoint_matches_torch_autograd(gpu_lib, H, W, rp, rs, T, N):
     from paper_1901_06110_gb300.autograd import UnrollParams
     wl, inst, guide = _case(H, W, 9)
@@ -49,8 +51,11 @@ def test_adjoint_matches_torch_autograd(gpu_lib, H, W, rp, rs, T, N):
     assert abs(loss - ref.item()) <= 1e-5 * ref.item()
     assert rel_l2(gy, y.grad.numpy()) <= 1e-4
     assert rel_l2(gg, g.grad.numpy()) <= 1e-4
-    assert abs(gh - ht.grad.item()) <= 1e-4 * abs(ht.grad.item()) + 1e-9
-    assert abs(gr - rt.grad.item()) <= 1e-4 * abs(rt.grad.item()) + 1e-9
+    # with one iteration x_1 does not depend on W, so torch leaves h without a gradient
+    href = ht.grad.item() if ht.grad is not None else 0.0
+    rref = rt.grad.item() if rt.grad is not None else 0.0
+    assert abs(gh - href) <= 1e-4 * abs(href) + 1e-9
+    assert abs(gr - rref) <= 1e-4 * abs(rref) + 1e-9
 
 
 def test_adjoint_matches_finite_differences(gpu_lib):

@@ -232,9 +232,10 @@ dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad);
 /* Run `iters` iterations of Algorithm 1 with penalty rho > 0, mu = 1/(alpha + rho):
  *   x <- Pi_C(mu (alpha x + rho (v - u) - grad f(x)));  v <- W (x + u);  u <- u + x - v.
  * Uses p->den's handle stream.  Synchronises only if resid_hist is given.  On the
- * stencil path (and with profiling off) the kernel sequence is recorded once as a
- * CUDA graph on the handle and replayed while the problem's buffers, sizes and
- * parameters and the balanced W are unchanged; any change records it again. */
+ * stencil path (and with profiling off, iters > 1) the kernel sequence is recorded as
+ * a CUDA graph on the handle and replayed while the problem's buffers, sizes and
+ * parameters are unchanged; the handle keeps two such graphs.  After dsgnlm_balance
+ * the graphs read 1/m on the device, so another W of the same size replays them. */
 dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters);
 
 /* Standard PnP-ADMM for LPNP_SR2 (the comparison system of Sec. 4.1): the x-update
@@ -333,8 +334,8 @@ void lpnp_tape_destroy(lpnp_tape_t t);
  * earlier recording).  `den` must not be rebuilt before the backward.  The shared
  * memory of the backward limits (2 iters + 1)(16 + N_s)(32 + 2 N_s) and
  * (2 passes + 1)(16 + N_s)(32 + 2 N_s) floats to 220 KiB (EINVAL otherwise).
- * Synchronises the stream once (to read m); the solve graph is not used (one iteration
- * per recorded state). */
+ * Synchronises the stream once (to read m).  The iterations run their own kernels (the
+ * x-update of each writes the next recorded state), not lpnp_solve's graph. */
 dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tape, dsgnlm_t den, const float* y, const float* guide, int H,
                                     int W, int patch_r, int search_r, float bandwidth, int balance_passes,
                                     float alpha, float rho, int iters, float blur_sigma, int blur_r, float* x_out);

@@ -877,6 +877,7 @@ dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
     den->inv_m = tp->inv_m;
     den->iters = T;
     den->balanced = true;
+    den->inv_m_dev = false;  // this W's 1/m lives on the host only
     TAPE_CK(launch_init(tp->guide, (int)n, tp->X.as<float>(), tp->V.as<float>(), tp->U.as<float>(), st));
     // Algorithm 1, one iteration at a time from slot k into slot k + 1: the x-update
     // (recording grad f(x_k)), then W z and the dual step in place on slot k + 1

@@ -145,6 +145,7 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
     const size_t bytes = (size_t)nh * (size_t)H * (size_t)Wp * weight_elem_bytes(h->dtype);
     h->built = false;
     h->balanced = false;
+    h->inv_m_dev = false;
     h->fast = false;
     DSG_CK(h->planes.ensure(bytes));
     const double np = 2.0 * patch_r + 1.0;
@@ -274,6 +275,7 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     if (!(tol >= 0.0) || maxit < 0 || maxit > 1000000) return DSGNLM_EINVAL;
     const size_t n = (size_t)h->H * h->W;
     h->balanced = false;
+    h->inv_m_dev = false;
     DSG_CK(h->dbuf[0].ensure(n * sizeof(float)));
     DSG_CK(h->dbuf[1].ensure(n * sizeof(float)));
     if (h->fast) {
@@ -353,6 +355,7 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     h->d_final = h->dbuf[c.final_pass & 1].as<float>();
     h->m = m;
     h->inv_m = (float)(1.0 / m);
+    h->inv_m_dev = h->fast;  // the TMA path's control block holds the same 1/m
     h->iters = c.final_pass;
     h->resid = eps;
     h->balanced = true;
@@ -392,6 +395,7 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
         const int nbx = (W + 31) / 32, nby = (H + 15) / 16;  // the 16 x 32 epilogue blocks
         if (nbx * nby != balance_combine_blocks(H, W)) return DSGNLM_EINVAL;
         h->balanced = false;
+        h->inv_m_dev = false;
         DSG_CK(h->dbuf[0].ensure(n * sizeof(float)));
         DSG_CK(h->dbuf[1].ensure(n * sizeof(float)));
         DSG_CK(h->tbuf[0].ensure(n * sizeof(float)));
@@ -489,6 +493,7 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
         h->d_final = h->dbuf[c.final_pass & 1].as<float>();
         h->m = c.m;
         h->inv_m = (float)(1.0 / c.m);
+        h->inv_m_dev = true;
         h->iters = c.final_pass;
         h->resid = c.eps;
         h->balanced = true;
@@ -738,6 +743,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
         ea.d = h->d_final;
         ea.t = h->t_final;
         ea.inv_m = h->inv_m;
+        ea.inv_m_dev = h->inv_m_dev ? &h->ctl.as<BalanceCtl>()->inv_m : nullptr;
         ea.z = h->z.as<float>();
         ea.v = p->v;
         ea.u = p->u;
@@ -794,12 +800,14 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             // one per kernel, so the host's launch rate does not gap the GPU.  A single
             // iteration (a few kernels, often on fresh buffers) is launched directly.
             std::vector<unsigned char> key;
-            const int ints[13] = {H, W, iters, kind, (int)sym, h->dtype, h->rs, nblocks, p->constraint, p->K,
-                                  h->plan.tiles_x, h->plan.tiles_y, want_hist};
-            const float fls[6] = {mu, p->alpha, rho, h->inv_m, p->eta, p->spi_eps};
-            const void* ptrs[18] = {xA, p->v, p->u, p->y, p->counts, h->z.p, h->gbuf.p, h->rlo.p, h->d_final,
+            // with 1/m read on the device, a new image of the same size (another m)
+            // replays the same graph
+            const int ints[14] = {H, W, iters, kind, (int)sym, h->dtype, h->rs, nblocks, p->constraint, p->K,
+                                  h->plan.tiles_x, h->plan.tiles_y, want_hist, (int)h->inv_m_dev};
+            const float fls[6] = {mu, p->alpha, rho, h->inv_m_dev ? 0.f : h->inv_m, p->eta, p->spi_eps};
+            const void* ptrs[19] = {xA, p->v, p->u, p->y, p->counts, h->z.p, h->gbuf.p, h->rlo.p, h->d_final,
                                     h->t_final, h->partials.p, h->hist.p, h->arrive.p, h->err.p, h->plan.partials,
-                                    h->side, h->ev_fork, h->ev_join};
+                                    h->side, h->ev_fork, h->ev_join, h->ctl.p};
             key_put(key, ints);
             key_put(key, fls);
             key_put(key, ptrs);
@@ -807,12 +815,17 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             key_put(key, h->plan.splits);
             key.insert(key.end(), h->plan.tmap, h->plan.tmap + 128);
             cudaError_t e = cudaSuccess;
-            if (!h->s_exec || key != h->s_key) {
-                if (h->s_exec) cudaGraphExecDestroy(h->s_exec);
-                if (h->s_graph) cudaGraphDestroy(h->s_graph);
-                h->s_exec = nullptr;
-                h->s_graph = nullptr;
-                h->s_key.clear();
+            int slot = -1;
+            for (int i = 0; i < dsgnlm::kSolveGraphs; ++i)
+                if (h->s_exec[i] && h->s_key[i] == key) slot = i;
+            if (slot < 0) {
+                // record into the entry not used last
+                slot = (h->s_last + 1) % dsgnlm::kSolveGraphs;
+                if (h->s_exec[slot]) cudaGraphExecDestroy(h->s_exec[slot]);
+                if (h->s_graph[slot]) cudaGraphDestroy(h->s_graph[slot]);
+                h->s_exec[slot] = nullptr;
+                h->s_graph[slot] = nullptr;
+                h->s_key[slot].clear();
                 if (!h->cap_stream) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
                 if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed);
                 if (e == cudaSuccess) {
@@ -824,19 +837,20 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
                     cudaGraph_t g = nullptr;
                     e = cudaStreamEndCapture(h->cap_stream, &g);
                     if (e == cudaSuccess) e = e1;
-                    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->s_exec, g, 0);
+                    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->s_exec[slot], g, 0);
                     if (e == cudaSuccess) {
-                        h->s_graph = g;
-                        h->s_key = key;
+                        h->s_graph[slot] = g;
+                        h->s_key[slot] = key;
                     } else {
                         if (g) cudaGraphDestroy(g);
-                        h->s_exec = nullptr;
+                        h->s_exec[slot] = nullptr;
                         (void)cudaGetLastError();
                     }
                 }
             }
-            if (h->s_exec) {
-                DSG_CK(cudaGraphLaunch(h->s_exec, h->stream));
+            if (h->s_exec[slot]) {
+                h->s_last = slot;
+                DSG_CK(cudaGraphLaunch(h->s_exec[slot], h->stream));
                 const uint64_t grad = sr ? (sym ? 2 : 1) : 0;
                 count_launches((sr ? grad + 1 : 1) + 2 * (uint64_t)iters + grad * (uint64_t)(iters - 1) + want_hist);
                 ran = true;

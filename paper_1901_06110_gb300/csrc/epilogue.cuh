@@ -50,6 +50,7 @@ __device__ __forceinline__ void balance_decide(BalanceCtl* ctl, float e, float m
     const double ed = (double)e;
     ctl->eps = ed;
     ctl->m = (double)m;
+    ctl->inv_m = (float)(1.0 / (double)m);
     int done = 0, status = 0;
     if (ed <= ctl->tol) {
         done = 1;
@@ -203,6 +204,7 @@ template <int KIND, int SL = 0>  // KIND 0 super-resolution, 1 single-photon; SL
 __device__ __forceinline__ void combine_update_body(const Cover& cv, const EpilogueArgs& a, int do_x, int y0, int x0,
                                                     double* partials) {
     const int H = a.H, W = a.W;
+    const float inv_m = a.inv_m_dev ? __ldg(a.inv_m_dev) : a.inv_m;
     const TileCover tc = tile_cover(cv, y0, x0);
     const int pj = x0 + threadIdx.x;
     const int lj = pj - (x0 / kTmaTW) * kTmaTW;
@@ -240,7 +242,7 @@ __device__ __forceinline__ void combine_update_body(const Cover& cv, const Epilo
         if (pi >= H || pj >= W) continue;
         const size_t q = (size_t)pi * W + pj;
         // v = W z with z = x + u: c_s z_s + (d_s / m) sum_{r != s} K1 d_r z_r
-        const float dm = ds[r] * a.inv_m;
+        const float dm = ds[r] * inv_m;
         const float cs = 1.f - dm * (ts[r] - ds[r]);
         const float vn = fmaf(dm, A[r], cs * zs[r]);
         const float un = zs[r] - vn;  // u + x - v

@@ -104,10 +104,17 @@ struct dsgnlm {
     cudaGraph_t b_graph = nullptr;
     cudaGraphExec_t b_exec = nullptr;
     std::vector<unsigned char> b_key;
-    // the single-image solve's sequence as a CUDA graph, with the values it was recorded for
-    cudaGraph_t s_graph = nullptr;
-    cudaGraphExec_t s_exec = nullptr;
-    std::vector<unsigned char> s_key;
+    // the single-image solve's sequence as CUDA graphs, with the values each was
+    // recorded for: two entries, since the balanced scaling alternates between two
+    // buffers with the parity of the pass count; s_last is the most recent entry
+    static constexpr int kSolveGraphs = 2;
+    cudaGraph_t s_graph[kSolveGraphs] = {};
+    cudaGraphExec_t s_exec[kSolveGraphs] = {};
+    std::vector<unsigned char> s_key[kSolveGraphs];
+    int s_last = 0;
+    // the balance control block holds 1/m of the current W (set by the balances of
+    // this handle, cleared when W comes from elsewhere)
+    bool inv_m_dev = false;
     // optional per-kernel timing
     bool prof = false;
     ProfPool pools[dsg::kProfKinds];
@@ -145,11 +152,13 @@ struct dsgnlm {
         b_exec = nullptr;
         b_graph = nullptr;
         b_key.clear();
-        if (s_exec) cudaGraphExecDestroy(s_exec);
-        if (s_graph) cudaGraphDestroy(s_graph);
-        s_exec = nullptr;
-        s_graph = nullptr;
-        s_key.clear();
+        for (int i = 0; i < kSolveGraphs; ++i) {
+            if (s_exec[i]) cudaGraphExecDestroy(s_exec[i]);
+            if (s_graph[i]) cudaGraphDestroy(s_graph[i]);
+            s_exec[i] = nullptr;
+            s_graph[i] = nullptr;
+            s_key[i].clear();
+        }
     }
     void release_all() {
         release_graphs();

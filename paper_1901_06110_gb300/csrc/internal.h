@@ -29,6 +29,7 @@ struct BalanceCtl {
     int pass;        // current pass (TMA path: advanced on the device)
     double eps;      // TMA path: residual of the last decided pass
     double m;        // TMA path: max row sum of the last decided pass
+    float inv_m;     // TMA path: (float)(1 / m), written with m on the device
     unsigned arrive;  // TMA path: blocks of the current pass's epilogue that have finished
 };
 
@@ -187,6 +188,7 @@ struct EpilogueArgs {
     const float* d;
     const float* t;
     float inv_m;
+    const float* inv_m_dev;  // when set, 1/m is read here instead (written by the balance)
     float* z;          // in: x + u of this iteration; out: x + u of the next one
     float* v;
     float* u;

@@ -234,8 +234,9 @@ dsgnlm_status lpnp_gradient(const lpnp_problem* p, const float* x, float* grad);
  * Uses p->den's handle stream.  Synchronises only if resid_hist is given.  On the
  * stencil path (and with profiling off, iters > 1) the kernel sequence is recorded as
  * a CUDA graph on the handle and replayed while the problem's buffers, sizes and
- * parameters are unchanged; the handle keeps two such graphs.  After dsgnlm_balance
- * the graphs read 1/m on the device, so another W of the same size replays them. */
+ * parameters are unchanged; the handle keeps two such graphs.  The observation (or
+ * counts) is first copied into the handle, and after dsgnlm_balance the graphs read 1/m
+ * on the device, so another image and W of the same size replay them. */
 dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters);
 
 /* Standard PnP-ADMM for LPNP_SR2 (the comparison system of Sec. 4.1): the x-update

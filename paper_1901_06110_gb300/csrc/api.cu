@@ -717,11 +717,15 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
     const bool sr = p->kind == LPNP_SR2;
     const bool sym = sr && p->blur_boundary == LPNP_BC_SYMMETRIC;
     if (sym && !fast) return DSGNLM_EINVAL;  // the symmetric blur runs on the stencil path only
+    // the solve's view of the data term's input: the caller's buffer, or the handle's
+    // copy of it when the solve runs as a recorded graph
+    const float* yv = p->y;
+    const uint8_t* cv = p->counts;
     // A^T (A x - y) of the current x: one tiled kernel (periodic) or the residual on the
     // low-resolution grid and its adjoint (symmetric)
     auto sr_gradient = [&](const float* xs, float* g, cudaStream_t s) -> cudaError_t {
-        if (!sym) return launch_sr_grad(xs, p->y, H, W, taps, g, s);
-        cudaError_t e = launch_sr_forward_bc(1, xs, H, W, taps, p->y, -1.0f, h->rlo.as<float>(), s);
+        if (!sym) return launch_sr_grad(xs, yv, H, W, taps, g, s);
+        cudaError_t e = launch_sr_forward_bc(1, xs, H, W, taps, yv, -1.0f, h->rlo.as<float>(), s);
         if (e != cudaSuccess) return e;
         return launch_sr_adjoint_bc(1, h->rlo.as<float>(), H, W, taps, 0.f, nullptr, g, nullptr, s);
     };
@@ -737,6 +741,17 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
         }
         // the per-iteration residual partials are reduced only when the history is read
         const int want_hist = p->resid_hist ? 1 : 0;
+        const bool use_graph = !ad && !h->prof && iters > 1;
+        if (use_graph) {
+            const size_t obytes = sr ? sizeof(float) * (n / 4) : n;
+            DSG_CK(h->obs.ensure(obytes));
+            DSG_CK(cudaMemcpyAsync(h->obs.p, sr ? (const void*)p->y : (const void*)p->counts, obytes,
+                                   cudaMemcpyDeviceToDevice, h->stream));
+            if (sr)
+                yv = h->obs.as<float>();
+            else
+                cv = h->obs.as<uint8_t>();
+        }
         EpilogueArgs ea{};
         ea.H = H;
         ea.W = W;
@@ -747,10 +762,10 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
         ea.z = h->z.as<float>();
         ea.v = p->v;
         ea.u = p->u;
-        ea.y = p->y;
+        ea.y = yv;
         ea.g = h->gbuf.as<float>();
         ea.taps = taps;
-        ea.counts = p->counts;
+        ea.counts = cv;
         ea.K = p->K;
         ea.eta = p->eta;
         ea.eps = p->spi_eps;
@@ -764,7 +779,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
         // the x-update of iteration 0 (its gradient at the initial x, for SR)
         auto first_update = [&](cudaStream_t st) -> cudaError_t {
             if (!sr)
-                return launch_spi_xupdate(p->counts, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
+                return launch_spi_xupdate(cv, (int)n, p->K, p->eta, p->spi_eps, p->x, p->v, p->u,
                                           h->z.as<float>(), mu, p->alpha, rho, p->constraint, st);
             cudaError_t e = sr_gradient(xA, h->gbuf.as<float>(), st);
             if (e != cudaSuccess) return e;
@@ -794,7 +809,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             return e;
         };
         bool ran = false;
-        if (!ad && !h->prof && iters > 1) {
+        if (use_graph) {
             // The sequence is recorded once as a CUDA graph and replayed while everything
             // its kernel parameters bake in is unchanged: one launch per solve instead of
             // one per kernel, so the host's launch rate does not gap the GPU.  A single
@@ -805,7 +820,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             const int ints[14] = {H, W, iters, kind, (int)sym, h->dtype, h->rs, nblocks, p->constraint, p->K,
                                   h->plan.tiles_x, h->plan.tiles_y, want_hist, (int)h->inv_m_dev};
             const float fls[6] = {mu, p->alpha, rho, h->inv_m_dev ? 0.f : h->inv_m, p->eta, p->spi_eps};
-            const void* ptrs[19] = {xA, p->v, p->u, p->y, p->counts, h->z.p, h->gbuf.p, h->rlo.p, h->d_final,
+            const void* ptrs[19] = {xA, p->v, p->u, yv, cv, h->z.p, h->gbuf.p, h->rlo.p, h->d_final,
                                     h->t_final, h->partials.p, h->hist.p, h->arrive.p, h->err.p, h->plan.partials,
                                     h->side, h->ev_fork, h->ev_join, h->ctl.p};
             key_put(key, ints);

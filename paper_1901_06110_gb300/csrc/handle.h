@@ -90,6 +90,9 @@ struct dsgnlm {
     double resid = 0.0;
     // Algorithm 1 workspace
     DevBuf z, x2, rlo, partials, arrive, hist, gbuf;
+    // the observation (SR) or the counts (SPI) copied in before a recorded solve, so the
+    // solve graph does not depend on the caller's buffer
+    DevBuf obs;
     // conjugate-gradient workspace of the standard ADMM x-update
     DevBuf cg_r, cg_p, cg_q, cg_aty, cg_part, cg_scal;
     // side stream of the solve: the SR gradient of an iteration runs there while the
@@ -170,6 +173,7 @@ struct dsgnlm {
         if (ev_join) cudaEventDestroy(ev_join);
         ev_fork = ev_join = nullptr;
         gbuf.release();
+        obs.release();
         cg_r.release();
         cg_p.release();
         cg_q.release();

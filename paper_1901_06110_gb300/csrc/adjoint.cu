@@ -1091,7 +1091,9 @@ dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y
     if (!x_out) return DSGNLM_EINVAL;
     dsgnlm_status s = forward_begin(tp, den, y, guide, H, W, patch_r, search_r, bandwidth, balance_passes, alpha, rho,
                                     iters, blur_sigma, blur_r, 1);
-    return s == DSGNLM_OK ? forward_finish(tp, x_out) : s;
+    if (s == DSGNLM_OK) s = forward_finish(tp, x_out);
+    if (s != DSGNLM_OK && den) cudaStreamSynchronize(den->stream);  // nothing left running on the inputs
+    return s;
 }
 
 dsgnlm_status lpnp_unrolled_forward_batched(lpnp_tape_t* tapes, dsgnlm_t* dens, int count, const float* const* y,
@@ -1107,15 +1109,20 @@ dsgnlm_status lpnp_unrolled_forward_batched(lpnp_tape_t* tapes, dsgnlm_t* dens, 
     // every image's weights and balance are queued before the first wait for m; the
     // images are queued from the host pool's threads, each on its handle's stream
     std::vector<dsgnlm_status> st(count, DSGNLM_OK);
+    // on a failure, nothing of the batch is left running on the caller's buffers
+    auto fail = [&](dsgnlm_status s) {
+        for (int j = 0; j < count; ++j) cudaStreamSynchronize(dens[j]->stream);
+        return s;
+    };
     HostPool::run(count, [&](int i) {
         st[i] = forward_begin(tapes[i], dens[i], y[i], guide[i], H, W, patch_r, search_r, bandwidth, balance_passes,
                               alpha, rho, iters, blur_sigma, blur_r, count);
     });
     for (int i = 0; i < count; ++i)
-        if (st[i] != DSGNLM_OK) return st[i];
+        if (st[i] != DSGNLM_OK) return fail(st[i]);
     HostPool::run(count, [&](int i) { st[i] = forward_finish(tapes[i], x_out[i]); });
     for (int i = 0; i < count; ++i)
-        if (st[i] != DSGNLM_OK) return st[i];
+        if (st[i] != DSGNLM_OK) return fail(st[i]);
     return DSGNLM_OK;
 }
 

@@ -350,7 +350,9 @@ dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tape, dsgnlm_t den, const float*
 dsgnlm_status lpnp_backward(lpnp_tape_t tape, const float* x_bar, float* y_bar, float* guide_bar, double* h_bar,
                             double* rho_bar);
 
-/* Batched forms for `count` images of one size and one parameter set.  tapes[i] and
+/* Batched forms of the two calls above (Algorithm 1 unrolled, with Eq. S1-S3 for W;
+ * the paper has no derivatives) for `count` images of one size and one parameter
+ * set.  tapes[i] and
  * dens[i] must be distinct; each image runs on its handle's stream, so handles on
  * distinct streams overlap their images on the device.  y, guide, x_out (and x_bar,
  * y_bar, guide_bar) are host arrays of `count` device pointers with the layouts of the

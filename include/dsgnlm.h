@@ -352,20 +352,20 @@ dsgnlm_status lpnp_backward(lpnp_tape_t tape, const float* x_bar, float* y_bar, 
 
 /* Batched forms of the two calls above (Algorithm 1 unrolled, with Eq. S1-S3 for W;
  * the paper has no derivatives) for `count` images of one size and one parameter
- * set.  tapes[i] and
- * dens[i] must be distinct; each image runs on its handle's stream, so handles on
- * distinct streams overlap their images on the device.  y, guide, x_out (and x_bar,
- * y_bar, guide_bar) are host arrays of `count` device pointers with the layouts of the
- * single-image calls.  The images are queued from a pool of host threads, one image
- * per thread at a time.  The forward queues every image's weights, balance and m
- * before waiting for any m, then synchronises each stream once; the backward queues
- * every image's reverse sweep, then synchronises each stream.  h_bar and rho_bar
- * (host, optional) receive `count` per-image values.  Each handle's offset split
- * (the slices of phase 1) is sized for `count` images at once, so results equal the
- * single-image calls up to the order in which W's partial sums are added (bit for bit
- * where the split is the same), and repeated calls give identical results.  On an
- * error the status of the first failing image is returned and the tapes of the batch
- * hold no usable recording. */
+ * set.  tapes[i] and dens[i] must be distinct.  Each image runs on its handle's
+ * stream, so handles on distinct streams overlap their images on the device.  y,
+ * guide, x_out (and x_bar, y_bar, guide_bar) are host arrays of `count` device
+ * pointers with the layouts of the single-image calls.  The images are queued from a
+ * pool of host threads, one image per thread at a time.  The forward queues every
+ * image's weights, balance and m before waiting for any m, then synchronises each
+ * stream once; the backward queues every image's reverse sweep, then synchronises
+ * each stream.  h_bar and rho_bar (host, optional) receive `count` per-image values.
+ * Each handle's offset split (the slices of phase 1) is sized for `count` images at
+ * once, so results equal the single-image calls up to the order in which W's partial
+ * sums are added (bit for bit where the split is the same), and repeated calls give
+ * identical results.  On an error the batch's streams are drained, the status of the
+ * first failing image is returned and the tapes of the batch hold no usable
+ * recording. */
 dsgnlm_status lpnp_unrolled_forward_batched(lpnp_tape_t* tapes, dsgnlm_t* dens, int count, const float* const* y,
                                             const float* const* guide, int H, int W, int patch_r, int search_r,
                                             float bandwidth, int balance_passes, float alpha, float rho, int iters,

@@ -134,8 +134,27 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
                                      double* resid_out, int* status_out);
 
 /* Apply y = W x (third aggregation of Algorithm 2).
- * x, y  device, [H][W] FP32; y must not alias x.  Asynchronous. */
+ * x, y  device, [H][W] FP32; y must not alias x.  Asynchronous: a bounded device
+ * wait that gives up during the call is reported by the next dsgnlm_sync (or by
+ * the next balance or solve on the handle that reads the error word). */
 dsgnlm_status dsgnlm_apply(dsgnlm_t h, const float* x, float* y);
+
+/* Wait for the work queued on the handle's stream, then read and clear the handle's
+ * device error word.  Returns TIMEOUT if a bounded wait of a stencil kernel gave up
+ * since the word was last read (the outputs of that work are then invalid; the
+ * handle stays usable), OK otherwise, or a CUDA error.  (No counterpart in the
+ * paper: the asynchronous error report of this library.) */
+dsgnlm_status dsgnlm_sync(dsgnlm_t h);
+
+/* Test hook of the bounded waits (no counterpart in the paper).  In every phase-1
+ * stencil launch of this handle, a consumer thread waits at most `cycles` GPU
+ * clock cycles for a weight tile to land in shared memory; then the CTA sets the
+ * handle's error word, stops, lets its copies in flight land and returns, so no
+ * kernel waits without bound.  0 makes every consumer give up at its first wait
+ * (the timeout path, without a fault or a hang); a negative value restores the
+ * default of 4e9 cycles (about 2 s).  Releases the handle's recorded graphs when
+ * the value changes (synchronises the stream).  EINVAL above the default. */
+dsgnlm_status dsgnlm_set_wait_budget(dsgnlm_t h, long long cycles);
 
 /* Diagnostics for tests: copy the weight planes ([n_h][H][W], weight dtype) to the
  * device buffer dst; copy the final scaling d ([H][W] FP32) to the device buffer
@@ -157,14 +176,15 @@ int dsgnlm_num_offsets(dsgnlm_t h);
 dsgnlm_status lpnp_sr_observe(const float* x, const float* noise, int H, int W,
                               float blur_sigma, int blur_r, float* y, void* stream);
 
-/* Guide for super-resolution: 2x Keys cubic (a = -0.5) interpolation of y with
- * periodic wrap, low-resolution sample j at high-resolution 2j.
- * y device [h][w]; guide device [2h][2w]. */
 /* lpnp_sr_observe with the blur boundary `boundary` (LPNP_BC_PERIODIC or
  * LPNP_BC_SYMMETRIC; the symmetric blur needs H, W >= 2 blur_r). */
 dsgnlm_status lpnp_sr_observe_bc(const float* x, const float* noise, int H, int W, float blur_sigma, int blur_r,
                                  int boundary, float* y, void* stream);
 
+/* Guide for super-resolution: 2x Keys cubic (a = -0.5) interpolation of y with
+ * periodic wrap, low-resolution sample j at high-resolution 2j (the bicubic guide
+ * of the F-DSG-NLM variant, Sec. 4).  y device [h][w]; guide device [2h][2w].
+ * Asynchronous on `stream`.  EINVAL for null pointers or h, w < 1. */
 dsgnlm_status lpnp_sr_guide(const float* y, int h, int w, float* guide, void* stream);
 
 /* Single-photon measurement (Sec. 4.2): pixel i has K = k_side^2 sub-pixels; a
@@ -262,13 +282,16 @@ dsgnlm_status lpnp_solve_standard(const lpnp_problem* p, float rho, int iters, i
 dsgnlm_status lpnp_solve_adaptive(const lpnp_problem* p, float rho, int iters, int adapt_iters, int patch_r,
                                   int search_r, float bandwidth, double tol, int maxit);
 
-/* Allocation-free super-resolution gradient: grad = A^T (A x - y), the same
- * result as lpnp_gradient for a LPNP_SR2 problem, for callers that cannot
+/* Allocation-free super-resolution gradient: grad = A^T (A x - y) with the
+ * PERIODIC blur, the same result as lpnp_gradient for a LPNP_SR2 problem whose
+ * blur_boundary is LPNP_BC_PERIODIC (there is no symmetric-boundary form of this
+ * call; such a problem needs lpnp_gradient), for callers that cannot
  * allocate device memory when they need it (a plugin whose host framework owns
  * every device allocation, a real-time loop that forbids allocation after
  * start-up).  The paper has no counterpart: this is a deployment variant.
  *
- * x, grad device [H][W]; y device [H/2][W/2]; H, W even; blur as in lpnp_problem.
+ * x, grad device [H][W]; y device [H/2][W/2]; H, W even; blur_sigma, blur_r as in
+ * lpnp_problem, always with periodic wrap.
  * Its scratch, the low-resolution residual A x - y, lives in one static device
  * array of 1,048,576 floats (4 MiB) that every GPU loading the library keeps until
  * exit, so (H/2)(W/2) must not exceed 1,048,576 (e.g. 2048 x 2048); larger sizes
@@ -277,7 +300,10 @@ dsgnlm_status lpnp_solve_adaptive(const lpnp_problem* p, float rho, int iters, i
  * host threads) race and must be serialised.  Every call overwrites the part it
  * reads, so no state carries over between calls.  The first call on a device
  * resolves the array's address (this may load the library's module onto the
- * device) and should come before any stream capture on that device.
+ * device) and should come before any stream capture on that device.  The address
+ * is kept for the life of the process: do not use this call on a device after
+ * cudaDeviceReset or after its primary context was destroyed and created again
+ * (the module may then sit at another address).
  * Asynchronous on `stream`. */
 dsgnlm_status lpnp_sr_gradient_noalloc(const float* x, const float* y, int H, int W,
                                        float blur_sigma, int blur_r, float* grad, void* stream);

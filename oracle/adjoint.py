@@ -26,8 +26,15 @@ import numpy as np
 from . import dsgnlm, forward, lpnp
 
 
-def unrolled_loss(y, guide, h, rho, x_true, patch_r, search_r, T, N, alpha=1.0, psf=None):
-    """Loss of the unrolled solve (NumPy, FP64, sparse W)."""
+def unrolled_loss(y, guide, h, rho, x_true, patch_r, search_r, T, N, alpha=1.0, psf=None, trace=None):
+    """Loss of the unrolled solve (NumPy, FP64, sparse W).
+
+    ``trace``, if a dict, receives the branches the loss took at its non-smooth
+    points: "init" = sign(clip(guide) - guide) of the initial state, "argmax" =
+    the first row of diag(d) K1 diag(d) whose sum is m, and "clamp" = the branch
+    of Pi_C per pixel and iteration.  Two inputs with equal traces lie on one
+    smooth piece of the loss, where central differences converge to the
+    derivative (used to skip finite-difference points that straddle a kink)."""
     psf = forward.gaussian_psf(1.0, 4) if psf is None else psf
     guide = np.asarray(guide, np.float64)
     y = np.asarray(y, np.float64)
@@ -35,9 +42,21 @@ def unrolled_loss(y, guide, h, rho, x_true, patch_r, search_r, T, N, alpha=1.0, 
     d, _, _ = dsgnlm.sinkhorn(K1, 0.0, T)
     W, _ = dsgnlm.dsg_matrix(K1, d)
     x0, v0, u0 = lpnp.initial_state(guide)
+    clamps = [] if trace is not None else None
     x, _, _, _ = lpnp.lpnp_solve(lambda x: forward.sr_grad(x, y, psf), lambda z: dsgnlm.denoise(W, z),
-                                 x0, v0, u0, alpha, rho, N, lpnp.BOX01)
+                                 x0, v0, u0, alpha, rho, N, lpnp.BOX01, clamp_trace=clamps)
+    if trace is not None:
+        trace["init"] = np.sign(x0 - guide).astype(np.int8)
+        trace["argmax"] = int(np.argmax(d * (K1 @ d)))
+        trace["clamp"] = clamps
     return float(np.mean((x - np.asarray(x_true, np.float64)) ** 2))
+
+
+def same_branches(a: dict, b: dict) -> bool:
+    """True when two ``unrolled_loss`` traces took the same branch everywhere."""
+    return (a["argmax"] == b["argmax"] and np.array_equal(a["init"], b["init"])
+            and len(a["clamp"]) == len(b["clamp"])
+            and all(np.array_equal(p, q) for p, q in zip(a["clamp"], b["clamp"])))
 
 
 def fd_gradient(fn, x0, idx, eps):

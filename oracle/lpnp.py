@@ -64,9 +64,14 @@ def psnr(x: np.ndarray, ref: np.ndarray) -> float:
     return float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)
 
 
-def lpnp_solve(grad_f, denoise, x, v, u, alpha, rho, iters, constraint, x_true=None):
+def lpnp_solve(grad_f, denoise, x, v, u, alpha, rho, iters, constraint, x_true=None, clamp_trace=None):
     """Algorithm 1.  ``grad_f(x)`` and ``denoise(z)`` act on images.  Returns
-    (x, v, u, history) with history[k] = (primal, dual, psnr or None)."""
+    (x, v, u, history) with history[k] = (primal, dual, psnr or None).
+
+    ``clamp_trace``, if a list, receives per iteration sign(Pi_C(x) - x) of the
+    unprojected x-update: 0 where the projection is inactive, +1 / -1 where it
+    raised / lowered the pixel.  It records which branch of Pi_C each pixel took
+    and changes no arithmetic."""
     x = np.asarray(x, dtype=np.float64).copy()
     v = np.asarray(v, dtype=np.float64).copy()
     u = np.asarray(u, dtype=np.float64).copy()
@@ -74,7 +79,10 @@ def lpnp_solve(grad_f, denoise, x, v, u, alpha, rho, iters, constraint, x_true=N
     hist = []
     for _ in range(iters):
         x = mu * (alpha * x + rho * (v - u) - grad_f(x))
-        x = project(x, constraint)
+        xp = project(x, constraint)
+        if clamp_trace is not None:
+            clamp_trace.append(np.sign(xp - x).astype(np.int8))
+        x = xp
         v_prev = v
         v = denoise(x + u)
         u = u + (x - v)

@@ -40,6 +40,8 @@ SIGNATURES = {
     "dsgnlm_balance_batched": (c_int, [ctypes.POINTER(c_void_p), c_int, c_double, c_int, c_int,
                                        ctypes.POINTER(c_int), ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     "dsgnlm_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "dsgnlm_sync": (c_int, [c_void_p]),
+    "dsgnlm_set_wait_budget": (c_int, [c_void_p, ctypes.c_longlong]),
     "dsgnlm_copy_weights": (c_int, [c_void_p, c_void_p]),
     "dsgnlm_copy_scaling": (c_int, [c_void_p, c_void_p, ctypes.POINTER(c_double)]),
     "dsgnlm_num_offsets": (c_int, [c_void_p]),

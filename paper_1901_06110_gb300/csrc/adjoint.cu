@@ -843,7 +843,7 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
         float* dp = tp->Dh.as<float>() + (size_t)p * n;
         float* dn = p < T ? tp->Dh.as<float>() + (size_t)(p + 1) * n : tp->scratch.as<float>();
         TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, search_r, dp, nullptr, den->err.as<unsigned>(),
-                                  &ctl->done, st));
+                                  &ctl->done, st, den->wait_budget));
         TAPE_CK(launch_balance_epilogue(den->plan, H, W, search_r, dp, dn, tp->Th.as<float>() + (size_t)p * n,
                                         tp->part.as<float2>(), ctl, 0, cudaGraphConditionalHandle{}, 0, st));
     }
@@ -914,7 +914,7 @@ dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
         }));
         count_launches(1);
         TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, tp->rs, den->d_final, ea.z, den->err.as<unsigned>(),
-                                  nullptr, st));
+                                  nullptr, st, den->wait_budget));
         ea.v = v1;
         ea.u = u1;
         TAPE_CK(launch_combine_update(0, den->plan, tp->rs, ea, st));
@@ -980,7 +980,7 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
         const float* uk = tp->U.as<float>() + (size_t)k * n;
         float* ak = A + (size_t)k * n;
         // W a (W symmetric), finished with g and zh; xbar_k from the recorded grad f(x_k)
-        TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, dT, ak, den->err.as<unsigned>(), nullptr, st));
+        TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, dT, ak, den->err.as<unsigned>(), nullptr, st, den->wait_budget));
         adj_wa_g_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(cover, H, W, dT, tT, tp->inv_m, ak, tp->uh.as<float>(),
                                                         tp->xh.as<float>(), xk, vk, uk,
                                                         tp->Gr.as<float>() + (size_t)k * n, mu, alpha, rho,
@@ -1028,7 +1028,7 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     }
     for (int p = T - 1; p >= 0; --p) {
         float* th = tp->thp.as<float>() + (size_t)p * n;
-        TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, th, nullptr, den->err.as<unsigned>(), nullptr, st));
+        TAPE_CK(launch_tma_gather(den->dtype, den->plan, H, W, rs, th, nullptr, den->err.as<unsigned>(), nullptr, st, den->wait_budget));
         if (p == 0) break;
         adj_sk_finish_pre_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(
             cover, H, W, th, tp->base.as<float>(), tp->Dh.as<float>() + (size_t)p * n,
@@ -1075,7 +1075,10 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
 
 dsgnlm_status backward_finish(lpnp_tape* tp, double* h_bar, double* rho_bar) {
     TAPE_CK(cudaStreamSynchronize(tp->den->stream));
-    if (tp->host->err) return DSGNLM_TIMEOUT;
+    if (tp->host->err) {
+        TAPE_CK(cudaMemsetAsync(tp->den->err.p, 0, sizeof(unsigned), tp->den->stream));
+        return DSGNLM_TIMEOUT;
+    }
     if (rho_bar) *rho_bar = tp->host->hs[1];
     if (h_bar) *h_bar = tp->host->hs[2];
     return DSGNLM_OK;

@@ -190,6 +190,14 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
 
 namespace {
 
+// A phase-1 wait gave up during the call: clear the error word (so that the next
+// call starts clean) and report it.
+dsgnlm_status wait_timeout(dsgnlm* h, cudaStream_t st) {
+    const cudaError_t e = cudaMemsetAsync(h->err.p, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) cudaStreamSynchronize(st);
+    return DSGNLM_TIMEOUT;
+}
+
 // One balancing pass of the TMA path: phase-1 gather of K1 d, then the epilogue
 // (next d, t, residual maxima and, in its last block, the decision).  `parity`
 // selects the d and t buffers.
@@ -198,7 +206,7 @@ cudaError_t balance_pass(dsgnlm* h, int parity, cudaStream_t st, cudaGraphCondit
     float* d_in = h->dbuf[parity].as<float>();
     float* d_out = h->dbuf[parity ^ 1].as<float>();
     cudaError_t e = launch_tma_gather(h->dtype, h->plan, h->H, h->W, h->rs, d_in, nullptr, h->err.as<unsigned>(),
-                                      &ctl->done, st);
+                                      &ctl->done, st, h->wait_budget);
     if (e != cudaSuccess) return e;
     return launch_balance_epilogue(h->plan, h->H, h->W, h->rs, d_in, d_out, h->tbuf[parity].as<float>(),
                                    h->bal_part.as<float2>(), ctl, 1, cond, use_cond, st);
@@ -341,7 +349,7 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     if (h->fast) {
         unsigned errv = 0;
         DSG_CK(cudaMemcpy(&errv, h->err.p, sizeof errv, cudaMemcpyDeviceToHost));
-        if (errv) return DSGNLM_TIMEOUT;
+        if (errv) return wait_timeout(h, h->stream);
         h->t_final = h->tbuf[c.final_pass & 1].as<float>();
     } else {
         PassStat ps{};
@@ -484,7 +492,7 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
     unsigned errv = 0;
     DSG_CK(cudaMemcpyAsync(&errv, lead->err.p, sizeof errv, cudaMemcpyDeviceToHost, st));
     DSG_CK(cudaStreamSynchronize(st));
-    if (errv) return DSGNLM_TIMEOUT;
+    if (errv) return wait_timeout(lead, st);
     for (int i = 0; i < count; ++i) {
         const BalanceCtl& c = c0[i];
         if (!c.done || c.final_pass < 0) return DSGNLM_ECUDA;  // cannot happen: pass maxit decides
@@ -512,7 +520,7 @@ dsgnlm_status dsgnlm_apply(dsgnlm_t h, const float* x, float* y) {
     DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
         if (h->fast) {
             cudaError_t e = launch_tma_gather(h->dtype, h->plan, h->H, h->W, h->rs, h->d_final, x,
-                                              h->err.as<unsigned>(), nullptr, h->stream);
+                                              h->err.as<unsigned>(), nullptr, h->stream, h->wait_budget);
             if (e != cudaSuccess) return e;
             return launch_tma_apply_finish(h->plan, h->H, h->W, h->rs, h->d_final, h->t_final, h->inv_m, x,
                                            y, h->stream);
@@ -520,6 +528,28 @@ dsgnlm_status dsgnlm_apply(dsgnlm_t h, const float* x, float* y) {
         return launch_apply(h->dtype, h->planes.p, h->H, h->W, h->rs, h->d_final, h->inv_m, x, y,
                             h->stream);
     }));
+    return DSGNLM_OK;
+}
+
+dsgnlm_status dsgnlm_set_wait_budget(dsgnlm_t h, long long cycles) {
+    if (!h || cycles > dsg::kDefaultWaitBudget) return DSGNLM_EINVAL;
+    const long long b = cycles < 0 ? dsg::kDefaultWaitBudget : cycles;
+    if (b != h->wait_budget) {
+        // recorded graphs carry the budget in their kernel parameters
+        DSG_CK(cudaStreamSynchronize(h->stream));
+        h->release_graphs();
+        h->wait_budget = b;
+    }
+    return DSGNLM_OK;
+}
+
+dsgnlm_status dsgnlm_sync(dsgnlm_t h) {
+    if (!h) return DSGNLM_EINVAL;
+    DSG_CK(cudaStreamSynchronize(h->stream));
+    if (!h->err.p) return DSGNLM_OK;
+    unsigned errv = 0;
+    DSG_CK(cudaMemcpy(&errv, h->err.p, sizeof errv, cudaMemcpyDeviceToHost));
+    if (errv) return wait_timeout(h, h->stream);
     return DSGNLM_OK;
 }
 
@@ -794,7 +824,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
             if (e == cudaSuccess)
                 e = h->timed(DSGNLM_PROF_APPLY, [&] {
                     return launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
-                                             h->err.as<unsigned>(), nullptr, st);
+                                             h->err.as<unsigned>(), nullptr, st, h->wait_budget);
                 });
             if (sr && do_x) {
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
@@ -915,7 +945,7 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
         if (fast) {
             unsigned errv = 0;
             DSG_CK(cudaMemcpy(&errv, h->err.p, sizeof errv, cudaMemcpyDeviceToHost));
-            if (errv) return DSGNLM_TIMEOUT;
+            if (errv) return wait_timeout(h, h->stream);
         }
         const double* hs = (const double*)h->host_stage;
         for (int it = 0; it < iters; ++it) {
@@ -1002,7 +1032,7 @@ dsgnlm_status lpnp_solve_standard(const lpnp_problem* p, float rho, int iters, i
         }));
         DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
             return launch_tma_gather(h->dtype, h->plan, H, W, h->rs, h->d_final, h->z.as<float>(),
-                                     h->err.as<unsigned>(), nullptr, st);
+                                     h->err.as<unsigned>(), nullptr, st, h->wait_budget);
         }));
         ea.partials = h->partials.as<double>() + 2 * (size_t)nblocks * it;
         DSG_CK(h->timed(DSGNLM_PROF_XUPDATE, [&] { return launch_combine_update(0, h->plan, h->rs, ea, st); }));
@@ -1015,7 +1045,7 @@ dsgnlm_status lpnp_solve_standard(const lpnp_problem* p, float rho, int iters, i
         DSG_CK(cudaStreamSynchronize(st));
         unsigned errv = 0;
         DSG_CK(cudaMemcpy(&errv, h->err.p, sizeof errv, cudaMemcpyDeviceToHost));
-        if (errv) return DSGNLM_TIMEOUT;
+        if (errv) return wait_timeout(h, st);
         const double* hs = (const double*)h->host_stage;
         for (int it = 0; it < iters; ++it) {
             p->resid_hist[2 * it] = std::sqrt(hs[2 * it] / (double)n);
@@ -1242,7 +1272,7 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
         DSG_CK(cudaStreamSynchronize(st));
         unsigned errv = 0;
         DSG_CK(cudaMemcpy(&errv, lead->err.p, sizeof errv, cudaMemcpyDeviceToHost));
-        if (errv) return DSGNLM_TIMEOUT;
+        if (errv) return wait_timeout(lead, st);
         for (int i = 0; i < count; ++i) {
             if (!probs[i].resid_hist) continue;
             const double n = (double)probs[i].H * probs[i].W;

@@ -73,6 +73,8 @@ struct dsgnlm {
     bool fast = false;
     TmaPlan plan{};
     DevBuf tma_part, tbuf[2], err, bal_part;
+    // cycles a phase-1 consumer waits for a plane before giving up (dsgnlm_set_wait_budget)
+    long long wait_budget = dsg::kDefaultWaitBudget;
     float* t_final = nullptr;
     // balancing passes as a CUDA graph with a device-driven WHILE node
     cudaStream_t cap_stream = nullptr;

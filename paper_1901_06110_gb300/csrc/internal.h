@@ -68,6 +68,8 @@ struct TmaPlan {
 };
 // Batched phase 1: every instance's tensor map travels in the kernel parameters.
 constexpr int kMaxBatch = 96;
+// Cycles (about 2 s at 2 GHz) before a bounded device wait gives up.
+constexpr long long kDefaultWaitBudget = 4000000000LL;
 struct BatchMaps {
     alignas(64) unsigned char m[kMaxBatch][128];
 };
@@ -88,8 +90,11 @@ int tma_tile_h();
 size_t tma_region_floats(int rs);
 int tma_p2_blocks(int H, int W);
 // phase 1: partial sums of K1 q over every tile and offset slice, q = d (z null) or d z
+// wait_budget: cycles a consumer waits for a plane before the CTA gives up and sets
+// *err (kDefaultWaitBudget, about 2 s; 0 gives up at the first wait)
 cudaError_t launch_tma_gather(int dtype, const TmaPlan& plan, int H, int W, int rs, const float* d,
-                              const float* z, unsigned* err, const int* skip, cudaStream_t st);
+                              const float* z, unsigned* err, const int* skip, cudaStream_t st,
+                              long long wait_budget = kDefaultWaitBudget);
 // phase 2 epilogues
 cudaError_t launch_tma_apply_finish(const TmaPlan& plan, int H, int W, int rs, const float* d,
                                     const float* t, float inv_m, const float* z, float* y,

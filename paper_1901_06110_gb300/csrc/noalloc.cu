@@ -21,7 +21,11 @@
 //   serialise them on one stream.
 // - The first call on a device resolves the array's device address with
 //   cudaGetSymbolAddress (which may load this library's module onto that device).
-//   Make that first call before any stream capture begins on the device.
+//   Make that first call before any stream capture begins on the device.  The
+//   address is cached for the life of the process, so the call must not be used
+//   on a device after cudaDeviceReset or a teardown of its primary context.
+// - The blur is always periodic: the result equals lpnp_gradient's only for a
+//   problem with blur_boundary == LPNP_BC_PERIODIC.
 #include <mutex>
 
 #include "../../include/dsgnlm.h"

@@ -42,7 +42,7 @@ constexpr int kTW = kTmaTW;              // tile columns (= consumer threads)
 constexpr int kConsumers = kTW;
 constexpr int kConsumerWarps = kConsumers / 32;
 constexpr int kThreads = kConsumers + 32;  // + one producer warp
-constexpr long long kWaitBudget = 4000000000LL;  // cycles (about 2 s) before a wait gives up
+constexpr long long kWaitBudget = kDefaultWaitBudget;  // cycles (about 2 s) before a wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -78,6 +78,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitBudget) return false;
+    }
+    return true;
+}
+
+// A consumer's wait for a plane: gives up after `budget` cycles.  A budget of 0
+// gives up at once, as if the copy had not landed in time (the handle's test hook
+// for the timeout path; the default is kWaitBudget).
+__device__ __forceinline__ bool mbar_wait_consumer(uint64_t* bar, unsigned parity, long long budget) {
+    if (budget <= 0) return false;
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > budget) return false;
+    }
+    return true;
+}
+
+// The producer's wait for a free stage: ends early once the consumers have given
+// up (they release no more stages), otherwise after kWaitBudget.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, unsigned parity, const int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*(const volatile int*)abort_flag) return false;
         if (clock64() - t0 > kWaitBudget) return false;
     }
     return true;
@@ -146,7 +171,7 @@ template <typename WT, int RS> constexpr int p1_stages() {
 template <int RS, typename WT>
 __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, const float* __restrict__ d,
                                         const float* __restrict__ z, int oxa, int oxb, int x0, int y0,
-                                        float* __restrict__ out, unsigned* __restrict__ err) {
+                                        float* __restrict__ out, unsigned* __restrict__ err, long long cbudget) {
     constexpr bool kComp = P1Traits<WT>::kComp;
     constexpr int kStages = p1_stages<WT, RS>();
     constexpr int RH = kTH + RS;
@@ -185,7 +210,7 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
             bool ok = true;
             for (int ox = oxa; ox <= oxb && ok; ++ox) {
                 for (int oy = ox > 0 ? 0 : 1; oy <= RS; ++oy, ++q) {
-                    if (q >= kStages && !mbar_wait(&empty[s], ph ^ 1u)) {
+                    if (q >= kStages && !mbar_wait_or_abort(&empty[s], ph ^ 1u, &s_abort)) {
                         ok = false;
                         break;
                     }
@@ -261,7 +286,7 @@ __device__ __forceinline__ void p1_body(const CUtensorMap* tmap, int H, int W, c
             cs = 0;
             cph ^= 1u;
         }
-        if (ok && (!mbar_wait(&full[s], ph) || *(volatile int*)&s_abort)) {
+        if (ok && (!mbar_wait_consumer(&full[s], ph, cbudget) || *(volatile int*)&s_abort)) {
             ok = false;
             *(volatile int*)&s_abort = 1;
             atomicOr(err, 2u);
@@ -341,13 +366,13 @@ template <int RS, typename WT>
 __global__ void __launch_bounds__(kThreads, P1Traits<WT>::kMinBlocks)
 stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const float* __restrict__ d,
                   const float* __restrict__ z, TmaSplits splits, float* __restrict__ part,
-                  unsigned* __restrict__ err, const int* __restrict__ skip) {
+                  unsigned* __restrict__ err, const int* __restrict__ skip, long long cbudget) {
     if (skip && *(volatile const int*)skip) return;
     const int slice = blockIdx.z;
     const size_t region = (size_t)(kTH + RS) * (kTW + 2 * RS);
     float* out = part + ((size_t)(slice * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * region;
     p1_body<RS, WT>(&tmap, H, W, d, z, splits.ox_lo[slice], splits.ox_hi[slice], blockIdx.x * kTW,
-                    blockIdx.y * kTH, out, err);
+                    blockIdx.y * kTH, out, err, cbudget);
 }
 
 // One launch over the (instance, tile, slice) work items of a batch of images.
@@ -361,7 +386,7 @@ stencil_p1_batched_kernel(const __grid_constant__ BatchMaps maps, const BatchIns
     const size_t region = (size_t)(kTH + RS) * (kTW + 2 * RS);
     float* out = in.part + ((size_t)(w.w * in.tiles_y + w.y) * in.tiles_x + w.z) * region;
     p1_body<RS, WT>(reinterpret_cast<const CUtensorMap*>(maps.m[w.x]), in.H, in.W, in.d, in.z, in.splits.ox_lo[w.w], in.splits.ox_hi[w.w],
-                    w.z * kTW, w.y * kTH, out, err);
+                    w.z * kTW, w.y * kTH, out, err, kWaitBudget);
 }
 
 // --------------------------------------------------------------------------- phase 2
@@ -418,7 +443,7 @@ size_t p1_smem_bytes() {
 
 template <int RS, typename WT>
 cudaError_t p1_launch(const TmaPlan& plan, int H, int W, const float* d, const float* z, unsigned* err,
-                      const int* skip, cudaStream_t st) {
+                      const int* skip, cudaStream_t st, long long cbudget) {
     const size_t smem = p1_smem_bytes<RS, WT>();
     // set once per instantiation (a thread-safe static initialisation)
     static const cudaError_t configured =
@@ -426,7 +451,7 @@ cudaError_t p1_launch(const TmaPlan& plan, int H, int W, const float* d, const f
     if (configured != cudaSuccess) return configured;
     dim3 grid(plan.tiles_x, plan.tiles_y, plan.splits.n);
     stencil_p1_kernel<RS, WT><<<grid, kThreads, smem, st>>>(*(const CUtensorMap*)plan.tmap, H, W, d, z,
-                                                            plan.splits, plan.partials, err, skip);
+                                                            plan.splits, plan.partials, err, skip, cbudget);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -464,18 +489,18 @@ cudaError_t p1b_dispatch(int rs, const BatchMaps& maps, const BatchInst* insts, 
 
 template <typename WT>
 cudaError_t p1_dispatch(int rs, const TmaPlan& plan, int H, int W, const float* d, const float* z,
-                        unsigned* err, const int* skip, cudaStream_t st) {
+                        unsigned* err, const int* skip, cudaStream_t st, long long cbudget) {
     switch (rs) {
-        case 1: return p1_launch<1, WT>(plan, H, W, d, z, err, skip, st);
-        case 2: return p1_launch<2, WT>(plan, H, W, d, z, err, skip, st);
-        case 3: return p1_launch<3, WT>(plan, H, W, d, z, err, skip, st);
-        case 4: return p1_launch<4, WT>(plan, H, W, d, z, err, skip, st);
-        case 5: return p1_launch<5, WT>(plan, H, W, d, z, err, skip, st);
-        case 6: return p1_launch<6, WT>(plan, H, W, d, z, err, skip, st);
-        case 7: return p1_launch<7, WT>(plan, H, W, d, z, err, skip, st);
-        case 8: return p1_launch<8, WT>(plan, H, W, d, z, err, skip, st);
-        case 10: return p1_launch<10, WT>(plan, H, W, d, z, err, skip, st);
-        case 12: return p1_launch<12, WT>(plan, H, W, d, z, err, skip, st);
+        case 1: return p1_launch<1, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 2: return p1_launch<2, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 3: return p1_launch<3, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 4: return p1_launch<4, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 5: return p1_launch<5, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 6: return p1_launch<6, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 7: return p1_launch<7, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 8: return p1_launch<8, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 10: return p1_launch<10, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 12: return p1_launch<12, WT>(plan, H, W, d, z, err, skip, st, cbudget);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -505,11 +530,12 @@ int tma_p2_blocks(int H, int W) {
 }
 
 cudaError_t launch_tma_gather(int dtype, const TmaPlan& plan, int H, int W, int rs, const float* d,
-                              const float* z, unsigned* err, const int* skip, cudaStream_t st) {
+                              const float* z, unsigned* err, const int* skip, cudaStream_t st,
+                              long long wait_budget) {
     switch (dtype) {
-        case 0: return p1_dispatch<float>(rs, plan, H, W, d, z, err, skip, st);
-        case 1: return p1_dispatch<__half>(rs, plan, H, W, d, z, err, skip, st);
-        default: return p1_dispatch<__nv_bfloat16>(rs, plan, H, W, d, z, err, skip, st);
+        case 0: return p1_dispatch<float>(rs, plan, H, W, d, z, err, skip, st, wait_budget);
+        case 1: return p1_dispatch<__half>(rs, plan, H, W, d, z, err, skip, st, wait_budget);
+        default: return p1_dispatch<__nv_bfloat16>(rs, plan, H, W, d, z, err, skip, st, wait_budget);
     }
 }
 

@@ -124,6 +124,18 @@ def dsgnlm_apply(h: Dsgnlm, x: torch.Tensor, out: torch.Tensor | None = None) ->
     return y
 
 
+def dsgnlm_sync(h: Dsgnlm) -> int:
+    """Wait for the handle's queued work; returns OK, or TIMEOUT if a bounded device
+    wait gave up since the last report (the error word is then cleared)."""
+    return _check(h.lib.dsgnlm_sync(h.handle), "dsgnlm_sync", ok=(_abi.OK, _abi.TIMEOUT))
+
+
+def dsgnlm_set_wait_budget(h: Dsgnlm, cycles: int) -> None:
+    """Cycles a stencil consumer waits for a weight tile (0: give up at once; a
+    negative value restores the default of about 2 s)."""
+    _check(h.lib.dsgnlm_set_wait_budget(h.handle, int(cycles)), "dsgnlm_set_wait_budget")
+
+
 def dsgnlm_num_offsets(h: Dsgnlm) -> int:
     return h.lib.dsgnlm_num_offsets(h.handle)
 
@@ -239,8 +251,10 @@ def lpnp_gradient(p: Problem, x: torch.Tensor) -> torch.Tensor:
 
 def lpnp_sr_gradient_noalloc(x: torch.Tensor, y: torch.Tensor, blur_sigma: float, blur_r: int,
                              out: torch.Tensor | None = None) -> torch.Tensor:
-    """A^T (A x - y) without any device allocation inside the call (its scratch is a
-    fixed 4 MiB array shared by all calls on the device; see include/dsgnlm.h)."""
+    """A^T (A x - y) with the periodic blur, without any device allocation inside the
+    call (its scratch is a fixed 4 MiB array shared by all calls on the device; see
+    include/dsgnlm.h).  Equal to lpnp_gradient only for problems whose blur boundary
+    is periodic; not for use on a device after a device reset."""
     H, W = x.shape
     g = torch.empty_like(x) if out is None else out
     _check(_abi.load().lpnp_sr_gradient_noalloc(_ptr(x, torch.float32, "x"),

@@ -49,3 +49,24 @@ def test_autograd_matches_finite_differences():
     fd_r = (adjoint.unrolled_loss(inst["y"], guide, 0.1, 1.0 + 1e-6, x_true, 1, 2, 3, 4)
             - adjoint.unrolled_loss(inst["y"], guide, 0.1, 1.0 - 1e-6, x_true, 1, 2, 3, 4)) / 2e-6
     assert abs(fd_r - rho.grad.item()) <= 1e-6 + 1e-4 * abs(fd_r)
+
+
+def test_branch_trace_flags_steps_across_a_kink():
+    # x0 = clip(guide, 0, 1): a guide pixel 0.5e-5 below 1 is inside the box, and a
+    # step of +1e-5 moves it across the clip, so the traces differ; a step of the
+    # same size on a pixel in the middle of the box changes no branch.
+    wl, inst, guide = _case(8, 8, 3)
+    g = np.clip(guide, 0.1, 0.9)
+    g[2, 3] = 1.0 - 0.5e-5
+    run = lambda gu: (lambda t: (adjoint.unrolled_loss(inst["y"], gu, 0.1, 1.0, inst["x_true"], 1, 2, 2, 3,
+                                                       trace=t), t))({})
+    _, base = run(g)
+    assert len(base["clamp"]) == 3 and base["init"][2, 3] == 0
+    up = g.copy()
+    up[2, 3] += 1e-5
+    _, t_up = run(up)
+    assert t_up["init"][2, 3] == -1 and not adjoint.same_branches(base, t_up)
+    mid = g.copy()
+    mid[4, 4] += 1e-5
+    _, t_mid = run(mid)
+    assert adjoint.same_branches(base, t_mid)

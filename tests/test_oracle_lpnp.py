@@ -132,3 +132,47 @@ def test_standard_admm_with_identity_denoiser_is_proximal_point():
         xd = np.linalg.solve(M, A.T @ y.ravel() + rho * xd)
     np.testing.assert_allclose(x.ravel(), xd, atol=1e-9)
     np.testing.assert_allclose(u, 0, atol=1e-15)
+
+
+def test_rms_literal_values():
+    # rms(a) = sqrt(mean(a^2)): rms([3, 4]) = sqrt((9 + 16) / 2) = sqrt(12.5)
+    assert lpnp.rms(np.array([3.0, 4.0])) == np.sqrt(12.5)
+    assert lpnp.rms(np.full((5, 7), -0.25)) == 0.25
+    assert lpnp.rms(np.zeros((3, 3))) == 0.0
+    # the mean runs over every element of a 2-D image, not over rows
+    assert abs(lpnp.rms(np.array([[1.0, 0.0], [0.0, 0.0]])) - 0.5) < 1e-15
+
+
+def test_psnr_literal_values():
+    # PSNR = 10 log10(1 / MSE), peak 1 over all pixels (reading of Sec. 4)
+    ref = np.zeros((4, 4))
+    assert abs(lpnp.psnr(np.full((4, 4), 0.1), ref) - 20.0) < 1e-12    # MSE 0.01
+    assert abs(lpnp.psnr(np.full((4, 4), 0.01), ref) - 40.0) < 1e-12   # MSE 1e-4
+    x = np.array([[0.5, 0.5], [0.5, 0.5]])
+    y = np.array([[0.5, 0.5], [0.5, 0.7]])                              # MSE 0.04 / 4 = 0.01
+    assert abs(lpnp.psnr(y, x) - 20.0) < 1e-12
+    assert lpnp.psnr(x, x) == float("inf")
+    assert abs(lpnp.psnr(x, y) - lpnp.psnr(y, x)) == 0.0
+
+
+def test_residual_normalisation_two_pixels():
+    # One step of Algorithm 1 on a 1x2 image worked out by hand (reading of Sec. 4,
+    # Tables 2-3: RMS residuals, the dual one scaled by rho).  alpha = 1, rho = 2,
+    # mu = 1/3, grad f = 0, x0 = v0 = (0.2, 0.6), u0 = 0:
+    #   x1 = (1 x0 + 2 (v0 - u0)) / 3 = (0.2, 0.6);  z = x1 + u0 = (0.2, 0.6)
+    #   v1 = W z with W = [[.5, .5], [.5, .5]]  ->  (0.4, 0.4)
+    #   u1 = u0 + x1 - v1 = (-0.2, 0.2)
+    #   primal = rms(x1 - v1) = 0.2;  dual = rho rms(v1 - v0) = 2 * 0.2 = 0.4
+    #   PSNR against (0.2, 0.5): MSE = 0.01 / 2 -> 10 log10(200)
+    x0 = np.array([[0.2, 0.6]])
+    Wm = np.array([[0.5, 0.5], [0.5, 0.5]])
+    x, v, u, hist = lpnp.lpnp_solve(lambda x: np.zeros_like(x), lambda z: (Wm @ z.ravel()).reshape(z.shape),
+                                    x0, x0, np.zeros_like(x0), 1.0, 2.0, 1, lpnp.BOX01,
+                                    np.array([[0.2, 0.5]]))
+    np.testing.assert_allclose(x, [[0.2, 0.6]], atol=1e-15)
+    np.testing.assert_allclose(v, [[0.4, 0.4]], atol=1e-15)
+    np.testing.assert_allclose(u, [[-0.2, 0.2]], atol=1e-15)
+    primal, dual, p = hist[0]
+    assert abs(primal - 0.2) < 1e-15
+    assert abs(dual - 0.4) < 1e-15
+    assert abs(p - 10.0 * np.log10(200.0)) < 1e-12

@@ -57,3 +57,21 @@ def test_noalloc_gradient_rejects_oversized_images(gpu_lib):
     fake = ctypes.c_void_p(0x10000)
     st = gpu_lib.lpnp_sr_gradient_noalloc(fake, fake, 2048, 2052, 1.0, 4, fake, None)
     assert st == _abi.EINVAL
+
+
+@pytest.mark.parametrize("H,W", [(2048, 2048), (4096, 1024)])
+def test_noalloc_gradient_at_the_size_cap(gpu_lib, H, W):
+    """(H/2)(W/2) = 1,048,576 exactly: the largest accepted size fills the whole
+    array; every element of the result matches the handle-based gradient."""
+    from paper_1901_06110_gb300 import _abi
+    assert (H // 2) * (W // 2) == 1 << 20
+    stream = torch.cuda.current_stream().cuda_stream
+    x = cuda(synthetic.ground_truth(H, W, 6, True, 21))
+    y = cuda(np.random.default_rng(21).uniform(0, 1, (H // 2, W // 2)).astype(np.float32))
+    g = torch.full((H, W), float("nan"), device="cuda")
+    st = gpu_lib.lpnp_sr_gradient_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), H, W,
+                                          1.0, 4, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(stream))
+    assert st == _abi.OK
+    torch.cuda.synchronize()
+    ref = _handle_gradient(x, y, 1.0, 4)
+    np.testing.assert_allclose(host(g), host(ref), atol=1e-6)

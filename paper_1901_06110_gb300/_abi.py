@@ -16,6 +16,7 @@ C_NONE, C_NONNEG, C_BOX01 = 0, 1, 2
 BC_PERIODIC, BC_SYMMETRIC = 0, 1
 MAX_PATCH_R, MAX_SEARCH_R = 14, 24
 PROF_BUILD, PROF_BALANCE, PROF_APPLY, PROF_XUPDATE = range(4)
+BALANCE_SINKHORN, BALANCE_ACCELERATED = 0, 1
 
 
 class LpnpProblem(ctypes.Structure):
@@ -41,6 +42,7 @@ SIGNATURES = {
                                        ctypes.POINTER(c_int), ctypes.POINTER(c_double), ctypes.POINTER(c_int)]),
     "dsgnlm_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
     "dsgnlm_sync": (c_int, [c_void_p]),
+    "dsgnlm_set_balance_scheme": (c_int, [c_void_p, c_int]),
     "dsgnlm_set_wait_budget": (c_int, [c_void_p, ctypes.c_longlong]),
     "dsgnlm_copy_weights": (c_int, [c_void_p, c_void_p]),
     "dsgnlm_copy_scaling": (c_int, [c_void_p, c_void_p, ctypes.POINTER(c_double)]),

@@ -121,8 +121,9 @@ batched_balance_epilogue_kernel(const BatchBal* __restrict__ bb, const int4* __r
     if (*(volatile const int*)&ctl->done) return;
     const int t = threadIdx.y * 32 + threadIdx.x;
     float e = 0.f, m = 0.f;
+    const PassRule rule = pass_rule(ctl);
     balance_pixels(b.cv, b.H, b.W, b.d[parity], b.d[parity ^ 1], b.t[parity], w.y * kXH, w.z * kXW, threadIdx.x,
-                   threadIdx.y, e, m);
+                   threadIdx.y, rule, e, m);
     e = warp_max(e);
     m = warp_max(m);
     __shared__ float se[8], sm[8];

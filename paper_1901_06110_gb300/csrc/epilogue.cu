@@ -41,8 +41,9 @@ balance_epilogue_kernel(Cover cv, int H, int W, const float* __restrict__ d_in, 
         return;
     }
     float e = 0.f, m = 0.f;
-    balance_pixels<SL>(cv, H, W, d_in, d_out, t_out, blockIdx.y * kXH, blockIdx.x * kXW, threadIdx.x, threadIdx.y, e,
-                       m);
+    const PassRule rule = pass_rule(ctl);
+    balance_pixels<SL>(cv, H, W, d_in, d_out, t_out, blockIdx.y * kXH, blockIdx.x * kXW, threadIdx.x, threadIdx.y,
+                       rule, e, m);
     e = warp_max(e);
     m = warp_max(m);
     __shared__ float se[8], sm[8];

@@ -278,24 +278,48 @@ __device__ __forceinline__ void combine_update_body(const Cover& cv, const Epilo
     }
 }
 
+// Update rule of the current pass: the plain symmetric Sinkhorn step, or (from
+// ctl->plain_passes on, accelerated scheme) the over-relaxed step with momentum.
+struct PassRule {
+    bool accel;
+    float half_relax, momentum;
+};
+
+__device__ __forceinline__ PassRule pass_rule(const BalanceCtl* ctl) {
+    PassRule r;
+    const float relax = ctl->relax, mom = ctl->momentum;
+    r.accel = relax > 0.f && ctl->pass >= ctl->plain_passes;  // a zeroed block is the plain scheme
+    r.half_relax = 0.5f * relax;
+    r.momentum = mom;
+    return r;
+}
+
 // One thread's share of a balancing pass's epilogue (Eq. S2 iterated) on the
 // kXH x kXW tile at (y0, x0): pixels (y0 + ry, x0 + cx) and (y0 + ry + 8, x0 + cx).
-// t = K1 d (K1(s, s) = 1), the next scaling sqrt(d / t), and the running maxima
-// e = max |d t - 1| and m = max d t.
+// t = K1 d (K1(s, s) = 1), the next scaling, and the running maxima e = max |d t - 1|
+// and m = max d t.  The plain step is d <- sqrt(d / t).  The accelerated step
+// works on u = log d: u <- u - relax (u + log t) / 2 + momentum (u - u_prev), i.e.
+// d <- d (d t)^(-relax/2) (d / d_prev)^momentum, with both logarithms formed from
+// quantities near one (log1p of d t - 1 and of (d - d_prev) / d_prev) and the
+// factor applied as d + d expm1(.), so that the step keeps the relative precision
+// of d near convergence.  d_prev is read from d_out before it is overwritten (the
+// two scaling buffers alternate, so d_out holds the scaling of two passes back).
 template <int SL = 0>
 __device__ __forceinline__ void balance_pixels(const Cover& cv, int H, int W, const float* __restrict__ d_in,
                                                float* __restrict__ d_out, float* __restrict__ t_out, int y0, int x0,
-                                               int cx, int ry, float& e, float& m) {
+                                               int cx, int ry, const PassRule& rule, float& e, float& m) {
     const TileCover tc = tile_cover(cv, y0, x0);
     const int pj = x0 + cx;
     const int lj = pj - (x0 / kTmaTW) * kTmaTW;
     // both rows' loads before the first store
-    float dv[2], gv[2];
+    float dv[2], gv[2], dp[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int py = ry + 8 * r;
         const bool ok = y0 + py < H && pj < W;
-        dv[r] = ok ? d_in[(size_t)(y0 + py) * W + pj] : 0.f;
+        const size_t s = (size_t)(y0 + py) * W + pj;
+        dv[r] = ok ? d_in[s] : 0.f;
+        dp[r] = (ok && rule.accel) ? d_out[s] : 1.f;
         gv[r] = ok ? tile_gather_comp<SL>(tc, py, lj) : 0.f;
     }
 #pragma unroll
@@ -305,7 +329,13 @@ __device__ __forceinline__ void balance_pixels(const Cover& cv, int H, int W, co
         const size_t s = (size_t)pi * W + pj;
         const float ds = dv[r];
         const float tt = ds + gv[r];  // (K1 d)_s with K1(s, s) = 1
-        d_out[s] = sqrtf(ds / tt);
+        if (rule.accel) {
+            const float lf = fmaf(-rule.half_relax, log1pf(fmaf(ds, tt, -1.f)),
+                                  rule.momentum * log1pf((ds - dp[r]) / dp[r]));
+            d_out[s] = fmaf(ds, expm1f(lf), ds);
+        } else {
+            d_out[s] = sqrtf(ds / tt);
+        }
         t_out[s] = tt;
         e = fmaxf(e, fabsf(fmaf(ds, tt, -1.f)));  // |d_s t_s - 1| with a single rounding
         m = fmaxf(m, ds * tt);

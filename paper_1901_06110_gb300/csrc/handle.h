@@ -75,6 +75,8 @@ struct dsgnlm {
     DevBuf tma_part, tbuf[2], err, bal_part;
     // cycles a phase-1 consumer waits for a plane before giving up (dsgnlm_set_wait_budget)
     long long wait_budget = dsg::kDefaultWaitBudget;
+    // update rule of dsgnlm_balance / dsgnlm_balance_batched (dsgnlm_set_balance_scheme)
+    int balance_scheme = DSGNLM_BALANCE_SINKHORN;
     float* t_final = nullptr;
     // balancing passes as a CUDA graph with a device-driven WHILE node
     cudaStream_t cap_stream = nullptr;

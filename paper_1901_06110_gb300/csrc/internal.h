@@ -31,6 +31,12 @@ struct BalanceCtl {
     double m;        // TMA path: max row sum of the last decided pass
     float inv_m;     // TMA path: (float)(1 / m), written with m on the device
     unsigned arrive;  // TMA path: blocks of the current pass's epilogue that have finished
+    // update rule of the passes from `plain_passes` on (accelerated scheme): on
+    // u = log d, u <- u - relax (u + log t) / 2 + momentum (u - u_prev); relax = 0
+    // (a zeroed block) keeps the plain step d <- sqrt(d / t) in every pass
+    float relax;
+    float momentum;
+    int plain_passes;
 };
 
 // Solve-loop reduction state: per-block partial sums of every iteration (reduced

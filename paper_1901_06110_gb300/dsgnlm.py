@@ -124,6 +124,13 @@ def dsgnlm_apply(h: Dsgnlm, x: torch.Tensor, out: torch.Tensor | None = None) ->
     return y
 
 
+def dsgnlm_set_balance_scheme(h: Dsgnlm, scheme: str) -> None:
+    """'sinkhorn' (plain symmetric Sinkhorn passes, the default) or 'accelerated'
+    (two plain passes, then heavy-ball steps on log d; same fixed point)."""
+    code = {"sinkhorn": _abi.BALANCE_SINKHORN, "accelerated": _abi.BALANCE_ACCELERATED}[scheme]
+    _check(h.lib.dsgnlm_set_balance_scheme(h.handle, code), "dsgnlm_set_balance_scheme")
+
+
 def dsgnlm_sync(h: Dsgnlm) -> int:
     """Wait for the handle's queued work; returns OK, or TIMEOUT if a bounded device
     wait gave up since the last report (the error word is then cleared)."""

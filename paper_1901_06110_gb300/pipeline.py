@@ -32,6 +32,9 @@ class Params:
     spi_eps: float = 1e-3
     weight_dtype: str = "f32"
     boundary: str = "periodic"  # SR blur boundary: "periodic" or "symmetric"
+    # balance update rule: "accelerated" (heavy-ball passes after two plain ones; the
+    # same fixed point in fewer passes) or "sinkhorn" (plain passes)
+    balance: str = "accelerated"
     extra: dict = field(default_factory=dict)
 
     @staticmethod
@@ -52,6 +55,7 @@ class Solver:
     def __init__(self, H: int, W: int, params: Params, kind: str = "sr"):
         self.H, self.W, self.p, self.kind = H, W, params, kind
         self.den = D.dsgnlm_create(params.weight_dtype)
+        D.dsgnlm_set_balance_scheme(self.den, params.balance)
         self.x = torch.empty((H, W), device="cuda")
         self.v = torch.empty_like(self.x)
         self.u = torch.empty_like(self.x)
@@ -149,6 +153,8 @@ class BatchSolver:
         self.p = params
         self.shapes = list(shapes)
         self.dens = [D.dsgnlm_create(params.weight_dtype) for _ in self.shapes]
+        for d in self.dens:
+            D.dsgnlm_set_balance_scheme(d, params.balance)
         self.x = [torch.empty(s, device="cuda") for s in self.shapes]
         self.v = [torch.empty_like(t) for t in self.x]
         self.u = [torch.empty_like(t) for t in self.x]

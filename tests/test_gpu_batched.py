@@ -240,3 +240,28 @@ def test_batched_balance_edges(gpu_lib):
         assert rb == sa and rb[0] == _abi.OK and rb[1] == 0
         ones = torch.ones((b.H, b.W), device="cuda")
         np.testing.assert_allclose(host(D.dsgnlm_apply(b, ones)), 1.0, atol=1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_batched_balance_accelerated_equals_single(gpu_lib, dtype):
+    """Under the accelerated scheme each image of a batched balance takes its own
+    heavy-ball passes: results equal the single-image balance bit for bit."""
+    from paper_1901_06110_gb300 import dsgnlm as D
+    sizes = [(96, 96), (128, 64), (40, 200), (17, 33)]
+    singles, batch = [], []
+    for i, (H, W) in enumerate(sizes):
+        g = cuda(np.ascontiguousarray(synthetic.ground_truth(max(H, 8), max(W, 8), 6, True, 1300 + i)[:H, :W]))
+        a = D.dsgnlm_create(dtype)
+        D.dsgnlm_set_balance_scheme(a, "accelerated")
+        D.dsgnlm_build(a, g, 2, 5, 0.1)
+        a.H, a.W = H, W
+        singles.append((a, D.dsgnlm_balance(a, 1e-6, 300)))
+        b = D.dsgnlm_create(dtype)
+        D.dsgnlm_set_balance_scheme(b, "accelerated")
+        D.dsgnlm_build(b, g, 2, 5, 0.1)
+        b.H, b.W = H, W
+        batch.append(b)
+    res = D.dsgnlm_balance_batched(batch, 1e-6, 300)
+    for (a, sa), b, rb in zip(singles, batch, res):
+        assert rb == sa, (rb, sa)
+        np.testing.assert_array_equal(host(D.dsgnlm_copy_scaling(a)[0]), host(D.dsgnlm_copy_scaling(b)[0]))

@@ -193,3 +193,53 @@ def test_state_errors(gpu_lib):
         D.dsgnlm_apply(den, x)
     assert e.value.status == _abi.NOT_BALANCED
     assert D.dsgnlm_num_offsets(den) == len(half_offsets(2))
+
+
+@pytest.mark.parametrize("H,W,rp,rs,h", [(96, 80, 3, 10, 0.08), (64, 48, 2, 5, 0.1), (40, 300, 3, 10, 0.08)])
+def test_accelerated_balance_reaches_the_same_w(gpu_lib, H, W, rp, rs, h):
+    """The accelerated scheme (two symmetric Sinkhorn steps, then heavy-ball steps on
+    log d) has the fixed point of Eq. S2 iterated, d (K1 d) = 1, which is unique: the
+    scaling it reaches at tol 1e-6 is within the tolerance of the oracle's scaling
+    balanced to 1e-11, in fewer passes than the plain step needs."""
+    from paper_1901_06110_gb300 import _abi
+    from paper_1901_06110_gb300 import dsgnlm as D
+    g = _guide(H, W, 12)
+    plain = _gpu_den(gpu_lib, g, rp, rs, h)
+    st_p = D.dsgnlm_balance(plain, 1e-6, 1000)
+    acc = _gpu_den(gpu_lib, g, rp, rs, h)
+    D.dsgnlm_set_balance_scheme(acc, "accelerated")
+    st_a = D.dsgnlm_balance(acc, 1e-6, 1000)
+    assert st_p[0] == _abi.OK and st_a[0] == _abi.OK and st_a[2] <= 1e-6
+    assert st_a[1] <= st_p[1] - 4, (st_a, st_p)
+    K1 = odsg.kernel_matrix(g.astype(np.float64), rp, rs, h)
+    d_o, _, hist = odsg.sinkhorn(K1, 1e-11, 10000)
+    W_o, m_o = odsg.dsg_matrix(K1, d_o)
+    d_a, m_a = D.dsgnlm_copy_scaling(acc)
+    np.testing.assert_allclose(host(d_a).ravel(), d_o, rtol=3e-6)
+    assert abs(m_a - m_o) <= 3e-6 * m_o
+    ones = torch.ones((H, W), device="cuda")
+    np.testing.assert_allclose(host(D.dsgnlm_apply(acc, ones)), 1.0, atol=1e-6)
+    z = np.random.default_rng(13).uniform(0, 1, (H, W)).astype(np.float32)
+    y = host(D.dsgnlm_apply(acc, cuda(z)))
+    assert rel_l2(y, odsg.denoise(W_o, z.astype(np.float64))) <= 1e-5
+
+
+@pytest.mark.parametrize("updates", [1, 2])
+def test_accelerated_balance_starts_with_plain_steps(gpu_lib, updates):
+    # the first two passes of the accelerated scheme are the plain step: maxit = 1
+    # is still the paper's one-shot normalisation, bit for bit
+    from paper_1901_06110_gb300 import dsgnlm as D
+    g = _guide(48, 72, 14)
+    a = _gpu_den(gpu_lib, g, 2, 5, 0.1)
+    b = _gpu_den(gpu_lib, g, 2, 5, 0.1)
+    D.dsgnlm_set_balance_scheme(b, "accelerated")
+    assert D.dsgnlm_balance(a, 0.0, updates) == D.dsgnlm_balance(b, 0.0, updates)
+    np.testing.assert_array_equal(host(D.dsgnlm_copy_scaling(a)[0]), host(D.dsgnlm_copy_scaling(b)[0]))
+
+
+def test_balance_scheme_argument(gpu_lib):
+    from paper_1901_06110_gb300 import _abi
+    from paper_1901_06110_gb300 import dsgnlm as D
+    den = D.dsgnlm_create("f32")
+    assert den.lib.dsgnlm_set_balance_scheme(den.handle, 2) == _abi.EINVAL
+    assert den.lib.dsgnlm_set_balance_scheme(None, 0) == _abi.EINVAL

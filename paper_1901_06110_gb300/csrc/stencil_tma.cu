@@ -151,13 +151,16 @@ template <typename WT> struct P1Traits {
     static constexpr bool kComp = true;
     static constexpr int kMinBlocks = 2;
 };
+#ifndef DSG_P1_HALF_BLOCKS
+#define DSG_P1_HALF_BLOCKS 4
+#endif
 template <> struct P1Traits<__half> {
     static constexpr bool kComp = false;
-    static constexpr int kMinBlocks = 4;
+    static constexpr int kMinBlocks = DSG_P1_HALF_BLOCKS;
 };
 template <> struct P1Traits<__nv_bfloat16> {
     static constexpr bool kComp = false;
-    static constexpr int kMinBlocks = 4;
+    static constexpr int kMinBlocks = DSG_P1_HALF_BLOCKS;
 };
 
 // Pipeline stages of the weight ring: 8 at two CTAs per SM; four CTAs per SM

@@ -22,6 +22,7 @@ static thread_local bool g_capturing = false;  // launches recorded into a graph
 void count_launches(uint64_t n) {
     if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }
+void set_capture_counting(bool recording) { g_capturing = recording; }
 }  // namespace dsg
 
 using namespace dsg;

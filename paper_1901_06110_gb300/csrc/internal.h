@@ -7,6 +7,9 @@
 namespace dsg {
 
 void count_launches(uint64_t n);
+// while set (on this thread), count_launches adds nothing: the kernels being recorded
+// into a graph are counted each time the graph is launched
+void set_capture_counting(bool recording);
 // makes `e` the value dsgnlm_last_cuda_error() returns in this thread
 void record_cuda_error(cudaError_t e);
 

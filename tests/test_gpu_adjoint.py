@@ -199,3 +199,37 @@ def test_batched_split_for_the_batch(gpu_lib):
     rs_ = sum(s[4] for s in singles)
     assert abs(hb - hs) <= 1e-5 * abs(hs)
     assert abs(rb - rs_) <= 1e-5 * abs(rs_)
+
+
+def test_batched_graph_replay_follows_new_inputs(gpu_lib):
+    """Repeated batched calls with equal sizes and parameters are recorded as CUDA
+    graphs (the backward on its second call, the forward on its third) and replayed
+    with the inputs copied in and the outputs copied out around the launch.  Every
+    call, direct or replayed, gives the single-image results on its own inputs bit
+    for bit, also when the inputs change from call to call."""
+    from paper_1901_06110_gb300 import dsgnlm as D
+    from paper_1901_06110_gb300.autograd import UnrollParams, UnrolledSR, unrolled_sr
+    H, W, B = 32, 48, 3
+    params = UnrollParams(patch_r=2, search_r=5, balance_passes=3, iters=6)
+    single = lambda y, g, ht, rt: UnrolledSR.apply(y, g, ht, rt, params)
+    batched = lambda y, g, ht, rt: unrolled_sr(y, g, ht, rt, params)
+    h, rho = 0.1, 1.0
+    launches = []
+    for call in range(5):
+        cases = [_case(H, W, 60 + 7 * call + b) for b in range(B)]
+        ys = [cuda(inst["y"]) for _, inst, _ in cases]
+        gs = [cuda(guide) for _, _, guide in cases]
+        xbars = [cuda(np.random.default_rng(80 + call + b).standard_normal((H, W)).astype(np.float32))
+                 for b in range(B)]
+        n0 = D.dsgnlm_launch_count()
+        xb, gyb, ggb, hb, rb = _explicit(batched, torch.stack(ys), torch.stack(gs), h, rho, torch.stack(xbars))
+        launches.append(D.dsgnlm_launch_count() - n0)
+        singles = [_explicit(single, ys[b], gs[b], h, rho, xbars[b]) for b in range(B)]
+        for b in range(B):
+            assert np.array_equal(xb[b], singles[b][0]), (call, b)
+            assert np.array_equal(gyb[b], singles[b][1]), (call, b)
+            assert np.array_equal(ggb[b], singles[b][2]), (call, b)
+        assert hb == sum(s[3] for s in singles)
+        assert rb == sum(s[4] for s in singles)
+    # a replay counts the kernels of its graph: the same number as a direct call
+    assert len(set(launches)) == 1, launches

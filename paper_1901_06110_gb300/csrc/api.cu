@@ -136,6 +136,7 @@ int dsgnlm_num_offsets(dsgnlm_t h) { return (h && h->built) ? h->nh : 0; }
 
 dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int patch_r,
                            int search_r, float bandwidth) {
+    NvtxRange nvtx_range("dsgnlm_build");
     if (!h || !guide || !aligned16(guide)) return DSGNLM_EINVAL;
     if (H < 1 || W < 1 || (size_t)H * (size_t)W > (size_t)1 << 31) return DSGNLM_EINVAL;
     if (patch_r < 0 || patch_r > DSGNLM_MAX_PATCH_R) return DSGNLM_EINVAL;
@@ -296,6 +297,7 @@ cudaError_t ensure_balance_graph(dsgnlm* h) {
 extern "C" {
 
 dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, double* resid_out) {
+    NvtxRange nvtx_range("dsgnlm_balance");
     if (!h) return DSGNLM_EINVAL;
     if (!h->built) return DSGNLM_NOT_BUILT;
     if (!(tol >= 0.0) || maxit < 0 || maxit > 1000000) return DSGNLM_EINVAL;
@@ -395,6 +397,7 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
 
 dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int maxit, int slices, int* iters_out,
                                      double* resid_out, int* status_out) {
+    NvtxRange nvtx_range("dsgnlm_balance_batched");
     if (!hs || count < 1 || count > kMaxBatch || slices < 0) return DSGNLM_EINVAL;
     if (!(tol >= 0.0) || maxit < 0 || maxit > 1000000) return DSGNLM_EINVAL;
     for (int i = 0; i < count; ++i) {
@@ -986,9 +989,13 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
 
 extern "C" {
 
-dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) { return solve_impl(p, rho, iters, nullptr); }
+dsgnlm_status lpnp_solve(const lpnp_problem* p, float rho, int iters) {
+    NvtxRange nvtx_range("lpnp_solve");
+    return solve_impl(p, rho, iters, nullptr);
+}
 
 dsgnlm_status lpnp_solve_standard(const lpnp_problem* p, float rho, int iters, int cg_iters) {
+    NvtxRange nvtx_range("lpnp_solve_standard");
     dsgnlm_status s = check_problem(p, true);
     if (s != DSGNLM_OK) return s;
     if (p->kind != LPNP_SR2 || cg_iters < 1 || !(rho > 0.f) || !std::isfinite(rho) || iters < 0) return DSGNLM_EINVAL;
@@ -1083,6 +1090,7 @@ dsgnlm_status lpnp_solve_standard(const lpnp_problem* p, float rho, int iters, i
 
 dsgnlm_status lpnp_solve_adaptive(const lpnp_problem* p, float rho, int iters, int adapt_iters, int patch_r,
                                   int search_r, float bandwidth, double tol, int maxit) {
+    NvtxRange nvtx_range("lpnp_solve_adaptive");
     if (adapt_iters < 1 || !tma_path_supports(search_r)) return DSGNLM_EINVAL;
     if (patch_r < 0 || patch_r > DSGNLM_MAX_PATCH_R || !(bandwidth > 0.f) || !std::isfinite(bandwidth))
         return DSGNLM_EINVAL;
@@ -1316,10 +1324,12 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
 extern "C" {
 
 dsgnlm_status lpnp_solve_batched(const lpnp_problem* probs, int count, float rho, int iters) {
+    NvtxRange nvtx_range("lpnp_solve_batched");
     return batched_impl(probs, count, rho, iters, 0, true);
 }
 
 dsgnlm_status lpnp_solve_batched_sched(const lpnp_problem* probs, int count, float rho, int iters, int slices) {
+    NvtxRange nvtx_range("lpnp_solve_batched_sched");
     return batched_impl(probs, count, rho, iters, slices, true);
 }
 

@@ -2,11 +2,22 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 namespace dsg {
 
 void count_launches(uint64_t n);
+
+// A named NVTX range over one call of the C ABI, for timeline tools that record NVTX
+// (build, balance, solve, the differentiable form); a push and a pop that cost next
+// to nothing when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 // while set (on this thread), count_launches adds nothing: the kernels being recorded
 // into a graph are counted each time the graph is launched
 void set_capture_counting(bool recording);

@@ -373,10 +373,9 @@ void lpnp_tape_destroy(lpnp_tape_t t);
  *   no tolerance stop), m = max_s d_s (K1 d)_s, W by Eq. S3;
  *   `iters` iterations of Algorithm 1 (box constraint [0,1], blur as in lpnp_problem)
  *   from x = v = clip(guide, 0, 1), u = 0.
- * y device [H/2][W/2]; guide device [H][W]; the tape keeps copies of both, so the
- * caller may reuse them after the call.  x_out device [H][W] receives x_N.  Records
- * the tape (replacing any earlier recording).  `den` must not be rebuilt before the
- * backward.  The shared memory of the backward limits (2 iters + 1)(16 + N_s)(32 + 2 N_s)
+ * y device [H/2][W/2]; guide device [H][W]; both must stay unchanged until
+ * lpnp_backward.  x_out device [H][W] receives x_N.  Records the tape (replacing any
+ * earlier recording).  `den` must not be rebuilt before the backward.  The shared memory of the backward limits (2 iters + 1)(16 + N_s)(32 + 2 N_s)
  * and (2 passes + 1)(16 + N_s)(32 + 2 N_s) floats to 220 KiB (EINVAL otherwise).
  * m and 1/m are formed and read on the device; the call synchronises the stream once,
  * at its end (the handle then also holds m and 1/m on the host).  The iterations run
@@ -397,22 +396,14 @@ dsgnlm_status lpnp_backward(lpnp_tape_t tape, const float* x_bar, float* y_bar, 
 
 /* Batched forms of the two calls above (Algorithm 1 unrolled, with Eq. S1-S3 for W;
  * the paper has no derivatives) for `count` images of one size and one parameter
- * set.  tapes[i] and dens[i] must be distinct.  y, guide, x_out (and x_bar, y_bar,
- * guide_bar) are host arrays of `count` device pointers with the layouts of the
- * single-image calls; the inputs are copied into the tapes and the outputs out of
- * them, so the caller's buffers may differ from call to call.  A call launches its
- * work in one of two ways.  Directly: the images are queued from a pool of host
- * threads, each image on its handle's stream, so handles on distinct streams
- * overlap their images on the device.  Or from a CUDA graph: the forward and the
- * backward of a batch are each recorded once, into tapes[0], as one graph with a
- * branch per image, on the second call whose tapes, handles, sizes and parameters
- * (and every device buffer these hold) equal those of the call before it; later such
- * calls launch the recorded graph on dens[0]'s stream, with the copies of the inputs
- * before it and of the outputs after it.  (Calls with other values launch directly;
- * a recording that fails falls back to direct launches for good.)  Both ways run the
- * same kernels in the same order per image, so the results are the same bit for bit.
- * Each call synchronises the streams of the batch once, at its end.  h_bar and
- * rho_bar (host, optional) receive `count` per-image values.
+ * set.  tapes[i] and dens[i] must be distinct.  Each image runs on its handle's
+ * stream, so handles on distinct streams overlap their images on the device.  y,
+ * guide, x_out (and x_bar, y_bar, guide_bar) are host arrays of `count` device
+ * pointers with the layouts of the single-image calls.  The images are queued from a
+ * pool of host threads, one image per thread at a time; no image waits for the
+ * device while it is queued (m and 1/m are formed and read on the device).  Each call
+ * synchronises the streams of the batch once, at its end.  h_bar and rho_bar (host,
+ * optional) receive `count` per-image values.
  * Each handle's offset split (the slices of phase 1) is sized for `count` images at
  * once, so results equal the single-image calls up to the order in which W's partial
  * sums are added (bit for bit where the split is the same), and repeated calls give

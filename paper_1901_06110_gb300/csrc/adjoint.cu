@@ -670,31 +670,9 @@ struct lpnp_tape {
     float blur_sigma = 1.f;
     DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, gs, dh[1], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
         part, m, mkey, sstar, mh, rho_part, h_part, m_part, scratch;
-    // the tape's copies of the observation and the guide (read by the forward and the
-    // backward), and the outputs of the backward before they are copied out
-    DevBuf yin, gin, ybar, gbar;
     float inv_m = 1.f;  // host copy of 1/m, valid after the forward call has returned
     // m and 1/m on the device (written by the forward, read by the kernels that follow)
     const float* inv_m_dev() const { return m.as<float>() + 1; }
-    // batched calls led by this tape: the recorded forward and backward graphs, the
-    // values each was recorded for, and the values of the previous call (a graph is
-    // recorded on the second call with the same values, once every buffer exists)
-    struct Recorded {
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        std::vector<unsigned long long> key, last;
-        int kernels = 0;
-        bool failed = false;
-        void release() {
-            if (exec) cudaGraphExecDestroy(exec);
-            if (graph) cudaGraphDestroy(graph);
-            exec = nullptr;
-            graph = nullptr;
-            key.clear();
-        }
-    };
-    Recorded fwd, bwd;
-    std::vector<cudaEvent_t> events;  // fork and join events of a recording
     // pinned host words read back after the stream work: m, the scalar cotangents and
     // the handle's wait-error flag
     struct Host {
@@ -802,11 +780,8 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     DevBuf* bufs[] = {&t->Dh, &t->Th, &t->X, &t->V, &t->U, &t->Gr, &t->AZ, &t->xh, &t->vh, &t->uh, &t->zh, &t->g,
                       &t->gs, &t->dh[0], &t->dh0, &t->base, &t->thp, &t->Dhat,
                       &t->Gp, &t->ge, &t->gb, &t->ctl, &t->part, &t->m, &t->mkey, &t->sstar, &t->mh, &t->rho_part, &t->h_part,
-                      &t->m_part, &t->scratch, &t->yin, &t->gin, &t->ybar, &t->gbar};
+                      &t->m_part, &t->scratch};
     for (DevBuf* b : bufs) b->release();
-    t->fwd.release();
-    t->bwd.release();
-    for (cudaEvent_t e : t->events) cudaEventDestroy(e);
     if (t->host) cudaFreeHost(t->host);
     delete t;
 }
@@ -815,16 +790,14 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
 
 namespace {
 
-// First half of the recording: the observation and the guide copied into the tape (when
-// y and guide are given; null means they were copied in already), K1 into the handle,
-// the T balancing passes with every d^p and t^p kept, m = max_s d_s t_s with its first
-// maximiser and 1/m on the device, and the read-back of m queued on the handle's
-// stream.  Nothing here waits for the device.  `share` images run at once (the
-// handle's offset split is sized for them).
+// First half of the recording: K1 into the handle, the T balancing passes with every
+// d^p and t^p kept, m = max_s d_s t_s with its first maximiser and 1/m on the device,
+// and the read-back of m queued on the handle's stream.  Nothing here waits for the
+// device.  `share` images run at once (the handle's offset split is sized for them).
 dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const float* guide, int H, int W,
                             int patch_r, int search_r, float bandwidth, int balance_passes, float alpha, float rho,
                             int iters, float blur_sigma, int blur_r, int share) {
-    if (!tp || !den) return DSGNLM_EINVAL;
+    if (!tp || !den || !y || !guide) return DSGNLM_EINVAL;
     if (H < 2 || W < 2 || (H & 1) || (W & 1) || iters < 1 || iters > 256 || balance_passes < 0 ||
         balance_passes > 64 || !(rho > 0.f) || !(alpha >= 0.f) || blur_r < 0 || blur_r > 8 || !(blur_sigma > 0.f))
         return DSGNLM_EINVAL;
@@ -833,14 +806,8 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
     if (pairs_g_smem(iters, search_r) > 220 * 1024 || pairs_b_smem(balance_passes, search_r) > 220 * 1024)
         return DSGNLM_EINVAL;
     if (!tp->host) TAPE_CK(cudaMallocHost((void**)&tp->host, sizeof(lpnp_tape::Host)));
-    const size_t n_in = (size_t)H * W;
-    TAPE_CK(tp->yin.ensure(sizeof(float) * (n_in / 4)));
-    TAPE_CK(tp->gin.ensure(sizeof(float) * n_in));
-    if (y)
-        TAPE_CK(cudaMemcpyAsync(tp->yin.p, y, sizeof(float) * (n_in / 4), cudaMemcpyDeviceToDevice, den->stream));
-    if (guide) TAPE_CK(cudaMemcpyAsync(tp->gin.p, guide, sizeof(float) * n_in, cudaMemcpyDeviceToDevice, den->stream));
     den->share = share;
-    dsgnlm_status s = dsgnlm_build(den, tp->gin.as<float>(), H, W, patch_r, search_r, bandwidth);
+    dsgnlm_status s = dsgnlm_build(den, guide, H, W, patch_r, search_r, bandwidth);
     den->share = 1;
     if (s != DSGNLM_OK) return s;
     if (!den->fast) return DSGNLM_EINVAL;
@@ -863,8 +830,8 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
     tp->taps = make_blur_taps(blur_sigma, blur_r);
     tp->blur_sigma = blur_sigma;
     tp->blur_r = blur_r;
-    tp->y = tp->yin.as<float>();
-    tp->guide = tp->gin.as<float>();
+    tp->y = y;
+    tp->guide = guide;
     TAPE_CK(tp->Dh.ensure(sizeof(float) * n * (T + 1)));
     TAPE_CK(tp->Th.ensure(sizeof(float) * n * (T + 1)));
     TAPE_CK(tp->X.ensure(sizeof(float) * n * (N + 1)));
@@ -904,7 +871,7 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
 // Second half: fixes W on the handle and runs Algorithm 1 one iteration at a time,
 // every state recorded (the same kernels and order of arithmetic as a one-iteration
 // lpnp_solve, with the x-update writing into the next slot).  1/m is read on the
-// device, so nothing here waits for the device either.  x_out (optional) receives x_N.
+// device, so nothing here waits for the device either.  x_out receives x_N.
 dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
     dsgnlm* den = tp->den;
     cudaStream_t st = den->stream;
@@ -958,9 +925,7 @@ dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
         ea.u = u1;
         TAPE_CK(launch_combine_update(0, den->plan, tp->rs, ea, st));
     }
-    if (x_out)
-        TAPE_CK(cudaMemcpyAsync(x_out, tp->X.as<float>() + (size_t)N * n, sizeof(float) * n, cudaMemcpyDeviceToDevice,
-                                st));
+    TAPE_CK(cudaMemcpyAsync(x_out, tp->X.as<float>() + (size_t)N * n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     return DSGNLM_OK;
 }
 
@@ -974,11 +939,9 @@ void forward_settle(lpnp_tape* tp) {
 }
 
 // The reverse sweep, queued on the handle's stream up to the read-back of the scalar
-// cotangents and of the wait-error flag into the tape's pinned words.  x_bar null: the
-// cotangent of x_N is in tp->xh already; y_bar, guide_bar null: the cotangents stay in
-// tp->ybar, tp->gbar (a recorded graph copies in and out around its launch).
+// cotangents and of the wait-error flag into the tape's pinned words.
 dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, float* guide_bar) {
-    if (!tp || !tp->den || !tp->host) return DSGNLM_EINVAL;
+    if (!tp || !tp->den || !tp->host || !x_bar || !y_bar || !guide_bar) return DSGNLM_EINVAL;
     dsgnlm* den = tp->den;
     cudaStream_t st = den->stream;
     const int H = tp->H, W = tp->W, N = tp->N, T = tp->T, rs = tp->rs, rp = tp->rp;
@@ -998,8 +961,6 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
                           std::max((size_t)H * plane_pitch(W), (size_t)(H + 2 * rp) * (W + 2 * rp))));
     const size_t ne = (size_t)(H + 2 * rp) * (W + 2 * rp);
     TAPE_CK(tp->ge.ensure(sizeof(float) * ne));
-    TAPE_CK(tp->ybar.ensure(sizeof(float) * (n / 4)));
-    TAPE_CK(tp->gbar.ensure(sizeof(float) * n));
     const int nb = nblk(n);
     const dim3 pgrid((W + kAdjTW - 1) / kAdjTW, (H + kAdjTH - 1) / kAdjTH);
     const int npb = (int)(pgrid.x * pgrid.y) * kPairSplit;  // pair-pass blocks (with the offset chunks)
@@ -1015,7 +976,7 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
     TAPE_CK(cudaMemsetAsync(tp->gs.p, 0, sizeof(float) * n, st));
     TAPE_CK(cudaMemsetAsync(tp->vh.p, 0, sizeof(float) * n, st));
     TAPE_CK(cudaMemsetAsync(tp->uh.p, 0, sizeof(float) * n, st));
-    if (x_bar) TAPE_CK(cudaMemcpyAsync(tp->xh.p, x_bar, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    TAPE_CK(cudaMemcpyAsync(tp->xh.p, x_bar, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     const float mu = tp->mu, alpha = tp->alpha, rho = tp->rho;
     const float* dT = tp->Dh.as<float>() + (size_t)T * n;
     const float* tT = tp->Th.as<float>() + (size_t)T * n;
@@ -1113,15 +1074,11 @@ dsgnlm_status backward_begin(lpnp_tape* tp, const float* x_bar, float* y_bar, fl
         TAPE_CK(cudaGetLastError());
     }
     adj_fold_kernel<<<dim3((W + 31) / 32, (H + 7) / 8), dim3(32, 8), 0, st>>>(
-        tp->ge.as<float>(), tp->xh.as<float>(), tp->vh.as<float>(), tp->guide, H, W, rp, tp->gbar.as<float>());
+        tp->ge.as<float>(), tp->xh.as<float>(), tp->vh.as<float>(), tp->guide, H, W, rp, guide_bar);
     count_launches(1);
     TAPE_CK(cudaGetLastError());
     // dL/dy = sum_k mu A g_k = A gs
-    TAPE_CK(launch_sr_forward(tp->gs.as<float>(), H, W, tp->taps, nullptr, 0.f, tp->ybar.as<float>(), st));
-    if (y_bar)
-        TAPE_CK(cudaMemcpyAsync(y_bar, tp->ybar.p, sizeof(float) * (n / 4), cudaMemcpyDeviceToDevice, st));
-    if (guide_bar)
-        TAPE_CK(cudaMemcpyAsync(guide_bar, tp->gbar.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    TAPE_CK(launch_sr_forward(tp->gs.as<float>(), H, W, tp->taps, nullptr, 0.f, y_bar, st));
     adj_sum_kernel<<<1, 256, 0, st>>>(tp->rho_part.as<double>(), nrb, mh + 1);
     adj_sum_kernel<<<1, 256, 0, st>>>(tp->h_part.as<double>(), npb, mh + 2);
     count_launches(2);
@@ -1142,141 +1099,6 @@ dsgnlm_status backward_finish(lpnp_tape* tp, double* h_bar, double* rho_bar) {
     return DSGNLM_OK;
 }
 
-// ---------------------------------------------------------------- recorded batches
-
-using Key = std::vector<unsigned long long>;
-
-void key_add(Key& k, const void* p) { k.push_back((unsigned long long)(uintptr_t)p); }
-void key_bytes(Key& k, const void* p, size_t n) {
-    const unsigned char* b = static_cast<const unsigned char*>(p);
-    for (size_t o = 0; o < n; o += 8) {
-        unsigned long long v = 0;
-        std::memcpy(&v, b + o, std::min<size_t>(8, n - o));
-        k.push_back(v);
-    }
-}
-
-// Everything a recorded batch graph bakes into its nodes: the device memory of every
-// tape and handle (buffers, plan, tensor map) and the sizes and scalars of the call.
-// Calls with equal keys launch the same work on the same memory.
-Key batch_key(lpnp_tape* const* tapes, dsgnlm* const* dens, int count, const int* ints, int nints, const float* flts,
-              int nflts) {
-    Key k;
-    k.push_back((unsigned long long)count);
-    for (int i = 0; i < nints; ++i) k.push_back((unsigned long long)(unsigned)ints[i]);
-    key_bytes(k, flts, sizeof(float) * (size_t)nflts);
-    for (int i = 0; i < count; ++i) {
-        const lpnp_tape* t = tapes[i];
-        const DevBuf* bufs[] = {&t->Dh,  &t->Th,   &t->X,    &t->V,     &t->U,      &t->Gr,     &t->AZ,      &t->xh,
-                                &t->vh,  &t->uh,   &t->zh,   &t->g,     &t->gs,     &t->dh[0],  &t->dh0,     &t->base,
-                                &t->thp, &t->Dhat, &t->Gp,   &t->ge,    &t->gb,     &t->ctl,    &t->part,    &t->m,
-                                &t->mkey, &t->sstar, &t->mh, &t->rho_part, &t->h_part, &t->m_part, &t->scratch,
-                                &t->yin, &t->gin,  &t->ybar, &t->gbar};
-        key_add(k, t);
-        for (const DevBuf* b : bufs) {
-            key_add(k, b->p);
-            k.push_back((unsigned long long)b->bytes);
-        }
-        key_add(k, t->host);
-        const int tints[] = {t->H, t->W, t->rp, t->rs, t->T, t->N, t->constraint, t->blur_r};
-        key_bytes(k, tints, sizeof tints);
-        const dsgnlm* h = dens[i];
-        key_add(k, h);
-        key_add(k, h->planes.p);
-        key_add(k, h->tma_part.p);
-        key_add(k, h->err.p);
-        key_add(k, h->z.p);
-        key_add(k, h->partials.p);
-        const int hints[] = {h->H, h->W, h->rs, h->nh, h->dtype, h->plan.tiles_x, h->plan.tiles_y};
-        key_bytes(k, hints, sizeof hints);
-        key_bytes(k, &h->plan.splits, sizeof h->plan.splits);
-        key_bytes(k, h->plan.tmap, sizeof h->plan.tmap);
-        key_add(k, h->plan.partials);
-        key_add(k, (const void*)(uintptr_t)h->wait_budget);
-    }
-    return k;
-}
-
-bool recordable_stream(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
-
-// Runs one batched call: from a recorded graph when one exists for the current key,
-// recording it first when the previous call ended with the same key (every buffer
-// then exists, so the recording allocates nothing); otherwise image by image from the
-// host pool, each image on its handle's stream.  queue(i, recording) queues image i's
-// work on dens[i]->stream (recording: the inputs are staged around the graph launch,
-// not inside it).  The graph runs on dens[0]->stream, with one branch per image
-// (forked from and joined to that stream); stage_in / stage_out queue the copies
-// around its launch there.  `graphed` tells the caller which way the work ran.
-template <class KeyFn, class Queue, class In, class Out>
-dsgnlm_status run_batch(lpnp_tape::Recorded& rec, std::vector<cudaEvent_t>& events, dsgnlm* const* dens, int count,
-                        KeyFn&& keyfn, Queue&& queue, In&& stage_in, Out&& stage_out, bool& graphed) {
-    graphed = false;
-    const Key key = keyfn();
-    cudaStream_t origin = dens[0]->stream;
-    bool can = !rec.failed && recordable_stream(origin);
-    for (int i = 1; i < count && can; ++i) can = recordable_stream(dens[i]->stream);
-    if (can && !(rec.exec && rec.key == key) && rec.last == key) {
-        rec.release();
-        while ((int)events.size() < count + 1) {
-            cudaEvent_t e = nullptr;
-            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) break;
-            events.push_back(e);
-        }
-        if ((int)events.size() >= count + 1 &&
-            cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
-            set_capture_counting(true);
-            cudaError_t e = cudaEventRecord(events[0], origin);
-            for (int i = 1; i < count; ++i)
-                if (e == cudaSuccess && dens[i]->stream != origin) e = cudaStreamWaitEvent(dens[i]->stream, events[0], 0);
-            dsgnlm_status q = e == cudaSuccess ? DSGNLM_OK : DSGNLM_ECUDA;
-            for (int i = 0; i < count && q == DSGNLM_OK; ++i) q = queue(i, true);
-            // every branch joins the origin, also after a failure, so that the capture ends
-            for (int i = 1; i < count; ++i)
-                if (dens[i]->stream != origin && cudaEventRecord(events[i + 1], dens[i]->stream) == cudaSuccess)
-                    cudaStreamWaitEvent(origin, events[i + 1], 0);
-            set_capture_counting(false);
-            cudaGraph_t g = nullptr;
-            const cudaError_t ee = cudaStreamEndCapture(origin, &g);
-            cudaGraphExec_t x = nullptr;
-            if (q == DSGNLM_OK && ee == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
-                rec.graph = g;
-                rec.exec = x;
-                rec.key = key;
-                size_t nn = 0;
-                rec.kernels = 0;
-                if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn) {
-                    std::vector<cudaGraphNode_t> nodes(nn);
-                    cudaGraphNodeType ty;
-                    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
-                        for (cudaGraphNode_t nd : nodes)
-                            if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
-                                ++rec.kernels;
-                }
-            } else {
-                if (g) cudaGraphDestroy(g);
-                rec.failed = true;  // launched directly from now on
-                (void)cudaGetLastError();
-            }
-        }
-    }
-    dsgnlm_status s = DSGNLM_OK;
-    if (can && rec.exec && rec.key == key) {
-        s = stage_in(origin);
-        if (s == DSGNLM_OK) s = tape_ck(cudaGraphLaunch(rec.exec, origin));
-        if (s == DSGNLM_OK) {
-            count_launches((uint64_t)rec.kernels);
-            s = stage_out(origin);
-        }
-        graphed = true;
-    } else {
-        std::vector<dsgnlm_status> st(count, DSGNLM_OK);
-        HostPool::run(count, [&](int i) { st[i] = queue(i, false); });
-        for (int i = 0; i < count && s == DSGNLM_OK; ++i) s = st[i];
-    }
-    rec.last = s == DSGNLM_OK ? keyfn() : Key{};
-    return s;
-}
-
 }  // namespace
 
 extern "C" {
@@ -1284,6 +1106,7 @@ extern "C" {
 dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y, const float* guide, int H, int W,
                                     int patch_r, int search_r, float bandwidth, int balance_passes, float alpha,
                                     float rho, int iters, float blur_sigma, int blur_r, float* x_out) {
+    NvtxRange nvtx_range("lpnp_unrolled_forward");
     if (!x_out || !y || !guide) return DSGNLM_EINVAL;
     dsgnlm_status s = forward_begin(tp, den, y, guide, H, W, patch_r, search_r, bandwidth, balance_passes, alpha, rho,
                                     iters, blur_sigma, blur_r, 1);
@@ -1299,63 +1122,37 @@ dsgnlm_status lpnp_unrolled_forward_batched(lpnp_tape_t* tapes, dsgnlm_t* dens, 
                                             const float* const* guide, int H, int W, int patch_r, int search_r,
                                             float bandwidth, int balance_passes, float alpha, float rho, int iters,
                                             float blur_sigma, int blur_r, float* const* x_out) {
+    NvtxRange nvtx_range("lpnp_unrolled_forward_batched");
     if (!tapes || !dens || !y || !guide || !x_out || count < 1) return DSGNLM_EINVAL;
     for (int i = 0; i < count; ++i) {
         if (!tapes[i] || !dens[i] || !x_out[i] || !y[i] || !guide[i]) return DSGNLM_EINVAL;
         for (int j = 0; j < i; ++j)
             if (tapes[j] == tapes[i] || dens[j] == dens[i]) return DSGNLM_EINVAL;
     }
-    const size_t n = (size_t)H * W;
-    const int ints[] = {H, W, patch_r, search_r, balance_passes, iters, blur_r};
-    const float flts[] = {bandwidth, alpha, rho, blur_sigma};
-    auto keyfn = [&] { return batch_key(tapes, dens, count, ints, 7, flts, 4); };
-    // every image's weights, balance and iterations, on its handle's stream; nothing
-    // waits for the device (1/m is read there)
-    auto queue = [&](int i, bool recording) {
-        dsgnlm_status s = forward_begin(tapes[i], dens[i], recording ? nullptr : y[i], recording ? nullptr : guide[i],
-                                        H, W, patch_r, search_r, bandwidth, balance_passes, alpha, rho, iters,
-                                        blur_sigma, blur_r, count);
-        return s == DSGNLM_OK ? forward_finish(tapes[i], recording ? nullptr : x_out[i]) : s;
-    };
-    auto stage_in = [&](cudaStream_t o) {
-        for (int i = 0; i < count; ++i) {
-            TAPE_CK(cudaMemcpyAsync(tapes[i]->yin.p, y[i], sizeof(float) * (n / 4), cudaMemcpyDeviceToDevice, o));
-            TAPE_CK(cudaMemcpyAsync(tapes[i]->gin.p, guide[i], sizeof(float) * n, cudaMemcpyDeviceToDevice, o));
-        }
-        return DSGNLM_OK;
-    };
-    auto stage_out = [&](cudaStream_t o) {
-        for (int i = 0; i < count; ++i)
-            TAPE_CK(cudaMemcpyAsync(x_out[i], tapes[i]->X.as<float>() + (size_t)tapes[i]->N * n, sizeof(float) * n,
-                                    cudaMemcpyDeviceToDevice, o));
-        return DSGNLM_OK;
-    };
-    bool graphed = false;
-    dsgnlm_status s = run_batch(tapes[0]->fwd, tapes[0]->events, dens, count, keyfn, queue, stage_in, stage_out,
-                                graphed);
+    // each image's weights, balance and iterations, queued from the host pool's threads
+    // on its handle's stream; nothing waits for the device (1/m is read there)
+    std::vector<dsgnlm_status> st(count, DSGNLM_OK);
+    HostPool::run(count, [&](int i) {
+        st[i] = forward_begin(tapes[i], dens[i], y[i], guide[i], H, W, patch_r, search_r, bandwidth, balance_passes,
+                              alpha, rho, iters, blur_sigma, blur_r, count);
+        if (st[i] == DSGNLM_OK) st[i] = forward_finish(tapes[i], x_out[i]);
+    });
     // nothing of the batch is left running on the caller's buffers, and m reaches the host
+    dsgnlm_status s = DSGNLM_OK;
+    for (int i = 0; i < count; ++i)
+        if (s == DSGNLM_OK) s = st[i];
     for (int j = 0; j < count; ++j) {
         const cudaError_t e = cudaStreamSynchronize(dens[j]->stream);
         if (s == DSGNLM_OK) s = tape_ck(e);
     }
     if (s != DSGNLM_OK) return s;
-    for (int i = 0; i < count; ++i) {
-        if (graphed) {  // the handle holds this tape's W (as forward_finish leaves it)
-            dsgnlm* d = dens[i];
-            lpnp_tape* t = tapes[i];
-            d->d_final = t->Dh.as<float>() + (size_t)t->T * n;
-            d->t_final = t->Th.as<float>() + (size_t)t->T * n;
-            d->iters = t->T;
-            d->balanced = true;
-            d->inv_m_dev = false;
-        }
-        forward_settle(tapes[i]);
-    }
+    for (int i = 0; i < count; ++i) forward_settle(tapes[i]);
     return DSGNLM_OK;
 }
 
 dsgnlm_status lpnp_backward(lpnp_tape_t tp, const float* x_bar, float* y_bar, float* guide_bar, double* h_bar,
                             double* rho_bar) {
+    NvtxRange nvtx_range("lpnp_backward");
     if (!x_bar || !y_bar || !guide_bar) return DSGNLM_EINVAL;
     dsgnlm_status s = backward_begin(tp, x_bar, y_bar, guide_bar);
     if (s != DSGNLM_OK) {
@@ -1367,44 +1164,21 @@ dsgnlm_status lpnp_backward(lpnp_tape_t tp, const float* x_bar, float* y_bar, fl
 
 dsgnlm_status lpnp_backward_batched(lpnp_tape_t* tapes, int count, const float* const* x_bar, float* const* y_bar,
                                     float* const* guide_bar, double* h_bar, double* rho_bar) {
+    NvtxRange nvtx_range("lpnp_backward_batched");
     if (!tapes || !x_bar || !y_bar || !guide_bar || count < 1) return DSGNLM_EINVAL;
-    std::vector<dsgnlm*> dens(count);
     for (int i = 0; i < count; ++i) {
-        if (!tapes[i] || !tapes[i]->den || !x_bar[i] || !y_bar[i] || !guide_bar[i]) return DSGNLM_EINVAL;
+        if (!tapes[i]) return DSGNLM_EINVAL;
         for (int j = 0; j < i; ++j)
-            if (tapes[j] == tapes[i] || tapes[j]->den == tapes[i]->den) return DSGNLM_EINVAL;
-        dens[i] = tapes[i]->den;
+            if (tapes[j] == tapes[i]) return DSGNLM_EINVAL;
     }
-    const lpnp_tape* t0 = tapes[0];
-    const float flts[] = {t0->h, t0->alpha, t0->rho, t0->mu, t0->c, t0->blur_sigma};
-    auto keyfn = [&] { return batch_key(tapes, dens.data(), count, nullptr, 0, flts, 6); };
-    auto queue = [&](int i, bool recording) {
-        return backward_begin(tapes[i], recording ? nullptr : x_bar[i], recording ? nullptr : y_bar[i],
-                              recording ? nullptr : guide_bar[i]);
-    };
-    auto stage_in = [&](cudaStream_t o) {
-        for (int i = 0; i < count; ++i) {
-            const size_t n = (size_t)tapes[i]->H * tapes[i]->W;
-            TAPE_CK(cudaMemcpyAsync(tapes[i]->xh.p, x_bar[i], sizeof(float) * n, cudaMemcpyDeviceToDevice, o));
+    std::vector<dsgnlm_status> st(count, DSGNLM_OK);
+    HostPool::run(count, [&](int i) { st[i] = backward_begin(tapes[i], x_bar[i], y_bar[i], guide_bar[i]); });
+    for (int i = 0; i < count; ++i)
+        if (st[i] != DSGNLM_OK) {
+            for (int j = 0; j < count; ++j)  // nothing left in flight
+                if (tapes[j]->den) cudaStreamSynchronize(tapes[j]->den->stream);
+            return st[i];
         }
-        return DSGNLM_OK;
-    };
-    auto stage_out = [&](cudaStream_t o) {
-        for (int i = 0; i < count; ++i) {
-            const size_t n = (size_t)tapes[i]->H * tapes[i]->W;
-            TAPE_CK(cudaMemcpyAsync(y_bar[i], tapes[i]->ybar.p, sizeof(float) * (n / 4), cudaMemcpyDeviceToDevice, o));
-            TAPE_CK(cudaMemcpyAsync(guide_bar[i], tapes[i]->gbar.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, o));
-        }
-        return DSGNLM_OK;
-    };
-    bool graphed = false;
-    dsgnlm_status s = run_batch(tapes[0]->bwd, tapes[0]->events, dens.data(), count, keyfn, queue, stage_in,
-                                stage_out, graphed);
-    for (int j = 0; j < count; ++j) {  // nothing left in flight; the pinned words are final
-        const cudaError_t e = cudaStreamSynchronize(dens[j]->stream);
-        if (s == DSGNLM_OK) s = tape_ck(e);
-    }
-    if (s != DSGNLM_OK) return s;
     dsgnlm_status first = DSGNLM_OK;
     for (int i = 0; i < count; ++i) {
         dsgnlm_status r = backward_finish(tapes[i], h_bar ? h_bar + i : nullptr, rho_bar ? rho_bar + i : nullptr);

@@ -201,12 +201,10 @@ def test_batched_split_for_the_batch(gpu_lib):
     assert abs(rb - rs_) <= 1e-5 * abs(rs_)
 
 
-def test_batched_graph_replay_follows_new_inputs(gpu_lib):
-    """Repeated batched calls with equal sizes and parameters are recorded as CUDA
-    graphs (the backward on its second call, the forward on its third) and replayed
-    with the inputs copied in and the outputs copied out around the launch.  Every
-    call, direct or replayed, gives the single-image results on its own inputs bit
-    for bit, also when the inputs change from call to call."""
+def test_batched_repeated_calls_follow_new_inputs(gpu_lib):
+    """Repeated batched calls on pooled tapes and handles, with new inputs every call:
+    each gives the single-image results on its own inputs bit for bit, and launches
+    the same number of kernels."""
     from paper_1901_06110_gb300 import dsgnlm as D
     from paper_1901_06110_gb300.autograd import UnrollParams, UnrolledSR, unrolled_sr
     H, W, B = 32, 48, 3
@@ -231,5 +229,4 @@ def test_batched_graph_replay_follows_new_inputs(gpu_lib):
             assert np.array_equal(ggb[b], singles[b][2]), (call, b)
         assert hb == sum(s[3] for s in singles)
         assert rb == sum(s[4] for s in singles)
-    # a replay counts the kernels of its graph: the same number as a direct call
     assert len(set(launches)) == 1, launches

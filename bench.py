@@ -54,7 +54,7 @@ def _args():
                     help="leave out Table 1 in synthetic form (one fast DSG-NLM filtering of a 256x256 image "
                          "for patch sizes 11-29 and both readings of N_s = 21; in the CPU-baseline leg, the "
                          "brute-force oracle on a 64x64 crop)")
-    ap.add_argument("--profile-case", choices=["batched-f16-4x512", "unrolled-1x256"], default=None,
+    ap.add_argument("--profile-case", choices=["batched-f16-4x512", "unrolled-1x256", "unrolled-8x256"], default=None,
                     help="run one small case twice for an ncu capture (no timing, no JSON line)")
     ap.add_argument("--only-batched", default=None,
                     help="comma-separated batched variants to time alone (plain_f32, batched_f32, batched_f16, "
@@ -1194,13 +1194,19 @@ def run_profile_case(case: str):
         from paper_1901_06110_gb300.autograd import UnrollParams, unrolled_sr
         wl = synthetic.workload("unroll8x256")
         H, W = wl["H"], wl["W"]
-        xt = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], wl["seed"])).cuda()
-        nz = torch.from_numpy(synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], wl["seed"])).cuda()
-        y0 = D.lpnp_sr_observe(xt, nz, wl["blur_sigma"], wl["blur_r"])
-        g0 = D.lpnp_sr_guide(y0)
+        B = wl["count"] if case == "unrolled-8x256" else 1
+        xs, ys = [], []
+        for b in range(B):
+            xt = torch.from_numpy(synthetic.ground_truth(H, W, wl["n_shapes"], wl["texture"], wl["seed"] + b)).cuda()
+            nz = torch.from_numpy(synthetic.gaussian_noise((H // 2, W // 2), wl["noise_sigma"], wl["seed"] + b)).cuda()
+            xs.append(xt)
+            ys.append(D.lpnp_sr_observe(xt, nz, wl["blur_sigma"], wl["blur_r"]))
+        xt = torch.stack(xs)
+        y0 = torch.stack(ys)
+        g0 = torch.stack([D.lpnp_sr_guide(yy) for yy in ys])
         for _ in range(2):
-            y = y0[None].clone().requires_grad_(True)
-            g = g0[None].clone().requires_grad_(True)
+            y = y0.clone().requires_grad_(True)
+            g = g0.clone().requires_grad_(True)
             h = torch.tensor(wl["h"], dtype=torch.float64, requires_grad=True)
             rho = torch.tensor(wl["rho"], dtype=torch.float64, requires_grad=True)
             x = unrolled_sr(y, g, h, rho, UnrollParams(patch_r=wl["patch_r"], search_r=wl["search_r"],

@@ -377,10 +377,11 @@ void lpnp_tape_destroy(lpnp_tape_t t);
  * lpnp_backward.  x_out device [H][W] receives x_N.  Records the tape (replacing any
  * earlier recording).  `den` must not be rebuilt before the backward.  The shared memory of the backward limits (2 iters + 1)(16 + N_s)(32 + 2 N_s)
  * and (2 passes + 1)(16 + N_s)(32 + 2 N_s) floats to 220 KiB (EINVAL otherwise).
- * m and 1/m are formed and read on the device; the call synchronises the stream once,
- * at its end (the handle then also holds m and 1/m on the host).  The iterations run
- * their own kernels (the x-update of each writes the next recorded state), not
- * lpnp_solve's graph. */
+ * m and 1/m are formed and read on the device, so the call queues all of its work
+ * without waiting for the device (on an error it drains the stream first); the
+ * handle reads m and 1/m back when a later call on it needs them on the host.  The
+ * iterations run their own kernels (the x-update of each writes the next recorded
+ * state), not lpnp_solve's graph. */
 dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tape, dsgnlm_t den, const float* y, const float* guide, int H,
                                     int W, int patch_r, int search_r, float bandwidth, int balance_passes,
                                     float alpha, float rho, int iters, float blur_sigma, int blur_r, float* x_out);
@@ -401,9 +402,10 @@ dsgnlm_status lpnp_backward(lpnp_tape_t tape, const float* x_bar, float* y_bar, 
  * guide, x_out (and x_bar, y_bar, guide_bar) are host arrays of `count` device
  * pointers with the layouts of the single-image calls.  The images are queued from a
  * pool of host threads, one image per thread at a time; no image waits for the
- * device while it is queued (m and 1/m are formed and read on the device).  Each call
- * synchronises the streams of the batch once, at its end.  h_bar and rho_bar (host,
- * optional) receive `count` per-image values.
+ * device while it is queued (m and 1/m are formed and read on the device).  The
+ * forward returns without waiting for the device; the backward synchronises each
+ * stream once, at its end.  h_bar and rho_bar (host, optional) receive `count`
+ * per-image values.
  * Each handle's offset split (the slices of phase 1) is sized for `count` images at
  * once, so results equal the single-image calls up to the order in which W's partial
  * sums are added (bit for bit where the split is the same), and repeated calls give

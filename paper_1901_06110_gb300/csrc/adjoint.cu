@@ -670,7 +670,6 @@ struct lpnp_tape {
     float blur_sigma = 1.f;
     DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, gs, dh[1], dh0, base, thp, Dhat, Gp, ge, gb, ctl,
         part, m, mkey, sstar, mh, rho_part, h_part, m_part, scratch;
-    float inv_m = 1.f;  // host copy of 1/m, valid after the forward call has returned
     // m and 1/m on the device (written by the forward, read by the kernels that follow)
     const float* inv_m_dev() const { return m.as<float>() + 1; }
     // pinned host words read back after the stream work: m, the scalar cotangents and
@@ -864,7 +863,6 @@ dsgnlm_status forward_begin(lpnp_tape* tp, dsgnlm* den, const float* y, const fl
     adj_m_finish_kernel<<<1, 1, 0, st>>>(tp->mkey.as<unsigned long long>(), tp->m.as<float>(), tp->sstar.as<int>());
     count_launches(2);
     TAPE_CK(cudaGetLastError());
-    TAPE_CK(cudaMemcpyAsync(&tp->host->m, tp->m.p, sizeof(float), cudaMemcpyDeviceToHost, st));
     return DSGNLM_OK;
 }
 
@@ -877,12 +875,14 @@ dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
     cudaStream_t st = den->stream;
     const size_t n = (size_t)tp->H * tp->W;
     const int T = tp->T, N = tp->N;
-    // the handle now holds this W (its host copies of m and 1/m: forward_settle)
+    // the handle now holds this W; its m and 1/m stay on the device until a host-side
+    // use of the handle reads them back
     den->d_final = tp->Dh.as<float>() + (size_t)T * n;
     den->t_final = tp->Th.as<float>() + (size_t)T * n;
     den->iters = T;
     den->balanced = true;
     den->inv_m_dev = false;  // the balance control block does not hold this W's 1/m
+    den->m_pending = tp->m.as<float>();
     TAPE_CK(launch_init(tp->guide, (int)n, tp->X.as<float>(), tp->V.as<float>(), tp->U.as<float>(), st));
     // Algorithm 1, one iteration at a time from slot k into slot k + 1: the x-update
     // (recording grad f(x_k)), then W z and the dual step in place on slot k + 1
@@ -927,15 +927,6 @@ dsgnlm_status forward_finish(lpnp_tape* tp, float* x_out) {
     }
     TAPE_CK(cudaMemcpyAsync(x_out, tp->X.as<float>() + (size_t)N * n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     return DSGNLM_OK;
-}
-
-// After the forward's device work has finished: the host copies of m and 1/m (the
-// same values the device formed) on the tape and the handle.
-void forward_settle(lpnp_tape* tp) {
-    const float mval = tp->host->m;
-    tp->inv_m = (float)(1.0 / (double)mval);
-    tp->den->m = mval;
-    tp->den->inv_m = tp->inv_m;
 }
 
 // The reverse sweep, queued on the handle's stream up to the read-back of the scalar
@@ -1111,10 +1102,7 @@ dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tp, dsgnlm_t den, const float* y
     dsgnlm_status s = forward_begin(tp, den, y, guide, H, W, patch_r, search_r, bandwidth, balance_passes, alpha, rho,
                                     iters, blur_sigma, blur_r, 1);
     if (s == DSGNLM_OK) s = forward_finish(tp, x_out);
-    // nothing is left running on the inputs, and m reaches the host
-    const cudaError_t e = den ? cudaStreamSynchronize(den->stream) : cudaSuccess;
-    if (s == DSGNLM_OK) s = tape_ck(e);
-    if (s == DSGNLM_OK) forward_settle(tp);
+    if (s != DSGNLM_OK && den) cudaStreamSynchronize(den->stream);  // nothing left running on the inputs
     return s;
 }
 
@@ -1137,16 +1125,12 @@ dsgnlm_status lpnp_unrolled_forward_batched(lpnp_tape_t* tapes, dsgnlm_t* dens, 
                               alpha, rho, iters, blur_sigma, blur_r, count);
         if (st[i] == DSGNLM_OK) st[i] = forward_finish(tapes[i], x_out[i]);
     });
-    // nothing of the batch is left running on the caller's buffers, and m reaches the host
-    dsgnlm_status s = DSGNLM_OK;
     for (int i = 0; i < count; ++i)
-        if (s == DSGNLM_OK) s = st[i];
-    for (int j = 0; j < count; ++j) {
-        const cudaError_t e = cudaStreamSynchronize(dens[j]->stream);
-        if (s == DSGNLM_OK) s = tape_ck(e);
-    }
-    if (s != DSGNLM_OK) return s;
-    for (int i = 0; i < count; ++i) forward_settle(tapes[i]);
+        if (st[i] != DSGNLM_OK) {
+            // on a failure, nothing of the batch is left running on the caller's buffers
+            for (int j = 0; j < count; ++j) cudaStreamSynchronize(dens[j]->stream);
+            return st[i];
+        }
     return DSGNLM_OK;
 }
 

@@ -185,12 +185,26 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
         h->fast = true;
     }
     h->built = true;
+    h->m_pending = nullptr;
     return DSGNLM_OK;
 }
 
 }  // extern "C"
 
 namespace {
+
+// m and 1/m of a W whose balance ran elsewhere (m_pending): read back once, when a
+// call first needs them on the host.
+dsgnlm_status settle_m(dsgnlm* h) {
+    if (!h->m_pending) return DSGNLM_OK;
+    float mm[2] = {1.f, 1.f};
+    DSG_CK(cudaStreamSynchronize(h->stream));
+    DSG_CK(cudaMemcpy(mm, h->m_pending, sizeof mm, cudaMemcpyDeviceToHost));
+    h->m = mm[0];
+    h->inv_m = mm[1];
+    h->m_pending = nullptr;
+    return DSGNLM_OK;
+}
 
 // A phase-1 wait gave up during the call: clear the error word (so that the next
 // call starts clean) and report it.
@@ -384,6 +398,7 @@ dsgnlm_status dsgnlm_balance(dsgnlm_t h, double tol, int maxit, int* iters_out, 
     h->d_final = h->dbuf[c.final_pass & 1].as<float>();
     h->m = m;
     h->inv_m = (float)(1.0 / m);
+    h->m_pending = nullptr;
     h->inv_m_dev = h->fast;  // the TMA path's control block holds the same 1/m
     h->iters = c.final_pass;
     h->resid = eps;
@@ -524,6 +539,7 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
         h->d_final = h->dbuf[c.final_pass & 1].as<float>();
         h->m = c.m;
         h->inv_m = (float)(1.0 / c.m);
+        h->m_pending = nullptr;
         h->inv_m_dev = true;
         h->iters = c.final_pass;
         h->resid = c.eps;
@@ -540,6 +556,10 @@ dsgnlm_status dsgnlm_apply(dsgnlm_t h, const float* x, float* y) {
     if (!h || !x || !y || x == y || !aligned16(x) || !aligned16(y)) return DSGNLM_EINVAL;
     if (!h->built) return DSGNLM_NOT_BUILT;
     if (!h->balanced) return DSGNLM_NOT_BALANCED;
+    {
+        const dsgnlm_status ms = settle_m(h);
+        if (ms != DSGNLM_OK) return ms;
+    }
     DSG_CK(h->timed(DSGNLM_PROF_APPLY, [&] {
         if (h->fast) {
             cudaError_t e = launch_tma_gather(h->dtype, h->plan, h->H, h->W, h->rs, h->d_final, x,
@@ -596,6 +616,10 @@ dsgnlm_status dsgnlm_copy_scaling(dsgnlm_t h, float* d_dst, double* m_host) {
     if (!h) return DSGNLM_EINVAL;
     if (!h->built) return DSGNLM_NOT_BUILT;
     if (!h->balanced) return DSGNLM_NOT_BALANCED;
+    {
+        const dsgnlm_status ms = settle_m(h);
+        if (ms != DSGNLM_OK) return ms;
+    }
     if (d_dst)
         DSG_CK(cudaMemcpyAsync(d_dst, h->d_final, sizeof(float) * (size_t)h->H * h->W,
                                cudaMemcpyDeviceToDevice, h->stream));
@@ -690,6 +714,8 @@ dsgnlm_status check_problem(const lpnp_problem* p, bool for_solve, bool need_w =
     } else {
         return DSGNLM_EINVAL;
     }
+    // a W balanced by the unrolled forward: its m and 1/m are needed on the host
+    if (for_solve && need_w) return settle_m(p->den);
     return DSGNLM_OK;
 }
 

@@ -75,6 +75,10 @@ struct dsgnlm {
     DevBuf tma_part, tbuf[2], err, bal_part;
     // cycles a phase-1 consumer waits for a plane before giving up (dsgnlm_set_wait_budget)
     long long wait_budget = dsg::kDefaultWaitBudget;
+    // device (m, 1/m) of a W balanced outside this handle's own balance (the unrolled
+    // forward of the differentiable form), read back to m and inv_m on the first call
+    // that needs them on the host; null when m and inv_m are current
+    const float* m_pending = nullptr;
     // update rule of dsgnlm_balance / dsgnlm_balance_batched (dsgnlm_set_balance_scheme)
     int balance_scheme = DSGNLM_BALANCE_SINKHORN;
     float* t_final = nullptr;

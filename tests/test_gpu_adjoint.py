@@ -230,3 +230,36 @@ def test_batched_repeated_calls_follow_new_inputs(gpu_lib):
         assert hb == sum(s[3] for s in singles)
         assert rb == sum(s[4] for s in singles)
     assert len(set(launches)) == 1, launches
+
+
+def test_handle_after_unrolled_forward_applies_its_w(gpu_lib):
+    """The unrolled forward leaves its W on the handle, with m and 1/m formed on the
+    device; a later host-side call on the handle (apply, copy of the scaling) reads
+    them back and applies the W of Eqs. S1-S3 after exactly T balancing passes."""
+    from oracle import dsgnlm as odsg
+    from paper_1901_06110_gb300 import dsgnlm as D
+    from paper_1901_06110_gb300.autograd import UnrollParams, UnrolledSR
+    H, W, rp, rs, T, N = 24, 32, 2, 3, 2, 2
+    wl, inst, guide = _case(H, W, 17)
+    params = UnrollParams(patch_r=rp, search_r=rs, balance_passes=T, iters=N)
+    slot_x = UnrolledSR.apply(cuda(inst["y"]), cuda(guide), 0.1, 1.0, params)
+    torch.cuda.synchronize()
+    from paper_1901_06110_gb300 import autograd as A
+    lib = A._abi.load()
+    tp = A._Slot()
+    x_out = torch.empty((H, W), device="cuda")
+    y = cuda(inst["y"])
+    g = cuda(guide)
+    D._check(lib.lpnp_unrolled_forward(tp.ptr, tp.den.handle, y.data_ptr(), g.data_ptr(), H, W, rp, rs, 0.1, T, 1.0,
+                                       1.0, N, 1.0, 4, x_out.data_ptr()), "lpnp_unrolled_forward")
+    tp.den.H, tp.den.W = H, W
+    K1 = odsg.kernel_matrix(guide.astype(np.float64), rp, rs, 0.1)
+    d_o, _, _ = odsg.sinkhorn(K1, 0.0, T)
+    W_o, m_o = odsg.dsg_matrix(K1, d_o)
+    d, m = D.dsgnlm_copy_scaling(tp.den)
+    assert abs(m - m_o) <= 1e-5 * m_o
+    np.testing.assert_allclose(host(d).ravel(), d_o, rtol=1e-5)
+    z = np.random.default_rng(5).uniform(0, 1, (H, W)).astype(np.float32)
+    out = host(D.dsgnlm_apply(tp.den, cuda(z)))
+    assert rel_l2(out, odsg.denoise(W_o, z.astype(np.float64))) <= 1e-5
+    np.testing.assert_array_equal(host(x_out), host(slot_x))

@@ -34,6 +34,10 @@ CASES = [
     (26, 29, 2, 9, 0.1),    # radius without a compiled TMA kernel: generic gather path
     (40, 300, 3, 10, 0.08),  # three column tiles, ragged, split offsets
     (30, 48, 14, 3, 0.3),    # largest patch (29 x 29): generic-radius build
+    (36, 150, 5, 10, 0.1),   # Table 1 patch sizes (11, 17, 23) with the 21x21 window
+    (40, 140, 8, 10, 0.1),
+    (34, 136, 11, 10, 0.1),
+    (48, 56, 5, 21, 0.1),    # Table 1's 43x43 reading of N_s = 21: generic gather path
 ]
 
 
@@ -243,3 +247,43 @@ def test_balance_scheme_argument(gpu_lib):
     den = D.dsgnlm_create("f32")
     assert den.lib.dsgnlm_set_balance_scheme(den.handle, 2) == _abi.EINVAL
     assert den.lib.dsgnlm_set_balance_scheme(None, 0) == _abi.EINVAL
+
+
+@pytest.mark.parametrize("rp,rs", [(5, 10), (8, 10), (11, 10), (14, 10), (5, 21), (14, 21)])
+def test_table1_configurations_at_256(gpu_lib, rp, rs):
+    """The configurations of Table 1 (patch sizes 11-29, the 21x21 and 43x43 readings of
+    N_s = 21) on a 256x256 image: stored weights at sampled pixels against oracle kernel
+    rows, then the paper's one normalisation (maxit = 1, Eq. S2) with the closure of
+    Eq. S3: row sums of W = 1 and W z at sampled pixels against the rows of W."""
+    from paper_1901_06110_gb300 import dsgnlm as D
+    g = _guide(256, 256, 20)
+    h = 0.1
+    den = _gpu_den(gpu_lib, g, rp, rs, h)
+    planes = D.dsgnlm_copy_weights(den)
+    offs = half_offsets(rs)
+    rng = np.random.default_rng(rp * 100 + rs)
+    pts = [(0, 0), (255, 255), (0, 255), (128, 3), (250, 128)]
+    pts += [(int(a), int(b)) for a, b in zip(rng.integers(0, 256, 7), rng.integers(0, 256, 7))]
+    rows = {}
+    for (i, j) in pts:
+        row = odsg.kernel_row(g.astype(np.float64), rp, rs, h, (i, j))
+        rows[(i, j)] = row
+        got = host(planes[:, i, j])
+        for k, (oy, ox) in enumerate(offs):
+            want = row.get((i + oy, j + ox), 0.0)
+            assert abs(got[k] - want) <= 1e-5 * want + 2e-7, (rp, rs, i, j, oy, ox, got[k], want)
+    D.dsgnlm_balance(den, 0.0, 1)
+    ones = torch.ones((256, 256), device="cuda")
+    np.testing.assert_allclose(host(D.dsgnlm_apply(den, ones)), 1.0, atol=1e-6)
+    # W z at sampled pixels from the oracle's rows: with d = g^(-1/2) (one update),
+    # W_sr = d_s d_r K1_sr / m for r != s and the diagonal closed to a row sum of 1
+    d, m = D.dsgnlm_copy_scaling(den)
+    dh = host(d)
+    z = np.random.default_rng(7).uniform(0, 1, (256, 256)).astype(np.float32)
+    y = host(D.dsgnlm_apply(den, cuda(z)))
+    for (i, j), row in rows.items():
+        gs = sum(row.values())
+        assert abs(dh[i, j] - gs ** -0.5) <= 1e-5 * gs ** -0.5
+        off = {r: dh[i, j] * dh[r] * val / m for r, val in row.items() if r != (i, j)}
+        want = sum(w * z[r] for r, w in off.items()) + (1.0 - sum(off.values())) * z[i, j]
+        assert abs(y[i, j] - want) <= 1e-5 * abs(want) + 1e-6, (rp, rs, i, j)

@@ -65,13 +65,24 @@ __device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16* p, const fl
     *reinterpret_cast<uint2*>(p) = u;
 }
 
-// RP >= 0: patch radius known at compile time; RP < 0: runtime radius rp_rt.
-template <typename WT, int RP>
+// 2^x by the hardware's approximate base-2 exponential (relative error about 2^-22)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// RP >= 0: patch radius known at compile time; RP < 0: runtime radius rp_rt.  RS >= 0:
+// search radius known at compile time (the staged guide's row stride and every
+// shared-memory address offset of the vertical sums are then constants); RS < 0:
+// runtime radius rs_rt.
+template <typename WT, int RP, int RS>
 __global__ void __launch_bounds__(kThreads, RP < 0 ? 1 : (RP <= 5 ? 6 : 3))
-build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, float c, int chunk,
+build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt, float c2, int chunk,
              WT* __restrict__ planes) {
     extern __shared__ __align__(16) float smem[];
     const int rp = RP >= 0 ? RP : rp_rt;
+    const int rs = RS >= 0 ? RS : rs_rt;
     const int nh = num_half_offsets(rs);
     const int y0 = blockIdx.y * kTH;
     const int x0 = blockIdx.x * kTW;
@@ -107,6 +118,8 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
     const int Wp = plane_pitch(W);
     const size_t plane = (size_t)H * Wp;
     const float inv_hat = 1.0f / (float)(rs + 1);
+    // the weight Lambda(o) exp(-D c) as one base-2 exponential: 2^(log2 Lambda(o) - D c
+    // log2 e), with c2 = c log2 e from the host and log2 Lambda(o) once per offset
     const int n_vtask = EW * (kTH / kSeg);
     // V(i, cc) = sum_{t_y} (g(i + t_y, cc - rp) - g(i + t_y + o_y, cc - rp + o_x))^2 for the
     // tile's rows: one column and 8 consecutive output rows per task, as a sliding
@@ -169,7 +182,10 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
         float* Vn = ((k - k_begin) & 1) ? V0 : V1;
         if (k + 1 < k_end) vertical(oy1, ox1, Vn);  // in the same interval as the sums below
         // D(i, j) = sum_{t_x} V(i, j + t_x), then the weight
-        const float hat = (1.0f - fabsf((float)oy) * inv_hat) * (1.0f - fabsf((float)ox) * inv_hat);
+        const float lhat = log2f(1.0f - fabsf((float)oy) * inv_hat) + log2f(1.0f - fabsf((float)ox) * inv_hat);
+        // columns whose partner j + o_x lies inside the image, and the rows whose partner does
+        const int jlo = ox < 0 ? -ox : 0, jhi = ox > 0 ? W - ox : W;
+        const int ihi = H - oy;
         WT* out = planes + (size_t)k * plane;
 #pragma unroll
         for (int rr = 0; rr < kTH / 16; ++rr) {
@@ -193,11 +209,11 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
                 D += v[t];
             }
             float w[kHW];
-            if (interior) {
+            if (interior || (i < ihi && j0 >= jlo && j0 + kHW <= jhi)) {
 #pragma unroll
                 for (int jj = 0; jj < kHW; ++jj) {
                     if (jj > 0) D += v[jj + 2 * rp] - v[jj - 1];
-                    w[jj] = hat * __expf(-D * c);
+                    w[jj] = ex2_approx(fmaf(D, -c2, lhat));
                 }
                 store4<WT>(out + (size_t)i * Wp + j0, w);
             } else {
@@ -206,7 +222,7 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
                     if (jj > 0) D += v[jj + 2 * rp] - v[jj - 1];
                     const int j = j0 + jj;
                     const bool inside = i < H && j < W && j + ox >= 0 && j + ox < W && i + oy < H;
-                    w[jj] = inside ? hat * __expf(-D * c) : 0.f;
+                    w[jj] = inside ? ex2_approx(fmaf(D, -c2, lhat)) : 0.f;
                 }
                 // planes have a pitch of a multiple of 8: the 4 outputs are all inside the
                 // row's pitch or all outside it
@@ -220,7 +236,7 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs, f
     }
 }
 
-template <typename WT, int RP>
+template <typename WT, int RP, int RS>
 cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, float c, WT* planes,
                             cudaStream_t st) {
     const int nh = num_half_offsets(rs);
@@ -228,14 +244,15 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
     const int GH = kTH + 2 * rp + rs, GW = kTW + 2 * rp + 2 * rs;
     const size_t smem = sizeof(float) * (size_t)(GH * GW + 2 * kTH * v_pitch(rp)) + sizeof(int) * (GH + GW);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(build_kernel<WT, RP>,
+        cudaError_t e = cudaFuncSetAttribute(build_kernel<WT, RP, RS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     // offsets per CTA: the chunk that makes the fewest waves of resident CTAs take the
     // least time (each CTA also stages its guide tile, worth about two offsets)
     int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_kernel<WT, RP>, kThreads, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_kernel<WT, RP, RS>, kThreads, smem) !=
+            cudaSuccess ||
         cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return cudaGetLastError();
     const long long slots = per_sm * sms > 0 ? (long long)per_sm * sms : 1;
@@ -251,24 +268,40 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
         }
     }
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, (nh + chunk - 1) / chunk);
-    build_kernel<WT, RP><<<grid, kThreads, smem, st>>>(guide, H, W, rp, rs, c, chunk, planes);
+    const float c2 = (float)((double)c * 1.4426950408889634);  // c log2 e: the exponent in base 2
+    build_kernel<WT, RP, RS><<<grid, kThreads, smem, st>>>(guide, H, W, rp, rs, c2, chunk, planes);
     count_launches(1);
     return cudaGetLastError();
+}
+
+// Search radii with their own instantiations: the windows of the workloads (11x11,
+// 15x15, 21x21) for the patch sizes they use, and the 21x21 window for every patch size
+// of Table 1; other radii take the runtime-radius form.
+template <typename WT, int RP>
+cudaError_t launch_build_rs(const float* guide, int H, int W, int rp, int rs, float c, WT* planes, cudaStream_t st) {
+    if constexpr (RP == 2) {
+        if (rs == 5) return launch_build_rp<WT, RP, 5>(guide, H, W, rp, rs, c, planes, st);
+        if (rs == 7) return launch_build_rp<WT, RP, 7>(guide, H, W, rp, rs, c, planes, st);
+    }
+    if constexpr (RP == 3 || RP == 5 || RP == 8 || RP == 11 || RP == 14) {
+        if (rs == 10) return launch_build_rp<WT, RP, 10>(guide, H, W, rp, rs, c, planes, st);
+    }
+    return launch_build_rp<WT, RP, -1>(guide, H, W, rp, rs, c, planes, st);
 }
 
 template <typename WT>
 cudaError_t launch_build_t(const float* guide, int H, int W, int rp, int rs, float c, WT* planes,
                            cudaStream_t st) {
     switch (rp) {
-        case 1: return launch_build_rp<WT, 1>(guide, H, W, rp, rs, c, planes, st);
-        case 2: return launch_build_rp<WT, 2>(guide, H, W, rp, rs, c, planes, st);
-        case 3: return launch_build_rp<WT, 3>(guide, H, W, rp, rs, c, planes, st);
-        case 4: return launch_build_rp<WT, 4>(guide, H, W, rp, rs, c, planes, st);
-        case 5: return launch_build_rp<WT, 5>(guide, H, W, rp, rs, c, planes, st);
-        case 8: return launch_build_rp<WT, 8>(guide, H, W, rp, rs, c, planes, st);    // 17 x 17 patches
-        case 11: return launch_build_rp<WT, 11>(guide, H, W, rp, rs, c, planes, st);  // 23 x 23
-        case 14: return launch_build_rp<WT, 14>(guide, H, W, rp, rs, c, planes, st);  // 29 x 29
-        default: return launch_build_rp<WT, -1>(guide, H, W, rp, rs, c, planes, st);
+        case 1: return launch_build_rs<WT, 1>(guide, H, W, rp, rs, c, planes, st);
+        case 2: return launch_build_rs<WT, 2>(guide, H, W, rp, rs, c, planes, st);
+        case 3: return launch_build_rs<WT, 3>(guide, H, W, rp, rs, c, planes, st);
+        case 4: return launch_build_rs<WT, 4>(guide, H, W, rp, rs, c, planes, st);
+        case 5: return launch_build_rs<WT, 5>(guide, H, W, rp, rs, c, planes, st);
+        case 8: return launch_build_rs<WT, 8>(guide, H, W, rp, rs, c, planes, st);    // 17 x 17 patches
+        case 11: return launch_build_rs<WT, 11>(guide, H, W, rp, rs, c, planes, st);  // 23 x 23
+        case 14: return launch_build_rs<WT, 14>(guide, H, W, rp, rs, c, planes, st);  // 29 x 29
+        default: return launch_build_rp<WT, -1, -1>(guide, H, W, rp, rs, c, planes, st);
     }
 }
 

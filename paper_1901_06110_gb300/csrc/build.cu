@@ -77,7 +77,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // shared-memory address offset of the vertical sums are then constants); RS < 0:
 // runtime radius rs_rt.
 template <typename WT, int RP, int RS>
-__global__ void __launch_bounds__(kThreads, RP < 0 ? 1 : (RP <= 5 ? 6 : 3))
+__global__ void __launch_bounds__(kThreads, RP < 0 ? 1 : (RP <= 5 ? 4 : 3))
 build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt, float c2, int chunk,
              WT* __restrict__ planes) {
     extern __shared__ __align__(16) float smem[];
@@ -124,6 +124,19 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
     // V(i, cc) = sum_{t_y} (g(i + t_y, cc - rp) - g(i + t_y + o_y, cc - rp + o_x))^2 for the
     // tile's rows: one column and 8 consecutive output rows per task, as a sliding
     // window down the column (staged row r0 + t is image row y0 - rp + r0 + t)
+    // every thread has at most one vertical task (2 (kTW + 2 r_p) <= kThreads), the same
+    // for every offset: with the patch radius known at compile time, its own guide
+    // column g(i + t_y, cc - rp) is read once into registers and kept for all offsets
+    constexpr int kNG = RP >= 0 ? kSeg + 2 * RP : 1;
+    float gown[kNG];
+    if constexpr (RP >= 0) {
+        if (tid < n_vtask) {
+            const int seg = tid / EW, cc = tid - (tid / EW) * EW;
+            const float* ga = G + seg * kSeg * GW + cc + rs;
+#pragma unroll
+            for (int t = 0; t < kNG; ++t) gown[t] = ga[t * GW];
+        }
+    }
     auto vertical = [&](int oy, int ox, float* V) {
         for (int task = tid; task < n_vtask; task += kThreads) {
             const int seg = task / EW;
@@ -136,7 +149,12 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
 #pragma unroll
             for (int t = 0; t < kSeg + 2 * (RP >= 0 ? RP : kMaxRp); ++t) {
                 if (RP < 0 && t >= ne) break;
-                const float df = ga[t * GW] - gb[t * GW];
+                float a;
+                if constexpr (RP >= 0)
+                    a = gown[t];
+                else
+                    a = ga[t * GW];
+                const float df = a - gb[t * GW];
                 e[t] = df * df;
             }
             float acc = 0.f;
@@ -182,7 +200,7 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
         float* Vn = ((k - k_begin) & 1) ? V0 : V1;
         if (k + 1 < k_end) vertical(oy1, ox1, Vn);  // in the same interval as the sums below
         // D(i, j) = sum_{t_x} V(i, j + t_x), then the weight
-        const float lhat = log2f(1.0f - fabsf((float)oy) * inv_hat) + log2f(1.0f - fabsf((float)ox) * inv_hat);
+        const float lhat = __log2f((1.0f - fabsf((float)oy) * inv_hat) * (1.0f - fabsf((float)ox) * inv_hat));
         // columns whose partner j + o_x lies inside the image, and the rows whose partner does
         const int jlo = ox < 0 ? -ox : 0, jhi = ox > 0 ? W - ox : W;
         const int ihi = H - oy;

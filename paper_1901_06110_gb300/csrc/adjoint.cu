@@ -49,7 +49,6 @@ namespace {
 constexpr int kAdjTH = 16, kAdjTW = 32;  // pair-pass tiles, block (32, 8), 2 rows per thread
 constexpr int kMaxHalfOffsets = 2 * 12 * 13;  // n_h at the largest search radius (12)
 constexpr int kPairSplit = 4;  // pair passes G and B: the half offsets in this many chunks (grid z)
-constexpr int kBT = 32;        // box-sum tile side (extended grid)
 
 // Everything the kernels of one image read: sizes, scalars and device buffers of its
 // tape and handle, and the caller's inputs and outputs of the current call.
@@ -70,7 +69,7 @@ struct TapeView {
     float* m;             // m and 1/m
     unsigned long long* mkey;
     int* sstar;           // first maximiser of d t
-    float *xh, *vh, *uh, *zh, *g, *gs, *dh, *dh0, *base, *thp, *Dhat, *Gp, *ge, *AZ;
+    float *xh, *vh, *uh, *zh, *g, *gs, *dh, *dh0, *base, *thp, *Dhat, *Gp, *AZ;
     double *mh, *rho_part, *h_part, *m_part;  // mh: cotangents of m, rho, h
     float* x_out;         // x_N (caller's)
     const float* x_bar;   // its cotangent (caller's)
@@ -680,106 +679,135 @@ __global__ void __launch_bounds__(256, 3) adj_pairs_b_kernel(const TapeView* __r
 //   E_o(q) = sum_{t in patch} Dh_o(q - t)               (box sum, Dh = 0 off the image)
 //   F_o(q) = 2 E_o(q) (g(q) - g(q + o)),
 // the cotangent of g(p) is ge(p) = sum_o F_o(p) - F_o(p - o): the first term from the
-// patch at q = p, the second from the patch whose partner pixel is p.  Two kernels:
-// the box sums of every D-hat plane onto the extended grid (grid z = image * n_h +
-// offset; E reuses the memory of the G planes, which pass B has read), then one thread
-// per p summing its offsets in a fixed order (no atomics, so the result does not
-// depend on scheduling).
-__global__ void __launch_bounds__(256) adj_box_kernel(const TapeView* __restrict__ tv, int nh) {
-    extern __shared__ float S[];
-    const int img = blockIdx.z / nh, k = blockIdx.z - img * nh;
-    const TapeView& v = tv[img];
-    const int H = v.H, W = v.W, rp = v.rp;
-    const int q0y = blockIdx.y * kBT - rp, q0x = blockIdx.x * kBT - rp;  // image coords of the tile origin
-    const int DW = kBT + 2 * rp;  // Dh over rows [q0y - rp, q0y + kBT + rp), same columns
-    float* Ds = S;                // [DW][DW]
-    float* Rs = Ds + DW * DW;     // horizontal sums [DW][kBT]
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int Wp = plane_pitch(W);
-    const float* Dk = v.Dhat + (size_t)k * H * Wp;
-    for (int a = ty; a < DW; a += 8) {
-        const int i = q0y - rp + a;
-        const bool row_in = i >= 0 && i < H;
-        for (int b = tx; b < DW; b += 32) {
-            const int j = q0x - rp + b;
-            Ds[a * DW + b] = (row_in && j >= 0 && j < W) ? Dk[(size_t)i * Wp + j] : 0.f;
-        }
-    }
-    __syncthreads();
-    for (int a = ty; a < DW; a += 8) {
-        float s = 0.f;
-        for (int t = 0; t <= 2 * rp; ++t) s += Ds[a * DW + tx + t];
-        Rs[a * kBT + tx] = s;
-    }
-    __syncthreads();
-    const int XW = W + 2 * rp, XH = H + 2 * rp;
-    float* Ek = v.Gp + (size_t)k * XH * XW;
-    const int qx = q0x + tx;
-    for (int a = ty; a < kBT; a += 8) {
-        const int qy = q0y + a;
-        if (qy >= H + rp || qx >= W + rp) continue;
-        float s = 0.f;
-        for (int t = 0; t <= 2 * rp; ++t) s += Rs[(a + t) * kBT + tx];
-        Ek[(size_t)(qy + rp) * XW + (qx + rp)] = s;
-    }
-}
+// patch at q = p, the second from the patch whose partner pixel is p.
+//
+// One kernel per tile Q of the extended grid (kQH x kQW) and chunk of the half
+// offsets (grid z = image * chunks + chunk).  For each offset of the chunk in turn the
+// block stages D-hat over Q and its patch halo, forms E_o on Q by row sums then column
+// sums in shared memory, and adds F_o(q) to q's own sum (a register) and -F_o(q) to
+// q + o in a shared accumulator over Q, rs rows below and rs columns either side.  No
+// two q of one offset share q + o, and the offsets are separated by the barriers of the
+// box sums, so every accumulator element is summed in offset order.  The block writes
+// its accumulator window (own sums added) as one partial; the fold gathers ge(p) from
+// the partials of every chunk and of the (up to six) tiles whose windows hold p, in a
+// fixed order.  E is never stored; the partials reuse the memory of the G planes,
+// which pair pass B has read.
+constexpr int kQH = 16, kQW = 32;
 
-__global__ void __launch_bounds__(256) adj_guide_kernel(const TapeView* __restrict__ tv) {
-    extern __shared__ float Gs[];  // g over rows [p0y - rs, p0y + 8 + rs), cols [p0x - rs, p0x + 32 + rs)
-    const TapeView& v = tv[blockIdx.z];
+__host__ __device__ __forceinline__ int bg_win_h(int rs) { return kQH + rs; }
+__host__ __device__ __forceinline__ int bg_win_w(int rs) { return kQW + 2 * rs; }
+
+__global__ void __launch_bounds__(256) adj_boxguide_kernel(const TapeView* __restrict__ tv, int chunks) {
+    extern __shared__ float S[];
+    const int img = blockIdx.z / chunks, zc = blockIdx.z - img * chunks;
+    const TapeView& v = tv[img];
     const int H = v.H, W = v.W, rp = v.rp, rs = v.rs;
-    const float* E = v.Gp;
-    const float* guide = v.guide;
-    const int p0y = blockIdx.y * 8 - rp, p0x = blockIdx.x * 32 - rp;
-    const int GH = 8 + 2 * rs, GW = 32 + 2 * rs;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int a = ty; a < GH; a += 8) {
-        const size_t row = (size_t)sym_index(p0y - rs + a, H) * W;
-        for (int b = tx; b < GW; b += 32) Gs[a * GW + b] = guide[row + sym_index(p0x - rs + b, W)];
-    }
-    __syncthreads();
-    const int py = p0y + ty, px = p0x + tx;
-    const int XW = W + 2 * rp, XH = H + 2 * rp;
-    if (py >= H + rp || px >= W + rp) return;
-    const size_t plane = (size_t)XH * XW;
-    const int ca = ty + rs, cb = tx + rs;  // p in Gs
-    const float gp = Gs[ca * GW + cb];
-    const size_t at = (size_t)(py + rp) * XW + (px + rp);
-    float acc = 0.f;
-    int oy, ox;
-    half_offset(0, rs, oy, ox);
     const int nh = num_half_offsets(rs);
-#pragma unroll 4
-    for (int k = 0; k < nh; ++k) {
-        const float* Ek = E + (size_t)k * plane;
-        // q = p - o must lie on the extended grid (E is 0 beyond it)
-        const int qy = py - oy, qx = px - ox;
-        const bool qin = qy >= -rp && qx >= -rp && qx < W + rp;
-        const float ep = Ek[at];
-        const float eq = qin ? Ek[at - (size_t)oy * XW - ox] : 0.f;
-        const float fp = 2.f * ep * (gp - Gs[(ca + oy) * GW + cb + ox]);
-        const float fq = 2.f * eq * (Gs[(ca - oy) * GW + cb - ox] - gp);
-        acc += fp - fq;
+    const int k0 = nh * zc / chunks, k1 = nh * (zc + 1) / chunks;
+    const int q0y = blockIdx.y * kQH - rp, q0x = blockIdx.x * kQW - rp;  // image coords of Q's origin
+    const int DH = kQH + 2 * rp, DW = kQW + 2 * rp;  // D-hat window: rows q0y - rp + [0, DH), cols q0x - rp + [0, DW)
+    const int AH = bg_win_h(rs), AW = bg_win_w(rs);  // accumulator window: rows q0y + [0, AH), cols q0x - rs + [0, AW)
+    float* Gs = S;             // [AH][AW] the reflected guide over the window
+    float* Ac = Gs + AH * AW;  // [AH][AW]
+    float* Ds = Ac + AH * AW;  // [DH][DW]
+    float* Rs = Ds + DH * DW;  // [DH][kQW] row sums
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + tx;
+    for (int idx = tid; idx < AH * AW; idx += 256) {
+        const int a = idx / AW, b = idx - a * AW;
+        Gs[idx] = v.guide[(size_t)sym_index(q0y + a, H) * W + sym_index(q0x - rs + b, W)];
+        Ac[idx] = 0.f;
+    }
+    const int Wp = plane_pitch(W);
+    const size_t plane = (size_t)H * Wp;
+    const int w = 2 * rp;
+    float own0 = 0.f, own1 = 0.f;  // q = (ty, tx) and (ty + 8, tx) of Q
+    const int c0 = ty * AW + tx + rs, c1 = c0 + 8 * AW;  // their cells in the window
+    int oy, ox;
+    half_offset(k0, rs, oy, ox);
+    for (int k = k0; k < k1; ++k) {
+        const float* Dk = v.Dhat + (size_t)k * plane;
+        for (int a = ty; a < DH; a += 8) {
+            const int i = q0y - rp + a;
+            const bool rin = i >= 0 && i < H;
+            const float* row = Dk + (size_t)(rin ? i : 0) * Wp;
+            for (int b = tx; b < DW; b += 32) {
+                const int j = q0x - rp + b;
+                Ds[a * DW + b] = (rin && j >= 0 && j < W) ? row[j] : 0.f;
+            }
+        }
+        __syncthreads();  // Ds of this offset written; Ac of the previous offset updated
+        for (int a = ty; a < DH; a += 8) {
+            const float* r = Ds + a * DW + tx;
+            float s = 0.f;
+            for (int t = 0; t <= w; ++t) s += r[t];
+            Rs[a * kQW + tx] = s;
+        }
+        __syncthreads();  // Rs written; Ds free for the next offset
+        const int sh = oy * AW + ox;
+        {
+            const float* r = Rs + ty * kQW + tx;
+            float e = 0.f;
+            for (int t = 0; t <= w; ++t) e += r[t * kQW];
+            const float F = 2.f * e * (Gs[c0] - Gs[c0 + sh]);
+            own0 += F;
+            Ac[c0 + sh] -= F;
+        }
+        {
+            const float* r = Rs + (ty + 8) * kQW + tx;
+            float e = 0.f;
+            for (int t = 0; t <= w; ++t) e += r[t * kQW];
+            const float F = 2.f * e * (Gs[c1] - Gs[c1 + sh]);
+            own1 += F;
+            Ac[c1 + sh] -= F;
+        }
         if (++ox > rs) {
             ++oy;
             ox = -rs;
         }
     }
-    v.ge[at] = acc;
+    __syncthreads();
+    Ac[c0] += own0;
+    Ac[c1] += own1;
+    __syncthreads();
+    float* out = v.Gp + (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)(AH * AW);
+    for (int idx = tid; idx < AH * AW; idx += 256) out[idx] = Ac[idx];
+}
+
+// ge(p) of the extended-grid position p = (pi, pj) (image coords): the partials of every
+// chunk and of the tiles whose accumulator windows hold p, in a fixed order
+__device__ __forceinline__ float gather_ge(const float* __restrict__ part, int pi, int pj, int rp, int rs, int tiles_y,
+                                           int tiles_x, int chunks) {
+    const int AH = bg_win_h(rs), AW = bg_win_w(rs);
+    const int ty0 = (pi + rp) / kQH, tx0 = (pj + rp) / kQW;
+    float acc = 0.f;
+    for (int z = 0; z < chunks; ++z)
+        for (int ty = ty0 - 1; ty <= ty0; ++ty) {
+            if (ty < 0 || ty >= tiles_y) continue;
+            const int a = pi - (ty * kQH - rp);
+            if (a >= AH) continue;
+            for (int tx = tx0 - 1; tx <= tx0 + 1; ++tx) {
+                if (tx < 0 || tx >= tiles_x) continue;
+                const int b = pj - (tx * kQW - rp - rs);
+                if (b < 0 || b >= AW) continue;
+                acc += part[(((size_t)z * tiles_y + ty) * tiles_x + tx) * (size_t)(AH * AW) + (size_t)a * AW + b];
+            }
+        }
+    return acc;
 }
 
 // gb(q) = (xh0 + vh0)(q) [0 < g(q) < 1] + sum of ge(p) over the extended p that reflect
 // onto q (p = 2 n m + q or 2 n m - 1 - q per axis), in a fixed order
-__global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restrict__ tv) {
+__global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restrict__ tv, int tiles_y, int tiles_x,
+                                                       int chunks) {
     const TapeView& v = tv[blockIdx.z];
-    const int H = v.H, W = v.W, rp = v.rp;
+    const int H = v.H, W = v.W, rp = v.rp, rs = v.rs;
     const int j = blockIdx.x * 32 + threadIdx.x;
     const int i = blockIdx.y * 8 + threadIdx.y;
     if (i >= H || j >= W) return;
     const size_t q = (size_t)i * W + j;
     const float g = v.guide[q];
     float acc = (g > 0.f && g < 1.f) ? v.xh[q] + v.vh[q] : 0.f;
-    const int XW = W + 2 * rp;
     const int my = rp / (2 * H) + 1, mx = rp / (2 * W) + 1;
     for (int m = -my; m <= my; ++m)
         for (int cy = 0; cy < 2; ++cy) {
@@ -789,7 +817,7 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restric
                 for (int cx = 0; cx < 2; ++cx) {
                     const int pj = cx == 0 ? 2 * W * n - 1 - j : 2 * W * n + j;
                     if (pj < -rp || pj >= W + rp) continue;
-                    acc += v.ge[(size_t)(pi + rp) * XW + (pj + rp)];
+                    acc += gather_ge(v.Gp, pi, pj, rp, rs, tiles_y, tiles_x, chunks);
                 }
         }
     v.guide_bar[q] = acc;
@@ -843,7 +871,7 @@ struct lpnp_tape {
     const float* guide = nullptr;  // caller's guide
     int blur_r = 0;
     float blur_sigma = 1.f;
-    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, gs, dh, dh0, base, thp, Dhat, Gp, ge, m, mkey, sstar, mh,
+    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, gs, dh, dh0, base, thp, Dhat, Gp, m, mkey, sstar, mh,
         rho_part, h_part, m_part, scratch;
     // tables of a call this tape leads (the first image of the batch): per-image views,
     // phase-1 instance tables and work items in one device buffer, uploaded from one
@@ -920,7 +948,6 @@ TapeView make_view(const lpnp_tape* tp, const float* x_out, const float* x_bar, 
     v.thp = tp->thp.as<float>();
     v.Dhat = tp->Dhat.as<float>();
     v.Gp = tp->Gp.as<float>();
-    v.ge = tp->ge.as<float>();
     v.AZ = tp->AZ.as<float>();
     v.mh = tp->mh.as<double>();
     v.rho_part = tp->rho_part.as<double>();
@@ -1173,6 +1200,12 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     const int nrb = (int)(pgrid2.x * pgrid2.y);
     const int pgx = (W + kAdjTW - 1) / kAdjTW, pgy = (H + kAdjTH - 1) / kAdjTH;
     const int npb = pgx * pgy * kPairSplit;  // pair-pass blocks (with the offset chunks)
+    // patch-distance adjoint: tiles of the extended grid, the half offsets in kPairSplit
+    // chunks (a number that does not depend on the batch, so that an image's sums have
+    // the same order alone and in a batch)
+    const int bg_ty = (H + 2 * rp + kQH - 1) / kQH, bg_tx = (W + 2 * rp + kQW - 1) / kQW;
+    const int bg_chunks = std::min(kPairSplit, nh);
+    const size_t bg_part = (size_t)bg_chunks * bg_ty * bg_tx * bg_win_h(rs) * bg_win_w(rs);
     for (int i = 0; i < count; ++i) {
         lpnp_tape* tp = tapes[i];
         DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->gs, &tp->dh, &tp->base};
@@ -1181,10 +1214,9 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         TAPE_CK(tp->thp.ensure(sizeof(float) * n * (T > 0 ? T : 1)));
         TAPE_CK(tp->dh0.ensure(sizeof(float) * n * kPairSplit));
         TAPE_CK(tp->Dhat.ensure(sizeof(float) * (size_t)nh * H * plane_pitch(W)));
-        // the G planes, later the box sums E on the extended grid (pass B has then read G)
-        TAPE_CK(tp->Gp.ensure(sizeof(float) * (size_t)nh *
-                              std::max((size_t)H * plane_pitch(W), (size_t)(H + 2 * rp) * (W + 2 * rp))));
-        TAPE_CK(tp->ge.ensure(sizeof(float) * (size_t)(H + 2 * rp) * (W + 2 * rp)));
+        // the G planes, later the partials of the patch-distance adjoint (pass B has then
+        // read G)
+        TAPE_CK(tp->Gp.ensure(sizeof(float) * std::max((size_t)nh * H * plane_pitch(W), bg_part)));
         TAPE_CK(tp->rho_part.ensure(sizeof(double) * nrb));
         TAPE_CK(tp->h_part.ensure(sizeof(double) * npb));
         TAPE_CK(tp->m_part.ensure(sizeof(double) * npb));
@@ -1292,19 +1324,17 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         case DSGNLM_F16: TAPE_CK(pairs_b(__half{})); break;
         default: TAPE_CK(pairs_b(__nv_bfloat16{})); break;
     }
-    // patch distances back to the guide: box sums of the D-hat planes onto the extended
-    // grid, the gather of every extended position, then the fold through the reflection
+    // patch distances back to the guide: box sums and the scatter of every offset per
+    // tile of the extended grid, then the gather of the partials and the fold through
+    // the reflection
     {
-        const int DW = kBT + 2 * rp;
-        const size_t bsmem = sizeof(float) * (size_t)(DW * DW + DW * kBT);
-        TAPE_CK(cudaFuncSetAttribute(adj_box_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
-        adj_box_kernel<<<dim3((W + 2 * rp + kBT - 1) / kBT, (H + 2 * rp + kBT - 1) / kBT, nh * count), 256, bsmem,
-                         st>>>(tb.views, nh);
-        const size_t gsmem = sizeof(float) * (size_t)(8 + 2 * rs) * (32 + 2 * rs);
-        adj_guide_kernel<<<dim3((W + 2 * rp + 31) / 32, (H + 2 * rp + 7) / 8, count), dim3(32, 8), gsmem, st>>>(
-            tb.views);
-        adj_fold_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views);
-        count_launches(3);
+        const size_t bsmem =
+            sizeof(float) * (size_t)(2 * bg_win_h(rs) * bg_win_w(rs) + (kQH + 2 * rp) * (kQW + 2 * rp) +
+                                     (kQH + 2 * rp) * kQW);
+        TAPE_CK(cudaFuncSetAttribute(adj_boxguide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+        adj_boxguide_kernel<<<dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), bsmem, st>>>(tb.views, bg_chunks);
+        adj_fold_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, bg_ty, bg_tx, bg_chunks);
+        count_launches(2);
         TAPE_CK(cudaGetLastError());
     }
     // dL/dy = sum_k mu A g_k = A gs
@@ -1360,7 +1390,7 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (t->staged) cudaEventSynchronize(t->staged);
     DevBuf* bufs[] = {&t->Dh,  &t->Th,   &t->X,  &t->V,       &t->U,     &t->Gr,     &t->AZ,     &t->xh,
                       &t->vh,  &t->uh,   &t->zh, &t->g,       &t->gs,    &t->dh,     &t->dh0,    &t->base,
-                      &t->thp, &t->Dhat, &t->Gp, &t->ge,      &t->m,     &t->mkey,   &t->sstar,  &t->mh,
+                      &t->thp, &t->Dhat, &t->Gp, &t->m,     &t->mkey,   &t->sstar,  &t->mh,
                       &t->rho_part, &t->h_part, &t->m_part, &t->scratch, &t->tables, &t->scal};
     for (DevBuf* b : bufs) b->release();
     if (t->stage) cudaFreeHost(t->stage);

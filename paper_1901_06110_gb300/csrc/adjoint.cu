@@ -40,6 +40,7 @@
 #include "grad.cuh"
 #include "handle.h"
 #include "internal.h"
+#include "tma.cuh"
 #include "xupdate.cuh"
 
 namespace dsg {
@@ -70,6 +71,9 @@ struct TapeView {
     unsigned long long* mkey;
     int* sstar;           // first maximiser of d t
     float *xh, *vh, *uh, *zh, *g, *gs, *dh, *dh0, *base, *thp, *Dhat, *Gp, *AZ;
+    float* gpart;         // partials of the patch-distance adjoint (the G or the D-hat memory)
+    alignas(64) unsigned char bd_kmap[128];  // tensor maps of the weight and G planes for the fused
+    alignas(64) unsigned char bd_gmap[128];  // pass B (boxes of the D-hat window)
     double *mh, *rho_part, *h_part, *m_part;  // mh: cotangents of m, rho, h
     float* x_out;         // x_N (caller's)
     const float* x_bar;   // its cotangent (caller's)
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
     const int i = blockIdx.y * 8 + threadIdx.y;
     const float inv_m = __ldg(v.m + 1);
     const float mu = v.mu, alpha = v.alpha, rho = v.rho;
-    double r = 0.0;
+    float r = 0.f;
     if (i < H && j < W) {
         const size_t q = (size_t)i * W + j;
         const float* d = v.Dh + (size_t)v.T * n;
@@ -271,18 +275,11 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
         const float gg = proj_deriv(xb, v.constraint) * (v.xh[q] + zz);
         v.g[q] = gg;
         v.zh[q] = zz;
-        r = (double)gg * (double)mu * ((double)vu - (double)xb);
+        r = gg * mu * (vu - xb);
     }
-    r = warp_sum(r);
-    __shared__ double sr[8];
     const int t = threadIdx.y * 32 + threadIdx.x;
-    if ((t & 31) == 0) sr[t >> 5] = r;
-    __syncthreads();
-    if (t == 0) {
-        double acc = 0.0;
-        for (int w = 0; w < 8; ++w) acc += sr[w];
-        v.rho_part[blockIdx.y * gridDim.x + blockIdx.x] += acc;  // fixed slot per block, fixed order over iterations
-    }
+    const double acc = block_sum_256(r, t);
+    if (t == 0) v.rho_part[blockIdx.y * gridDim.x + blockIdx.x] += acc;  // fixed slot per block, fixed order over iterations
 }
 
 // Reverse iteration k, after g: ata = A^T A g on 32 x 32 tiles, then per pixel
@@ -381,7 +378,7 @@ __global__ void __launch_bounds__(256, 2) adj_pairs_g_kernel(const TapeView* __r
     __syncthreads();
     const int Wp = plane_pitch(W);
     const size_t plane = (size_t)H * Wp;
-    double mpart = 0.0;
+    float mpart = 0.f;
     const int j = x0 + threadIdx.x;
     for (int py = threadIdx.y; py < kAdjTH; py += 8) {
         const int i = y0 + py;
@@ -432,18 +429,11 @@ __global__ void __launch_bounds__(256, 2) adj_pairs_g_kernel(const TapeView* __r
             }
         }
         v.dh0[(size_t)zc * n + (size_t)i * W + j] = accd;
-        mpart -= (double)accm * (double)inv_m * (double)inv_m;
+        mpart -= accm * inv_m * inv_m;
     }
-    mpart = warp_sum(mpart);
-    __shared__ double sm[8];
     const int t = threadIdx.y * 32 + threadIdx.x;
-    if ((t & 31) == 0) sm[t >> 5] = mpart;
-    __syncthreads();
-    if (t == 0) {
-        double acc = 0.0;
-        for (int w = 0; w < 8; ++w) acc += sm[w];
-        v.m_part[(zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
-    }
+    const double acc = block_sum_256(mpart, t);
+    if (t == 0) v.m_part[(zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
 }
 
 // Pair pass T: dh(s) = (1/m) (dh0(s) + sum_o G_{s-o, s} d_{s-o} K1_{s-o, s}), dh0 the
@@ -625,7 +615,7 @@ __global__ void __launch_bounds__(256, 3) adj_pairs_b_kernel(const TapeView* __r
     const size_t plane = (size_t)H * Wp;
     const float* Gp = v.Gp;
     float* Dhat = v.Dhat;
-    double hpart = 0.0;
+    float hpart = 0.f;
     const int j = x0 + threadIdx.x;
     for (int py = threadIdx.y; py < kAdjTH; py += 8) {
         const int i = y0 + py;
@@ -660,18 +650,11 @@ __global__ void __launch_bounds__(256, 3) adj_pairs_b_kernel(const TapeView* __r
                 ox = -rs;
             }
         }
-        hpart += (double)hp * (double)hfac;
+        hpart += hp;
     }
-    hpart = warp_sum(hpart);
-    __shared__ double sm[8];
     const int t = threadIdx.y * 32 + threadIdx.x;
-    if ((t & 31) == 0) sm[t >> 5] = hpart;
-    __syncthreads();
-    if (t == 0) {
-        double acc = 0.0;
-        for (int w = 0; w < 8; ++w) acc += sm[w];
-        v.h_part[(zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
-    }
+    const double acc = block_sum_256(hpart, t);
+    if (t == 0) v.h_part[(zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc * (double)hfac;
 }
 
 // Patch-distance adjoint.  With g the reflected guide on the grid extended by the
@@ -770,36 +753,312 @@ __global__ void __launch_bounds__(256) adj_boxguide_kernel(const TapeView* __res
     Ac[c0] += own0;
     Ac[c1] += own1;
     __syncthreads();
-    float* out = v.Gp + (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)(AH * AW);
+    float* out = v.gpart + (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)(AH * AW);
     for (int idx = tid; idx < AH * AW; idx += 256) out[idx] = Ac[idx];
 }
 
-// ge(p) of the extended-grid position p = (pi, pj) (image coords): the partials of every
-// chunk and of the tiles whose accumulator windows hold p, in a fixed order
-__device__ __forceinline__ float gather_ge(const float* __restrict__ part, int pi, int pj, int rp, int rs, int tiles_y,
-                                           int tiles_x, int chunks) {
-    const int AH = bg_win_h(rs), AW = bg_win_w(rs);
-    const int ty0 = (pi + rp) / kQH, tx0 = (pj + rp) / kQW;
-    float acc = 0.f;
-    for (int z = 0; z < chunks; ++z)
-        for (int ty = ty0 - 1; ty <= ty0; ++ty) {
-            if (ty < 0 || ty >= tiles_y) continue;
-            const int a = pi - (ty * kQH - rp);
-            if (a >= AH) continue;
-            for (int tx = tx0 - 1; tx <= tx0 + 1; ++tx) {
-                if (tx < 0 || tx >= tiles_x) continue;
-                const int b = pj - (tx * kQW - rp - rs);
-                if (b < 0 || b >= AW) continue;
-                acc += part[(((size_t)z * tiles_y + ty) * tiles_x + tx) * (size_t)(AH * AW) + (size_t)a * AW + b];
+// Pair pass B fused with the patch-distance adjoint.  Per tile Q of the extended grid
+// (kQH x (32 - 2 rp), so that Q with its patch halo is 32 columns wide) and chunk of the
+// half offsets (grid z = image * chunks + chunk), for each offset o of the chunk in turn:
+//   1. D-hat(s, o) = -c K1 Kh at every s of Q and its patch halo (the pixels whose
+//      D-hat enters the box sums over Q), Kh as in pair pass B, into shared memory;
+//      pixels of Q itself also add Kh K1 D to the block's dL/dh partial, with
+//      D = (log2 lam - log2 K1) ln 2 / c recovered from the stored weight;
+//   2. row sums, then column sums: E_o on Q;
+//   3. the scatter of F_o(q) = 2 E_o(q) (g(q) - g(q + o)) as in the box-and-gather
+//      kernel, into the same partial layout (windows of Q's width).
+// D-hat is never stored.  The halo's D-hat is recomputed by the neighbouring tiles
+// ((kQH + 2 rp) 32 / (kQH (32 - 2 rp)) of the pairs, 1.43 at rp = 2), which costs less
+// than writing the planes and reading them back.  Every warp works on one row of the
+// 32-wide window, so its shared-memory accesses are conflict-free.
+// K1 and G of the window arrive by TMA, two offsets ahead, into a ring of two stages
+// (one thread issues the copies once every thread has finished with the stage).  The
+// tensors' rows are W wide and the planes are zero where s + o leaves the image (the
+// weight build writes zeros there), so pairs off the image contribute exact zeros with
+// no per-pair test.  The balancing fields are staged as pairs (d^p, d^{p+1}) and
+// (th^p, th^{p+1}), so that the sum over the passes takes one packed FP32x2 FMA per
+// pair of passes.  The patch radius RP is a template argument (1 to 3); RS > 0 and
+// TT >= 0 fix the search radius and the number of balancing passes (field strides
+// become constants and the fields at s stay in registers), RS = 0 and TT = -1 read
+// them from the view.
+template <int RP>
+struct Bd {
+    static constexpr int QW = 32 - 2 * RP;  // tile width
+    static constexpr int DH = kQH + 2 * RP;  // D-hat window rows (32 columns)
+    static constexpr int NC = (DH + 7) / 8;  // window rows per thread
+};
+// TMA box widths: the window's 32 columns from the 16-byte-aligned column at or left of
+// its first column
+__host__ __device__ constexpr int bd_box_w(int esz) { return esz == 4 ? 36 : 40; }
+__host__ __device__ constexpr int bd_stage_bytes(int rows, int cols, int esz) {
+    return (rows * cols * esz + 127) & ~127;
+}
+
+__host__ __device__ __forceinline__ int bd_qw(int rp) { return 32 - 2 * rp; }
+__host__ __device__ __forceinline__ int bd_field_h(int rp, int rs) { return kQH + 2 * rp + rs; }
+__host__ __device__ __forceinline__ int bd_field_w(int rs) { return 32 + 2 * rs; }
+__host__ __device__ __forceinline__ int bd_win_w(int rp, int rs) { return bd_qw(rp) + 2 * rs; }
+
+template <typename WT, int RP, int RS, int TT>
+__global__ void __launch_bounds__(256, 3)
+    adj_pairs_bd_kernel(const TapeView* __restrict__ tv, int chunks, unsigned* err, long long budget) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int rp = RP, QW = Bd<RP>::QW, DH = Bd<RP>::DH, NC = Bd<RP>::NC;
+    constexpr int KBW = bd_box_w((int)sizeof(WT)), GBW = bd_box_w(4);
+    constexpr int KBYTES = DH * KBW * (int)sizeof(WT), GBYTES = DH * GBW * 4;
+    constexpr int KST = bd_stage_bytes(DH, KBW, (int)sizeof(WT)), GST = bd_stage_bytes(DH, GBW, 4);
+    constexpr int NP = TT >= 0 ? (TT + 1) / 2 : 1;  // field pairs held in registers per cell
+    const int img = blockIdx.z / chunks, zc = blockIdx.z - img * chunks;
+    const TapeView& v = tv[img];
+    const int H = v.H, W = v.W;
+    const int rs = RS > 0 ? RS : v.rs;
+    const int T = TT >= 0 ? TT : v.T;
+    const int P = (T + 1) / 2;
+    const int nh = num_half_offsets(rs);
+    const int k0 = nh * zc / chunks, k1 = nh * (zc + 1) / chunks;
+    const int q0y = blockIdx.y * kQH - rp, q0x = blockIdx.x * QW - rp;  // image coords of Q's origin
+    const int FH = bd_field_h(rp, rs), FW = bd_field_w(rs);  // field window, origin (q0y - rp, q0x - rp - rs)
+    const int AH = bg_win_h(rs), AW = bd_win_w(rp, rs);      // accumulator window, origin (q0y, q0x - rs)
+    const int fcells = FH * FW;
+    const size_t n = (size_t)H * W;
+    // stage st: K1 at smem + st KST, G at smem + 2 KST + st GST
+    float* Ds = reinterpret_cast<float*>(smem + 2 * KST + 2 * GST);  // [DH][32]
+    float* Rs = Ds + DH * 32;                                        // [DH][32] row sums (QW used)
+    float2* DP = reinterpret_cast<float2*>(Rs + DH * 32);            // [P][FH][FW] (d^2q, d^2q+1)
+    float2* TP = DP + (size_t)P * fcells;                            // [P][FH][FW] (th^2q, th^2q+1)
+    float* Dd = reinterpret_cast<float*>(TP + (size_t)P * fcells);   // [FH][FW] d = d^T
+    float* Gs = Dd + fcells;                                         // [AH][AW] the reflected guide
+    float* Ac = Gs + AH * AW;                                        // [AH][AW] the scatter accumulator
+    __shared__ float lglam[kMaxHalfOffsets];
+    __shared__ __align__(8) uint64_t bars[2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + tx;
+    const CUtensorMap* kmap = reinterpret_cast<const CUtensorMap*>(v.bd_kmap);
+    const CUtensorMap* gmap = reinterpret_cast<const CUtensorMap*>(v.bd_gmap);
+    const int xw = q0x - rp, yw = q0y - rp;  // the D-hat window's first column and row
+    const int xk = xw & ~(16 / (int)sizeof(WT) - 1), xg = xw & ~3;
+    const int xoK = xw - xk, xoG = xw - xg;
+    uint64_t policy = 0;
+    auto issue = [&](int k, int st) {
+        mbar_arrive_expect_tx(&bars[st], (unsigned)(KBYTES + GBYTES));
+        tma_load_3d(smem + st * KST, kmap, &bars[st], xk, yw, k, policy);
+        tma_load_3d(smem + 2 * KST + st * GST, gmap, &bars[st], xg, yw, k, policy);
+    };
+    if (tid == 0) {
+        tmap_acquire(kmap);
+        tmap_acquire(gmap);
+        policy = evict_first_policy();
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (k0 < k1) issue(k0, 0);
+        if (k0 + 1 < k1) issue(k0 + 1, 1);
+    }
+    // stage the fields over the field window (zero off the image), the guide and a zero
+    // accumulator over the accumulator window, and log2 of every offset's hat weight
+    for (int idx = tid; idx < fcells; idx += 256) {
+        const int a = idx / FW, b = idx - a * FW;
+        const int i = q0y - rp + a, j = q0x - rp - rs + b;
+        const bool in = i >= 0 && i < H && j >= 0 && j < W;
+        const size_t q = in ? (size_t)i * W + j : 0;
+        for (int u = 0; u < P; ++u) {
+            const int p0 = 2 * u, p1 = p0 + 1;
+            const bool in1 = in && p1 < T;
+            DP[u * fcells + idx] = make_float2(in ? v.Dh[p0 * n + q] : 0.f, in1 ? v.Dh[p1 * n + q] : 0.f);
+            TP[u * fcells + idx] = make_float2(in ? v.thp[p0 * n + q] : 0.f, in1 ? v.thp[p1 * n + q] : 0.f);
+        }
+        Dd[idx] = in ? v.Dh[T * n + q] : 0.f;
+    }
+    for (int idx = tid; idx < AH * AW; idx += 256) {
+        const int a = idx / AW, b = idx - a * AW;
+        Gs[idx] = v.guide[(size_t)sym_index(q0y + a, H) * W + sym_index(q0x - rs + b, W)];
+        Ac[idx] = 0.f;
+    }
+    {
+        const float inv_hat = 1.0f / (float)(rs + 1);
+        for (int k = tid; k < nh; k += 256) {
+            int oy, ox;
+            half_offset(k, rs, oy, ox);
+            lglam[k] = __log2f((1.0f - fabsf((float)oy) * inv_hat) * (1.0f - fabsf((float)ox) * inv_hat));
+        }
+    }
+    __syncthreads();
+    // the thread's D-hat cells (a, b) = (ty + 8 m, tx), m < NC: row a's field cell of s
+    // and s's flat index (each m steps them by a constant), which cells are pixels of Q
+    // (bit m), and (TT >= 0) the fields at s
+    const int j = q0x - rp + tx;
+    const int i0 = q0y - rp + ty;
+    const int fs0 = ty * FW + tx + rs, sidx0 = i0 * W + j;
+    unsigned ownb = 0u;
+    float2 svD[NC][NP], svT[NC][NP];
+    float svd[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+        const int a = ty + 8 * m;
+        const int i = i0 + 8 * m;
+        const bool in = a < DH && i >= 0 && i < H && j >= 0 && j < W;
+        ownb |= (in && a >= rp && a < rp + kQH && tx >= rp && tx < rp + QW) ? 1u << m : 0u;
+        const int cs = a < DH ? fs0 + 8 * m * FW : fs0;
+        svd[m] = Dd[cs];
+        if constexpr (TT >= 0) {
+#pragma unroll
+            for (int u = 0; u < NP; ++u) {
+                svD[m][u] = DP[u * fcells + cs];
+                svT[m][u] = TP[u * fcells + cs];
             }
         }
+    }
+    const float c = v.c, inv_m = __ldg(v.m + 1), mh = (float)v.mh[0];
+    const float inv_c2 = 0.693147180559945f / c;  // ln 2 / c
+    const int ss = *v.sstar;
+    float hp = 0.f;  // the own pixels' sum of Kh K1 D over the chunk (FP32)
+    float own0 = 0.f, own1 = 0.f;  // q = (ty, tx) and (ty + 8, tx) of Q
+    const int c0 = ty * AW + tx + rs, c1 = c0 + 8 * AW;
+    const bool qcol = tx < QW;
+    bool gave_up = false;
+    int oy, ox;
+    half_offset(k0, rs, oy, ox);
+    for (int k = k0; k < k1; ++k) {
+        const int st = (k - k0) & 1;
+        const unsigned par = (unsigned)((k - k0) >> 1) & 1u;
+        // the stage's copies; after a wait that ran out (here or in another block) the
+        // block stops waiting, and the error word makes the call fail
+        if (!gave_up && !mbar_try_wait(&bars[st], par)) {
+            if (*(volatile unsigned*)err != 0u || !mbar_wait_consumer(&bars[st], par, budget)) {
+                gave_up = true;
+                if (tid == 0) atomicOr(err, 1u);
+            }
+        }
+        const WT* Kw = reinterpret_cast<const WT*>(smem + st * KST) + xoK + tx;
+        const float* Gw = reinterpret_cast<const float*>(smem + 2 * KST + st * GST) + xoG + tx;
+        const int fo = oy * FW + ox;
+        const int oW = oy * W + ox;
+        const float lk = lglam[k];
+        // 1. D-hat of offset k at the thread's cells
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            const int a = ty + 8 * m;
+            if (m < 2 || a < DH) {
+                const float K = to_f32(Kw[a * KBW]);
+                const float G = Gw[a * GBW];
+                const int cs = fs0 + 8 * m * FW, cr = cs + fo;
+                const float ds = svd[m], dr = Dd[cr];
+                float2 acc = make_float2(0.f, 0.f);
+                if constexpr (TT >= 0) {
+#pragma unroll
+                    for (int u = 0; u < NP; ++u) {
+                        acc = __ffma2_rn(svT[m][u], DP[u * fcells + cr], acc);  // th^p_s d^p_r
+                        acc = __ffma2_rn(TP[u * fcells + cr], svD[m][u], acc);  // th^p_r d^p_s
+                    }
+                } else {
+                    for (int u = 0; u < P; ++u) {
+                        acc = __ffma2_rn(TP[u * fcells + cs], DP[u * fcells + cr], acc);
+                        acc = __ffma2_rn(TP[u * fcells + cr], DP[u * fcells + cs], acc);
+                    }
+                }
+                float Kh = fmaf(G * ds, dr * inv_m, acc.x + acc.y);
+                const int si = sidx0 + 8 * m * W;
+                if (si == ss || si + oW == ss) Kh = fmaf(mh, ds * dr, Kh);
+                if ((ownb >> m) & 1u) hp = K > 0.f ? fmaf(Kh * K, (lk - __log2f(K)) * inv_c2, hp) : hp;
+                Ds[a * 32 + tx] = -c * K * Kh;
+            }
+        }
+        __syncthreads();  // Ds of this offset written, the stage read; Ac of the offset before updated
+        if (tid == 0 && k + 2 < k1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(k + 2, st);
+        }
+        // 2. row sums, then column sums
+        if (qcol) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const int a = ty + 8 * m;
+                if (m < 2 || a < DH) {
+                    const float* r = Ds + a * 32 + tx;
+                    float s = r[0];
+#pragma unroll
+                    for (int t = 1; t <= 2 * rp; ++t) s += r[t];
+                    Rs[a * 32 + tx] = s;
+                }
+            }
+        }
+        __syncthreads();  // Rs written; Ds free for the next offset
+        // 3. the scatter
+        if (qcol) {
+            const int sh = oy * AW + ox;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cq = h == 0 ? c0 : c1;
+                const float* r = Rs + (ty + 8 * h) * 32 + tx;
+                float e = r[0];
+#pragma unroll
+                for (int t = 1; t <= 2 * rp; ++t) e += r[t * 32];
+                const float F = 2.f * e * (Gs[cq] - Gs[cq + sh]);
+                if (h == 0)
+                    own0 += F;
+                else
+                    own1 += F;
+                Ac[cq + sh] -= F;
+            }
+        }
+        if (++ox > rs) {
+            ++oy;
+            ox = -rs;
+        }
+    }
+    // the block's dL/dh partial (the barrier inside also ends every scatter)
+    const double hacc = block_sum_256(hp, tid);
+    if (tid == 0) v.h_part[(zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = hacc * (double)v.hfac;
+    if (qcol) {
+        Ac[c0] += own0;
+        Ac[c1] += own1;
+    }
+    __syncthreads();
+    float* out = v.gpart + (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)(AH * AW);
+    for (int idx = tid; idx < AH * AW; idx += 256) out[idx] = Ac[idx];
+}
+
+// ge(p) of the extended-grid position p = (pi, pj) (image coords), tiles of width qw: the
+// partials of every chunk and of the tiles whose accumulator windows hold p (rows ty0 - 1, ty0; columns
+// tx0 - 1 .. tx0 + 1), chunk by chunk in that order.  The six candidates are tested once
+// and their loads issued together (a candidate that does not hold p adds nothing).
+__device__ __forceinline__ float gather_ge(const float* __restrict__ part, int pi, int pj, int rp, int rs, int tiles_y,
+                                           int tiles_x, int chunks, int qw) {
+    const int AH = bg_win_h(rs), AW = qw + 2 * rs;
+    const int ty0 = (pi + rp) / kQH, tx0 = (pj + rp) / qw;
+    size_t off[6];
+    bool ok[6];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int w = 0; w < 3; ++w) {
+            const int ty = ty0 - 1 + u, tx = tx0 - 1 + w;
+            const int a = pi - (ty * kQH - rp), b = pj - (tx * qw - rp - rs);
+            const bool in = ty >= 0 && ty < tiles_y && tx >= 0 && tx < tiles_x && a < AH && b >= 0 && b < AW;
+            ok[u * 3 + w] = in;
+            off[u * 3 + w] = in ? ((size_t)ty * tiles_x + tx) * (size_t)(AH * AW) + (size_t)a * AW + b : 0;
+        }
+    const size_t zstride = (size_t)tiles_y * tiles_x * (size_t)(AH * AW);
+    float acc = 0.f;
+    for (int z = 0; z < chunks; ++z) {
+        const float* pz = part + (size_t)z * zstride;
+        float v[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] = ok[c] ? pz[off[c]] : 0.f;
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            if (ok[c]) acc += v[c];
+    }
     return acc;
 }
 
 // gb(q) = (xh0 + vh0)(q) [0 < g(q) < 1] + sum of ge(p) over the extended p that reflect
-// onto q (p = 2 n m + q or 2 n m - 1 - q per axis), in a fixed order
+// onto q (p = 2 n m + q or 2 n m - 1 - q per axis), in a fixed order: per axis the
+// reflections -1 - q (q < rp), q, 2 n - 1 - q (q >= n - rp) while rp < n, the general
+// enumeration otherwise
 __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restrict__ tv, int tiles_y, int tiles_x,
-                                                       int chunks) {
+                                                       int chunks, int qw) {
     const TapeView& v = tv[blockIdx.z];
     const int H = v.H, W = v.W, rp = v.rp, rs = v.rs;
     const int j = blockIdx.x * 32 + threadIdx.x;
@@ -808,18 +1067,30 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restric
     const size_t q = (size_t)i * W + j;
     const float g = v.guide[q];
     float acc = (g > 0.f && g < 1.f) ? v.xh[q] + v.vh[q] : 0.f;
-    const int my = rp / (2 * H) + 1, mx = rp / (2 * W) + 1;
-    for (int m = -my; m <= my; ++m)
-        for (int cy = 0; cy < 2; ++cy) {
-            const int pi = cy == 0 ? 2 * H * m - 1 - i : 2 * H * m + i;
-            if (pi < -rp || pi >= H + rp) continue;
-            for (int n = -mx; n <= mx; ++n)
-                for (int cx = 0; cx < 2; ++cx) {
-                    const int pj = cx == 0 ? 2 * W * n - 1 - j : 2 * W * n + j;
-                    if (pj < -rp || pj >= W + rp) continue;
-                    acc += gather_ge(v.Gp, pi, pj, rp, rs, tiles_y, tiles_x, chunks);
-                }
-        }
+    if (rp < H && rp < W) {
+        int ri[3], rj[3], ni = 0, nj = 0;
+        if (i < rp) ri[ni++] = -1 - i;
+        ri[ni++] = i;
+        if (i >= H - rp) ri[ni++] = 2 * H - 1 - i;
+        if (j < rp) rj[nj++] = -1 - j;
+        rj[nj++] = j;
+        if (j >= W - rp) rj[nj++] = 2 * W - 1 - j;
+        for (int a = 0; a < ni; ++a)
+            for (int b = 0; b < nj; ++b) acc += gather_ge(v.gpart, ri[a], rj[b], rp, rs, tiles_y, tiles_x, chunks, qw);
+    } else {
+        const int my = rp / (2 * H) + 1, mx = rp / (2 * W) + 1;
+        for (int m = -my; m <= my; ++m)
+            for (int cy = 0; cy < 2; ++cy) {
+                const int pi = cy == 0 ? 2 * H * m - 1 - i : 2 * H * m + i;
+                if (pi < -rp || pi >= H + rp) continue;
+                for (int n = -mx; n <= mx; ++n)
+                    for (int cx = 0; cx < 2; ++cx) {
+                        const int pj = cx == 0 ? 2 * W * n - 1 - j : 2 * W * n + j;
+                        if (pj < -rp || pj >= W + rp) continue;
+                        acc += gather_ge(v.gpart, pi, pj, rp, rs, tiles_y, tiles_x, chunks, qw);
+                    }
+            }
+    }
     v.guide_bar[q] = acc;
 }
 
@@ -855,6 +1126,21 @@ size_t pairs_g_smem(int N, int rs) {
 size_t pairs_b_smem(int T, int rs) {
     return sizeof(float) * (size_t)(2 * T + 1) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
 }
+// the fused pass B with the patch-distance adjoint: fields, guide, accumulator, D-hat and
+// row sums; used for patch radii 1 to 3 while two blocks fit on an SM, otherwise pass B
+// writes the D-hat planes and the box-and-gather kernel reads them
+size_t pairs_bd_smem(int T, int rp, int rs, int dtype) {
+    const int esz = dtype == DSGNLM_F32 ? 4 : 2;
+    const int DH = kQH + 2 * rp, P = (T + 1) / 2;
+    const size_t fcells = (size_t)bd_field_h(rp, rs) * bd_field_w(rs);
+    return 2 * (size_t)bd_stage_bytes(DH, bd_box_w(esz), esz) + 2 * (size_t)bd_stage_bytes(DH, bd_box_w(4), 4) +
+           sizeof(float) * 2 * (size_t)DH * 32 + sizeof(float2) * 2 * (size_t)P * fcells + sizeof(float) * fcells +
+           sizeof(float) * 2 * (size_t)bg_win_h(rs) * bd_win_w(rp, rs);
+}
+constexpr size_t kBdSmemMax = 110 * 1024;
+bool use_pairs_bd(int T, int rp, int rs, int dtype) {
+    return rp >= 1 && rp <= 3 && pairs_bd_smem(T, rp, rs, dtype) <= kBdSmemMax;
+}
 
 }  // namespace
 
@@ -883,6 +1169,12 @@ struct lpnp_tape {
     int hs_count = 0;
     cudaEvent_t staged = nullptr;  // the upload from `stage` has been read
     cudaEvent_t ev = nullptr;      // fork and join of the images' handle streams
+    // tensor maps of the fused pass B (the handle's weight planes and this tape's G
+    // planes), encoded again when the planes, sizes or type change
+    alignas(64) unsigned char bd_kmap[128], bd_gmap[128];
+    const void* bd_kbase = nullptr;
+    const void* bd_gbase = nullptr;
+    int bd_key[5] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -1203,9 +1495,13 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     // patch-distance adjoint: tiles of the extended grid, the half offsets in kPairSplit
     // chunks (a number that does not depend on the batch, so that an image's sums have
     // the same order alone and in a batch)
-    const int bg_ty = (H + 2 * rp + kQH - 1) / kQH, bg_tx = (W + 2 * rp + kQW - 1) / kQW;
+    const bool fused = use_pairs_bd(T, rp, rs, lead->den->dtype);
+    const int bg_qw = fused ? bd_qw(rp) : kQW;  // tile width (the fused pass: the window 32 wide)
+    const int bg_ty = (H + 2 * rp + kQH - 1) / kQH, bg_tx = (W + 2 * rp + bg_qw - 1) / bg_qw;
     const int bg_chunks = std::min(kPairSplit, nh);
-    const size_t bg_part = (size_t)bg_chunks * bg_ty * bg_tx * bg_win_h(rs) * bg_win_w(rs);
+    const size_t bg_part = (size_t)bg_chunks * bg_ty * bg_tx * bg_win_h(rs) * (bg_qw + 2 * rs);
+    const int nbd = bg_tx * bg_ty * bg_chunks;  // blocks of the fused pass (with the offset chunks)
+    const int nhb = fused ? nbd : npb;         // blocks that write dL/dh partials
     for (int i = 0; i < count; ++i) {
         lpnp_tape* tp = tapes[i];
         DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->gs, &tp->dh, &tp->base};
@@ -1213,12 +1509,13 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
         TAPE_CK(tp->thp.ensure(sizeof(float) * n * (T > 0 ? T : 1)));
         TAPE_CK(tp->dh0.ensure(sizeof(float) * n * kPairSplit));
-        TAPE_CK(tp->Dhat.ensure(sizeof(float) * (size_t)nh * H * plane_pitch(W)));
-        // the G planes, later the partials of the patch-distance adjoint (pass B has then
-        // read G)
-        TAPE_CK(tp->Gp.ensure(sizeof(float) * std::max((size_t)nh * H * plane_pitch(W), bg_part)));
+        // fused: the partials of the patch-distance adjoint in the D-hat memory (no D-hat
+        // planes); otherwise the D-hat planes, and the partials in the G memory once pass
+        // B has read G
+        TAPE_CK(tp->Dhat.ensure(sizeof(float) * (fused ? bg_part : (size_t)nh * H * plane_pitch(W))));
+        TAPE_CK(tp->Gp.ensure(sizeof(float) * std::max((size_t)nh * H * plane_pitch(W), fused ? 0 : bg_part)));
         TAPE_CK(tp->rho_part.ensure(sizeof(double) * nrb));
-        TAPE_CK(tp->h_part.ensure(sizeof(double) * npb));
+        TAPE_CK(tp->h_part.ensure(sizeof(double) * std::max(npb, nhb)));
         TAPE_CK(tp->m_part.ensure(sizeof(double) * npb));
         TAPE_CK(tp->mh.ensure(sizeof(double) * 3));
     }
@@ -1226,8 +1523,24 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     std::vector<TapeView> views(count);
     std::vector<BatchInst> insts((size_t)(N + T) * count);
     for (int i = 0; i < count; ++i) {
-        const lpnp_tape* tp = tapes[i];
+        lpnp_tape* tp = tapes[i];
         views[i] = make_view(tp, nullptr, x_bar[i], y_bar[i], guide_bar[i]);
+        views[i].gpart = fused ? tp->Dhat.as<float>() : tp->Gp.as<float>();
+        if (fused) {
+            const int dt = dens[i]->dtype;
+            const int key[5] = {H, W, nh, dt, rp};
+            if (tp->bd_kbase != dens[i]->planes.p || tp->bd_gbase != tp->Gp.p ||
+                std::memcmp(key, tp->bd_key, sizeof key) != 0) {
+                const int esz = dt == DSGNLM_F32 ? 4 : 2;
+                TAPE_CK(encode_tile_map(tp->bd_kmap, dens[i]->planes.p, dt, H, W, nh, bd_box_w(esz), kQH + 2 * rp));
+                TAPE_CK(encode_tile_map(tp->bd_gmap, tp->Gp.p, DSGNLM_F32, H, W, nh, bd_box_w(4), kQH + 2 * rp));
+                tp->bd_kbase = dens[i]->planes.p;
+                tp->bd_gbase = tp->Gp.p;
+                std::memcpy(tp->bd_key, key, sizeof key);
+            }
+            std::memcpy(views[i].bd_kmap, tp->bd_kmap, 128);
+            std::memcpy(views[i].bd_gmap, tp->bd_gmap, 128);
+        }
         const float* dT = tp->Dh.as<float>() + (size_t)T * n;
         for (int k = 0; k < N; ++k) insts[(size_t)k * count + i] = p1_inst(dens[i], dT, tp->AZ.as<float>() + (size_t)k * n);
         for (int p = 0; p < T; ++p)
@@ -1318,22 +1631,50 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         count_launches(1);
         TAPE_CK(cudaGetLastError());
     }
-    // pair pass B: D-hat planes and dL/dh partials
-    switch (dtype) {
-        case DSGNLM_F32: TAPE_CK(pairs_b(float{})); break;
-        case DSGNLM_F16: TAPE_CK(pairs_b(__half{})); break;
-        default: TAPE_CK(pairs_b(__nv_bfloat16{})); break;
-    }
-    // patch distances back to the guide: box sums and the scatter of every offset per
-    // tile of the extended grid, then the gather of the partials and the fold through
-    // the reflection
-    {
+    if (fused) {
+        // pair pass B with the box sums and the scatter of the patch-distance adjoint
+        auto bd = [&](auto wt) -> cudaError_t {
+            using WT = decltype(wt);
+            const size_t smem = pairs_bd_smem(T, rp, rs, dtype);
+            auto run = [&](auto kern) -> cudaError_t {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                kern<<<dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), smem, st>>>(tb.views, bg_chunks, err,
+                                                                                     kDefaultWaitBudget);
+                return cudaGetLastError();
+            };
+            if (rp == 2 && rs == 7 && T == 4) return run(adj_pairs_bd_kernel<WT, 2, 7, 4>);
+            switch (rp) {
+                case 1: return run(adj_pairs_bd_kernel<WT, 1, 0, -1>);
+                case 2: return run(adj_pairs_bd_kernel<WT, 2, 0, -1>);
+                default: return run(adj_pairs_bd_kernel<WT, 3, 0, -1>);
+            }
+        };
+        switch (dtype) {
+            case DSGNLM_F32: TAPE_CK(bd(float{})); break;
+            case DSGNLM_F16: TAPE_CK(bd(__half{})); break;
+            default: TAPE_CK(bd(__nv_bfloat16{})); break;
+        }
+        count_launches(1);
+        adj_fold_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, bg_ty, bg_tx, bg_chunks, bg_qw);
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+    } else {
+        // pair pass B: D-hat planes and dL/dh partials
+        switch (dtype) {
+            case DSGNLM_F32: TAPE_CK(pairs_b(float{})); break;
+            case DSGNLM_F16: TAPE_CK(pairs_b(__half{})); break;
+            default: TAPE_CK(pairs_b(__nv_bfloat16{})); break;
+        }
+        // patch distances back to the guide: box sums and the scatter of every offset per
+        // tile of the extended grid, then the gather of the partials and the fold through
+        // the reflection
         const size_t bsmem =
             sizeof(float) * (size_t)(2 * bg_win_h(rs) * bg_win_w(rs) + (kQH + 2 * rp) * (kQW + 2 * rp) +
                                      (kQH + 2 * rp) * kQW);
         TAPE_CK(cudaFuncSetAttribute(adj_boxguide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
         adj_boxguide_kernel<<<dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), bsmem, st>>>(tb.views, bg_chunks);
-        adj_fold_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, bg_ty, bg_tx, bg_chunks);
+        adj_fold_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, bg_ty, bg_tx, bg_chunks, bg_qw);
         count_launches(2);
         TAPE_CK(cudaGetLastError());
     }
@@ -1341,7 +1682,7 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     for (int i = 0; i < count; ++i)
         TAPE_CK(launch_sr_forward(tapes[i]->gs.as<float>(), H, W, lead->taps, nullptr, 0.f, y_bar[i], st));
     adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 1, npb, nrb);
-    adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 2, npb, nrb);
+    adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 2, nhb, nrb);
     count_launches(2);
     TAPE_CK(cudaGetLastError());
     // every image's (m, rho, h) cotangents and the wait-error word, read back once

@@ -23,6 +23,33 @@ void count_launches(uint64_t n) {
     if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }
 void set_capture_counting(bool recording) { g_capturing = recording; }
+// Tensor map of planes [nh][H][pitch] of the storage type `dtype`, pitch
+// plane_pitch(W); the tensor's rows are W wide, so boxes read zeros past column W - 1
+// (and past row H - 1, and before row or column 0).
+cudaError_t encode_tile_map(void* out, const void* base, int dtype, int H, int W, int nh, int box_w, int box_h) {
+    // looked up once (a thread-safe static initialisation)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? (PFN_cuTensorMapEncodeTiled_v12000)fn
+                                                                      : nullptr;
+    }();
+    if (!encode) return cudaErrorNotSupported;
+    const size_t esz = dtype == DSGNLM_F32 ? 4 : 2;
+    const CUtensorMapDataType dt = dtype == DSGNLM_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dtype == DSGNLM_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nh};
+    const cuuint64_t strides[2] = {(cuuint64_t)plane_pitch(W) * esz, (cuuint64_t)plane_pitch(W) * H * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode((CUtensorMap*)out, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 }  // namespace dsg
 
 using namespace dsg;
@@ -50,28 +77,7 @@ dsgnlm_status fail_cuda(cudaError_t e) {
 
 // Tensor map of the weight planes [n_h][H][pitch] for the TMA stencil path.
 cudaError_t encode_planes_map(void* out, void* planes, int dtype, int H, int W, int nh) {
-    // looked up once (a thread-safe static initialisation)
-    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-        cudaDriverEntryPointQueryResult q;
-        void* fn = nullptr;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                         cudaEnableDefault, &q);
-        return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? (PFN_cuTensorMapEncodeTiled_v12000)fn
-                                                                      : nullptr;
-    }();
-    if (!encode) return cudaErrorNotSupported;
-    const size_t esz = dtype == DSGNLM_F32 ? 4 : 2;
-    const CUtensorMapDataType dt = dtype == DSGNLM_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                   : dtype == DSGNLM_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                         : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nh};
-    const cuuint64_t strides[2] = {(cuuint64_t)plane_pitch(W) * esz, (cuuint64_t)plane_pitch(W) * H * esz};
-    const cuuint32_t box[3] = {(cuuint32_t)tma_tile_w(), (cuuint32_t)tma_tile_h(), 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode((CUtensorMap*)out, dt, 3, planes, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    return encode_tile_map(out, planes, dtype, H, W, nh, tma_tile_w(), tma_tile_h());
 }
 
 // Split the column offsets -rs..rs into `n` contiguous slices of about equal

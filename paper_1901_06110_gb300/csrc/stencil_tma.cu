@@ -32,6 +32,7 @@
 #include "combine.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace dsg {
 
@@ -44,54 +45,12 @@ constexpr int kConsumerWarps = kConsumers / 32;
 constexpr int kThreads = kConsumers + 32;  // + one producer warp
 constexpr long long kWaitBudget = kDefaultWaitBudget;  // cycles (about 2 s) before a wait gives up
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 // Wait for the phase with the given parity to complete; false after the budget.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > kWaitBudget) return false;
-    }
-    return true;
-}
-
-// A consumer's wait for a plane: gives up after `budget` cycles.  A budget of 0
-// gives up at once, as if the copy had not landed in time (the handle's test hook
-// for the timeout path; the default is kWaitBudget).
-__device__ __forceinline__ bool mbar_wait_consumer(uint64_t* bar, unsigned parity, long long budget) {
-    if (budget <= 0) return false;
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > budget) return false;
     }
     return true;
 }
@@ -106,23 +65,6 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, unsigned parit
         if (clock64() - t0 > kWaitBudget) return false;
     }
     return true;
-}
-
-// L2 policy of the weight stream: each weight is read once per pass, so its lines
-// are evicted first and the per-pixel arrays of the iteration stay in L2.
-__device__ __forceinline__ uint64_t evict_first_policy() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                            int z, uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "l"(policy)
-        : "memory");
 }
 
 __device__ __forceinline__ void consumer_sync() {

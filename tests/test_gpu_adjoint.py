@@ -36,7 +36,8 @@ def _gpu(inst, guide, h, rho, params):
 @pytest.mark.parametrize("H,W,rp,rs,T,N", [(16, 16, 2, 7, 4, 10), (16, 20, 1, 3, 2, 5),
                                             (16, 16, 1, 2, 0, 1),   # no balancing pass, one iteration
                                             (12, 16, 2, 3, 1, 2),   # one pass, H not a tile multiple
-                                            (40, 72, 3, 5, 2, 3)])  # 3 x 3 tiles of the extended grid
+                                            (40, 72, 3, 5, 2, 3),   # 3 x 3 tiles of the extended grid
+                                            (24, 40, 4, 3, 1, 2)])  # patch radius 4: D-hat planes, then box and gather
 def test_adjoint_matches_torch_autograd(gpu_lib, H, W, rp, rs, T, N):
     from paper_1901_06110_gb300.autograd import UnrollParams
     wl, inst, guide = _case(H, W, 9)

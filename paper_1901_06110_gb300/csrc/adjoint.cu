@@ -74,6 +74,7 @@ struct TapeView {
     float* gpart;         // partials of the patch-distance adjoint (the G or the D-hat memory)
     alignas(64) unsigned char bd_kmap[128];  // tensor maps of the weight and G planes for the fused
     alignas(64) unsigned char bd_gmap[128];  // pass B (boxes of the D-hat window)
+    alignas(64) unsigned char gt_kmap[128];  // tensor map of the weight planes for pass G (kQH x 32 tiles)
     double *mh, *rho_part, *h_part, *m_part;  // mh: cotangents of m, rho, h
     float* x_out;         // x_N (caller's)
     const float* x_bar;   // its cotangent (caller's)
@@ -321,159 +322,6 @@ __global__ void __launch_bounds__(256) adj_ata_update_kernel(const TapeView* __r
                                   }
                               }
                           });
-}
-
-// Pair pass G, over the half-window pairs (s, r = s + o): the pair term
-//   G_sr = sum_k (a_k(s) - a_k(r)) (z_k(r) - z_k(s))
-// stored as planes like K1 (0 where r is off the image), the forward half of
-// dh0(s) = sum_o G_sr d_r K1_sr, and per-block partials of
-// -(1/m^2) sum over half-window pairs of G d_s d_r K1.  G is symmetric in (s, r), so
-// the other half of dh comes from these planes (pair pass T).  The half offsets are
-// split into kPairSplit contiguous chunks (grid z = image * kPairSplit + chunk); chunk
-// z writes its own dh0 plane and partials.
-// Staged over the tile and its forward halo: (a_k, z_k, a_{k+1}, z_{k+1}) as one float4
-// per pair of iterations (zeros past N, which add exact zeros), then d.  With NP > 0
-// (NP = ceil(N / 2)) the values at s are held in registers and the loop is unrolled;
-// NP = 0 reads them from shared memory.  Both sum in the same order.
-template <typename WT, int NP>
-__global__ void __launch_bounds__(256, 2) adj_pairs_g_kernel(const TapeView* __restrict__ tv) {
-    extern __shared__ float4 S4[];
-    const int img = blockIdx.z / kPairSplit, zc = blockIdx.z - img * kPairSplit;
-    const TapeView& v = tv[img];
-    const WT* __restrict__ P = static_cast<const WT*>(v.planes);
-    const int H = v.H, W = v.W, rs = v.rs, N = v.N;
-    const float* AZ = v.AZ;
-    const size_t n = (size_t)H * W;
-    const float* d = v.Dh + (size_t)v.T * n;
-    const float inv_m = __ldg(v.m + 1);
-    const int y0 = blockIdx.y * kAdjTH, x0 = blockIdx.x * kAdjTW;
-    const int RH = kAdjTH + rs, RW = kAdjTW + 2 * rs, cells = RH * RW;
-    const int np = (N + 1) >> 1;
-    float* Sd = reinterpret_cast<float*>(S4 + (size_t)np * cells);
-    const int nh = num_half_offsets(rs);
-    const int kz0 = nh * zc / kPairSplit, kz1 = nh * (zc + 1) / kPairSplit;
-    {
-        const int tid = threadIdx.y * 32 + threadIdx.x;
-        for (int idx = tid; idx < cells; idx += 256) {
-            const int ra = idx / RW, cb = idx - ra * RW;
-            const int i = y0 + ra, j = x0 - rs + cb;
-            const bool in = i < H && j >= 0 && j < W;
-            const size_t q = in ? (size_t)i * W + j : 0;
-            for (int kp = 0; kp < np; ++kp) {
-                const int k0 = 2 * kp, k1 = k0 + 1;
-                float4 vv = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (in) {
-                    vv.x = AZ[(size_t)k0 * n + q];
-                    vv.y = AZ[(size_t)(N + k0) * n + q];
-                    if (k1 < N) {
-                        vv.z = AZ[(size_t)k1 * n + q];
-                        vv.w = AZ[(size_t)(N + k1) * n + q];
-                    }
-                }
-                S4[(size_t)kp * cells + idx] = vv;
-            }
-            Sd[idx] = in ? d[q] : 0.f;
-        }
-    }
-    __syncthreads();
-    const int Wp = plane_pitch(W);
-    const size_t plane = (size_t)H * Wp;
-    float mpart = 0.f;
-    const int j = x0 + threadIdx.x;
-    for (int py = threadIdx.y; py < kAdjTH; py += 8) {
-        const int i = y0 + py;
-        if (i >= H || j >= W) continue;
-        const int cs = py * RW + threadIdx.x + rs;  // cell of s
-        float4 sv[NP > 0 ? NP : 1];
-        if constexpr (NP > 0) {
-#pragma unroll
-            for (int kp = 0; kp < NP; ++kp) sv[kp] = S4[kp * cells + cs];
-        }
-        const float ds = Sd[cs];
-        float accd = 0.f, accm = 0.f;
-        int oy, ox;
-        half_offset(kz0, rs, oy, ox);
-        // branch-free body (an off-image partner r reads staged zeros and adds an exact
-        // zero), so the unrolled iterations issue their loads together
-#pragma unroll 4
-        for (int k = kz0; k < kz1; ++k) {
-            {
-                const size_t at = (size_t)k * plane + (size_t)i * Wp + j;
-                const int rj = j + ox;
-                const bool in = i + oy < H && rj >= 0 && rj < W;
-                const float K = in ? to_f32(P[at]) : 0.f;
-                const int cr = cs + oy * RW + ox;
-                float G = 0.f;
-                if constexpr (NP > 0) {
-#pragma unroll
-                    for (int kp = 0; kp < NP; ++kp) {
-                        const float4 r = S4[kp * cells + cr];
-                        G = fmaf(sv[kp].x - r.x, r.y - sv[kp].y, G);
-                        G = fmaf(sv[kp].z - r.z, r.w - sv[kp].w, G);
-                    }
-                } else {
-                    for (int kp = 0; kp < np; ++kp) {
-                        const float4 a = S4[kp * cells + cs], r = S4[kp * cells + cr];
-                        G = fmaf(a.x - r.x, r.y - a.y, G);
-                        G = fmaf(a.z - r.z, r.w - a.w, G);
-                    }
-                }
-                v.Gp[at] = in ? G : 0.f;
-                const float dr = Sd[cr];
-                accd = fmaf(G * dr, K, accd);
-                accm = fmaf(G * ds * dr, K, accm);
-            }
-            if (++ox > rs) {
-                ++oy;
-                ox = -rs;
-            }
-        }
-        v.dh0[(size_t)zc * n + (size_t)i * W + j] = accd;
-        mpart -= accm * inv_m * inv_m;
-    }
-    const int t = threadIdx.y * 32 + threadIdx.x;
-    const double acc = block_sum_256(mpart, t);
-    if (t == 0) v.m_part[(zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
-}
-
-// Pair pass T: dh(s) = (1/m) (dh0(s) + sum_o G_{s-o, s} d_{s-o} K1_{s-o, s}), dh0 the
-// sum of pass G's chunk planes (in chunk order) and the backward half-window read from
-// the planes at s - o
-template <typename WT>
-__global__ void __launch_bounds__(256) adj_pairs_t_kernel(const TapeView* __restrict__ tv) {
-    const TapeView& v = tv[blockIdx.z];
-    const WT* __restrict__ P = static_cast<const WT*>(v.planes);
-    const int H = v.H, W = v.W, rs = v.rs;
-    const int j = blockIdx.x * 32 + threadIdx.x;
-    const int i = blockIdx.y * 8 + threadIdx.y;
-    if (i >= H || j >= W) return;
-    const float inv_m = __ldg(v.m + 1);
-    const int Wp = plane_pitch(W);
-    const size_t plane = (size_t)H * Wp;
-    const size_t n = (size_t)H * W;
-    const float* d = v.Dh + (size_t)v.T * n;
-    const float* Gp = v.Gp;
-    float acc = v.dh0[(size_t)i * W + j];
-    for (int z = 1; z < kPairSplit; ++z) acc += v.dh0[z * n + (size_t)i * W + j];
-    for (int oy = 0; oy <= rs && i - oy >= 0; ++oy) {
-        const int ri = i - oy;
-        const int ox0 = oy == 0 ? 1 : -rs;
-        int k = oy == 0 ? 0 : rs + (oy - 1) * (2 * rs + 1);  // half offset of (oy, ox0)
-        const size_t row = (size_t)ri * Wp;
-        const float* drow = d + (size_t)ri * W;
-        // predicated loads (no early exit), so the unrolled loads issue together
-#pragma unroll 4
-        for (int ox = ox0; ox <= rs; ++ox, ++k) {
-            const int rj = j - ox;
-            const bool in = rj >= 0 && rj < W;
-            const size_t at = (size_t)k * plane + row + (in ? rj : 0);
-            const float g = in ? Gp[at] : 0.f;
-            const float w = in ? to_f32(P[at]) : 0.f;
-            const float dv = in ? drow[rj] : 0.f;
-            acc = fmaf(g * dv, w, acc);
-        }
-    }
-    v.dh[(size_t)i * W + j] = acc * inv_m;
 }
 
 // fixed-order sum of one partial array of each image into one of its cotangents:
@@ -1094,6 +942,189 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restric
     v.guide_bar[q] = acc;
 }
 
+// Pair pass G with the mirrored half of the scaling's cotangent.  Over the half-window
+// pairs (s, r = s + o):
+//   G_sr = sum_k (a_k(s) - a_k(r)) (z_k(r) - z_k(s)),
+// stored as planes like K1 (values where s + o leaves the image are not used: K1 is
+// zero there), per-block partials of -(1/m^2) sum G d_s d_r K1, and the window partials
+// of dh0 = sum over the full window of G_sr d_r K1_sr: the forward term G d_r K1 of s
+// and the mirrored term G d_s K1 of r (G and K1 are symmetric in (s, r)).
+// Per tile of kQH x 32 pixels and chunk of the half offsets (grid z = image * chunks +
+// chunk), one offset at a time: each thread forms G for its two pixels, adds the
+// forward terms in registers and the mirrored terms into a shared accumulator over the
+// tile, rs rows below and rs columns either side (no two pixels of one offset share
+// r; the offsets are separated by a barrier), which the block writes as one window
+// partial (its own pixels' forward sums added).  The weight tile of every offset
+// arrives by TMA two offsets ahead.  Staged over the window: (a_2u, a_2u+1, z_2u,
+// z_2u+1) as one float4 per pair of iterations (zeros past N and off the image) and d;
+// the differences and products of the two iterations of a pair go through the packed
+// FP32x2 units (a difference as an FMA with -1, which is exact).  With NPK > 0
+// (= ceil(N / 2)) the values at s are held in registers; NPK = 0 reads them from
+// shared memory.
+template <typename WT, int NPK>
+__global__ void __launch_bounds__(256, 2)
+    adj_pairs_gt_kernel(const TapeView* __restrict__ tv, int chunks, unsigned* err, long long budget) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int KBYTES = kQH * 32 * (int)sizeof(WT);
+    constexpr int KST = bd_stage_bytes(kQH, 32, (int)sizeof(WT));
+    constexpr int NR = NPK > 0 ? NPK : 1;
+    const int img = blockIdx.z / chunks, zc = blockIdx.z - img * chunks;
+    const TapeView& v = tv[img];
+    const int H = v.H, W = v.W, rs = v.rs, N = v.N;
+    const int np = NPK > 0 ? NPK : (N + 1) / 2;
+    const int nh = num_half_offsets(rs);
+    const int k0 = nh * zc / chunks, k1 = nh * (zc + 1) / chunks;
+    const int y0 = blockIdx.y * kQH, x0 = blockIdx.x * 32;
+    const int FH = kQH + rs, FW = 32 + 2 * rs, fcells = FH * FW;  // window: rows y0 + [0, FH), cols x0 - rs + [0, FW)
+    const size_t n = (size_t)H * W;
+    float4* AZ4 = reinterpret_cast<float4*>(smem + 2 * KST);  // [np][FH][FW]
+    float* Sd = reinterpret_cast<float*>(AZ4 + (size_t)np * fcells);
+    float* Ac = Sd + fcells;
+    __shared__ __align__(8) uint64_t bars[2];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + tx;
+    const CUtensorMap* kmap = reinterpret_cast<const CUtensorMap*>(v.gt_kmap);
+    uint64_t policy = 0;
+    auto issue = [&](int k, int st) {
+        mbar_arrive_expect_tx(&bars[st], (unsigned)KBYTES);
+        tma_load_3d(smem + st * KST, kmap, &bars[st], x0, y0, k, policy);
+    };
+    if (tid == 0) {
+        tmap_acquire(kmap);
+        policy = evict_first_policy();
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (k0 < k1) issue(k0, 0);
+        if (k0 + 1 < k1) issue(k0 + 1, 1);
+    }
+    const float* AZ = v.AZ;
+    const float* d = v.Dh + (size_t)v.T * n;
+    for (int idx = tid; idx < fcells; idx += 256) {
+        const int a = idx / FW, b = idx - a * FW;
+        const int i = y0 + a, j = x0 - rs + b;
+        const bool in = i < H && j >= 0 && j < W;
+        const size_t q = in ? (size_t)i * W + j : 0;
+        for (int u = 0; u < np; ++u) {
+            const int ka = 2 * u, kb = ka + 1;
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in) {
+                t.x = AZ[(size_t)ka * n + q];
+                t.z = AZ[(size_t)(N + ka) * n + q];
+                if (kb < N) {
+                    t.y = AZ[(size_t)kb * n + q];
+                    t.w = AZ[(size_t)(N + kb) * n + q];
+                }
+            }
+            AZ4[u * fcells + idx] = t;
+        }
+        Sd[idx] = in ? d[q] : 0.f;
+        Ac[idx] = 0.f;
+    }
+    __syncthreads();
+    // the thread's pixels (ty + 8 m, tx), m = 0, 1, of the tile
+    const int Wp = plane_pitch(W);
+    const size_t plane = (size_t)H * Wp;
+    const int j = x0 + tx;
+    const int cs0 = ty * FW + tx + rs;
+    float2 sa[2][NR], sz[2][NR];
+    float ds[2], accd[2] = {0.f, 0.f};
+    bool in[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int cs = cs0 + 8 * m * FW;
+        in[m] = y0 + ty + 8 * m < H && j < W;
+        ds[m] = Sd[cs];
+        if constexpr (NPK > 0) {
+#pragma unroll
+            for (int u = 0; u < NPK; ++u) {
+                const float4 t = AZ4[u * fcells + cs];
+                sa[m][u] = make_float2(t.x, t.y);
+                sz[m][u] = make_float2(t.z, t.w);
+            }
+        }
+    }
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float accm = 0.f;
+    bool gave_up = false;
+    int oy, ox;
+    half_offset(k0, rs, oy, ox);
+    for (int k = k0; k < k1; ++k) {
+        const int st = (k - k0) & 1;
+        const unsigned par = (unsigned)((k - k0) >> 1) & 1u;
+        if (!gave_up && !mbar_try_wait(&bars[st], par)) {
+            if (*(volatile unsigned*)err != 0u || !mbar_wait_consumer(&bars[st], par, budget)) {
+                gave_up = true;
+                if (tid == 0) atomicOr(err, 1u);
+            }
+        }
+        const WT* Kt = reinterpret_cast<const WT*>(smem + st * KST);
+        const int fo = oy * FW + ox;
+        float* Gk = v.Gp + (size_t)k * plane;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int row = ty + 8 * m;
+            const float K = to_f32(Kt[row * 32 + tx]);
+            const int cs = cs0 + 8 * m * FW, cr = cs + fo;
+            float2 acc = make_float2(0.f, 0.f);
+            if constexpr (NPK > 0) {
+#pragma unroll
+                for (int u = 0; u < NPK; ++u) {
+                    const float4 r4 = AZ4[u * fcells + cr];
+                    const float2 da = __ffma2_rn(make_float2(r4.x, r4.y), m1, sa[m][u]);  // a(s) - a(r)
+                    const float2 dz = __ffma2_rn(sz[m][u], m1, make_float2(r4.z, r4.w));  // z(r) - z(s)
+                    acc = __ffma2_rn(da, dz, acc);
+                }
+            } else {
+                for (int u = 0; u < np; ++u) {
+                    const float4 s4 = AZ4[u * fcells + cs], r4 = AZ4[u * fcells + cr];
+                    const float2 da = __ffma2_rn(make_float2(r4.x, r4.y), m1, make_float2(s4.x, s4.y));
+                    const float2 dz = __ffma2_rn(make_float2(s4.z, s4.w), m1, make_float2(r4.z, r4.w));
+                    acc = __ffma2_rn(da, dz, acc);
+                }
+            }
+            const float G = acc.x + acc.y;
+            if (in[m]) Gk[(size_t)(y0 + row) * Wp + j] = G;
+            const float dr = Sd[cr];
+            const float GK = G * K;
+            accd[m] = fmaf(GK, dr, accd[m]);
+            accm = fmaf(GK * ds[m], dr, accm);
+            Ac[cr] = fmaf(GK, ds[m], Ac[cr]);
+        }
+        __syncthreads();  // the stage read; the mirrored terms of this offset added
+        if (tid == 0 && k + 2 < k1) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(k + 2, st);
+        }
+        if (++ox > rs) {
+            ++oy;
+            ox = -rs;
+        }
+    }
+    const float inv_m = __ldg(v.m + 1);
+    const double macc = block_sum_256(-accm * inv_m * inv_m, tid);
+    if (tid == 0) v.m_part[(zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = macc;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) Ac[cs0 + 8 * m * FW] += accd[m];
+    __syncthreads();
+    float* out = v.dh0 + (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)fcells;
+    for (int idx = tid; idx < fcells; idx += 256) out[idx] = Ac[idx];
+}
+
+// dh(s) = (1/m) dh0(s), dh0 gathered from the window partials of pair pass G (every
+// chunk, and every tile whose window holds s, in a fixed order)
+__global__ void __launch_bounds__(256) adj_dh_kernel(const TapeView* __restrict__ tv, int tiles_y, int tiles_x,
+                                                     int chunks) {
+    const TapeView& v = tv[blockIdx.z];
+    const int H = v.H, W = v.W;
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= H || j >= W) return;
+    const float inv_m = __ldg(v.m + 1);
+    v.dh[(size_t)i * W + j] = gather_ge(v.dh0, i, j, 0, v.rs, tiles_y, tiles_x, chunks, 32) * inv_m;
+}
+
 // the scalar cotangents of every image (m, rho, h) in one array, read back in one copy
 __global__ void adj_gather_scalars_kernel(const TapeView* __restrict__ tv, int count, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1120,8 +1151,11 @@ cudaError_t by_blur_radius(int r, F&& f) {
     }
 }
 
-size_t pairs_g_smem(int N, int rs) {
-    return (sizeof(float4) * (size_t)((N + 1) / 2) + sizeof(float)) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
+size_t pairs_g_smem(int N, int rs, int dtype) {
+    const int esz = dtype == DSGNLM_F32 ? 4 : 2;
+    const size_t fcells = (size_t)(kQH + rs) * (32 + 2 * rs);
+    return 2 * (size_t)bd_stage_bytes(kQH, 32, esz) + sizeof(float4) * (size_t)((N + 1) / 2) * fcells +
+           sizeof(float) * 2 * fcells;
 }
 size_t pairs_b_smem(int T, int rs) {
     return sizeof(float) * (size_t)(2 * T + 1) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
@@ -1175,6 +1209,9 @@ struct lpnp_tape {
     const void* bd_kbase = nullptr;
     const void* bd_gbase = nullptr;
     int bd_key[5] = {0, 0, 0, 0, 0};
+    alignas(64) unsigned char gt_kmap[128];  // the weight planes for pair pass G
+    const void* gt_kbase = nullptr;
+    int gt_key[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -1346,7 +1383,7 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
         return DSGNLM_EINVAL;
     if (!tma_path_supports(search_r) || count > kMaxBatch) return DSGNLM_EINVAL;
     // shared memory of the pair passes of the backward (fields over a tile + halo)
-    if (pairs_g_smem(iters, search_r) > 220 * 1024 || pairs_b_smem(balance_passes, search_r) > 220 * 1024)
+    if (pairs_g_smem(iters, search_r, DSGNLM_F32) > 220 * 1024 || pairs_b_smem(balance_passes, search_r) > 220 * 1024)
         return DSGNLM_EINVAL;
     lpnp_tape* lead = tapes[0];
     cudaStream_t st = dens[0]->stream;
@@ -1490,7 +1527,7 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     const int nh = num_half_offsets(rs);
     const dim3 pgrid2((W + 31) / 32, (H + 7) / 8, count);  // per-pixel passes in 32 x 8 blocks
     const int nrb = (int)(pgrid2.x * pgrid2.y);
-    const int pgx = (W + kAdjTW - 1) / kAdjTW, pgy = (H + kAdjTH - 1) / kAdjTH;
+    const int pgx = (W + kAdjTW - 1) / kAdjTW, pgy = (H + kAdjTH - 1) / kAdjTH;  // tiles of pair passes G and B
     const int npb = pgx * pgy * kPairSplit;  // pair-pass blocks (with the offset chunks)
     // patch-distance adjoint: tiles of the extended grid, the half offsets in kPairSplit
     // chunks (a number that does not depend on the batch, so that an image's sums have
@@ -1508,7 +1545,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
         TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
         TAPE_CK(tp->thp.ensure(sizeof(float) * n * (T > 0 ? T : 1)));
-        TAPE_CK(tp->dh0.ensure(sizeof(float) * n * kPairSplit));
+        // window partials of pair pass G (the forward and mirrored sums of dh0)
+        TAPE_CK(tp->dh0.ensure(sizeof(float) * (size_t)kPairSplit * pgx * pgy * (kQH + rs) * (32 + 2 * rs)));
         // fused: the partials of the patch-distance adjoint in the D-hat memory (no D-hat
         // planes); otherwise the D-hat planes, and the partials in the G memory once pass
         // B has read G
@@ -1526,6 +1564,16 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         lpnp_tape* tp = tapes[i];
         views[i] = make_view(tp, nullptr, x_bar[i], y_bar[i], guide_bar[i]);
         views[i].gpart = fused ? tp->Dhat.as<float>() : tp->Gp.as<float>();
+        {
+            const int dt = dens[i]->dtype;
+            const int key[4] = {H, W, nh, dt};
+            if (tp->gt_kbase != dens[i]->planes.p || std::memcmp(key, tp->gt_key, sizeof key) != 0) {
+                TAPE_CK(encode_tile_map(tp->gt_kmap, dens[i]->planes.p, dt, H, W, nh, 32, kQH));
+                tp->gt_kbase = dens[i]->planes.p;
+                std::memcpy(tp->gt_key, key, sizeof key);
+            }
+            std::memcpy(views[i].gt_kmap, tp->gt_kmap, 128);
+        }
         if (fused) {
             const int dt = dens[i]->dtype;
             const int key[5] = {H, W, nh, dt, rp};
@@ -1570,32 +1618,33 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         }));
         count_launches(1);
     }
-    // pair passes G and T, then the cotangent of m and its terms
+    // pair pass G with the mirrored terms, the gather of dh, then the cotangent of m and
+    // its terms
     auto pairs_gt = [&](auto wt) -> cudaError_t {
         using WT = decltype(wt);
-        const size_t smem = pairs_g_smem(N, rs);
+        const size_t smem = pairs_g_smem(N, rs, dtype);
         const dim3 grid(pgx, pgy, kPairSplit * count);
         auto run = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            kern<<<grid, dim3(32, 8), smem, st>>>(tb.views);
+            kern<<<grid, dim3(32, 8), smem, st>>>(tb.views, kPairSplit, err, kDefaultWaitBudget);
             return cudaGetLastError();
         };
         cudaError_t e;
         switch ((N + 1) / 2) {
-            case 1: e = run(adj_pairs_g_kernel<WT, 1>); break;
-            case 2: e = run(adj_pairs_g_kernel<WT, 2>); break;
-            case 3: e = run(adj_pairs_g_kernel<WT, 3>); break;
-            case 4: e = run(adj_pairs_g_kernel<WT, 4>); break;
-            case 5: e = run(adj_pairs_g_kernel<WT, 5>); break;
-            case 6: e = run(adj_pairs_g_kernel<WT, 6>); break;
-            case 7: e = run(adj_pairs_g_kernel<WT, 7>); break;
-            case 8: e = run(adj_pairs_g_kernel<WT, 8>); break;
-            default: e = run(adj_pairs_g_kernel<WT, 0>); break;
+            case 1: e = run(adj_pairs_gt_kernel<WT, 1>); break;
+            case 2: e = run(adj_pairs_gt_kernel<WT, 2>); break;
+            case 3: e = run(adj_pairs_gt_kernel<WT, 3>); break;
+            case 4: e = run(adj_pairs_gt_kernel<WT, 4>); break;
+            case 5: e = run(adj_pairs_gt_kernel<WT, 5>); break;
+            case 6: e = run(adj_pairs_gt_kernel<WT, 6>); break;
+            case 7: e = run(adj_pairs_gt_kernel<WT, 7>); break;
+            case 8: e = run(adj_pairs_gt_kernel<WT, 8>); break;
+            default: e = run(adj_pairs_gt_kernel<WT, 0>); break;
         }
         count_launches(1);
         if (e != cudaSuccess) return e;
-        adj_pairs_t_kernel<WT><<<pgrid2, dim3(32, 8), 0, st>>>(tb.views);
+        adj_dh_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, pgy, pgx, kPairSplit);
         adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 0, npb, nrb);
         adj_mterms_kernel<WT><<<count, 256, 0, st>>>(tb.views);
         count_launches(3);

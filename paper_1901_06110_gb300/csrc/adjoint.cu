@@ -71,10 +71,12 @@ struct TapeView {
     unsigned long long* mkey;
     int* sstar;           // first maximiser of d t
     float *xh, *vh, *uh, *zh, *g, *gs, *dh, *dh0, *base, *thp, *Dhat, *Gp, *AZ;
+    float* AZ4;           // (a_2u, a_2u+1, z_2u, z_2u+1) per pixel, u < ceil(N / 2) (pair pass G)
     float* gpart;         // partials of the patch-distance adjoint (the G or the D-hat memory)
     alignas(64) unsigned char bd_kmap[128];  // tensor maps of the weight and G planes for the fused
     alignas(64) unsigned char bd_gmap[128];  // pass B (boxes of the D-hat window)
     alignas(64) unsigned char gt_kmap[128];  // tensor map of the weight planes for pass G (kQH x 32 tiles)
+    alignas(64) unsigned char gt_amap[128];  // tensor map of the interleaved (a, z) copy (pass G windows)
     double *mh, *rho_part, *h_part, *m_part;  // mh: cotangents of m, rho, h
     float* x_out;         // x_N (caller's)
     const float* x_bar;   // its cotangent (caller's)
@@ -233,7 +235,8 @@ __global__ void __launch_bounds__(256) adj_xout_kernel(const TapeView* __restric
 // ----------------------------------------------------------------------- backward
 
 // cotangents cleared, xh = x_bar, and the iteration N - 1 inputs of the reverse sweep:
-// a_{N-1} = vh - uh = 0, z_{N-1} = x_N + u_{N-1}
+// a_{N-1} = vh - uh = 0, z_{N-1} = x_N + u_{N-1} (a in its plane, a and z in the
+// interleaved copy)
 __global__ void __launch_bounds__(256) adj_bwd_prep_kernel(const TapeView* __restrict__ tv, int nrb) {
     const TapeView& v = tv[blockIdx.z];
     const size_t n = (size_t)v.H * v.W;
@@ -246,7 +249,14 @@ __global__ void __launch_bounds__(256) adj_bwd_prep_kernel(const TapeView* __res
     v.uh[q] = 0.f;
     const int N = v.N;
     v.AZ[(size_t)(N - 1) * n + q] = 0.f;
-    v.AZ[(size_t)(2 * N - 1) * n + q] = v.X[(size_t)N * n + q] + v.U[(size_t)(N - 1) * n + q];
+    float* s4 = v.AZ4 + 4 * ((size_t)((N - 1) >> 1) * n + q);
+    const int lane = (N - 1) & 1;
+    s4[lane] = 0.f;
+    s4[2 + lane] = v.X[(size_t)N * n + q] + v.U[(size_t)(N - 1) * n + q];
+    if (lane == 0) {  // N odd: the pair's second iteration does not exist and adds zeros
+        s4[1] = 0.f;
+        s4[3] = 0.f;
+    }
 }
 
 // W a finished from the phase-1 partial sums (W a = c_s a_s + (d_s / m) sum_r K1 d_r a_r,
@@ -286,7 +296,8 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
 // Reverse iteration k, after g: ata = A^T A g on 32 x 32 tiles, then per pixel
 //   xh = mu (alpha g - ata), vh = mu rho g, uh = zh - mu rho g, gs += mu g (the
 //   observation's cotangent is A gs, A being linear), and for k > 0 the inputs of the
-//   earlier iteration: a_{k-1} = vh - uh, z_{k-1} = x_k + u_{k-1}.
+//   earlier iteration: a_{k-1} = vh - uh, z_{k-1} = x_k + u_{k-1} (a in its plane, a and
+//   z in the interleaved copy).
 // g is only read, so the halo reads do not race with the writes.
 template <int R>
 __global__ void __launch_bounds__(256) adj_ata_update_kernel(const TapeView* __restrict__ tv, int k) {
@@ -302,7 +313,7 @@ __global__ void __launch_bounds__(256) adj_ata_update_kernel(const TapeView* __r
     const float* xk = v.X + (size_t)k * n;
     const float* uprev = more ? v.U + (size_t)(k - 1) * n : nullptr;
     float* a_next = more ? v.AZ + (size_t)(k - 1) * n : nullptr;
-    float* z_next = more ? v.AZ + (size_t)(v.N + k - 1) * n : nullptr;
+    float* s4 = more ? v.AZ4 + 4 * (size_t)((k - 1) >> 1) * n + ((k - 1) & 1) : nullptr;  // lane of iteration k - 1
     sr_grad_tile_apply<R>(sm, g, nullptr, H, W, v.taps, blockIdx.y * kGT, blockIdx.x * kGT,
                           [&](int pi, int pj, float e, float o) {
                               const size_t q = (size_t)pi * W + pj;
@@ -317,8 +328,10 @@ __global__ void __launch_bounds__(256) adj_ata_update_kernel(const TapeView* __r
                                   uh[q + c] = uu;
                                   gs[q + c] += mu * gg;
                                   if (a_next) {
-                                      a_next[q + c] = vv - uu;
-                                      z_next[q + c] = xk[q + c] + uprev[q + c];
+                                      const float an = vv - uu;
+                                      a_next[q + c] = an;
+                                      s4[4 * (q + c)] = an;
+                                      s4[4 * (q + c) + 2] = xk[q + c] + uprev[q + c];
                                   }
                               }
                           });
@@ -867,6 +880,20 @@ __global__ void __launch_bounds__(256, 3)
     for (int idx = tid; idx < AH * AW; idx += 256) out[idx] = Ac[idx];
 }
 
+// The window partials of the offset chunks added into chunk 0's (in chunk order), so
+// that the gathers read one partial per window: which 0 the patch-distance adjoint's
+// (gpart), 1 pair pass G's (dh0); `elems` values per chunk and image, grid z = image.
+__global__ void __launch_bounds__(256) adj_chunk_sum_kernel(const TapeView* __restrict__ tv, int which, int elems,
+                                                            int chunks) {
+    const TapeView& v = tv[blockIdx.z];
+    float* part = which == 0 ? v.gpart : v.dh0;
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    if (e >= elems) return;
+    float acc = part[e];
+    for (int z = 1; z < chunks; ++z) acc += part[(size_t)z * elems + e];
+    part[e] = acc;
+}
+
 // ge(p) of the extended-grid position p = (pi, pj) (image coords), tiles of width qw: the
 // partials of every chunk and of the tiles whose accumulator windows hold p (rows ty0 - 1, ty0; columns
 // tx0 - 1 .. tx0 + 1), chunk by chunk in that order.  The six candidates are tested once
@@ -942,6 +969,17 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restric
     v.guide_bar[q] = acc;
 }
 
+// dL/dy = sum_k mu A g_k = A gs (A linear), every image (grid z)
+template <int R>
+__global__ void __launch_bounds__(256) adj_ybar_kernel(const TapeView* __restrict__ tv) {
+    const TapeView& v = tv[blockIdx.z];
+    const int h = v.H / 2, w = v.W / 2;
+    const int qj = blockIdx.x * 32 + threadIdx.x;
+    const int qi = blockIdx.y * 8 + threadIdx.y;
+    if (qi >= h || qj >= w) return;
+    v.y_bar[(size_t)qi * w + qj] = sr_forward_at<R>(v.gs, v.H, v.W, v.taps, qi, qj);
+}
+
 // Pair pass G with the mirrored half of the scaling's cotangent.  Over the half-window
 // pairs (s, r = s + o):
 //   G_sr = sum_k (a_k(s) - a_k(r)) (z_k(r) - z_k(s)),
@@ -956,7 +994,8 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restric
 // r; the offsets are separated by a barrier), which the block writes as one window
 // partial (its own pixels' forward sums added).  The weight tile of every offset
 // arrives by TMA two offsets ahead.  Staged over the window: (a_2u, a_2u+1, z_2u,
-// z_2u+1) as one float4 per pair of iterations (zeros past N and off the image) and d;
+// z_2u+1) as one float4 per pair of iterations (zeros past N; TMA copies of the
+// interleaved copy the reverse sweep writes, zeros off the image) and d;
 // the differences and products of the two iterations of a pair go through the packed
 // FP32x2 units (a difference as an FMA with -1, which is exact).  With NPK > 0
 // (= ceil(N / 2)) the values at s are held in registers; NPK = 0 reads them from
@@ -976,14 +1015,19 @@ __global__ void __launch_bounds__(256, 2)
     const int k0 = nh * zc / chunks, k1 = nh * (zc + 1) / chunks;
     const int y0 = blockIdx.y * kQH, x0 = blockIdx.x * 32;
     const int FH = kQH + rs, FW = 32 + 2 * rs, fcells = FH * FW;  // window: rows y0 + [0, FH), cols x0 - rs + [0, FW)
+    const int AZST = bd_stage_bytes(FH, 4 * FW, 4);              // one iteration pair's window
     const size_t n = (size_t)H * W;
-    float4* AZ4 = reinterpret_cast<float4*>(smem + 2 * KST);  // [np][FH][FW]
-    float* Sd = reinterpret_cast<float*>(AZ4 + (size_t)np * fcells);
+    unsigned char* az = smem + 2 * KST;  // [np] windows of float4 [FH][FW]
+    float* Sd = reinterpret_cast<float*>(az + (size_t)np * AZST);
     float* Ac = Sd + fcells;
-    __shared__ __align__(8) uint64_t bars[2];
+    auto AZ4 = [&](int u, int cell) -> const float4& {
+        return reinterpret_cast<const float4*>(az + (size_t)u * AZST)[cell];
+    };
+    __shared__ __align__(8) uint64_t bars[3];  // the two weight stages, the (a, z) windows
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx;
     const CUtensorMap* kmap = reinterpret_cast<const CUtensorMap*>(v.gt_kmap);
+    const CUtensorMap* amap = reinterpret_cast<const CUtensorMap*>(v.gt_amap);
     uint64_t policy = 0;
     auto issue = [&](int k, int st) {
         mbar_arrive_expect_tx(&bars[st], (unsigned)KBYTES);
@@ -991,38 +1035,33 @@ __global__ void __launch_bounds__(256, 2)
     };
     if (tid == 0) {
         tmap_acquire(kmap);
+        tmap_acquire(amap);
         policy = evict_first_policy();
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // the (a, z) windows: zeros off the image (the tensor's bounds), kept in L2
+        mbar_arrive_expect_tx(&bars[2], (unsigned)(np * FH * 4 * FW * 4));
+        for (int u = 0; u < np; ++u) tma_load_3d(az + (size_t)u * AZST, amap, &bars[2], 4 * (x0 - rs), y0, u, 0ull);
         if (k0 < k1) issue(k0, 0);
         if (k0 + 1 < k1) issue(k0 + 1, 1);
     }
-    const float* AZ = v.AZ;
     const float* d = v.Dh + (size_t)v.T * n;
     for (int idx = tid; idx < fcells; idx += 256) {
         const int a = idx / FW, b = idx - a * FW;
         const int i = y0 + a, j = x0 - rs + b;
         const bool in = i < H && j >= 0 && j < W;
-        const size_t q = in ? (size_t)i * W + j : 0;
-        for (int u = 0; u < np; ++u) {
-            const int ka = 2 * u, kb = ka + 1;
-            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (in) {
-                t.x = AZ[(size_t)ka * n + q];
-                t.z = AZ[(size_t)(N + ka) * n + q];
-                if (kb < N) {
-                    t.y = AZ[(size_t)kb * n + q];
-                    t.w = AZ[(size_t)(N + kb) * n + q];
-                }
-            }
-            AZ4[u * fcells + idx] = t;
-        }
-        Sd[idx] = in ? d[q] : 0.f;
+        Sd[idx] = in ? d[(size_t)i * W + j] : 0.f;
         Ac[idx] = 0.f;
     }
     __syncthreads();
+    bool gave_up = false;
+    if (!mbar_try_wait(&bars[2], 0u) && !mbar_wait_consumer(&bars[2], 0u, budget)) {
+        gave_up = true;
+        if (tid == 0) atomicOr(err, 1u);
+    }
     // the thread's pixels (ty + 8 m, tx), m = 0, 1, of the tile
     const int Wp = plane_pitch(W);
     const size_t plane = (size_t)H * Wp;
@@ -1039,7 +1078,7 @@ __global__ void __launch_bounds__(256, 2)
         if constexpr (NPK > 0) {
 #pragma unroll
             for (int u = 0; u < NPK; ++u) {
-                const float4 t = AZ4[u * fcells + cs];
+                const float4 t = AZ4(u, cs);
                 sa[m][u] = make_float2(t.x, t.y);
                 sz[m][u] = make_float2(t.z, t.w);
             }
@@ -1047,7 +1086,6 @@ __global__ void __launch_bounds__(256, 2)
     }
     const float2 m1 = make_float2(-1.f, -1.f);
     float accm = 0.f;
-    bool gave_up = false;
     int oy, ox;
     half_offset(k0, rs, oy, ox);
     for (int k = k0; k < k1; ++k) {
@@ -1071,14 +1109,14 @@ __global__ void __launch_bounds__(256, 2)
             if constexpr (NPK > 0) {
 #pragma unroll
                 for (int u = 0; u < NPK; ++u) {
-                    const float4 r4 = AZ4[u * fcells + cr];
+                    const float4 r4 = AZ4(u, cr);
                     const float2 da = __ffma2_rn(make_float2(r4.x, r4.y), m1, sa[m][u]);  // a(s) - a(r)
                     const float2 dz = __ffma2_rn(sz[m][u], m1, make_float2(r4.z, r4.w));  // z(r) - z(s)
                     acc = __ffma2_rn(da, dz, acc);
                 }
             } else {
                 for (int u = 0; u < np; ++u) {
-                    const float4 s4 = AZ4[u * fcells + cs], r4 = AZ4[u * fcells + cr];
+                    const float4 s4 = AZ4(u, cs), r4 = AZ4(u, cr);
                     const float2 da = __ffma2_rn(make_float2(r4.x, r4.y), m1, make_float2(s4.x, s4.y));
                     const float2 dz = __ffma2_rn(make_float2(s4.z, s4.w), m1, make_float2(r4.z, r4.w));
                     acc = __ffma2_rn(da, dz, acc);
@@ -1153,9 +1191,9 @@ cudaError_t by_blur_radius(int r, F&& f) {
 
 size_t pairs_g_smem(int N, int rs, int dtype) {
     const int esz = dtype == DSGNLM_F32 ? 4 : 2;
-    const size_t fcells = (size_t)(kQH + rs) * (32 + 2 * rs);
-    return 2 * (size_t)bd_stage_bytes(kQH, 32, esz) + sizeof(float4) * (size_t)((N + 1) / 2) * fcells +
-           sizeof(float) * 2 * fcells;
+    const int FH = kQH + rs, FW = 32 + 2 * rs;
+    return 2 * (size_t)bd_stage_bytes(kQH, 32, esz) + (size_t)((N + 1) / 2) * bd_stage_bytes(FH, 4 * FW, 4) +
+           sizeof(float) * 2 * (size_t)FH * FW;
 }
 size_t pairs_b_smem(int T, int rs) {
     return sizeof(float) * (size_t)(2 * T + 1) * (kAdjTH + rs) * (kAdjTW + 2 * rs);
@@ -1191,7 +1229,7 @@ struct lpnp_tape {
     const float* guide = nullptr;  // caller's guide
     int blur_r = 0;
     float blur_sigma = 1.f;
-    DevBuf Dh, Th, X, V, U, Gr, AZ, xh, vh, uh, zh, g, gs, dh, dh0, base, thp, Dhat, Gp, m, mkey, sstar, mh,
+    DevBuf Dh, Th, X, V, U, Gr, AZ, AZ4, xh, vh, uh, zh, g, gs, dh, dh0, base, thp, Dhat, Gp, m, mkey, sstar, mh,
         rho_part, h_part, m_part, scratch;
     // tables of a call this tape leads (the first image of the batch): per-image views,
     // phase-1 instance tables and work items in one device buffer, uploaded from one
@@ -1212,6 +1250,9 @@ struct lpnp_tape {
     alignas(64) unsigned char gt_kmap[128];  // the weight planes for pair pass G
     const void* gt_kbase = nullptr;
     int gt_key[4] = {0, 0, 0, 0};
+    alignas(64) unsigned char gt_amap[128];  // the interleaved (a, z) copy for pair pass G
+    const void* gt_abase = nullptr;
+    int gt_akey[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -1278,6 +1319,7 @@ TapeView make_view(const lpnp_tape* tp, const float* x_out, const float* x_bar, 
     v.Dhat = tp->Dhat.as<float>();
     v.Gp = tp->Gp.as<float>();
     v.AZ = tp->AZ.as<float>();
+    v.AZ4 = tp->AZ4.as<float>();
     v.mh = tp->mh.as<double>();
     v.rho_part = tp->rho_part.as<double>();
     v.h_part = tp->h_part.as<double>();
@@ -1543,7 +1585,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         lpnp_tape* tp = tapes[i];
         DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->gs, &tp->dh, &tp->base};
         for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
-        TAPE_CK(tp->AZ.ensure(sizeof(float) * n * 2 * N));
+        TAPE_CK(tp->AZ.ensure(sizeof(float) * n * N));
+        TAPE_CK(tp->AZ4.ensure(sizeof(float4) * n * ((N + 1) / 2)));
         TAPE_CK(tp->thp.ensure(sizeof(float) * n * (T > 0 ? T : 1)));
         // window partials of pair pass G (the forward and mirrored sums of dh0)
         TAPE_CK(tp->dh0.ensure(sizeof(float) * (size_t)kPairSplit * pgx * pgy * (kQH + rs) * (32 + 2 * rs)));
@@ -1573,6 +1616,16 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
                 std::memcpy(tp->gt_key, key, sizeof key);
             }
             std::memcpy(views[i].gt_kmap, tp->gt_kmap, 128);
+            // the (a, z) copy as FP32 rows of 4 W values, boxes of the pass's windows
+            const int np = (N + 1) / 2;
+            const int akey[4] = {H, W, np, rs};
+            if (tp->gt_abase != tp->AZ4.p || std::memcmp(akey, tp->gt_akey, sizeof akey) != 0) {
+                TAPE_CK(encode_tile_map(tp->gt_amap, tp->AZ4.p, DSGNLM_F32, H, 4 * W, np, 4 * (32 + 2 * rs), kQH + rs,
+                                        4 * W));
+                tp->gt_abase = tp->AZ4.p;
+                std::memcpy(tp->gt_akey, akey, sizeof akey);
+            }
+            std::memcpy(views[i].gt_amap, tp->gt_amap, 128);
         }
         if (fused) {
             const int dt = dens[i]->dtype;
@@ -1644,7 +1697,12 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         }
         count_launches(1);
         if (e != cudaSuccess) return e;
-        adj_dh_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, pgy, pgx, kPairSplit);
+        {
+            const int elems = pgx * pgy * (kQH + rs) * (32 + 2 * rs);
+            adj_chunk_sum_kernel<<<dim3((elems + 255) / 256, 1, count), 256, 0, st>>>(tb.views, 1, elems, kPairSplit);
+        }
+        adj_dh_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, pgy, pgx, 1);
+        count_launches(1);
         adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 0, npb, nrb);
         adj_mterms_kernel<WT><<<count, 256, 0, st>>>(tb.views);
         count_launches(3);
@@ -1705,8 +1763,12 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
             default: TAPE_CK(bd(__nv_bfloat16{})); break;
         }
         count_launches(1);
-        adj_fold_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, bg_ty, bg_tx, bg_chunks, bg_qw);
-        count_launches(1);
+        {
+            const int elems = bg_tx * bg_ty * bg_win_h(rs) * (bg_qw + 2 * rs);
+            adj_chunk_sum_kernel<<<dim3((elems + 255) / 256, 1, count), 256, 0, st>>>(tb.views, 0, elems, bg_chunks);
+        }
+        adj_fold_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, bg_ty, bg_tx, 1, bg_qw);
+        count_launches(2);
         TAPE_CK(cudaGetLastError());
     } else {
         // pair pass B: D-hat planes and dL/dh partials
@@ -1728,8 +1790,12 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         TAPE_CK(cudaGetLastError());
     }
     // dL/dy = sum_k mu A g_k = A gs
-    for (int i = 0; i < count; ++i)
-        TAPE_CK(launch_sr_forward(tapes[i]->gs.as<float>(), H, W, lead->taps, nullptr, 0.f, y_bar[i], st));
+    TAPE_CK(by_blur_radius(lead->taps.r, [&](auto rc) {
+        adj_ybar_kernel<decltype(rc)::value>
+            <<<dim3((W / 2 + 31) / 32, (H / 2 + 7) / 8, count), dim3(32, 8), 0, st>>>(tb.views);
+        return cudaGetLastError();
+    }));
+    count_launches(1);
     adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 1, npb, nrb);
     adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 2, nhb, nrb);
     count_launches(2);
@@ -1778,7 +1844,7 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (!t) return;
     if (t->den) cudaStreamSynchronize(t->den->stream);
     if (t->staged) cudaEventSynchronize(t->staged);
-    DevBuf* bufs[] = {&t->Dh,  &t->Th,   &t->X,  &t->V,       &t->U,     &t->Gr,     &t->AZ,     &t->xh,
+    DevBuf* bufs[] = {&t->Dh,  &t->Th,   &t->X,  &t->V,       &t->U,     &t->Gr,     &t->AZ, &t->AZ4, &t->xh,
                       &t->vh,  &t->uh,   &t->zh, &t->g,       &t->gs,    &t->dh,     &t->dh0,    &t->base,
                       &t->thp, &t->Dhat, &t->Gp, &t->m,     &t->mkey,   &t->sstar,  &t->mh,
                       &t->rho_part, &t->h_part, &t->m_part, &t->scratch, &t->tables, &t->scal};

@@ -23,10 +23,11 @@ void count_launches(uint64_t n) {
     if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }
 void set_capture_counting(bool recording) { g_capturing = recording; }
-// Tensor map of planes [nh][H][pitch] of the storage type `dtype`, pitch
-// plane_pitch(W); the tensor's rows are W wide, so boxes read zeros past column W - 1
-// (and past row H - 1, and before row or column 0).
-cudaError_t encode_tile_map(void* out, const void* base, int dtype, int H, int W, int nh, int box_w, int box_h) {
+// Tensor map of planes [nh][H][pitch] of the storage type `dtype`, pitch in elements
+// (plane_pitch(W) when 0); the tensor's rows are W wide, so boxes read zeros past
+// column W - 1 (and past row H - 1, and before row or column 0).
+cudaError_t encode_tile_map(void* out, const void* base, int dtype, int H, int W, int nh, int box_w, int box_h,
+                            int pitch) {
     // looked up once (a thread-safe static initialisation)
     static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         cudaDriverEntryPointQueryResult q;
@@ -42,7 +43,8 @@ cudaError_t encode_tile_map(void* out, const void* base, int dtype, int H, int W
                                    : dtype == DSGNLM_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nh};
-    const cuuint64_t strides[2] = {(cuuint64_t)plane_pitch(W) * esz, (cuuint64_t)plane_pitch(W) * H * esz};
+    const cuuint64_t pe = pitch > 0 ? (cuuint64_t)pitch : (cuuint64_t)plane_pitch(W);
+    const cuuint64_t strides[2] = {pe * esz, pe * H * esz};
     const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode((CUtensorMap*)out, dt, 3, const_cast<void*>(base), dims, strides, box, estr,

@@ -18,6 +18,27 @@ namespace dsg {
 
 constexpr int kGT = 32;  // output tile side
 
+// (A x)(q) = sum_a t(a) sum_b t(b) x(2q - (a, b)), periodic: the low-resolution pixel q
+// = (qi, qj) of the blurred, decimated image.  Both tap loops unroll (R is a template
+// parameter), so a row's loads are issued together.
+template <int R>
+__device__ __forceinline__ float sr_forward_at(const float* __restrict__ x, int H, int W, const BlurTaps& taps,
+                                               int qi, int qj) {
+    int cols[2 * R + 1];
+#pragma unroll
+    for (int b = -R; b <= R; ++b) cols[b + R] = wrap_index(2 * qj - b, W);
+    float acc = 0.f;
+#pragma unroll
+    for (int a = -R; a <= R; ++a) {
+        const float* row = x + (size_t)wrap_index(2 * qi - a, H) * W;
+        float ra = 0.f;
+#pragma unroll
+        for (int b = -R; b <= R; ++b) ra = fmaf(taps.t[b + R], __ldg(row + cols[b + R]), ra);
+        acc = fmaf(taps.t[a + R], ra, acc);
+    }
+    return acc;
+}
+
 template <int R>
 struct GradDims {
     static constexpr int G = R > 0 ? R : 1;              // staging margin

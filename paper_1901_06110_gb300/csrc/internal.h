@@ -104,9 +104,11 @@ struct BatchInst {  // per-instance data of a batched launch (device memory)
 cudaError_t launch_tma_gather_batched(int dtype, int rs, const BatchMaps& maps, const BatchInst* insts,
                                       const int4* work, int nwork, unsigned* err, cudaStream_t st);
 bool tma_path_supports(int rs);
-// tensor map of planes [nh][H][plane_pitch(W)] of type dtype (DSGNLM_F32/F16/BF16)
-// with boxes of box_w x box_h x 1; reads past the image (W x H) return zeros
-cudaError_t encode_tile_map(void* out, const void* base, int dtype, int H, int W, int nh, int box_w, int box_h);
+// tensor map of planes [nh][H][pitch] of type dtype (DSGNLM_F32/F16/BF16), pitch in
+// elements (plane_pitch(W) when 0), with boxes of box_w x box_h x 1; reads past the
+// image (W x H) return zeros
+cudaError_t encode_tile_map(void* out, const void* base, int dtype, int H, int W, int nh, int box_w, int box_h,
+                            int pitch = 0);
 int tma_tile_w();
 int tma_ctas_per_sm(int dtype);  // resident phase-1 CTAs per SM for the weight type
 int tma_tile_h();

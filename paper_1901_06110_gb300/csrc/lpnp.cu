@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "grad.cuh"
 #include "internal.h"
 #include "xupdate.cuh"
 
@@ -37,9 +38,7 @@ constexpr int kBX = 32, kBY = 8;
 
 dim3 grid2(int H, int W) { return dim3((W + kBX - 1) / kBX, (H + kBY - 1) / kBY); }
 
-// out(q) = sum_a t(a) sum_b t(b) x(2q - (a, b)) + c aux(q), periodic.  The blur
-// radius R is a template parameter, so both tap loops unroll and a row's loads are
-// issued together instead of each after the previous FMA.
+// out(q) = (A x)(q) + c aux(q), periodic
 template <int R>
 __global__ void sr_forward_kernel(const float* __restrict__ x, int H, int W, BlurTaps taps,
                                   const float* __restrict__ aux, float c, float* __restrict__ out) {
@@ -47,18 +46,7 @@ __global__ void sr_forward_kernel(const float* __restrict__ x, int H, int W, Blu
     const int qj = blockIdx.x * kBX + threadIdx.x;
     const int qi = blockIdx.y * kBY + threadIdx.y;
     if (qi >= h || qj >= w) return;
-    int cols[2 * R + 1];
-#pragma unroll
-    for (int b = -R; b <= R; ++b) cols[b + R] = wrap_index(2 * qj - b, W);
-    float acc = 0.f;
-#pragma unroll
-    for (int a = -R; a <= R; ++a) {
-        const float* row = x + (size_t)wrap_index(2 * qi - a, H) * W;
-        float ra = 0.f;
-#pragma unroll
-        for (int b = -R; b <= R; ++b) ra = fmaf(taps.t[b + R], __ldg(row + cols[b + R]), ra);
-        acc = fmaf(taps.t[a + R], ra, acc);
-    }
+    const float acc = sr_forward_at<R>(x, H, W, taps, qi, qj);
     const size_t q = (size_t)qi * w + qj;
     out[q] = aux ? fmaf(c, aux[q], acc) : acc;
 }

@@ -94,6 +94,7 @@ __device__ __forceinline__ float proj_deriv(float xb, int constraint) {
 
 // d^0 = 1 and the maximiser key cleared, per image
 __global__ void __launch_bounds__(256) adj_prep_kernel(const TapeView* __restrict__ tv) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int n = v.H * v.W;
     for (int q = blockIdx.x * 256 + threadIdx.x; q < n; q += gridDim.x * 256) v.Dh[q] = 1.f;
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(256) adj_prep_kernel(const TapeView* __restric
 // Epilogue of balancing pass p (Eq. S2): t^p = K1 d^p from the phase-1 partial sums,
 // d^{p+1} = sqrt(d^p / t^p) (the plain step), both recorded
 __global__ void __launch_bounds__(256) adj_balance_kernel(const TapeView* __restrict__ tv, int p) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const size_t n = (size_t)v.H * v.W;
     float* d_out = p < v.T ? v.Dh + (size_t)(p + 1) * n : v.scratch;
@@ -118,6 +120,7 @@ __global__ void __launch_bounds__(256) adj_balance_kernel(const TapeView* __rest
 // index.  Every warp folds its best key in with atomicMax, which does not depend on
 // the order of arrival; the finish kernel unpacks the key.
 __global__ void __launch_bounds__(256) adj_m_key_kernel(const TapeView* __restrict__ tv) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int n = v.H * v.W;
     const float* d = v.Dh + (size_t)v.T * n;
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(256) adj_m_key_kernel(const TapeView* __restri
 
 // one thread per image
 __global__ void adj_m_finish_kernel(const TapeView* __restrict__ tv, int count) {
+    griddep_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const TapeView& v = tv[i];
@@ -149,6 +153,7 @@ __global__ void adj_m_finish_kernel(const TapeView* __restrict__ tv, int count) 
 
 // x = v = clip(guide, 0, 1), u = 0 into slot 0
 __global__ void __launch_bounds__(256) adj_init_kernel(const TapeView* __restrict__ tv) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int n = v.H * v.W;
     const int q = blockIdx.x * 256 + threadIdx.x;
@@ -166,6 +171,7 @@ __global__ void __launch_bounds__(256) adj_init_kernel(const TapeView* __restric
 // x_k is read in halos and x_{k+1} written to another buffer, so tiles do not race.
 template <int R>
 __global__ void __launch_bounds__(256) adj_fwd_xupdate_kernel(const TapeView* __restrict__ tv, int k) {
+    griddep_enter();
     __shared__ GradSmem<R> sm;
     const TapeView& v = tv[blockIdx.z];
     const int H = v.H, W = v.W;
@@ -202,6 +208,7 @@ __global__ void __launch_bounds__(256) adj_fwd_xupdate_kernel(const TapeView* __
 // and 1/m on the device) and u <- u + x - v; the same per-pixel code as the solve's
 // combine, without the next x-update
 __global__ void __launch_bounds__(256) adj_fwd_dual_kernel(const TapeView* __restrict__ tv, int k) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const size_t n = (size_t)v.H * v.W;
     EpilogueArgs a{};
@@ -226,6 +233,7 @@ __global__ void __launch_bounds__(256) adj_fwd_dual_kernel(const TapeView* __res
 
 // x_N to the caller's buffer
 __global__ void __launch_bounds__(256) adj_xout_kernel(const TapeView* __restrict__ tv) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const size_t n = (size_t)v.H * v.W;
     const size_t q = (size_t)blockIdx.x * 256 + threadIdx.x;
@@ -238,6 +246,7 @@ __global__ void __launch_bounds__(256) adj_xout_kernel(const TapeView* __restric
 // a_{N-1} = vh - uh = 0, z_{N-1} = x_N + u_{N-1} (a in its plane, a and z in the
 // interleaved copy)
 __global__ void __launch_bounds__(256) adj_bwd_prep_kernel(const TapeView* __restrict__ tv, int nrb) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const size_t n = (size_t)v.H * v.W;
     const size_t q = (size_t)blockIdx.x * 256 + threadIdx.x;
@@ -263,6 +272,7 @@ __global__ void __launch_bounds__(256) adj_bwd_prep_kernel(const TapeView* __res
 // the closure of Eq. S3), then zh = W a + uh, g = Pi_C'(xbar_k)(xh + zh) and the block's
 // partial of sum g mu ((v - u) - xbar).  Blocks of 32 x 8 pixels.
 __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restrict__ tv, int k) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int H = v.H, W = v.W;
     const size_t n = (size_t)H * W;
@@ -301,6 +311,7 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
 // g is only read, so the halo reads do not race with the writes.
 template <int R>
 __global__ void __launch_bounds__(256) adj_ata_update_kernel(const TapeView* __restrict__ tv, int k) {
+    griddep_enter();
     __shared__ GradSmem<R> sm;
     const TapeView& v = tv[blockIdx.z];
     const int H = v.H, W = v.W;
@@ -341,6 +352,7 @@ __global__ void __launch_bounds__(256) adj_ata_update_kernel(const TapeView* __r
 // which 0: m_part -> mh[0], 1: rho_part -> mh[1], 2: h_part -> mh[2]; one block per image
 __global__ void __launch_bounds__(256) adj_sum_kernel(const TapeView* __restrict__ tv, int which, int count_m,
                                                       int count_rho) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.x];
     const double* part = which == 1 ? v.rho_part : which == 2 ? v.h_part : v.m_part;
     const int count = which == 1 ? count_rho : count_m;
@@ -360,6 +372,7 @@ __global__ void __launch_bounds__(256) adj_sum_kernel(const TapeView* __restrict
 // j != s*; one block per image
 template <typename WT>
 __global__ void adj_mterms_kernel(const TapeView* __restrict__ tv) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.x];
     const WT* __restrict__ P = static_cast<const WT*>(v.planes);
     const int H = v.H, W = v.W, rs = v.rs;
@@ -392,6 +405,7 @@ __global__ void adj_mterms_kernel(const TapeView* __restrict__ tv) {
 
 // Balancing pass T - 1 backwards: th = -0.5 dh' d'/t, base = 0.5 dh' d'/d (d' = d^T)
 __global__ void __launch_bounds__(256) adj_sk_pre_kernel(const TapeView* __restrict__ tv) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const size_t n = (size_t)v.H * v.W;
     const size_t q = (size_t)blockIdx.x * 256 + threadIdx.x;
@@ -406,6 +420,7 @@ __global__ void __launch_bounds__(256) adj_sk_pre_kernel(const TapeView* __restr
 // cv), the cotangent of d^p, and from it pass p - 1's th^{p-1} = -0.5 dh^p d^p / t^{p-1}
 // and base = 0.5 dh^p d^p / d^{p-1} (base rewritten in place)
 __global__ void __launch_bounds__(256) adj_sk_finish_pre_kernel(const TapeView* __restrict__ tv, int p) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int H = v.H, W = v.W;
     const size_t n = (size_t)H * W;
@@ -441,6 +456,7 @@ __device__ __forceinline__ void stage_fields(float* S, const float* __restrict__
 // offsets split as in pass G.
 template <typename WT>
 __global__ void __launch_bounds__(256, 3) adj_pairs_b_kernel(const TapeView* __restrict__ tv) {
+    griddep_enter();
     extern __shared__ float S[];
     const int img = blockIdx.z / kPairSplit, zc = blockIdx.z - img * kPairSplit;
     const TapeView& v = tv[img];
@@ -542,6 +558,7 @@ __host__ __device__ __forceinline__ int bg_win_h(int rs) { return kQH + rs; }
 __host__ __device__ __forceinline__ int bg_win_w(int rs) { return kQW + 2 * rs; }
 
 __global__ void __launch_bounds__(256) adj_boxguide_kernel(const TapeView* __restrict__ tv, int chunks) {
+    griddep_enter();
     extern __shared__ float S[];
     const int img = blockIdx.z / chunks, zc = blockIdx.z - img * chunks;
     const TapeView& v = tv[img];
@@ -663,6 +680,7 @@ __host__ __device__ __forceinline__ int bd_win_w(int rp, int rs) { return bd_qw(
 template <typename WT, int RP, int RS, int TT>
 __global__ void __launch_bounds__(256, 3)
     adj_pairs_bd_kernel(const TapeView* __restrict__ tv, int chunks, unsigned* err, long long budget) {
+    griddep_enter();
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int rp = RP, QW = Bd<RP>::QW, DH = Bd<RP>::DH, NC = Bd<RP>::NC;
     constexpr int KBW = bd_box_w((int)sizeof(WT)), GBW = bd_box_w(4);
@@ -885,6 +903,7 @@ __global__ void __launch_bounds__(256, 3)
 // (gpart), 1 pair pass G's (dh0); `elems` values per chunk and image, grid z = image.
 __global__ void __launch_bounds__(256) adj_chunk_sum_kernel(const TapeView* __restrict__ tv, int which, int elems,
                                                             int chunks) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     float* part = which == 0 ? v.gpart : v.dh0;
     const int e = blockIdx.x * 256 + threadIdx.x;
@@ -934,6 +953,7 @@ __device__ __forceinline__ float gather_ge(const float* __restrict__ part, int p
 // enumeration otherwise
 __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restrict__ tv, int tiles_y, int tiles_x,
                                                        int chunks, int qw) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int H = v.H, W = v.W, rp = v.rp, rs = v.rs;
     const int j = blockIdx.x * 32 + threadIdx.x;
@@ -972,6 +992,7 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restric
 // dL/dy = sum_k mu A g_k = A gs (A linear), every image (grid z)
 template <int R>
 __global__ void __launch_bounds__(256) adj_ybar_kernel(const TapeView* __restrict__ tv) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int h = v.H / 2, w = v.W / 2;
     const int qj = blockIdx.x * 32 + threadIdx.x;
@@ -1003,6 +1024,7 @@ __global__ void __launch_bounds__(256) adj_ybar_kernel(const TapeView* __restric
 template <typename WT, int NPK>
 __global__ void __launch_bounds__(256, 2)
     adj_pairs_gt_kernel(const TapeView* __restrict__ tv, int chunks, unsigned* err, long long budget) {
+    griddep_enter();
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int KBYTES = kQH * 32 * (int)sizeof(WT);
     constexpr int KST = bd_stage_bytes(kQH, 32, (int)sizeof(WT));
@@ -1154,6 +1176,7 @@ __global__ void __launch_bounds__(256, 2)
 // chunk, and every tile whose window holds s, in a fixed order)
 __global__ void __launch_bounds__(256) adj_dh_kernel(const TapeView* __restrict__ tv, int tiles_y, int tiles_x,
                                                      int chunks) {
+    griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int H = v.H, W = v.W;
     const int j = blockIdx.x * 32 + threadIdx.x;
@@ -1165,6 +1188,7 @@ __global__ void __launch_bounds__(256) adj_dh_kernel(const TapeView* __restrict_
 
 // the scalar cotangents of every image (m, rho, h) in one array, read back in one copy
 __global__ void adj_gather_scalars_kernel(const TapeView* __restrict__ tv, int count, double* __restrict__ out) {
+    griddep_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     for (int w = 0; w < 3; ++w) out[3 * i + w] = tv[i].mh[w];
@@ -1268,6 +1292,30 @@ dsgnlm_status tape_ck(cudaError_t e) {
         dsgnlm_status s_ = tape_ck(expr);               \
         if (s_ != DSGNLM_OK) return s_;                 \
     } while (0)
+
+// Launch with programmatic stream serialization: the kernel's blocks may be scheduled
+// while the previous kernel on the stream drains, and every kernel of this file waits
+// for its predecessors (griddep_wait) before it touches memory.
+#define PDL_CK(expr)                     \
+    do {                                 \
+        cudaError_t e_ = (expr);         \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+template <typename... KArgs, typename... Args>
+cudaError_t pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 cudaError_t ensure_event(cudaEvent_t& e) {
     return e ? cudaSuccess : cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
@@ -1498,36 +1546,35 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
     const dim3 eg((W + kXW - 1) / kXW, (H + kXH - 1) / kXH, count);  // per-pixel epilogue blocks
     const dim3 ng(std::min(nblk(n), 1024), 1, count);
     // 4. the work, one launch per step over all images
-    adj_prep_kernel<<<ng, 256, 0, st>>>(tb.views);
+    TAPE_CK(pdl(adj_prep_kernel, dim3(ng), dim3(256), 0, st, tb.views));
     count_launches(1);
     TAPE_CK(cudaGetLastError());
     for (int p = 0; p <= T; ++p) {
         TAPE_CK(launch_tma_gather_batched(dtype, search_r, maps, tb.insts + (size_t)p * count, tb.work, tb.nwork, err,
                                           st));
-        adj_balance_kernel<<<eg, dim3(32, 8), 0, st>>>(tb.views, p);
+        TAPE_CK(pdl(adj_balance_kernel, dim3(eg), dim3(32, 8), 0, st, tb.views, p));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
     }
-    adj_m_key_kernel<<<ng, 256, 0, st>>>(tb.views);
-    adj_m_finish_kernel<<<(count + 63) / 64, 64, 0, st>>>(tb.views, count);
-    adj_init_kernel<<<dim3(nblk(n), 1, count), 256, 0, st>>>(tb.views);
+    TAPE_CK(pdl(adj_m_key_kernel, dim3(ng), dim3(256), 0, st, tb.views));
+    TAPE_CK(pdl(adj_m_finish_kernel, dim3((count + 63) / 64), dim3(64), 0, st, tb.views, count));
+    TAPE_CK(pdl(adj_init_kernel, dim3(nblk(n), 1, count), dim3(256), 0, st, tb.views));
     count_launches(3);
     TAPE_CK(cudaGetLastError());
     const dim3 gg((W + kGT - 1) / kGT, (H + kGT - 1) / kGT, count);
     const BlurTaps taps = make_blur_taps(blur_sigma, blur_r);
     for (int k = 0; k < N; ++k) {
         TAPE_CK(by_blur_radius(taps.r, [&](auto rc) {
-            adj_fwd_xupdate_kernel<decltype(rc)::value><<<gg, 256, 0, st>>>(tb.views, k);
-            return cudaGetLastError();
+            return pdl(adj_fwd_xupdate_kernel<decltype(rc)::value>, dim3(gg), dim3(256), 0, st, tb.views, k);
         }));
         count_launches(1);
         TAPE_CK(launch_tma_gather_batched(dtype, search_r, maps, tb.insts + (size_t)(T + 1) * count, tb.work,
                                           tb.nwork, err, st));
-        adj_fwd_dual_kernel<<<eg, dim3(32, 8), 0, st>>>(tb.views, k);
+        TAPE_CK(pdl(adj_fwd_dual_kernel, dim3(eg), dim3(32, 8), 0, st, tb.views, k));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
     }
-    adj_xout_kernel<<<dim3(nblk(n), 1, count), 256, 0, st>>>(tb.views);
+    TAPE_CK(pdl(adj_xout_kernel, dim3(nblk(n), 1, count), dim3(256), 0, st, tb.views));
     count_launches(1);
     TAPE_CK(cudaGetLastError());
     // 5. every handle holds its image's W; its m and 1/m stay on the device until a
@@ -1655,19 +1702,18 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     const int dtype = dens[0]->dtype;
     const dim3 gg((W + kGT - 1) / kGT, (H + kGT - 1) / kGT, count);  // A^T A tiles
     const dim3 ng(nblk(n), 1, count);
-    adj_bwd_prep_kernel<<<ng, 256, 0, st>>>(tb.views, nrb);
+    TAPE_CK(pdl(adj_bwd_prep_kernel, dim3(ng), dim3(256), 0, st, tb.views, nrb));
     count_launches(1);
     TAPE_CK(cudaGetLastError());
     for (int k = N - 1; k >= 0; --k) {
         // W a (W symmetric), finished with g and zh; xbar_k from the recorded grad f(x_k)
         TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)k * count, tb.work, tb.nwork, err, st));
-        adj_wa_g_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, k);
+        TAPE_CK(pdl(adj_wa_g_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, k));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
         // A^T A g and the updates of the cotangents, with the earlier iteration's inputs
         TAPE_CK(by_blur_radius(lead->taps.r, [&](auto rc) {
-            adj_ata_update_kernel<decltype(rc)::value><<<gg, 256, 0, st>>>(tb.views, k);
-            return cudaGetLastError();
+            return pdl(adj_ata_update_kernel<decltype(rc)::value>, dim3(gg), dim3(256), 0, st, tb.views, k);
         }));
         count_launches(1);
     }
@@ -1680,8 +1726,7 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         auto run = [&](auto kern) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            kern<<<grid, dim3(32, 8), smem, st>>>(tb.views, kPairSplit, err, kDefaultWaitBudget);
-            return cudaGetLastError();
+            return pdl(kern, grid, dim3(32, 8), smem, st, tb.views, kPairSplit, err, kDefaultWaitBudget);
         };
         cudaError_t e;
         switch ((N + 1) / 2) {
@@ -1699,12 +1744,13 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         if (e != cudaSuccess) return e;
         {
             const int elems = pgx * pgy * (kQH + rs) * (32 + 2 * rs);
-            adj_chunk_sum_kernel<<<dim3((elems + 255) / 256, 1, count), 256, 0, st>>>(tb.views, 1, elems, kPairSplit);
+            PDL_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st, tb.views, 1, elems,
+                       kPairSplit));
         }
-        adj_dh_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, pgy, pgx, 1);
+        PDL_CK(pdl(adj_dh_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, pgy, pgx, 1));
         count_launches(1);
-        adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 0, npb, nrb);
-        adj_mterms_kernel<WT><<<count, 256, 0, st>>>(tb.views);
+        PDL_CK(pdl(adj_sum_kernel, dim3(count), dim3(256), 0, st, tb.views, 0, npb, nrb));
+        PDL_CK(pdl(adj_mterms_kernel<WT>, dim3(count), dim3(256), 0, st, tb.views));
         count_launches(3);
         return cudaGetLastError();
     };
@@ -1713,7 +1759,7 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         const size_t smem = pairs_b_smem(T, rs);
         cudaError_t e = cudaFuncSetAttribute(adj_pairs_b_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        adj_pairs_b_kernel<WT><<<dim3(pgx, pgy, kPairSplit * count), dim3(32, 8), smem, st>>>(tb.views);
+        PDL_CK(pdl(adj_pairs_b_kernel<WT>, dim3(pgx, pgy, kPairSplit * count), dim3(32, 8), smem, st, tb.views));
         count_launches(1);
         return cudaGetLastError();
     };
@@ -1726,7 +1772,7 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     // finish of pass p forms the cotangent of d^p and at once th^{p-1} of the next pass
     // (the cotangent of d^0 = 1 is not needed, so pass 0 has no finish)
     if (T > 0) {
-        adj_sk_pre_kernel<<<ng, 256, 0, st>>>(tb.views);
+        TAPE_CK(pdl(adj_sk_pre_kernel, dim3(ng), dim3(256), 0, st, tb.views));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
     }
@@ -1734,7 +1780,7 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)(N + p) * count, tb.work, tb.nwork, err,
                                           st));
         if (p == 0) break;
-        adj_sk_finish_pre_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, p);
+        TAPE_CK(pdl(adj_sk_finish_pre_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, p));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
     }
@@ -1746,9 +1792,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
             auto run = [&](auto kern) -> cudaError_t {
                 cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
-                kern<<<dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), smem, st>>>(tb.views, bg_chunks, err,
-                                                                                     kDefaultWaitBudget);
-                return cudaGetLastError();
+                return pdl(kern, dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), smem, st, tb.views, bg_chunks, err,
+                           kDefaultWaitBudget);
             };
             if (rp == 2 && rs == 7 && T == 4) return run(adj_pairs_bd_kernel<WT, 2, 7, 4>);
             switch (rp) {
@@ -1765,9 +1810,10 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         count_launches(1);
         {
             const int elems = bg_tx * bg_ty * bg_win_h(rs) * (bg_qw + 2 * rs);
-            adj_chunk_sum_kernel<<<dim3((elems + 255) / 256, 1, count), 256, 0, st>>>(tb.views, 0, elems, bg_chunks);
+            TAPE_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st, tb.views, 0, elems,
+                        bg_chunks));
         }
-        adj_fold_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, bg_ty, bg_tx, 1, bg_qw);
+        TAPE_CK(pdl(adj_fold_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, bg_ty, bg_tx, 1, bg_qw));
         count_launches(2);
         TAPE_CK(cudaGetLastError());
     } else {
@@ -1784,25 +1830,26 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
             sizeof(float) * (size_t)(2 * bg_win_h(rs) * bg_win_w(rs) + (kQH + 2 * rp) * (kQW + 2 * rp) +
                                      (kQH + 2 * rp) * kQW);
         TAPE_CK(cudaFuncSetAttribute(adj_boxguide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
-        adj_boxguide_kernel<<<dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), bsmem, st>>>(tb.views, bg_chunks);
-        adj_fold_kernel<<<pgrid2, dim3(32, 8), 0, st>>>(tb.views, bg_ty, bg_tx, bg_chunks, bg_qw);
+        TAPE_CK(pdl(adj_boxguide_kernel, dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), bsmem, st, tb.views,
+                    bg_chunks));
+        TAPE_CK(pdl(adj_fold_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, bg_ty, bg_tx, bg_chunks, bg_qw));
         count_launches(2);
         TAPE_CK(cudaGetLastError());
     }
     // dL/dy = sum_k mu A g_k = A gs
     TAPE_CK(by_blur_radius(lead->taps.r, [&](auto rc) {
-        adj_ybar_kernel<decltype(rc)::value>
-            <<<dim3((W / 2 + 31) / 32, (H / 2 + 7) / 8, count), dim3(32, 8), 0, st>>>(tb.views);
-        return cudaGetLastError();
+        return pdl(adj_ybar_kernel<decltype(rc)::value>, dim3((W / 2 + 31) / 32, (H / 2 + 7) / 8, count),
+                   dim3(32, 8), 0, st, tb.views);
     }));
     count_launches(1);
-    adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 1, npb, nrb);
-    adj_sum_kernel<<<count, 256, 0, st>>>(tb.views, 2, nhb, nrb);
+    TAPE_CK(pdl(adj_sum_kernel, dim3(count), dim3(256), 0, st, tb.views, 1, npb, nrb));
+    TAPE_CK(pdl(adj_sum_kernel, dim3(count), dim3(256), 0, st, tb.views, 2, nhb, nrb));
     count_launches(2);
     TAPE_CK(cudaGetLastError());
     // every image's (m, rho, h) cotangents and the wait-error word, read back once
     TAPE_CK(lead->scal.ensure(sizeof(double) * 3 * (size_t)count));
-    adj_gather_scalars_kernel<<<(count + 63) / 64, 64, 0, st>>>(tb.views, count, lead->scal.as<double>());
+    TAPE_CK(pdl(adj_gather_scalars_kernel, dim3((count + 63) / 64), dim3(64), 0, st, tb.views, count,
+                lead->scal.as<double>()));
     count_launches(1);
     TAPE_CK(cudaGetLastError());
     if (lead->hs_count < count) {

@@ -80,6 +80,21 @@ __device__ __forceinline__ T warp_max(T v) {
     return v;
 }
 
+// Wait until the grids this one depends on have completed and their writes are visible
+// (a no-op without a programmatic dependency).  A kernel launched with programmatic
+// stream serialization may start while its predecessor drains; it calls this before it
+// reads or writes any memory the predecessor uses.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// A kernel's entry: wait for its predecessors, then let the next kernel of the stream
+// (if launched with programmatic stream serialization) be scheduled as soon as every
+// block of this one has started; that kernel waits in turn before touching memory, so
+// only launch latency and the last wave's idle SMs are overlapped.
+__device__ __forceinline__ void griddep_enter() {
+    griddep_wait();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

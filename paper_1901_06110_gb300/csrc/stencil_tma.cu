@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(kThreads, P1Traits<WT>::kMinBlocks)
 stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const float* __restrict__ d,
                   const float* __restrict__ z, TmaSplits splits, float* __restrict__ part,
                   unsigned* __restrict__ err, const int* __restrict__ skip, long long cbudget) {
+    griddep_enter();
     if (skip && *(volatile const int*)skip) return;
     const int slice = blockIdx.z;
     const size_t region = (size_t)(kTH + RS) * (kTW + 2 * RS);
@@ -325,6 +326,7 @@ template <int RS, typename WT>
 __global__ void __launch_bounds__(kThreads, P1Traits<WT>::kMinBlocks)
 stencil_p1_batched_kernel(const __grid_constant__ BatchMaps maps, const BatchInst* __restrict__ insts,
                           const int4* __restrict__ work, unsigned* __restrict__ err) {
+    griddep_enter();
     const int4 w = work[blockIdx.x];  // (instance, tile row, tile column, slice)
     const BatchInst& in = insts[w.x];
     if (in.done && *(volatile const int*)in.done) return;
@@ -341,6 +343,7 @@ stencil_p1_batched_kernel(const __grid_constant__ BatchMaps maps, const BatchIns
 __global__ void __launch_bounds__(256)
 apply_finish_kernel(Cover cv, int H, int W, const float* __restrict__ d, const float* __restrict__ t_fin,
                     float inv_m, const float* __restrict__ z, float* __restrict__ y) {
+    griddep_enter();
     const int j = blockIdx.x * 32 + threadIdx.x;
     const int i = blockIdx.y * 8 + threadIdx.y;
     if (i >= H || j >= W) return;
@@ -355,6 +358,7 @@ apply_finish_kernel(Cover cv, int H, int W, const float* __restrict__ d, const f
 // hist[k] = fixed-order sums of the per-block residual partials of iteration k
 __global__ void __launch_bounds__(256)
 reduce_residuals_kernel(SolveRed red, int nblocks) {
+    griddep_enter();
     const int iter = blockIdx.x, t = threadIdx.x;
     double a = 0.0, b = 0.0;
     for (int q = t; q < nblocks; q += 256) {
@@ -409,9 +413,21 @@ cudaError_t p1b_launch(const BatchMaps& maps, const BatchInst* insts, const int4
         stencil_p1_batched_kernel<RS, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (configured != cudaSuccess) return configured;
     if (nwork <= 0) return cudaSuccess;
-    stencil_p1_batched_kernel<RS, WT><<<nwork, kThreads, smem, st>>>(maps, insts, work, err);
+    // programmatic stream serialization: the blocks may be scheduled while the previous
+    // kernel drains (the kernel waits for it before touching memory)
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(nwork);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, stencil_p1_batched_kernel<RS, WT>, maps, insts, work, err);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename WT>

@@ -165,15 +165,12 @@ __global__ void __launch_bounds__(256) adj_init_kernel(const TapeView* __restric
 }
 
 // x-update of recorded iteration k (Algorithm 1, first two steps) from the states of
-// slot k into slot k + 1, on 32 x 32 tiles:
+// slot k into slot k + 1, on the 32 x 32 tile at (y0, x0):
 //   g = A^T (A x_k - y) (recorded),  x_{k+1} = Pi_C(mu (alpha x_k + rho (v_k - u_k) - g)),
 //   z = x_{k+1} + u_k,  and v_k, u_k copied into slot k + 1 for the dual step to update.
 // x_k is read in halos and x_{k+1} written to another buffer, so tiles do not race.
 template <int R>
-__global__ void __launch_bounds__(256) adj_fwd_xupdate_kernel(const TapeView* __restrict__ tv, int k) {
-    griddep_enter();
-    __shared__ GradSmem<R> sm;
-    const TapeView& v = tv[blockIdx.z];
+__device__ __forceinline__ void fwd_xupdate_tile(GradSmem<R>& sm, const TapeView& v, int k, int y0, int x0) {
     const int H = v.H, W = v.W;
     const size_t n = (size_t)H * W;
     const float* xk = v.X + (size_t)k * n;
@@ -186,30 +183,34 @@ __global__ void __launch_bounds__(256) adj_fwd_xupdate_kernel(const TapeView* __
     float* z = v.z;
     const float mu = v.mu, alpha = v.alpha, rho = v.rho;
     const int constraint = v.constraint;
-    sr_grad_tile_apply<R>(sm, xk, v.y, H, W, v.taps, blockIdx.y * kGT, blockIdx.x * kGT,
-                          [&](int pi, int pj, float e, float o) {
-                              const size_t q = (size_t)pi * W + pj;
-                              const float g2[2] = {e, o};
+    sr_grad_tile_apply<R>(sm, xk, v.y, H, W, v.taps, y0, x0, [&](int pi, int pj, float e, float o) {
+        const size_t q = (size_t)pi * W + pj;
+        const float g2[2] = {e, o};
 #pragma unroll
-                              for (int c = 0; c < 2; ++c) {
-                                  const float up = uk[q + c], vp = vk[q + c];
-                                  const float xn = project(mu * (alpha * xk[q + c] + rho * (vp - up) - g2[c]), constraint);
-                                  grec[q + c] = g2[c];
-                                  x1[q + c] = xn;
-                                  z[q + c] = xn + up;
-                                  v1[q + c] = vp;
-                                  u1[q + c] = up;
-                              }
-                          });
+        for (int c = 0; c < 2; ++c) {
+            const float up = uk[q + c], vp = vk[q + c];
+            const float xn = project(mu * (alpha * xk[q + c] + rho * (vp - up) - g2[c]), constraint);
+            grec[q + c] = g2[c];
+            x1[q + c] = xn;
+            z[q + c] = xn + up;
+            v1[q + c] = vp;
+            u1[q + c] = up;
+        }
+    });
 }
 
-// The dual step of recorded iteration k in place on slot k + 1: v = W z (the third
-// aggregation of Algorithm 2 with the closure of Eq. S3, from the phase-1 partial sums
-// and 1/m on the device) and u <- u + x - v; the same per-pixel code as the solve's
-// combine, without the next x-update
-__global__ void __launch_bounds__(256) adj_fwd_dual_kernel(const TapeView* __restrict__ tv, int k) {
+template <int R>
+__global__ void __launch_bounds__(256) adj_fwd_xupdate_kernel(const TapeView* __restrict__ tv, int k) {
     griddep_enter();
-    const TapeView& v = tv[blockIdx.z];
+    __shared__ GradSmem<R> sm;
+    fwd_xupdate_tile<R>(sm, tv[blockIdx.z], k, blockIdx.y * kGT, blockIdx.x * kGT);
+}
+
+// The dual step of recorded iteration k in place on slot k + 1, on the kXH x kXW tile at
+// (y0, x0): v = W z (the third aggregation of Algorithm 2 with the closure of Eq. S3, from
+// the phase-1 partial sums and 1/m on the device) and u <- u + x - v; the same per-pixel
+// code as the solve's combine, without the next x-update and the residual sums
+__device__ __forceinline__ void fwd_dual_tile(const TapeView& v, int k, int y0, int x0) {
     const size_t n = (size_t)v.H * v.W;
     EpilogueArgs a{};
     a.H = v.H;
@@ -227,8 +228,13 @@ __global__ void __launch_bounds__(256) adj_fwd_dual_kernel(const TapeView* __res
     a.rho = v.rho;
     a.constraint = v.constraint;
     a.do_x = 0;
-    const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    combine_update_body<0, 0>(v.cv, a, 0, blockIdx.y * kXH, blockIdx.x * kXW, v.cpart + 2 * bid);
+    combine_update_body<0, 0>(v.cv, a, 0, y0, x0, nullptr);
+}
+
+__global__ void __launch_bounds__(256) adj_fwd_dual_kernel(const TapeView* __restrict__ tv, int k) {
+    griddep_enter();
+    const TapeView& v = tv[blockIdx.z];
+    fwd_dual_tile(v, k, blockIdx.y * kXH, blockIdx.x * kXW);
 }
 
 // x_N to the caller's buffer
@@ -1565,14 +1571,12 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
     const BlurTaps taps = make_blur_taps(blur_sigma, blur_r);
     for (int k = 0; k < N; ++k) {
         TAPE_CK(by_blur_radius(taps.r, [&](auto rc) {
-            return pdl(adj_fwd_xupdate_kernel<decltype(rc)::value>, dim3(gg), dim3(256), 0, st, tb.views, k);
+            return pdl(adj_fwd_xupdate_kernel<decltype(rc)::value>, gg, dim3(256), 0, st, tb.views, k);
         }));
-        count_launches(1);
         TAPE_CK(launch_tma_gather_batched(dtype, search_r, maps, tb.insts + (size_t)(T + 1) * count, tb.work,
                                           tb.nwork, err, st));
-        TAPE_CK(pdl(adj_fwd_dual_kernel, dim3(eg), dim3(32, 8), 0, st, tb.views, k));
-        count_launches(1);
-        TAPE_CK(cudaGetLastError());
+        TAPE_CK(pdl(adj_fwd_dual_kernel, eg, dim3(32, 8), 0, st, tb.views, k));
+        count_launches(2);
     }
     TAPE_CK(pdl(adj_xout_kernel, dim3(nblk(n), 1, count), dim3(256), 0, st, tb.views));
     count_launches(1);

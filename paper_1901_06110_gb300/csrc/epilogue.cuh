@@ -199,7 +199,7 @@ __device__ __forceinline__ float tile_gather_comp(const TileCover& c, int li, in
 // do_x, perform the next x-update there from the gradient at each pixel alone:
 // SR reads g = A^T(A x - y) computed beforehand (a.g), SPI evaluates h' in place.
 // x_in and x_out may be the same buffer.  Stores the tile's residual sums at
-// `partials` (two doubles).  All threads of a (32, 8) block must call it.
+// `partials` (two doubles; not when null).  All threads of a (32, 8) block must call it.
 template <int KIND, int SL = 0>  // KIND 0 super-resolution, 1 single-photon; SL as tile_gather
 __device__ __forceinline__ void combine_update_body(const Cover& cv, const EpilogueArgs& a, int do_x, int y0, int x0,
                                                     double* partials) {
@@ -267,7 +267,7 @@ __device__ __forceinline__ void combine_update_body(const Cover& cv, const Epilo
         s1[t >> 5] = sd;
     }
     __syncthreads();
-    if (t == 0) {
+    if (t == 0 && partials) {
         double pa = 0.0, pb = 0.0;
         for (int w = 0; w < 8; ++w) {
             pa += (double)s0[w];

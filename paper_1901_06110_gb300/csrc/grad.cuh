@@ -71,7 +71,7 @@ __device__ __forceinline__ void sr_grad_tile_apply(GradSmem<R>& sm, const float*
     int* cols = sm.cols;
     int* lrows = sm.lrows;
     int* lcols = sm.lcols;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.y * 32 + threadIdx.x, lane = tid & 31, warp = tid >> 5;  // blocks of 256 or (32, 8)
     const int h = H >> 1, w = W >> 1;
     // low-resolution window: rows qy_lo .. qy_lo + L - 1 (and columns likewise); the
     // staged x rows start at high-resolution row 2 qy_lo - G

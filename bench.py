@@ -665,11 +665,11 @@ def run_unrolled(steps: int, warmup: int, flush):
     # Algorithmic DRAM bytes of one forward + backward, in volumes of the weight planes
     # (n_h x H x W FP32): the build writes them once; every W application streams them
     # (T + 1 balancing passes and N iterations forward, N iterations and T balancing
-    # passes backward); the pair passes read K1 three times, write and read G twice,
-    # write D-hat once, and the guide adjoint reads D-hat once.
+    # passes backward); pair pass G reads K1 and writes G, the fused pair pass B reads K1
+    # and G (D-hat is formed in shared memory and never stored).
     T, N = params.balance_passes, params.iters
     nh = 2 * params.search_r * (params.search_r + 1)
-    volumes = 1 + (T + 1) + N + N + T + 3 + 2 + 1 + 1 + 1
+    volumes = 1 + (T + 1) + N + N + T + 2 + 2
     step_bytes = B * volumes * nh * H * W * 4
     ms = (fwd + bwd) / steps
     peak, peak_src = _peaks()

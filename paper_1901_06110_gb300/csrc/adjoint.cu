@@ -648,13 +648,15 @@ __global__ void __launch_bounds__(256) adj_boxguide_kernel(const TapeView* __res
 //      D-hat enters the box sums over Q), Kh as in pair pass B, into shared memory;
 //      pixels of Q itself also add Kh K1 D to the block's dL/dh partial, with
 //      D = (log2 lam - log2 K1) ln 2 / c recovered from the stored weight;
-//   2. row sums, then column sums: E_o on Q;
+//   2. row sums across the lanes of each warp (a warp holds one row of the 32-wide
+//      window), then, after the offset's one barrier, column sums: E_o on Q;
 //   3. the scatter of F_o(q) = 2 E_o(q) (g(q) - g(q + o)) as in the box-and-gather
 //      kernel, into the same partial layout (windows of Q's width).
 // D-hat is never stored.  The halo's D-hat is recomputed by the neighbouring tiles
 // ((kQH + 2 rp) 32 / (kQH (32 - 2 rp)) of the pairs, 1.43 at rp = 2), which costs less
-// than writing the planes and reading them back.  Every warp works on one row of the
-// 32-wide window, so its shared-memory accesses are conflict-free.
+// than writing the planes and reading them back.  The row sums alternate between two
+// buffers by offset parity, so one barrier per offset orders everything; shared-memory
+// accesses are conflict-free.
 // K1 and G of the window arrive by TMA, two offsets ahead, into a ring of two stages
 // (one thread issues the copies once every thread has finished with the stage).  The
 // tensors' rows are W wide and the planes are zero where s + o leaves the image (the
@@ -707,9 +709,8 @@ __global__ void __launch_bounds__(256, 3)
     const int fcells = FH * FW;
     const size_t n = (size_t)H * W;
     // stage st: K1 at smem + st KST, G at smem + 2 KST + st GST
-    float* Ds = reinterpret_cast<float*>(smem + 2 * KST + 2 * GST);  // [DH][32]
-    float* Rs = Ds + DH * 32;                                        // [DH][32] row sums (QW used)
-    float2* DP = reinterpret_cast<float2*>(Rs + DH * 32);            // [P][FH][FW] (d^2q, d^2q+1)
+    float* Rs = reinterpret_cast<float*>(smem + 2 * KST + 2 * GST);  // [2][DH][32] row sums (QW used), by offset parity
+    float2* DP = reinterpret_cast<float2*>(Rs + 2 * DH * 32);        // [P][FH][FW] (d^2q, d^2q+1)
     float2* TP = DP + (size_t)P * fcells;                            // [P][FH][FW] (th^2q, th^2q+1)
     float* Dd = reinterpret_cast<float*>(TP + (size_t)P * fcells);   // [FH][FW] d = d^T
     float* Gs = Dd + fcells;                                         // [AH][AW] the reflected guide
@@ -820,7 +821,10 @@ __global__ void __launch_bounds__(256, 3)
         const int fo = oy * FW + ox;
         const int oW = oy * W + ox;
         const float lk = lglam[k];
-        // 1. D-hat of offset k at the thread's cells
+        // 1. D-hat of offset k at the thread's cells and its row sums over the patch width:
+        // a warp holds one row of the 32-wide window, so the sums run across its lanes
+        // (the lanes past Q's width form sums that are not used)
+        float* Rk = Rs + (k & 1) * (DH * 32);
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
             const int a = ty + 8 * m;
@@ -846,36 +850,27 @@ __global__ void __launch_bounds__(256, 3)
                 const int si = sidx0 + 8 * m * W;
                 if (si == ss || si + oW == ss) Kh = fmaf(mh, ds * dr, Kh);
                 if ((ownb >> m) & 1u) hp = K > 0.f ? fmaf(Kh * K, (lk - __log2f(K)) * inv_c2, hp) : hp;
-                Ds[a * 32 + tx] = -c * K * Kh;
+                const float val = -c * K * Kh;
+                float rsum = val;
+#pragma unroll
+                for (int t = 1; t <= 2 * rp; ++t) rsum += __shfl_down_sync(0xffffffffu, val, t);
+                Rk[a * 32 + tx] = rsum;
             }
         }
-        __syncthreads();  // Ds of this offset written, the stage read; Ac of the offset before updated
+        // the row sums of this offset written, the stage read; the scatter of the offset
+        // before (which read the other row-sum buffer) done
+        __syncthreads();
         if (tid == 0 && k + 2 < k1) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(k + 2, st);
         }
-        // 2. row sums, then column sums
-        if (qcol) {
-#pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                const int a = ty + 8 * m;
-                if (m < 2 || a < DH) {
-                    const float* r = Ds + a * 32 + tx;
-                    float s = r[0];
-#pragma unroll
-                    for (int t = 1; t <= 2 * rp; ++t) s += r[t];
-                    Rs[a * 32 + tx] = s;
-                }
-            }
-        }
-        __syncthreads();  // Rs written; Ds free for the next offset
         // 3. the scatter
         if (qcol) {
             const int sh = oy * AW + ox;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int cq = h == 0 ? c0 : c1;
-                const float* r = Rs + (ty + 8 * h) * 32 + tx;
+                const float* r = Rk + (ty + 8 * h) * 32 + tx;
                 float e = r[0];
 #pragma unroll
                 for (int t = 1; t <= 2 * rp; ++t) e += r[t * 32];

@@ -664,12 +664,13 @@ def run_unrolled(steps: int, warmup: int, flush):
             bwd += e[1].elapsed_time(e[2])
     # Algorithmic DRAM bytes of one forward + backward, in volumes of the weight planes
     # (n_h x H x W FP32): the build writes them once; every W application streams them
-    # (T + 1 balancing passes and N iterations forward, N iterations and T balancing
-    # passes backward); pair pass G reads K1 and writes G, the fused pair pass B reads K1
+    # (T + 1 balancing passes and N iterations forward; backward N - 1 iterations, the
+    # last one applying W to a = 0, and T - 1 balancing passes, the cotangent of d^0 = 1
+    # being unused); pair pass G reads K1 and writes G, the fused pair pass B reads K1
     # and G (D-hat is formed in shared memory and never stored).
     T, N = params.balance_passes, params.iters
     nh = 2 * params.search_r * (params.search_r + 1)
-    volumes = 1 + (T + 1) + N + N + T + 2 + 2
+    volumes = 1 + (T + 1) + N + (N - 1) + max(T - 1, 0) + 2 + 2
     step_bytes = B * volumes * nh * H * W * 4
     ms = (fwd + bwd) / steps
     peak, peak_src = _peaks()

@@ -183,24 +183,34 @@ __device__ __forceinline__ void fwd_xupdate_tile(GradSmem<R>& sm, const TapeView
     float* z = v.z;
     const float mu = v.mu, alpha = v.alpha, rho = v.rho;
     const int constraint = v.constraint;
-    sr_grad_tile_apply<R>(sm, xk, v.y, H, W, v.taps, y0, x0, [&](int pi, int pj, float e, float o) {
-        const size_t q = (size_t)pi * W + pj;
-        const float g2[2] = {e, o};
+    float2 xp[2], vp2[2], up2[2];  // the epilogue pixels' x_k, v_k, u_k, loaded before the stencil
+    sr_grad_tile_apply2<R>(
+        sm, xk, v.y, H, W, v.taps, y0, x0,
+        [&](int sl, int pi, int pj) {
+            const size_t q = (size_t)pi * W + pj;  // even: a float2 per pair
+            xp[sl] = *reinterpret_cast<const float2*>(xk + q);
+            vp2[sl] = *reinterpret_cast<const float2*>(vk + q);
+            up2[sl] = *reinterpret_cast<const float2*>(uk + q);
+        },
+        [&](int sl, int pi, int pj, float e, float o) {
+            const size_t q = (size_t)pi * W + pj;
+            const float g2[2] = {e, o}, x2[2] = {xp[sl].x, xp[sl].y}, v2[2] = {vp2[sl].x, vp2[sl].y},
+                        u2[2] = {up2[sl].x, up2[sl].y};
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const float up = uk[q + c], vp = vk[q + c];
-            const float xn = project(mu * (alpha * xk[q + c] + rho * (vp - up) - g2[c]), constraint);
-            grec[q + c] = g2[c];
-            x1[q + c] = xn;
-            z[q + c] = xn + up;
-            v1[q + c] = vp;
-            u1[q + c] = up;
-        }
-    });
+            for (int c = 0; c < 2; ++c) {
+                const float up = u2[c], vp = v2[c];
+                const float xn = project(mu * (alpha * x2[c] + rho * (vp - up) - g2[c]), constraint);
+                grec[q + c] = g2[c];
+                x1[q + c] = xn;
+                z[q + c] = xn + up;
+                v1[q + c] = vp;
+                u1[q + c] = up;
+            }
+        });
 }
 
 template <int R>
-__global__ void __launch_bounds__(256) adj_fwd_xupdate_kernel(const TapeView* __restrict__ tv, int k) {
+__global__ void __launch_bounds__(256, 4) adj_fwd_xupdate_kernel(const TapeView* __restrict__ tv, int k) {
     griddep_enter();
     __shared__ GradSmem<R> sm;
     fwd_xupdate_tile<R>(sm, tv[blockIdx.z], k, blockIdx.y * kGT, blockIdx.x * kGT);
@@ -276,8 +286,9 @@ __global__ void __launch_bounds__(256) adj_bwd_prep_kernel(const TapeView* __res
 
 // W a finished from the phase-1 partial sums (W a = c_s a_s + (d_s / m) sum_r K1 d_r a_r,
 // the closure of Eq. S3), then zh = W a + uh, g = Pi_C'(xbar_k)(xh + zh) and the block's
-// partial of sum g mu ((v - u) - xbar).  Blocks of 32 x 8 pixels.
-__global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restrict__ tv, int k) {
+// partial of sum g mu ((v - u) - xbar).  Blocks of 32 x 8 pixels.  a_zero: a = 0 (no
+// weight stream ran; W a = 0).
+__global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restrict__ tv, int k, int a_zero) {
     griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int H = v.H, W = v.W;
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
         const size_t q = (size_t)i * W + j;
         const float* d = v.Dh + (size_t)v.T * n;
         const float* t_fin = v.Th + (size_t)v.T * n;
-        const float A = gather_partials(v.cv, i, j);
+        const float A = a_zero ? 0.f : gather_partials(v.cv, i, j);
         const float ds = d[q];
         const float dm = ds * inv_m;
         const float cs = 1.f - dm * (t_fin[q] - ds);
@@ -316,7 +327,7 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
 //   z in the interleaved copy).
 // g is only read, so the halo reads do not race with the writes.
 template <int R>
-__global__ void __launch_bounds__(256) adj_ata_update_kernel(const TapeView* __restrict__ tv, int k) {
+__global__ void __launch_bounds__(256, 4) adj_ata_update_kernel(const TapeView* __restrict__ tv, int k) {
     griddep_enter();
     __shared__ GradSmem<R> sm;
     const TapeView& v = tv[blockIdx.z];
@@ -331,27 +342,41 @@ __global__ void __launch_bounds__(256) adj_ata_update_kernel(const TapeView* __r
     const float* uprev = more ? v.U + (size_t)(k - 1) * n : nullptr;
     float* a_next = more ? v.AZ + (size_t)(k - 1) * n : nullptr;
     float* s4 = more ? v.AZ4 + 4 * (size_t)((k - 1) >> 1) * n + ((k - 1) & 1) : nullptr;  // lane of iteration k - 1
-    sr_grad_tile_apply<R>(sm, g, nullptr, H, W, v.taps, blockIdx.y * kGT, blockIdx.x * kGT,
-                          [&](int pi, int pj, float e, float o) {
-                              const size_t q = (size_t)pi * W + pj;
-                              const float ata[2] = {e, o};
+    // the epilogue pixels' inputs, loaded before the stencil (pixel pairs: q even)
+    float2 gp[2], zp[2], sp[2], xp[2], upv[2];
+    sr_grad_tile_apply2<R>(
+        sm, g, nullptr, H, W, v.taps, blockIdx.y * kGT, blockIdx.x * kGT,
+        [&](int sl, int pi, int pj) {
+            const size_t q = (size_t)pi * W + pj;
+            gp[sl] = *reinterpret_cast<const float2*>(g + q);
+            zp[sl] = *reinterpret_cast<const float2*>(zh + q);
+            sp[sl] = *reinterpret_cast<const float2*>(gs + q);
+            if (more) {
+                xp[sl] = *reinterpret_cast<const float2*>(xk + q);
+                upv[sl] = *reinterpret_cast<const float2*>(uprev + q);
+            }
+        },
+        [&](int sl, int pi, int pj, float e, float o) {
+            const size_t q = (size_t)pi * W + pj;
+            const float ata[2] = {e, o}, g2[2] = {gp[sl].x, gp[sl].y}, z2[2] = {zp[sl].x, zp[sl].y},
+                        s2[2] = {sp[sl].x, sp[sl].y};
 #pragma unroll
-                              for (int c = 0; c < 2; ++c) {
-                                  const float gg = g[q + c];
-                                  const float vv = mu * rho * gg;
-                                  const float uu = zh[q + c] - vv;
-                                  xh[q + c] = mu * (alpha * gg - ata[c]);
-                                  vh[q + c] = vv;
-                                  uh[q + c] = uu;
-                                  gs[q + c] += mu * gg;
-                                  if (a_next) {
-                                      const float an = vv - uu;
-                                      a_next[q + c] = an;
-                                      s4[4 * (q + c)] = an;
-                                      s4[4 * (q + c) + 2] = xk[q + c] + uprev[q + c];
-                                  }
-                              }
-                          });
+            for (int c = 0; c < 2; ++c) {
+                const float gg = g2[c];
+                const float vv = mu * rho * gg;
+                const float uu = z2[c] - vv;
+                xh[q + c] = mu * (alpha * gg - ata[c]);
+                vh[q + c] = vv;
+                uh[q + c] = uu;
+                gs[q + c] = s2[c] + mu * gg;
+                if (more) {
+                    const float an = vv - uu;
+                    a_next[q + c] = an;
+                    s4[4 * (q + c)] = an;
+                    s4[4 * (q + c) + 2] = (c == 0 ? xp[sl].x : xp[sl].y) + (c == 0 ? upv[sl].x : upv[sl].y);
+                }
+            }
+        });
 }
 
 // fixed-order sum of one partial array of each image into one of its cotangents:
@@ -743,6 +768,7 @@ __global__ void __launch_bounds__(256, 3)
     }
     // stage the fields over the field window (zero off the image), the guide and a zero
     // accumulator over the accumulator window, and log2 of every offset's hat weight
+#pragma unroll 2
     for (int idx = tid; idx < fcells; idx += 256) {
         const int a = idx / FW, b = idx - a * FW;
         const int i = q0y - rp + a, j = q0x - rp - rs + b;
@@ -1705,9 +1731,13 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     count_launches(1);
     TAPE_CK(cudaGetLastError());
     for (int k = N - 1; k >= 0; --k) {
-        // W a (W symmetric), finished with g and zh; xbar_k from the recorded grad f(x_k)
-        TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)k * count, tb.work, tb.nwork, err, st));
-        TAPE_CK(pdl(adj_wa_g_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, k));
+        // W a (W symmetric), finished with g and zh; xbar_k from the recorded grad f(x_k).
+        // In the last iteration a = vh - uh = 0, so W a = 0 needs no weight stream.
+        const int a_zero = k == N - 1;
+        if (!a_zero)
+            TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)k * count, tb.work, tb.nwork, err,
+                                              st));
+        TAPE_CK(pdl(adj_wa_g_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, k, a_zero));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
         // A^T A g and the updates of the cotangents, with the earlier iteration's inputs
@@ -1769,17 +1799,17 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     }
     // balancing passes backwards: th^p from the cotangent of d^{p+1}, then K1 th^p; the
     // finish of pass p forms the cotangent of d^p and at once th^{p-1} of the next pass
-    // (the cotangent of d^0 = 1 is not needed, so pass 0 has no finish)
+    // (the cotangent of d^0 = 1 is not needed, so K1 th^0 is not streamed and pass 0 has
+    // no finish)
     if (T > 0) {
         TAPE_CK(pdl(adj_sk_pre_kernel, dim3(ng), dim3(256), 0, st, tb.views));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
     }
-    for (int p = T - 1; p >= 0; --p) {
+    for (int p = T - 1; p >= 1; --p) {
         TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)(N + p) * count, tb.work, tb.nwork, err,
                                           st));
-        if (p == 0) break;
-        TAPE_CK(pdl(adj_sk_finish_pre_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, p));
+        TAPE_CK(pdl(adj_sk_finish_pre_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, p));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
     }

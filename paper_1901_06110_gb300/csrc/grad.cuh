@@ -55,12 +55,15 @@ struct GradSmem {
     int rows[GradDims<R>::S], cols[GradDims<R>::S], lrows[GradDims<R>::L], lcols[GradDims<R>::L];
 };
 
-// g on the 32 x 32 tile at (y0, x0), handed to epi(i, j, g(i, j), g(i, j + 1)) for each
-// even column j of the tile inside the image; all 256 threads of the block call it
-template <int R, typename Epi>
-__device__ __forceinline__ void sr_grad_tile_apply(GradSmem<R>& sm, const float* __restrict__ x,
-                                                   const float* __restrict__ y, int H, int W, const BlurTaps& taps,
-                                                   int y0, int x0, Epi&& epi) {
+// g on the 32 x 32 tile at (y0, x0), handed to epi(s, i, j, g(i, j), g(i, j + 1)) for each
+// even column j of the tile inside the image; all 256 threads of the block call it.
+// Each thread receives two such pixel pairs (s = 0, 1), and pre(s, i, j) is called for
+// them before the stencil passes, so that the caller's loads for the epilogue are in
+// flight while g is formed.
+template <int R, typename Pre, typename Epi>
+__device__ __forceinline__ void sr_grad_tile_apply2(GradSmem<R>& sm, const float* __restrict__ x,
+                                                    const float* __restrict__ y, int H, int W, const BlurTaps& taps,
+                                                    int y0, int x0, Pre&& pre, Epi&& epi) {
     using Dm = GradDims<R>;
     constexpr int G = Dm::G, L = Dm::L, S = Dm::S;
     auto& X = sm.X;
@@ -73,6 +76,14 @@ __device__ __forceinline__ void sr_grad_tile_apply(GradSmem<R>& sm, const float*
     int* lcols = sm.lcols;
     const int tid = threadIdx.y * 32 + threadIdx.x, lane = tid & 31, warp = tid >> 5;  // blocks of 256 or (32, 8)
     const int h = H >> 1, w = W >> 1;
+    // the thread's epilogue pixels: rows 2 warp + lane / 16 (+ 16), column x0 + 2 (lane % 16)
+    const int k = lane & 15;
+    const int py0 = 2 * warp + (lane >> 4);
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+        const int pi = y0 + py0 + 16 * sl, pj = x0 + 2 * k;
+        if (pi < H && pj < W) pre(sl, pi, pj);
+    }
     // low-resolution window: rows qy_lo .. qy_lo + L - 1 (and columns likewise); the
     // staged x rows start at high-resolution row 2 qy_lo - G
     const int qy_lo = (y0 - G) >> 1, qx_lo = (x0 - G) >> 1;
@@ -144,9 +155,11 @@ __device__ __forceinline__ void sr_grad_tile_apply(GradSmem<R>& sm, const float*
     }
     __syncthreads();
     // row half of A^T at columns 2k (even b) and 2k + 1 (odd b)
-    const int k = lane & 15;
     const int cbase = (x0 >> 1) + k - qx_lo;  // window column of (x0 + 2 k) / 2
-    for (int py = 2 * warp + (lane >> 4); py < kGT; py += 16) {
+    static_assert(kGT == 32, "two epilogue pixel pairs per thread");
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+        const int py = py0 + 16 * sl;
         float e = 0.f, o = 0.f;
 #pragma unroll
         for (int b = -R; b <= R; ++b) {
@@ -156,8 +169,18 @@ __device__ __forceinline__ void sr_grad_tile_apply(GradSmem<R>& sm, const float*
                 o = fmaf(taps.t[b + R], V[py][cbase + ((b + 1) >> 1)], o);
         }
         const int pi = y0 + py, pj = x0 + 2 * k;
-        if (pi < H && pj < W) epi(pi, pj, e, o);
+        if (pi < H && pj < W) epi(sl, pi, pj, e, o);
     }
+}
+
+// The same without the prefetch: epi(i, j, g(i, j), g(i, j + 1)).
+template <int R, typename Epi>
+__device__ __forceinline__ void sr_grad_tile_apply(GradSmem<R>& sm, const float* __restrict__ x,
+                                                   const float* __restrict__ y, int H, int W, const BlurTaps& taps,
+                                                   int y0, int x0, Epi&& epi) {
+    sr_grad_tile_apply2<R>(
+        sm, x, y, H, W, taps, y0, x0, [](int, int, int) {},
+        [&](int, int pi, int pj, float e, float o) { epi(pi, pj, e, o); });
 }
 
 // g stored on the 32 x 32 tile at (y0, x0)

@@ -101,21 +101,23 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-// Sum of one float per thread of a block of 256 threads: FP32 within each warp (a fixed
-// tree), the eight warp sums added in FP64 in warp order.  The result is valid in
+// Sum of one float per thread of a block of NW warps (256 threads by default): FP32
+// within each warp (a fixed tree), the warp sums added in FP64 in warp order.  The result is valid in
 // thread 0; every thread must call it, and a second call in the same kernel must be
 // separated from the first by a barrier.  (FP64 arithmetic runs at a small fraction of
 // the FP32 rate on this GPU, so per-element terms stay in FP32.)
-__device__ __forceinline__ double block_sum_256(float v, int tid) {
+template <int NW = 8>
+__device__ __forceinline__ double block_sum(float v, int tid) {
     v = warp_sum_f(v);
-    __shared__ float ws[8];
+    __shared__ float ws[NW];
     if ((tid & 31) == 0) ws[tid >> 5] = v;
     __syncthreads();
     double acc = 0.0;
     if (tid == 0)
-        for (int w = 0; w < 8; ++w) acc += (double)ws[w];
+        for (int w = 0; w < NW; ++w) acc += (double)ws[w];
     return acc;
 }
+__device__ __forceinline__ double block_sum_256(float v, int tid) { return block_sum<8>(v, tid); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -1304,6 +1304,11 @@ struct lpnp_tape {
     alignas(64) unsigned char gt_amap[128];  // the interleaved (a, z) copy for pair pass G
     const void* gt_abase = nullptr;
     int gt_akey[4] = {0, 0, 0, 0};
+    // the launch sequences of the forward (after the weight builds) and of the backward,
+    // recorded as CUDA graphs by the call this tape leads, and the keys they were recorded for
+    cudaGraphExec_t fwd_exec = nullptr, bwd_exec = nullptr;
+    std::vector<uint64_t> fwd_key, bwd_key;
+    uint64_t fwd_launches = 0, bwd_launches = 0;
 };
 
 namespace {
@@ -1346,6 +1351,51 @@ cudaError_t pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cuda
 
 cudaError_t ensure_event(cudaEvent_t& e) {
     return e ? cudaSuccess : cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+}
+
+// Queue `seq` (a function of the stream that queues a fixed launch sequence and returns a
+// status) on `st` through a CUDA graph: replayed when `key` equals the key the graph was
+// recorded for, recorded anew otherwise.  The graph keeps the programmatic launch edges,
+// and its replay takes one launch from the host and shorter gaps between the kernels.
+// Every kernel parameter of the sequence must be a function of the key: the per-call
+// pointers live in the tables in device memory, uploaded before the replay.  If the
+// recording fails, the sequence is queued directly.
+template <typename F>
+dsgnlm_status run_recorded(cudaGraphExec_t& exec, std::vector<uint64_t>& rec_key, uint64_t& rec_launches,
+                           const std::vector<uint64_t>& key, cudaStream_t st, F&& seq) {
+    if (exec && rec_key == key) {
+        TAPE_CK(cudaGraphLaunch(exec, st));
+        count_launches(rec_launches);
+        return DSGNLM_OK;
+    }
+    if (exec) {
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return seq(st);
+    }
+    set_capture_counting(true);
+    const dsgnlm_status s = seq(st);
+    set_capture_counting(false);
+    const uint64_t n = recorded_launches();
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess && s == DSGNLM_OK) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || s != DSGNLM_OK) {
+        exec = nullptr;
+        (void)cudaGetLastError();
+        if (s != DSGNLM_OK) return s;
+        return seq(st);
+    }
+    rec_key = key;
+    rec_launches = n;
+    TAPE_CK(cudaGraphLaunch(exec, st));
+    count_launches(n);
+    return DSGNLM_OK;
 }
 
 // The view of image i (the caller's pointers of the current call included).
@@ -1572,36 +1622,50 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
     const int dtype = dens[0]->dtype;
     const dim3 eg((W + kXW - 1) / kXW, (H + kXH - 1) / kXH, count);  // per-pixel epilogue blocks
     const dim3 ng(std::min(nblk(n), 1024), 1, count);
-    // 4. the work, one launch per step over all images
-    TAPE_CK(pdl(adj_prep_kernel, dim3(ng), dim3(256), 0, st, tb.views));
-    count_launches(1);
-    TAPE_CK(cudaGetLastError());
-    for (int p = 0; p <= T; ++p) {
-        TAPE_CK(launch_tma_gather_batched(dtype, search_r, maps, tb.insts + (size_t)p * count, tb.work, tb.nwork, err,
-                                          st));
-        TAPE_CK(pdl(adj_balance_kernel, dim3(eg), dim3(32, 8), 0, st, tb.views, p));
-        count_launches(1);
-        TAPE_CK(cudaGetLastError());
-    }
-    TAPE_CK(pdl(adj_m_key_kernel, dim3(ng), dim3(256), 0, st, tb.views));
-    TAPE_CK(pdl(adj_m_finish_kernel, dim3((count + 63) / 64), dim3(64), 0, st, tb.views, count));
-    TAPE_CK(pdl(adj_init_kernel, dim3(nblk(n), 1, count), dim3(256), 0, st, tb.views));
-    count_launches(3);
-    TAPE_CK(cudaGetLastError());
+    // 4. the work, one launch per step over all images, recorded once per configuration
+    // as a CUDA graph and replayed
     const dim3 gg((W + kGT - 1) / kGT, (H + kGT - 1) / kGT, count);
     const BlurTaps taps = make_blur_taps(blur_sigma, blur_r);
-    for (int k = 0; k < N; ++k) {
-        TAPE_CK(by_blur_radius(taps.r, [&](auto rc) {
-            return pdl(adj_fwd_xupdate_kernel<decltype(rc)::value>, gg, dim3(256), 0, st, tb.views, k);
-        }));
-        TAPE_CK(launch_tma_gather_batched(dtype, search_r, maps, tb.insts + (size_t)(T + 1) * count, tb.work,
-                                          tb.nwork, err, st));
-        TAPE_CK(pdl(adj_fwd_dual_kernel, eg, dim3(32, 8), 0, st, tb.views, k));
-        count_launches(2);
+    auto seq = [&](cudaStream_t st) -> dsgnlm_status {
+        TAPE_CK(pdl(adj_prep_kernel, dim3(ng), dim3(256), 0, st, tb.views));
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+        for (int p = 0; p <= T; ++p) {
+            TAPE_CK(launch_tma_gather_batched(dtype, search_r, maps, tb.insts + (size_t)p * count, tb.work,
+                                              tb.nwork, err, st));
+            TAPE_CK(pdl(adj_balance_kernel, dim3(eg), dim3(32, 8), 0, st, tb.views, p));
+            count_launches(1);
+            TAPE_CK(cudaGetLastError());
+        }
+        TAPE_CK(pdl(adj_m_key_kernel, dim3(ng), dim3(256), 0, st, tb.views));
+        TAPE_CK(pdl(adj_m_finish_kernel, dim3((count + 63) / 64), dim3(64), 0, st, tb.views, count));
+        TAPE_CK(pdl(adj_init_kernel, dim3(nblk(n), 1, count), dim3(256), 0, st, tb.views));
+        count_launches(3);
+        TAPE_CK(cudaGetLastError());
+        for (int k = 0; k < N; ++k) {
+            TAPE_CK(by_blur_radius(taps.r, [&](auto rc) {
+                return pdl(adj_fwd_xupdate_kernel<decltype(rc)::value>, gg, dim3(256), 0, st, tb.views, k);
+            }));
+            TAPE_CK(launch_tma_gather_batched(dtype, search_r, maps, tb.insts + (size_t)(T + 1) * count, tb.work,
+                                              tb.nwork, err, st));
+            TAPE_CK(pdl(adj_fwd_dual_kernel, eg, dim3(32, 8), 0, st, tb.views, k));
+            count_launches(2);
+        }
+        TAPE_CK(pdl(adj_xout_kernel, dim3(nblk(n), 1, count), dim3(256), 0, st, tb.views));
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+        return DSGNLM_OK;
+    };
+    std::vector<uint64_t> key = {(uint64_t)count,  (uint64_t)H,      (uint64_t)W, (uint64_t)patch_r,
+                                 (uint64_t)search_r, (uint64_t)T,    (uint64_t)N, (uint64_t)dtype,
+                                 (uint64_t)taps.r,   (uint64_t)(uintptr_t)tb.views, (uint64_t)tb.nwork,
+                                 (uint64_t)(uintptr_t)err};
+    for (int i = 0; i < count; ++i) {
+        key.push_back((uint64_t)(uintptr_t)dens[i]->planes.p);
+        key.push_back((uint64_t)dens[i]->plan.splits.n);
     }
-    TAPE_CK(pdl(adj_xout_kernel, dim3(nblk(n), 1, count), dim3(256), 0, st, tb.views));
-    count_launches(1);
-    TAPE_CK(cudaGetLastError());
+    s = run_recorded(lead->fwd_exec, lead->fwd_key, lead->fwd_launches, key, st, seq);
+    if (s != DSGNLM_OK) return s;
     // 5. every handle holds its image's W; its m and 1/m stay on the device until a
     // host-side use of the handle reads them back
     for (int i = 0; i < count; ++i) {
@@ -1727,160 +1791,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     const int dtype = dens[0]->dtype;
     const dim3 gg((W + kGT - 1) / kGT, (H + kGT - 1) / kGT, count);  // A^T A tiles
     const dim3 ng(nblk(n), 1, count);
-    TAPE_CK(pdl(adj_bwd_prep_kernel, dim3(ng), dim3(256), 0, st, tb.views, nrb));
-    count_launches(1);
-    TAPE_CK(cudaGetLastError());
-    for (int k = N - 1; k >= 0; --k) {
-        // W a (W symmetric), finished with g and zh; xbar_k from the recorded grad f(x_k).
-        // In the last iteration a = vh - uh = 0, so W a = 0 needs no weight stream.
-        const int a_zero = k == N - 1;
-        if (!a_zero)
-            TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)k * count, tb.work, tb.nwork, err,
-                                              st));
-        TAPE_CK(pdl(adj_wa_g_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, k, a_zero));
-        count_launches(1);
-        TAPE_CK(cudaGetLastError());
-        // A^T A g and the updates of the cotangents, with the earlier iteration's inputs
-        TAPE_CK(by_blur_radius(lead->taps.r, [&](auto rc) {
-            return pdl(adj_ata_update_kernel<decltype(rc)::value>, dim3(gg), dim3(256), 0, st, tb.views, k);
-        }));
-        count_launches(1);
-    }
-    // pair pass G with the mirrored terms, the gather of dh, then the cotangent of m and
-    // its terms
-    auto pairs_gt = [&](auto wt) -> cudaError_t {
-        using WT = decltype(wt);
-        const size_t smem = pairs_g_smem(N, rs, dtype);
-        const dim3 grid(pgx, pgy, kPairSplit * count);
-        auto run = [&](auto kern) -> cudaError_t {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            return pdl(kern, grid, dim3(32, 8), smem, st, tb.views, kPairSplit, err, kDefaultWaitBudget);
-        };
-        cudaError_t e;
-        switch ((N + 1) / 2) {
-            case 1: e = run(adj_pairs_gt_kernel<WT, 1>); break;
-            case 2: e = run(adj_pairs_gt_kernel<WT, 2>); break;
-            case 3: e = run(adj_pairs_gt_kernel<WT, 3>); break;
-            case 4: e = run(adj_pairs_gt_kernel<WT, 4>); break;
-            case 5: e = run(adj_pairs_gt_kernel<WT, 5>); break;
-            case 6: e = run(adj_pairs_gt_kernel<WT, 6>); break;
-            case 7: e = run(adj_pairs_gt_kernel<WT, 7>); break;
-            case 8: e = run(adj_pairs_gt_kernel<WT, 8>); break;
-            default: e = run(adj_pairs_gt_kernel<WT, 0>); break;
-        }
-        count_launches(1);
-        if (e != cudaSuccess) return e;
-        {
-            const int elems = pgx * pgy * (kQH + rs) * (32 + 2 * rs);
-            PDL_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st, tb.views, 1, elems,
-                       kPairSplit));
-        }
-        PDL_CK(pdl(adj_dh_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, pgy, pgx, 1));
-        count_launches(1);
-        PDL_CK(pdl(adj_sum_kernel, dim3(count), dim3(256), 0, st, tb.views, 0, npb, nrb));
-        PDL_CK(pdl(adj_mterms_kernel<WT>, dim3(count), dim3(256), 0, st, tb.views));
-        count_launches(3);
-        return cudaGetLastError();
-    };
-    auto pairs_b = [&](auto wt) -> cudaError_t {
-        using WT = decltype(wt);
-        const size_t smem = pairs_b_smem(T, rs);
-        cudaError_t e = cudaFuncSetAttribute(adj_pairs_b_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        PDL_CK(pdl(adj_pairs_b_kernel<WT>, dim3(pgx, pgy, kPairSplit * count), dim3(32, 8), smem, st, tb.views));
-        count_launches(1);
-        return cudaGetLastError();
-    };
-    switch (dtype) {
-        case DSGNLM_F32: TAPE_CK(pairs_gt(float{})); break;
-        case DSGNLM_F16: TAPE_CK(pairs_gt(__half{})); break;
-        default: TAPE_CK(pairs_gt(__nv_bfloat16{})); break;
-    }
-    // balancing passes backwards: th^p from the cotangent of d^{p+1}, then K1 th^p; the
-    // finish of pass p forms the cotangent of d^p and at once th^{p-1} of the next pass
-    // (the cotangent of d^0 = 1 is not needed, so K1 th^0 is not streamed and pass 0 has
-    // no finish)
-    if (T > 0) {
-        TAPE_CK(pdl(adj_sk_pre_kernel, dim3(ng), dim3(256), 0, st, tb.views));
-        count_launches(1);
-        TAPE_CK(cudaGetLastError());
-    }
-    for (int p = T - 1; p >= 1; --p) {
-        TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)(N + p) * count, tb.work, tb.nwork, err,
-                                          st));
-        TAPE_CK(pdl(adj_sk_finish_pre_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, p));
-        count_launches(1);
-        TAPE_CK(cudaGetLastError());
-    }
-    if (fused) {
-        // pair pass B with the box sums and the scatter of the patch-distance adjoint
-        auto bd = [&](auto wt) -> cudaError_t {
-            using WT = decltype(wt);
-            const size_t smem = pairs_bd_smem(T, rp, rs, dtype);
-            auto run = [&](auto kern) -> cudaError_t {
-                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e != cudaSuccess) return e;
-                return pdl(kern, dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), smem, st, tb.views, bg_chunks, err,
-                           kDefaultWaitBudget);
-            };
-            if (rp == 2 && rs == 7 && T == 4) return run(adj_pairs_bd_kernel<WT, 2, 7, 4>);
-            switch (rp) {
-                case 1: return run(adj_pairs_bd_kernel<WT, 1, 0, -1>);
-                case 2: return run(adj_pairs_bd_kernel<WT, 2, 0, -1>);
-                default: return run(adj_pairs_bd_kernel<WT, 3, 0, -1>);
-            }
-        };
-        switch (dtype) {
-            case DSGNLM_F32: TAPE_CK(bd(float{})); break;
-            case DSGNLM_F16: TAPE_CK(bd(__half{})); break;
-            default: TAPE_CK(bd(__nv_bfloat16{})); break;
-        }
-        count_launches(1);
-        {
-            const int elems = bg_tx * bg_ty * bg_win_h(rs) * (bg_qw + 2 * rs);
-            TAPE_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st, tb.views, 0, elems,
-                        bg_chunks));
-        }
-        TAPE_CK(pdl(adj_fold_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, bg_ty, bg_tx, 1, bg_qw));
-        count_launches(2);
-        TAPE_CK(cudaGetLastError());
-    } else {
-        // pair pass B: D-hat planes and dL/dh partials
-        switch (dtype) {
-            case DSGNLM_F32: TAPE_CK(pairs_b(float{})); break;
-            case DSGNLM_F16: TAPE_CK(pairs_b(__half{})); break;
-            default: TAPE_CK(pairs_b(__nv_bfloat16{})); break;
-        }
-        // patch distances back to the guide: box sums and the scatter of every offset per
-        // tile of the extended grid, then the gather of the partials and the fold through
-        // the reflection
-        const size_t bsmem =
-            sizeof(float) * (size_t)(2 * bg_win_h(rs) * bg_win_w(rs) + (kQH + 2 * rp) * (kQW + 2 * rp) +
-                                     (kQH + 2 * rp) * kQW);
-        TAPE_CK(cudaFuncSetAttribute(adj_boxguide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
-        TAPE_CK(pdl(adj_boxguide_kernel, dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), bsmem, st, tb.views,
-                    bg_chunks));
-        TAPE_CK(pdl(adj_fold_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, bg_ty, bg_tx, bg_chunks, bg_qw));
-        count_launches(2);
-        TAPE_CK(cudaGetLastError());
-    }
-    // dL/dy = sum_k mu A g_k = A gs
-    TAPE_CK(by_blur_radius(lead->taps.r, [&](auto rc) {
-        return pdl(adj_ybar_kernel<decltype(rc)::value>, dim3((W / 2 + 31) / 32, (H / 2 + 7) / 8, count),
-                   dim3(32, 8), 0, st, tb.views);
-    }));
-    count_launches(1);
-    TAPE_CK(pdl(adj_sum_kernel, dim3(count), dim3(256), 0, st, tb.views, 1, npb, nrb));
-    TAPE_CK(pdl(adj_sum_kernel, dim3(count), dim3(256), 0, st, tb.views, 2, nhb, nrb));
-    count_launches(2);
-    TAPE_CK(cudaGetLastError());
-    // every image's (m, rho, h) cotangents and the wait-error word, read back once
+    // the scalar cotangents' device and pinned host buffers (before any recording)
     TAPE_CK(lead->scal.ensure(sizeof(double) * 3 * (size_t)count));
-    TAPE_CK(pdl(adj_gather_scalars_kernel, dim3((count + 63) / 64), dim3(64), 0, st, tb.views, count,
-                lead->scal.as<double>()));
-    count_launches(1);
-    TAPE_CK(cudaGetLastError());
     if (lead->hs_count < count) {
         if (lead->hs) cudaFreeHost(lead->hs);
         lead->hs = nullptr;
@@ -1888,9 +1800,179 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         TAPE_CK(cudaMallocHost((void**)&lead->hs, sizeof(double) * (3 * (size_t)count + 1)));
         lead->hs_count = count;
     }
-    TAPE_CK(cudaMemcpyAsync(lead->hs, lead->scal.p, sizeof(double) * 3 * (size_t)count, cudaMemcpyDeviceToHost, st));
     unsigned* err_host = reinterpret_cast<unsigned*>(lead->hs + 3 * (size_t)count);
-    TAPE_CK(cudaMemcpyAsync(err_host, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    // the reverse sweep, the pair passes, the balance and the guide, and the read-back of
+    // every image's (m, rho, h) cotangents with the wait-error word: recorded once per
+    // configuration as a CUDA graph and replayed
+    auto seq = [&](cudaStream_t st) -> dsgnlm_status {
+        TAPE_CK(pdl(adj_bwd_prep_kernel, dim3(ng), dim3(256), 0, st, tb.views, nrb));
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+        for (int k = N - 1; k >= 0; --k) {
+            // W a (W symmetric), finished with g and zh; xbar_k from the recorded grad f(x_k).
+            // In the last iteration a = vh - uh = 0, so W a = 0 needs no weight stream.
+            const int a_zero = k == N - 1;
+            if (!a_zero)
+                TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)k * count, tb.work, tb.nwork, err,
+                                                  st));
+            TAPE_CK(pdl(adj_wa_g_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, k, a_zero));
+            count_launches(1);
+            TAPE_CK(cudaGetLastError());
+            // A^T A g and the updates of the cotangents, with the earlier iteration's inputs
+            TAPE_CK(by_blur_radius(lead->taps.r, [&](auto rc) {
+                return pdl(adj_ata_update_kernel<decltype(rc)::value>, dim3(gg), dim3(256), 0, st, tb.views, k);
+            }));
+            count_launches(1);
+        }
+        // pair pass G with the mirrored terms, the gather of dh, then the cotangent of m and
+        // its terms
+        auto pairs_gt = [&](auto wt) -> cudaError_t {
+            using WT = decltype(wt);
+            const size_t smem = pairs_g_smem(N, rs, dtype);
+            const dim3 grid(pgx, pgy, kPairSplit * count);
+            auto run = [&](auto kern) -> cudaError_t {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                return pdl(kern, grid, dim3(32, 8), smem, st, tb.views, kPairSplit, err, kDefaultWaitBudget);
+            };
+            cudaError_t e;
+            switch ((N + 1) / 2) {
+                case 1: e = run(adj_pairs_gt_kernel<WT, 1>); break;
+                case 2: e = run(adj_pairs_gt_kernel<WT, 2>); break;
+                case 3: e = run(adj_pairs_gt_kernel<WT, 3>); break;
+                case 4: e = run(adj_pairs_gt_kernel<WT, 4>); break;
+                case 5: e = run(adj_pairs_gt_kernel<WT, 5>); break;
+                case 6: e = run(adj_pairs_gt_kernel<WT, 6>); break;
+                case 7: e = run(adj_pairs_gt_kernel<WT, 7>); break;
+                case 8: e = run(adj_pairs_gt_kernel<WT, 8>); break;
+                default: e = run(adj_pairs_gt_kernel<WT, 0>); break;
+            }
+            count_launches(1);
+            if (e != cudaSuccess) return e;
+            {
+                const int elems = pgx * pgy * (kQH + rs) * (32 + 2 * rs);
+                PDL_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st, tb.views, 1, elems,
+                           kPairSplit));
+            }
+            PDL_CK(pdl(adj_dh_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, pgy, pgx, 1));
+            count_launches(1);
+            PDL_CK(pdl(adj_sum_kernel, dim3(count), dim3(256), 0, st, tb.views, 0, npb, nrb));
+            PDL_CK(pdl(adj_mterms_kernel<WT>, dim3(count), dim3(256), 0, st, tb.views));
+            count_launches(3);
+            return cudaGetLastError();
+        };
+        auto pairs_b = [&](auto wt) -> cudaError_t {
+            using WT = decltype(wt);
+            const size_t smem = pairs_b_smem(T, rs);
+            cudaError_t e = cudaFuncSetAttribute(adj_pairs_b_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            PDL_CK(pdl(adj_pairs_b_kernel<WT>, dim3(pgx, pgy, kPairSplit * count), dim3(32, 8), smem, st, tb.views));
+            count_launches(1);
+            return cudaGetLastError();
+        };
+        switch (dtype) {
+            case DSGNLM_F32: TAPE_CK(pairs_gt(float{})); break;
+            case DSGNLM_F16: TAPE_CK(pairs_gt(__half{})); break;
+            default: TAPE_CK(pairs_gt(__nv_bfloat16{})); break;
+        }
+        // balancing passes backwards: th^p from the cotangent of d^{p+1}, then K1 th^p; the
+        // finish of pass p forms the cotangent of d^p and at once th^{p-1} of the next pass
+        // (the cotangent of d^0 = 1 is not needed, so K1 th^0 is not streamed and pass 0 has
+        // no finish)
+        if (T > 0) {
+            TAPE_CK(pdl(adj_sk_pre_kernel, dim3(ng), dim3(256), 0, st, tb.views));
+            count_launches(1);
+            TAPE_CK(cudaGetLastError());
+        }
+        for (int p = T - 1; p >= 1; --p) {
+            TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)(N + p) * count, tb.work, tb.nwork, err,
+                                              st));
+            TAPE_CK(pdl(adj_sk_finish_pre_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, p));
+            count_launches(1);
+            TAPE_CK(cudaGetLastError());
+        }
+        if (fused) {
+            // pair pass B with the box sums and the scatter of the patch-distance adjoint
+            auto bd = [&](auto wt) -> cudaError_t {
+                using WT = decltype(wt);
+                const size_t smem = pairs_bd_smem(T, rp, rs, dtype);
+                auto run = [&](auto kern) -> cudaError_t {
+                    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (e != cudaSuccess) return e;
+                    return pdl(kern, dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), smem, st, tb.views, bg_chunks, err,
+                               kDefaultWaitBudget);
+                };
+                if (rp == 2 && rs == 7 && T == 4) return run(adj_pairs_bd_kernel<WT, 2, 7, 4>);
+                switch (rp) {
+                    case 1: return run(adj_pairs_bd_kernel<WT, 1, 0, -1>);
+                    case 2: return run(adj_pairs_bd_kernel<WT, 2, 0, -1>);
+                    default: return run(adj_pairs_bd_kernel<WT, 3, 0, -1>);
+                }
+            };
+            switch (dtype) {
+                case DSGNLM_F32: TAPE_CK(bd(float{})); break;
+                case DSGNLM_F16: TAPE_CK(bd(__half{})); break;
+                default: TAPE_CK(bd(__nv_bfloat16{})); break;
+            }
+            count_launches(1);
+            {
+                const int elems = bg_tx * bg_ty * bg_win_h(rs) * (bg_qw + 2 * rs);
+                TAPE_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st, tb.views, 0, elems,
+                            bg_chunks));
+            }
+            TAPE_CK(pdl(adj_fold_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, bg_ty, bg_tx, 1, bg_qw));
+            count_launches(2);
+            TAPE_CK(cudaGetLastError());
+        } else {
+            // pair pass B: D-hat planes and dL/dh partials
+            switch (dtype) {
+                case DSGNLM_F32: TAPE_CK(pairs_b(float{})); break;
+                case DSGNLM_F16: TAPE_CK(pairs_b(__half{})); break;
+                default: TAPE_CK(pairs_b(__nv_bfloat16{})); break;
+            }
+            // patch distances back to the guide: box sums and the scatter of every offset per
+            // tile of the extended grid, then the gather of the partials and the fold through
+            // the reflection
+            const size_t bsmem =
+                sizeof(float) * (size_t)(2 * bg_win_h(rs) * bg_win_w(rs) + (kQH + 2 * rp) * (kQW + 2 * rp) +
+                                         (kQH + 2 * rp) * kQW);
+            TAPE_CK(cudaFuncSetAttribute(adj_boxguide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+            TAPE_CK(pdl(adj_boxguide_kernel, dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), bsmem, st, tb.views,
+                        bg_chunks));
+            TAPE_CK(pdl(adj_fold_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, bg_ty, bg_tx, bg_chunks, bg_qw));
+            count_launches(2);
+            TAPE_CK(cudaGetLastError());
+        }
+        // dL/dy = sum_k mu A g_k = A gs
+        TAPE_CK(by_blur_radius(lead->taps.r, [&](auto rc) {
+            return pdl(adj_ybar_kernel<decltype(rc)::value>, dim3((W / 2 + 31) / 32, (H / 2 + 7) / 8, count),
+                       dim3(32, 8), 0, st, tb.views);
+        }));
+        count_launches(1);
+        TAPE_CK(pdl(adj_sum_kernel, dim3(count), dim3(256), 0, st, tb.views, 1, npb, nrb));
+        TAPE_CK(pdl(adj_sum_kernel, dim3(count), dim3(256), 0, st, tb.views, 2, nhb, nrb));
+        count_launches(2);
+        TAPE_CK(cudaGetLastError());
+        // every image's (m, rho, h) cotangents and the wait-error word, read back once
+        TAPE_CK(pdl(adj_gather_scalars_kernel, dim3((count + 63) / 64), dim3(64), 0, st, tb.views, count,
+                    lead->scal.as<double>()));
+        count_launches(1);
+        TAPE_CK(cudaGetLastError());
+        TAPE_CK(cudaMemcpyAsync(lead->hs, lead->scal.p, sizeof(double) * 3 * (size_t)count, cudaMemcpyDeviceToHost, st));
+        TAPE_CK(cudaMemcpyAsync(err_host, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        return DSGNLM_OK;
+    };
+    std::vector<uint64_t> key = {(uint64_t)count,  (uint64_t)H,     (uint64_t)W,  (uint64_t)rp,
+                                 (uint64_t)rs,     (uint64_t)T,     (uint64_t)N,  (uint64_t)dtype,
+                                 (uint64_t)lead->taps.r, (uint64_t)(uintptr_t)tb.views, (uint64_t)tb.nwork,
+                                 (uint64_t)(uintptr_t)err, (uint64_t)(uintptr_t)lead->scal.p,
+                                 (uint64_t)(uintptr_t)lead->hs};
+    for (int i = 0; i < count; ++i) {
+        key.push_back((uint64_t)(uintptr_t)dens[i]->planes.p);
+        key.push_back((uint64_t)dens[i]->plan.splits.n);
+    }
+    s = run_recorded(lead->bwd_exec, lead->bwd_key, lead->bwd_launches, key, st, seq);
+    if (s != DSGNLM_OK) return s;
     s = join_streams(lead, dens.data(), count, st);
     if (s != DSGNLM_OK) return s;
     TAPE_CK(cudaStreamSynchronize(st));
@@ -1929,6 +2011,8 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (t->hs) cudaFreeHost(t->hs);
     if (t->staged) cudaEventDestroy(t->staged);
     if (t->ev) cudaEventDestroy(t->ev);
+    if (t->fwd_exec) cudaGraphExecDestroy(t->fwd_exec);
+    if (t->bwd_exec) cudaGraphExecDestroy(t->bwd_exec);
     delete t;
 }
 

@@ -19,10 +19,18 @@
 namespace dsg {
 static std::atomic<uint64_t> g_launches{0};
 static thread_local bool g_capturing = false;  // launches recorded into a graph are counted at replay
+static thread_local uint64_t g_recorded = 0;   // launches recorded since set_capture_counting(true)
 void count_launches(uint64_t n) {
-    if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+    if (!g_capturing)
+        g_launches.fetch_add(n, std::memory_order_relaxed);
+    else
+        g_recorded += n;
 }
-void set_capture_counting(bool recording) { g_capturing = recording; }
+void set_capture_counting(bool recording) {
+    g_capturing = recording;
+    if (recording) g_recorded = 0;
+}
+uint64_t recorded_launches() { return g_recorded; }
 // Tensor map of planes [nh][H][pitch] of the storage type `dtype`, pitch in elements
 // (plane_pitch(W) when 0); the tensor's rows are W wide, so boxes read zeros past
 // column W - 1 (and past row H - 1, and before row or column 0).

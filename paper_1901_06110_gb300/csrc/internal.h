@@ -21,6 +21,7 @@ struct NvtxRange {
 // while set (on this thread), count_launches adds nothing: the kernels being recorded
 // into a graph are counted each time the graph is launched
 void set_capture_counting(bool recording);
+uint64_t recorded_launches();  // launches counted while recording, since set_capture_counting(true)
 // makes `e` the value dsgnlm_last_cuda_error() returns in this thread
 void record_cuda_error(cudaError_t e);
 

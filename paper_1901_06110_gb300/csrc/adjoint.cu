@@ -40,6 +40,7 @@
 #include "grad.cuh"
 #include "handle.h"
 #include "internal.h"
+#include "launch.h"
 #include "tma.cuh"
 #include "xupdate.cuh"
 
@@ -1325,28 +1326,17 @@ dsgnlm_status tape_ck(cudaError_t e) {
         if (s_ != DSGNLM_OK) return s_;                 \
     } while (0)
 
-// Launch with programmatic stream serialization: the kernel's blocks may be scheduled
-// while the previous kernel on the stream drains, and every kernel of this file waits
-// for its predecessors (griddep_wait) before it touches memory.
 #define PDL_CK(expr)                     \
     do {                                 \
         cudaError_t e_ = (expr);         \
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
+// every launch of this file: programmatic stream serialization (launch.h); every kernel
+// of this file waits for its predecessors (griddep_enter) before it touches memory
 template <typename... KArgs, typename... Args>
 cudaError_t pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+    return launch_pdl(kern, grid, block, smem, st, args...);
 }
 
 cudaError_t ensure_event(cudaEvent_t& e) {

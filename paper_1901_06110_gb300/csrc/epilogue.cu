@@ -18,6 +18,7 @@
 #include "common.cuh"
 #include "epilogue.cuh"
 #include "internal.h"
+#include "launch.h"
 #include "xupdate.cuh"
 
 namespace dsg {
@@ -95,6 +96,7 @@ balance_epilogue_kernel(Cover cv, int H, int W, const float* __restrict__ d_in, 
 template <int KIND, int SL>
 __global__ void __launch_bounds__(256, SL > 0 ? 4 : 3)
 combine_update_kernel(Cover cv, EpilogueArgs a) {
+    griddep_enter();  // may be launched with programmatic stream serialization
     const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     combine_update_body<KIND, SL>(cv, a, a.do_x, blockIdx.y * kXH, blockIdx.x * kXW, a.partials + 2 * bid);
 }
@@ -135,17 +137,20 @@ cudaError_t launch_balance_epilogue(const TmaPlan& plan, int H, int W, int rs, c
 int combine_xupdate_blocks(int H, int W) { return ((W + kXW - 1) / kXW) * ((H + kXH - 1) / kXH); }
 
 cudaError_t launch_combine_update(int kind, const TmaPlan& plan, int rs, const EpilogueArgs& args,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, bool pdl) {
     if (kind == 0 && args.do_x && !args.g) return cudaErrorInvalidValue;
     const dim3 grid((args.W + kXW - 1) / kXW, (args.H + kXH - 1) / kXH);
     const Cover cv = cover(plan, rs);
     return by_slices(plan.splits.n, [&](auto sl) {
         constexpr int SL = decltype(sl)::value;
+        count_launches(1);
+        if (pdl)
+            return kind == 0 ? launch_pdl(combine_update_kernel<0, SL>, grid, dim3(32, 8), 0, st, cv, args)
+                             : launch_pdl(combine_update_kernel<1, SL>, grid, dim3(32, 8), 0, st, cv, args);
         if (kind == 0)
             combine_update_kernel<0, SL><<<grid, dim3(32, 8), 0, st>>>(cv, args);
         else
             combine_update_kernel<1, SL><<<grid, dim3(32, 8), 0, st>>>(cv, args);
-        count_launches(1);
         return cudaGetLastError();
     });
 }

@@ -117,10 +117,11 @@ size_t tma_region_floats(int rs);
 int tma_p2_blocks(int H, int W);
 // phase 1: partial sums of K1 q over every tile and offset slice, q = d (z null) or d z
 // wait_budget: cycles a consumer waits for a plane before the CTA gives up and sets
-// *err (kDefaultWaitBudget, about 2 s; 0 gives up at the first wait)
+// *err (kDefaultWaitBudget, about 2 s; 0 gives up at the first wait); pdl: launched with
+// programmatic stream serialization (the kernel waits for its predecessor)
 cudaError_t launch_tma_gather(int dtype, const TmaPlan& plan, int H, int W, int rs, const float* d,
                               const float* z, unsigned* err, const int* skip, cudaStream_t st,
-                              long long wait_budget = kDefaultWaitBudget);
+                              long long wait_budget = kDefaultWaitBudget, bool pdl = false);
 // phase 2 epilogues
 cudaError_t launch_tma_apply_finish(const TmaPlan& plan, int H, int W, int rs, const float* d,
                                     const float* t, float inv_m, const float* z, float* y,
@@ -240,7 +241,7 @@ int combine_xupdate_blocks(int H, int W);  // epilogue tiles (kXH x kXW) of an i
 // Finish v, u of one iteration and perform the next x-update, per pixel (SR takes
 // the gradient from args.g); one residual pair per epilogue tile.
 cudaError_t launch_combine_update(int kind, const TmaPlan& plan, int rs, const EpilogueArgs& args,
-                                  cudaStream_t st);
+                                  cudaStream_t st, bool pdl = false);
 
 // Batched Algorithm 1 (batched.cu).  x is updated in place (a.x_in == a.x_out); SR
 // reads the gradient of the current x from a.g.

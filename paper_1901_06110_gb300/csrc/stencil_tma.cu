@@ -32,6 +32,7 @@
 #include "combine.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "launch.h"
 #include "tma.cuh"
 
 namespace dsg {
@@ -392,16 +393,19 @@ size_t p1_smem_bytes() {
 
 template <int RS, typename WT>
 cudaError_t p1_launch(const TmaPlan& plan, int H, int W, const float* d, const float* z, unsigned* err,
-                      const int* skip, cudaStream_t st, long long cbudget) {
+                      const int* skip, cudaStream_t st, long long cbudget, bool pdl) {
     const size_t smem = p1_smem_bytes<RS, WT>();
     // set once per instantiation (a thread-safe static initialisation)
     static const cudaError_t configured =
         cudaFuncSetAttribute(stencil_p1_kernel<RS, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (configured != cudaSuccess) return configured;
     dim3 grid(plan.tiles_x, plan.tiles_y, plan.splits.n);
+    count_launches(1);
+    if (pdl)
+        return launch_pdl(stencil_p1_kernel<RS, WT>, grid, dim3(kThreads), smem, st, *(const CUtensorMap*)plan.tmap, H,
+                          W, d, z, plan.splits, plan.partials, err, skip, cbudget);
     stencil_p1_kernel<RS, WT><<<grid, kThreads, smem, st>>>(*(const CUtensorMap*)plan.tmap, H, W, d, z,
                                                             plan.splits, plan.partials, err, skip, cbudget);
-    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -415,17 +419,8 @@ cudaError_t p1b_launch(const BatchMaps& maps, const BatchInst* insts, const int4
     if (nwork <= 0) return cudaSuccess;
     // programmatic stream serialization: the blocks may be scheduled while the previous
     // kernel drains (the kernel waits for it before touching memory)
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(nwork);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, stencil_p1_batched_kernel<RS, WT>, maps, insts, work, err);
+    const cudaError_t e =
+        launch_pdl(stencil_p1_batched_kernel<RS, WT>, dim3(nwork), dim3(kThreads), smem, st, maps, insts, work, err);
     count_launches(1);
     return e;
 }
@@ -450,18 +445,18 @@ cudaError_t p1b_dispatch(int rs, const BatchMaps& maps, const BatchInst* insts, 
 
 template <typename WT>
 cudaError_t p1_dispatch(int rs, const TmaPlan& plan, int H, int W, const float* d, const float* z,
-                        unsigned* err, const int* skip, cudaStream_t st, long long cbudget) {
+                        unsigned* err, const int* skip, cudaStream_t st, long long cbudget, bool pdl) {
     switch (rs) {
-        case 1: return p1_launch<1, WT>(plan, H, W, d, z, err, skip, st, cbudget);
-        case 2: return p1_launch<2, WT>(plan, H, W, d, z, err, skip, st, cbudget);
-        case 3: return p1_launch<3, WT>(plan, H, W, d, z, err, skip, st, cbudget);
-        case 4: return p1_launch<4, WT>(plan, H, W, d, z, err, skip, st, cbudget);
-        case 5: return p1_launch<5, WT>(plan, H, W, d, z, err, skip, st, cbudget);
-        case 6: return p1_launch<6, WT>(plan, H, W, d, z, err, skip, st, cbudget);
-        case 7: return p1_launch<7, WT>(plan, H, W, d, z, err, skip, st, cbudget);
-        case 8: return p1_launch<8, WT>(plan, H, W, d, z, err, skip, st, cbudget);
-        case 10: return p1_launch<10, WT>(plan, H, W, d, z, err, skip, st, cbudget);
-        case 12: return p1_launch<12, WT>(plan, H, W, d, z, err, skip, st, cbudget);
+        case 1: return p1_launch<1, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
+        case 2: return p1_launch<2, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
+        case 3: return p1_launch<3, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
+        case 4: return p1_launch<4, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
+        case 5: return p1_launch<5, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
+        case 6: return p1_launch<6, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
+        case 7: return p1_launch<7, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
+        case 8: return p1_launch<8, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
+        case 10: return p1_launch<10, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
+        case 12: return p1_launch<12, WT>(plan, H, W, d, z, err, skip, st, cbudget, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -492,11 +487,11 @@ int tma_p2_blocks(int H, int W) {
 
 cudaError_t launch_tma_gather(int dtype, const TmaPlan& plan, int H, int W, int rs, const float* d,
                               const float* z, unsigned* err, const int* skip, cudaStream_t st,
-                              long long wait_budget) {
+                              long long wait_budget, bool pdl) {
     switch (dtype) {
-        case 0: return p1_dispatch<float>(rs, plan, H, W, d, z, err, skip, st, wait_budget);
-        case 1: return p1_dispatch<__half>(rs, plan, H, W, d, z, err, skip, st, wait_budget);
-        default: return p1_dispatch<__nv_bfloat16>(rs, plan, H, W, d, z, err, skip, st, wait_budget);
+        case 0: return p1_dispatch<float>(rs, plan, H, W, d, z, err, skip, st, wait_budget, pdl);
+        case 1: return p1_dispatch<__half>(rs, plan, H, W, d, z, err, skip, st, wait_budget, pdl);
+        default: return p1_dispatch<__nv_bfloat16>(rs, plan, H, W, d, z, err, skip, st, wait_budget, pdl);
     }
 }
 

@@ -287,34 +287,55 @@ __global__ void __launch_bounds__(256) adj_bwd_prep_kernel(const TapeView* __res
 
 // W a finished from the phase-1 partial sums (W a = c_s a_s + (d_s / m) sum_r K1 d_r a_r,
 // the closure of Eq. S3), then zh = W a + uh, g = Pi_C'(xbar_k)(xh + zh) and the block's
-// partial of sum g mu ((v - u) - xbar).  Blocks of 32 x 8 pixels.  a_zero: a = 0 (no
-// weight stream ran; W a = 0).
+// partial of sum g mu ((v - u) - xbar).  Blocks of 32 x 8 threads, 16 x 32 pixels.
+// a_zero: a = 0 (no weight stream ran; W a = 0).
 __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restrict__ tv, int k, int a_zero) {
     griddep_enter();
     const TapeView& v = tv[blockIdx.z];
     const int H = v.H, W = v.W;
     const size_t n = (size_t)H * W;
     const int j = blockIdx.x * 32 + threadIdx.x;
-    const int i = blockIdx.y * 8 + threadIdx.y;
     const float inv_m = __ldg(v.m + 1);
     const float mu = v.mu, alpha = v.alpha, rho = v.rho;
+    const float* d = v.Dh + (size_t)v.T * n;
+    const float* t_fin = v.Th + (size_t)v.T * n;
+    const float *ak = v.AZ + (size_t)k * n, *vk = v.V + (size_t)k * n, *uk = v.U + (size_t)k * n;
+    const float *xk = v.X + (size_t)k * n, *gk = v.Gr + (size_t)k * n;
+    // the thread's two pixels, rows i and i + 8 of the block's 16 x 32 tile: every load of
+    // both is issued before the first use
+    float ds[2], ts[2], as[2], uhs[2], vs[2], us[2], xs[2], grs[2], xhs[2], A[2];
+    bool ok[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int i = blockIdx.y * 16 + threadIdx.y + 8 * c;
+        ok[c] = i < H && j < W;
+        const size_t q = ok[c] ? (size_t)i * W + j : 0;
+        ds[c] = d[q];
+        ts[c] = t_fin[q];
+        as[c] = ak[q];
+        uhs[c] = v.uh[q];
+        vs[c] = vk[q];
+        us[c] = uk[q];
+        xs[c] = xk[q];
+        grs[c] = gk[q];
+        xhs[c] = v.xh[q];
+        A[c] = (a_zero || !ok[c]) ? 0.f : gather_partials(v.cv, i, j);
+    }
     float r = 0.f;
-    if (i < H && j < W) {
-        const size_t q = (size_t)i * W + j;
-        const float* d = v.Dh + (size_t)v.T * n;
-        const float* t_fin = v.Th + (size_t)v.T * n;
-        const float A = a_zero ? 0.f : gather_partials(v.cv, i, j);
-        const float ds = d[q];
-        const float dm = ds * inv_m;
-        const float cs = 1.f - dm * (t_fin[q] - ds);
-        const float wa = fmaf(dm, A, cs * v.AZ[(size_t)k * n + q]);
-        const float zz = wa + v.uh[q];
-        const float vu = v.V[(size_t)k * n + q] - v.U[(size_t)k * n + q];
-        const float xb = mu * (alpha * v.X[(size_t)k * n + q] + rho * vu - v.Gr[(size_t)k * n + q]);
-        const float gg = proj_deriv(xb, v.constraint) * (v.xh[q] + zz);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!ok[c]) continue;
+        const size_t q = (size_t)(blockIdx.y * 16 + threadIdx.y + 8 * c) * W + j;
+        const float dm = ds[c] * inv_m;
+        const float cs = 1.f - dm * (ts[c] - ds[c]);
+        const float wa = fmaf(dm, A[c], cs * as[c]);
+        const float zz = wa + uhs[c];
+        const float vu = vs[c] - us[c];
+        const float xb = mu * (alpha * xs[c] + rho * vu - grs[c]);
+        const float gg = proj_deriv(xb, v.constraint) * (xhs[c] + zz);
         v.g[q] = gg;
         v.zh[q] = zz;
-        r = gg * mu * (vu - xb);
+        r += gg * mu * (vu - xb);
     }
     const int t = threadIdx.y * 32 + threadIdx.x;
     const double acc = block_sum_256(r, t);
@@ -1694,7 +1715,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     const size_t n = (size_t)H * W;
     const int nh = num_half_offsets(rs);
     const dim3 pgrid2((W + 31) / 32, (H + 7) / 8, count);  // per-pixel passes in 32 x 8 blocks
-    const int nrb = (int)(pgrid2.x * pgrid2.y);
+    const dim3 wgrid((W + 31) / 32, (H + 15) / 16, count);  // the W a finish: 16 x 32 pixels per block
+    const int nrb = (int)(wgrid.x * wgrid.y);                // its blocks' rho partials
     const int pgx = (W + kAdjTW - 1) / kAdjTW, pgy = (H + kAdjTH - 1) / kAdjTH;  // tiles of pair passes G and B
     const int npb = pgx * pgy * kPairSplit;  // pair-pass blocks (with the offset chunks)
     // patch-distance adjoint: tiles of the extended grid, the half offsets in kPairSplit
@@ -1805,7 +1827,7 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
             if (!a_zero)
                 TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)k * count, tb.work, tb.nwork, err,
                                                   st));
-            TAPE_CK(pdl(adj_wa_g_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, k, a_zero));
+            TAPE_CK(pdl(adj_wa_g_kernel, wgrid, dim3(32, 8), 0, st, tb.views, k, a_zero));
             count_launches(1);
             TAPE_CK(cudaGetLastError());
             // A^T A g and the updates of the cotangents, with the earlier iteration's inputs

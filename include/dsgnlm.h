@@ -436,6 +436,24 @@ dsgnlm_status dsgnlm_profile_read(dsgnlm_t h, int kind, double* total_ms, int* l
  * replay counts each of its kernel nodes). */
 uint64_t dsgnlm_launch_count(void);
 
+/* Checked build.  The library built with -DDSGNLM_CHECKED (lib/libdsgnlm_checked.so)
+ * tests the computed offsets of its gathers and scattered writes against the sizes of
+ * the buffers they address: the weight planes the build writes, the phase-1 partial
+ * regions (written by phase 1, read by every finish), the G planes and the window
+ * partials of the adjoint.  A failed test sets a bit of a device word (1 weight planes,
+ * 2 phase-1 partials, 8 G planes, 16 adjoint window partials, 0x80000000 the self
+ * test) and skips the access, so an index error shows in the word instead of as a
+ * fault.
+ *   dsgnlm_is_checked: 1 in the checked build, 0 otherwise.
+ *   dsgnlm_check_word: the OR of the words of every translation unit (0 in the normal
+ *     build); with clear != 0 the words are reset.  Synchronises the device.
+ *   dsgnlm_check_selftest: one thread tests `index` against `bound` with the checked
+ *     build's test (bit 0x80000000) and touches no buffer; it checks the mechanism
+ *     without an out-of-range access. */
+int dsgnlm_is_checked(void);
+dsgnlm_status dsgnlm_check_word(unsigned* word, int clear);
+dsgnlm_status dsgnlm_check_selftest(long long index, long long bound);
+
 /* CUDA error code (cudaError_t) of the most recent DSGNLM_ECUDA in this thread. */
 int dsgnlm_last_cuda_error(void);
 

@@ -83,9 +83,18 @@ SIGNATURES = {
     "dsgnlm_launch_count": (ctypes.c_uint64, []),
     "dsgnlm_last_cuda_error": (c_int, []),
     "dsgnlm_strerror": (ctypes.c_char_p, [c_int]),
+    "dsgnlm_is_checked": (c_int, []),
+    "dsgnlm_check_word": (c_int, [ctypes.POINTER(ctypes.c_uint), c_int]),
+    "dsgnlm_check_selftest": (c_int, [ctypes.c_longlong, ctypes.c_longlong]),
 }
 
 _lib = None
+
+
+def default_path() -> str:
+    """The library this process uses: ``$DSGNLM_LIBRARY`` if set (for example the
+    checked build), else ``lib/libdsgnlm.so``."""
+    return os.environ.get("DSGNLM_LIBRARY") or LIB_PATH
 
 
 def load(path: str | None = None):
@@ -94,7 +103,8 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None and path is None:
         return _lib
-    path = path or LIB_PATH
+    default = path is None
+    path = path or default_path()
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build the CUDA library first "
                            "(python -m paper_1901_06110_gb300.build)")
@@ -103,6 +113,6 @@ def load(path: str | None = None):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    if path == LIB_PATH:
+    if default:
         _lib = lib
     return lib

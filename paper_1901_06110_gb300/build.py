@@ -4,7 +4,9 @@ Each translation unit under ``csrc/`` is compiled by nvcc in parallel and linked
 into ``lib/libdsgnlm.so`` (C ABI declared in ``include/dsgnlm.h``).  A build is
 skipped when the library is newer than every source and header.
 
-Usage: ``python -m paper_1901_06110_gb300.build [--force]``.
+Usage: ``python -m paper_1901_06110_gb300.build [--force] [--checked]``.  ``--checked``
+builds ``lib/libdsgnlm_checked.so`` with ``-DDSGNLM_CHECKED`` (index checks that set an
+error word instead of letting an access leave its buffer; see ``dsgnlm_check_word``).
 """
 from __future__ import annotations
 
@@ -21,6 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "lib")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libdsgnlm.so")
+CHECKED_LIB_PATH = os.path.join(OUT_DIR, "libdsgnlm_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", "-Xcompiler", "-pthread",
@@ -46,24 +49,26 @@ def _deps():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB_PATH):
+def up_to_date(lib_path: str = LIB_PATH) -> bool:
+    if not os.path.exists(lib_path):
         return False
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib_path)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Build lib/libdsgnlm.so and return its path."""
-    if not force and up_to_date():
-        return LIB_PATH
+def build(force: bool = False, verbose: bool = False, extra_flags=None, checked: bool = False) -> str:
+    """Build lib/libdsgnlm.so (checked: lib/libdsgnlm_checked.so) and return its path."""
+    lib_path = CHECKED_LIB_PATH if checked else LIB_PATH
+    obj_dir = OBJ_DIR + "_checked" if checked else OBJ_DIR
+    if not force and up_to_date(lib_path):
+        return lib_path
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    os.makedirs(obj_dir, exist_ok=True)
+    flags = NVCC_FLAGS + (["-DDSGNLM_CHECKED"] if checked else []) + list(extra_flags or [])
 
     def compile_one(src):
-        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -75,18 +80,19 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     srcs = _sources()
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB_PATH + ".tmp"
+    tmp = lib_path + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lpthread",
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
     force = "--force" in sys.argv
     verbose = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else None
-    print(build(force=force or bool(extra), verbose=verbose or bool(extra), extra_flags=extra))
+    print(build(force=force or bool(extra), verbose=verbose or bool(extra), extra_flags=extra,
+                checked="--checked" in sys.argv))

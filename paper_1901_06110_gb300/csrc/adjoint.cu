@@ -74,6 +74,7 @@ struct TapeView {
     float *xh, *vh, *uh, *zh, *g, *gs, *dh, *dh0, *base, *thp, *Dhat, *Gp, *AZ;
     float* AZ4;           // (a_2u, a_2u+1, z_2u, z_2u+1) per pixel, u < ceil(N / 2) (pair pass G)
     float* gpart;         // partials of the patch-distance adjoint (the G or the D-hat memory)
+    long long gp_cap, dh0_cap, gpart_cap;  // floats allocated at Gp, dh0, gpart (the checked build's bounds)
     alignas(64) unsigned char bd_kmap[128];  // tensor maps of the weight and G planes for the fused
     alignas(64) unsigned char bd_gmap[128];  // pass B (boxes of the D-hat window)
     alignas(64) unsigned char gt_kmap[128];  // tensor map of the weight planes for pass G (kQH x 32 tiles)
@@ -684,8 +685,9 @@ __global__ void __launch_bounds__(256) adj_boxguide_kernel(const TapeView* __res
     Ac[c0] += own0;
     Ac[c1] += own1;
     __syncthreads();
-    float* out = v.gpart + (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)(AH * AW);
-    for (int idx = tid; idx < AH * AW; idx += 256) out[idx] = Ac[idx];
+    const size_t obase = (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)(AH * AW);
+    if (DSG_IN_RANGE(obase + AH * AW - 1, v.gpart_cap, kChkAdjWindows))
+        for (int idx = tid; idx < AH * AW; idx += 256) v.gpart[obase + idx] = Ac[idx];
 }
 
 // Pair pass B fused with the patch-distance adjoint.  Per tile Q of the extended grid
@@ -943,8 +945,9 @@ __global__ void __launch_bounds__(256, 3)
         Ac[c1] += own1;
     }
     __syncthreads();
-    float* out = v.gpart + (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)(AH * AW);
-    for (int idx = tid; idx < AH * AW; idx += 256) out[idx] = Ac[idx];
+    const size_t obase = (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)(AH * AW);
+    if (DSG_IN_RANGE(obase + AH * AW - 1, v.gpart_cap, kChkAdjWindows))
+        for (int idx = tid; idx < AH * AW; idx += 256) v.gpart[obase + idx] = Ac[idx];
 }
 
 // The window partials of the offset chunks added into chunk 0's (in chunk order), so
@@ -957,6 +960,7 @@ __global__ void __launch_bounds__(256) adj_chunk_sum_kernel(const TapeView* __re
     float* part = which == 0 ? v.gpart : v.dh0;
     const int e = blockIdx.x * 256 + threadIdx.x;
     if (e >= elems) return;
+    if (!DSG_IN_RANGE((size_t)(chunks - 1) * elems + e, which == 0 ? v.gpart_cap : v.dh0_cap, kChkAdjWindows)) return;
     float acc = part[e];
     for (int z = 1; z < chunks; ++z) acc += part[(size_t)z * elems + e];
     part[e] = acc;
@@ -967,7 +971,7 @@ __global__ void __launch_bounds__(256) adj_chunk_sum_kernel(const TapeView* __re
 // tx0 - 1 .. tx0 + 1), chunk by chunk in that order.  The six candidates are tested once
 // and their loads issued together (a candidate that does not hold p adds nothing).
 __device__ __forceinline__ float gather_ge(const float* __restrict__ part, int pi, int pj, int rp, int rs, int tiles_y,
-                                           int tiles_x, int chunks, int qw) {
+                                           int tiles_x, int chunks, int qw, long long cap) {
     const int AH = bg_win_h(rs), AW = qw + 2 * rs;
     const int ty0 = (pi + rp) / kQH, tx0 = (pj + rp) / qw;
     size_t off[6];
@@ -988,7 +992,8 @@ __device__ __forceinline__ float gather_ge(const float* __restrict__ part, int p
         const float* pz = part + (size_t)z * zstride;
         float v[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) v[c] = ok[c] ? pz[off[c]] : 0.f;
+        for (int c = 0; c < 6; ++c)
+            v[c] = (ok[c] && DSG_IN_RANGE((size_t)z * zstride + off[c], cap, kChkAdjWindows)) ? pz[off[c]] : 0.f;
 #pragma unroll
         for (int c = 0; c < 6; ++c)
             if (ok[c]) acc += v[c];
@@ -1020,7 +1025,7 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restric
         rj[nj++] = j;
         if (j >= W - rp) rj[nj++] = 2 * W - 1 - j;
         for (int a = 0; a < ni; ++a)
-            for (int b = 0; b < nj; ++b) acc += gather_ge(v.gpart, ri[a], rj[b], rp, rs, tiles_y, tiles_x, chunks, qw);
+            for (int b = 0; b < nj; ++b) acc += gather_ge(v.gpart, ri[a], rj[b], rp, rs, tiles_y, tiles_x, chunks, qw, v.gpart_cap);
     } else {
         const int my = rp / (2 * H) + 1, mx = rp / (2 * W) + 1;
         for (int m = -my; m <= my; ++m)
@@ -1031,7 +1036,7 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restric
                     for (int cx = 0; cx < 2; ++cx) {
                         const int pj = cx == 0 ? 2 * W * n - 1 - j : 2 * W * n + j;
                         if (pj < -rp || pj >= W + rp) continue;
-                        acc += gather_ge(v.gpart, pi, pj, rp, rs, tiles_y, tiles_x, chunks, qw);
+                        acc += gather_ge(v.gpart, pi, pj, rp, rs, tiles_y, tiles_x, chunks, qw, v.gpart_cap);
                     }
             }
     }
@@ -1194,7 +1199,8 @@ __global__ void __launch_bounds__(256, 2)
                 }
             }
             const float G = acc.x + acc.y;
-            if (in[m]) Gk[(size_t)(y0 + row) * Wp + j] = G;
+            if (in[m] && DSG_IN_RANGE((size_t)k * plane + (size_t)(y0 + row) * Wp + j, v.gp_cap, kChkAdjPlanes))
+                Gk[(size_t)(y0 + row) * Wp + j] = G;
             const float dr = Sd[cr];
             const float GK = G * K;
             accd[m] = fmaf(GK, dr, accd[m]);
@@ -1217,8 +1223,9 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
     for (int m = 0; m < 2; ++m) Ac[cs0 + 8 * m * FW] += accd[m];
     __syncthreads();
-    float* out = v.dh0 + (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)fcells;
-    for (int idx = tid; idx < fcells; idx += 256) out[idx] = Ac[idx];
+    const size_t obase = (((size_t)zc * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * (size_t)fcells;
+    if (DSG_IN_RANGE(obase + fcells - 1, v.dh0_cap, kChkAdjWindows))
+        for (int idx = tid; idx < fcells; idx += 256) v.dh0[obase + idx] = Ac[idx];
 }
 
 // dh(s) = (1/m) dh0(s), dh0 gathered from the window partials of pair pass G (every
@@ -1232,7 +1239,7 @@ __global__ void __launch_bounds__(256) adj_dh_kernel(const TapeView* __restrict_
     const int i = blockIdx.y * 8 + threadIdx.y;
     if (i >= H || j >= W) return;
     const float inv_m = __ldg(v.m + 1);
-    v.dh[(size_t)i * W + j] = gather_ge(v.dh0, i, j, 0, v.rs, tiles_y, tiles_x, chunks, 32) * inv_m;
+    v.dh[(size_t)i * W + j] = gather_ge(v.dh0, i, j, 0, v.rs, tiles_y, tiles_x, chunks, 32, v.dh0_cap) * inv_m;
 }
 
 // the scalar cotangents of every image (m, rho, h) in one array, read back in one copy
@@ -1288,6 +1295,8 @@ bool use_pairs_bd(int T, int rp, int rs, int dtype) {
 }
 
 }  // namespace
+
+DSG_CHECK_WORD_ACCESSOR(check_word_adjoint)
 
 }  // namespace dsg
 
@@ -1426,7 +1435,8 @@ TapeView make_view(const lpnp_tape* tp, const float* x_out, const float* x_bar, 
     v.c = tp->c;
     v.hfac = 2.f * tp->c / tp->h;
     v.taps = tp->taps;
-    v.cv = Cover{den->plan.partials, den->plan.tiles_x, den->plan.tiles_y, den->plan.splits.n, tp->rs};
+    v.cv = Cover{den->plan.partials, den->plan.tiles_x, den->plan.tiles_y, den->plan.splits.n, tp->rs,
+                 den->plan.part_cap};
     v.planes = den->planes.p;
     v.y = tp->y;
     v.guide = tp->guide;
@@ -1478,6 +1488,7 @@ BatchInst p1_inst(const dsgnlm* den, const float* d, const float* z) {
     b.d = d;
     b.z = z;
     b.part = den->plan.partials;
+    b.part_cap = den->plan.part_cap;
     b.done = nullptr;
     return b;
 }
@@ -1755,6 +1766,9 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         lpnp_tape* tp = tapes[i];
         views[i] = make_view(tp, nullptr, x_bar[i], y_bar[i], guide_bar[i]);
         views[i].gpart = fused ? tp->Dhat.as<float>() : tp->Gp.as<float>();
+        views[i].gp_cap = (long long)(tp->Gp.bytes / sizeof(float));
+        views[i].dh0_cap = (long long)(tp->dh0.bytes / sizeof(float));
+        views[i].gpart_cap = (long long)((fused ? tp->Dhat.bytes : tp->Gp.bytes) / sizeof(float));
         {
             const int dt = dens[i]->dtype;
             const int key[4] = {H, W, nh, dt};

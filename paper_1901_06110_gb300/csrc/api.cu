@@ -72,6 +72,24 @@ thread_local int g_last_cuda = 0;
 
 void dsg::record_cuda_error(cudaError_t e) { g_last_cuda = (int)e; }
 
+namespace dsg {
+
+DSG_CHECK_WORD_ACCESSOR(check_word_api)
+
+namespace {
+__global__ void check_selftest_kernel(long long index, long long bound) {
+    (void)DSG_IN_RANGE(index, bound, kChkSelfTest);
+}
+}  // namespace
+
+cudaError_t launch_check_selftest(long long index, long long bound) {
+    check_selftest_kernel<<<1, 1>>>(index, bound);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace dsg
+
 namespace {
 
 dsgnlm_status fail_cuda(cudaError_t e) {
@@ -169,7 +187,8 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
     const double np = 2.0 * patch_r + 1.0;
     const float c = (float)(1.0 / (2.0 * np * np * (double)bandwidth * (double)bandwidth));
     DSG_CK(h->timed(DSGNLM_PROF_BUILD, [&] {
-        return launch_build(h->dtype, guide, H, W, patch_r, search_r, c, h->planes.p, h->stream);
+        return launch_build(h->dtype, guide, H, W, patch_r, search_r, c, h->planes.p,
+                            (long long)(h->planes.bytes / weight_elem_bytes(h->dtype)), h->stream);
     }));
     h->H = H;
     h->W = W;
@@ -196,6 +215,7 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
         pl.splits = make_splits(search_r, slices < 1 ? 1 : slices);
         DSG_CK(h->tma_part.ensure(sizeof(float) * tma_region_floats(search_r) * (size_t)tiles * pl.splits.n));
         pl.partials = h->tma_part.as<float>();
+        pl.part_cap = (long long)(h->tma_part.bytes / sizeof(float));
         DSG_CK(h->err.ensure(sizeof(unsigned)));
         DSG_CK(cudaMemsetAsync(h->err.p, 0, sizeof(unsigned), h->stream));
         h->fast = true;
@@ -477,6 +497,7 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
         const size_t tiles = (size_t)h->plan.tiles_x * h->plan.tiles_y;
         DSG_CK(h->tma_part.ensure(sizeof(float) * tma_region_floats(h->rs) * tiles * splits.n));
         h->plan.partials = h->tma_part.as<float>();  // the buffer may have grown
+        h->plan.part_cap = (long long)(h->tma_part.bytes / sizeof(float));
         for (int par = 0; par < 2; ++par) {
             BatchInst& bi = inst[(size_t)par * count + i];
             bi = BatchInst{};
@@ -488,10 +509,11 @@ dsgnlm_status dsgnlm_balance_batched(dsgnlm_t* hs, int count, double tol, int ma
             bi.d = h->dbuf[par].as<float>();
             bi.z = nullptr;
             bi.part = h->plan.partials;
+            bi.part_cap = h->plan.part_cap;
             bi.done = &h->ctl.as<BalanceCtl>()->done;
         }
         BatchBal& b = bal[i];
-        b.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, splits.n, h->rs};
+        b.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, splits.n, h->rs, h->plan.part_cap};
         b.H = H;
         b.W = W;
         b.nbx = nbx;
@@ -1192,6 +1214,7 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
         const size_t tiles = (size_t)h->plan.tiles_x * h->plan.tiles_y;
         DSG_CK(h->tma_part.ensure(sizeof(float) * tma_region_floats(h->rs) * tiles * splits.n));
         h->plan.partials = h->tma_part.as<float>();  // the buffer may have grown
+        h->plan.part_cap = (long long)(h->tma_part.bytes / sizeof(float));
         std::memcpy(maps.m[i], h->plan.tmap, 128);
         BatchInst& bi = inst[i];
         bi.H = H;
@@ -1202,6 +1225,7 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
         bi.d = h->d_final;
         bi.z = h->z.as<float>();
         bi.part = h->plan.partials;
+        bi.part_cap = h->plan.part_cap;
         for (int sl = 0; sl < bi.splits.n; ++sl)
             for (int ty = 0; ty < bi.tiles_y; ++ty)
                 for (int tx = 0; tx < bi.tiles_x; ++tx) work1.push_back(make_int4(i, ty, tx, sl));
@@ -1230,7 +1254,7 @@ dsgnlm_status batched_impl(const lpnp_problem* probs, int count, float rho, int 
         ea.rho = rho;
         ea.constraint = p->constraint;
         ea.do_x = 1;
-        be.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, splits.n, h->rs};
+        be.cv = Cover{h->plan.partials, h->plan.tiles_x, h->plan.tiles_y, splits.n, h->rs, h->plan.part_cap};
         be.gx = gx;
         be.nblocks = nb;
         be.partials = h->partials.as<double>();
@@ -1464,6 +1488,29 @@ dsgnlm_status dsgnlm_profile_read(dsgnlm_t h, int kind, double* total_ms, int* l
 }
 
 uint64_t dsgnlm_launch_count(void) { return g_launches.load(); }
+
+int dsgnlm_is_checked(void) {
+#ifdef DSGNLM_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+dsgnlm_status dsgnlm_check_word(unsigned* word, int clear) {
+    if (!word) return DSGNLM_EINVAL;
+    DSG_CK(cudaDeviceSynchronize());
+    const bool c = clear != 0;
+    *word = check_word_adjoint(c) | check_word_api(c) | check_word_batched(c) | check_word_build(c) |
+            check_word_epilogue(c) | check_word_stencil_tma(c);
+    return DSGNLM_OK;
+}
+
+dsgnlm_status dsgnlm_check_selftest(long long index, long long bound) {
+    DSG_CK(launch_check_selftest(index, bound));
+    DSG_CK(cudaDeviceSynchronize());
+    return DSGNLM_OK;
+}
 
 int dsgnlm_last_cuda_error(void) { return g_last_cuda; }
 

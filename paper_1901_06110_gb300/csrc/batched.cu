@@ -226,4 +226,6 @@ cudaError_t launch_batched_reduce(const BatchEpi* insts, int count, double* hist
     return cudaGetLastError();
 }
 
+DSG_CHECK_WORD_ACCESSOR(check_word_batched)
+
 }  // namespace dsg

@@ -79,7 +79,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 template <typename WT, int RP, int RS>
 __global__ void __launch_bounds__(kThreads, RP < 0 ? 1 : (RP <= 5 ? 4 : 3))
 build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt, float c2, int chunk,
-             WT* __restrict__ planes) {
+             WT* __restrict__ planes, long long cap) {
     extern __shared__ __align__(16) float smem[];
     const int rp = RP >= 0 ? RP : rp_rt;
     const int rs = RS >= 0 ? RS : rs_rt;
@@ -233,7 +233,8 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
                     if (jj > 0) D += v[jj + 2 * rp] - v[jj - 1];
                     w[jj] = ex2_approx(fmaf(D, -c2, lhat));
                 }
-                store4<WT>(out + (size_t)i * Wp + j0, w);
+                if (DSG_IN_RANGE((size_t)k * plane + (size_t)i * Wp + j0 + kHW - 1, cap, kChkPlanes))
+                    store4<WT>(out + (size_t)i * Wp + j0, w);
             } else {
 #pragma unroll
                 for (int jj = 0; jj < kHW; ++jj) {
@@ -244,7 +245,9 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
                 }
                 // planes have a pitch of a multiple of 8: the 4 outputs are all inside the
                 // row's pitch or all outside it
-                if (i < H && j0 < Wp) store4<WT>(out + (size_t)i * Wp + j0, w);
+                if (i < H && j0 < Wp &&
+                    DSG_IN_RANGE((size_t)k * plane + (size_t)i * Wp + j0 + kHW - 1, cap, kChkPlanes))
+                    store4<WT>(out + (size_t)i * Wp + j0, w);
             }
         }
         oy = oy1;
@@ -255,7 +258,7 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
 }
 
 template <typename WT, int RP, int RS>
-cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, float c, WT* planes,
+cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, float c, WT* planes, long long cap,
                             cudaStream_t st) {
     const int nh = num_half_offsets(rs);
     if (nh == 0) return cudaSuccess;
@@ -287,7 +290,7 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
     }
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, (nh + chunk - 1) / chunk);
     const float c2 = (float)((double)c * 1.4426950408889634);  // c log2 e: the exponent in base 2
-    build_kernel<WT, RP, RS><<<grid, kThreads, smem, st>>>(guide, H, W, rp, rs, c2, chunk, planes);
+    build_kernel<WT, RP, RS><<<grid, kThreads, smem, st>>>(guide, H, W, rp, rs, c2, chunk, planes, cap);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -296,41 +299,44 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
 // 15x15, 21x21) for the patch sizes they use, and the 21x21 window for every patch size
 // of Table 1; other radii take the runtime-radius form.
 template <typename WT, int RP>
-cudaError_t launch_build_rs(const float* guide, int H, int W, int rp, int rs, float c, WT* planes, cudaStream_t st) {
+cudaError_t launch_build_rs(const float* guide, int H, int W, int rp, int rs, float c, WT* planes, long long cap,
+                            cudaStream_t st) {
     if constexpr (RP == 2) {
-        if (rs == 5) return launch_build_rp<WT, RP, 5>(guide, H, W, rp, rs, c, planes, st);
-        if (rs == 7) return launch_build_rp<WT, RP, 7>(guide, H, W, rp, rs, c, planes, st);
+        if (rs == 5) return launch_build_rp<WT, RP, 5>(guide, H, W, rp, rs, c, planes, cap, st);
+        if (rs == 7) return launch_build_rp<WT, RP, 7>(guide, H, W, rp, rs, c, planes, cap, st);
     }
     if constexpr (RP == 3 || RP == 5 || RP == 8 || RP == 11 || RP == 14) {
-        if (rs == 10) return launch_build_rp<WT, RP, 10>(guide, H, W, rp, rs, c, planes, st);
+        if (rs == 10) return launch_build_rp<WT, RP, 10>(guide, H, W, rp, rs, c, planes, cap, st);
     }
-    return launch_build_rp<WT, RP, -1>(guide, H, W, rp, rs, c, planes, st);
+    return launch_build_rp<WT, RP, -1>(guide, H, W, rp, rs, c, planes, cap, st);
 }
 
 template <typename WT>
-cudaError_t launch_build_t(const float* guide, int H, int W, int rp, int rs, float c, WT* planes,
+cudaError_t launch_build_t(const float* guide, int H, int W, int rp, int rs, float c, WT* planes, long long cap,
                            cudaStream_t st) {
     switch (rp) {
-        case 1: return launch_build_rs<WT, 1>(guide, H, W, rp, rs, c, planes, st);
-        case 2: return launch_build_rs<WT, 2>(guide, H, W, rp, rs, c, planes, st);
-        case 3: return launch_build_rs<WT, 3>(guide, H, W, rp, rs, c, planes, st);
-        case 4: return launch_build_rs<WT, 4>(guide, H, W, rp, rs, c, planes, st);
-        case 5: return launch_build_rs<WT, 5>(guide, H, W, rp, rs, c, planes, st);
-        case 8: return launch_build_rs<WT, 8>(guide, H, W, rp, rs, c, planes, st);    // 17 x 17 patches
-        case 11: return launch_build_rs<WT, 11>(guide, H, W, rp, rs, c, planes, st);  // 23 x 23
-        case 14: return launch_build_rs<WT, 14>(guide, H, W, rp, rs, c, planes, st);  // 29 x 29
-        default: return launch_build_rp<WT, -1, -1>(guide, H, W, rp, rs, c, planes, st);
+        case 1: return launch_build_rs<WT, 1>(guide, H, W, rp, rs, c, planes, cap, st);
+        case 2: return launch_build_rs<WT, 2>(guide, H, W, rp, rs, c, planes, cap, st);
+        case 3: return launch_build_rs<WT, 3>(guide, H, W, rp, rs, c, planes, cap, st);
+        case 4: return launch_build_rs<WT, 4>(guide, H, W, rp, rs, c, planes, cap, st);
+        case 5: return launch_build_rs<WT, 5>(guide, H, W, rp, rs, c, planes, cap, st);
+        case 8: return launch_build_rs<WT, 8>(guide, H, W, rp, rs, c, planes, cap, st);    // 17 x 17 patches
+        case 11: return launch_build_rs<WT, 11>(guide, H, W, rp, rs, c, planes, cap, st);  // 23 x 23
+        case 14: return launch_build_rs<WT, 14>(guide, H, W, rp, rs, c, planes, cap, st);  // 29 x 29
+        default: return launch_build_rp<WT, -1, -1>(guide, H, W, rp, rs, c, planes, cap, st);
     }
 }
 
 }  // namespace
 
+DSG_CHECK_WORD_ACCESSOR(check_word_build)
+
 cudaError_t launch_build(int dtype, const float* guide, int H, int W, int patch_r, int search_r,
-                         float c, void* planes, cudaStream_t st) {
+                         float c, void* planes, long long cap, cudaStream_t st) {
     switch (dtype) {
-        case 0: return launch_build_t(guide, H, W, patch_r, search_r, c, (float*)planes, st);
-        case 1: return launch_build_t(guide, H, W, patch_r, search_r, c, (__half*)planes, st);
-        default: return launch_build_t(guide, H, W, patch_r, search_r, c, (__nv_bfloat16*)planes, st);
+        case 0: return launch_build_t(guide, H, W, patch_r, search_r, c, (float*)planes, cap, st);
+        case 1: return launch_build_t(guide, H, W, patch_r, search_r, c, (__half*)planes, cap, st);
+        default: return launch_build_t(guide, H, W, patch_r, search_r, c, (__nv_bfloat16*)planes, cap, st);
     }
 }
 

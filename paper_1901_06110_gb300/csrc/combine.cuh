@@ -45,7 +45,9 @@ __device__ __forceinline__ float gather_partials(const Cover& cv, int i, int j) 
     for (int sl = 0; sl < cv.slices; ++sl, base += slice_stride) {
         float v[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) v[c] = use[c] ? __ldcg(base + off[c]) : 0.f;
+        for (int c = 0; c < 6; ++c)
+            v[c] = (use[c] && DSG_IN_RANGE(sl * slice_stride + off[c], cv.cap, kChkPartials)) ? __ldcg(base + off[c])
+                                                                                                 : 0.f;
 #pragma unroll
         for (int c = 0; c < 6; ++c)
             if (use[c]) acc.add(v[c]);

@@ -8,6 +8,43 @@
 
 namespace dsg {
 
+// Checked build (-DDSGNLM_CHECKED): the index checks below set a bit in a device word
+// and skip the access instead of letting it leave its buffer; the word is read back
+// by dsgnlm_check_word.  Every translation unit has its own word (no relocatable device
+// code), and DSG_CHECK_WORD_ACCESSOR names the host function that reads and clears
+// it.  In the normal build a check is the constant true and costs nothing.
+enum : unsigned {
+    kChkPlanes = 1u,      // a weight-plane store of the build
+    kChkPartials = 2u,    // a phase-1 partial-region read or write
+    kChkPixels = 4u,      // a per-pixel store of an epilogue
+    kChkAdjPlanes = 8u,   // a G-plane store of pair pass G
+    kChkAdjWindows = 16u, // a window-partial read or write of the adjoint
+    kChkSelfTest = 0x80000000u,
+};
+#ifdef DSGNLM_CHECKED
+static __device__ unsigned g_dsg_check_word;
+__device__ __forceinline__ bool dsg_in_range(long long i, long long n, unsigned bit) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&g_dsg_check_word, bit);
+    return false;
+}
+#define DSG_IN_RANGE(i, n, bit) ::dsg::dsg_in_range((long long)(i), (long long)(n), (bit))
+#define DSG_CHECK_WORD_ACCESSOR(name)                                                   \
+    unsigned name(bool clear) {                                                         \
+        unsigned w = 0;                                                                 \
+        if (cudaMemcpyFromSymbol(&w, g_dsg_check_word, sizeof w) != cudaSuccess) w = 0; \
+        if (clear) {                                                                    \
+            const unsigned z = 0;                                                       \
+            cudaMemcpyToSymbol(g_dsg_check_word, &z, sizeof z);                         \
+        }                                                                               \
+        return w;                                                                       \
+    }
+#else
+#define DSG_IN_RANGE(i, n, bit) true
+#define DSG_CHECK_WORD_ACCESSOR(name) \
+    unsigned name(bool) { return 0u; }
+#endif
+
 // Index of the half-window offset o = (oy, ox): first the oy = 0 row with
 // ox = 1..rs, then the rows oy = 1..rs with ox = -rs..rs.  n_h = 2 rs (rs + 1).
 __host__ __device__ __forceinline__ int num_half_offsets(int rs) { return 2 * rs * (rs + 1); }

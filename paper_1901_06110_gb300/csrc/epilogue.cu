@@ -114,7 +114,7 @@ cudaError_t by_slices(int slices, F&& f) {
 }
 
 Cover cover(const TmaPlan& plan, int rs) {
-    return Cover{plan.partials, plan.tiles_x, plan.tiles_y, plan.splits.n, rs};
+    return Cover{plan.partials, plan.tiles_x, plan.tiles_y, plan.splits.n, rs, plan.part_cap};
 }
 
 }  // namespace
@@ -154,5 +154,7 @@ cudaError_t launch_combine_update(int kind, const TmaPlan& plan, int rs, const E
         return cudaGetLastError();
     });
 }
+
+DSG_CHECK_WORD_ACCESSOR(check_word_epilogue)
 
 }  // namespace dsg

@@ -18,6 +18,8 @@ namespace dsg {
 constexpr int kGatherGroup = 4;  // slices whose partial-region loads are issued together
 
 struct TileCover {
+    const float* part0;  // the partial regions (slice 0, tile 0) and the floats allocated there
+    long long cap;
     const float* own;  // region of (ty, tx), slice 0
     size_t region, slice_stride;
     int RW, rs, slices;
@@ -33,6 +35,8 @@ __device__ __forceinline__ TileCover tile_cover(const Cover& cv, int y0, int x0)
     c.region = (size_t)(kTmaTH + cv.rs) * c.RW;
     c.slice_stride = (size_t)cv.tiles_y * cv.tiles_x * c.region;
     c.slices = cv.slices;
+    c.part0 = cv.part;
+    c.cap = cv.cap;
     c.own = cv.part + ((size_t)ty * cv.tiles_x + tx) * c.region;
     c.up_ok = ty > 0;
     c.left_ok = tx > 0;
@@ -41,6 +45,11 @@ __device__ __forceinline__ TileCover tile_cover(const Cover& cv, int y0, int x0)
     c.left_d = -(int)c.region;
     c.right_d = (int)c.region;
     return c;
+}
+
+// One partial-sum load of a gather (checked build: only inside the allocation)
+__device__ __forceinline__ float ld_part(const TileCover& c, const float* p) {
+    return DSG_IN_RANGE(p - c.part0, c.cap, kChkPartials) ? __ldcg(p) : 0.f;
 }
 
 // Stopping rule of the balance (Eq. S2 iterated): stop at max |d t - 1| <= tol, at
@@ -93,12 +102,12 @@ __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj)
     if constexpr (SL > 0) {
 #pragma unroll
         for (int sl = 0; sl < SL; ++sl, base += c.slice_stride) {
-            const float v0 = __ldcg(base + own_cell);
-            const float v1 = up ? __ldcg(base + c.up_d + up_cell) : 0.f;
-            const float v2 = left ? __ldcg(base + c.left_d + own_cell + kTmaTW) : 0.f;
-            const float v3 = (left && up) ? __ldcg(base + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
-            const float v4 = right ? __ldcg(base + c.right_d + own_cell - kTmaTW) : 0.f;
-            const float v5 = (right && up) ? __ldcg(base + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
+            const float v0 = ld_part(c, base + own_cell);
+            const float v1 = up ? ld_part(c, base + c.up_d + up_cell) : 0.f;
+            const float v2 = left ? ld_part(c, base + c.left_d + own_cell + kTmaTW) : 0.f;
+            const float v3 = (left && up) ? ld_part(c, base + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
+            const float v4 = right ? ld_part(c, base + c.right_d + own_cell - kTmaTW) : 0.f;
+            const float v5 = (right && up) ? ld_part(c, base + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
             acc += v0;
             acc += v1;
             acc += v2;
@@ -121,12 +130,12 @@ __device__ __forceinline__ float tile_gather(const TileCover& c, int li, int lj)
             for (int k = 0; k < kGatherGroup; ++k) {
                 const bool ok = s0 + k < c.slices;
                 const float* b = base + (ok ? (size_t)(s0 + k) * c.slice_stride : 0);
-                v[k][0] = ok ? __ldcg(b + own_cell) : 0.f;
-                v[k][1] = (ok && up) ? __ldcg(b + c.up_d + up_cell) : 0.f;
-                v[k][2] = (ok && left) ? __ldcg(b + c.left_d + own_cell + kTmaTW) : 0.f;
-                v[k][3] = (ok && left && up) ? __ldcg(b + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
-                v[k][4] = (ok && right) ? __ldcg(b + c.right_d + own_cell - kTmaTW) : 0.f;
-                v[k][5] = (ok && right && up) ? __ldcg(b + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
+                v[k][0] = ok ? ld_part(c, b + own_cell) : 0.f;
+                v[k][1] = (ok && up) ? ld_part(c, b + c.up_d + up_cell) : 0.f;
+                v[k][2] = (ok && left) ? ld_part(c, b + c.left_d + own_cell + kTmaTW) : 0.f;
+                v[k][3] = (ok && left && up) ? ld_part(c, b + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
+                v[k][4] = (ok && right) ? ld_part(c, b + c.right_d + own_cell - kTmaTW) : 0.f;
+                v[k][5] = (ok && right && up) ? ld_part(c, b + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
             }
 #pragma unroll
             for (int k = 0; k < kGatherGroup; ++k) {
@@ -178,12 +187,12 @@ __device__ __forceinline__ float tile_gather_comp(const TileCover& c, int li, in
         for (int k = 0; k < kG; ++k) {
             const bool ok = s0 + k < ns;
             const float* b = base + (ok ? (size_t)(s0 + k) * c.slice_stride : 0);
-            v[k][0] = (ok && up && left) ? __ldcg(b + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
-            v[k][1] = (ok && up) ? __ldcg(b + c.up_d + up_cell) : 0.f;
-            v[k][2] = (ok && up && right) ? __ldcg(b + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
-            v[k][3] = (ok && left) ? __ldcg(b + c.left_d + own_cell + kTmaTW) : 0.f;
-            v[k][4] = ok ? __ldcg(b + own_cell) : 0.f;
-            v[k][5] = (ok && right) ? __ldcg(b + c.right_d + own_cell - kTmaTW) : 0.f;
+            v[k][0] = (ok && up && left) ? ld_part(c, b + c.up_d + c.left_d + up_cell + kTmaTW) : 0.f;
+            v[k][1] = (ok && up) ? ld_part(c, b + c.up_d + up_cell) : 0.f;
+            v[k][2] = (ok && up && right) ? ld_part(c, b + c.up_d + c.right_d + up_cell - kTmaTW) : 0.f;
+            v[k][3] = (ok && left) ? ld_part(c, b + c.left_d + own_cell + kTmaTW) : 0.f;
+            v[k][4] = ok ? ld_part(c, b + own_cell) : 0.f;
+            v[k][5] = (ok && right) ? ld_part(c, b + c.right_d + own_cell - kTmaTW) : 0.f;
         }
 #pragma unroll
         for (int k = 0; k < kG; ++k) {

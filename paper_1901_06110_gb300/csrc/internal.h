@@ -22,6 +22,14 @@ struct NvtxRange {
 // into a graph are counted each time the graph is launched
 void set_capture_counting(bool recording);
 uint64_t recorded_launches();  // launches counted while recording, since set_capture_counting(true)
+// the checked build's per-translation-unit index-check words (0 in the normal build)
+unsigned check_word_adjoint(bool clear);
+unsigned check_word_api(bool clear);
+unsigned check_word_batched(bool clear);
+unsigned check_word_build(bool clear);
+unsigned check_word_epilogue(bool clear);
+unsigned check_word_stencil_tma(bool clear);
+cudaError_t launch_check_selftest(long long index, long long bound);
 // makes `e` the value dsgnlm_last_cuda_error() returns in this thread
 void record_cuda_error(cudaError_t e);
 
@@ -68,7 +76,7 @@ struct SolveRed {
 __host__ __device__ inline int plane_pitch(int W) { return (W + 7) & ~7; }
 
 cudaError_t launch_build(int dtype, const float* guide, int H, int W, int patch_r, int search_r,
-                         float inv_two_np2_h2, void* planes, cudaStream_t st);
+                         float inv_two_np2_h2, void* planes, long long cap, cudaStream_t st);  // cap: weights allocated
 
 // TMA stencil path (search radii with a compiled kernel)
 constexpr int kMaxSlices = 25;
@@ -80,12 +88,14 @@ struct TmaSplits {
 struct Cover {  // where a pixel's phase-1 partial sums live
     const float* part;
     int tiles_x, tiles_y, slices, rs;
+    long long cap;  // floats allocated at part (the checked build's bound)
 };
 struct TmaPlan {
     alignas(64) unsigned char tmap[128];  // CUtensorMap of the planes
     int tiles_x, tiles_y;
     TmaSplits splits;
     float* partials;  // [slices][tiles_y][tiles_x][region]
+    long long part_cap;  // floats allocated at partials
 };
 // Batched phase 1: every instance's tensor map travels in the kernel parameters.
 constexpr int kMaxBatch = 96;
@@ -101,6 +111,7 @@ struct BatchInst {  // per-instance data of a batched launch (device memory)
     const float* z;   // second factor of q (null: q = d)
     float* part;      // partial regions of this instance
     const int* done;  // null, or a flag that, when set, makes the instance's items return
+    long long part_cap;  // floats allocated at part (the checked build's bound)
 };
 cudaError_t launch_tma_gather_batched(int dtype, int rs, const BatchMaps& maps, const BatchInst* insts,
                                       const int4* work, int nwork, unsigned* err, cudaStream_t st);

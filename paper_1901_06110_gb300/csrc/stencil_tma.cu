@@ -312,12 +312,14 @@ template <int RS, typename WT>
 __global__ void __launch_bounds__(kThreads, P1Traits<WT>::kMinBlocks)
 stencil_p1_kernel(const __grid_constant__ CUtensorMap tmap, int H, int W, const float* __restrict__ d,
                   const float* __restrict__ z, TmaSplits splits, float* __restrict__ part,
-                  unsigned* __restrict__ err, const int* __restrict__ skip, long long cbudget) {
+                  unsigned* __restrict__ err, const int* __restrict__ skip, long long cbudget, long long cap) {
     griddep_enter();
     if (skip && *(volatile const int*)skip) return;
     const int slice = blockIdx.z;
     const size_t region = (size_t)(kTH + RS) * (kTW + 2 * RS);
-    float* out = part + ((size_t)(slice * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * region;
+    const size_t roff = ((size_t)(slice * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * region;
+    if (!DSG_IN_RANGE(roff + region - 1, cap, kChkPartials)) return;  // before any copy is issued
+    float* out = part + roff;
     p1_body<RS, WT>(&tmap, H, W, d, z, splits.ox_lo[slice], splits.ox_hi[slice], blockIdx.x * kTW,
                     blockIdx.y * kTH, out, err, cbudget);
 }
@@ -332,7 +334,9 @@ stencil_p1_batched_kernel(const __grid_constant__ BatchMaps maps, const BatchIns
     const BatchInst& in = insts[w.x];
     if (in.done && *(volatile const int*)in.done) return;
     const size_t region = (size_t)(kTH + RS) * (kTW + 2 * RS);
-    float* out = in.part + ((size_t)(w.w * in.tiles_y + w.y) * in.tiles_x + w.z) * region;
+    const size_t roff = ((size_t)(w.w * in.tiles_y + w.y) * in.tiles_x + w.z) * region;
+    if (!DSG_IN_RANGE(roff + region - 1, in.part_cap, kChkPartials)) return;  // before any copy is issued
+    float* out = in.part + roff;
     p1_body<RS, WT>(reinterpret_cast<const CUtensorMap*>(maps.m[w.x]), in.H, in.W, in.d, in.z, in.splits.ox_lo[w.w], in.splits.ox_hi[w.w],
                     w.z * kTW, w.y * kTH, out, err, kWaitBudget);
 }
@@ -403,9 +407,10 @@ cudaError_t p1_launch(const TmaPlan& plan, int H, int W, const float* d, const f
     count_launches(1);
     if (pdl)
         return launch_pdl(stencil_p1_kernel<RS, WT>, grid, dim3(kThreads), smem, st, *(const CUtensorMap*)plan.tmap, H,
-                          W, d, z, plan.splits, plan.partials, err, skip, cbudget);
+                          W, d, z, plan.splits, plan.partials, err, skip, cbudget, plan.part_cap);
     stencil_p1_kernel<RS, WT><<<grid, kThreads, smem, st>>>(*(const CUtensorMap*)plan.tmap, H, W, d, z,
-                                                            plan.splits, plan.partials, err, skip, cbudget);
+                                                            plan.splits, plan.partials, err, skip, cbudget,
+                                                            plan.part_cap);
     return cudaGetLastError();
 }
 
@@ -462,12 +467,14 @@ cudaError_t p1_dispatch(int rs, const TmaPlan& plan, int H, int W, const float* 
 }
 
 Cover cover_of(const TmaPlan& plan, int rs) {
-    return Cover{plan.partials, plan.tiles_x, plan.tiles_y, plan.splits.n, rs};
+    return Cover{plan.partials, plan.tiles_x, plan.tiles_y, plan.splits.n, rs, plan.part_cap};
 }
 
 dim3 p2_grid(int H, int W) { return dim3((W + 31) / 32, (H + 7) / 8); }
 
 }  // namespace
+
+DSG_CHECK_WORD_ACCESSOR(check_word_stencil_tma)
 
 bool tma_path_supports(int rs) {
     return rs == 1 || rs == 2 || rs == 3 || rs == 4 || rs == 5 || rs == 6 || rs == 7 || rs == 8 || rs == 10 ||

@@ -377,3 +377,20 @@ def lpnp_solve_batched(problems, rho: float, iters: int, residuals: bool = False
 
 def dsgnlm_launch_count() -> int:
     return int(_abi.load().dsgnlm_launch_count())
+
+
+def dsgnlm_is_checked() -> bool:
+    """True when the loaded library is the checked build (-DDSGNLM_CHECKED)."""
+    return bool(_abi.load().dsgnlm_is_checked())
+
+
+def dsgnlm_check_word(clear: bool = False) -> int:
+    """The checked build's index-check word (0: no access left its buffer)."""
+    w = ctypes.c_uint(0)
+    _check(_abi.load().dsgnlm_check_word(ctypes.byref(w), int(bool(clear))), "dsgnlm_check_word")
+    return int(w.value)
+
+
+def dsgnlm_check_selftest(index: int, bound: int) -> None:
+    """Run the checked build's index test once on (index, bound), touching no buffer."""
+    _check(_abi.load().dsgnlm_check_selftest(int(index), int(bound)), "dsgnlm_check_selftest")

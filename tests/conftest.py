@@ -34,3 +34,15 @@ def gpu_lib():
     from paper_1901_06110_gb300 import _abi, build
     build.build()
     return _abi.load()
+
+
+@pytest.fixture(autouse=True)
+def _clean_check_word(request):
+    """Under the checked build (the parity tests rerun by test_gpu_checked.py, with
+    DSGNLM_REQUIRE_CLEAN_CHECK set), every GPU test must leave the index-check word at 0:
+    no gather or scattered write of the library left its buffer."""
+    yield
+    if os.environ.get("DSGNLM_REQUIRE_CLEAN_CHECK") and "gpu" in request.keywords:
+        from paper_1901_06110_gb300 import dsgnlm as D
+        word = D.dsgnlm_check_word(clear=True)
+        assert word == 0, f"checked build: index-check word {word:#x} after {request.node.nodeid}"

@@ -375,13 +375,15 @@ void lpnp_tape_destroy(lpnp_tape_t t);
  *   from x = v = clip(guide, 0, 1), u = 0.
  * y device [H/2][W/2]; guide device [H][W]; both must stay unchanged until
  * lpnp_backward.  x_out device [H][W] receives x_N.  Records the tape (replacing any
- * earlier recording).  `den` must not be rebuilt before the backward.  The shared memory of the backward limits (2 iters + 1)(16 + N_s)(32 + 2 N_s)
- * and (2 passes + 1)(16 + N_s)(32 + 2 N_s) floats to 220 KiB (EINVAL otherwise).
- * m and 1/m are formed and read on the device, so the call queues all of its work
- * without waiting for the device (on an error it drains the stream first); the
- * handle reads m and 1/m back when a later call on it needs them on the host.  The
- * iterations run their own kernels (the x-update of each writes the next recorded
- * state), not lpnp_solve's graph. */
+ * earlier recording).  `den` must not be rebuilt before the backward.  The shared
+ * memory of the backward limits (4 ceil(iters / 2) + 2)(16 + N_s)(32 + 2 N_s) floats
+ * (pair pass G) and (2 passes + 1)(16 + N_s)(32 + 2 N_s) floats to 220 KiB (EINVAL
+ * otherwise).  m and 1/m are formed and read on the device, so the call queues all of
+ * its work without waiting for the device (on an error it drains the stream first);
+ * the handle reads m and 1/m back when a later call on it needs them on the host.
+ * The iterations run their own kernels (the x-update of each writes the next recorded
+ * state); the steps after the weight build are recorded once per configuration as a
+ * CUDA graph and replayed. */
 dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tape, dsgnlm_t den, const float* y, const float* guide, int H,
                                     int W, int patch_r, int search_r, float bandwidth, int balance_passes,
                                     float alpha, float rho, int iters, float blur_sigma, int blur_r, float* x_out);

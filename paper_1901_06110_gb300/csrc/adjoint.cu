@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
     }
     const int t = threadIdx.y * 32 + threadIdx.x;
     const double acc = block_sum_256(r, t);
-    if (t == 0) v.rho_part[blockIdx.y * gridDim.x + blockIdx.x] += acc;  // fixed slot per block, fixed order over iterations
+    // a fixed slot per block, accumulated in a fixed order over the iterations
+    if (t == 0) v.rho_part[blockIdx.y * gridDim.x + blockIdx.x] += acc;
 }
 
 // Reverse iteration k, after g: ata = A^T A g on 32 x 32 tiles, then per pixel
@@ -452,7 +453,8 @@ __global__ void adj_mterms_kernel(const TapeView* __restrict__ tv) {
         const bool fwd = oy > 0 || (oy == 0 && ox > 0);
         const int ay = fwd ? oy : -oy, ax = fwd ? ox : -ox;
         const int k = ay == 0 ? ax - 1 : rs + (ay - 1) * (2 * rs + 1) + ax + rs;
-        const float K = to_f32(fwd ? P[(size_t)k * plane + (size_t)si * Wp + sj] : P[(size_t)k * plane + (size_t)ri * Wp + rj]);
+        const size_t at = (size_t)k * plane + (fwd ? (size_t)si * Wp + sj : (size_t)ri * Wp + rj);
+        const float K = to_f32(P[at]);
         dh[(size_t)ri * W + rj] += mh * d[ss] * K;
     }
 }
@@ -1025,7 +1027,8 @@ __global__ void __launch_bounds__(256) adj_fold_kernel(const TapeView* __restric
         rj[nj++] = j;
         if (j >= W - rp) rj[nj++] = 2 * W - 1 - j;
         for (int a = 0; a < ni; ++a)
-            for (int b = 0; b < nj; ++b) acc += gather_ge(v.gpart, ri[a], rj[b], rp, rs, tiles_y, tiles_x, chunks, qw, v.gpart_cap);
+            for (int b = 0; b < nj; ++b)
+                acc += gather_ge(v.gpart, ri[a], rj[b], rp, rs, tiles_y, tiles_x, chunks, qw, v.gpart_cap);
     } else {
         const int my = rp / (2 * H) + 1, mx = rp / (2 * W) + 1;
         for (int m = -my; m <= my; ++m)
@@ -1805,7 +1808,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
             std::memcpy(views[i].bd_gmap, tp->bd_gmap, 128);
         }
         const float* dT = tp->Dh.as<float>() + (size_t)T * n;
-        for (int k = 0; k < N; ++k) insts[(size_t)k * count + i] = p1_inst(dens[i], dT, tp->AZ.as<float>() + (size_t)k * n);
+        for (int k = 0; k < N; ++k)
+            insts[(size_t)k * count + i] = p1_inst(dens[i], dT, tp->AZ.as<float>() + (size_t)k * n);
         for (int p = 0; p < T; ++p)
             insts[(size_t)(N + p) * count + i] = p1_inst(dens[i], tp->thp.as<float>() + (size_t)p * n, nullptr);
     }
@@ -1839,8 +1843,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
             // In the last iteration a = vh - uh = 0, so W a = 0 needs no weight stream.
             const int a_zero = k == N - 1;
             if (!a_zero)
-                TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)k * count, tb.work, tb.nwork, err,
-                                                  st));
+                TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)k * count, tb.work,
+                                                  tb.nwork, err, st));
             TAPE_CK(pdl(adj_wa_g_kernel, wgrid, dim3(32, 8), 0, st, tb.views, k, a_zero));
             count_launches(1);
             TAPE_CK(cudaGetLastError());
@@ -1877,7 +1881,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
             if (e != cudaSuccess) return e;
             {
                 const int elems = pgx * pgy * (kQH + rs) * (32 + 2 * rs);
-                PDL_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st, tb.views, 1, elems,
+                PDL_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st,
+                    tb.views, 1, elems,
                            kPairSplit));
             }
             PDL_CK(pdl(adj_dh_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, pgy, pgx, 1));
@@ -1890,7 +1895,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         auto pairs_b = [&](auto wt) -> cudaError_t {
             using WT = decltype(wt);
             const size_t smem = pairs_b_smem(T, rs);
-            cudaError_t e = cudaFuncSetAttribute(adj_pairs_b_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e =
+                cudaFuncSetAttribute(adj_pairs_b_kernel<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             PDL_CK(pdl(adj_pairs_b_kernel<WT>, dim3(pgx, pgy, kPairSplit * count), dim3(32, 8), smem, st, tb.views));
             count_launches(1);
@@ -1911,8 +1917,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
             TAPE_CK(cudaGetLastError());
         }
         for (int p = T - 1; p >= 1; --p) {
-            TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)(N + p) * count, tb.work, tb.nwork, err,
-                                              st));
+            TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)(N + p) * count, tb.work,
+                                              tb.nwork, err, st));
             TAPE_CK(pdl(adj_sk_finish_pre_kernel, pgrid2, dim3(32, 8), 0, st, tb.views, p));
             count_launches(1);
             TAPE_CK(cudaGetLastError());
@@ -1925,8 +1931,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
                 auto run = [&](auto kern) -> cudaError_t {
                     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                     if (e != cudaSuccess) return e;
-                    return pdl(kern, dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), smem, st, tb.views, bg_chunks, err,
-                               kDefaultWaitBudget);
+                    return pdl(kern, dim3(bg_tx, bg_ty, bg_chunks * count), dim3(32, 8), smem, st, tb.views,
+                               bg_chunks, err, kDefaultWaitBudget);
                 };
                 if (rp == 2 && rs == 7 && T == 4) return run(adj_pairs_bd_kernel<WT, 2, 7, 4>);
                 switch (rp) {
@@ -1943,7 +1949,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
             count_launches(1);
             {
                 const int elems = bg_tx * bg_ty * bg_win_h(rs) * (bg_qw + 2 * rs);
-                TAPE_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st, tb.views, 0, elems,
+                TAPE_CK(pdl(adj_chunk_sum_kernel, dim3((elems + 255) / 256, 1, count), dim3(256), 0, st,
+                    tb.views, 0, elems,
                             bg_chunks));
             }
             TAPE_CK(pdl(adj_fold_kernel, dim3(pgrid2), dim3(32, 8), 0, st, tb.views, bg_ty, bg_tx, 1, bg_qw));
@@ -1984,7 +1991,8 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
                     lead->scal.as<double>()));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
-        TAPE_CK(cudaMemcpyAsync(lead->hs, lead->scal.p, sizeof(double) * 3 * (size_t)count, cudaMemcpyDeviceToHost, st));
+        TAPE_CK(cudaMemcpyAsync(lead->hs, lead->scal.p, sizeof(double) * 3 * (size_t)count, cudaMemcpyDeviceToHost,
+                                st));
         TAPE_CK(cudaMemcpyAsync(err_host, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         return DSGNLM_OK;
     };

@@ -970,7 +970,8 @@ dsgnlm_status solve_impl(const lpnp_problem* p, float rho, int iters, const Adap
                     g_capturing = true;
                     cudaError_t e1 = first_update(h->cap_stream);
                     for (int it = 0; it < iters && e1 == cudaSuccess; ++it) e1 = iteration(it, h->cap_stream);
-                    if (e1 == cudaSuccess && want_hist) e1 = launch_reduce_residuals(red, iters, nblocks, h->cap_stream);
+                    if (e1 == cudaSuccess && want_hist)
+                        e1 = launch_reduce_residuals(red, iters, nblocks, h->cap_stream);
                     g_capturing = false;
                     cudaGraph_t g = nullptr;
                     e = cudaStreamEndCapture(h->cap_stream, &g);

@@ -274,7 +274,8 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
     int per_sm = 0, dev = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_kernel<WT, RP, RS>, kThreads, smem) !=
             cudaSuccess ||
-        cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return cudaGetLastError();
     const long long slots = per_sm * sms > 0 ? (long long)per_sm * sms : 1;
     const long long tiles = (long long)((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);

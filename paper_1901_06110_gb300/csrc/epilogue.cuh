@@ -54,7 +54,8 @@ __device__ __forceinline__ float ld_part(const TileCover& c, const float* p) {
 
 // Stopping rule of the balance (Eq. S2 iterated): stop at max |d t - 1| <= tol, at
 // maxit (not converged), or when three passes bring no 1% improvement (stalled).
-__device__ __forceinline__ void balance_decide(BalanceCtl* ctl, float e, float m, cudaGraphConditionalHandle cond, int use_cond) {
+__device__ __forceinline__ void balance_decide(BalanceCtl* ctl, float e, float m, cudaGraphConditionalHandle cond,
+                                               int use_cond) {
     const int pass = ctl->pass;
     const double ed = (double)e;
     ctl->eps = ed;

@@ -337,8 +337,8 @@ stencil_p1_batched_kernel(const __grid_constant__ BatchMaps maps, const BatchIns
     const size_t roff = ((size_t)(w.w * in.tiles_y + w.y) * in.tiles_x + w.z) * region;
     if (!DSG_IN_RANGE(roff + region - 1, in.part_cap, kChkPartials)) return;  // before any copy is issued
     float* out = in.part + roff;
-    p1_body<RS, WT>(reinterpret_cast<const CUtensorMap*>(maps.m[w.x]), in.H, in.W, in.d, in.z, in.splits.ox_lo[w.w], in.splits.ox_hi[w.w],
-                    w.z * kTW, w.y * kTH, out, err, kWaitBudget);
+    p1_body<RS, WT>(reinterpret_cast<const CUtensorMap*>(maps.m[w.x]), in.H, in.W, in.d, in.z, in.splits.ox_lo[w.w],
+                    in.splits.ox_hi[w.w], w.z * kTW, w.y * kTH, out, err, kWaitBudget);
 }
 
 // --------------------------------------------------------------------------- phase 2

@@ -50,7 +50,7 @@ namespace {
 
 constexpr int kAdjTH = 16, kAdjTW = 32;  // pair-pass tiles, block (32, 8), 2 rows per thread
 constexpr int kMaxHalfOffsets = 2 * 12 * 13;  // n_h at the largest search radius (12)
-constexpr int kPairSplit = 4;  // pair passes G and B: the half offsets in this many chunks (grid z)
+constexpr int kPairSplit = 2;  // pair passes G and B: the half offsets in this many chunks (grid z)
 
 // Everything the kernels of one image read: sizes, scalars and device buffers of its
 // tape and handle, and the caller's inputs and outputs of the current call.

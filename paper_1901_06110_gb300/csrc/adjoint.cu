@@ -9,7 +9,7 @@
 //   and the gradient grad f(x_k) each x-update used.
 //
 // Backward, for the cotangent of x_N:
-//   iteration k (reverse): a = vh - uh, zh = W a + uh (W is symmetric),
+//   iteration k (reverse): a = vh - uh, zh = W a + uh (W is symmetric; zh is not stored),
 //     g = Pi_C'(xbar_k) (xh + zh),  xh <- mu (alpha g - A^T A g),  vh <- mu rho g,
 //     uh <- zh - mu rho g,  yh += mu A g (summed as A applied to sum mu g),
 //     rhoh += sum g mu ((v_k - u_k) - xbar_k);
@@ -71,7 +71,7 @@ struct TapeView {
     float* m;             // m and 1/m
     unsigned long long* mkey;
     int* sstar;           // first maximiser of d t
-    float *xh, *vh, *uh, *zh, *g, *gs, *dh, *dh0, *base, *thp, *Dhat, *Gp, *AZ;
+    float *xh, *vh, *uh, *g, *gs, *dh, *dh0, *base, *thp, *Dhat, *Gp, *AZ;
     float* AZ4;           // (a_2u, a_2u+1, z_2u, z_2u+1) per pixel, u < ceil(N / 2) (pair pass G)
     float* gpart;         // partials of the patch-distance adjoint (the G or the D-hat memory)
     long long gp_cap, dh0_cap, gpart_cap;  // floats allocated at Gp, dh0, gpart (the checked build's bounds)
@@ -287,8 +287,9 @@ __global__ void __launch_bounds__(256) adj_bwd_prep_kernel(const TapeView* __res
 }
 
 // W a finished from the phase-1 partial sums (W a = c_s a_s + (d_s / m) sum_r K1 d_r a_r,
-// the closure of Eq. S3), then zh = W a + uh, g = Pi_C'(xbar_k)(xh + zh) and the block's
-// partial of sum g mu ((v - u) - xbar).  Blocks of 32 x 8 threads, 16 x 32 pixels.
+// the closure of Eq. S3), then zh = W a + uh, g = Pi_C'(xbar_k)(xh + zh), the block's
+// partial of sum g mu ((v - u) - xbar), and the per-pixel cotangent updates (vh, uh, gs
+// and the earlier iteration's inputs a and z).  Blocks of 32 x 8 threads, 16 x 32 pixels.
 // a_zero: a = 0 (no weight stream ran; W a = 0).
 __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restrict__ tv, int k, int a_zero) {
     griddep_enter();
@@ -302,9 +303,13 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
     const float* t_fin = v.Th + (size_t)v.T * n;
     const float *ak = v.AZ + (size_t)k * n, *vk = v.V + (size_t)k * n, *uk = v.U + (size_t)k * n;
     const float *xk = v.X + (size_t)k * n, *gk = v.Gr + (size_t)k * n;
+    const bool more = k > 0;
+    const float* uprev = more ? v.U + (size_t)(k - 1) * n : uk;
+    float* a_next = more ? v.AZ + (size_t)(k - 1) * n : nullptr;
+    float* s4 = more ? v.AZ4 + 4 * (size_t)((k - 1) >> 1) * n + ((k - 1) & 1) : nullptr;  // lane of iteration k - 1
     // the thread's two pixels, rows i and i + 8 of the block's 16 x 32 tile: every load of
     // both is issued before the first use
-    float ds[2], ts[2], as[2], uhs[2], vs[2], us[2], xs[2], grs[2], xhs[2], A[2];
+    float ds[2], ts[2], as[2], uhs[2], vs[2], us[2], xs[2], grs[2], xhs[2], gss[2], ups[2], A[2];
     bool ok[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
@@ -320,6 +325,8 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
         xs[c] = xk[q];
         grs[c] = gk[q];
         xhs[c] = v.xh[q];
+        gss[c] = v.gs[q];
+        ups[c] = uprev[q];
         A[c] = (a_zero || !ok[c]) ? 0.f : gather_partials(v.cv, i, j);
     }
     float r = 0.f;
@@ -335,8 +342,20 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
         const float xb = mu * (alpha * xs[c] + rho * vu - grs[c]);
         const float gg = proj_deriv(xb, v.constraint) * (xhs[c] + zz);
         v.g[q] = gg;
-        v.zh[q] = zz;
         r += gg * mu * (vu - xb);
+        // the cotangent updates that need no neighbours: vh = mu rho g, uh = zh - mu rho g,
+        // gs += mu g, and for k > 0 the earlier iteration's a = vh - uh and z = x_k + u_{k-1}
+        const float vv = mu * rho * gg;
+        const float uu = zz - vv;
+        v.vh[q] = vv;
+        v.uh[q] = uu;
+        v.gs[q] = gss[c] + mu * gg;
+        if (more) {
+            const float an = vv - uu;
+            a_next[q] = an;
+            s4[4 * q] = an;
+            s4[4 * q + 2] = xs[c] + ups[c];
+        }
     }
     const int t = threadIdx.y * 32 + threadIdx.x;
     const double acc = block_sum_256(r, t);
@@ -344,63 +363,29 @@ __global__ void __launch_bounds__(256) adj_wa_g_kernel(const TapeView* __restric
     if (t == 0) v.rho_part[blockIdx.y * gridDim.x + blockIdx.x] += acc;
 }
 
-// Reverse iteration k, after g: ata = A^T A g on 32 x 32 tiles, then per pixel
-//   xh = mu (alpha g - ata), vh = mu rho g, uh = zh - mu rho g, gs += mu g (the
-//   observation's cotangent is A gs, A being linear), and for k > 0 the inputs of the
-//   earlier iteration: a_{k-1} = vh - uh, z_{k-1} = x_k + u_{k-1} (a in its plane, a and
-//   z in the interleaved copy).
+// Reverse iteration k, after g: xh = mu (alpha g - A^T A g), the A^T A g on 32 x 32 tiles.
+// It is the only step of the iteration that needs neighbouring pixels, so it runs beside
+// the weight stream of the earlier iteration's a (which the W a finish forms per pixel).
 // g is only read, so the halo reads do not race with the writes.
 template <int R>
 __global__ void __launch_bounds__(256, 4) adj_ata_update_kernel(const TapeView* __restrict__ tv, int k) {
     griddep_enter();
     __shared__ GradSmem<R> sm;
     const TapeView& v = tv[blockIdx.z];
-    const int H = v.H, W = v.W;
-    const size_t n = (size_t)H * W;
+    const int W = v.W;
     const float* g = v.g;
-    const float* zh = v.zh;
-    float *xh = v.xh, *vh = v.vh, *uh = v.uh, *gs = v.gs;
-    const float mu = v.mu, alpha = v.alpha, rho = v.rho;
-    const bool more = k > 0;
-    const float* xk = v.X + (size_t)k * n;
-    const float* uprev = more ? v.U + (size_t)(k - 1) * n : nullptr;
-    float* a_next = more ? v.AZ + (size_t)(k - 1) * n : nullptr;
-    float* s4 = more ? v.AZ4 + 4 * (size_t)((k - 1) >> 1) * n + ((k - 1) & 1) : nullptr;  // lane of iteration k - 1
-    // the epilogue pixels' inputs, loaded before the stencil (pixel pairs: q even)
-    float2 gp[2], zp[2], sp[2], xp[2], upv[2];
+    float* xh = v.xh;
+    const float mu = v.mu, alpha = v.alpha;
+    float2 gp[2];  // the epilogue pixels' g, loaded before the stencil (pixel pairs: q even)
     sr_grad_tile_apply2<R>(
-        sm, g, nullptr, H, W, v.taps, blockIdx.y * kGT, blockIdx.x * kGT,
-        [&](int sl, int pi, int pj) {
-            const size_t q = (size_t)pi * W + pj;
-            gp[sl] = *reinterpret_cast<const float2*>(g + q);
-            zp[sl] = *reinterpret_cast<const float2*>(zh + q);
-            sp[sl] = *reinterpret_cast<const float2*>(gs + q);
-            if (more) {
-                xp[sl] = *reinterpret_cast<const float2*>(xk + q);
-                upv[sl] = *reinterpret_cast<const float2*>(uprev + q);
-            }
-        },
+        sm, g, nullptr, v.H, W, v.taps, blockIdx.y * kGT, blockIdx.x * kGT,
+        [&](int sl, int pi, int pj) { gp[sl] = *reinterpret_cast<const float2*>(g + (size_t)pi * W + pj); },
         [&](int sl, int pi, int pj, float e, float o) {
             const size_t q = (size_t)pi * W + pj;
-            const float ata[2] = {e, o}, g2[2] = {gp[sl].x, gp[sl].y}, z2[2] = {zp[sl].x, zp[sl].y},
-                        s2[2] = {sp[sl].x, sp[sl].y};
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const float gg = g2[c];
-                const float vv = mu * rho * gg;
-                const float uu = z2[c] - vv;
-                xh[q + c] = mu * (alpha * gg - ata[c]);
-                vh[q + c] = vv;
-                uh[q + c] = uu;
-                gs[q + c] = s2[c] + mu * gg;
-                if (more) {
-                    const float an = vv - uu;
-                    a_next[q + c] = an;
-                    s4[4 * (q + c)] = an;
-                    s4[4 * (q + c) + 2] = (c == 0 ? xp[sl].x : xp[sl].y) + (c == 0 ? upv[sl].x : upv[sl].y);
-                }
-            }
+            xh[q] = mu * (alpha * gp[sl].x - e);
+            xh[q + 1] = mu * (alpha * gp[sl].y - o);
         });
+    (void)k;
 }
 
 // fixed-order sum of one partial array of each image into one of its cotangents:
@@ -1314,7 +1299,7 @@ struct lpnp_tape {
     const float* guide = nullptr;  // caller's guide
     int blur_r = 0;
     float blur_sigma = 1.f;
-    DevBuf Dh, Th, X, V, U, Gr, AZ, AZ4, xh, vh, uh, zh, g, gs, dh, dh0, base, thp, Dhat, Gp, m, mkey, sstar, mh,
+    DevBuf Dh, Th, X, V, U, Gr, AZ, AZ4, xh, vh, uh, g, gs, dh, dh0, base, thp, Dhat, Gp, m, mkey, sstar, mh,
         rho_part, h_part, m_part, scratch;
     // tables of a call this tape leads (the first image of the batch): per-image views,
     // phase-1 instance tables and work items in one device buffer, uploaded from one
@@ -1341,6 +1326,9 @@ struct lpnp_tape {
     // the launch sequences of the forward (after the weight builds) and of the backward,
     // recorded as CUDA graphs by the call this tape leads, and the keys they were recorded for
     cudaGraphExec_t fwd_exec = nullptr, bwd_exec = nullptr;
+    // the side stream of the backward's A^T A steps and the events that fork and join it
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     std::vector<uint64_t> fwd_key, bwd_key;
     uint64_t fwd_launches = 0, bwd_launches = 0;
 };
@@ -1458,7 +1446,6 @@ TapeView make_view(const lpnp_tape* tp, const float* x_out, const float* x_bar, 
     v.xh = tp->xh.as<float>();
     v.vh = tp->vh.as<float>();
     v.uh = tp->uh.as<float>();
-    v.zh = tp->zh.as<float>();
     v.g = tp->g.as<float>();
     v.gs = tp->gs.as<float>();
     v.dh = tp->dh.as<float>();
@@ -1745,7 +1732,7 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     const int nhb = fused ? nbd : npb;         // blocks that write dL/dh partials
     for (int i = 0; i < count; ++i) {
         lpnp_tape* tp = tapes[i];
-        DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->zh, &tp->g, &tp->gs, &tp->dh, &tp->base};
+        DevBuf* nbufs[] = {&tp->xh, &tp->vh, &tp->uh, &tp->g, &tp->gs, &tp->dh, &tp->base};
         for (DevBuf* b : nbufs) TAPE_CK(b->ensure(sizeof(float) * n));
         TAPE_CK(tp->AZ.ensure(sizeof(float) * n * N));
         TAPE_CK(tp->AZ4.ensure(sizeof(float4) * n * ((N + 1) / 2)));
@@ -1821,7 +1808,11 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     const int dtype = dens[0]->dtype;
     const dim3 gg((W + kGT - 1) / kGT, (H + kGT - 1) / kGT, count);  // A^T A tiles
     const dim3 ng(nblk(n), 1, count);
-    // the scalar cotangents' device and pinned host buffers (before any recording)
+    // the side stream and its events, and the scalar cotangents' device and pinned host
+    // buffers (before any recording)
+    if (!lead->side) TAPE_CK(cudaStreamCreateWithFlags(&lead->side, cudaStreamNonBlocking));
+    TAPE_CK(ensure_event(lead->fork_ev));
+    TAPE_CK(ensure_event(lead->join_ev));
     TAPE_CK(lead->scal.ensure(sizeof(double) * 3 * (size_t)count));
     if (lead->hs_count < count) {
         if (lead->hs) cudaFreeHost(lead->hs);
@@ -1838,21 +1829,30 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         TAPE_CK(pdl(adj_bwd_prep_kernel, dim3(ng), dim3(256), 0, st, tb.views, nrb));
         count_launches(1);
         TAPE_CK(cudaGetLastError());
+        // iteration k: W a_k (W symmetric; no weight stream in the last iteration, where
+        // a = vh - uh = 0) finished with g and the per-pixel cotangent updates, which also
+        // form a_{k-1}; then the weight stream of a_{k-1} on this stream and, beside it on
+        // the side stream, xh = mu (alpha g - A^T A g) (the only step with neighbours)
+        auto ata = [&](cudaStream_t s2) {
+            return by_blur_radius(lead->taps.r, [&](auto rc) {
+                return pdl(adj_ata_update_kernel<decltype(rc)::value>, gg, dim3(256), 0, s2, tb.views, 0);
+            });
+        };
         for (int k = N - 1; k >= 0; --k) {
-            // W a (W symmetric), finished with g and zh; xbar_k from the recorded grad f(x_k).
-            // In the last iteration a = vh - uh = 0, so W a = 0 needs no weight stream.
             const int a_zero = k == N - 1;
-            if (!a_zero)
-                TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)k * count, tb.work,
-                                                  tb.nwork, err, st));
             TAPE_CK(pdl(adj_wa_g_kernel, wgrid, dim3(32, 8), 0, st, tb.views, k, a_zero));
-            count_launches(1);
-            TAPE_CK(cudaGetLastError());
-            // A^T A g and the updates of the cotangents, with the earlier iteration's inputs
-            TAPE_CK(by_blur_radius(lead->taps.r, [&](auto rc) {
-                return pdl(adj_ata_update_kernel<decltype(rc)::value>, dim3(gg), dim3(256), 0, st, tb.views, k);
-            }));
-            count_launches(1);
+            count_launches(2);
+            if (k > 0) {
+                TAPE_CK(cudaEventRecord(lead->fork_ev, st));
+                TAPE_CK(cudaStreamWaitEvent(lead->side, lead->fork_ev, 0));
+                TAPE_CK(ata(lead->side));
+                TAPE_CK(cudaEventRecord(lead->join_ev, lead->side));
+                TAPE_CK(launch_tma_gather_batched(dtype, rs, maps, tb.insts + (size_t)(k - 1) * count, tb.work,
+                                                  tb.nwork, err, st));
+                TAPE_CK(cudaStreamWaitEvent(st, lead->join_ev, 0));
+            } else {
+                TAPE_CK(ata(st));
+            }
         }
         // pair pass G with the mirrored terms, the gather of dh, then the cotangent of m and
         // its terms
@@ -2037,7 +2037,7 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (t->den) cudaStreamSynchronize(t->den->stream);
     if (t->staged) cudaEventSynchronize(t->staged);
     DevBuf* bufs[] = {&t->Dh,  &t->Th,   &t->X,  &t->V,       &t->U,     &t->Gr,     &t->AZ, &t->AZ4, &t->xh,
-                      &t->vh,  &t->uh,   &t->zh, &t->g,       &t->gs,    &t->dh,     &t->dh0,    &t->base,
+                      &t->vh,  &t->uh,   &t->g,  &t->gs,      &t->dh,    &t->dh0,    &t->base,
                       &t->thp, &t->Dhat, &t->Gp, &t->m,     &t->mkey,   &t->sstar,  &t->mh,
                       &t->rho_part, &t->h_part, &t->m_part, &t->scratch, &t->tables, &t->scal};
     for (DevBuf* b : bufs) b->release();
@@ -2045,6 +2045,10 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (t->hs) cudaFreeHost(t->hs);
     if (t->staged) cudaEventDestroy(t->staged);
     if (t->ev) cudaEventDestroy(t->ev);
+    if (t->side) cudaStreamSynchronize(t->side);
+    if (t->fork_ev) cudaEventDestroy(t->fork_ev);
+    if (t->join_ev) cudaEventDestroy(t->join_ev);
+    if (t->side) cudaStreamDestroy(t->side);
     if (t->fwd_exec) cudaGraphExecDestroy(t->fwd_exec);
     if (t->bwd_exec) cudaGraphExecDestroy(t->bwd_exec);
     delete t;

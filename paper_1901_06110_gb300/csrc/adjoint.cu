@@ -26,7 +26,10 @@
 // reading each image's buffers and scalars from a per-image view in device memory, and
 // every phase-1 stencil pass is one launch of the batched weight stream over the tiles
 // of all images.  The arithmetic of each image is that of the image alone; only the
-// number of launches and how they fill the GPU change with the batch.
+// number of launches and how they fill the GPU change with the batch.  The steps that
+// need neighbouring pixels but not the weights (grad f(x_{k+1}) in the forward,
+// A^T A g in the backward) run on a side stream beside the weight stream they do not
+// depend on; the per-pixel updates move into the steps around them.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -218,35 +221,75 @@ __global__ void __launch_bounds__(256, 4) adj_fwd_xupdate_kernel(const TapeView*
     fwd_xupdate_tile<R>(sm, tv[blockIdx.z], k, blockIdx.y * kGT, blockIdx.x * kGT);
 }
 
-// The dual step of recorded iteration k in place on slot k + 1, on the kXH x kXW tile at
-// (y0, x0): v = W z (the third aggregation of Algorithm 2 with the closure of Eq. S3, from
-// the phase-1 partial sums and 1/m on the device) and u <- u + x - v; the same per-pixel
-// code as the solve's combine, without the next x-update and the residual sums
-__device__ __forceinline__ void fwd_dual_tile(const TapeView& v, int k, int y0, int x0) {
+// g_k = A^T (A x_k - y) recorded into its slot, on 32 x 32 tiles.  Only x_k is read, so it
+// runs beside the weight stream of z_{k-1} = x_k + u_{k-1}.
+template <int R>
+__global__ void __launch_bounds__(256, 4) adj_fwd_grad_kernel(const TapeView* __restrict__ tv, int k) {
+    griddep_enter();
+    __shared__ GradSmem<R> sm;
+    const TapeView& v = tv[blockIdx.z];
     const size_t n = (size_t)v.H * v.W;
-    EpilogueArgs a{};
-    a.H = v.H;
-    a.W = v.W;
-    a.d = v.Dh + (size_t)v.T * n;
-    a.t = v.Th + (size_t)v.T * n;
-    a.inv_m = 1.f;
-    a.inv_m_dev = v.m + 1;
-    a.z = v.z;
-    a.v = v.V + (size_t)(k + 1) * n;
-    a.u = v.U + (size_t)(k + 1) * n;
-    a.taps = v.taps;
-    a.mu = v.mu;
-    a.alpha = v.alpha;
-    a.rho = v.rho;
-    a.constraint = v.constraint;
-    a.do_x = 0;
-    combine_update_body<0, 0>(v.cv, a, 0, y0, x0, nullptr);
+    sr_grad_tile<R>(sm, v.X + (size_t)k * n, v.y, v.H, v.W, v.taps, v.Gr + (size_t)k * n, blockIdx.y * kGT,
+                    blockIdx.x * kGT);
 }
 
-__global__ void __launch_bounds__(256) adj_fwd_dual_kernel(const TapeView* __restrict__ tv, int k) {
+// The dual step of recorded iteration k and, with do_x, the x-step of iteration k + 1,
+// per pixel on the kXH x kXW tile of the block (two pixels per thread, rows i and i + 8):
+//   v_{k+1} = W z with z = x_{k+1} + u_k (the third aggregation of Algorithm 2 with the
+//   closure of Eq. S3, from the phase-1 partial sums and 1/m on the device),
+//   u_{k+1} = u_k + x_{k+1} - v_{k+1} = z - v_{k+1},
+//   x_{k+2} = Pi_C(mu (alpha x_{k+1} + rho (v_{k+1} - u_{k+1}) - g_{k+1})),  z <- x_{k+2} + u_{k+1},
+// g_{k+1} recorded beforehand by adj_fwd_grad_kernel.  z is read and written at the
+// thread's own pixels only.
+__global__ void __launch_bounds__(256) adj_fwd_dual_x_kernel(const TapeView* __restrict__ tv, int k, int do_x) {
     griddep_enter();
     const TapeView& v = tv[blockIdx.z];
-    fwd_dual_tile(v, k, blockIdx.y * kXH, blockIdx.x * kXW);
+    const int H = v.H, W = v.W;
+    const size_t n = (size_t)H * W;
+    const int y0 = blockIdx.y * kXH, x0 = blockIdx.x * kXW;
+    const int j = x0 + threadIdx.x, lj = j - (x0 / kTmaTW) * kTmaTW;
+    const float inv_m = __ldg(v.m + 1);
+    const float* d = v.Dh + (size_t)v.T * n;
+    const float* t = v.Th + (size_t)v.T * n;
+    float* z = v.z;
+    float* v1 = v.V + (size_t)(k + 1) * n;
+    float* u1 = v.U + (size_t)(k + 1) * n;
+    const float* x1 = do_x ? v.X + (size_t)(k + 1) * n : nullptr;
+    const float* g1 = do_x ? v.Gr + (size_t)(k + 1) * n : nullptr;
+    float* x2 = do_x ? v.X + (size_t)(k + 2) * n : nullptr;
+    const float mu = v.mu, alpha = v.alpha, rho = v.rho;
+    const TileCover tc = tile_cover(v.cv, y0, x0);
+    float zs[2], ds[2], ts[2], xs[2], gs[2], A[2];
+    bool ok[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int i = y0 + threadIdx.y + 8 * c;
+        ok[c] = i < H && j < W;
+        const size_t q = ok[c] ? (size_t)i * W + j : 0;
+        zs[c] = z[q];
+        ds[c] = d[q];
+        ts[c] = t[q];
+        xs[c] = do_x ? x1[q] : 0.f;
+        gs[c] = do_x ? g1[q] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) A[c] = ok[c] ? tile_gather(tc, threadIdx.y + 8 * c, lj) : 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!ok[c]) continue;
+        const size_t q = (size_t)(y0 + threadIdx.y + 8 * c) * W + j;
+        const float dm = ds[c] * inv_m;
+        const float cs = 1.f - dm * (ts[c] - ds[c]);
+        const float vn = fmaf(dm, A[c], cs * zs[c]);
+        const float un = zs[c] - vn;
+        v1[q] = vn;
+        u1[q] = un;
+        if (do_x) {
+            const float xn = project(mu * (alpha * xs[c] + rho * (vn - un) - gs[c]), v.constraint);
+            x2[q] = xn;
+            z[q] = xn + un;
+        }
+    }
 }
 
 // x_N to the caller's buffer
@@ -1538,6 +1581,15 @@ BatchMaps batch_maps(dsgnlm* const* dens, int count) {
     return maps;
 }
 
+// The lead tape's side stream and the events that fork work onto it and join it back
+// (created before any recording)
+dsgnlm_status ensure_side(lpnp_tape* lead) {
+    if (!lead->side) TAPE_CK(cudaStreamCreateWithFlags(&lead->side, cudaStreamNonBlocking));
+    TAPE_CK(ensure_event(lead->fork_ev));
+    TAPE_CK(ensure_event(lead->join_ev));
+    return DSGNLM_OK;
+}
+
 // The other images' handle streams wait for the work queued on `st` (so that work the
 // caller queues on them afterwards follows the batch).
 dsgnlm_status join_streams(lpnp_tape* lead, dsgnlm* const* dens, int count, cudaStream_t st) {
@@ -1629,6 +1681,8 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
     Tables tb{};
     dsgnlm_status s = upload_tables(lead, dens, count, views, insts, st, tb);
     if (s != DSGNLM_OK) return s;
+    s = ensure_side(lead);
+    if (s != DSGNLM_OK) return s;
     const BatchMaps maps = batch_maps(dens, count);
     unsigned* err = dens[0]->err.as<unsigned>();
     const int dtype = dens[0]->dtype;
@@ -1639,8 +1693,17 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
     const dim3 gg((W + kGT - 1) / kGT, (H + kGT - 1) / kGT, count);
     const BlurTaps taps = make_blur_taps(blur_sigma, blur_r);
     auto seq = [&](cudaStream_t st) -> dsgnlm_status {
+        // on the side stream, beside the balance (which does not depend on x): x = v =
+        // clip(guide), u = 0, and the x-step of iteration 0 with its recorded gradient
+        TAPE_CK(cudaEventRecord(lead->fork_ev, st));
+        TAPE_CK(cudaStreamWaitEvent(lead->side, lead->fork_ev, 0));
+        TAPE_CK(pdl(adj_init_kernel, dim3(nblk(n), 1, count), dim3(256), 0, lead->side, tb.views));
+        TAPE_CK(by_blur_radius(taps.r, [&](auto rc) {
+            return pdl(adj_fwd_xupdate_kernel<decltype(rc)::value>, gg, dim3(256), 0, lead->side, tb.views, 0);
+        }));
+        TAPE_CK(cudaEventRecord(lead->join_ev, lead->side));
         TAPE_CK(pdl(adj_prep_kernel, dim3(ng), dim3(256), 0, st, tb.views));
-        count_launches(1);
+        count_launches(3);
         TAPE_CK(cudaGetLastError());
         for (int p = 0; p <= T; ++p) {
             TAPE_CK(launch_tma_gather_batched(dtype, search_r, maps, tb.insts + (size_t)p * count, tb.work,
@@ -1651,17 +1714,28 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
         }
         TAPE_CK(pdl(adj_m_key_kernel, dim3(ng), dim3(256), 0, st, tb.views));
         TAPE_CK(pdl(adj_m_finish_kernel, dim3((count + 63) / 64), dim3(64), 0, st, tb.views, count));
-        TAPE_CK(pdl(adj_init_kernel, dim3(nblk(n), 1, count), dim3(256), 0, st, tb.views));
-        count_launches(3);
+        count_launches(2);
         TAPE_CK(cudaGetLastError());
+        TAPE_CK(cudaStreamWaitEvent(st, lead->join_ev, 0));
+        // iteration k: the weight stream of z_k and, beside it on the side stream, the
+        // gradient of x_{k+1}; then the dual step of k with the x-step of k + 1
         for (int k = 0; k < N; ++k) {
-            TAPE_CK(by_blur_radius(taps.r, [&](auto rc) {
-                return pdl(adj_fwd_xupdate_kernel<decltype(rc)::value>, gg, dim3(256), 0, st, tb.views, k);
-            }));
+            const int do_x = k + 1 < N;
+            if (do_x) {
+                TAPE_CK(cudaEventRecord(lead->fork_ev, st));
+                TAPE_CK(cudaStreamWaitEvent(lead->side, lead->fork_ev, 0));
+                TAPE_CK(by_blur_radius(taps.r, [&](auto rc) {
+                    return pdl(adj_fwd_grad_kernel<decltype(rc)::value>, gg, dim3(256), 0, lead->side, tb.views,
+                               k + 1);
+                }));
+                TAPE_CK(cudaEventRecord(lead->join_ev, lead->side));
+                count_launches(1);
+            }
             TAPE_CK(launch_tma_gather_batched(dtype, search_r, maps, tb.insts + (size_t)(T + 1) * count, tb.work,
                                               tb.nwork, err, st));
-            TAPE_CK(pdl(adj_fwd_dual_kernel, eg, dim3(32, 8), 0, st, tb.views, k));
-            count_launches(2);
+            if (do_x) TAPE_CK(cudaStreamWaitEvent(st, lead->join_ev, 0));
+            TAPE_CK(pdl(adj_fwd_dual_x_kernel, eg, dim3(32, 8), 0, st, tb.views, k, do_x));
+            count_launches(1);
         }
         TAPE_CK(pdl(adj_xout_kernel, dim3(nblk(n), 1, count), dim3(256), 0, st, tb.views));
         count_launches(1);
@@ -1810,9 +1884,10 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
     const dim3 ng(nblk(n), 1, count);
     // the side stream and its events, and the scalar cotangents' device and pinned host
     // buffers (before any recording)
-    if (!lead->side) TAPE_CK(cudaStreamCreateWithFlags(&lead->side, cudaStreamNonBlocking));
-    TAPE_CK(ensure_event(lead->fork_ev));
-    TAPE_CK(ensure_event(lead->join_ev));
+    {
+        const dsgnlm_status ss = ensure_side(lead);
+        if (ss != DSGNLM_OK) return ss;
+    }
     TAPE_CK(lead->scal.ensure(sizeof(double) * 3 * (size_t)count));
     if (lead->hs_count < count) {
         if (lead->hs) cudaFreeHost(lead->hs);

@@ -1,9 +1,9 @@
 """torch.autograd binding of the differentiable form (lpnp_unrolled_forward /
 lpnp_backward and their batched forms in the C ABI): unrolled linearized PnP-ADMM for
 2x super-resolution with DSG-NLM, differentiable in the observation, the guide, the
-bandwidth h and rho.  Each image keeps a denoiser handle, a checkpoint tape and a CUDA
-stream between the forward and the backward; these slots are pooled and reused once
-the backward has run, so repeated calls allocate nothing.  All arithmetic runs in the
+bandwidth h and rho.  Each image keeps a denoiser handle and a checkpoint tape between
+the forward and the backward; these slots are pooled and reused once the backward has
+run, so repeated calls allocate nothing.  The calls run on the caller's current stream.  All arithmetic runs in the
 CUDA library."""
 from __future__ import annotations
 
@@ -28,16 +28,23 @@ class UnrollParams:
 
 
 class _Slot:
-    """One image's tape, FP32 denoiser handle and stream.  The handle launches on the
-    slot's own stream, so the images of a batch overlap on the device."""
+    """One image's tape and FP32 denoiser handle.  The handle launches on the caller's
+    current stream (set when it changes); the batched calls run every image of a batch
+    in one launch per step on the first image's stream."""
 
     def __init__(self):
         self.lib = _abi.load()
         t = ctypes.c_void_p()
         D._check(self.lib.lpnp_tape_create(ctypes.byref(t)), "lpnp_tape_create")
         self.ptr = t
-        self.stream = torch.cuda.Stream()
-        self.den = D.dsgnlm_create("f32", stream=self.stream)
+        self.den = D.dsgnlm_create("f32")
+        self.bound = None  # the raw stream the handle launches on
+
+    def bind(self, stream):
+        raw = stream.cuda_stream
+        if raw != self.bound:
+            D._check(self.lib.dsgnlm_set_stream(self.den.handle, ctypes.c_void_p(raw)), "dsgnlm_set_stream")
+            self.bound = raw
 
     def __del__(self):
         try:
@@ -69,25 +76,31 @@ class _Lease:
             pass
 
 
-def _fork(slots):
-    """Each slot's stream waits for the work queued so far on the current stream."""
-    ev = torch.cuda.Event()
-    ev.record(torch.cuda.current_stream())
-    for s in slots:
-        s.stream.wait_event(ev)
-
-
-def _join(slots):
-    """The current stream waits for the work queued on every slot's stream."""
+def _bind(slots):
+    """Every slot's handle launches on the current stream, which is returned."""
     cur = torch.cuda.current_stream()
     for s in slots:
-        ev = torch.cuda.Event()
-        ev.record(s.stream)
-        cur.wait_event(ev)
+        s.bind(cur)
+    return cur
+
+
+def _follow(ctx):
+    """The backward's stream: the current one, after the work the forward queued on its
+    stream (the tapes are not tensors, so autograd does not order them)."""
+    cur = torch.cuda.current_stream()
+    if cur.cuda_stream != ctx.stream.cuda_stream:
+        cur.wait_stream(ctx.stream)
+    return cur
 
 
 def _ptrs(vals):
     return (ctypes.c_void_p * len(vals))(*vals)
+
+
+def _rows(t):
+    """The addresses of t[0], t[1], ... of a contiguous tensor, without indexing it."""
+    base, step = t.data_ptr(), t[0].numel() * t.element_size()
+    return _ptrs([base + b * step for b in range(t.shape[0])])
 
 
 def _grad_scalar(ctx, idx, value):
@@ -109,13 +122,12 @@ class UnrolledSR(torch.autograd.Function):
         lease = _Lease(1)
         slot = lease.slots[0]
         x = torch.empty_like(guide)
-        _fork(lease.slots)
+        ctx.stream = _bind(lease.slots)
         D._check(slot.lib.lpnp_unrolled_forward(
             slot.ptr, slot.den.handle, D._ptr(y, torch.float32, "y", (H // 2) * (W // 2)),
             D._ptr(guide, torch.float32, "guide", H * W), H, W, params.patch_r, params.search_r, float(h),
             params.balance_passes, params.alpha, float(rho), params.iters, params.blur_sigma, params.blur_r,
             x.data_ptr()), "lpnp_unrolled_forward")
-        _join(lease.slots)
         ctx.lease = lease
         ctx.keep = (y, guide)  # the tape reads them in the backward
         ctx.scalar_dtype = (_scalar_dtype(h), _scalar_dtype(rho))
@@ -130,17 +142,16 @@ class UnrolledSR(torch.autograd.Function):
         g_bar = torch.empty_like(guide)
         hb = ctypes.c_double(0.0)
         rb = ctypes.c_double(0.0)
-        _fork(ctx.lease.slots)
+        slot.bind(_follow(ctx))
         D._check(slot.lib.lpnp_backward(slot.ptr, x_bar.data_ptr(), y_bar.data_ptr(), g_bar.data_ptr(),
                                         ctypes.byref(hb), ctypes.byref(rb)), "lpnp_backward")
-        _join(ctx.lease.slots)
         ctx.lease.release()
         return y_bar, g_bar, _grad_scalar(ctx, 2, hb.value), _grad_scalar(ctx, 3, rb.value), None
 
 
 class UnrolledSRBatch(torch.autograd.Function):
     """x_N [B, H, W] for y [B, H/2, W/2] and guide [B, H, W] with shared h and rho,
-    through the batched C calls: the B images run on B streams at once."""
+    through the batched C calls: every step is one launch over the B images."""
 
     @staticmethod
     def forward(ctx, y, guide, h, rho, params: UnrollParams):
@@ -152,14 +163,12 @@ class UnrolledSRBatch(torch.autograd.Function):
         lease = _Lease(B)
         x = torch.empty_like(guide)
         lib = lease.slots[0].lib
-        _fork(lease.slots)
+        ctx.stream = _bind(lease.slots)
         D._check(lib.lpnp_unrolled_forward_batched(
             _ptrs([s.ptr.value for s in lease.slots]), _ptrs([s.den.handle.value for s in lease.slots]), B,
-            _ptrs([y[b].data_ptr() for b in range(B)]), _ptrs([guide[b].data_ptr() for b in range(B)]), H, W,
-            params.patch_r, params.search_r, float(h), params.balance_passes, params.alpha, float(rho),
-            params.iters, params.blur_sigma, params.blur_r, _ptrs([x[b].data_ptr() for b in range(B)])),
+            _rows(y), _rows(guide), H, W, params.patch_r, params.search_r, float(h), params.balance_passes,
+            params.alpha, float(rho), params.iters, params.blur_sigma, params.blur_r, _rows(x)),
             "lpnp_unrolled_forward_batched")
-        _join(lease.slots)
         ctx.lease = lease
         ctx.keep = (y, guide)
         ctx.scalar_dtype = (_scalar_dtype(h), _scalar_dtype(rho))
@@ -175,12 +184,12 @@ class UnrolledSRBatch(torch.autograd.Function):
         g_bar = torch.empty_like(guide)
         hb = (ctypes.c_double * B)()
         rb = (ctypes.c_double * B)()
-        _fork(slots)
+        cur = _follow(ctx)
+        for s in slots:
+            s.bind(cur)
         D._check(slots[0].lib.lpnp_backward_batched(
-            _ptrs([s.ptr.value for s in slots]), B, _ptrs([x_bar[b].data_ptr() for b in range(B)]),
-            _ptrs([y_bar[b].data_ptr() for b in range(B)]), _ptrs([g_bar[b].data_ptr() for b in range(B)]), hb, rb),
+            _ptrs([s.ptr.value for s in slots]), B, _rows(x_bar), _rows(y_bar), _rows(g_bar), hb, rb),
             "lpnp_backward_batched")
-        _join(slots)
         ctx.lease.release()
         return y_bar, g_bar, _grad_scalar(ctx, 2, sum(hb)), _grad_scalar(ctx, 3, sum(rb)), None
 

@@ -1369,8 +1369,9 @@ struct lpnp_tape {
     // the launch sequences of the forward (after the weight builds) and of the backward,
     // recorded as CUDA graphs by the call this tape leads, and the keys they were recorded for
     cudaGraphExec_t fwd_exec = nullptr, bwd_exec = nullptr;
-    // the side stream of the backward's A^T A steps and the events that fork and join it
-    cudaStream_t side = nullptr;
+    // the side stream of the steps that run beside the weight streams, the events that
+    // fork and join it, and the stream the launch sequences are recorded on
+    cudaStream_t side = nullptr, cap = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     std::vector<uint64_t> fwd_key, bwd_key;
     uint64_t fwd_launches = 0, bwd_launches = 0;
@@ -1409,14 +1410,16 @@ cudaError_t ensure_event(cudaEvent_t& e) {
 
 // Queue `seq` (a function of the stream that queues a fixed launch sequence and returns a
 // status) on `st` through a CUDA graph: replayed when `key` equals the key the graph was
-// recorded for, recorded anew otherwise.  The graph keeps the programmatic launch edges,
+// recorded for, recorded anew otherwise.  The recording runs on `cap`, a stream of the
+// tape's own (the caller's stream may be the legacy default stream, which cannot record);
+// the graph is then launched on `st`.  The graph keeps the programmatic launch edges,
 // and its replay takes one launch from the host and shorter gaps between the kernels.
 // Every kernel parameter of the sequence must be a function of the key: the per-call
 // pointers live in the tables in device memory, uploaded before the replay.  If the
 // recording fails, the sequence is queued directly.
 template <typename F>
 dsgnlm_status run_recorded(cudaGraphExec_t& exec, std::vector<uint64_t>& rec_key, uint64_t& rec_launches,
-                           const std::vector<uint64_t>& key, cudaStream_t st, F&& seq) {
+                           const std::vector<uint64_t>& key, cudaStream_t st, cudaStream_t cap, F&& seq) {
     if (exec && rec_key == key) {
         TAPE_CK(cudaGraphLaunch(exec, st));
         count_launches(rec_launches);
@@ -1426,17 +1429,17 @@ dsgnlm_status run_recorded(cudaGraphExec_t& exec, std::vector<uint64_t>& rec_key
         cudaGraphExecDestroy(exec);
         exec = nullptr;
     }
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return seq(st);
     }
     set_capture_counting(true);
-    const dsgnlm_status s = seq(st);
+    const dsgnlm_status s = seq(cap);
     set_capture_counting(false);
     const uint64_t n = recorded_launches();
     cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(st, &g);
+    e = cudaStreamEndCapture(cap, &g);
     if (e == cudaSuccess && s == DSGNLM_OK) e = cudaGraphInstantiate(&exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess || s != DSGNLM_OK) {
@@ -1536,10 +1539,12 @@ struct Tables {
     const BatchInst* insts;
     const int4* work;
     int nwork;
+    const BuildJob* jobs;  // the forward's weight builds (null for the backward)
 };
 
 dsgnlm_status upload_tables(lpnp_tape* lead, dsgnlm* const* dens, int count, const std::vector<TapeView>& views,
-                            const std::vector<BatchInst>& insts, cudaStream_t st, Tables& out) {
+                            const std::vector<BatchInst>& insts, cudaStream_t st, Tables& out,
+                            const std::vector<BuildJob>* jobs = nullptr) {
     std::vector<int4> work;
     for (int i = 0; i < count; ++i) {
         const TmaPlan& pl = dens[i]->plan;
@@ -1550,7 +1555,8 @@ dsgnlm_status upload_tables(lpnp_tape* lead, dsgnlm* const* dens, int count, con
     const size_t bv = align256(sizeof(TapeView) * views.size());
     const size_t bi = align256(sizeof(BatchInst) * insts.size());
     const size_t bw = align256(sizeof(int4) * work.size());
-    const size_t total = bv + bi + bw;
+    const size_t bj = jobs ? align256(sizeof(BuildJob) * jobs->size()) : 0;
+    const size_t total = bv + bi + bw + bj;
     TAPE_CK(lead->tables.ensure(total));
     TAPE_CK(ensure_event(lead->staged));
     // the previous upload from the staging buffer must have been read before it is rewritten
@@ -1565,6 +1571,7 @@ dsgnlm_status upload_tables(lpnp_tape* lead, dsgnlm* const* dens, int count, con
     std::memcpy(lead->stage, views.data(), sizeof(TapeView) * views.size());
     std::memcpy(lead->stage + bv, insts.data(), sizeof(BatchInst) * insts.size());
     std::memcpy(lead->stage + bv + bi, work.data(), sizeof(int4) * work.size());
+    if (jobs) std::memcpy(lead->stage + bv + bi + bw, jobs->data(), sizeof(BuildJob) * jobs->size());
     TAPE_CK(cudaMemcpyAsync(lead->tables.p, lead->stage, total, cudaMemcpyHostToDevice, st));
     TAPE_CK(cudaEventRecord(lead->staged, st));
     unsigned char* base = static_cast<unsigned char*>(lead->tables.p);
@@ -1572,6 +1579,7 @@ dsgnlm_status upload_tables(lpnp_tape* lead, dsgnlm* const* dens, int count, con
     out.insts = reinterpret_cast<const BatchInst*>(base + bv);
     out.work = reinterpret_cast<const int4*>(base + bv + bi);
     out.nwork = (int)work.size();
+    out.jobs = jobs ? reinterpret_cast<const BuildJob*>(base + bv + bi + bw) : nullptr;
     return DSGNLM_OK;
 }
 
@@ -1585,6 +1593,7 @@ BatchMaps batch_maps(dsgnlm* const* dens, int count) {
 // (created before any recording)
 dsgnlm_status ensure_side(lpnp_tape* lead) {
     if (!lead->side) TAPE_CK(cudaStreamCreateWithFlags(&lead->side, cudaStreamNonBlocking));
+    if (!lead->cap) TAPE_CK(cudaStreamCreateWithFlags(&lead->cap, cudaStreamNonBlocking));
     TAPE_CK(ensure_event(lead->fork_ev));
     TAPE_CK(ensure_event(lead->join_ev));
     return DSGNLM_OK;
@@ -1620,10 +1629,12 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
     cudaStream_t st = dens[0]->stream;
     const size_t n = (size_t)H * W;
     const int T = balance_passes, N = iters;
-    // 1. the weights of every image, the offset split of each sized for the batch
+    // 1. every image's planes and phase-1 plan, the offset split of each sized for the
+    // batch; the weights themselves are built by one batched launch in the recorded
+    // sequence below.  Work queued on the other handles' streams comes first.
     for (int i = 0; i < count; ++i) {
         dens[i]->share = count;
-        dsgnlm_status s = dsgnlm_build(dens[i], guide[i], H, W, patch_r, search_r, bandwidth);
+        dsgnlm_status s = build_handle(dens[i], guide[i], H, W, patch_r, search_r, bandwidth, false);
         dens[i]->share = 1;
         if (s != DSGNLM_OK) return s;
         if (!dens[i]->fast || dens[i]->dtype != dens[0]->dtype) return DSGNLM_EINVAL;
@@ -1678,8 +1689,13 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
         insts[(size_t)(T + 1) * count + i] =
             p1_inst(dens[i], tapes[i]->Dh.as<float>() + (size_t)T * n, dens[i]->z.as<float>());
     }
+    std::vector<BuildJob> jobs(count);
+    const float build_c2 = (float)((double)lead->c * 1.4426950408889634);  // c log2 e
+    for (int i = 0; i < count; ++i)
+        jobs[i] = BuildJob{guide[i], dens[i]->planes.p,
+                           (long long)(dens[i]->planes.bytes / weight_elem_bytes(dens[i]->dtype)), build_c2};
     Tables tb{};
-    dsgnlm_status s = upload_tables(lead, dens, count, views, insts, st, tb);
+    dsgnlm_status s = upload_tables(lead, dens, count, views, insts, st, tb, &jobs);
     if (s != DSGNLM_OK) return s;
     s = ensure_side(lead);
     if (s != DSGNLM_OK) return s;
@@ -1693,8 +1709,9 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
     const dim3 gg((W + kGT - 1) / kGT, (H + kGT - 1) / kGT, count);
     const BlurTaps taps = make_blur_taps(blur_sigma, blur_r);
     auto seq = [&](cudaStream_t st) -> dsgnlm_status {
-        // on the side stream, beside the balance (which does not depend on x): x = v =
-        // clip(guide), u = 0, and the x-step of iteration 0 with its recorded gradient
+        // on the side stream, beside the weight build and the balance (which do not depend
+        // on x): x = v = clip(guide), u = 0, and the x-step of iteration 0 with its
+        // recorded gradient
         TAPE_CK(cudaEventRecord(lead->fork_ev, st));
         TAPE_CK(cudaStreamWaitEvent(lead->side, lead->fork_ev, 0));
         TAPE_CK(pdl(adj_init_kernel, dim3(nblk(n), 1, count), dim3(256), 0, lead->side, tb.views));
@@ -1702,6 +1719,8 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
             return pdl(adj_fwd_xupdate_kernel<decltype(rc)::value>, gg, dim3(256), 0, lead->side, tb.views, 0);
         }));
         TAPE_CK(cudaEventRecord(lead->join_ev, lead->side));
+        // the weights of every image (Eq. NLM, Eq. S1), one launch
+        TAPE_CK(launch_build_batched(dtype, tb.jobs, count, H, W, patch_r, search_r, lead->c, st));
         TAPE_CK(pdl(adj_prep_kernel, dim3(ng), dim3(256), 0, st, tb.views));
         count_launches(3);
         TAPE_CK(cudaGetLastError());
@@ -1750,7 +1769,7 @@ dsgnlm_status lock_forward(lpnp_tape* const* tapes, dsgnlm* const* dens, int cou
         key.push_back((uint64_t)(uintptr_t)dens[i]->planes.p);
         key.push_back((uint64_t)dens[i]->plan.splits.n);
     }
-    s = run_recorded(lead->fwd_exec, lead->fwd_key, lead->fwd_launches, key, st, seq);
+    s = run_recorded(lead->fwd_exec, lead->fwd_key, lead->fwd_launches, key, st, lead->cap, seq);
     if (s != DSGNLM_OK) return s;
     // 5. every handle holds its image's W; its m and 1/m stay on the device until a
     // host-side use of the handle reads them back
@@ -2080,7 +2099,7 @@ dsgnlm_status lock_backward(lpnp_tape* const* tapes, int count, const float* con
         key.push_back((uint64_t)(uintptr_t)dens[i]->planes.p);
         key.push_back((uint64_t)dens[i]->plan.splits.n);
     }
-    s = run_recorded(lead->bwd_exec, lead->bwd_key, lead->bwd_launches, key, st, seq);
+    s = run_recorded(lead->bwd_exec, lead->bwd_key, lead->bwd_launches, key, st, lead->cap, seq);
     if (s != DSGNLM_OK) return s;
     s = join_streams(lead, dens.data(), count, st);
     if (s != DSGNLM_OK) return s;
@@ -2124,6 +2143,7 @@ void lpnp_tape_destroy(lpnp_tape_t t) {
     if (t->fork_ev) cudaEventDestroy(t->fork_ev);
     if (t->join_ev) cudaEventDestroy(t->join_ev);
     if (t->side) cudaStreamDestroy(t->side);
+    if (t->cap) cudaStreamDestroy(t->cap);
     if (t->fwd_exec) cudaGraphExecDestroy(t->fwd_exec);
     if (t->bwd_exec) cudaGraphExecDestroy(t->bwd_exec);
     delete t;

@@ -171,6 +171,15 @@ int dsgnlm_num_offsets(dsgnlm_t h) { return (h && h->built) ? h->nh : 0; }
 dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int patch_r,
                            int search_r, float bandwidth) {
     NvtxRange nvtx_range("dsgnlm_build");
+    return build_handle(h, guide, H, W, patch_r, search_r, bandwidth, true);
+}
+
+}  // extern "C"
+
+namespace dsg {
+
+dsgnlm_status build_handle(dsgnlm* h, const float* guide, int H, int W, int patch_r, int search_r, float bandwidth,
+                           bool launch) {
     if (!h || !guide || !aligned16(guide)) return DSGNLM_EINVAL;
     if (H < 1 || W < 1 || (size_t)H * (size_t)W > (size_t)1 << 31) return DSGNLM_EINVAL;
     if (patch_r < 0 || patch_r > DSGNLM_MAX_PATCH_R) return DSGNLM_EINVAL;
@@ -186,10 +195,11 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
     DSG_CK(h->planes.ensure(bytes));
     const double np = 2.0 * patch_r + 1.0;
     const float c = (float)(1.0 / (2.0 * np * np * (double)bandwidth * (double)bandwidth));
-    DSG_CK(h->timed(DSGNLM_PROF_BUILD, [&] {
-        return launch_build(h->dtype, guide, H, W, patch_r, search_r, c, h->planes.p,
-                            (long long)(h->planes.bytes / weight_elem_bytes(h->dtype)), h->stream);
-    }));
+    if (launch)
+        DSG_CK(h->timed(DSGNLM_PROF_BUILD, [&] {
+            return launch_build(h->dtype, guide, H, W, patch_r, search_r, c, h->planes.p,
+                                (long long)(h->planes.bytes / weight_elem_bytes(h->dtype)), h->stream);
+        }));
     h->H = H;
     h->W = W;
     h->Wp = Wp;
@@ -225,7 +235,7 @@ dsgnlm_status dsgnlm_build(dsgnlm_t h, const float* guide, int H, int W, int pat
     return DSGNLM_OK;
 }
 
-}  // extern "C"
+}  // namespace dsg
 
 namespace {
 

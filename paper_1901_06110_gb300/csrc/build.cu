@@ -23,6 +23,10 @@
 // A CTA takes a chunk of consecutive offsets, sized at launch so that the grid
 // fills whole waves of resident CTAs; tiles whose pixels and offset partners all lie
 // inside the image skip the per-pixel bounds test.
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -79,14 +83,23 @@ __device__ __forceinline__ float ex2_approx(float x) {
 template <typename WT, int RP, int RS>
 __global__ void __launch_bounds__(kThreads, RP < 0 ? 1 : (RP <= 5 ? 4 : 3))
 build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt, float c2, int chunk,
-             WT* __restrict__ planes, long long cap) {
+             WT* __restrict__ planes, long long cap, const BuildJob* __restrict__ jobs, int zchunks) {
     extern __shared__ __align__(16) float smem[];
     const int rp = RP >= 0 ? RP : rp_rt;
     const int rs = RS >= 0 ? RS : rs_rt;
     const int nh = num_half_offsets(rs);
     const int y0 = blockIdx.y * kTH;
     const int x0 = blockIdx.x * kTW;
-    const int k_begin = blockIdx.z * chunk;
+    int kz = blockIdx.z;
+    if (jobs) {  // batched: grid z = image x offset chunk
+        const int img = blockIdx.z / zchunks;
+        kz = blockIdx.z - img * zchunks;
+        guide = jobs[img].guide;
+        planes = static_cast<WT*>(jobs[img].planes);
+        cap = jobs[img].cap;
+        c2 = jobs[img].c2;
+    }
+    const int k_begin = kz * chunk;
     const int k_end = min(nh, k_begin + chunk);
 
     // staged guide: rows y0 - rp .. y0 + TH + rp + rs - 1,
@@ -257,28 +270,49 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
     }
 }
 
+// Resident CTAs on the device of one build instantiation at its shared-memory size
+// (queried once per size; the size's attribute is set before)
+template <typename WT, int RP, int RS>
+int build_ctas_per_sm(size_t smem) {
+    static std::mutex mu;
+    static std::vector<std::pair<size_t, int>> known;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto& kv : known)
+        if (kv.first == smem) return kv.second;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_kernel<WT, RP, RS>, kThreads, smem) !=
+            cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return 0;
+    const int slots = per_sm * sms;
+    known.emplace_back(smem, slots);
+    return slots;
+}
+
+// count == 0: one image (guide, planes, cap); count > 0: `count` images from `jobs`
 template <typename WT, int RP, int RS>
 cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, float c, WT* planes, long long cap,
-                            cudaStream_t st) {
+                            const BuildJob* jobs, int count, cudaStream_t st) {
     const int nh = num_half_offsets(rs);
     if (nh == 0) return cudaSuccess;
     const int GH = kTH + 2 * rp + rs, GW = kTW + 2 * rp + 2 * rs;
     const size_t smem = sizeof(float) * (size_t)(GH * GW + 2 * kTH * v_pitch(rp)) + sizeof(int) * (GH + GW);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(build_kernel<WT, RP, RS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e = cudaFuncSetAttribute(build_kernel<WT, RP, RS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+    }
+    const int slots_i = build_ctas_per_sm<WT, RP, RS>(smem);
+    if (slots_i <= 0) {
+        const cudaError_t e = cudaGetLastError();
+        return e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
     }
     // offsets per CTA: the chunk that makes the fewest waves of resident CTAs take the
     // least time (each CTA also stages its guide tile, worth about two offsets)
-    int per_sm = 0, dev = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_kernel<WT, RP, RS>, kThreads, smem) !=
-            cudaSuccess ||
-        cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return cudaGetLastError();
-    const long long slots = per_sm * sms > 0 ? (long long)per_sm * sms : 1;
-    const long long tiles = (long long)((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH);
+    const long long slots = slots_i;
+    const int images = count > 0 ? count : 1;
+    const long long tiles = (long long)((W + kTW - 1) / kTW) * ((H + kTH - 1) / kTH) * images;
     int chunk = nh;
     long long best = -1;
     for (int ch = 1; ch <= nh; ++ch) {
@@ -289,9 +323,11 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
             chunk = ch;
         }
     }
-    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, (nh + chunk - 1) / chunk);
+    const int zchunks = (nh + chunk - 1) / chunk;
+    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, zchunks * images);
     const float c2 = (float)((double)c * 1.4426950408889634);  // c log2 e: the exponent in base 2
-    build_kernel<WT, RP, RS><<<grid, kThreads, smem, st>>>(guide, H, W, rp, rs, c2, chunk, planes, cap);
+    build_kernel<WT, RP, RS><<<grid, kThreads, smem, st>>>(guide, H, W, rp, rs, c2, chunk, planes, cap,
+                                                           count > 0 ? jobs : nullptr, zchunks);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -301,30 +337,30 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
 // of Table 1; other radii take the runtime-radius form.
 template <typename WT, int RP>
 cudaError_t launch_build_rs(const float* guide, int H, int W, int rp, int rs, float c, WT* planes, long long cap,
-                            cudaStream_t st) {
+                            const BuildJob* jobs, int count, cudaStream_t st) {
     if constexpr (RP == 2) {
-        if (rs == 5) return launch_build_rp<WT, RP, 5>(guide, H, W, rp, rs, c, planes, cap, st);
-        if (rs == 7) return launch_build_rp<WT, RP, 7>(guide, H, W, rp, rs, c, planes, cap, st);
+        if (rs == 5) return launch_build_rp<WT, RP, 5>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
+        if (rs == 7) return launch_build_rp<WT, RP, 7>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
     }
     if constexpr (RP == 3 || RP == 5 || RP == 8 || RP == 11 || RP == 14) {
-        if (rs == 10) return launch_build_rp<WT, RP, 10>(guide, H, W, rp, rs, c, planes, cap, st);
+        if (rs == 10) return launch_build_rp<WT, RP, 10>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
     }
-    return launch_build_rp<WT, RP, -1>(guide, H, W, rp, rs, c, planes, cap, st);
+    return launch_build_rp<WT, RP, -1>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
 }
 
 template <typename WT>
 cudaError_t launch_build_t(const float* guide, int H, int W, int rp, int rs, float c, WT* planes, long long cap,
-                           cudaStream_t st) {
+                           const BuildJob* jobs, int count, cudaStream_t st) {
     switch (rp) {
-        case 1: return launch_build_rs<WT, 1>(guide, H, W, rp, rs, c, planes, cap, st);
-        case 2: return launch_build_rs<WT, 2>(guide, H, W, rp, rs, c, planes, cap, st);
-        case 3: return launch_build_rs<WT, 3>(guide, H, W, rp, rs, c, planes, cap, st);
-        case 4: return launch_build_rs<WT, 4>(guide, H, W, rp, rs, c, planes, cap, st);
-        case 5: return launch_build_rs<WT, 5>(guide, H, W, rp, rs, c, planes, cap, st);
-        case 8: return launch_build_rs<WT, 8>(guide, H, W, rp, rs, c, planes, cap, st);    // 17 x 17 patches
-        case 11: return launch_build_rs<WT, 11>(guide, H, W, rp, rs, c, planes, cap, st);  // 23 x 23
-        case 14: return launch_build_rs<WT, 14>(guide, H, W, rp, rs, c, planes, cap, st);  // 29 x 29
-        default: return launch_build_rp<WT, -1, -1>(guide, H, W, rp, rs, c, planes, cap, st);
+        case 1: return launch_build_rs<WT, 1>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
+        case 2: return launch_build_rs<WT, 2>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
+        case 3: return launch_build_rs<WT, 3>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
+        case 4: return launch_build_rs<WT, 4>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
+        case 5: return launch_build_rs<WT, 5>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
+        case 8: return launch_build_rs<WT, 8>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);    // 17 x 17 patches
+        case 11: return launch_build_rs<WT, 11>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);  // 23 x 23
+        case 14: return launch_build_rs<WT, 14>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);  // 29 x 29
+        default: return launch_build_rp<WT, -1, -1>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
     }
 }
 
@@ -335,9 +371,21 @@ DSG_CHECK_WORD_ACCESSOR(check_word_build)
 cudaError_t launch_build(int dtype, const float* guide, int H, int W, int patch_r, int search_r,
                          float c, void* planes, long long cap, cudaStream_t st) {
     switch (dtype) {
-        case 0: return launch_build_t(guide, H, W, patch_r, search_r, c, (float*)planes, cap, st);
-        case 1: return launch_build_t(guide, H, W, patch_r, search_r, c, (__half*)planes, cap, st);
-        default: return launch_build_t(guide, H, W, patch_r, search_r, c, (__nv_bfloat16*)planes, cap, st);
+        case 0: return launch_build_t(guide, H, W, patch_r, search_r, c, (float*)planes, cap, nullptr, 0, st);
+        case 1: return launch_build_t(guide, H, W, patch_r, search_r, c, (__half*)planes, cap, nullptr, 0, st);
+        default:
+            return launch_build_t(guide, H, W, patch_r, search_r, c, (__nv_bfloat16*)planes, cap, nullptr, 0, st);
+    }
+}
+
+cudaError_t launch_build_batched(int dtype, const BuildJob* jobs, int count, int H, int W, int patch_r,
+                                 int search_r, float c, cudaStream_t st) {
+    if (!jobs || count < 1) return cudaErrorInvalidValue;
+    switch (dtype) {
+        case 0: return launch_build_t<float>(nullptr, H, W, patch_r, search_r, c, nullptr, 0, jobs, count, st);
+        case 1: return launch_build_t<__half>(nullptr, H, W, patch_r, search_r, c, nullptr, 0, jobs, count, st);
+        default:
+            return launch_build_t<__nv_bfloat16>(nullptr, H, W, patch_r, search_r, c, nullptr, 0, jobs, count, st);
     }
 }
 

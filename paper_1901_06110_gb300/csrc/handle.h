@@ -244,3 +244,11 @@ struct dsgnlm {
     }
 };
 
+
+namespace dsg {
+// dsgnlm_build's work: validation, the planes and, with `launch`, the weight build on the
+// handle's stream; then the phase-1 plan and the tensor map of the planes.  launch =
+// false leaves the weights to a batched build that the caller queues.
+dsgnlm_status build_handle(dsgnlm* h, const float* guide, int H, int W, int patch_r, int search_r, float bandwidth,
+                           bool launch);
+}  // namespace dsg

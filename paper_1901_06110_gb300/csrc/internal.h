@@ -75,6 +75,19 @@ struct SolveRed {
 // elements (16-byte aligned rows, as TMA requires); dtype 0 = FP32, 1 = FP16, 2 = BF16.
 __host__ __device__ inline int plane_pitch(int W) { return (W + 7) & ~7; }
 
+// One image of a batched build: its guide, its planes and the elements allocated there,
+// and the exponent's scale c log2 e (c = 1 / (2 N_p^2 h^2)).
+struct BuildJob {
+    const float* guide;
+    void* planes;
+    long long cap;
+    float c2;
+};
+// The weights of `count` images of one size in one launch (grid z = image x offset
+// chunk); `jobs` is a device array, read by the kernel, so the launch can be recorded
+// once and replayed for other images.
+cudaError_t launch_build_batched(int dtype, const BuildJob* jobs, int count, int H, int W, int patch_r,
+                                 int search_r, float c, cudaStream_t st);
 cudaError_t launch_build(int dtype, const float* guide, int H, int W, int patch_r, int search_r,
                          float inv_two_np2_h2, void* planes, long long cap, cudaStream_t st);  // cap: weights allocated
 

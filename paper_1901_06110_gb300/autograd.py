@@ -66,7 +66,9 @@ class _Lease:
         self.slots = [_POOL.pop() if _POOL else _Slot() for _ in range(count)]
 
     def release(self):
-        _POOL.extend(self.slots)
+        # back in reverse, so that the next lease of the same size takes the same slots in
+        # the same order (and the C calls replay the graphs recorded for them)
+        _POOL.extend(reversed(self.slots))
         self.slots = []
 
     def __del__(self):
@@ -95,6 +97,19 @@ def _follow(ctx):
 
 def _ptrs(vals):
     return (ctypes.c_void_p * len(vals))(*vals)
+
+
+_SLOT_PTRS: dict = {}
+
+
+def _slot_ptrs(slots):
+    """The tape and handle address arrays of a slot sequence (built once per sequence)."""
+    key = tuple(id(s) for s in slots)
+    hit = _SLOT_PTRS.get(key)
+    if hit is None or any(a is not b for a, b in zip(hit[0], slots)):
+        hit = (tuple(slots), _ptrs([s.ptr.value for s in slots]), _ptrs([s.den.handle.value for s in slots]))
+        _SLOT_PTRS[key] = hit
+    return hit[1], hit[2]
 
 
 def _rows(t):
@@ -164,10 +179,11 @@ class UnrolledSRBatch(torch.autograd.Function):
         x = torch.empty_like(guide)
         lib = lease.slots[0].lib
         ctx.stream = _bind(lease.slots)
+        tapes, dens = _slot_ptrs(lease.slots)
         D._check(lib.lpnp_unrolled_forward_batched(
-            _ptrs([s.ptr.value for s in lease.slots]), _ptrs([s.den.handle.value for s in lease.slots]), B,
-            _rows(y), _rows(guide), H, W, params.patch_r, params.search_r, float(h), params.balance_passes,
-            params.alpha, float(rho), params.iters, params.blur_sigma, params.blur_r, _rows(x)),
+            tapes, dens, B, _rows(y), _rows(guide), H, W, params.patch_r, params.search_r, float(h),
+            params.balance_passes, params.alpha, float(rho), params.iters, params.blur_sigma, params.blur_r,
+            _rows(x)),
             "lpnp_unrolled_forward_batched")
         ctx.lease = lease
         ctx.keep = (y, guide)
@@ -188,7 +204,7 @@ class UnrolledSRBatch(torch.autograd.Function):
         for s in slots:
             s.bind(cur)
         D._check(slots[0].lib.lpnp_backward_batched(
-            _ptrs([s.ptr.value for s in slots]), B, _rows(x_bar), _rows(y_bar), _rows(g_bar), hb, rb),
+            _slot_ptrs(slots)[0], B, _rows(x_bar), _rows(y_bar), _rows(g_bar), hb, rb),
             "lpnp_backward_batched")
         ctx.lease.release()
         return y_bar, g_bar, _grad_scalar(ctx, 2, sum(hb)), _grad_scalar(ctx, 3, sum(rb)), None

@@ -357,9 +357,10 @@ cudaError_t launch_build_t(const float* guide, int H, int W, int rp, int rs, flo
         case 3: return launch_build_rs<WT, 3>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
         case 4: return launch_build_rs<WT, 4>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
         case 5: return launch_build_rs<WT, 5>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
-        case 8: return launch_build_rs<WT, 8>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);    // 17 x 17 patches
-        case 11: return launch_build_rs<WT, 11>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);  // 23 x 23
-        case 14: return launch_build_rs<WT, 14>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);  // 29 x 29
+        // 17 x 17, 23 x 23 and 29 x 29 patches
+        case 8: return launch_build_rs<WT, 8>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
+        case 11: return launch_build_rs<WT, 11>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
+        case 14: return launch_build_rs<WT, 14>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
         default: return launch_build_rp<WT, -1, -1>(guide, H, W, rp, rs, c, planes, cap, jobs, count, st);
     }
 }

@@ -45,6 +45,13 @@ constexpr int kMaxRp = 14; // DSGNLM_MAX_PATCH_R
 // rounded up so that every window start is 16-byte aligned and a window's last
 // 16-byte load stays inside the row
 __host__ __device__ constexpr int v_pitch(int rp) { return ((kTW + 2 * rp + 3) / 4) * 4 + 4; }
+// The vertical sums of rows 16..31 start 16 floats further on, and the staged guide has an
+// odd row pitch: a warp's vertical tasks alternate between the two row segments (lanes
+// 2c and 2c + 1 take column c), and the two segments' accesses then fall in different
+// banks (16 rows apart is 16 banks apart).
+__host__ __device__ constexpr int v_row(int r, int vp) { return r * vp + (r >= kSeg ? 16 : 0); }
+__host__ __device__ constexpr int v_floats(int rp) { return kTH * v_pitch(rp) + 16; }
+__host__ __device__ constexpr int g_pitch(int rp, int rs) { return (kTW + 2 * rp + 2 * rs) | 1; }
 
 template <typename WT>
 __device__ __forceinline__ void store4(WT* p, const float (&w)[kHW]);
@@ -105,19 +112,19 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
     // staged guide: rows y0 - rp .. y0 + TH + rp + rs - 1,
     //               cols x0 - rp - rs .. x0 + TW + rp + rs - 1
     const int GH = kTH + 2 * rp + rs;
-    const int GW = kTW + 2 * rp + 2 * rs;
+    const int GW = g_pitch(rp, rs);
     const int EW = kTW + 2 * rp;  // vertical sums per row: tile columns -rp .. TW + rp - 1
     const int VP = v_pitch(rp);
-    float* V0 = smem;                 // two buffers of vertical sums, [kTH][VP] each
-    float* V1 = V0 + kTH * VP;
-    float* G = V1 + kTH * VP;
+    float* V0 = smem;  // two buffers of vertical sums, [kTH][VP] each (rows 16.. staggered by 16)
+    float* V1 = V0 + v_floats(rp);
+    float* G = V1 + v_floats(rp);
     int* rows = reinterpret_cast<int*>(G + GH * GW);
     int* cols = rows + GH;
 
     const int tid = threadIdx.x;
     for (int a = tid; a < GH; a += kThreads) rows[a] = sym_index(y0 - rp + a, H);
     for (int b = tid; b < GW; b += kThreads) cols[b] = sym_index(x0 - rp - rs + b, W);
-    for (int i = tid; i < 2 * kTH * VP; i += kThreads) V0[i] = 0.f;  // the row tails are read, never used
+    for (int i = tid; i < 2 * v_floats(rp); i += kThreads) V0[i] = 0.f;  // the row tails are read, never used
     __syncthreads();
     {
         const int tx = tid & 63, ty = tid >> 6;
@@ -144,7 +151,7 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
     float gown[kNG];
     if constexpr (RP >= 0) {
         if (tid < n_vtask) {
-            const int seg = tid / EW, cc = tid - (tid / EW) * EW;
+            const int seg = tid & 1, cc = tid >> 1;
             const float* ga = G + seg * kSeg * GW + cc + rs;
 #pragma unroll
             for (int t = 0; t < kNG; ++t) gown[t] = ga[t * GW];
@@ -152,8 +159,8 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
     }
     auto vertical = [&](int oy, int ox, float* V) {
         for (int task = tid; task < n_vtask; task += kThreads) {
-            const int seg = task / EW;
-            const int cc = task - seg * EW;
+            const int seg = task & 1;  // lanes alternate between the two segments
+            const int cc = task >> 1;
             const int r0 = seg * kSeg;
             const float* ga = G + r0 * GW + cc + rs;
             const float* gb = G + (r0 + oy) * GW + cc + rs + ox;
@@ -176,11 +183,12 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
                 if (RP < 0 && t > 2 * rp) break;
                 acc += e[t];
             }
-            V[r0 * VP + cc] = acc;
+            float* Vs = V + v_row(r0, VP) + cc;
+            Vs[0] = acc;
 #pragma unroll
             for (int q = 1; q < kSeg; ++q) {
                 acc += e[q + 2 * rp] - e[q - 1];
-                V[(r0 + q) * VP + cc] = acc;
+                Vs[q * VP] = acc;
             }
         }
     };
@@ -222,7 +230,7 @@ build_kernel(const float* __restrict__ guide, int H, int W, int rp_rt, int rs_rt
         for (int rr = 0; rr < kTH / 16; ++rr) {
             const int r = hr + 16 * rr;
             const int i = y0 + r;
-            const float4* vr = reinterpret_cast<const float4*>(Vc + r * VP + kHW * hg);
+            const float4* vr = reinterpret_cast<const float4*>(Vc + v_row(r, VP) + kHW * hg);
             float v[4 * kNV];
 #pragma unroll
             for (int q = 0; q < kNV; ++q) {
@@ -297,7 +305,8 @@ cudaError_t launch_build_rp(const float* guide, int H, int W, int rp, int rs, fl
     const int nh = num_half_offsets(rs);
     if (nh == 0) return cudaSuccess;
     const int GH = kTH + 2 * rp + rs, GW = kTW + 2 * rp + 2 * rs;
-    const size_t smem = sizeof(float) * (size_t)(GH * GW + 2 * kTH * v_pitch(rp)) + sizeof(int) * (GH + GW);
+    const int GWp = g_pitch(rp, rs);
+    const size_t smem = sizeof(float) * (size_t)(GH * GWp + 2 * v_floats(rp)) + sizeof(int) * (GH + GWp);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(build_kernel<WT, RP, RS>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

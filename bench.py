@@ -38,7 +38,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one stencil_p1 launch from an ncu capture of the
 # full 512x512 workload, with the hash of the kernel source it was taken on; the
 # figure is reported only while the source is unchanged.
-NCU_TRAFFIC = {"stencil_tma.cu": "9993bfd44282e45d", "bytes": 235539968}
+NCU_TRAFFIC = {"stencil_tma.cu": "d9af687657e9db79", "bytes": 235566080}
 
 
 def _args():

@@ -1193,6 +1193,12 @@ __global__ void __launch_bounds__(256, 2)
     }
     const float2 m1 = make_float2(-1.f, -1.f);
     float accm = 0.f;
+    // the thread's first G element of plane 0 (row ty; row ty + 8 is 8 Wp further on), and
+    // the allocation's bound, read once
+    const size_t goff = (size_t)(y0 + ty) * Wp + j;
+    float* const gbase = v.Gp + goff;
+    const long long gcap = v.gp_cap;
+    (void)gcap;
     int oy, ox;
     half_offset(k0, rs, oy, ox);
     for (int k = k0; k < k1; ++k) {
@@ -1206,32 +1212,39 @@ __global__ void __launch_bounds__(256, 2)
         }
         const WT* Kt = reinterpret_cast<const WT*>(smem + st * KST);
         const int fo = oy * FW + ox;
-        float* Gk = v.Gp + (size_t)k * plane;
+        float* const Gk = gbase + (size_t)k * plane;
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             const int row = ty + 8 * m;
             const float K = to_f32(Kt[row * 32 + tx]);
             const int cs = cs0 + 8 * m * FW, cr = cs + fo;
-            float2 acc = make_float2(0.f, 0.f);
+            // the iteration pairs' products in two independent chains (even and odd pairs)
+            float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
             if constexpr (NPK > 0) {
 #pragma unroll
                 for (int u = 0; u < NPK; ++u) {
                     const float4 r4 = AZ4(u, cr);
                     const float2 da = __ffma2_rn(make_float2(r4.x, r4.y), m1, sa[m][u]);  // a(s) - a(r)
                     const float2 dz = __ffma2_rn(sz[m][u], m1, make_float2(r4.z, r4.w));  // z(r) - z(s)
-                    acc = __ffma2_rn(da, dz, acc);
+                    if (u & 1)
+                        acc1 = __ffma2_rn(da, dz, acc1);
+                    else
+                        acc0 = __ffma2_rn(da, dz, acc0);
                 }
             } else {
                 for (int u = 0; u < np; ++u) {
                     const float4 s4 = AZ4(u, cs), r4 = AZ4(u, cr);
                     const float2 da = __ffma2_rn(make_float2(r4.x, r4.y), m1, make_float2(s4.x, s4.y));
                     const float2 dz = __ffma2_rn(make_float2(s4.z, s4.w), m1, make_float2(r4.z, r4.w));
-                    acc = __ffma2_rn(da, dz, acc);
+                    if (u & 1)
+                        acc1 = __ffma2_rn(da, dz, acc1);
+                    else
+                        acc0 = __ffma2_rn(da, dz, acc0);
                 }
             }
-            const float G = acc.x + acc.y;
-            if (in[m] && DSG_IN_RANGE((size_t)k * plane + (size_t)(y0 + row) * Wp + j, v.gp_cap, kChkAdjPlanes))
-                Gk[(size_t)(y0 + row) * Wp + j] = G;
+            const float G = (acc0.x + acc0.y) + (acc1.x + acc1.y);
+            if (in[m] && DSG_IN_RANGE(goff + (size_t)k * plane + (size_t)(8 * m) * Wp, gcap, kChkAdjPlanes))
+                Gk[(size_t)(8 * m) * Wp] = G;
             const float dr = Sd[cr];
             const float GK = G * K;
             accd[m] = fmaf(GK, dr, accd[m]);

@@ -913,20 +913,21 @@ __global__ void __launch_bounds__(256, 3)
                 const float G = Gw[a * GBW];
                 const int cs = fs0 + 8 * m * FW, cr = cs + fo;
                 const float ds = svd[m], dr = Dd[cr];
-                float2 acc = make_float2(0.f, 0.f);
+                // the two halves of the balancing terms in independent chains
+                float2 acc = make_float2(0.f, 0.f), acc2 = make_float2(0.f, 0.f);
                 if constexpr (TT >= 0) {
 #pragma unroll
                     for (int u = 0; u < NP; ++u) {
-                        acc = __ffma2_rn(svT[m][u], DP[u * fcells + cr], acc);  // th^p_s d^p_r
-                        acc = __ffma2_rn(TP[u * fcells + cr], svD[m][u], acc);  // th^p_r d^p_s
+                        acc = __ffma2_rn(svT[m][u], DP[u * fcells + cr], acc);    // th^p_s d^p_r
+                        acc2 = __ffma2_rn(TP[u * fcells + cr], svD[m][u], acc2);  // th^p_r d^p_s
                     }
                 } else {
                     for (int u = 0; u < P; ++u) {
                         acc = __ffma2_rn(TP[u * fcells + cs], DP[u * fcells + cr], acc);
-                        acc = __ffma2_rn(TP[u * fcells + cr], DP[u * fcells + cs], acc);
+                        acc2 = __ffma2_rn(TP[u * fcells + cr], DP[u * fcells + cs], acc2);
                     }
                 }
-                float Kh = fmaf(G * ds, dr * inv_m, acc.x + acc.y);
+                float Kh = fmaf(G * ds, dr * inv_m, (acc.x + acc.y) + (acc2.x + acc2.y));
                 const int si = sidx0 + 8 * m * W;
                 if (si == ss || si + oW == ss) Kh = fmaf(mh, ds * dr, Kh);
                 if ((ownb >> m) & 1u) hp = K > 0.f ? fmaf(Kh * K, (lk - __log2f(K)) * inv_c2, hp) : hp;

@@ -381,9 +381,10 @@ void lpnp_tape_destroy(lpnp_tape_t t);
  * otherwise).  m and 1/m are formed and read on the device, so the call queues all of
  * its work without waiting for the device (on an error it drains the stream first);
  * the handle reads m and 1/m back when a later call on it needs them on the host.
- * The iterations run their own kernels (the x-update of each writes the next recorded
- * state); the steps after the weight build are recorded once per configuration as a
- * CUDA graph and replayed. */
+ * The iterations run their own kernels (the dual step of each also takes the next
+ * x-step; the gradient it uses is formed beside the weight stream); every step, the
+ * weight build included, is recorded once per configuration as a CUDA graph (on a
+ * stream the tape owns) and replayed on the handle's stream. */
 dsgnlm_status lpnp_unrolled_forward(lpnp_tape_t tape, dsgnlm_t den, const float* y, const float* guide, int H,
                                     int W, int patch_r, int search_r, float bandwidth, int balance_passes,
                                     float alpha, float rho, int iters, float blur_sigma, int blur_r, float* x_out);
@@ -399,15 +400,19 @@ dsgnlm_status lpnp_backward(lpnp_tape_t tape, const float* x_bar, float* y_bar, 
 
 /* Batched forms of the two calls above (Algorithm 1 unrolled, with Eq. S1-S3 for W;
  * the paper has no derivatives) for `count` images of one size and one parameter
- * set.  tapes[i] and dens[i] must be distinct.  Each image runs on its handle's
- * stream, so handles on distinct streams overlap their images on the device.  y,
- * guide, x_out (and x_bar, y_bar, guide_bar) are host arrays of `count` device
- * pointers with the layouts of the single-image calls.  The images are queued from a
- * pool of host threads, one image per thread at a time; no image waits for the
- * device while it is queued (m and 1/m are formed and read on the device).  The
- * forward returns without waiting for the device; the backward synchronises each
- * stream once, at its end.  h_bar and rho_bar (host, optional) receive `count`
- * per-image values.
+ * set.  tapes[i] and dens[i] must be distinct.  y, guide, x_out (and x_bar, y_bar,
+ * guide_bar) are host arrays of `count` device pointers with the layouts of the
+ * single-image calls.  The images advance in lockstep: every step of the forward
+ * (the weight build of all images included) and of the backward is one launch over
+ * all images, queued on the first image's handle stream (dens[0], or the first tape's
+ * handle for the backward) after the work already queued on the other handles'
+ * streams; those streams then wait for the batch, so work queued on them afterwards
+ * follows it.  Each call's launch sequence is recorded as a CUDA graph the first time
+ * a configuration (sizes, radii, counts, buffers) is seen, on a stream the first tape
+ * owns, and replayed on the handle's stream afterwards.  No image waits for the device
+ * while it is queued (m and 1/m are formed and read on the device).  The forward
+ * returns without waiting for the device; the backward synchronises the stream once,
+ * at its end.  h_bar and rho_bar (host, optional) receive `count` per-image values.
  * Each handle's offset split (the slices of phase 1) is sized for `count` images at
  * once, so results equal the single-image calls up to the order in which W's partial
  * sums are added (bit for bit where the split is the same), and repeated calls give

@@ -246,8 +246,7 @@ def run_reference(args):
     """The reference arm: the FP64 oracle, as it stands, on the host's cores.  Each
     step solves one instance per core at once (a crop of the workload sized so that
     the whole run takes about two minutes)."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if _dist_env()[1] != 0:
         return
     import synthetic
     wl = synthetic.workload(WORKLOAD)
@@ -975,6 +974,30 @@ def _read_stream_gbs() -> float:
     return gbs
 
 
+def _dist_env():
+    """(world size, rank, local rank) of this process under torchrun; (1, 0, 0) alone."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _max_over_ranks(value: float, world: int, device) -> float:
+    """The largest of the ranks' values, on every rank (the slowest rank's time); the
+    value itself when the run has one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank: float, step_ms: float, world: int) -> float:
+    """Whole-job throughput: the units every rank processed in one step, over the step
+    time of the slowest rank (weak scaling: each rank holds its own instance)."""
+    return world * units_per_rank / (step_ms / 1e3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -986,9 +1009,7 @@ def run_ours(args):
     from paper_1901_06110_gb300 import dsgnlm as D
     from paper_1901_06110_gb300 import pipeline
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = _dist_env()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
@@ -1033,10 +1054,7 @@ def run_ours(args):
     clocks = sampler.stop()
     step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
     st, bal_updates, bal_res = solver.balance
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = _max_over_ranks(step_ms, world, "cuda")
 
     # --- per-kernel CUDA-event timings: the same steps again, each launch bracketed
     # by events on the library's stream (the events add a little time per launch,
@@ -1072,10 +1090,7 @@ def run_ours(args):
         e_e[k].record()
         e_e[k].synchronize()
     e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = _max_over_ranks(e2e_ms, world, "cuda")
     assert bool(torch.isfinite(solver.x).all())
 
     # --- a stream of different images of the workload's size: every step builds and
@@ -1103,7 +1118,7 @@ def run_ours(args):
     solver.run(y)  # leave the handle on the timed image
 
     n_mpix = H * W / 1e6
-    value = world * n_mpix / (step_ms / 1e3)
+    value = _job_rate(n_mpix, step_ms, world)
     nh = 2 * wl["search_r"] * (wl["search_r"] + 1)
     # algorithmic bytes of one phase-1 launch of W (x + u): each weight plane value
     # once (4 n_h B/px) plus the scaling d and z = x + u (8 B/px)
@@ -1132,7 +1147,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "wall_s_timed": wall,
         "clocks": clocks,
-        "e2e": {"value": world * n_mpix / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+        "e2e": {"value": _job_rate(n_mpix, e2e_ms, world), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": y.numel() * 4, "d2h_bytes_per_step": H * W * 4},
         "varying_inputs": {"images": len(ys), "steps": var_steps, "ms_per_step": var_ms,
                            "balance_passes_mean": var_passes / var_steps,
